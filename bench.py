@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the EMC hot path: pattern.rotation pairs/s per EMC iteration.
+
+One step = one whole EMC iteration (Algorithm 2.1: expansion, both E-step
+passes, M-step update, compression and the final division) over the frames
+resident in HBM, through libemc's emc_iteration. Default workload "emc64":
+64^3 grid, 64x64 detector with 10% of pixels masked, n=10 rotation sampling
+(50100 rotations), 20000 Poisson frames at 1 photon/pixel.
+
+value  = M_rot * M_data / (seconds per iteration), summed over GPUs (replicas)
+e2e    = the same metric through the public API with the frames copied from
+         pinned host memory and the new model read back every step
+roofline (dominant kernel), cpu_baseline (the FP64 oracle on host cores),
+clocks sampled during the timed region, per-form results (FP32 SIMT, BF16,
+BF16 split) are added to the single JSON line rank 0 prints.
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+the method here) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pattern·rotation pairs/s per EMC iteration: FP32 vs BF16-split vs learned"
+WORKLOAD_TEXT = {
+    "emc32": "32^3 grid, 32x32 detector, n=4 -> 3240 rotations, 1000 Poisson frames, "
+             "0.5 photons/pixel",
+    "emc64": "64^3 grid, 64x64 detector (10% masked), n=10 -> 50100 rotations, 20000 Poisson "
+             "frames, 1 photon/pixel",
+    "emc128": "128^3 grid, 128x128 detector, n=16 -> 204960 rotations, 100000 Poisson frames, "
+              "0.3 photons/pixel",
+}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3"}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16_split", choices=list(DTYPE))
+    ap.add_argument("--workload", default="emc64", choices=list(WORKLOAD_TEXT))
+    ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
+    ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
+    ap.add_argument("--forms", default="fp32,bf16",
+                    help="other precisions to time briefly (comma list, '' for none)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def workload(args, device):
+    from paper_1409_4256_gb300 import synth
+    cfg = dict(synth.WORKLOADS[args.workload])
+    if args.n_data:
+        cfg["n_data"] = args.n_data
+    if args.n_quat:
+        cfg["n_quat"] = args.n_quat
+    ds = synth.make_dataset(cfg["N"], cfg["D"], cfg["n_data"], cfg["mean_photons"],
+                            masked_fraction=cfg["masked_fraction"],
+                            fluence_sigma=cfg["fluence_sigma"], device=device)
+    return cfg, ds
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) > 8:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(cfg, ds, quat, w, n_rot_s, n_data_s):
+    """Time one oracle EMC iteration on a bounded sample; returns pairs/s."""
+    from oracle import oracle
+    oracle.build()
+    idx = np.linspace(0, quat.shape[0] - 1, n_rot_s).astype(np.int64)
+    q_s, w_s = quat[idx], w[idx] / w[idx].sum()
+    K = ds.K[:n_data_s].astype(np.float64)
+    grid = ds.model_start.astype(np.float32).astype(np.float64)
+    floor = 1e-10 * float(grid.mean())
+    t0 = time.perf_counter()
+    oracle.iteration(grid, q_s, w_s, ds.q, K, floor)
+    dt = time.perf_counter() - t0
+    return n_rot_s * n_data_s / dt, dt, oracle.num_threads()
+
+
+def sample_sizes(cfg, ds, n_rot):
+    # about 10-20 s of oracle work on 16 host cores (~1e6 pairs/s at 4096 pixels)
+    target_pairs = 1.2e7 * 2732.0 / max(ds.q.shape[0], 1)
+    n_data_s = min(ds.K.shape[0], 4000)
+    n_rot_s = int(min(n_rot, max(64, target_pairs / n_data_s)))
+    return n_rot_s, n_data_s
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1409_4256_gb300 import synth
+    from oracle import oracle
+    cfg, ds = workload(args, "cpu")
+    oracle.build()
+    quat, w = oracle.quat_generate(cfg["n_quat"])
+    n_rot_s, n_data_s = sample_sizes(cfg, ds, quat.shape[0])
+    n_rot_s = max(64, n_rot_s // 4)  # each step a quarter of the baseline sample
+    for _ in range(args.warmup):
+        oracle_sample(cfg, ds, quat, w, max(32, n_rot_s // 8), min(500, n_data_s))
+    times = []
+    for _ in range(args.steps):
+        v, dt, cores = oracle_sample(cfg, ds, quat, w, n_rot_s, n_data_s)
+        times.append(dt)
+    tot = sum(times)
+    value = args.steps * n_rot_s * n_data_s / tot
+    sample = (f"{n_rot_s} of {quat.shape[0]} rotations x {n_data_s} of {cfg['n_data']} frames "
+              f"per step, one full FP64 oracle iteration each")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+                       "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
+    """Warm up, then time `steps` iterations with CUDA events on `stream`."""
+    out = torch.empty_like(grid)
+    phases = {k: 0.0 for k in ("ms_expand", "ms_loglik", "ms_normalize", "ms_update",
+                                "ms_compress")}
+    kernels = 0
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            ctx.iteration(grid, out, stats=True, stream=stream)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lls = []
+        for _ in range(steps):
+            _, st = ctx.iteration(grid, out, stats=True, stream=stream)
+            for k in phases:
+                phases[k] += st[k]
+            kernels += st["kernels"]
+            lls.append(st["loglik"])
+            if st["device_status"] != 0:
+                raise RuntimeError(f"device status {st['device_status']}")
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return ms, {k: v / steps for k, v in phases.items()}, kernels, lls[-1]
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1409_4256_gb300 import build as libbuild
+    from paper_1409_4256_gb300 import emc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    libbuild.build()
+
+    cfg, ds = workload(args, str(dev))
+    quat, w = emc.quat_generate(cfg["n_quat"])
+    n_rot, n_data, n_pix = quat.shape[0], ds.K.shape[0], ds.q.shape[0]
+    pairs = n_rot * n_data
+    grid = torch.as_tensor(ds.model_start.astype(np.float32), device=dev)
+    floor = 1e-10 * float(ds.model_start.mean())
+    K_dev = torch.as_tensor(ds.K, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def make_ctx(prec):
+        c = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision=prec, w_floor=floor,
+                        device=str(dev), stream=stream)
+        c.set_frames(K_dev, stream=stream)
+        return c
+
+    ctx = make_ctx(args.precision)
+    with ClockSampler(local) as clk:
+        ms, phases, kernels, loglik = time_form(torch, emc, ctx, grid, args.steps, args.warmup,
+                                                stream, dist)
+    clocks = clk.summary()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * pairs / (ms * 1e-3)
+
+    # ---- e2e: host frames in, new model out, through the public API ----------
+    K_host = torch.as_tensor(ds.K).pin_memory()
+    out_host = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
+    out_dev = torch.empty_like(grid)
+    e2e_steps = max(2, min(args.steps, 5))
+    with torch.cuda.stream(stream):
+        for it in range(e2e_steps + 1):
+            if it == 1:
+                stream.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            K_dev.copy_(K_host, non_blocking=True)
+            ctx.set_frames(K_dev, stream=stream)
+            ctx.iteration(grid, out_dev, stats=False, stream=stream)
+            out_host.copy_(out_dev, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
+           "h2d_bytes_per_step": int(ds.K.nbytes), "d2h_bytes_per_step": int(out_host.numel() * 4)}
+
+    # ---- roofline of the dominant kernel ------------------------------------
+    pk, pk_src = peaks()
+    dom_ms = phases["ms_loglik"]
+    flops = 2.0 * n_pix * n_rot * n_data  # score contraction sum_i K_ik log W_ij
+    if args.precision == "fp32":
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max clock"}
+    else:
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "peak_source": f"{pk_src} bf16 sustained"}
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    roof.update({"kernel": "E-step pass 1 (scores + online log-sum-exp)", "achieved": achieved,
+                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": None, "algorithmic_flops_per_launch": flops})
+
+    # ---- other precision forms, briefly --------------------------------------
+    forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
+    for f in [x for x in args.forms.split(",") if x and x != args.precision]:
+        try:
+            c2 = make_ctx(f)
+            fms, fph, _, fll = time_form(torch, emc, c2, grid, 2, 1, stream, dist)
+            forms[f] = {"value": world * pairs / (fms * 1e-3), "ms_per_step": fms, "loglik": fll,
+                        "ms_loglik": fph["ms_loglik"]}
+            del c2
+        except Exception as e:  # a form that is not built yet is reported, not hidden
+            forms[f] = {"error": str(e)[:200]}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) --------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_rot_s, n_data_s = sample_sizes(cfg, ds, n_rot)
+        v, dt, cores = oracle_sample(cfg, ds, quat, w, n_rot_s, n_data_s)
+        cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"one FP64 oracle iteration over {n_rot_s} of {n_rot} rotations x "
+                         f"{n_data_s} of {n_data} frames ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE[args.precision], "data": "synthetic",
+                "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+                           "precision": args.precision, "rotations": n_rot, "frames": n_data,
+                           "pixels_used": n_pix, "parallelism": "replicas",
+                           "l2": "inputs larger than L2 (log W and frames re-read every step)"},
+                "phases_ms": phases, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": kernels, "forms": forms, "loglik": loglik}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * emc.h -- C ABI of libemc, the GB300 (sm_103a) EMC hot path.
+ *
+ * EMC (Expand-Maximize-Compress), Ekeberg, Engblom & Liu, arXiv:1409.4256,
+ * Algorithm 2.1, with the Poisson noise model of Sec. 2.2:
+ *   e-step  (Eq. 2.9)  W_ij  = sum_l f(p_l - R_j q_i) WW_l      (trilinear f)
+ *   E-step  (Eq. 2.4)  P_jk  = w_j T_jk / sum_j' w_j' T_j'k,
+ *                      log T_jk = sum_i K_ik log W_ij - W_ij    (log K! dropped)
+ *   M-step  (Eq. 2.11) Num_ij = sum_k P_jk K_ik,  den_j = sum_k P_jk
+ *   c-step  (Eq. 2.12) WW'_l = sum_ij f Num_ij / sum_ij f den_j
+ * Indices: i pixel, j rotation, k frame (pattern), l grid voxel.
+ *
+ * Conventions for every call
+ *  - Return value: EMC_OK (0) or a negative emc_status. Arguments, sizes and
+ *    alignments are checked on the host before anything is launched; a failed
+ *    check launches nothing. Calls taking a stream are asynchronous and
+ *    stream-ordered; problems found on the device (counts out of range, a
+ *    non-finite score, a bounded wait that gave up) are recorded in a device
+ *    status word that emc_ctx_status() reads.
+ *  - Ownership: every array argument is owned by the caller. Device arrays
+ *    are plain device pointers; host arrays are marked "host". The library
+ *    never allocates device memory: all scratch comes from the workspace the
+ *    caller passes to emc_ctx_create(), sized by emc_workspace_size().
+ *  - Grid layout: float [N][N][N], voxel (x, y, z) at (x*N + y)*N + z; the
+ *    zero frequency sits at index N/2 along each axis, and a point q maps to
+ *    grid coordinate q + N/2.
+ *  - Rotations: unit quaternions (w, x, y, z), R_j applied to pixel positions.
+ *  - Padding: pixels are padded to ld_pix (a multiple of 64, strictly more than
+ *    n_pix), frames to ld_data (a multiple of 256), rotation blocks to a
+ *    multiple of 128 rows. Sizes of every per-call buffer come from
+ *    emc_buffer_sizes().
+ */
+#ifndef EMC_H
+#define EMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* emc_stream; /* a cudaStream_t; NULL = legacy default */
+
+typedef enum emc_status {
+  EMC_OK = 0,
+  EMC_ERR_ARG = -1,         /* bad argument, size or alignment */
+  EMC_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+  EMC_ERR_NOMEM = -3,       /* workspace too small */
+  EMC_ERR_UNSUPPORTED = -4, /* input outside what the kernels handle exactly */
+  EMC_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+  EMC_ERR_NUMERIC = -6      /* non-finite or out-of-range value met on device */
+} emc_status;
+
+typedef enum emc_precision {
+  /* log W in FP32, FP32 SIMT contractions with compensated accumulation */
+  EMC_PREC_FP32 = 0,
+  /* log W rounded to one BF16, tcgen05 BF16 MMA with FP32 accumulation */
+  EMC_PREC_BF16 = 1,
+  /* log W = hi + mid + lo in BF16 with hi on a fixed 1/8 grid (accumulated
+   * exactly), tcgen05 BF16 MMA; P = hi + lo in BF16 for the update */
+  EMC_PREC_BF16_SPLIT = 2
+} emc_precision;
+
+typedef enum emc_compress_mode {
+  EMC_COMPRESS_DEFERRED = 0, /* Eq. 2.11-2.12: normalise after compression */
+  EMC_COMPRESS_IDW = 1       /* Eq. 2.5 per slice, then Eq. 2.10 */
+} emc_compress_mode;
+
+typedef struct emc_config {
+  int32_t N;             /* grid side, 4 <= N <= 1024 */
+  int32_t precision;     /* emc_precision */
+  int64_t n_pix;         /* used (unmasked, inside-support) pixels, >= 1 */
+  int64_t n_rot;         /* sampled rotations M_rot, >= 1 */
+  int64_t n_data;        /* frames M_data, >= 1 */
+  double w_floor;        /* expanded W_ij is floored at this value, > 0 */
+  int32_t compress_mode; /* emc_compress_mode */
+  int32_t flags;         /* reserved, 0 */
+  int64_t rot_chunk;     /* rotations per pass-2 chunk inside emc_iteration;
+                            0 = all rotations in one chunk */
+} emc_config;
+
+/* Per-call buffer sizes in bytes for a block of nrot rotations. */
+typedef struct emc_buffer_sizes {
+  int64_t ld_pix;      /* padded pixel stride (elements) */
+  int64_t ld_data;     /* padded frame stride (elements) */
+  int64_t rows;        /* nrot padded to a multiple of 128 */
+  size_t logw_bytes;   /* emc_expand output L */
+  size_t bias_bytes;   /* double[rows] */
+  size_t prob_bytes;   /* emc_normalize output P */
+  size_t num_bytes;    /* float[rows][ld_pix] */
+  size_t den_bytes;    /* float[rows] */
+  size_t lse_bytes;    /* double[ld_data] (each of lse_m, lse_s) */
+  size_t grid_bytes;   /* double[N^3] (each of g_num, g_den) */
+} emc_buffer_sizes;
+
+typedef struct emc_iter_stats {
+  double loglik;       /* sum_k lse_k (Poisson log-likelihood without log K!) */
+  double ms_expand, ms_loglik, ms_normalize, ms_update, ms_compress, ms_total;
+  int32_t device_status; /* emc_status recorded on the device (0 = OK) */
+  int32_t kernels;       /* kernel launches made by the call */
+} emc_iter_stats;
+
+typedef struct emc_ctx emc_ctx;
+
+/* Text for a status code (static storage). */
+const char* emc_status_string(int status);
+
+/* Rotation sampling of Eq. 2.7 (Sec. 2.2): the 600-cell with each cell
+ * divided n times gives M_rot = 10 (5 n^3 + n) rotations, q ~ -q identified.
+ * emc_quat_count returns that number (or -1 for n < 1).
+ * emc_quat_generate writes unit quaternions quat[cap][4] (host, w first,
+ * first non-zero component positive, sorted by round(q * 2^30)) and prior
+ * weights weight[cap] (host, sum 1; w_j ~ 1/|x_j|^4 for the flat lattice point
+ * x_j, or equal weights when uniform != 0). Returns the count written, or a
+ * negative emc_status (EMC_ERR_ARG if cap is too small). */
+int64_t emc_quat_count(int n);
+int64_t emc_quat_generate(int n, int uniform, double* quat, double* weight, int64_t cap);
+
+/* Buffer sizes for a configuration and a rotation block of nrot rows. */
+int emc_buffer_sizes_for(const emc_config* cfg, int64_t nrot, emc_buffer_sizes* out);
+
+/* Bytes of device workspace emc_ctx_create needs for cfg. */
+int emc_workspace_size(const emc_config* cfg, size_t* bytes);
+
+/* Create a context. q: host double[n_pix][3] pixel positions (Sec. 2.2,
+ * q_i on the Ewald sphere, grid units). quat: host double[n_rot][4].
+ * weight: host double[n_rot] prior weights w_j (> 0). workspace: device
+ * memory of at least emc_workspace_size() bytes, 256-byte aligned, owned by
+ * the caller and used until emc_ctx_destroy. Geometry and rotations are
+ * copied into the workspace on `stream`. */
+int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat,
+                   const double* weight, void* workspace, size_t workspace_bytes,
+                   emc_stream stream, emc_ctx** out);
+int emc_ctx_destroy(emc_ctx* ctx);
+
+/* Read (synchronously) and clear the device status word. */
+int emc_ctx_status(emc_ctx* ctx, int* device_status);
+
+/* Load frames K (Sec. 2.1, photon counts): device int32 [n_data][ld_k],
+ * ld_k >= n_pix, into the context's padded BF16 frame buffer. Counts must lie
+ * in [0, 256] (exact in BF16) and sum to below 65536 per frame; otherwise the
+ * device status becomes EMC_ERR_UNSUPPORTED. */
+int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stream);
+
+/* e-step, Eq. 2.9, for rotations [rot0, rot0 + nrot):
+ * W_ij = max(trilinear(grid, R_j q_i), w_floor);
+ * L (device): FP32 -> float[rows][ld_pix] = log W;
+ *             BF16 -> bf16[rows][ld_pix];
+ *             BF16_SPLIT -> bf16[3][rows][ld_pix] (hi, mid, lo planes);
+ *             padding columns and rows are written as 0.
+ * bias (device double[rows]) = log w_j - sum_i W_ij (-inf on padding rows). */
+int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void* L,
+               double* bias, emc_stream stream);
+
+/* E-step pass 1 (Eq. 2.4 denominators): for every frame k, the running
+ * (max m_k, sum s_k) with lse_k = m_k + log s_k over rotations in this block:
+ * S_jk = sum_i K_ik log W_ij + bias_j. lse_m, lse_s: device double[ld_data];
+ * accumulate = 0 starts from (m, s) = (-inf, 0), else merges into them. */
+int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, double* lse_m,
+               double* lse_s, int accumulate, emc_stream stream);
+
+/* E-step pass 2 (Eq. 2.4): P_jk = exp(S_jk - lse_k), scores recomputed.
+ * P (device): FP32 -> float[rows][ld_data]; BF16 / BF16_SPLIT ->
+ * bf16[2][rows][ld_data] (hi, lo planes, P = hi + lo; lo is 0 for BF16).
+ * Padding frames and rows are written as 0. */
+int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
+                  const double* lse_m, const double* lse_s, void* P, emc_stream stream);
+
+/* M-step, Eq. 2.11: Num (device float[rows][ld_pix]) = P K over frames;
+ * den (device float[rows]) = sum_k P_jk. */
+int emc_update(emc_ctx* ctx, const void* P, int64_t nrot, float* Num, float* den,
+               emc_stream stream);
+
+/* c-step accumulation, Eq. 2.12 (or Eq. 2.5 + 2.10 in IDW mode), for
+ * rotations [rot0, rot0 + nrot): g_num_l += sum_ij f Num_ij,
+ * g_den_l += sum_ij f den_j. g_num, g_den: device double[N^3]; accumulate = 0
+ * zeroes them first. */
+int emc_compress(emc_ctx* ctx, int64_t rot0, int64_t nrot, const float* Num, const float* den,
+                 double* g_num, double* g_den, int accumulate, emc_stream stream);
+
+/* Final division of Eq. 2.12: grid_out_l = g_num_l / g_den_l where
+ * g_den_l > 0, else grid_prev_l. grid_out may alias grid_prev. */
+int emc_finalize(emc_ctx* ctx, const double* g_num, const double* g_den, const float* grid_prev,
+                 float* grid_out, emc_stream stream);
+
+/* One pass of Algorithm 2.1 on the loaded frames, using the workspace for
+ * every intermediate: e-step, E-step (two passes), M-step and c-step over
+ * rotation chunks of cfg.rot_chunk. grid_out may not alias grid_in.
+ * stats (host, may be NULL) is filled after the call synchronises `stream`. */
+int emc_iteration(emc_ctx* ctx, const float* grid_in, float* grid_out, emc_iter_stats* stats,
+                  emc_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMC_H */

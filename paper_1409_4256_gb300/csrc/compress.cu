@@ -1,0 +1,62 @@
+// compress.cu -- c-step of EMC (Eq. 2.12; Eq. 2.5 + 2.10 in IDW mode).
+//
+// One CTA per rotation row j, threads over pixels. Each (i, j) recomputes the
+// double-float grid point p = R_j q_i + N/2 (the same weights f(p_l - R_j q_i)
+// that expansion used) and scatters f * Num_ij into g_num and f * den_j into
+// g_den with FP64 atomics resolved in L2 (the N^3 FP64 grids, 2 MB at 64^3,
+// stay L2-resident). The paper's insert_slices kernel also used one block
+// per slice.
+#include "emc_common.cuh"
+#include "emc_internal.h"
+
+namespace emc {
+
+constexpr int kCompressThreads = 256;
+
+__global__ void __launch_bounds__(kCompressThreads)
+    compress_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
+                    int64_t ld_pix, int N, const double* __restrict__ quat,
+                    const float* __restrict__ Num, const float* __restrict__ den, int mode,
+                    double* __restrict__ g_num, double* __restrict__ g_den) {
+  const int64_t row = blockIdx.x;
+  __shared__ RotDF R;
+  const float dj = den[row];
+  if (mode == EMC_COMPRESS_IDW && !(dj > 0.f)) return;
+  if (threadIdx.x == 0) quat_to_rot_df(quat + 4 * row, &R);
+  __syncthreads();
+  const float half_n = 0.5f * (float)N;
+  const int64_t nn = (int64_t)N * N;
+  const float* Nr = Num + row * ld_pix;
+  const float inv_d = (mode == EMC_COMPRESS_IDW) ? 1.0f / dj : 1.0f;
+  const float dv = (mode == EMC_COMPRESS_IDW) ? 1.0f : dj;
+  for (int64_t i = threadIdx.x; i < n_pix; i += kCompressThreads) {
+    float4 a = qh[i], b = ql[i];
+    if (a.w == 0.f) continue;
+    int f[3];
+    float t[3];
+    rotate_to_grid(R, a, b, half_n, f, t);
+    const float v = Nr[i] * inv_d;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      int x = f[0] + ((c >> 2) & 1), y = f[1] + ((c >> 1) & 1), z = f[2] + (c & 1);
+      if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= N) continue;
+      float w = (((c >> 2) & 1) ? t[0] : 1.f - t[0]) * (((c >> 1) & 1) ? t[1] : 1.f - t[1]) *
+                ((c & 1) ? t[2] : 1.f - t[2]);
+      if (w == 0.f) continue;
+      int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
+      atomicAdd(g_num + l, (double)w * (double)v);
+      atomicAdd(g_den + l, (double)w * (double)dv);
+    }
+  }
+}
+
+cudaError_t launch_compress(const Geom& g, const double* quat, int64_t nrot, const float* Num,
+                            const float* den, int mode, double* g_num, double* g_den,
+                            cudaStream_t s) {
+  if (nrot <= 0) return cudaSuccess;
+  compress_kernel<<<(unsigned)nrot, kCompressThreads, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
+                                                             quat, Num, den, mode, g_num, g_den);
+  return cudaGetLastError();
+}
+
+}  // namespace emc

@@ -1,0 +1,484 @@
+// emc_abi.cu -- the C ABI of include/emc.h: context, workspace layout,
+// argument checks and the stream-ordered step calls.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "emc_common.cuh"
+#include "emc_internal.h"
+
+using namespace emc;
+
+namespace {
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
+  size_t qh, ql, quat, logw, Kb, status, L, bias, lse_m, lse_s, part_m, part_s, P, Num, den, gnum,
+      gden, scalar, total;
+};
+
+int planes_L(int prec) { return prec == EMC_PREC_BF16_SPLIT ? 3 : 1; }
+size_t elem_L(int prec) { return prec == EMC_PREC_FP32 ? 4 : 2; }
+int planes_P(int prec) { return prec == EMC_PREC_FP32 ? 1 : 2; }
+size_t elem_P(int prec) { return prec == EMC_PREC_FP32 ? 4 : 2; }
+
+int check_config(const emc_config* c) {
+  if (!c) return EMC_ERR_ARG;
+  if (c->N < 4 || c->N > 1024) return EMC_ERR_ARG;
+  if (c->n_pix < 1 || c->n_rot < 1 || c->n_data < 1) return EMC_ERR_ARG;
+  if (c->n_pix > (1LL << 24) || c->n_rot > (1LL << 31) || c->n_data > (1LL << 31))
+    return EMC_ERR_ARG;
+  if (c->precision < EMC_PREC_FP32 || c->precision > EMC_PREC_BF16_SPLIT) return EMC_ERR_ARG;
+  if (c->compress_mode != EMC_COMPRESS_DEFERRED && c->compress_mode != EMC_COMPRESS_IDW)
+    return EMC_ERR_ARG;
+  if (!(c->w_floor > 0.0) || !isfinite(c->w_floor)) return EMC_ERR_ARG;
+  if (c->precision == EMC_PREC_BF16_SPLIT && log(c->w_floor) < (double)kHiMin)
+    return EMC_ERR_UNSUPPORTED;
+  if (c->rot_chunk < 0 || c->flags != 0) return EMC_ERR_ARG;
+  return EMC_OK;
+}
+
+Layout make_layout(const emc_config* c) {
+  Layout y;
+  y.ld_pix = round_up(c->n_pix + 1, 64);
+  y.ld_data = round_up(c->n_data, 256);
+  y.rows = round_up(c->n_rot, 128);
+  y.chunk_rows = c->rot_chunk > 0 ? std::min(round_up(c->rot_chunk, 128), y.rows) : y.rows;
+  y.part_tiles = y.rows / 64;
+  const int p = c->precision;
+  const int64_t nvox = (int64_t)c->N * c->N * c->N;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  y.qh = take(sizeof(float4) * y.ld_pix);
+  y.ql = take(sizeof(float4) * y.ld_pix);
+  y.quat = take(sizeof(double) * 4 * c->n_rot);
+  y.logw = take(sizeof(double) * c->n_rot);
+  y.Kb = take(2 * (size_t)y.ld_data * y.ld_pix);
+  y.status = take(256);
+  y.L = take(planes_L(p) * elem_L(p) * (size_t)y.rows * y.ld_pix);
+  y.bias = take(sizeof(double) * y.rows);
+  y.lse_m = take(sizeof(double) * y.ld_data);
+  y.lse_s = take(sizeof(double) * y.ld_data);
+  y.part_m = take(sizeof(double) * (size_t)y.part_tiles * y.ld_data);
+  y.part_s = take(sizeof(float) * (size_t)y.part_tiles * y.ld_data);
+  y.P = take(planes_P(p) * elem_P(p) * (size_t)y.chunk_rows * y.ld_data);
+  y.Num = take(sizeof(float) * (size_t)y.chunk_rows * y.ld_pix);
+  y.den = take(sizeof(float) * y.chunk_rows);
+  y.gnum = take(sizeof(double) * nvox);
+  y.gden = take(sizeof(double) * nvox);
+  y.scalar = take(256);
+  y.total = o;
+  return y;
+}
+
+#define CU(x)                                      \
+  do {                                             \
+    if ((x) != cudaSuccess) return EMC_ERR_CUDA;   \
+  } while (0)
+
+}  // namespace
+
+struct emc_ctx {
+  emc_config cfg;
+  Layout lay;
+  char* ws;
+  size_t ws_bytes;
+  Geom geom;
+  double* quat;
+  double* logw;
+  uint16_t* Kb;
+  int32_t* status;
+  bool frames_loaded;
+  cudaEvent_t ev[8];
+  int kernels;  // launches made by the last emc_iteration
+};
+
+extern "C" {
+
+const char* emc_status_string(int status) {
+  switch (status) {
+    case EMC_OK: return "ok";
+    case EMC_ERR_ARG: return "invalid argument, size or alignment";
+    case EMC_ERR_CUDA: return "CUDA runtime error";
+    case EMC_ERR_NOMEM: return "workspace too small";
+    case EMC_ERR_UNSUPPORTED: return "input outside the exactly handled range";
+    case EMC_ERR_TIMEOUT: return "bounded device wait gave up";
+    case EMC_ERR_NUMERIC: return "non-finite or out-of-range value on device";
+    default: return "unknown status";
+  }
+}
+
+int64_t emc_quat_count(int n) {
+  if (n < 1) return -1;
+  return 10LL * (5LL * n * n * n + n);
+}
+
+int64_t emc_quat_generate(int n, int uniform, double* quat, double* weight, int64_t cap) {
+  return emc::quat_generate(n, uniform, quat, weight, cap);
+}
+
+int emc_buffer_sizes_for(const emc_config* cfg, int64_t nrot, emc_buffer_sizes* out) {
+  int st = check_config(cfg);
+  if (st) return st;
+  if (!out || nrot < 1 || nrot > cfg->n_rot) return EMC_ERR_ARG;
+  Layout y = make_layout(cfg);
+  const int p = cfg->precision;
+  out->ld_pix = y.ld_pix;
+  out->ld_data = y.ld_data;
+  out->rows = round_up(nrot, 128);
+  out->logw_bytes = planes_L(p) * elem_L(p) * (size_t)out->rows * y.ld_pix;
+  out->bias_bytes = sizeof(double) * out->rows;
+  out->prob_bytes = planes_P(p) * elem_P(p) * (size_t)out->rows * y.ld_data;
+  out->num_bytes = sizeof(float) * (size_t)out->rows * y.ld_pix;
+  out->den_bytes = sizeof(float) * out->rows;
+  out->lse_bytes = sizeof(double) * y.ld_data;
+  out->grid_bytes = sizeof(double) * (size_t)cfg->N * cfg->N * cfg->N;
+  return EMC_OK;
+}
+
+int emc_workspace_size(const emc_config* cfg, size_t* bytes) {
+  int st = check_config(cfg);
+  if (st) return st;
+  if (!bytes) return EMC_ERR_ARG;
+  *bytes = make_layout(cfg).total;
+  return EMC_OK;
+}
+
+int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, const double* weight,
+                   void* workspace, size_t workspace_bytes, emc_stream stream, emc_ctx** out) {
+  int st = check_config(cfg);
+  if (st) return st;
+  if (!q || !quat || !weight || !workspace || !out) return EMC_ERR_ARG;
+  if (((uintptr_t)workspace) & 255) return EMC_ERR_ARG;
+  Layout y = make_layout(cfg);
+  if (workspace_bytes < y.total) return EMC_ERR_NOMEM;
+  for (int64_t j = 0; j < cfg->n_rot; j++) {
+    if (!(weight[j] > 0.0) || !isfinite(weight[j])) return EMC_ERR_ARG;
+    double n2 = 0;
+    for (int c = 0; c < 4; c++) n2 += quat[4 * j + c] * quat[4 * j + c];
+    if (fabs(n2 - 1.0) > 1e-6) return EMC_ERR_ARG;
+  }
+  const double qlim = 0.5 * cfg->N;
+  for (int64_t i = 0; i < cfg->n_pix; i++)
+    for (int c = 0; c < 3; c++)
+      if (!isfinite(q[3 * i + c]) || fabs(q[3 * i + c]) > qlim) return EMC_ERR_ARG;
+
+  // host staging of the small geometry arrays
+  std::vector<float4> qh(y.ld_pix), ql(y.ld_pix);
+  for (int64_t i = 0; i < y.ld_pix; i++) {
+    float4 a = make_float4(0, 0, 0, 0), b = make_float4(0, 0, 0, 0);
+    if (i < cfg->n_pix) {
+      float h[3], l[3];
+      for (int c = 0; c < 3; c++) {
+        h[c] = (float)q[3 * i + c];
+        l[c] = (float)(q[3 * i + c] - (double)h[c]);
+      }
+      a = make_float4(h[0], h[1], h[2], 1.f);
+      b = make_float4(l[0], l[1], l[2], 0.f);
+    }
+    qh[i] = a;
+    ql[i] = b;
+  }
+  std::vector<double> lw(cfg->n_rot);
+  for (int64_t j = 0; j < cfg->n_rot; j++) lw[j] = log(weight[j]);
+
+  emc_ctx* c = (emc_ctx*)calloc(1, sizeof(emc_ctx));
+  if (!c) return EMC_ERR_NOMEM;
+  c->cfg = *cfg;
+  c->lay = y;
+  c->ws = (char*)workspace;
+  c->ws_bytes = workspace_bytes;
+  c->geom.qh = (const float4*)(c->ws + y.qh);
+  c->geom.ql = (const float4*)(c->ws + y.ql);
+  c->geom.n_pix = cfg->n_pix;
+  c->geom.ld_pix = y.ld_pix;
+  c->geom.N = cfg->N;
+  c->quat = (double*)(c->ws + y.quat);
+  c->logw = (double*)(c->ws + y.logw);
+  c->Kb = (uint16_t*)(c->ws + y.Kb);
+  c->status = (int32_t*)(c->ws + y.status);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool ok = true;
+  ok &= cudaMemcpyAsync(c->ws + y.qh, qh.data(), sizeof(float4) * y.ld_pix,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.ql, ql.data(), sizeof(float4) * y.ld_pix,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->quat, quat, sizeof(double) * 4 * cfg->n_rot, cudaMemcpyHostToDevice,
+                        s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->logw, lw.data(), sizeof(double) * cfg->n_rot, cudaMemcpyHostToDevice,
+                        s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->status, 0, 256, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;  // host staging buffers go out of scope
+  for (int e = 0; e < 8 && ok; e++) ok &= cudaEventCreate(&c->ev[e]) == cudaSuccess;
+  if (!ok) {
+    for (int e = 0; e < 8; e++)
+      if (c->ev[e]) cudaEventDestroy(c->ev[e]);
+    free(c);
+    return EMC_ERR_CUDA;
+  }
+  *out = c;
+  return EMC_OK;
+}
+
+int emc_ctx_destroy(emc_ctx* ctx) {
+  if (!ctx) return EMC_ERR_ARG;
+  for (int e = 0; e < 8; e++)
+    if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
+  free(ctx);
+  return EMC_OK;
+}
+
+int emc_ctx_status(emc_ctx* ctx, int* device_status) {
+  if (!ctx || !device_status) return EMC_ERR_ARG;
+  int32_t v = 0;
+  CU(cudaMemcpy(&v, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  CU(cudaMemset(ctx->status, 0, sizeof(int32_t)));
+  *device_status = v;
+  return EMC_OK;
+}
+
+int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stream) {
+  if (!ctx || !K || ld_k < ctx->cfg.n_pix) return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb,
+                        ctx->status, (cudaStream_t)stream));
+  ctx->frames_loaded = true;
+  return EMC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal step implementations (used by both the step calls and the fused
+// iteration).
+// ---------------------------------------------------------------------------
+namespace {
+
+int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L, double* bias,
+              cudaStream_t s) {
+  const int64_t rows = round_up(nrot, 128);
+  Planes p{L, rows * c->lay.ld_pix, c->lay.ld_pix};
+  CU(launch_expand(c->geom, grid, c->quat + 4 * rot0, c->logw + rot0, nrot, rows,
+                   c->cfg.precision, (float)c->cfg.w_floor, p, bias, c->status, s));
+  return EMC_OK;
+}
+
+// L is the full block [planes][rows][ld_pix] (plane stride = Lrows * ld_pix);
+// the rows processed here start at row_off inside it.
+int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const double* bias,
+              int64_t nrot, double* lse_m, double* lse_s, int accumulate, cudaStream_t s) {
+  const Layout& y = c->lay;
+  const int64_t rows = round_up(nrot, 128);
+  double* pm = (double*)(c->ws + y.part_m);
+  float* ps = (float*)(c->ws + y.part_s);
+  int64_t tiles;
+  if (c->cfg.precision == EMC_PREC_FP32) {
+    const float* Lf = (const float*)L + row_off * y.ld_pix;
+    CU(launch_simt_pass1(Lf, y.ld_pix, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, pm, ps, s));
+    tiles = simt_pass1_tiles(rows);
+  } else {
+    Planes p{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
+    int nterms = c->cfg.precision == EMC_PREC_BF16_SPLIT ? 3 : 1;
+    CU(launch_tc_pass1(p, nterms, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix, pm, ps,
+                       c->status, s));
+    tiles = tc_pass1_tiles(rows);
+  }
+  CU(launch_lse_merge(pm, ps, tiles, y.ld_data, c->cfg.n_data, lse_m, lse_s, accumulate,
+                      c->status, s));
+  return EMC_OK;
+}
+
+int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const double* bias,
+                 int64_t nrot, const double* lse_m, const double* lse_s, void* P, int64_t Prows,
+                 cudaStream_t s) {
+  const Layout& y = c->lay;
+  const int64_t rows = round_up(nrot, 128);
+  if (c->cfg.precision == EMC_PREC_FP32) {
+    const float* Lf = (const float*)L + row_off * y.ld_pix;
+    CU(launch_simt_normalize(Lf, y.ld_pix, bias, rows, nrot, c->Kb, y.ld_data, c->cfg.n_data,
+                             lse_m, lse_s, (float*)P, s));
+  } else {
+    Planes lp{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
+    Planes pp{P, Prows * y.ld_data, y.ld_data};
+    int nterms = c->cfg.precision == EMC_PREC_BF16_SPLIT ? 3 : 1;
+    CU(launch_tc_normalize(lp, nterms, bias, rows, nrot, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix,
+                           lse_m, lse_s, pp, c->status, s));
+  }
+  return EMC_OK;
+}
+
+int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num, float* den,
+              cudaStream_t s) {
+  const Layout& y = c->lay;
+  const int64_t rows = round_up(nrot, 128);
+  if (c->cfg.precision == EMC_PREC_FP32) {
+    CU(launch_simt_update((const float*)P, y.ld_data, rows, c->Kb, y.ld_pix, c->cfg.n_pix, Num,
+                          den, s));
+  } else {
+    Planes pp{(void*)P, Prows * y.ld_data, y.ld_data};
+    CU(launch_tc_update(pp, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num, den, c->status,
+                        s));
+  }
+  return EMC_OK;
+}
+
+int check_rot_range(emc_ctx* c, int64_t rot0, int64_t nrot) {
+  if (rot0 < 0 || nrot < 1 || rot0 + nrot > c->cfg.n_rot) return EMC_ERR_ARG;
+  return EMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void* L, double* bias,
+               emc_stream stream) {
+  if (!ctx || !grid || !L || !bias) return EMC_ERR_ARG;
+  if (check_rot_range(ctx, rot0, nrot)) return EMC_ERR_ARG;
+  return do_expand(ctx, grid, rot0, nrot, L, bias, (cudaStream_t)stream);
+}
+
+int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, double* lse_m,
+               double* lse_s, int accumulate, emc_stream stream) {
+  if (!ctx || !L || !bias || !lse_m || !lse_s) return EMC_ERR_ARG;
+  if (check_rot_range(ctx, 0, nrot)) return EMC_ERR_ARG;
+  if (!ctx->frames_loaded) return EMC_ERR_ARG;
+  return do_loglik(ctx, L, round_up(nrot, 128), 0, bias, nrot, lse_m, lse_s, accumulate,
+                   (cudaStream_t)stream);
+}
+
+int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
+                  const double* lse_m, const double* lse_s, void* P, emc_stream stream) {
+  if (!ctx || !L || !bias || !lse_m || !lse_s || !P) return EMC_ERR_ARG;
+  if (check_rot_range(ctx, 0, nrot)) return EMC_ERR_ARG;
+  if (!ctx->frames_loaded) return EMC_ERR_ARG;
+  const int64_t rows = round_up(nrot, 128);
+  return do_normalize(ctx, L, rows, 0, bias, nrot, lse_m, lse_s, P, rows, (cudaStream_t)stream);
+}
+
+int emc_update(emc_ctx* ctx, const void* P, int64_t nrot, float* Num, float* den,
+               emc_stream stream) {
+  if (!ctx || !P || !Num || !den) return EMC_ERR_ARG;
+  if (check_rot_range(ctx, 0, nrot)) return EMC_ERR_ARG;
+  if (!ctx->frames_loaded) return EMC_ERR_ARG;
+  return do_update(ctx, P, round_up(nrot, 128), nrot, Num, den, (cudaStream_t)stream);
+}
+
+int emc_compress(emc_ctx* ctx, int64_t rot0, int64_t nrot, const float* Num, const float* den,
+                 double* g_num, double* g_den, int accumulate, emc_stream stream) {
+  if (!ctx || !Num || !den || !g_num || !g_den) return EMC_ERR_ARG;
+  if (check_rot_range(ctx, rot0, nrot)) return EMC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t gb = sizeof(double) * (size_t)ctx->cfg.N * ctx->cfg.N * ctx->cfg.N;
+  if (!accumulate) {
+    CU(cudaMemsetAsync(g_num, 0, gb, s));
+    CU(cudaMemsetAsync(g_den, 0, gb, s));
+  }
+  CU(launch_compress(ctx->geom, ctx->quat + 4 * rot0, nrot, Num, den, ctx->cfg.compress_mode,
+                     g_num, g_den, s));
+  return EMC_OK;
+}
+
+int emc_finalize(emc_ctx* ctx, const double* g_num, const double* g_den, const float* grid_prev,
+                 float* grid_out, emc_stream stream) {
+  if (!ctx || !g_num || !g_den || !grid_prev || !grid_out) return EMC_ERR_ARG;
+  const int64_t nvox = (int64_t)ctx->cfg.N * ctx->cfg.N * ctx->cfg.N;
+  CU(launch_finalize(nvox, g_num, g_den, grid_prev, grid_out, (cudaStream_t)stream));
+  return EMC_OK;
+}
+
+int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_stats* stats,
+                  emc_stream stream) {
+  if (!c || !grid_in || !grid_out || grid_in == grid_out) return EMC_ERR_ARG;
+  if (!c->frames_loaded) return EMC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Layout& y = c->lay;
+  const int64_t n_rot = c->cfg.n_rot;
+  void* L = c->ws + y.L;
+  double* bias = (double*)(c->ws + y.bias);
+  double* lse_m = (double*)(c->ws + y.lse_m);
+  double* lse_s = (double*)(c->ws + y.lse_s);
+  void* P = c->ws + y.P;
+  float* Num = (float*)(c->ws + y.Num);
+  float* den = (float*)(c->ws + y.den);
+  double* gn = (double*)(c->ws + y.gnum);
+  double* gd = (double*)(c->ws + y.gden);
+  double* ll = (double*)(c->ws + y.scalar);
+  const size_t gb = sizeof(double) * (size_t)c->cfg.N * c->cfg.N * c->cfg.N;
+  const size_t Lelem = elem_L(c->cfg.precision);
+  int kernels = 0;
+  int st;
+
+  if (stats) CU(cudaEventRecord(c->ev[0], s));
+  if ((st = do_expand(c, grid_in, 0, n_rot, L, bias, s))) return st;
+  kernels++;
+  if (stats) CU(cudaEventRecord(c->ev[1], s));
+  if ((st = do_loglik(c, L, y.rows, 0, bias, n_rot, lse_m, lse_s, 0, s))) return st;
+  CU(launch_loglik_sum(lse_m, lse_s, c->cfg.n_data, ll, s));
+  kernels += 3;
+  if (stats) CU(cudaEventRecord(c->ev[2], s));
+  CU(cudaMemsetAsync(gn, 0, gb, s));
+  CU(cudaMemsetAsync(gd, 0, gb, s));
+  float t_norm = 0.f, t_upd = 0.f, t_cmp = 0.f;
+  for (int64_t r0 = 0; r0 < n_rot; r0 += y.chunk_rows) {
+    const int64_t nr = std::min(y.chunk_rows, n_rot - r0);
+    const int64_t crows = round_up(nr, 128);
+    if (stats) CU(cudaEventRecord(c->ev[3], s));
+    if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lse_m, lse_s, P, crows, s))) return st;
+    if (stats) CU(cudaEventRecord(c->ev[4], s));
+    if ((st = do_update(c, P, crows, nr, Num, den, s))) return st;
+    if (stats) CU(cudaEventRecord(c->ev[5], s));
+    CU(launch_compress(c->geom, c->quat + 4 * r0, nr, Num, den, c->cfg.compress_mode, gn, gd, s));
+    if (stats) CU(cudaEventRecord(c->ev[6], s));
+    kernels += 3;
+    if (stats) {
+      // chunk timings need a host wait per chunk; only when stats are asked for
+      float a = 0, b = 0, d = 0;
+      CU(cudaEventSynchronize(c->ev[6]));
+      CU(cudaEventElapsedTime(&a, c->ev[3], c->ev[4]));
+      CU(cudaEventElapsedTime(&b, c->ev[4], c->ev[5]));
+      CU(cudaEventElapsedTime(&d, c->ev[5], c->ev[6]));
+      t_norm += a;
+      t_upd += b;
+      t_cmp += d;
+    }
+  }
+  (void)Lelem;
+  if (stats) CU(cudaEventRecord(c->ev[3], s));
+  CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, grid_in, grid_out, s));
+  kernels++;
+  if (stats) CU(cudaEventRecord(c->ev[7], s));
+  c->kernels = kernels;
+  if (stats) {
+    CU(cudaEventSynchronize(c->ev[7]));
+    float te = 0, tl = 0, tf = 0, tt = 0;
+    CU(cudaEventElapsedTime(&te, c->ev[0], c->ev[1]));
+    CU(cudaEventElapsedTime(&tl, c->ev[1], c->ev[2]));
+    CU(cudaEventElapsedTime(&tf, c->ev[3], c->ev[7]));
+    CU(cudaEventElapsedTime(&tt, c->ev[0], c->ev[7]));
+    memset(stats, 0, sizeof(*stats));
+    stats->ms_expand = te;
+    stats->ms_loglik = tl;
+    stats->ms_normalize = t_norm;
+    stats->ms_update = t_upd;
+    stats->ms_compress = t_cmp + tf;
+    stats->ms_total = tt;
+    CU(cudaMemcpy(&stats->loglik, ll, sizeof(double), cudaMemcpyDeviceToHost));
+    int32_t dst = 0;
+    CU(cudaMemcpy(&dst, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    stats->device_status = dst;
+    stats->kernels = kernels;
+  }
+  return EMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// emc_common.cuh -- device helpers shared by the libemc kernels (sm_103a).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/emc.h"
+
+namespace emc {
+
+// ---------------------------------------------------------------------------
+// Device status word: the first error recorded wins.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float ("f2") arithmetic: value = h + l with |l| <= ulp(h)/2.
+// Rotated pixel coordinates need ~1e-8 voxel accuracy (the scores of Eq. 2.3
+// react to log W at the 1e-7 level), which plain FP32 (ulp(64) = 7.6e-6)
+// cannot give; FP64 is rare on this part, so pairs of FP32 are used instead.
+// ---------------------------------------------------------------------------
+struct f2 {
+  float h, l;
+};
+
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = a + b;
+  float e = b - (s - a);
+  return {s, e};
+}
+__device__ __forceinline__ f2 two_prod(float a, float b) {
+  float p = a * b;
+  float e = fmaf(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ f2 df_mul(f2 a, f2 b) {
+  f2 p = two_prod(a.h, b.h);
+  p.l = fmaf(a.h, b.l, fmaf(a.l, b.h, p.l));
+  return fast_two_sum(p.h, p.l);
+}
+__device__ __forceinline__ f2 df_add(f2 a, f2 b) {
+  f2 s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return fast_two_sum(s.h, s.l);
+}
+
+// Rotation R (row-major 3x3) as double-float pairs.
+struct RotDF {
+  f2 r[9];
+};
+
+// Hamilton rotation matrix of a unit quaternion (w, x, y, z), in FP64, split.
+__device__ __forceinline__ void quat_to_rot_df(const double* q, RotDF* out) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double R[9];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+  for (int t = 0; t < 9; t++) {
+    float h = (float)R[t];
+    out->r[t].h = h;
+    out->r[t].l = (float)(R[t] - (double)h);
+  }
+}
+
+// Grid coordinate p = R q + N/2 of one pixel, split into the integer corner
+// f (floor) and the fraction t in [0, 1], both accurate to ~1e-9 voxel.
+__device__ __forceinline__ void rotate_to_grid(const RotDF& R, float4 qh, float4 ql, float half_n,
+                                               int* f, float* t) {
+  f2 qv[3] = {{qh.x, ql.x}, {qh.y, ql.y}, {qh.z, ql.z}};
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    f2 s = {half_n, 0.f};
+#pragma unroll
+    for (int b = 0; b < 3; b++) s = df_add(s, df_mul(R.r[3 * a + b], qv[b]));
+    float fl = floorf(s.h);
+    float fr = (s.h - fl) + s.l;  // s.h - fl is exact
+    if (fr < 0.f) {
+      fl -= 1.f;
+      fr += 1.f;
+    } else if (fr >= 1.f) {
+      fl += 1.f;
+      fr -= 1.f;
+    }
+    f[a] = (int)fl;
+    t[a] = fminf(fmaxf(fr, 0.f), 1.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// BF16 helpers (round to nearest even).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  __nv_bfloat16 b = __float2bfloat16_rn(x);
+  return *reinterpret_cast<uint16_t*>(&b);
+}
+__device__ __forceinline__ float bf16_val(uint16_t u) {
+  return __uint_as_float(((uint32_t)u) << 16);
+}
+
+// The fixed grid of the hi term of the three-term split: multiples of 1/8 in
+// [-32, 32); every such value has at most 8 significant bits (exact in BF16)
+// and sums of (integer count <= 256) x (hi) stay on the 1/8 grid, so FP32
+// accumulates them exactly while |sum| < 2^21.
+constexpr float kHiScale = 8.0f;
+constexpr float kHiMin = -32.0f;
+constexpr float kHiMax = 32.0f - 0.125f;
+
+}  // namespace emc

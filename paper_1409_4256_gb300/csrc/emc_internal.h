@@ -1,0 +1,78 @@
+// emc_internal.h -- launchers shared between the ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/emc.h"
+
+namespace emc {
+
+// Pixel geometry as stored in the workspace: positions q_i split into FP32
+// hi/lo pairs, w component 1 for a used pixel and 0 for padding.
+struct Geom {
+  const float4* qh;
+  const float4* ql;
+  int64_t n_pix;
+  int64_t ld_pix;
+  int N;
+};
+
+// A block of rows of a (possibly multi-plane) row-major matrix.
+struct Planes {
+  void* base;            // first row of plane 0
+  int64_t plane_stride;  // elements between planes
+  int64_t ld;            // elements between rows
+};
+
+cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                               int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int32_t* status,
+                               cudaStream_t s);
+
+cudaError_t launch_expand(const Geom& g, const float* grid, const double* quat,
+                          const double* logw, int64_t nrot, int64_t rows, int precision,
+                          float w_floor, Planes L, double* bias, int32_t* status, cudaStream_t s);
+
+// FP32 SIMT forms (precision EMC_PREC_FP32).
+cudaError_t launch_simt_pass1(const float* L, int64_t ld_pix, const double* bias, int64_t rows,
+                              const uint16_t* Kb, int64_t ld_data, int64_t n_data,
+                              double* part_m, float* part_s, cudaStream_t s);
+cudaError_t launch_simt_normalize(const float* L, int64_t ld_pix, const double* bias, int64_t rows,
+                                  int64_t nrot, const uint16_t* Kb, int64_t ld_data,
+                                  int64_t n_data, const double* lse_m, const double* lse_s,
+                                  float* P, cudaStream_t s);
+cudaError_t launch_simt_update(const float* P, int64_t ld_data, int64_t rows, const uint16_t* Kb,
+                               int64_t ld_pix, int64_t n_pix, float* Num, float* den,
+                               cudaStream_t s);
+int64_t simt_pass1_tiles(int64_t rows);
+
+// Merge of per-tile (max, sum) pairs into the running per-frame (m, s).
+cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
+                             int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
+                             int accumulate, int32_t* status, cudaStream_t s);
+cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
+                              double* out, cudaStream_t s);
+
+// tcgen05 forms (precision EMC_PREC_BF16 / EMC_PREC_BF16_SPLIT).
+struct TcPlan;
+cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int64_t rows,
+                            const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
+                            double* part_m, float* part_s, int32_t* status, cudaStream_t s);
+cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias, int64_t rows,
+                                int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
+                                int64_t ld_pix, const double* lse_m, const double* lse_s,
+                                Planes P, int32_t* status, cudaStream_t s);
+cudaError_t launch_tc_update(const Planes& P, int64_t rows, const uint16_t* Kb, int64_t ld_data,
+                             int64_t ld_pix, int64_t n_pix, float* Num, float* den,
+                             int32_t* status, cudaStream_t s);
+int64_t tc_pass1_tiles(int64_t rows);
+
+cudaError_t launch_compress(const Geom& g, const double* quat, int64_t nrot, const float* Num,
+                            const float* den, int mode, double* g_num, double* g_den,
+                            cudaStream_t s);
+cudaError_t launch_finalize(int64_t n_vox, const double* g_num, const double* g_den,
+                            const float* grid_prev, float* grid_out, cudaStream_t s);
+
+// Host side of Eq. 2.7 (emc_quat.cpp).
+int64_t quat_generate(int n, int uniform, double* quat, double* weight, int64_t cap);
+
+}  // namespace emc

@@ -1,0 +1,120 @@
+// expand.cu -- e-step of EMC (Eq. 2.9) and the per-rotation bias of Eq. 2.3.
+//
+// One CTA per rotation row j, threads striding over pixels. For every pixel
+// the grid point p = R_j q_i + N/2 is formed in double-float, the trilinear
+// weights f(p_l - p) of the eight surrounding voxels (Eq. 2.8, tent kernel)
+// blend the L2-resident grid, W_ij = max(W, w_floor) and log W_ij is stored in
+// the layout the contraction of the chosen precision reads. The same CTA sums
+// W_ij over pixels in FP64 (block reduction) and writes
+//   bias_j = log w_j - sum_i W_ij,
+// the rotation-only part of S_jk = sum_i K_ik log W_ij - W_ij + log w_j.
+// Writes are coalesced along pixels; HBM traffic is the L write (4 B/(i,j)
+// for FP32, 2 B for BF16, 6 B for the three-term split).
+#include "emc_common.cuh"
+#include "emc_internal.h"
+
+namespace emc {
+
+constexpr int kExpandThreads = 256;
+
+template <int PREC>
+__global__ void __launch_bounds__(kExpandThreads)
+    expand_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
+                  int64_t ld_pix, int N, const float* __restrict__ grid,
+                  const double* __restrict__ quat, const double* __restrict__ logw, int64_t nrot,
+                  float w_floor, void* __restrict__ Lbase, int64_t plane_stride,
+                  double* __restrict__ bias, int32_t* status) {
+  const int64_t row = blockIdx.x;
+  __shared__ RotDF R;
+  __shared__ double red[kExpandThreads / 32];
+  const bool valid_row = row < nrot;
+  if (threadIdx.x == 0 && valid_row) quat_to_rot_df(quat + 4 * row, &R);
+  __syncthreads();
+
+  float* Lf = reinterpret_cast<float*>(Lbase) + row * ld_pix;
+  uint16_t* Lb = reinterpret_cast<uint16_t*>(Lbase) + row * ld_pix;
+  const float half_n = 0.5f * (float)N;
+  const int64_t nn = (int64_t)N * N;
+  double wsum = 0.0;
+  int bad = 0;
+
+  for (int64_t i = threadIdx.x; i < ld_pix; i += kExpandThreads) {
+    float L = 0.f;
+    bool used = false;
+    if (valid_row && i < n_pix) {
+      float4 a = qh[i], b = ql[i];
+      if (a.w != 0.f) {
+        used = true;
+        int f[3];
+        float t[3];
+        rotate_to_grid(R, a, b, half_n, f, t);
+        float W = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+          int x = f[0] + ((c >> 2) & 1), y = f[1] + ((c >> 1) & 1), z = f[2] + (c & 1);
+          if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= N) continue;
+          float w = (((c >> 2) & 1) ? t[0] : 1.f - t[0]) * (((c >> 1) & 1) ? t[1] : 1.f - t[1]) *
+                    ((c & 1) ? t[2] : 1.f - t[2]);
+          W = fmaf(w, __ldg(grid + (int64_t)x * nn + (int64_t)y * N + z), W);
+        }
+        W = fmaxf(W, w_floor);
+        wsum += (double)W;
+        L = logf(W);
+      }
+    }
+    if (PREC == EMC_PREC_FP32) {
+      Lf[i] = L;
+    } else if (PREC == EMC_PREC_BF16) {
+      Lb[i] = bf16_bits(L);
+    } else {
+      // three-term split: hi on the 1/8 grid, residual r = mid + lo
+      float hi = rintf(L * kHiScale) * (1.0f / kHiScale);
+      if (used && (hi < kHiMin || hi > kHiMax)) bad = 1;
+      hi = fminf(fmaxf(hi, kHiMin), kHiMax);
+      float r = L - hi;  // exact
+      uint16_t mid = bf16_bits(r);
+      uint16_t lo = bf16_bits(r - bf16_val(mid));
+      Lb[i] = bf16_bits(hi);
+      Lb[i + plane_stride] = mid;
+      Lb[i + 2 * plane_stride] = lo;
+    }
+  }
+  if (bad) set_status(status, EMC_ERR_UNSUPPORTED);
+
+  // FP64 block reduction of sum_i W_ij
+  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kExpandThreads / 32; w++) s += red[w];
+    bias[row] = valid_row ? logw[row] - s : -INFINITY;
+  }
+}
+
+cudaError_t launch_expand(const Geom& g, const float* grid, const double* quat,
+                          const double* logw, int64_t nrot, int64_t rows, int precision,
+                          float w_floor, Planes L, double* bias, int32_t* status, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  dim3 grd((unsigned)rows), blk(kExpandThreads);
+  switch (precision) {
+    case EMC_PREC_FP32:
+      expand_kernel<EMC_PREC_FP32><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid,
+                                                       quat, logw, nrot, w_floor, L.base,
+                                                       L.plane_stride, bias, status);
+      break;
+    case EMC_PREC_BF16:
+      expand_kernel<EMC_PREC_BF16><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid,
+                                                       quat, logw, nrot, w_floor, L.base,
+                                                       L.plane_stride, bias, status);
+      break;
+    default:
+      expand_kernel<EMC_PREC_BF16_SPLIT><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
+                                                             grid, quat, logw, nrot, w_floor,
+                                                             L.base, L.plane_stride, bias, status);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace emc

@@ -1,0 +1,130 @@
+// misc.cu -- frame preparation, log-sum-exp merges and the final division.
+#include "emc_common.cuh"
+#include "emc_internal.h"
+
+namespace emc {
+
+// Frames K (Sec. 2.1) int32 [n_data][ld_k] -> BF16 [ld_data][ld_pix]:
+// columns < n_pix hold the counts, column n_pix holds 1 for every real frame
+// (so that the M-step contraction also yields den_j = sum_k P_jk), everything
+// else 0. Counts outside [0, 256] or a frame total >= 65536 would break the
+// exact BF16 / exact hi-term accumulation and are flagged.
+__global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, int64_t n_data,
+                                   int64_t n_pix, int64_t ld_pix, uint16_t* __restrict__ Kb,
+                                   int32_t* status) {
+  const int64_t k = blockIdx.x;
+  __shared__ long long red[8];
+  long long tot = 0;
+  int bad = 0;
+  for (int64_t i = threadIdx.x; i < ld_pix; i += blockDim.x) {
+    float v = 0.f;
+    if (k < n_data) {
+      if (i < n_pix) {
+        int32_t c = K[k * ld_k + i];
+        if (c < 0 || c > 256) bad = 1;
+        tot += c;
+        v = (float)c;
+      } else if (i == n_pix) {
+        v = 1.f;
+      }
+    }
+    Kb[k * ld_pix + i] = bf16_bits(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    if (s >= 65536) bad = 1;
+  }
+  if (bad) set_status(status, EMC_ERR_UNSUPPORTED);
+}
+
+cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                               int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int32_t* status,
+                               cudaStream_t s) {
+  prep_frames_kernel<<<(unsigned)ld_data, 256, 0, s>>>(K, ld_k, n_data, n_pix, ld_pix, Kb, status);
+  return cudaGetLastError();
+}
+
+// Per frame k: fold the per-tile pairs (m_t, s_t) -- each meaning
+// sum over the tile's rotations of exp(S_jk) = s_t exp(m_t) -- into the running
+// (m_k, s_k) in FP64 (Eq. 2.4's denominator; only maxima and sums travel, as
+// in Sec. 3.3). Reads are coalesced along k.
+__global__ void lse_merge_kernel(const double* __restrict__ part_m, const float* __restrict__ part_s,
+                                 int64_t n_tiles, int64_t ld_data, int64_t n_data,
+                                 double* __restrict__ lse_m, double* __restrict__ lse_s,
+                                 int accumulate, int32_t* status) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_data) return;
+  double M = accumulate ? lse_m[k] : -INFINITY;
+  double S = accumulate ? lse_s[k] : 0.0;
+  double mt = -INFINITY;
+  for (int64_t t = 0; t < n_tiles; t++) mt = fmax(mt, part_m[t * ld_data + k]);
+  double Mn = fmax(M, mt);
+  if (Mn == -INFINITY) {  // nothing seen yet
+    lse_m[k] = M;
+    lse_s[k] = S;
+    return;
+  }
+  double acc = (S > 0.0) ? S * exp(M - Mn) : 0.0;
+  for (int64_t t = 0; t < n_tiles; t++) {
+    double m = part_m[t * ld_data + k];
+    float sv = part_s[t * ld_data + k];
+    if (sv > 0.f) acc += (double)sv * exp(m - Mn);
+  }
+  if (!isfinite(Mn) || !(acc > 0.0) || !isfinite(acc)) set_status(status, EMC_ERR_NUMERIC);
+  lse_m[k] = Mn;
+  lse_s[k] = acc;
+}
+
+cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
+                             int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
+                             int accumulate, int32_t* status, cudaStream_t s) {
+  unsigned blocks = (unsigned)((n_data + 255) / 256);
+  lse_merge_kernel<<<blocks, 256, 0, s>>>(part_m, part_s, n_tiles, ld_data, n_data, lse_m, lse_s,
+                                          accumulate, status);
+  return cudaGetLastError();
+}
+
+// Total log-likelihood sum_k (m_k + log s_k), one CTA, FP64.
+__global__ void loglik_sum_kernel(const double* __restrict__ lse_m, const double* __restrict__ lse_s,
+                                  int64_t n_data, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < n_data; k += blockDim.x) acc += lse_m[k] + log(lse_s[k]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    *out = s;
+  }
+}
+
+cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
+                              double* out, cudaStream_t s) {
+  loglik_sum_kernel<<<1, 1024, 0, s>>>(lse_m, lse_s, n_data, out);
+  return cudaGetLastError();
+}
+
+// Eq. 2.12's final division (the paper's insert_slices_division), over voxels.
+__global__ void finalize_kernel(int64_t n_vox, const double* __restrict__ g_num,
+                                const double* __restrict__ g_den, const float* grid_prev,
+                                float* grid_out) {
+  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_vox) return;
+  double d = g_den[l];
+  grid_out[l] = d > 0.0 ? (float)(g_num[l] / d) : grid_prev[l];
+}
+
+cudaError_t launch_finalize(int64_t n_vox, const double* g_num, const double* g_den,
+                            const float* grid_prev, float* grid_out, cudaStream_t s) {
+  unsigned blocks = (unsigned)((n_vox + 255) / 256);
+  finalize_kernel<<<blocks, 256, 0, s>>>(n_vox, g_num, g_den, grid_prev, grid_out);
+  return cudaGetLastError();
+}
+
+}  // namespace emc

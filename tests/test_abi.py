@@ -1,0 +1,73 @@
+"""The C-ABI library loads, exports every entry point include/emc.h declares,
+and its host-only parts behave (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libemc():
+    from paper_1409_4256_gb300 import build, emc
+    build.build()
+    return emc.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*[\w\s\*]+?\b(emc_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_exports_every_declared_symbol(libemc):
+    names = _declared()
+    assert len(names) >= 15
+    for n in sorted(names):
+        assert hasattr(libemc, n), n
+
+
+def test_binding_covers_header():
+    from paper_1409_4256_gb300 import emc
+    assert _declared() == set(emc._SIGS)
+
+
+def test_quat_count_and_generate_match_oracle(libemc, oracle):
+    from paper_1409_4256_gb300 import emc
+    for n in (1, 2, 3, 4, 5):
+        assert emc.quat_count(n) == 10 * (5 * n ** 3 + n)
+        qa, wa = emc.quat_generate(n)
+        qb, wb = oracle.quat_generate(n)
+        assert qa.shape == qb.shape
+        assert np.abs(qa - qb).max() < 1e-12
+        assert np.abs(wa / wb - 1).max() < 1e-12
+    qa, wa = emc.quat_generate(3, uniform=True)
+    assert np.allclose(wa, 1 / len(wa))
+
+
+def test_status_strings_and_config_checks(libemc):
+    from paper_1409_4256_gb300 import emc
+    assert emc.status_string(0) == "ok"
+    assert "argument" in emc.status_string(-1)
+    cfg = emc.Config(N=32, precision=2, n_pix=100, n_rot=50, n_data=10, w_floor=1e-10,
+                     compress_mode=0, flags=0, rot_chunk=0)
+    nb = ctypes.c_size_t()
+    assert libemc.emc_workspace_size(ctypes.byref(cfg), ctypes.byref(nb)) == 0 and nb.value > 0
+    bad = emc.Config(N=2, precision=2, n_pix=100, n_rot=50, n_data=10, w_floor=1e-10)
+    assert libemc.emc_workspace_size(ctypes.byref(bad), ctypes.byref(nb)) == -1
+    neg = emc.Config(N=32, precision=2, n_pix=100, n_rot=50, n_data=10, w_floor=-1.0)
+    assert libemc.emc_workspace_size(ctypes.byref(neg), ctypes.byref(nb)) == -1
+    tiny = emc.Config(N=32, precision=2, n_pix=100, n_rot=50, n_data=10, w_floor=1e-30)
+    assert libemc.emc_workspace_size(ctypes.byref(tiny), ctypes.byref(nb)) == -4
+    b = emc.BufferSizes()
+    assert libemc.emc_buffer_sizes_for(ctypes.byref(cfg), 50, ctypes.byref(b)) == 0
+    assert b.ld_pix == 128 and b.ld_data == 256 and b.rows == 128
+    assert b.logw_bytes == 3 * 2 * 128 * 128
+    assert libemc.emc_buffer_sizes_for(ctypes.byref(cfg), 51, ctypes.byref(b)) == -1

@@ -1,0 +1,217 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64
+oracle on the same seeded inputs.
+
+Problem: 32^3 grid, 32x32 detector (812 used pixels -> ld_pix 832, ragged),
+n=3 rotation sampling (1380 rotations = 10 full 128-row tiles + 100),
+300 frames (ld_data 512, ragged), 0.5 photons/pixel.
+
+Tolerances (the floating-point bar for P and the model; derivations in the
+design notes):
+  max |dP| <= 1e-4, rel-L2(model) <= 1e-5  for FP32 and the BF16 split form;
+  log W within 2e-6 + 2e-7 |log W| (FP32 trilinear + logf);
+  lse within 1e-4 absolute (an lse error d scales all P of a frame by e^-d).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+EXACT_PRECISIONS = ["fp32", "bf16_split"]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4256_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ref(small_problem, oracle):
+    """The oracle's whole chain on the small problem."""
+    p = small_problem
+    W = oracle.expand(p["grid"], p["quat"], p["q"], p["w_floor"])
+    S = oracle.scores(W, p["w"], p["K"].astype(np.float64))
+    P, lse, L = oracle.estep(S)
+    Num, den = oracle.mstep(P, p["K"].astype(np.float64))
+    out, gn, gd = oracle.compress(p["N"], p["quat"], p["q"], Num, den, p["grid"])
+    out_idw, _, _ = oracle.compress(p["N"], p["quat"], p["q"], Num, den, p["grid"], mode=1)
+    bias = np.log(p["w"]) - W.sum(1)
+    return dict(W=W, S=S, P=P, lse=lse, L=L, Num=Num, den=den, out=out, gn=gn, gd=gd,
+                out_idw=out_idw, bias=bias)
+
+
+def make_ctx(torch, p, precision, **kw):
+    from paper_1409_4256_gb300 import emc
+    ctx = emc.Context(p["N"], p["q"], p["quat"], p["w"], p["K"].shape[0], precision=precision,
+                      w_floor=p["w_floor"], **kw)
+    ctx.set_frames(torch.as_tensor(p["K"], device="cuda"))
+    return ctx
+
+
+def grid_dev(torch, p):
+    return torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
+
+
+def decode_L(torch, ctx, L, nrot, precision):
+    b = ctx.buffer_sizes(nrot)
+    if precision == "fp32":
+        return L.view(torch.float32).view(b.rows, b.ld_pix).double().cpu().numpy()
+    planes = L.view(torch.bfloat16).view(-1, b.rows, b.ld_pix).double().cpu().numpy()
+    return planes.sum(0)
+
+
+def decode_P(torch, ctx, P, nrot, precision):
+    b = ctx.buffer_sizes(nrot)
+    if precision == "fp32":
+        return P.view(torch.float32).view(b.rows, b.ld_data).double().cpu().numpy()
+    planes = P.view(torch.bfloat16).view(2, b.rows, b.ld_data).double().cpu().numpy()
+    return planes[0] + planes[1]
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("precision", EXACT_PRECISIONS)
+def test_expand(torch_cuda, small_problem, ref, precision):
+    torch, p = torch_cuda, small_problem
+    ctx = make_ctx(torch, p, precision)
+    nrot, npix = p["quat"].shape[0], p["q"].shape[0]
+    L, bias = ctx.expand(grid_dev(torch, p), 0, nrot)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    Lg = decode_L(torch, ctx, L, nrot, precision)
+    Lo = np.log(ref["W"])
+    err = np.abs(Lg[:nrot, :npix] - Lo)
+    assert np.all(err <= 2e-6 + 2e-7 * np.abs(Lo)), err.max()
+    assert np.all(Lg[:, npix:] == 0) and np.all(Lg[nrot:] == 0)
+    bg = bias.cpu().numpy()
+    assert np.abs(bg[:nrot] - ref["bias"]).max() < 1e-6 * np.abs(ref["bias"]).max()
+    assert np.all(np.isneginf(bg[nrot:]))
+
+
+@pytest.mark.parametrize("precision", EXACT_PRECISIONS)
+def test_estep_two_passes(torch_cuda, small_problem, ref, precision):
+    torch, p = torch_cuda, small_problem
+    ctx = make_ctx(torch, p, precision)
+    nrot, nd = p["quat"].shape[0], p["K"].shape[0]
+    L, bias = ctx.expand(grid_dev(torch, p), 0, nrot)
+    lse_m, lse_s = ctx.loglik(L, bias, nrot)
+    P = ctx.normalize(L, bias, nrot, lse_m, lse_s)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    lse = (lse_m + torch.log(lse_s)).cpu().numpy()[:nd]
+    assert np.abs(lse - ref["lse"]).max() <= 1e-4
+    Pg = decode_P(torch, ctx, P, nrot, precision)
+    dP = np.abs(Pg[:nrot, :nd] - ref["P"]).max()
+    assert dP <= 1e-4, dP
+    assert np.all(Pg[nrot:] == 0) and np.all(Pg[:, nd:] == 0)
+    assert np.allclose(Pg[:nrot, :nd].sum(0), 1.0, atol=1e-3)
+
+
+@pytest.mark.parametrize("precision", EXACT_PRECISIONS)
+def test_loglik_accumulates_over_rotation_blocks(torch_cuda, small_problem, ref, precision):
+    # two rotation blocks merged through accumulate=1 equal one block
+    torch, p = torch_cuda, small_problem
+    ctx = make_ctx(torch, p, precision)
+    nd = p["K"].shape[0]
+    g = grid_dev(torch, p)
+    La, ba = ctx.expand(g, 0, 700)
+    Lb, bb = ctx.expand(g, 700, 680)
+    m, s = ctx.loglik(La, ba, 700)
+    # the second block must be the last rows of the rotation list: emc_loglik
+    # takes nrot rows of an expanded block; rot0 is only a property of expand
+    m, s = ctx.loglik(Lb, bb, 680, m, s, accumulate=True)
+    torch.cuda.synchronize()
+    lse = (m + torch.log(s)).cpu().numpy()[:nd]
+    assert np.abs(lse - ref["lse"]).max() <= 1e-4
+
+
+@pytest.mark.parametrize("precision", EXACT_PRECISIONS)
+def test_update_and_compress(torch_cuda, small_problem, ref, precision):
+    torch, p = torch_cuda, small_problem
+    ctx = make_ctx(torch, p, precision)
+    nrot, npix = p["quat"].shape[0], p["q"].shape[0]
+    g = grid_dev(torch, p)
+    L, bias = ctx.expand(g, 0, nrot)
+    m, s = ctx.loglik(L, bias, nrot)
+    P = ctx.normalize(L, bias, nrot, m, s)
+    Num, den = ctx.update(P, nrot)
+    gn, gd = ctx.compress(0, nrot, Num, den)
+    out = ctx.finalize(gn, gd, g)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    Ng = Num.cpu().numpy().astype(np.float64)
+    assert rel_l2(Ng[:nrot, :npix], ref["Num"]) <= 1e-4
+    assert rel_l2(den.cpu().numpy()[:nrot].astype(np.float64), ref["den"]) <= 1e-4
+    assert rel_l2(gd.cpu().numpy(), ref["gd"]) <= 1e-5
+    assert rel_l2(out.cpu().numpy().astype(np.float64), ref["out"]) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", EXACT_PRECISIONS)
+def test_iteration(torch_cuda, small_problem, ref, precision):
+    torch, p = torch_cuda, small_problem
+    ctx = make_ctx(torch, p, precision)
+    out, st = ctx.iteration(grid_dev(torch, p))
+    assert st["device_status"] == 0
+    assert rel_l2(out.cpu().numpy().astype(np.float64), ref["out"]) <= 1e-5
+    assert abs(st["loglik"] - ref["L"]) <= 1e-4 * p["K"].shape[0]
+    assert st["kernels"] > 0
+
+
+@pytest.mark.parametrize("precision", EXACT_PRECISIONS)
+def test_iteration_chunked_equals_whole(torch_cuda, small_problem, precision):
+    torch, p = torch_cuda, small_problem
+    g = grid_dev(torch, p)
+    a, _ = make_ctx(torch, p, precision).iteration(g)
+    b, _ = make_ctx(torch, p, precision, rot_chunk=256).iteration(g)
+    assert rel_l2(b.cpu().numpy().astype(np.float64), a.cpu().numpy().astype(np.float64)) < 1e-7
+
+
+def test_iteration_idw_mode(torch_cuda, small_problem, ref):
+    torch, p = torch_cuda, small_problem
+    ctx = make_ctx(torch, p, "fp32", compress_mode=1)
+    out, st = ctx.iteration(grid_dev(torch, p))
+    assert rel_l2(out.cpu().numpy().astype(np.float64), ref["out_idw"]) <= 1e-5
+
+
+def test_single_rotation(torch_cuda, small_problem, oracle):
+    # M_rot = 1: every responsibility is 1
+    torch, p = torch_cuda, small_problem
+    q1 = dict(p, quat=p["quat"][:1], w=np.ones(1))
+    ctx = make_ctx(torch, q1, "fp32")
+    L, bias = ctx.expand(grid_dev(torch, q1), 0, 1)
+    m, s = ctx.loglik(L, bias, 1)
+    P = ctx.normalize(L, bias, 1, m, s)
+    torch.cuda.synchronize()
+    Pg = decode_P(torch, ctx, P, 1, "fp32")
+    assert np.all(Pg[0, :p["K"].shape[0]] == 1.0)
+
+
+def test_counts_out_of_range_are_flagged(torch_cuda, small_problem):
+    torch, p = torch_cuda, small_problem
+    from paper_1409_4256_gb300 import emc
+    ctx = emc.Context(p["N"], p["q"], p["quat"], p["w"], 4, precision="fp32", w_floor=p["w_floor"])
+    K = torch.zeros((4, p["q"].shape[0]), dtype=torch.int32, device="cuda")
+    K[2, 5] = 300
+    ctx.set_frames(K)
+    torch.cuda.synchronize()
+    assert ctx.status() == -4  # EMC_ERR_UNSUPPORTED
+    K[2, 5] = 256  # the largest count BF16 holds exactly is accepted
+    ctx.set_frames(K)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+
+
+def test_bad_arguments_raise(torch_cuda, small_problem):
+    torch, p = torch_cuda, small_problem
+    from paper_1409_4256_gb300 import emc
+    ctx = make_ctx(torch, p, "fp32")
+    with pytest.raises(emc.EmcError):
+        ctx.expand(grid_dev(torch, p), 1379, 5)
+    with pytest.raises(emc.EmcError):
+        ctx.expand(grid_dev(torch, p), -1, 5)
