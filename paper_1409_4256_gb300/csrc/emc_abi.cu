@@ -18,8 +18,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
-  size_t qh, ql, quat, logw, Kb, status, L, bias, lse_m, lse_s, part_m, part_s, P, Num, den, gnum,
-      gden, scalar, total;
+  size_t qh, ql, quat, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, P, Num,
+      den, gnum, gden, scalar, total;
 };
 
 int planes_L(int prec) { return prec == EMC_PREC_BF16_SPLIT ? 3 : 1; }
@@ -68,6 +68,7 @@ Layout make_layout(const emc_config* c) {
   y.bias = take(sizeof(double) * y.rows);
   y.lse_m = take(sizeof(double) * y.ld_data);
   y.lse_s = take(sizeof(double) * y.ld_data);
+  y.lse2 = take(sizeof(float2) * y.ld_data);
   y.part_m = take(sizeof(double) * (size_t)y.part_tiles * y.ld_data);
   y.part_s = take(sizeof(float) * (size_t)y.part_tiles * y.ld_data);
   y.P = take(planes_P(p) * elem_P(p) * (size_t)y.chunk_rows * y.ld_data);
@@ -311,7 +312,7 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
     Planes pp{P, Prows * y.ld_data, y.ld_data};
     int nterms = c->cfg.precision == EMC_PREC_BF16_SPLIT ? 3 : 1;
     CU(launch_tc_normalize(lp, nterms, bias, rows, nrot, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix,
-                           lse_m, lse_s, pp, c->status, s));
+                           lse_m, lse_s, (float2*)(c->ws + y.lse2), pp, c->status, s));
   }
   return EMC_OK;
 }
@@ -325,8 +326,9 @@ int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num
                           den, s));
   } else {
     Planes pp{(void*)P, Prows * y.ld_data, y.ld_data};
-    CU(launch_tc_update(pp, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num, den, c->status,
-                        s));
+    const int nterms = c->cfg.precision == EMC_PREC_BF16_SPLIT ? 2 : 1;
+    CU(launch_tc_update(pp, nterms, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num, den,
+                        c->status, s));
   }
   return EMC_OK;
 }

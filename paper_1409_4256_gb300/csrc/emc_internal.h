@@ -53,16 +53,17 @@ cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t 
                               double* out, cudaStream_t s);
 
 // tcgen05 forms (precision EMC_PREC_BF16 / EMC_PREC_BF16_SPLIT).
-struct TcPlan;
 cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, int32_t* status, cudaStream_t s);
+// lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
 cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias, int64_t rows,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
-                                Planes P, int32_t* status, cudaStream_t s);
-cudaError_t launch_tc_update(const Planes& P, int64_t rows, const uint16_t* Kb, int64_t ld_data,
-                             int64_t ld_pix, int64_t n_pix, float* Num, float* den,
+                                float2* lse2, Planes P, int32_t* status, cudaStream_t s);
+// nterms: 2 (P = hi + lo planes) or 1 (hi plane only).
+cudaError_t launch_tc_update(const Planes& P, int nterms, int64_t rows, const uint16_t* Kb,
+                             int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
                              int32_t* status, cudaStream_t s);
 int64_t tc_pass1_tiles(int64_t rows);
 

@@ -3,9 +3,13 @@
 // Scores S_jk = sum_i K_ik log W_ij + bias_j (Eq. 2.3 plus the prior of
 // Eq. 2.4) as a tiled FP32 FFMA contraction over pixels: 64 rotations x 128
 // frames per CTA, 4 x 8 outputs per thread, 16-pixel smem stages. Dot products
-// reach |S| ~ 1e4 while P needs S to ~1e-4, so each 256-pixel block is
-// accumulated in FP32 and folded into an error-free (hi, lo) pair (two-sum);
-// the epilogue combines hi + lo + bias in FP64.
+// reach |S| ~ 1e4 while P needs S to ~1e-4, beyond what a chain of FP32 FMAs
+// keeps. log W is therefore split while it is staged into shared memory:
+// hi = log W rounded to the 1/8 grid and r = log W - hi (|r| <= 1/16, exact).
+// Counts are integers, so every partial sum of K * hi is a multiple of 1/8
+// below 2^21 and the FFMA chain of the hi accumulator never rounds; the r
+// accumulator stays small (a random walk of size ~ sqrt(sum K^2) / 28), so its
+// rounding is ~1e-5 absolute. The epilogue adds hi + r + bias in FP64.
 //  pass 1 : per frame, per tile of 64 rotations, (max_j S_jk, sum_j exp(S_jk - max))
 //  pass 2 : P_jk = exp(S_jk - lse_k) written as FP32 [rows][ld_data]
 //  update : Num_ji = sum_k P_jk K_ki (Eq. 2.11), FP32 FFMA; the K column of
@@ -17,26 +21,23 @@ namespace emc {
 
 constexpr int SB_M = 64, SB_N = 128, SB_K = 16, S_THREADS = 256;
 constexpr int SA_LD = SB_M + 4, SBN_LD = SB_N + 4;
-constexpr int kFoldTiles = 16;  // fold into the (hi, lo) pair every 256 pixels
-
 struct ScoreAcc {
-  float hi[4][8], lo[4][8];
+  float hi[4][8], r[4][8];
 };
 
 // Main loop shared by pass 1 and pass 2. Tile origin: rows r0, frames c0.
 __device__ __forceinline__ void simt_scores_tile(const float* __restrict__ L, int64_t ld_pix,
                                                  const uint16_t* __restrict__ Kb, int64_t r0,
-                                                 int64_t c0, float (*As)[SA_LD],
-                                                 float (*Bs)[SBN_LD], ScoreAcc& out) {
+                                                 int64_t c0, float (*Ah)[SA_LD],
+                                                 float (*Ar)[SA_LD], float (*Bs)[SBN_LD],
+                                                 ScoreAcc& out) {
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  float acc[4][8];
 #pragma unroll
   for (int a = 0; a < 4; a++)
 #pragma unroll
     for (int b = 0; b < 8; b++) {
-      acc[a][b] = 0.f;
       out.hi[a][b] = 0.f;
-      out.lo[a][b] = 0.f;
+      out.r[a][b] = 0.f;
     }
   const int ar = t >> 2, ac = (t & 3) * 4;  // A: row, pixel offset
   const int br = t >> 1, bc = (t & 1) * 8;  // B: frame, pixel offset
@@ -47,10 +48,13 @@ __device__ __forceinline__ void simt_scores_tile(const float* __restrict__ L, in
   uint4 rb = *reinterpret_cast<const uint4*>(Bp);
   for (int64_t kt = 0; kt < ntiles; kt++) {
     __syncthreads();
-    As[ac + 0][ar] = ra.x;
-    As[ac + 1][ar] = ra.y;
-    As[ac + 2][ar] = ra.z;
-    As[ac + 3][ar] = ra.w;
+    const float av4[4] = {ra.x, ra.y, ra.z, ra.w};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const float h = rintf(av4[c] * 8.f) * 0.125f;
+      Ah[ac + c][ar] = h;
+      Ar[ac + c][ar] = av4[c] - h;
+    }
     const uint32_t w4[4] = {rb.x, rb.y, rb.z, rb.w};
 #pragma unroll
     for (int c = 0; c < 4; c++) {
@@ -64,25 +68,19 @@ __device__ __forceinline__ void simt_scores_tile(const float* __restrict__ L, in
     }
 #pragma unroll
     for (int kk = 0; kk < SB_K; kk++) {
-      float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      float4 a = *reinterpret_cast<const float4*>(&Ah[kk][ty * 4]);
+      float4 e = *reinterpret_cast<const float4*>(&Ar[kk][ty * 4]);
       float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
       float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float ah[4] = {a.x, a.y, a.z, a.w};
+      const float aq[4] = {e.x, e.y, e.z, e.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    if ((kt + 1) % kFoldTiles == 0 || kt + 1 == ntiles) {
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
         for (int j = 0; j < 8; j++) {
-          f2 s = two_sum(out.hi[i][j], acc[i][j]);
-          out.hi[i][j] = s.h;
-          out.lo[i][j] += s.l;
-          acc[i][j] = 0.f;
+          out.hi[i][j] = fmaf(ah[i], bv[j], out.hi[i][j]);
+          out.r[i][j] = fmaf(aq[i], bv[j], out.r[i][j]);
         }
     }
   }
@@ -92,12 +90,13 @@ __global__ void __launch_bounds__(S_THREADS)
     simt_pass1_kernel(const float* __restrict__ L, int64_t ld_pix, const double* __restrict__ bias,
                       const uint16_t* __restrict__ Kb, int64_t ld_data,
                       double* __restrict__ part_m, float* __restrict__ part_s) {
-  __shared__ __align__(16) float As[SB_K][SA_LD];
+  __shared__ __align__(16) float Ah[SB_K][SA_LD];
+  __shared__ __align__(16) float Ar[SB_K][SA_LD];
   __shared__ __align__(16) float Bs[SB_K][SBN_LD];
   __shared__ double red[16][SB_N];
   const int64_t r0 = (int64_t)blockIdx.y * SB_M, c0 = (int64_t)blockIdx.x * SB_N;
   ScoreAcc sc;
-  simt_scores_tile(L, ld_pix, Kb, r0, c0, As, Bs, sc);
+  simt_scores_tile(L, ld_pix, Kb, r0, c0, Ah, Ar, Bs, sc);
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
   double b[4];
 #pragma unroll
@@ -108,7 +107,7 @@ __global__ void __launch_bounds__(S_THREADS)
     double m = -INFINITY;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-      x[i][j] = ((double)sc.hi[i][j] + (double)sc.lo[i][j]) + b[i];
+      x[i][j] = ((double)sc.hi[i][j] + (double)sc.r[i][j]) + b[i];
       m = fmax(m, x[i][j]);
     }
     red[ty][tx * 8 + j] = m;
@@ -150,11 +149,12 @@ __global__ void __launch_bounds__(S_THREADS)
                           const uint16_t* __restrict__ Kb, int64_t ld_data, int64_t n_data,
                           const double* __restrict__ lse_m, const double* __restrict__ lse_s,
                           float* __restrict__ P) {
-  __shared__ __align__(16) float As[SB_K][SA_LD];
+  __shared__ __align__(16) float Ah[SB_K][SA_LD];
+  __shared__ __align__(16) float Ar[SB_K][SA_LD];
   __shared__ __align__(16) float Bs[SB_K][SBN_LD];
   const int64_t r0 = (int64_t)blockIdx.y * SB_M, c0 = (int64_t)blockIdx.x * SB_N;
   ScoreAcc sc;
-  simt_scores_tile(L, ld_pix, Kb, r0, c0, As, Bs, sc);
+  simt_scores_tile(L, ld_pix, Kb, r0, c0, Ah, Ar, Bs, sc);
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
   double lse[8];
 #pragma unroll
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(S_THREADS)
     float v[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-      double x = ((double)sc.hi[i][j] + (double)sc.lo[i][j]) + b - lse[j];
+      double x = ((double)sc.hi[i][j] + (double)sc.r[i][j]) + b - lse[j];
       v[j] = (row < nrot && c0 + tx * 8 + j < n_data) ? expf((float)x) : 0.f;
     }
     float4* dst = reinterpret_cast<float4*>(P + row * ld_data + c0 + tx * 8);

@@ -1,23 +1,554 @@
-// tc.cu -- tcgen05 forms of the Maximize step (placeholder until the tensor-core kernels land).
+// tc.cu -- tcgen05 (5th-generation tensor core) forms of the Maximize step.
+//
+// One persistent, warp-specialised kernel template serves the three dense
+// contractions of the E- and M-steps (Eqs. 2.3-2.4 and 2.11):
+//   PASS1     S = L K^T over pixels -> per frame (max_j, sum_j exp) per 128-row tile
+//   NORMALIZE S = L K^T over pixels -> P_jk = exp(S_jk - lse_k), BF16 hi/lo planes
+//   UPDATE    Num = P K over frames (K read MN-major) -> FP32 rows + den_j
+// with M = 128 rotations per tile and N = 256 frames (or pixels).
+//
+// Roles (320 threads, one CTA per SM):
+//   warp 0      one thread issues TMA loads of A (1-3 BF16 planes) and B into a
+//               ring of shared-memory stages (128-byte swizzle, 64-wide K blocks)
+//   warp 1      allocates TMEM; one thread issues tcgen05.mma (128x256x16) into
+//               FP32 accumulators in TMEM and commits stages / tiles to mbarriers
+//   warps 2-9   epilogue: tcgen05.ld from TMEM (warp w reads lanes 32*(w%4)..,
+//               columns 128*((w-2)/4)..), arithmetic, global stores
+// Every mbarrier wait is bounded in time; a wait that gives up records
+// EMC_ERR_TIMEOUT, raises a CTA-wide abort flag and lets all roles leave.
+//
+// Exactness of the three-term split (precision EMC_PREC_BF16_SPLIT): the hi
+// plane of log W lies on the 1/8 grid with |hi| <= 32 and counts are integers
+// <= 256, so every product and every partial sum of the hi accumulator is a
+// multiple of 1/8 below 2^21 and FP32 holds it exactly whatever the order or
+// rounding of the accumulation. mid and lo (|mid + lo| <= 1/16) go to a second
+// accumulator whose magnitude stays small. The epilogue adds the per-rotation
+// bias split the same way (hi on the grid, lo small), folds the small part's
+// multiples of 1/8 into the exact part and only then subtracts the reference
+// (running max in pass 1, lse_k in pass 2), so the exponent is accurate to a
+// few FP32 ulps of a number of order one.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "emc_common.cuh"
 #include "emc_internal.h"
+#include "tc_ptx.cuh"
 
 namespace emc {
 
-int64_t tc_pass1_tiles(int64_t rows) { return rows / 128; }
+using namespace tc;
 
-cudaError_t launch_tc_pass1(const Planes&, int, const double*, int64_t, const uint16_t*, int64_t,
-                            int64_t, int64_t, double*, float*, int32_t*, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+enum { MODE_PASS1 = 0, MODE_NORMALIZE = 1, MODE_UPDATE = 2 };
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a tile takes tens of microseconds
+constexpr int kSmemBudget = 220 * 1024;
+constexpr int kScratchBytes = 8 * 1024;
+constexpr float kSentinel = -3.0e38f;
+
+template <int MODE, int NA>
+struct TcCfg {
+  static constexpr int A_BYTES = BM * BK * 2;  // one 128 x 64 BF16 plane
+  static constexpr int B_BYTES = BN * BK * 2;  // 256 x 64 BF16
+  static constexpr int STAGE = NA * A_BYTES + B_BYTES;
+  static constexpr int NACC = (MODE != MODE_UPDATE && NA == 3) ? 2 : 1;
+  static constexpr int STAGES_RAW = (kSmemBudget - kScratchBytes - 1024 - 256) / STAGE;
+  static constexpr int STAGES = STAGES_RAW > 4 ? 4 : STAGES_RAW;
+  static constexpr uint32_t TMEM_COLS = NACC * BN;
+  static constexpr int SMEM = 1024 + STAGES * STAGE + 256 + kScratchBytes;
+  static constexpr uint32_t IDESC = idesc_bf16(BM, BN, MODE == MODE_UPDATE ? 1 : 0);
+  static_assert(STAGES >= 2, "shared memory too small for two stages");
+};
+
+struct TcArgs {
+  int n_mtiles, n_ntiles, group, kblocks;
+  int64_t nrot;      // valid rows of A
+  int64_t n_data, ld_data, ld_pix, n_pix;
+  const double* bias;      // scores: [rows]
+  const float2* lse2;      // normalize: [ld_data] (hi on the 1/8 grid, lo)
+  double* part_m;          // pass 1: [n_mtiles][ld_data]
+  float* part_s;
+  uint16_t* P;             // normalize: planes [2][rows][ld_data]
+  int64_t P_plane;
+  float* Num;              // update: [rows][ld_pix]
+  float* den;              // update: [rows]
+  int32_t* status;
+};
+
+__device__ __forceinline__ void tile_coords(int t, const TcArgs& a, int* mt, int* nt) {
+  const int per_group = a.group * a.n_ntiles;
+  const int g = t / per_group, rem = t % per_group;
+  const int gsize = min(a.group, a.n_mtiles - g * a.group);
+  *nt = rem / gsize;
+  *mt = g * a.group + rem % gsize;
 }
-cudaError_t launch_tc_normalize(const Planes&, int, const double*, int64_t, int64_t,
-                                const uint16_t*, int64_t, int64_t, int64_t, const double*,
-                                const double*, Planes, int32_t*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+// Butterfly transpose-reduction: on entry every lane holds 32 values (one per
+// column); on exit v[0] of lane l is the reduction over the 32 lanes of
+// column l. 31 shuffles for 32 columns.
+template <bool MAX>
+__device__ __forceinline__ float warp_transpose_reduce(float (&v)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; i++) {
+      const float send = upper ? v[i] : v[i + off];
+      const float keep = upper ? v[i + off] : v[i];
+      const float recv = __shfl_xor_sync(0xffffffffu, send, off);
+      v[i] = MAX ? fmaxf(keep, recv) : keep + recv;
+    }
+  }
+  return v[0];
 }
-cudaError_t launch_tc_update(const Planes&, int64_t, const uint16_t*, int64_t, int64_t, int64_t,
-                             float*, float*, int32_t*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+__device__ __forceinline__ void fail(volatile int* abort, int32_t* status) {
+  *abort = 1;
+  set_status(status, EMC_ERR_TIMEOUT);
+}
+
+template <int MODE, int NA>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const TcArgs a) {
+  using C = TcCfg<MODE, NA>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  uint8_t* stages = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* acc_full = empty + C::STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float2* scratch = reinterpret_cast<float2*>(smem + C::STAGES * C::STAGE + 256);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; s++) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);
+    mbar_init(drain, 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    prefetch_tmap(&mapA);
+    prefetch_tmap(&mapB);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int T = a.n_mtiles * a.n_ntiles;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer --
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
+        int mt, nt;
+        tile_coords(t, a, &mt, &nt);
+        for (int kb = 0; kb < a.kblocks; kb++, it++) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+          if (!mbar_wait(empty + s, ph ^ 1u, abort, kWaitLimitNs)) {
+            fail(abort, a.status);
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(full + s, C::STAGE);
+          uint8_t* st = stages + s * C::STAGE;
+#pragma unroll
+          for (int p = 0; p < NA; p++)
+            tma_load_3d(st + p * C::A_BYTES, &mapA, full + s, kb * BK, mt * BM, p);
+          uint8_t* sb = st + NA * C::A_BYTES;
+          if (MODE != MODE_UPDATE) {
+            tma_load_2d(sb, &mapB, full + s, kb * BK, nt * BN);
+          } else {
+#pragma unroll
+            for (int j = 0; j < BN / 64; j++)
+              tma_load_2d(sb + j * (64 * BK * 2), &mapB, full + s, nt * BN + j * 64, kb * BK);
+          }
+        }
+      }
+      if (!ok) {
+        // let copies already issued land before the CTA retires
+        for (int back = 1; back <= C::STAGES && it - back >= 0; back++) {
+          const int j = it - back;
+          mbar_wait(full + (j % C::STAGES), (uint32_t)(j / C::STAGES) & 1u, abort, kWaitLimitNs);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA --
+    if (lane == 0) {
+      int it = 0, tcount = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < T && ok; t += gridDim.x, tcount++) {
+        if (!mbar_wait(acc_empty, ((uint32_t)tcount & 1u) ^ 1u, abort, kWaitLimitNs)) {
+          fail(abort, a.status);
+          break;
+        }
+        tc_fence_after();
+        for (int kb = 0; kb < a.kblocks; kb++, it++) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+          if (!mbar_wait(full + s, ph, abort, kWaitLimitNs)) {
+            fail(abort, a.status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = smem_u32(stages + s * C::STAGE);
+          const uint32_t sB = sA + NA * C::A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 16; k++) {
+            if (MODE != MODE_UPDATE) {
+              const uint64_t bdesc = sdesc_sw128(sB + k * 32, 16, 1024);
+#pragma unroll
+              for (int p = 0; p < NA; p++) {
+                const uint64_t adesc = sdesc_sw128(sA + p * C::A_BYTES + k * 32, 16, 1024);
+                const int acc = (NA == 3 && p > 0) ? 1 : 0;
+                const bool first = (kb == 0 && k == 0 && p <= 1);
+                umma_bf16(tmem + acc * BN, adesc, bdesc, C::IDESC, first ? 0u : 1u);
+              }
+            } else {
+              // B is MN-major: 64-pixel chunks 8 KB apart (LBO), 8-frame groups
+              // 1 KB apart (SBO); 16 frames per instruction advance 2 KB.
+              const uint64_t bdesc = sdesc_sw128(sB + k * 2048, 64 * BK * 2, 1024);
+#pragma unroll
+              for (int p = 0; p < NA; p++) {
+                const uint64_t adesc = sdesc_sw128(sA + p * C::A_BYTES + k * 32, 16, 1024);
+                const bool first = (kb == 0 && k == 0 && p == 0);
+                umma_bf16(tmem, adesc, bdesc, C::IDESC, first ? 0u : 1u);
+              }
+            }
+          }
+          umma_commit(empty + s);
+        }
+        if (ok) umma_commit(acc_full);
+      }
+      // every issued MMA must finish before TMEM is released
+      umma_commit(drain);
+      mbar_wait(drain, 0, abort, kWaitLimitNs);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue --
+    const int e = warp - 2;
+    const int q = warp & 3;         // TMEM lane quarter this warp may read
+    const int half = e >> 2;        // column half: 0 -> [0,128), 1 -> [128,256)
+    const int r_in = 32 * q + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    const int et = e * 32 + lane;   // 0..255 among epilogue threads
+    int tcount = 0;
+    for (int t = blockIdx.x; t < T; t += gridDim.x, tcount++) {
+      int mt, nt;
+      tile_coords(t, a, &mt, &nt);
+      const int64_t row = (int64_t)mt * BM + r_in;
+      float bh = 0.f, bl = 0.f;
+      bool valid = row < a.nrot;
+      if (MODE != MODE_UPDATE) {
+        const double b = a.bias[row];
+        valid = valid && b > -INFINITY;
+        if (valid) {
+          const double h = rint(b * 8.0) * 0.125;
+          bh = (float)h;
+          bl = (float)(b - h);
+        }
+      }
+      if (MODE == MODE_NORMALIZE) {
+        scratch[et] = a.lse2[(int64_t)nt * BN + et];
+        named_bar(1, kEpiThreads);
+      }
+      if (!mbar_wait(acc_full, (uint32_t)tcount & 1u, abort, kWaitLimitNs)) {
+        fail(abort, a.status);
+        break;
+      }
+      tc_fence_after();
+      bool big = false;
+#pragma unroll 1
+      for (int c = 0; c < 4; c++) {
+        const int col0 = half * 128 + c * 32;
+        uint32_t v0[32], v1[32];
+        tmem_ld32(lane_addr + col0, v0);
+        if (C::NACC == 2) tmem_ld32(lane_addr + BN + col0, v1);
+        tmem_ld_wait();
+        if (c == 3) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty);
+        }
+        if (MODE == MODE_UPDATE) {
+          const int64_t n0 = (int64_t)nt * BN + col0;
+          if (n0 < a.ld_pix) {
+            float* dst = a.Num + row * a.ld_pix + n0;
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<uint4*>(dst + i) = make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
+            if (a.n_pix >= n0 && a.n_pix < n0 + 32) {
+#pragma unroll
+              for (int i = 0; i < 32; i++)
+                if (n0 + i == a.n_pix) a.den[row] = __uint_as_float(v0[i]);
+            }
+          }
+          continue;
+        }
+        // scores: exact part xh (multiples of 1/8), small part xl
+        float xh[32], xl[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+          float h = __uint_as_float(v0[i]) + bh;
+          float l = (C::NACC == 2 ? __uint_as_float(v1[i]) : 0.f) + bl;
+          const float rr = rintf(l * 8.f) * 0.125f;
+          h += rr;
+          l -= rr;
+          big |= fabsf(h) > 1048576.f;
+          xh[i] = valid ? h : kSentinel;
+          xl[i] = valid ? l : 0.f;
+        }
+        if (MODE == MODE_PASS1) {
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; i++) v[i] = xh[i];
+          const float mcol = warp_transpose_reduce<true>(v, lane);
+#pragma unroll
+          for (int i = 0; i < 32; i++) {
+            const float mi = __shfl_sync(0xffffffffu, mcol, i);
+            v[i] = valid ? __expf((xh[i] - mi) + xl[i]) : 0.f;
+          }
+          const float scol = warp_transpose_reduce<false>(v, lane);
+          scratch[q * BN + col0 + lane] = make_float2(mcol, scol);
+        } else {
+          const int64_t k0 = (int64_t)nt * BN + col0;
+          uint32_t ph[16], pl[16];
+#pragma unroll
+          for (int i = 0; i < 32; i += 2) {
+            float pr[2];
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+              const float2 L = scratch[col0 + i + u];
+              const float d = (xh[i + u] - L.x) + (xl[i + u] - L.y);
+              pr[u] = (valid && k0 + i + u < a.n_data) ? __expf(d) : 0.f;
+            }
+            const uint16_t h0 = bf16_bits(pr[0]), h1 = bf16_bits(pr[1]);
+            ph[i / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            if (NA == 3) {
+              const uint16_t l0 = bf16_bits(pr[0] - bf16_val(h0));
+              const uint16_t l1 = bf16_bits(pr[1] - bf16_val(h1));
+              pl[i / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            } else {
+              pl[i / 2] = 0u;
+            }
+          }
+          uint16_t* dh = a.P + row * a.ld_data + k0;
+          uint16_t* dl = dh + a.P_plane;
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) {
+            *reinterpret_cast<uint4*>(dh + 2 * i) = make_uint4(ph[i], ph[i + 1], ph[i + 2], ph[i + 3]);
+            *reinterpret_cast<uint4*>(dl + 2 * i) = make_uint4(pl[i], pl[i + 1], pl[i + 2], pl[i + 3]);
+          }
+        }
+      }
+      if (NA == 3 && big && valid) set_status(a.status, EMC_ERR_NUMERIC);
+      if (MODE == MODE_PASS1) {
+        named_bar(1, kEpiThreads);
+        const int col = et;  // one frame column per epilogue thread
+        float M = scratch[col].x;
+#pragma unroll
+        for (int qq = 1; qq < 4; qq++) M = fmaxf(M, scratch[qq * BN + col].x);
+        float S = 0.f;
+#pragma unroll
+        for (int qq = 0; qq < 4; qq++) {
+          const float2 ms = scratch[qq * BN + col];
+          if (ms.y > 0.f) S += ms.y * __expf(ms.x - M);
+        }
+        const int64_t o = (int64_t)mt * a.ld_data + (int64_t)nt * BN + col;
+        a.part_m[o] = (double)M;
+        a.part_s[o] = S;
+        named_bar(1, kEpiThreads);
+      } else if (MODE == MODE_NORMALIZE) {
+        named_bar(1, kEpiThreads);  // scratch is rewritten by the next tile
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// lse_k = m_k + log s_k (FP64) split into a 1/8-grid part and a small part.
+__global__ void lse_split_kernel(const double* __restrict__ lse_m, const double* __restrict__ lse_s,
+                                 int64_t n_data, int64_t ld_data, float2* __restrict__ out) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ld_data) return;
+  if (k >= n_data) {
+    out[k] = make_float2(0.f, 0.f);
+    return;
+  }
+  const double l = lse_m[k] + log(lse_s[k]);
+  const double h = rint(l * 8.0) * 0.125;
+  out[k] = make_float2((float)h, (float)(l - h));
+}
+
+// ------------------------------------------------------------- host side --
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// BF16 tensor map, 128-byte swizzle; dims innermost first, strides in bytes.
+bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
+              const uint64_t* strides, const uint32_t* box) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t d[3], st[2];
+  cuuint32_t b[3], es[3] = {1, 1, 1};
+  for (int i = 0; i < rank; i++) {
+    d[i] = dims[i];
+    b[i] = box[i];
+  }
+  for (int i = 0; i < rank - 1; i++) st[i] = strides[i];
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st,
+            b, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+template <int MODE, int NA>
+cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs a, cudaStream_t s) {
+  using C = TcCfg<MODE, NA>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_kernel<MODE, NA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int T = a.n_mtiles * a.n_ntiles;
+  if (T <= 0) return cudaSuccess;
+  const int grid = T < num_sms() ? T : num_sms();
+  tc_kernel<MODE, NA><<<grid, kThreads, C::SMEM, s>>>(mA, mB, a);
+  return cudaGetLastError();
+}
+
+bool maps_scores(const Planes& L, int nterms, int64_t rows, const uint16_t* Kb, int64_t ld_data,
+                 int64_t ld_pix, CUtensorMap* mA, CUtensorMap* mB) {
+  const uint64_t dA[3] = {(uint64_t)ld_pix, (uint64_t)rows, (uint64_t)nterms};
+  const uint64_t sA[2] = {(uint64_t)L.ld * 2, (uint64_t)L.plane_stride * 2};
+  const uint32_t bA[3] = {BK, BM, 1};
+  const uint64_t dB[2] = {(uint64_t)ld_pix, (uint64_t)ld_data};
+  const uint64_t sB[1] = {(uint64_t)ld_pix * 2};
+  const uint32_t bB[2] = {BK, BN};
+  return make_map(mA, L.base, 3, dA, sA, bA) && make_map(mB, Kb, 2, dB, sB, bB);
+}
+
+TcArgs base_args(int64_t rows, int n_ntiles, int kblocks) {
+  TcArgs a{};
+  a.n_mtiles = (int)(rows / BM);
+  a.n_ntiles = n_ntiles;
+  a.group = 8;
+  a.kblocks = kblocks;
+  return a;
+}
+
+}  // namespace
+
+int64_t tc_pass1_tiles(int64_t rows) { return rows / BM; }
+
+cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int64_t rows,
+                            const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
+                            double* part_m, float* part_s, int32_t* status, cudaStream_t s) {
+  CUtensorMap mA, mB;
+  if (!maps_scores(L, nterms, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
+  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / BK));
+  a.nrot = rows;  // validity comes from the bias (-inf on padding rows)
+  a.n_data = n_data;
+  a.ld_data = ld_data;
+  a.ld_pix = ld_pix;
+  a.bias = bias;
+  a.part_m = part_m;
+  a.part_s = part_s;
+  a.status = status;
+  return nterms == 3 ? launch<MODE_PASS1, 3>(mA, mB, a, s) : launch<MODE_PASS1, 1>(mA, mB, a, s);
+}
+
+cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias, int64_t rows,
+                                int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
+                                int64_t ld_pix, const double* lse_m, const double* lse_s,
+                                float2* lse2, Planes P, int32_t* status, cudaStream_t s) {
+  lse_split_kernel<<<(unsigned)((ld_data + 255) / 256), 256, 0, s>>>(lse_m, lse_s, n_data, ld_data,
+                                                                   lse2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mA, mB;
+  if (!maps_scores(L, nterms, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
+  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / BK));
+  a.nrot = nrot;
+  a.n_data = n_data;
+  a.ld_data = ld_data;
+  a.ld_pix = ld_pix;
+  a.bias = bias;
+  a.lse2 = lse2;
+  a.P = reinterpret_cast<uint16_t*>(P.base);
+  a.P_plane = P.plane_stride;
+  a.status = status;
+  return nterms == 3 ? launch<MODE_NORMALIZE, 3>(mA, mB, a, s)
+                     : launch<MODE_NORMALIZE, 1>(mA, mB, a, s);
+}
+
+cudaError_t launch_tc_update(const Planes& P, int nterms, int64_t rows, const uint16_t* Kb,
+                             int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
+                             int32_t* status, cudaStream_t s) {
+  CUtensorMap mA, mB;
+  const uint64_t dA[3] = {(uint64_t)ld_data, (uint64_t)rows, (uint64_t)nterms};
+  const uint64_t sA[2] = {(uint64_t)P.ld * 2, (uint64_t)P.plane_stride * 2};
+  const uint32_t bA[3] = {BK, BM, 1};
+  const uint64_t dB[2] = {(uint64_t)ld_pix, (uint64_t)ld_data};
+  const uint64_t sB[1] = {(uint64_t)ld_pix * 2};
+  const uint32_t bB[2] = {64, BK};
+  if (!make_map(&mA, P.base, 3, dA, sA, bA) || !make_map(&mB, Kb, 2, dB, sB, bB))
+    return cudaErrorInvalidValue;
+  TcArgs a = base_args(rows, (int)((ld_pix + BN - 1) / BN), (int)(ld_data / BK));
+  a.nrot = rows;
+  a.ld_pix = ld_pix;
+  a.n_pix = n_pix;
+  a.ld_data = ld_data;
+  a.Num = Num;
+  a.den = den;
+  a.status = status;
+  return nterms == 2 ? launch<MODE_UPDATE, 2>(mA, mB, a, s) : launch<MODE_UPDATE, 1>(mA, mB, a, s);
 }
 
 }  // namespace emc
