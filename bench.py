@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--forms", default="fp32,bf16",
                     help="other precisions to time briefly (comma list, '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--recompute", action="store_true",
+                    help="two-pass streamed E-step (pass 2 recomputes the scores) instead of "
+                         "keeping the pass-1 scores in HBM")
     return ap.parse_args()
 
 
@@ -264,7 +267,7 @@ def run_ours(args):
 
     def make_ctx(prec):
         c = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision=prec, w_floor=floor,
-                        device=str(dev), stream=stream)
+                        store_scores=not args.recompute, device=str(dev), stream=stream)
         c.set_frames(K_dev, stream=stream)
         return c
 
@@ -347,6 +350,7 @@ def run_ours(args):
                 "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
                            "precision": args.precision, "rotations": n_rot, "frames": n_data,
+                           "estep": "recompute" if args.recompute else "stored scores",
                            "pixels_used": n_pix, "parallelism": "replicas",
                            "l2": "inputs larger than L2 (log W and frames re-read every step)"},
                 "phases_ms": phases, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

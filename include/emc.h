@@ -67,6 +67,12 @@ typedef enum emc_compress_mode {
   EMC_COMPRESS_IDW = 1       /* Eq. 2.5 per slice, then Eq. 2.10 */
 } emc_compress_mode;
 
+/* emc_config.flags */
+#define EMC_FLAG_STORE_SCORES 1 /* emc_iteration keeps pass-1 scores in the
+                                   workspace (rows x ld_data x 4 B plus 1/32 of
+                                   that) and derives P from them instead of
+                                   recomputing the contraction */
+
 typedef struct emc_config {
   int32_t N;             /* grid side, 4 <= N <= 1024 */
   int32_t precision;     /* emc_precision */
@@ -75,7 +81,7 @@ typedef struct emc_config {
   int64_t n_data;        /* frames M_data, >= 1 */
   double w_floor;        /* expanded W_ij is floored at this value, > 0 */
   int32_t compress_mode; /* emc_compress_mode */
-  int32_t flags;         /* reserved, 0 */
+  int32_t flags;         /* EMC_FLAG_* bits */
   int64_t rot_chunk;     /* rotations per pass-2 chunk inside emc_iteration;
                             0 = all rotations in one chunk */
 } emc_config;
@@ -91,6 +97,7 @@ typedef struct emc_buffer_sizes {
   size_t num_bytes;    /* float[rows][ld_pix] */
   size_t den_bytes;    /* float[rows] */
   size_t lse_bytes;    /* double[ld_data] (each of lse_m, lse_s) */
+  size_t score_bytes;  /* optional stored scores of emc_loglik / emc_normalize */
   size_t grid_bytes;   /* double[N^3] (each of g_num, g_den) */
 } emc_buffer_sizes;
 
@@ -156,16 +163,24 @@ int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void
 /* E-step pass 1 (Eq. 2.4 denominators): for every frame k, the running
  * (max m_k, sum s_k) with lse_k = m_k + log s_k over rotations in this block:
  * S_jk = sum_i K_ik log W_ij + bias_j. lse_m, lse_s: device double[ld_data];
- * accumulate = 0 starts from (m, s) = (-inf, 0), else merges into them. */
+ * accumulate = 0 starts from (m, s) = (-inf, 0), else merges into them.
+ * scores (device, score_bytes, may be NULL): when given, the scores are also
+ * stored, as float d[rows][ld_data] relative to float r[rows/32][ld_data]
+ * (the maximum of each 32-row group of a column, on the 1/8 grid; d follows
+ * directly after d in the same buffer): S_jk = d_jk + r_(j/32)k. */
 int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, double* lse_m,
-               double* lse_s, int accumulate, emc_stream stream);
+               double* lse_s, int accumulate, void* scores, emc_stream stream);
 
-/* E-step pass 2 (Eq. 2.4): P_jk = exp(S_jk - lse_k), scores recomputed.
+/* E-step pass 2 (Eq. 2.4): P_jk = exp(S_jk - lse_k). With scores == NULL the
+ * scores are recomputed from L and bias (two-pass streamed form, nothing of
+ * size rotations x frames kept); otherwise they are read from the buffer
+ * emc_loglik filled (L and bias are then not read and may be NULL).
  * P (device): FP32 -> float[rows][ld_data]; BF16 / BF16_SPLIT ->
  * bf16[2][rows][ld_data] (hi, lo planes, P = hi + lo; lo is 0 for BF16).
  * Padding frames and rows are written as 0. */
 int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
-                  const double* lse_m, const double* lse_s, void* P, emc_stream stream);
+                  const double* lse_m, const double* lse_s, const void* scores, void* P,
+                  emc_stream stream);
 
 /* M-step, Eq. 2.11: Num (device float[rows][ld_pix]) = P K over frames;
  * den (device float[rows]) = sum_k P_jk. */

@@ -18,9 +18,13 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
-  size_t qh, ql, quat, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, P, Num,
-      den, gnum, gden, scalar, total;
+  size_t qh, ql, quat, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
+      Num, den, gnum, gden, scalar, total;
 };
+
+size_t score_bytes(int64_t rows, int64_t ld_data) {
+  return sizeof(float) * (size_t)(rows + rows / 32) * ld_data;
+}
 
 int planes_L(int prec) { return prec == EMC_PREC_BF16_SPLIT ? 3 : 1; }
 size_t elem_L(int prec) { return prec == EMC_PREC_FP32 ? 4 : 2; }
@@ -39,7 +43,7 @@ int check_config(const emc_config* c) {
   if (!(c->w_floor > 0.0) || !isfinite(c->w_floor)) return EMC_ERR_ARG;
   if (c->precision == EMC_PREC_BF16_SPLIT && log(c->w_floor) < (double)kHiMin)
     return EMC_ERR_UNSUPPORTED;
-  if (c->rot_chunk < 0 || c->flags != 0) return EMC_ERR_ARG;
+  if (c->rot_chunk < 0 || (c->flags & ~EMC_FLAG_STORE_SCORES) != 0) return EMC_ERR_ARG;
   return EMC_OK;
 }
 
@@ -71,6 +75,7 @@ Layout make_layout(const emc_config* c) {
   y.lse2 = take(sizeof(float2) * y.ld_data);
   y.part_m = take(sizeof(double) * (size_t)y.part_tiles * y.ld_data);
   y.part_s = take(sizeof(float) * (size_t)y.part_tiles * y.ld_data);
+  y.S = (c->flags & EMC_FLAG_STORE_SCORES) ? take(score_bytes(y.rows, y.ld_data)) : 0;
   y.P = take(planes_P(p) * elem_P(p) * (size_t)y.chunk_rows * y.ld_data);
   y.Num = take(sizeof(float) * (size_t)y.chunk_rows * y.ld_pix);
   y.den = take(sizeof(float) * y.chunk_rows);
@@ -142,6 +147,7 @@ int emc_buffer_sizes_for(const emc_config* cfg, int64_t nrot, emc_buffer_sizes* 
   out->num_bytes = sizeof(float) * (size_t)out->rows * y.ld_pix;
   out->den_bytes = sizeof(float) * out->rows;
   out->lse_bytes = sizeof(double) * y.ld_data;
+  out->score_bytes = score_bytes(out->rows, y.ld_data);
   out->grid_bytes = sizeof(double) * (size_t)cfg->N * cfg->N * cfg->N;
   return EMC_OK;
 }
@@ -275,22 +281,27 @@ int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L
 
 // L is the full block [planes][rows][ld_pix] (plane stride = Lrows * ld_pix);
 // the rows processed here start at row_off inside it.
+// scores: NULL or a buffer of score_bytes(rows, ld_data) for this block.
 int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const double* bias,
-              int64_t nrot, double* lse_m, double* lse_s, int accumulate, cudaStream_t s) {
+              int64_t nrot, double* lse_m, double* lse_s, int accumulate, void* scores,
+              cudaStream_t s) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
   double* pm = (double*)(c->ws + y.part_m);
   float* ps = (float*)(c->ws + y.part_s);
+  float* S = (float*)scores;
+  float* Sref = S ? S + rows * y.ld_data : nullptr;
   int64_t tiles;
   if (c->cfg.precision == EMC_PREC_FP32) {
     const float* Lf = (const float*)L + row_off * y.ld_pix;
-    CU(launch_simt_pass1(Lf, y.ld_pix, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, pm, ps, s));
+    CU(launch_simt_pass1(Lf, y.ld_pix, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, pm, ps, S,
+                         Sref, s));
     tiles = simt_pass1_tiles(rows);
   } else {
     Planes p{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
     int nterms = c->cfg.precision == EMC_PREC_BF16_SPLIT ? 3 : 1;
     CU(launch_tc_pass1(p, nterms, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix, pm, ps,
-                       c->status, s));
+                       S, Sref, c->status, s));
     tiles = tc_pass1_tiles(rows);
   }
   CU(launch_lse_merge(pm, ps, tiles, y.ld_data, c->cfg.n_data, lse_m, lse_s, accumulate,
@@ -298,11 +309,19 @@ int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const d
   return EMC_OK;
 }
 
+// S, Sref: stored scores of these rows (NULL: recompute from L and bias).
 int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const double* bias,
-                 int64_t nrot, const double* lse_m, const double* lse_s, void* P, int64_t Prows,
-                 cudaStream_t s) {
+                 int64_t nrot, const double* lse_m, const double* lse_s, const float* S,
+                 const float* Sref, void* P, int64_t Prows, cudaStream_t s) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
+  if (S) {
+    float2* lse2 = (float2*)(c->ws + y.lse2);
+    CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s));
+    CU(launch_normalize_scores(S, Sref, lse2, rows, nrot, y.ld_data, c->cfg.n_data,
+                               c->cfg.precision, P, Prows * y.ld_data, s));
+    return EMC_OK;
+  }
   if (c->cfg.precision == EMC_PREC_FP32) {
     const float* Lf = (const float*)L + row_off * y.ld_pix;
     CU(launch_simt_normalize(Lf, y.ld_pix, bias, rows, nrot, c->Kb, y.ld_data, c->cfg.n_data,
@@ -350,21 +369,28 @@ int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void
 }
 
 int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, double* lse_m,
-               double* lse_s, int accumulate, emc_stream stream) {
+               double* lse_s, int accumulate, void* scores, emc_stream stream) {
   if (!ctx || !L || !bias || !lse_m || !lse_s) return EMC_ERR_ARG;
   if (check_rot_range(ctx, 0, nrot)) return EMC_ERR_ARG;
   if (!ctx->frames_loaded) return EMC_ERR_ARG;
-  return do_loglik(ctx, L, round_up(nrot, 128), 0, bias, nrot, lse_m, lse_s, accumulate,
+  if (((uintptr_t)scores) & 15) return EMC_ERR_ARG;
+  return do_loglik(ctx, L, round_up(nrot, 128), 0, bias, nrot, lse_m, lse_s, accumulate, scores,
                    (cudaStream_t)stream);
 }
 
 int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
-                  const double* lse_m, const double* lse_s, void* P, emc_stream stream) {
-  if (!ctx || !L || !bias || !lse_m || !lse_s || !P) return EMC_ERR_ARG;
+                  const double* lse_m, const double* lse_s, const void* scores, void* P,
+                  emc_stream stream) {
+  if (!ctx || !lse_m || !lse_s || !P) return EMC_ERR_ARG;
+  if (!scores && (!L || !bias)) return EMC_ERR_ARG;
   if (check_rot_range(ctx, 0, nrot)) return EMC_ERR_ARG;
   if (!ctx->frames_loaded) return EMC_ERR_ARG;
+  if (((uintptr_t)scores) & 15) return EMC_ERR_ARG;
   const int64_t rows = round_up(nrot, 128);
-  return do_normalize(ctx, L, rows, 0, bias, nrot, lse_m, lse_s, P, rows, (cudaStream_t)stream);
+  const float* S = (const float*)scores;
+  const float* Sref = S ? S + rows * ctx->lay.ld_data : nullptr;
+  return do_normalize(ctx, L, rows, 0, bias, nrot, lse_m, lse_s, S, Sref, P, rows,
+                      (cudaStream_t)stream);
 }
 
 int emc_update(emc_ctx* ctx, const void* P, int64_t nrot, float* Num, float* den,
@@ -424,7 +450,8 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   if ((st = do_expand(c, grid_in, 0, n_rot, L, bias, s))) return st;
   kernels++;
   if (stats) CU(cudaEventRecord(c->ev[1], s));
-  if ((st = do_loglik(c, L, y.rows, 0, bias, n_rot, lse_m, lse_s, 0, s))) return st;
+  float* S = (c->cfg.flags & EMC_FLAG_STORE_SCORES) ? (float*)(c->ws + y.S) : nullptr;
+  if ((st = do_loglik(c, L, y.rows, 0, bias, n_rot, lse_m, lse_s, 0, S, s))) return st;
   CU(launch_loglik_sum(lse_m, lse_s, c->cfg.n_data, ll, s));
   kernels += 3;
   if (stats) CU(cudaEventRecord(c->ev[2], s));
@@ -435,7 +462,10 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     const int64_t nr = std::min(y.chunk_rows, n_rot - r0);
     const int64_t crows = round_up(nr, 128);
     if (stats) CU(cudaEventRecord(c->ev[3], s));
-    if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lse_m, lse_s, P, crows, s))) return st;
+    const float* Sc = S ? S + r0 * y.ld_data : nullptr;
+    const float* Sr = S ? S + y.rows * y.ld_data + (r0 / 32) * y.ld_data : nullptr;
+    if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lse_m, lse_s, Sc, Sr, P, crows, s)))
+      return st;
     if (stats) CU(cudaEventRecord(c->ev[4], s));
     if ((st = do_update(c, P, crows, nr, Num, den, s))) return st;
     if (stats) CU(cudaEventRecord(c->ev[5], s));

@@ -33,9 +33,12 @@ cudaError_t launch_expand(const Geom& g, const float* grid, const double* quat,
                           float w_floor, Planes L, double* bias, int32_t* status, cudaStream_t s);
 
 // FP32 SIMT forms (precision EMC_PREC_FP32).
+// S, Sref (optional, both or neither): scores relative to 32-row group maxima
+// [rows][ld_data] and the maxima (on the 1/8 grid) [rows / 32][ld_data].
 cudaError_t launch_simt_pass1(const float* L, int64_t ld_pix, const double* bias, int64_t rows,
                               const uint16_t* Kb, int64_t ld_data, int64_t n_data,
-                              double* part_m, float* part_s, cudaStream_t s);
+                              double* part_m, float* part_s, float* S, float* Sref,
+                              cudaStream_t s);
 cudaError_t launch_simt_normalize(const float* L, int64_t ld_pix, const double* bias, int64_t rows,
                                   int64_t nrot, const uint16_t* Kb, int64_t ld_data,
                                   int64_t n_data, const double* lse_m, const double* lse_s,
@@ -49,13 +52,20 @@ int64_t simt_pass1_tiles(int64_t rows);
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
                              int accumulate, int32_t* status, cudaStream_t s);
+cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n_data,
+                             int64_t ld_data, float2* out, cudaStream_t s);
+// E-step pass 2 from stored scores; P layout as emc_normalize documents.
+cudaError_t launch_normalize_scores(const float* S, const float* Sref, const float2* lse2,
+                                    int64_t rows, int64_t nrot, int64_t ld_data, int64_t n_data,
+                                    int precision, void* P, int64_t P_plane, cudaStream_t s);
 cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
                               double* out, cudaStream_t s);
 
 // tcgen05 forms (precision EMC_PREC_BF16 / EMC_PREC_BF16_SPLIT).
 cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
-                            double* part_m, float* part_s, int32_t* status, cudaStream_t s);
+                            double* part_m, float* part_s, float* S, float* Sref,
+                            int32_t* status, cudaStream_t s);
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
 cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias, int64_t rows,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,

@@ -110,6 +110,90 @@ cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t 
   return cudaGetLastError();
 }
 
+// lse_k = m_k + log s_k (FP64) split into a part on the 1/8 grid and a small
+// FP32 rest, so that kernels can subtract it from grid-aligned scores exactly.
+__global__ void lse_split_kernel(const double* __restrict__ lse_m, const double* __restrict__ lse_s,
+                                 int64_t n_data, int64_t ld_data, float2* __restrict__ out) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ld_data) return;
+  if (k >= n_data) {
+    out[k] = make_float2(0.f, 0.f);
+    return;
+  }
+  const double l = lse_m[k] + log(lse_s[k]);
+  const double h = rint(l * 8.0) * 0.125;
+  out[k] = make_float2((float)h, (float)(l - h));
+}
+
+cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n_data,
+                             int64_t ld_data, float2* out, cudaStream_t s) {
+  lse_split_kernel<<<(unsigned)((ld_data + 255) / 256), 256, 0, s>>>(lse_m, lse_s, n_data, ld_data,
+                                                                   out);
+  return cudaGetLastError();
+}
+
+// E-step pass 2 from stored scores (Eq. 2.4): P_jk = exp(S_jk - lse_k) with
+// S_jk held as d_jk (relative to its 32-row group maximum r_gk, which lies on
+// the 1/8 grid); r_gk - hi(lse_k) is exact, so
+//   P_jk = exp(d_jk + ((r_gk - hi_k) - lo_k)).
+// One thread per 4 consecutive frames of one row: 16-byte loads of d,
+// 8-byte (BF16 x4) or 16-byte (FP32 x4) stores of P. HBM-bound: 4 B read and
+// 4 B written per (j, k).
+template <int OUT>  // 0: FP32 P; 1: BF16 hi plane only; 2: BF16 hi + lo planes
+__global__ void normalize_scores_kernel(const float* __restrict__ S, const float* __restrict__ Sref,
+                                        const float2* __restrict__ lse2, int64_t rows,
+                                        int64_t nrot, int64_t ld_data, int64_t n_data,
+                                        void* __restrict__ P, int64_t P_plane) {
+  const int64_t q4 = ld_data / 4;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * q4) return;
+  const int64_t j = idx / q4, k = (idx % q4) * 4;
+  const float4 d = *reinterpret_cast<const float4*>(S + j * ld_data + k);
+  const float4 r = *reinterpret_cast<const float4*>(Sref + (j >> 5) * ld_data + k);
+  const float dv[4] = {d.x, d.y, d.z, d.w};
+  const float rv[4] = {r.x, r.y, r.z, r.w};
+  float p[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const float2 L = lse2[k + u];
+    const float e = dv[u] + ((rv[u] - L.x) - L.y);
+    p[u] = (j < nrot && k + u < n_data) ? __expf(e) : 0.f;
+  }
+  if (OUT == 0) {
+    *reinterpret_cast<float4*>(reinterpret_cast<float*>(P) + j * ld_data + k) =
+        make_float4(p[0], p[1], p[2], p[3]);
+  } else {
+    uint16_t h[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      h[u] = bf16_bits(p[u]);
+      l[u] = OUT == 2 ? bf16_bits(p[u] - bf16_val(h[u])) : (uint16_t)0;
+    }
+    uint16_t* ph = reinterpret_cast<uint16_t*>(P) + j * ld_data + k;
+    *reinterpret_cast<uint2*>(ph) = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16),
+                                               (uint32_t)h[2] | ((uint32_t)h[3] << 16));
+    *reinterpret_cast<uint2*>(ph + P_plane) = make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16),
+                                                         (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+  }
+}
+
+cudaError_t launch_normalize_scores(const float* S, const float* Sref, const float2* lse2,
+                                    int64_t rows, int64_t nrot, int64_t ld_data, int64_t n_data,
+                                    int precision, void* P, int64_t P_plane, cudaStream_t s) {
+  const int64_t n = rows * (ld_data / 4);
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (precision == EMC_PREC_FP32)
+    normalize_scores_kernel<0><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
+                                                       P_plane);
+  else if (precision == EMC_PREC_BF16)
+    normalize_scores_kernel<1><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
+                                                       P_plane);
+  else
+    normalize_scores_kernel<2><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
+                                                       P_plane);
+  return cudaGetLastError();
+}
+
 // Eq. 2.12's final division (the paper's insert_slices_division), over voxels.
 __global__ void finalize_kernel(int64_t n_vox, const double* __restrict__ g_num,
                                 const double* __restrict__ g_den, const float* grid_prev,

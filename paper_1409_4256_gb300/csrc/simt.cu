@@ -89,7 +89,8 @@ __device__ __forceinline__ void simt_scores_tile(const float* __restrict__ L, in
 __global__ void __launch_bounds__(S_THREADS)
     simt_pass1_kernel(const float* __restrict__ L, int64_t ld_pix, const double* __restrict__ bias,
                       const uint16_t* __restrict__ Kb, int64_t ld_data,
-                      double* __restrict__ part_m, float* __restrict__ part_s) {
+                      double* __restrict__ part_m, float* __restrict__ part_s,
+                      float* __restrict__ S, float* __restrict__ Sref) {
   __shared__ __align__(16) float Ah[SB_K][SA_LD];
   __shared__ __align__(16) float Ar[SB_K][SA_LD];
   __shared__ __align__(16) float Bs[SB_K][SBN_LD];
@@ -121,6 +122,29 @@ __global__ void __launch_bounds__(S_THREADS)
     mcol[j] = m;
   }
   __syncthreads();
+  if (S) {
+    // scores relative to the tile's column maximum rounded to the 1/8 grid
+    float ref[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+      ref[j] = mcol[j] == -INFINITY ? -3.0e38f : (float)(rint(mcol[j] * 8.0) * 0.125);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) v[j] = (float)(x[i][j] - (double)ref[j]);
+      float4* dst = reinterpret_cast<float4*>(S + (r0 + ty * 4 + i) * ld_data + c0 + tx * 8);
+      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    if (ty == 0) {
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        Sref[(r0 / 32) * ld_data + c0 + tx * 8 + j] = ref[j];
+        Sref[(r0 / 32 + 1) * ld_data + c0 + tx * 8 + j] = ref[j];
+      }
+    }
+  }
 #pragma unroll
   for (int j = 0; j < 8; j++) {
     float s = 0.f;
@@ -248,10 +272,12 @@ int64_t simt_pass1_tiles(int64_t rows) { return rows / SB_M; }
 
 cudaError_t launch_simt_pass1(const float* L, int64_t ld_pix, const double* bias, int64_t rows,
                               const uint16_t* Kb, int64_t ld_data, int64_t n_data,
-                              double* part_m, float* part_s, cudaStream_t s) {
+                              double* part_m, float* part_s, float* S, float* Sref,
+                              cudaStream_t s) {
   (void)n_data;
   dim3 grd((unsigned)(ld_data / SB_N), (unsigned)(rows / SB_M));
-  simt_pass1_kernel<<<grd, S_THREADS, 0, s>>>(L, ld_pix, bias, Kb, ld_data, part_m, part_s);
+  simt_pass1_kernel<<<grd, S_THREADS, 0, s>>>(L, ld_pix, bias, Kb, ld_data, part_m, part_s, S,
+                                              Sref);
   return cudaGetLastError();
 }
 

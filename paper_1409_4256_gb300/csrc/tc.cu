@@ -73,6 +73,8 @@ struct TcArgs {
   const float2* lse2;      // normalize: [ld_data] (hi on the 1/8 grid, lo)
   double* part_m;          // pass 1: [n_mtiles][ld_data]
   float* part_s;
+  float* S;                // pass 1, optional: shifted scores [rows][ld_data]
+  float* Sref;             // pass 1, optional: 32-row group maxima [rows / 32][ld_data]
   uint16_t* P;             // normalize: planes [2][rows][ld_data]
   int64_t P_plane;
   float* Num;              // update: [rows][ld_pix]
@@ -327,10 +329,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 32; i++) v[i] = xh[i];
           const float mcol = warp_transpose_reduce<true>(v, lane);
+          const int64_t k0 = (int64_t)nt * BN + col0;
+          float* Srow = a.S ? a.S + row * a.ld_data + k0 : nullptr;
 #pragma unroll
           for (int i = 0; i < 32; i++) {
             const float mi = __shfl_sync(0xffffffffu, mcol, i);
-            v[i] = valid ? __expf((xh[i] - mi) + xl[i]) : 0.f;
+            const float d = (xh[i] - mi) + xl[i];
+            v[i] = valid ? __expf(d) : 0.f;
+            xl[i] = d;
+          }
+          if (Srow) {
+            // S_jk relative to the 32-row group maximum of column k
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(Srow + i) = make_float4(xl[i], xl[i + 1], xl[i + 2], xl[i + 3]);
+            a.Sref[((int64_t)mt * 4 + q) * a.ld_data + k0 + lane] = mcol;
           }
           const float scol = warp_transpose_reduce<false>(v, lane);
           scratch[q * BN + col0 + lane] = make_float2(mcol, scol);
@@ -392,20 +405,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem, C::TMEM_COLS);
   }
-}
-
-// lse_k = m_k + log s_k (FP64) split into a 1/8-grid part and a small part.
-__global__ void lse_split_kernel(const double* __restrict__ lse_m, const double* __restrict__ lse_s,
-                                 int64_t n_data, int64_t ld_data, float2* __restrict__ out) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= ld_data) return;
-  if (k >= n_data) {
-    out[k] = make_float2(0.f, 0.f);
-    return;
-  }
-  const double l = lse_m[k] + log(lse_s[k]);
-  const double h = rint(l * 8.0) * 0.125;
-  out[k] = make_float2((float)h, (float)(l - h));
 }
 
 // ------------------------------------------------------------- host side --
@@ -489,7 +488,8 @@ int64_t tc_pass1_tiles(int64_t rows) { return rows / BM; }
 
 cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
-                            double* part_m, float* part_s, int32_t* status, cudaStream_t s) {
+                            double* part_m, float* part_s, float* S, float* Sref,
+                            int32_t* status, cudaStream_t s) {
   CUtensorMap mA, mB;
   if (!maps_scores(L, nterms, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
   TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / BK));
@@ -500,6 +500,8 @@ cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int
   a.bias = bias;
   a.part_m = part_m;
   a.part_s = part_s;
+  a.S = S;
+  a.Sref = Sref;
   a.status = status;
   return nterms == 3 ? launch<MODE_PASS1, 3>(mA, mB, a, s) : launch<MODE_PASS1, 1>(mA, mB, a, s);
 }
@@ -508,9 +510,7 @@ cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
                                 float2* lse2, Planes P, int32_t* status, cudaStream_t s) {
-  lse_split_kernel<<<(unsigned)((ld_data + 255) / 256), 256, 0, s>>>(lse_m, lse_s, n_data, ld_data,
-                                                                   lse2);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_lse_split(lse_m, lse_s, n_data, ld_data, lse2, s);
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if (!maps_scores(L, nterms, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;

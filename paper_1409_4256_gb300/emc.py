@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libemc.so")
 PREC_FP32, PREC_BF16, PREC_BF16_SPLIT = 0, 1, 2
 PRECISIONS = {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16_split": PREC_BF16_SPLIT}
 COMPRESS_DEFERRED, COMPRESS_IDW = 0, 1
+FLAG_STORE_SCORES = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -41,7 +42,7 @@ class BufferSizes(ctypes.Structure):
                 ("logw_bytes", ctypes.c_size_t), ("bias_bytes", ctypes.c_size_t),
                 ("prob_bytes", ctypes.c_size_t), ("num_bytes", ctypes.c_size_t),
                 ("den_bytes", ctypes.c_size_t), ("lse_bytes", ctypes.c_size_t),
-                ("grid_bytes", ctypes.c_size_t)]
+                ("score_bytes", ctypes.c_size_t), ("grid_bytes", ctypes.c_size_t)]
 
 
 class IterStats(ctypes.Structure):
@@ -68,8 +69,8 @@ _SIGS = {
     "emc_ctx_status": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "emc_set_frames": (_i32, [_vp, _vp, _i64, _vp]),
     "emc_expand": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
-    "emc_loglik": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
-    "emc_normalize": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "emc_loglik": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp]),
+    "emc_normalize": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     "emc_update": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "emc_compress": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i32, _vp]),
     "emc_finalize": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -134,7 +135,8 @@ class Context:
 
     def __init__(self, N: int, q: np.ndarray, quat: np.ndarray, weight: np.ndarray, n_data: int,
                  precision="bf16_split", w_floor: float = 1e-10, compress_mode: int = 0,
-                 rot_chunk: int = 0, device: str = "cuda", stream=None):
+                 rot_chunk: int = 0, store_scores: bool = False, device: str = "cuda",
+                 stream=None):
         import torch
         self.torch = torch
         if isinstance(precision, str):
@@ -143,8 +145,8 @@ class Context:
         quat = np.ascontiguousarray(quat, dtype=np.float64)
         weight = np.ascontiguousarray(weight, dtype=np.float64)
         self.cfg = Config(N=N, precision=precision, n_pix=q.shape[0], n_rot=quat.shape[0],
-                          n_data=n_data, w_floor=w_floor, compress_mode=compress_mode, flags=0,
-                          rot_chunk=rot_chunk)
+                          n_data=n_data, w_floor=w_floor, compress_mode=compress_mode,
+                          flags=FLAG_STORE_SCORES if store_scores else 0, rot_chunk=rot_chunk)
         L = lib()
         nb = ctypes.c_size_t()
         _check(L.emc_workspace_size(ctypes.byref(self.cfg), ctypes.byref(nb)), "emc_workspace_size")
@@ -211,20 +213,24 @@ class Context:
                                 _stream(stream)), "emc_expand")
         return L, bias
 
+    def scores_buffer(self, nrot: int):
+        """A buffer for the stored scores of emc_loglik / emc_normalize."""
+        return self._bytes(self.buffer_sizes(nrot).score_bytes)
+
     def loglik(self, L, bias, nrot: int, lse_m=None, lse_s=None, accumulate: bool = False,
-               stream=None):
+               scores=None, stream=None):
         if lse_m is None:
             lse_m = self.torch.empty(self.ld_data, dtype=self.torch.float64, device=self.device)
             lse_s = self.torch.empty(self.ld_data, dtype=self.torch.float64, device=self.device)
         _check(lib().emc_loglik(self.h, _ptr(L), _ptr(bias), nrot, _ptr(lse_m), _ptr(lse_s),
-                                int(accumulate), _stream(stream)), "emc_loglik")
+                                int(accumulate), _ptr(scores), _stream(stream)), "emc_loglik")
         return lse_m, lse_s
 
-    def normalize(self, L, bias, nrot: int, lse_m, lse_s, stream=None):
+    def normalize(self, L, bias, nrot: int, lse_m, lse_s, scores=None, stream=None):
         b = self.buffer_sizes(nrot)
         P = self._bytes(b.prob_bytes)
         _check(lib().emc_normalize(self.h, _ptr(L), _ptr(bias), nrot, _ptr(lse_m), _ptr(lse_s),
-                                   _ptr(P), _stream(stream)), "emc_normalize")
+                                   _ptr(scores), _ptr(P), _stream(stream)), "emc_normalize")
         return P
 
     def update(self, P, nrot: int, stream=None):

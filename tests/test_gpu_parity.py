@@ -114,6 +114,45 @@ def test_estep_two_passes(torch_cuda, small_problem, ref, precision):
 
 
 @pytest.mark.parametrize("precision", EXACT_PRECISIONS)
+def test_estep_from_stored_scores(torch_cuda, small_problem, ref, precision):
+    # pass 1 stores the scores; pass 2 reads them instead of recomputing
+    torch, p = torch_cuda, small_problem
+    ctx = make_ctx(torch, p, precision)
+    nrot, nd = p["quat"].shape[0], p["K"].shape[0]
+    L, bias = ctx.expand(grid_dev(torch, p), 0, nrot)
+    Sbuf = ctx.scores_buffer(nrot)
+    lse_m, lse_s = ctx.loglik(L, bias, nrot, scores=Sbuf)
+    P = ctx.normalize(None, None, nrot, lse_m, lse_s, scores=Sbuf)
+    P2 = ctx.normalize(L, bias, nrot, lse_m, lse_s)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    Pg = decode_P(torch, ctx, P, nrot, precision)
+    assert np.abs(Pg[:nrot, :nd] - ref["P"]).max() <= 1e-4
+    assert np.all(Pg[nrot:] == 0) and np.all(Pg[:, nd:] == 0)
+    # the stored scores reproduce the oracle's S_jk
+    b = ctx.buffer_sizes(nrot)
+    Sf = Sbuf.view(torch.float32).cpu().numpy().astype(np.float64)
+    d = Sf[:b.rows * b.ld_data].reshape(b.rows, b.ld_data)
+    r = Sf[b.rows * b.ld_data:].reshape(b.rows // 32, b.ld_data)
+    S = d + np.repeat(r, 32, axis=0)
+    sel = ref["P"] > 1e-6
+    assert np.abs(S[:nrot, :nd][sel] - ref["S"][sel]).max() < 1e-3
+    # both pass-2 forms agree
+    assert np.abs(decode_P(torch, ctx, P2, nrot, precision) - Pg).max() < 1e-5
+
+
+@pytest.mark.parametrize("precision", EXACT_PRECISIONS)
+def test_iteration_stored_scores_equals_recompute(torch_cuda, small_problem, ref, precision):
+    torch, p = torch_cuda, small_problem
+    g = grid_dev(torch, p)
+    a, sa = make_ctx(torch, p, precision, store_scores=True).iteration(g)
+    b, sb = make_ctx(torch, p, precision, store_scores=True, rot_chunk=384).iteration(g)
+    assert sa["device_status"] == 0 and sb["device_status"] == 0
+    assert rel_l2(a.cpu().numpy().astype(np.float64), ref["out"]) <= 1e-5
+    assert rel_l2(b.cpu().numpy().astype(np.float64), ref["out"]) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", EXACT_PRECISIONS)
 def test_loglik_accumulates_over_rotation_blocks(torch_cuda, small_problem, ref, precision):
     # two rotation blocks merged through accumulate=1 equal one block
     torch, p = torch_cuda, small_problem
