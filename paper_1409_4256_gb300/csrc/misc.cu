@@ -68,11 +68,14 @@ __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float*
     lse_s[k] = S;
     return;
   }
+  // FP64 accumulation; the factors exp(m_t - Mn) <= 1 are taken in FP32 (relative
+  // error ~1e-6 for the terms that matter, |m_t - Mn| < 30) -- FP64 exp is rare on
+  // this part and the loop runs over every rotation tile
   double acc = (S > 0.0) ? S * exp(M - Mn) : 0.0;
   for (int64_t t = 0; t < n_tiles; t++) {
     double m = part_m[t * ld_data + k];
     float sv = part_s[t * ld_data + k];
-    if (sv > 0.f) acc += (double)sv * exp(m - Mn);
+    if (sv > 0.f) acc += (double)(sv * __expf((float)(m - Mn)));
   }
   if (!isfinite(Mn) || !(acc > 0.0) || !isfinite(acc)) set_status(status, EMC_ERR_NUMERIC);
   lse_m[k] = Mn;
@@ -88,25 +91,28 @@ cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t 
   return cudaGetLastError();
 }
 
-// Total log-likelihood sum_k (m_k + log s_k), one CTA, FP64.
+// Total log-likelihood sum_k (m_k + log s_k) in FP64: one frame per thread,
+// block sums combined with FP64 atomics into *out (zeroed first).
 __global__ void loglik_sum_kernel(const double* __restrict__ lse_m, const double* __restrict__ lse_s,
                                   int64_t n_data, double* out) {
-  __shared__ double red[32];
-  double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < n_data; k += blockDim.x) acc += lse_m[k] + log(lse_s[k]);
+  __shared__ double red[8];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = k < n_data ? lse_m[k] + log(lse_s[k]) : 0.0;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
-    *out = s;
+    atomicAdd(out, s);
   }
 }
 
 cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
                               double* out, cudaStream_t s) {
-  loglik_sum_kernel<<<1, 1024, 0, s>>>(lse_m, lse_s, n_data, out);
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  loglik_sum_kernel<<<(unsigned)((n_data + 255) / 256), 256, 0, s>>>(lse_m, lse_s, n_data, out);
   return cudaGetLastError();
 }
 
