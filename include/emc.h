@@ -182,6 +182,36 @@ int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
                   const double* lse_m, const double* lse_s, const void* scores, void* P,
                   emc_stream stream);
 
+/* E-step pass 1 for callers that cannot allocate device memory (the paper
+ * has no counterpart: this is an interface addition, not a step of the
+ * method). Some callers cannot call cudaMalloc -- code inside a host
+ * application or framework that owns every device allocation, or a process
+ * whose memory pool is already committed -- and so cannot provide the
+ * workspace emc_ctx_create needs. This call needs no context and no
+ * workspace: it computes what emc_loglik computes, keeping its only scratch
+ * (per-tile max/sum pairs) in a 32 MiB static device array inside the
+ * library, and allocates nothing at call time.
+ *  cfg: N, precision, n_pix, n_rot, n_data are read (host).
+ *  L, bias: device, as emc_expand writes them for nrot rotations.
+ *  frames: device BF16 [ld_data][ld_pix] (ld_pix = round_up(n_pix + 1, 64),
+ *          ld_data = round_up(n_data, 256)): counts in columns < n_pix, 1 in
+ *          column n_pix for every real frame, 0 everywhere else.
+ *  lse_m, lse_s, accumulate: as emc_loglik.
+ *  device_status: optional device int32; a bounded wait that gives up or a
+ *          non-finite merge writes a negative emc_status there (first wins).
+ * Rotations are processed in blocks that fit the static array; frames with
+ * ld_data above about 1.4 million make even one block too large and the call
+ * returns EMC_ERR_UNSUPPORTED before launching anything. Every GPU that loads
+ * the library holds the 32 MiB array until the process exits. All calls share
+ * it and it keeps the last call's contents (each call overwrites what it
+ * reads); calls that overlap on the GPU race on it and must be serialised by
+ * the caller. The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. */
+int emc_loglik_static(const emc_config* cfg, const void* L, const double* bias,
+                      const uint16_t* frames, int64_t nrot, double* lse_m, double* lse_s,
+                      int accumulate, int32_t* device_status, emc_stream stream);
+
 /* M-step, Eq. 2.11: Num (device float[rows][ld_pix]) = P K over frames;
  * den (device float[rows]) = sum_k P_jk. */
 int emc_update(emc_ctx* ctx, const void* P, int64_t nrot, float* Num, float* den,

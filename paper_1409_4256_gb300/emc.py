@@ -75,6 +75,8 @@ _SIGS = {
     "emc_compress": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i32, _vp]),
     "emc_finalize": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "emc_iteration": (_i32, [_vp, _vp, _vp, ctypes.POINTER(IterStats), _vp]),
+    "emc_loglik_static": (_i32, [ctypes.POINTER(Config), _vp, _vp, _vp, _i64, _vp, _vp, _i32,
+                                 _vp, _vp]),
 }
 
 
@@ -117,6 +119,15 @@ def quat_generate(n: int, uniform: bool = False):
     if r != m:
         raise EmcError(f"emc_quat_generate returned {r}, expected {m}")
     return quat, w
+
+
+def loglik_static(cfg: Config, L, bias, frames, nrot: int, lse_m, lse_s,
+                  accumulate: bool = False, device_status=None, stream=None) -> None:
+    """emc_loglik_static: E-step pass 1 with no context, no workspace and no
+    device allocation (its scratch is a static array inside the library)."""
+    _check(lib().emc_loglik_static(ctypes.byref(cfg), _ptr(L), _ptr(bias), _ptr(frames), nrot,
+                                   _ptr(lse_m), _ptr(lse_s), int(accumulate),
+                                   _ptr(device_status), _stream(stream)), "emc_loglik_static")
 
 
 def _ptr(t) -> int:
