@@ -84,6 +84,9 @@ typedef struct emc_config {
   int32_t flags;         /* EMC_FLAG_* bits */
   int64_t rot_chunk;     /* rotations per pass-2 chunk inside emc_iteration;
                             0 = all rotations in one chunk */
+  int32_t n_cand;        /* candidate rotations per frame for the sparse
+                            Maximize (0 = none; at most min(n_rot, 4096)) */
+  int32_t reserved;      /* 0 */
 } emc_config;
 
 /* Per-call buffer sizes in bytes for a block of nrot rotations. */
@@ -235,6 +238,89 @@ int emc_finalize(emc_ctx* ctx, const double* g_num, const double* g_den, const f
  * stats (host, may be NULL) is filled after the call synchronises `stream`. */
 int emc_iteration(emc_ctx* ctx, const float* grid_in, float* grid_out, emc_iter_stats* stats,
                   emc_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Learned rotation proposal and the sparse Maximize. The paper has no learned
+ * component; these calls implement the workload's proposal stage: a frame's
+ * binned counts feed a small network whose top-M logits become the candidate
+ * rotations C_k, and Eq. 2.4 / 2.11 then run over (j, k), j in C_k, only.
+ * ---------------------------------------------------------------------- */
+
+/* Features of the loaded frames: feat (device float[ld_data][512]) =
+ * log(1 + mean count) over the pixels of each (radial, angular) bin, radial
+ * bin floor(32 |q_i| / max|q|) (<= 31), angular bin
+ * floor(16 (atan2(q_y, q_x) + pi) / (2 pi)) (<= 15), index radial * 16 +
+ * angular; empty bins and padding frames give 0. */
+int emc_features(emc_ctx* ctx, float* feat, emc_stream stream);
+
+/* MLP: 512 inputs -> three hidden layers of 512 GELU units -> n_out logits.
+ * Parameters (device FP32, caller-owned, emc_mlp_param_count floats):
+ * W1[512][512], b1[512], W2[512][512], b2, W3[512][512], b3,
+ * W4[512][ld_out], b4[ld_out], ld_out = round_up(n_out, 64); layer input x
+ * (row vector) maps to x W + b. Products use BF16-rounded operands with FP32
+ * accumulation. work: device scratch of emc_mlp_work_size(n_out, batch) bytes
+ * (activations kept for the backward pass). */
+int64_t emc_mlp_param_count(int64_t n_out);
+int emc_mlp_work_size(int64_t n_out, int64_t batch, size_t* bytes);
+
+/* Forward of `batch` rows X (device float[batch][512]) into logits (device
+ * float[batch][ld_out]; columns >= n_out are not written). */
+int emc_mlp_forward(int64_t n_out, const float* params, const float* X, int64_t batch, void* work,
+                    float* logits, emc_stream stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected, step counts from
+ * 1) on the loss -(1/batch) sum_k sum_r tprob[k][r] log softmax(z_k)[tidx[k][r]]
+ * over the batch: tidx (device int32[batch][R]), tprob (device float[batch][R]);
+ * grads, adam_m, adam_v: device FP32 like params (zero them before the first
+ * step; grads is overwritten each step). *loss (device double) is incremented
+ * by the batch loss. */
+int emc_mlp_train_step(int64_t n_out, float* params, float* grads, float* adam_m, float* adam_v,
+                       int step, float lr, const float* X, const int32_t* tidx,
+                       const float* tprob, int64_t batch, int R, void* work, double* loss,
+                       emc_stream stream);
+
+/* Indices of the M largest of the first n values of each row of logits
+ * (device float[batch][ld]) into cand (device int32[batch][M]): first the
+ * values above the M-th largest in index order, then equal values in index
+ * order (ties towards lower indices). */
+int emc_topm(const float* logits, int64_t batch, int64_t n, int64_t ld, int M, int32_t* cand,
+             emc_stream stream);
+
+/* Soft training targets from a dense E-step: for every frame the R <= 64
+ * rotations of largest S_jk and softmax weights over them (device
+ * tidx int32[n_data][R], tprob float[n_data][R]). scores: a buffer filled by
+ * emc_loglik, or NULL for the context's own (EMC_FLAG_STORE_SCORES, from the
+ * last emc_iteration). */
+int emc_targets_from_scores(emc_ctx* ctx, const void* scores, int R, int32_t* tidx, float* tprob,
+                            emc_stream stream);
+
+/* Load candidate sets cand (device int32[n_data][n_cand], rotation indices)
+ * and build the per-rotation pair lists the sparse calls use. An index outside
+ * [0, n_rot) sets EMC_ERR_ARG in the device status. */
+int emc_set_candidates(emc_ctx* ctx, const int32_t* cand, emc_stream stream);
+
+/* Eq. 2.4 over the candidate sets, from L and bias of emc_expand over all
+ * rotations: P (device float[ld_data][n_cand], slot order of the candidates;
+ * padding frames 0) and lse (device double[ld_data]). */
+int emc_sparse_estep(emc_ctx* ctx, const void* L, const double* bias, float* P, double* lse,
+                     emc_stream stream);
+
+/* Eq. 2.11 over the candidate sets: Num (device float[rows][ld_pix]) and den
+ * (device float[rows]) for every rotation (rows without candidates: 0). */
+int emc_sparse_update(emc_ctx* ctx, const float* P, float* Num, float* den, emc_stream stream);
+
+/* One pass of Algorithm 2.1 with the Maximize step over the candidate sets
+ * (e-step, sparse E- and M-steps, c-step); needs rot_chunk 0. stats->loglik is
+ * sum_k of the candidate-set lse_k. */
+int emc_sparse_iteration(emc_ctx* ctx, const float* grid_in, float* grid_out,
+                         emc_iter_stats* stats, emc_stream stream);
+
+/* Missed responsibility mass of the candidate sets under a dense E-step:
+ * missed[k] = 1 - sum_{j in C_k} P_jk (device float[n_data]). scores, lse_m,
+ * lse_s: from emc_loglik, or NULL for the context's own from the last
+ * emc_iteration (needs EMC_FLAG_STORE_SCORES). */
+int emc_missed_mass(emc_ctx* ctx, const void* scores, const double* lse_m, const double* lse_s,
+                    float* missed, emc_stream stream);
 
 #ifdef __cplusplus
 }

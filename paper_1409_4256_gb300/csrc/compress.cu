@@ -21,7 +21,9 @@ __global__ void __launch_bounds__(kCompressThreads)
   const int64_t row = blockIdx.x;
   __shared__ RotDF R;
   const float dj = den[row];
-  if (mode == EMC_COMPRESS_IDW && !(dj > 0.f)) return;
+  // a rotation without responsibility mass has Num = 0 and den = 0 (both
+  // modes): it adds nothing, and sparse iterations leave most rows so
+  if (!(dj > 0.f)) return;
   if (threadIdx.x == 0) quat_to_rot_df(quat + 4 * row, &R);
   __syncthreads();
   const float half_n = 0.5f * (float)N;

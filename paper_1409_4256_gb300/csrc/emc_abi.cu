@@ -19,7 +19,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
   size_t qh, ql, quat, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
-      Num, den, gnum, gden, scalar, total;
+      Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, total;
 };
 
 size_t score_bytes(int64_t rows, int64_t ld_data) {
@@ -44,6 +44,7 @@ int check_config(const emc_config* c) {
   if (c->precision == EMC_PREC_BF16_SPLIT && log(c->w_floor) < (double)kHiMin)
     return EMC_ERR_UNSUPPORTED;
   if (c->rot_chunk < 0 || (c->flags & ~EMC_FLAG_STORE_SCORES) != 0) return EMC_ERR_ARG;
+  if (c->n_cand < 0 || c->n_cand > c->n_rot || c->n_cand > 4096) return EMC_ERR_ARG;
   return EMC_OK;
 }
 
@@ -82,6 +83,16 @@ Layout make_layout(const emc_config* c) {
   y.gnum = take(sizeof(double) * nvox);
   y.gden = take(sizeof(double) * nvox);
   y.scalar = take(256);
+  y.fbin = take(sizeof(int16_t) * y.ld_pix);
+  y.finv = take(sizeof(float) * kFeat);
+  const int64_t M = c->n_cand;
+  y.cand = M ? take(sizeof(int32_t) * (size_t)y.ld_data * M) : 0;
+  y.ccnt = M ? take(sizeof(int32_t) * (size_t)y.rows) : 0;
+  y.coff = M ? take(sizeof(int64_t) * (size_t)(y.rows + 1)) : 0;
+  y.cent = M ? take(sizeof(int2) * (size_t)c->n_data * M) : 0;
+  y.Sc = M ? take(sizeof(double) * (size_t)y.ld_data * M) : 0;
+  y.Pc = M ? take(sizeof(float) * (size_t)y.ld_data * M) : 0;
+  y.lsec = M ? take(sizeof(double) * (size_t)y.ld_data) : 0;
   y.total = o;
   return y;
 }
@@ -104,6 +115,7 @@ struct emc_ctx {
   uint16_t* Kb;
   int32_t* status;
   bool frames_loaded;
+  bool cand_loaded;
   cudaEvent_t ev[8];
   int kernels;  // launches made by the last emc_iteration
 };
@@ -197,6 +209,30 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   }
   std::vector<double> lw(cfg->n_rot);
   for (int64_t j = 0; j < cfg->n_rot; j++) lw[j] = log(weight[j]);
+  // feature bins of the learned proposal: radial floor(32 |q| / max|q|),
+  // angular floor(16 (atan2(q_y, q_x) + pi) / (2 pi)); both capped at the top bin
+  std::vector<int16_t> fbin(y.ld_pix, 0);
+  std::vector<float> finv(kFeat, 0.f);
+  {
+    std::vector<double> r(cfg->n_pix);
+    double rmax = 0.0;
+    for (int64_t i = 0; i < cfg->n_pix; i++) {
+      const double* qi = q + 3 * i;
+      r[i] = sqrt(qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2]);
+      rmax = r[i] > rmax ? r[i] : rmax;
+    }
+    std::vector<int64_t> cnt(kFeat, 0);
+    for (int64_t i = 0; i < cfg->n_pix; i++) {
+      const double* qi = q + 3 * i;
+      int64_t rb = rmax > 0 ? (int64_t)floor(32.0 * r[i] / rmax) : 0;
+      rb = rb > 31 ? 31 : rb;
+      int64_t ab = (int64_t)floor(16.0 * (atan2(qi[1], qi[0]) + M_PI) / (2.0 * M_PI));
+      ab = ab > 15 ? 15 : (ab < 0 ? 0 : ab);
+      fbin[i] = (int16_t)(rb * 16 + ab);
+      cnt[rb * 16 + ab]++;
+    }
+    for (int b = 0; b < kFeat; b++) finv[b] = cnt[b] ? (float)(1.0 / (double)cnt[b]) : 0.f;
+  }
 
   emc_ctx* c = (emc_ctx*)calloc(1, sizeof(emc_ctx));
   if (!c) return EMC_ERR_NOMEM;
@@ -224,6 +260,10 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   ok &= cudaMemcpyAsync(c->logw, lw.data(), sizeof(double) * cfg->n_rot, cudaMemcpyHostToDevice,
                         s) == cudaSuccess;
   ok &= cudaMemsetAsync(c->status, 0, 256, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.fbin, fbin.data(), sizeof(int16_t) * y.ld_pix,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.finv, finv.data(), sizeof(float) * kFeat, cudaMemcpyHostToDevice,
+                        s) == cudaSuccess;
   ok &= cudaStreamSynchronize(s) == cudaSuccess;  // host staging buffers go out of scope
   for (int e = 0; e < 8 && ok; e++) ok &= cudaEventCreate(&c->ev[e]) == cudaSuccess;
   if (!ok) {
@@ -510,6 +550,189 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     stats->device_status = dst;
     stats->kernels = kernels;
   }
+  return EMC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned rotation proposal and the sparse Maximize
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int emc_features(emc_ctx* ctx, float* feat, emc_stream stream) {
+  if (!ctx || !feat || !ctx->frames_loaded) return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  CU(launch_features(ctx->Kb, y.ld_pix, ctx->cfg.n_pix, ctx->cfg.n_data, y.ld_data,
+                     (const int16_t*)(ctx->ws + y.fbin), (const float*)(ctx->ws + y.finv), feat,
+                     (cudaStream_t)stream));
+  return EMC_OK;
+}
+
+int64_t emc_mlp_param_count(int64_t n_out) {
+  if (n_out < 1) return EMC_ERR_ARG;
+  return mlp_layout(n_out, 1).n_params;
+}
+
+int emc_mlp_work_size(int64_t n_out, int64_t batch, size_t* bytes) {
+  if (n_out < 1 || batch < 1 || !bytes) return EMC_ERR_ARG;
+  *bytes = sizeof(float) * (size_t)mlp_layout(n_out, batch).work_floats;
+  return EMC_OK;
+}
+
+int emc_mlp_forward(int64_t n_out, const float* params, const float* X, int64_t batch, void* work,
+                    float* logits, emc_stream stream) {
+  if (n_out < 1 || batch < 1 || batch > (1 << 30) || !params || !X || !work || !logits)
+    return EMC_ERR_ARG;
+  CU(mlp_forward(mlp_layout(n_out, batch), params, X, (int)batch, (float*)work, logits,
+                 (cudaStream_t)stream));
+  return EMC_OK;
+}
+
+int emc_mlp_train_step(int64_t n_out, float* params, float* grads, float* adam_m, float* adam_v,
+                       int step, float lr, const float* X, const int32_t* tidx, const float* tprob,
+                       int64_t batch, int R, void* work, double* loss, emc_stream stream) {
+  if (n_out < 1 || batch < 1 || batch > (1 << 30) || step < 1 || !(lr > 0.f) || R < 1 ||
+      !params || !grads || !adam_m || !adam_v || !X || !tidx || !tprob || !work || !loss)
+    return EMC_ERR_ARG;
+  CU(mlp_train_step(mlp_layout(n_out, batch), params, grads, adam_m, adam_v, step, lr, X, tidx,
+                    tprob, (int)batch, R, (float*)work, loss, (cudaStream_t)stream));
+  return EMC_OK;
+}
+
+int emc_topm(const float* logits, int64_t batch, int64_t n, int64_t ld, int M, int32_t* cand,
+             emc_stream stream) {
+  if (!logits || !cand || batch < 0 || n < 1 || n > INT32_MAX || ld < n || M < 1 || M > n)
+    return EMC_ERR_ARG;
+  CU(launch_topm(logits, batch, n, ld, M, cand, (cudaStream_t)stream));
+  return EMC_OK;
+}
+
+int emc_targets_from_scores(emc_ctx* ctx, const void* scores, int R, int32_t* tidx, float* tprob,
+                            emc_stream stream) {
+  if (!ctx || !tidx || !tprob || R < 1 || R > kMaxTargets || R > ctx->cfg.n_rot) return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  if (!scores) {
+    if (!(ctx->cfg.flags & EMC_FLAG_STORE_SCORES)) return EMC_ERR_ARG;
+    scores = ctx->ws + y.S;
+  }
+  const float* S = (const float*)scores;
+  CU(launch_topr_columns(S, S + y.rows * y.ld_data, y.ld_data, ctx->cfg.n_rot, ctx->cfg.n_data, R,
+                         tidx, tprob, (cudaStream_t)stream));
+  return EMC_OK;
+}
+
+int emc_set_candidates(emc_ctx* ctx, const int32_t* cand, emc_stream stream) {
+  if (!ctx || !cand || ctx->cfg.n_cand < 1) return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  const int M = ctx->cfg.n_cand;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* dc = (int32_t*)(ctx->ws + y.cand);
+  CU(cudaMemcpyAsync(dc, cand, sizeof(int32_t) * (size_t)ctx->cfg.n_data * M,
+                     cudaMemcpyDeviceToDevice, s));
+  CU(launch_csr_build(dc, ctx->cfg.n_data, M, ctx->cfg.n_rot, y.rows,
+                      (int32_t*)(ctx->ws + y.ccnt), (int64_t*)(ctx->ws + y.coff),
+                      (int2*)(ctx->ws + y.cent), ctx->status, s));
+  ctx->cand_loaded = true;
+  return EMC_OK;
+}
+
+int emc_sparse_estep(emc_ctx* ctx, const void* L, const double* bias, float* P, double* lse,
+                     emc_stream stream) {
+  if (!ctx || !L || !bias || !P || !lse || !ctx->frames_loaded || !ctx->cand_loaded)
+    return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int M = ctx->cfg.n_cand;
+  Planes lp{(void*)L, y.rows * y.ld_pix, y.ld_pix};
+  double* Sc = (double*)(ctx->ws + y.Sc);
+  CU(launch_sparse_scores(lp, ctx->cfg.precision, y.rows, bias, ctx->Kb, y.ld_pix,
+                          (const int64_t*)(ctx->ws + y.coff), (const int2*)(ctx->ws + y.cent), M, Sc,
+                          s));
+  CU(launch_sparse_lse(Sc, ctx->cfg.n_data, y.ld_data, M, P, lse, ctx->status, s));
+  return EMC_OK;
+}
+
+int emc_sparse_update(emc_ctx* ctx, const float* P, float* Num, float* den, emc_stream stream) {
+  if (!ctx || !P || !Num || !den || !ctx->frames_loaded || !ctx->cand_loaded) return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  CU(launch_sparse_update(ctx->Kb, y.ld_pix, ctx->cfg.n_pix, (const int64_t*)(ctx->ws + y.coff),
+                          (const int2*)(ctx->ws + y.cent), ctx->cfg.n_cand, P, y.rows, Num, den,
+                          (cudaStream_t)stream));
+  return EMC_OK;
+}
+
+int emc_sparse_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_stats* stats,
+                         emc_stream stream) {
+  if (!c || !grid_in || !grid_out || grid_in == grid_out) return EMC_ERR_ARG;
+  if (!c->frames_loaded || !c->cand_loaded) return EMC_ERR_ARG;
+  if (c->lay.chunk_rows != c->lay.rows) return EMC_ERR_UNSUPPORTED;  // Num holds every row
+  cudaStream_t s = (cudaStream_t)stream;
+  const Layout& y = c->lay;
+  void* L = c->ws + y.L;
+  double* bias = (double*)(c->ws + y.bias);
+  float* Pc = (float*)(c->ws + y.Pc);
+  double* lsec = (double*)(c->ws + y.lsec);
+  float* Num = (float*)(c->ws + y.Num);
+  float* den = (float*)(c->ws + y.den);
+  double* gn = (double*)(c->ws + y.gnum);
+  double* gd = (double*)(c->ws + y.gden);
+  double* ll = (double*)(c->ws + y.scalar);
+  const size_t gb = sizeof(double) * (size_t)c->cfg.N * c->cfg.N * c->cfg.N;
+  int st;
+  if (stats) CU(cudaEventRecord(c->ev[0], s));
+  if ((st = do_expand(c, grid_in, 0, c->cfg.n_rot, L, bias, s))) return st;
+  if (stats) CU(cudaEventRecord(c->ev[1], s));
+  if ((st = emc_sparse_estep(c, L, bias, Pc, lsec, stream))) return st;
+  CU(launch_loglik_sum(lsec, nullptr, c->cfg.n_data, ll, s));  // sum_k lse_k over C_k
+  if (stats) CU(cudaEventRecord(c->ev[2], s));
+  if ((st = emc_sparse_update(c, Pc, Num, den, stream))) return st;
+  if (stats) CU(cudaEventRecord(c->ev[3], s));
+  CU(cudaMemsetAsync(gn, 0, gb, s));
+  CU(cudaMemsetAsync(gd, 0, gb, s));
+  CU(launch_compress(c->geom, c->quat, c->cfg.n_rot, Num, den, c->cfg.compress_mode, gn, gd, s));
+  CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, grid_in, grid_out, s));
+  if (stats) CU(cudaEventRecord(c->ev[4], s));
+  if (stats) {
+    CU(cudaEventSynchronize(c->ev[4]));
+    float te = 0, tl = 0, tu = 0, tc = 0, tt = 0;
+    CU(cudaEventElapsedTime(&te, c->ev[0], c->ev[1]));
+    CU(cudaEventElapsedTime(&tl, c->ev[1], c->ev[2]));
+    CU(cudaEventElapsedTime(&tu, c->ev[2], c->ev[3]));
+    CU(cudaEventElapsedTime(&tc, c->ev[3], c->ev[4]));
+    CU(cudaEventElapsedTime(&tt, c->ev[0], c->ev[4]));
+    memset(stats, 0, sizeof(*stats));
+    stats->ms_expand = te;
+    stats->ms_loglik = tl;
+    stats->ms_update = tu;
+    stats->ms_compress = tc;
+    stats->ms_total = tt;
+    CU(cudaMemcpy(&stats->loglik, ll, sizeof(double), cudaMemcpyDeviceToHost));
+    int32_t dst = 0;
+    CU(cudaMemcpy(&dst, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    stats->device_status = dst;
+    stats->kernels = 9;
+  }
+  return EMC_OK;
+}
+
+int emc_missed_mass(emc_ctx* ctx, const void* scores, const double* lse_m, const double* lse_s,
+                    float* missed, emc_stream stream) {
+  if (!ctx || !missed || !ctx->cand_loaded) return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  if (!scores) {
+    if (!(ctx->cfg.flags & EMC_FLAG_STORE_SCORES)) return EMC_ERR_ARG;
+    scores = ctx->ws + y.S;
+  }
+  if (!lse_m) lse_m = (const double*)(ctx->ws + y.lse_m);
+  if (!lse_s) lse_s = (const double*)(ctx->ws + y.lse_s);
+  cudaStream_t s = (cudaStream_t)stream;
+  float2* lse2 = (float2*)(ctx->ws + y.lse2);
+  CU(launch_lse_split(lse_m, lse_s, ctx->cfg.n_data, y.ld_data, lse2, s));
+  const float* S = (const float*)scores;
+  CU(launch_missed_mass(S, S + y.rows * y.ld_data, y.ld_data, lse2,
+                        (const int32_t*)(ctx->ws + y.cand), ctx->cfg.n_cand, ctx->cfg.n_data,
+                        missed, s));
   return EMC_OK;
 }
 

@@ -83,6 +83,49 @@ cudaError_t launch_compress(const Geom& g, const double* quat, int64_t nrot, con
 cudaError_t launch_finalize(int64_t n_vox, const double* g_num, const double* g_den,
                             const float* grid_prev, float* grid_out, cudaStream_t s);
 
+// ---- learned proposal (learned.cu) ----
+constexpr int kFeat = 512;        // 32 radial x 16 angular bins = MLP width
+constexpr int kMaxTargets = 64;   // soft targets per frame at most
+
+struct MlpLayout {
+  int64_t n_out, ld_out;          // logits per frame, padded to 64
+  int64_t W[4], b[4];             // offsets (floats) in the parameter array
+  int64_t n_params;
+  int64_t B;                      // batch rows the work buffer holds
+  int64_t work_floats;
+};
+MlpLayout mlp_layout(int64_t n_out, int64_t B);
+cudaError_t launch_features(const uint16_t* Kb, int64_t ld_pix, int64_t n_pix, int64_t n_data,
+                            int64_t ld_data, const int16_t* bin, const float* inv_count,
+                            float* feat, cudaStream_t s);
+cudaError_t mlp_forward(const MlpLayout& y, const float* params, const float* X, int B,
+                        float* work, float* logits, cudaStream_t s);
+cudaError_t mlp_train_step(const MlpLayout& y, float* params, float* grads, float* adam_m,
+                           float* adam_v, int step, float lr, const float* X,
+                           const int32_t* tidx, const float* tprob, int B, int R, float* work,
+                           double* loss, cudaStream_t s);
+
+// ---- candidates and the sparse Maximize (sparse.cu) ----
+cudaError_t launch_topm(const float* logits, int64_t B, int64_t n, int64_t ld, int M,
+                        int32_t* cand, cudaStream_t s);
+cudaError_t launch_topr_columns(const float* S, const float* Sref, int64_t ld, int64_t nrot,
+                                int64_t n_data, int R, int32_t* tidx, float* tprob,
+                                cudaStream_t s);
+cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t n_rot,
+                             int64_t rows, int32_t* cnt, int64_t* off, int2* ent,
+                             int32_t* status, cudaStream_t s);
+cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, const double* bias,
+                                 const uint16_t* Kb, int64_t ld_pix, const int64_t* off,
+                                 const int2* ent, int M, double* Sc, cudaStream_t s);
+cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data, int M, float* Pc,
+                              double* lse_c, int32_t* status, cudaStream_t s);
+cudaError_t launch_sparse_update(const uint16_t* Kb, int64_t ld_pix, int64_t n_pix,
+                                 const int64_t* off, const int2* ent, int M, const float* Pc,
+                                 int64_t rows, float* Num, float* den, cudaStream_t s);
+cudaError_t launch_missed_mass(const float* S, const float* Sref, int64_t ld_data,
+                               const float2* lse2, const int32_t* cand, int M, int64_t n_data,
+                               float* missed, cudaStream_t s);
+
 // Host side of Eq. 2.7 (emc_quat.cpp).
 int64_t quat_generate(int n, int uniform, double* quat, double* weight, int64_t cap);
 

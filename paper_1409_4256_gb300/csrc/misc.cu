@@ -91,13 +91,13 @@ cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t 
   return cudaGetLastError();
 }
 
-// Total log-likelihood sum_k (m_k + log s_k) in FP64: one frame per thread,
+// Total log-likelihood sum_k (m_k + log s_k) in FP64 (lse_s NULL: sum_k m_k): one frame per thread,
 // block sums combined with FP64 atomics into *out (zeroed first).
 __global__ void loglik_sum_kernel(const double* __restrict__ lse_m, const double* __restrict__ lse_s,
                                   int64_t n_data, double* out) {
   __shared__ double red[8];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc = k < n_data ? lse_m[k] + log(lse_s[k]) : 0.0;
+  double acc = k < n_data ? lse_m[k] + (lse_s ? log(lse_s[k]) : 0.0) : 0.0;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();

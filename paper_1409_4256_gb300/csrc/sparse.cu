@@ -1,0 +1,402 @@
+// sparse.cu -- candidate selection and the Maximize step over candidate sets.
+//
+// Given M candidate rotations C_k per frame (from the learned proposal), the
+// E- and M-steps (Eq. 2.4, 2.11) run over the pairs (j, k), j in C_k, only:
+//   S_jk = sum_i K_ik log W_ij + bias_j,  lse_k = log sum_{j in C_k} exp S_jk,
+//   P_jk = exp(S_jk - lse_k),  Num_j = sum_{k: j in C_k} P_jk K_k.
+// The pairs are transposed once into a CSR list per rotation, so that both
+// contractions read one log W row (staged in shared memory) and gather the
+// frames' rows of K, which are 3x smaller than a split log W row and stay in L2
+// at the 64^3 size. Scores use the same exact split as the dense forms (hi on
+// the 1/8 grid accumulated exactly, a small residual).
+#include "emc_common.cuh"
+#include "emc_internal.h"
+
+namespace emc {
+
+// ------------------------------------------------------------------- top-M --
+__device__ __forceinline__ uint32_t order_key(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Block-wide exclusive prefix of a 0/1 flag (blockDim.x == 256); returns the
+// prefix and writes the block total to *total.
+__device__ __forceinline__ int block_prefix(int flag, int* warp_tot, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, flag);
+  const int in_warp = __popc(bal & ((1u << lane) - 1u));
+  if (lane == 0) warp_tot[wid] = __popc(bal);
+  __syncthreads();
+  int before = 0, tot = 0;
+  for (int w = 0; w < 8; w++) {
+    if (w < wid) before += warp_tot[w];
+    tot += warp_tot[w];
+  }
+  __syncthreads();
+  *total = tot;
+  return before + in_warp;
+}
+
+// One CTA (256 threads) per row: radix selection of the M-th largest key over
+// four 8-bit digits, then the keys above it in index order followed by the
+// first equal keys in index order (ties towards the lower index).
+__global__ void __launch_bounds__(256)
+    topm_kernel(const float* __restrict__ logits, int64_t ld, int n, int M,
+                int32_t* __restrict__ cand) {
+  const float* z = logits + (int64_t)blockIdx.x * ld;
+  int32_t* out = cand + (int64_t)blockIdx.x * M;
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_prefix, s_mask;
+  __shared__ int s_need;
+  __shared__ int warp_tot[8];
+  if (threadIdx.x == 0) {
+    s_prefix = 0;
+    s_mask = 0;
+    s_need = M;
+  }
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t prefix = s_prefix, mask = s_mask;
+    for (int j = threadIdx.x; j < n; j += 256) {
+      const uint32_t k = order_key(z[j]);
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int cum = 0;
+      for (int b = 255; b >= 0; b--) {
+        if (cum + (int)hist[b] >= s_need) {
+          s_prefix = prefix | ((uint32_t)b << shift);
+          s_need -= cum;
+          break;
+        }
+        cum += (int)hist[b];
+      }
+      s_mask = mask | (255u << shift);
+    }
+    __syncthreads();
+  }
+  const uint32_t T = s_prefix;
+  const int need = s_need;  // how many keys equal to T are taken
+  int gt_before = 0, eq_before = 0;
+  for (int base = 0; base < n; base += 256) {
+    const int j = base + threadIdx.x;
+    const uint32_t k = j < n ? order_key(z[j]) : 0u;
+    const int gt = j < n && k > T, eq = j < n && k == T;
+    int tgt, teq;
+    const int pg = block_prefix(gt, warp_tot, &tgt);
+    const int pe = block_prefix(eq, warp_tot, &teq);
+    if (gt) out[gt_before + pg] = j;
+    if (eq && eq_before + pe < need) out[(M - need) + eq_before + pe] = j;
+    gt_before += tgt;
+    eq_before += teq;
+  }
+}
+
+cudaError_t launch_topm(const float* logits, int64_t B, int64_t n, int64_t ld, int M,
+                        int32_t* cand, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  topm_kernel<<<(unsigned)B, 256, 0, s>>>(logits, ld, (int)n, M, cand);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- training targets (top R) --
+// Per frame (one thread, threads on consecutive frames so row reads coalesce):
+// the R largest stored dense scores over rows [0, nrot) and their softmax
+// (targets proportional to the dense responsibilities).
+__global__ void topr_columns_kernel(const float* __restrict__ S, const float* __restrict__ Sref,
+                                    int64_t ld, int64_t nrot, int64_t n_data, int R,
+                                    int32_t* __restrict__ tidx, float* __restrict__ tprob) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_data) return;
+  float val[kMaxTargets];
+  int idx[kMaxTargets];
+  for (int r = 0; r < R; r++) {
+    val[r] = -INFINITY;
+    idx[r] = 0;
+  }
+  int mpos = 0;
+  float mval = -INFINITY;
+  for (int64_t j = 0; j < nrot; j++) {
+    const float v = S[j * ld + k] + Sref[(j >> 5) * ld + k];
+    if (v > mval) {
+      val[mpos] = v;
+      idx[mpos] = (int)j;
+      mval = val[0];
+      mpos = 0;
+      for (int r = 1; r < R; r++)
+        if (val[r] < mval) {
+          mval = val[r];
+          mpos = r;
+        }
+    }
+  }
+  float mx = -INFINITY;
+  for (int r = 0; r < R; r++) mx = fmaxf(mx, val[r]);
+  float sum = 0.f;
+  for (int r = 0; r < R; r++) sum += __expf(val[r] - mx);
+  for (int r = 0; r < R; r++) {
+    tidx[k * R + r] = idx[r];
+    tprob[k * R + r] = __expf(val[r] - mx) / sum;
+  }
+}
+
+cudaError_t launch_topr_columns(const float* S, const float* Sref, int64_t ld, int64_t nrot,
+                                int64_t n_data, int R, int32_t* tidx, float* tprob,
+                                cudaStream_t s) {
+  if (R < 1 || R > kMaxTargets) return cudaErrorInvalidValue;
+  topr_columns_kernel<<<(unsigned)((n_data + 127) / 128), 128, 0, s>>>(S, Sref, ld, nrot, n_data,
+                                                                       R, tidx, tprob);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- CSR by rotation --
+__global__ void csr_count_kernel(const int32_t* __restrict__ cand, int64_t n_pairs,
+                                 int64_t n_rot, int32_t* __restrict__ cnt, int32_t* status) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_pairs) return;
+  const int32_t j = cand[e];
+  if (j < 0 || j >= n_rot) {
+    set_status(status, EMC_ERR_ARG);
+    return;
+  }
+  atomicAdd(&cnt[j], 1);
+}
+
+// exclusive scan of cnt[0, n) into off[0, n] with one CTA of 1024 threads
+__global__ void csr_scan_kernel(const int32_t* __restrict__ cnt, int64_t n,
+                                int64_t* __restrict__ off) {
+  __shared__ int64_t part[1024];
+  const int64_t per = (n + 1023) / 1024;
+  const int64_t b = threadIdx.x * per, e = min(n, b + per);
+  int64_t s = 0;
+  for (int64_t i = b; i < e; i++) s += cnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int t = 0; t < 1024; t++) {
+      const int64_t v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+    off[n] = acc;
+  }
+  __syncthreads();
+  int64_t acc = part[threadIdx.x];
+  for (int64_t i = b; i < e; i++) {
+    off[i] = acc;
+    acc += cnt[i];
+  }
+}
+
+__global__ void csr_fill_kernel(const int32_t* __restrict__ cand, int64_t n_pairs, int M,
+                                const int64_t* __restrict__ off, int32_t* __restrict__ cur,
+                                int2* __restrict__ ent) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_pairs) return;
+  const int32_t j = cand[e];
+  const int64_t pos = off[j] + atomicAdd(&cur[j], 1);
+  ent[pos] = make_int2((int)(e / M), (int)(e % M));
+}
+
+cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t n_rot,
+                             int64_t rows, int32_t* cnt, int64_t* off, int2* ent,
+                             int32_t* status, cudaStream_t s) {
+  const int64_t n_pairs = n_data * M;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * rows, s);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((n_pairs + 255) / 256);
+  csr_count_kernel<<<blocks, 256, 0, s>>>(cand, n_pairs, n_rot, cnt, status);
+  csr_scan_kernel<<<1, 1024, 0, s>>>(cnt, rows, off);
+  if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * rows, s)) != cudaSuccess) return e;
+  csr_fill_kernel<<<blocks, 256, 0, s>>>(cand, n_pairs, M, off, cnt, ent);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ sparse contractions --
+// One CTA per rotation row: log W_j split into (hi on the 1/8 grid, rest) in
+// shared memory; each warp takes one (frame, slot) pair of the row's list.
+template <int PREC>
+__global__ void __launch_bounds__(256)
+    sparse_scores_kernel(const void* __restrict__ L, int64_t plane_stride, int64_t ld_pix,
+                         const double* __restrict__ bias, const uint16_t* __restrict__ Kb,
+                         const int64_t* __restrict__ off, const int2* __restrict__ ent, int M,
+                         double* __restrict__ Sc) {
+  const int64_t j = blockIdx.x;
+  const int64_t e0 = off[j], e1 = off[j + 1];
+  if (e0 == e1) return;
+  extern __shared__ float sm[];
+  float* Lh = sm;
+  float* Lr = sm + ld_pix;
+  for (int64_t i = threadIdx.x; i < ld_pix; i += blockDim.x) {
+    float h, r;
+    if (PREC == EMC_PREC_FP32) {
+      const float x = reinterpret_cast<const float*>(L)[j * ld_pix + i];
+      h = rintf(x * 8.f) * 0.125f;
+      r = x - h;
+    } else {
+      const uint16_t* Lb = reinterpret_cast<const uint16_t*>(L) + j * ld_pix + i;
+      h = bf16_val(Lb[0]);
+      r = PREC == EMC_PREC_BF16_SPLIT ? bf16_val(Lb[plane_stride]) + bf16_val(Lb[2 * plane_stride])
+                                      : 0.f;
+    }
+    Lh[i] = h;
+    Lr[i] = r;
+  }
+  __syncthreads();
+  const double bj = bias[j];
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = e0 + (threadIdx.x >> 5); e < e1; e += blockDim.x >> 5) {
+    const int2 km = ent[e];
+    const uint32_t* Kr = reinterpret_cast<const uint32_t*>(Kb + (int64_t)km.x * ld_pix);
+    float ah = 0.f, ar = 0.f;
+    for (int64_t i2 = lane; i2 < ld_pix / 2; i2 += 32) {
+      const uint32_t w = Kr[i2];
+      const float k0 = __uint_as_float(w << 16), k1 = __uint_as_float(w & 0xffff0000u);
+      ah = fmaf(k0, Lh[2 * i2], ah);
+      ah = fmaf(k1, Lh[2 * i2 + 1], ah);
+      ar = fmaf(k0, Lr[2 * i2], ar);
+      ar = fmaf(k1, Lr[2 * i2 + 1], ar);
+    }
+    for (int o = 16; o; o >>= 1) {
+      ah += __shfl_xor_sync(0xffffffffu, ah, o);
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+    }
+    if (lane == 0) Sc[(int64_t)km.x * M + km.y] = ((double)ah + (double)ar) + bj;
+  }
+}
+
+// One warp per frame: lse over the frame's M candidates, P = exp(S - lse).
+__global__ void sparse_lse_kernel(const double* __restrict__ Sc, int64_t n_data, int64_t ld_data,
+                                  int M, float* __restrict__ Pc, double* __restrict__ lse_c,
+                                  int32_t* status) {
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= ld_data) return;
+  const double* s = Sc + k * M;
+  float* p = Pc + k * M;
+  if (k >= n_data) {
+    for (int m = lane; m < M; m += 32) p[m] = 0.f;
+    return;
+  }
+  double mx = -INFINITY;
+  for (int m = lane; m < M; m += 32) mx = fmax(mx, s[m]);
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  double sum = 0.0;
+  for (int m = lane; m < M; m += 32) sum += (double)__expf((float)(s[m] - mx));
+  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  const double lse = mx + log(sum);
+  if (!isfinite(lse)) set_status(status, EMC_ERR_NUMERIC);
+  for (int m = lane; m < M; m += 32) p[m] = __expf((float)(s[m] - lse));
+  if (lane == 0) lse_c[k] = lse;
+}
+
+// One CTA per rotation row: Num_j = sum over the row's list of P_jk K_k; the
+// K column of ones at n_pix gives den_j. Rows without candidates are zeroed.
+__global__ void __launch_bounds__(256)
+    sparse_update_kernel(const uint16_t* __restrict__ Kb, int64_t ld_pix, int64_t n_pix,
+                         const int64_t* __restrict__ off, const int2* __restrict__ ent, int M,
+                         const float* __restrict__ Pc, float* __restrict__ Num,
+                         float* __restrict__ den) {
+  const int64_t j = blockIdx.x;
+  const int64_t e0 = off[j], e1 = off[j + 1];
+  float* out = Num + j * ld_pix;
+  constexpr int kSeg = 512;
+  __shared__ int sk[kSeg];
+  __shared__ float sp[kSeg];
+  for (int64_t i0 = 0; i0 < ld_pix; i0 += 256) {
+    const int64_t i = i0 + threadIdx.x;
+    float acc = 0.f;
+    for (int64_t s0 = e0; s0 < e1; s0 += kSeg) {
+      const int ns = (int)min((int64_t)kSeg, e1 - s0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < ns; t += 256) {
+        const int2 km = ent[s0 + t];
+        sk[t] = km.x;
+        sp[t] = Pc[(int64_t)km.x * M + km.y];
+      }
+      __syncthreads();
+      if (i < ld_pix)
+        for (int t = 0; t < ns; t++) acc = fmaf(sp[t], bf16_val(Kb[(int64_t)sk[t] * ld_pix + i]), acc);
+    }
+    if (i < ld_pix) {
+      out[i] = acc;
+      if (i == n_pix) den[j] = acc;
+    }
+  }
+}
+
+// 1 - sum_{j in C_k} P_jk of a dense E-step, from its stored scores.
+__global__ void missed_mass_kernel(const float* __restrict__ S, const float* __restrict__ Sref,
+                                   int64_t ld_data, const float2* __restrict__ lse2,
+                                   const int32_t* __restrict__ cand, int M, int64_t n_data,
+                                   float* __restrict__ missed) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_data) return;
+  const float2 L = lse2[k];
+  double sum = 0.0;
+  for (int m = 0; m < M; m++) {
+    const int64_t j = cand[k * M + m];
+    const float e = S[j * ld_data + k] + ((Sref[(j >> 5) * ld_data + k] - L.x) - L.y);
+    sum += (double)__expf(e);
+  }
+  missed[k] = (float)(1.0 - sum);
+}
+
+cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, const double* bias,
+                                 const uint16_t* Kb, int64_t ld_pix, const int64_t* off,
+                                 const int2* ent, int M, double* Sc, cudaStream_t s) {
+  const size_t smem = 2 * sizeof(float) * (size_t)ld_pix;
+  cudaError_t e;
+  switch (precision) {
+    case EMC_PREC_FP32:
+      e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_FP32>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      sparse_scores_kernel<EMC_PREC_FP32><<<(unsigned)rows, 256, smem, s>>>(
+          L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
+      break;
+    case EMC_PREC_BF16:
+      e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_BF16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      sparse_scores_kernel<EMC_PREC_BF16><<<(unsigned)rows, 256, smem, s>>>(
+          L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
+      break;
+    default:
+      e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_BF16_SPLIT>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      sparse_scores_kernel<EMC_PREC_BF16_SPLIT><<<(unsigned)rows, 256, smem, s>>>(
+          L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data, int M, float* Pc,
+                              double* lse_c, int32_t* status, cudaStream_t s) {
+  sparse_lse_kernel<<<(unsigned)((ld_data * 32 + 255) / 256), 256, 0, s>>>(Sc, n_data, ld_data, M,
+                                                                          Pc, lse_c, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_update(const uint16_t* Kb, int64_t ld_pix, int64_t n_pix,
+                                 const int64_t* off, const int2* ent, int M, const float* Pc,
+                                 int64_t rows, float* Num, float* den, cudaStream_t s) {
+  sparse_update_kernel<<<(unsigned)rows, 256, 0, s>>>(Kb, ld_pix, n_pix, off, ent, M, Pc, Num, den);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_missed_mass(const float* S, const float* Sref, int64_t ld_data,
+                               const float2* lse2, const int32_t* cand, int M, int64_t n_data,
+                               float* missed, cudaStream_t s) {
+  missed_mass_kernel<<<(unsigned)((n_data + 255) / 256), 256, 0, s>>>(S, Sref, ld_data, lse2, cand,
+                                                                     M, n_data, missed);
+  return cudaGetLastError();
+}
+
+}  // namespace emc

@@ -34,7 +34,8 @@ class Config(ctypes.Structure):
                 ("n_pix", ctypes.c_int64), ("n_rot", ctypes.c_int64),
                 ("n_data", ctypes.c_int64), ("w_floor", ctypes.c_double),
                 ("compress_mode", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("rot_chunk", ctypes.c_int64)]
+                ("rot_chunk", ctypes.c_int64), ("n_cand", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class BufferSizes(ctypes.Structure):
@@ -77,6 +78,19 @@ _SIGS = {
     "emc_iteration": (_i32, [_vp, _vp, _vp, ctypes.POINTER(IterStats), _vp]),
     "emc_loglik_static": (_i32, [ctypes.POINTER(Config), _vp, _vp, _vp, _i64, _vp, _vp, _i32,
                                  _vp, _vp]),
+    "emc_features": (_i32, [_vp, _vp, _vp]),
+    "emc_mlp_param_count": (_i64, [_i64]),
+    "emc_mlp_work_size": (_i32, [_i64, _i64, ctypes.POINTER(ctypes.c_size_t)]),
+    "emc_mlp_forward": (_i32, [_i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "emc_mlp_train_step": (_i32, [_i64, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp, _vp,
+                                  _i64, _i32, _vp, _vp, _vp]),
+    "emc_topm": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
+    "emc_targets_from_scores": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    "emc_set_candidates": (_i32, [_vp, _vp, _vp]),
+    "emc_sparse_estep": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "emc_sparse_update": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "emc_sparse_iteration": (_i32, [_vp, _vp, _vp, ctypes.POINTER(IterStats), _vp]),
+    "emc_missed_mass": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -130,6 +144,35 @@ def loglik_static(cfg: Config, L, bias, frames, nrot: int, lse_m, lse_s,
                                    _ptr(device_status), _stream(stream)), "emc_loglik_static")
 
 
+def mlp_param_count(n_out: int) -> int:
+    r = int(lib().emc_mlp_param_count(n_out))
+    if r < 0:
+        raise EmcError(f"emc_mlp_param_count: {status_string(r)}")
+    return r
+
+
+def mlp_work_size(n_out: int, batch: int) -> int:
+    nb = ctypes.c_size_t()
+    _check(lib().emc_mlp_work_size(n_out, batch, ctypes.byref(nb)), "emc_mlp_work_size")
+    return int(nb.value)
+
+
+def mlp_forward(n_out: int, params, X, batch: int, work, logits, stream=None) -> None:
+    _check(lib().emc_mlp_forward(n_out, _ptr(params), _ptr(X), batch, _ptr(work), _ptr(logits),
+                                 _stream(stream)), "emc_mlp_forward")
+
+
+def mlp_train_step(n_out: int, params, grads, m, v, step: int, lr: float, X, tidx, tprob,
+                   batch: int, R: int, work, loss, stream=None) -> None:
+    _check(lib().emc_mlp_train_step(n_out, _ptr(params), _ptr(grads), _ptr(m), _ptr(v), step, lr,
+                                    _ptr(X), _ptr(tidx), _ptr(tprob), batch, R, _ptr(work),
+                                    _ptr(loss), _stream(stream)), "emc_mlp_train_step")
+
+
+def topm(logits, batch: int, n: int, ld: int, M: int, cand, stream=None) -> None:
+    _check(lib().emc_topm(_ptr(logits), batch, n, ld, M, _ptr(cand), _stream(stream)), "emc_topm")
+
+
 def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
@@ -146,8 +189,8 @@ class Context:
 
     def __init__(self, N: int, q: np.ndarray, quat: np.ndarray, weight: np.ndarray, n_data: int,
                  precision="bf16_split", w_floor: float = 1e-10, compress_mode: int = 0,
-                 rot_chunk: int = 0, store_scores: bool = False, device: str = "cuda",
-                 stream=None):
+                 rot_chunk: int = 0, store_scores: bool = False, n_cand: int = 0,
+                 device: str = "cuda", stream=None):
         import torch
         self.torch = torch
         if isinstance(precision, str):
@@ -157,7 +200,8 @@ class Context:
         weight = np.ascontiguousarray(weight, dtype=np.float64)
         self.cfg = Config(N=N, precision=precision, n_pix=q.shape[0], n_rot=quat.shape[0],
                           n_data=n_data, w_floor=w_floor, compress_mode=compress_mode,
-                          flags=FLAG_STORE_SCORES if store_scores else 0, rot_chunk=rot_chunk)
+                          flags=FLAG_STORE_SCORES if store_scores else 0, rot_chunk=rot_chunk,
+                          n_cand=n_cand, reserved=0)
         L = lib()
         nb = ctypes.c_size_t()
         _check(L.emc_workspace_size(ctypes.byref(self.cfg), ctypes.byref(nb)), "emc_workspace_size")
@@ -279,3 +323,55 @@ class Context:
         if not stats:
             return grid_out, None
         return grid_out, {f: getattr(st, f) for f, _ in IterStats._fields_}
+
+    # -- learned proposal and sparse Maximize ------------------------------------
+    def features(self, stream=None):
+        feat = self.torch.empty((self.ld_data, 512), dtype=self.torch.float32, device=self.device)
+        _check(lib().emc_features(self.h, _ptr(feat), _stream(stream)), "emc_features")
+        return feat
+
+    def targets_from_scores(self, R: int, scores=None, stream=None):
+        nd = self.cfg.n_data
+        tidx = self.torch.empty((nd, R), dtype=self.torch.int32, device=self.device)
+        tprob = self.torch.empty((nd, R), dtype=self.torch.float32, device=self.device)
+        _check(lib().emc_targets_from_scores(self.h, _ptr(scores), R, _ptr(tidx), _ptr(tprob),
+                                             _stream(stream)), "emc_targets_from_scores")
+        return tidx, tprob
+
+    def set_candidates(self, cand, stream=None):
+        assert cand.dtype == self.torch.int32 and cand.is_contiguous()
+        _check(lib().emc_set_candidates(self.h, _ptr(cand), _stream(stream)),
+               "emc_set_candidates")
+
+    def sparse_estep(self, L, bias, stream=None):
+        P = self.torch.empty((self.ld_data, self.cfg.n_cand), dtype=self.torch.float32,
+                             device=self.device)
+        lse = self.torch.empty(self.ld_data, dtype=self.torch.float64, device=self.device)
+        _check(lib().emc_sparse_estep(self.h, _ptr(L), _ptr(bias), _ptr(P), _ptr(lse),
+                                      _stream(stream)), "emc_sparse_estep")
+        return P, lse
+
+    def sparse_update(self, P, stream=None):
+        b = self.sizes_all
+        Num = self.torch.empty((b.rows, b.ld_pix), dtype=self.torch.float32, device=self.device)
+        den = self.torch.empty(b.rows, dtype=self.torch.float32, device=self.device)
+        _check(lib().emc_sparse_update(self.h, _ptr(P), _ptr(Num), _ptr(den), _stream(stream)),
+               "emc_sparse_update")
+        return Num, den
+
+    def sparse_iteration(self, grid_in, grid_out=None, stats: bool = True, stream=None):
+        if grid_out is None:
+            grid_out = self.torch.empty_like(grid_in)
+        st = IterStats()
+        _check(lib().emc_sparse_iteration(self.h, _ptr(grid_in), _ptr(grid_out),
+                                          ctypes.byref(st) if stats else None, _stream(stream)),
+               "emc_sparse_iteration")
+        if not stats:
+            return grid_out, None
+        return grid_out, {f: getattr(st, f) for f, _ in IterStats._fields_}
+
+    def missed_mass(self, scores=None, lse_m=None, lse_s=None, stream=None):
+        out = self.torch.empty(self.cfg.n_data, dtype=self.torch.float32, device=self.device)
+        _check(lib().emc_missed_mass(self.h, _ptr(scores), _ptr(lse_m), _ptr(lse_s), _ptr(out),
+                                     _stream(stream)), "emc_missed_mass")
+        return out

@@ -1,0 +1,263 @@
+"""GPU parity of the learned proposal and the sparse Maximize against the
+FP64 oracle (oracle/learned.py, oracle/emc_oracle.c) on the same inputs.
+
+Tolerances: features 1e-5 absolute (FP32 log1p of exact bin sums); MLP logits,
+loss and gradients rel-L2 2e-2 (products take BF16-rounded operands);
+sparse responsibilities max|dP| <= 1e-4, lse 1e-4, model rel-L2 <= 1e-5 (the
+same bar as the dense forms, same exact score split)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4256_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def dense_ref(small_problem, oracle):
+    p = small_problem
+    W = oracle.expand(p["grid"], p["quat"], p["q"], p["w_floor"])
+    S = oracle.scores(W, p["w"], p["K"].astype(np.float64))
+    P, lse, L = oracle.estep(S)
+    return dict(W=W, S=S, P=P, lse=lse)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def ctx_for(torch, p, precision="bf16_split", n_cand=0, store_scores=False):
+    from paper_1409_4256_gb300 import emc
+    c = emc.Context(p["N"], p["q"], p["quat"], p["w"], p["K"].shape[0], precision=precision,
+                    w_floor=p["w_floor"], n_cand=n_cand, store_scores=store_scores)
+    c.set_frames(torch.as_tensor(p["K"], device="cuda"))
+    return c
+
+
+def test_features(torch_cuda, small_problem):
+    from oracle import learned as ol
+    torch, p = torch_cuda, small_problem
+    ctx = ctx_for(torch, p)
+    f = ctx.features()
+    torch.cuda.synchronize()
+    nd = p["K"].shape[0]
+    ref = ol.features(p["q"], p["K"])
+    got = f.cpu().numpy()
+    assert np.abs(got[:nd] - ref).max() < 1e-5
+    assert np.all(got[nd:] == 0)
+
+
+def _oracle_params(torch, prop):
+    from oracle import learned as ol
+    y = prop.params.cpu().numpy().astype(np.float64)
+    H, ld = 512, prop.ld_out
+    ps, o = [], 0
+    for l in range(4):
+        out = H if l < 3 else ld
+        ps.append(y[o:o + H * out].reshape(H, out))
+        o += H * out
+        ps.append(y[o:o + out])
+        o += out
+    ps[6] = ps[6][:, :prop.n_out]
+    ps[7] = ps[7][:prop.n_out]
+    return ps
+
+
+def test_mlp_forward_and_gradients(torch_cuda):
+    from oracle import learned as ol
+    from paper_1409_4256_gb300 import emc, learned
+    torch = torch_cuda
+    n_out, B, R = 300, 64, 8
+    prop = learned.Proposal(n_out)
+    rng = np.random.default_rng(5)
+    X = rng.uniform(0, 2, size=(B, 512)).astype(np.float32)
+    tidx = np.stack([rng.choice(n_out, R, replace=False) for _ in range(B)]).astype(np.int32)
+    tprob = rng.random((B, R)).astype(np.float32)
+    tprob /= tprob.sum(axis=1, keepdims=True)
+    Xd = torch.as_tensor(X, device="cuda")
+    ps = _oracle_params(torch, prop)
+    # forward
+    z = prop.logits(Xd, batch=B).cpu().numpy()[:, :n_out]
+    zr, _ = ol.mlp_forward(ps, X.astype(np.float64))
+    assert rel_l2(z, zr) < 2e-2
+    # one training step: loss and the gradients it used
+    work = torch.empty(emc.mlp_work_size(n_out, B), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    emc.mlp_train_step(n_out, prop.params, prop.grads, prop.m, prop.v, 1, 1e-3, Xd,
+                       torch.as_tensor(tidx, device="cuda"), torch.as_tensor(tprob, device="cuda"),
+                       B, R, work, loss)
+    torch.cuda.synchronize()
+    T = ol.dense_targets(tidx, tprob.astype(np.float64), n_out)
+    lr_, gr = ol.mlp_loss_grads(ps, X.astype(np.float64), T)
+    assert abs(loss.item() - lr_) < 2e-2 * abs(lr_)
+    g = prop.grads.cpu().numpy().astype(np.float64)
+    H, ld = 512, prop.ld_out
+    o = 0
+    for l in range(4):
+        out = H if l < 3 else ld
+        gw = g[o:o + H * out].reshape(H, out)
+        o += H * out
+        gb = g[o:o + out]
+        o += out
+        cols = out if l < 3 else n_out
+        assert rel_l2(gw[:, :cols], gr[2 * l]) < 2e-2, l
+        assert rel_l2(gb[:cols], gr[2 * l + 1]) < 2e-2, l
+        if l == 3:
+            assert np.all(gw[:, n_out:] == 0) and np.all(gb[n_out:] == 0)
+
+
+def test_training_reduces_loss(torch_cuda):
+    from paper_1409_4256_gb300 import learned
+    torch = torch_cuda
+    n_out, n = 200, 1024
+    rng = np.random.default_rng(6)
+    # a learnable toy: the target class is a fixed random projection's argmax
+    X = rng.normal(size=(n, 512)).astype(np.float32)
+    lab = np.argmax(X @ rng.normal(size=(512, n_out)), axis=1).astype(np.int32)
+    prop = learned.Proposal(n_out)
+    hist = prop.train(torch.as_tensor(X, device="cuda"),
+                      torch.as_tensor(lab[:, None], device="cuda"),
+                      torch.ones((n, 1), dtype=torch.float32, device="cuda"),
+                      np.arange(n), epochs=6, batch=128, lr=1e-3)
+    assert hist[-1] < 0.5 * hist[0]
+
+
+def test_topm_matches_sorting(torch_cuda):
+    from oracle import learned as ol
+    from paper_1409_4256_gb300 import emc
+    torch = torch_cuda
+    rng = np.random.default_rng(7)
+    B, n, ld, M = 37, 5000, 5056, 129
+    z = rng.normal(size=(B, ld)).astype(np.float32)
+    z[3, :100] = 7.0  # a block of equal values straddling the cut
+    z[3, 100:] = rng.uniform(-1, 1, size=ld - 100).astype(np.float32)
+    cand = torch.empty((B, M), dtype=torch.int32, device="cuda")
+    emc.topm(torch.as_tensor(z, device="cuda"), B, n, ld, M, cand)
+    got = np.sort(cand.cpu().numpy(), axis=1)
+    ref = ol.topm(z[:, :n].astype(np.float64), M)
+    assert np.array_equal(got, ref)
+
+
+def _candidates(dense_ref, M, seed=8):
+    # the top M/2 dense scores plus M/2 random others, sorted per frame
+    S = dense_ref["S"]
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(S.shape[1]):
+        top = np.argsort(-S[:, k])[:M // 2]
+        rest = rng.choice(np.setdiff1d(np.arange(S.shape[0]), top), M - M // 2, replace=False)
+        out.append(np.sort(np.concatenate([top, rest])))
+    return np.array(out, dtype=np.int32)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_split"])
+def test_sparse_steps(torch_cuda, small_problem, dense_ref, precision):
+    from oracle import learned as ol
+    torch, p = torch_cuda, small_problem
+    M = 96
+    cand = _candidates(dense_ref, M)
+    nrot, nd = p["quat"].shape[0], p["K"].shape[0]
+    ctx = ctx_for(torch, p, precision, n_cand=M)
+    ctx.set_candidates(torch.as_tensor(cand, device="cuda"))
+    L, bias = ctx.expand(torch.as_tensor(p["grid"].astype(np.float32), device="cuda"), 0, nrot)
+    P, lse = ctx.sparse_estep(L, bias)
+    Num, den = ctx.sparse_update(P)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    Pr, lser = ol.sparse_estep(dense_ref["S"], cand)
+    assert np.abs(P.cpu().numpy()[:nd] - Pr).max() <= 1e-4
+    assert np.abs(lse.cpu().numpy()[:nd] - lser).max() <= 1e-4
+    Nr, dr = ol.sparse_mstep(Pr, cand, p["K"], nrot)
+    assert rel_l2(Num.cpu().numpy()[:nrot, :p["q"].shape[0]], Nr) <= 1e-4
+    assert rel_l2(den.cpu().numpy()[:nrot], dr) <= 1e-4
+
+
+def test_sparse_iteration_matches_oracle(torch_cuda, small_problem, dense_ref, oracle):
+    from oracle import learned as ol
+    torch, p = torch_cuda, small_problem
+    M = 96
+    cand = _candidates(dense_ref, M, seed=9)
+    nrot = p["quat"].shape[0]
+    Pr, _ = ol.sparse_estep(dense_ref["S"], cand)
+    Nr, dr = ol.sparse_mstep(Pr, cand, p["K"], nrot)
+    want, _, _ = oracle.compress(p["N"], p["quat"], p["q"], Nr, dr, p["grid"])
+    ctx = ctx_for(torch, p, "bf16_split", n_cand=M)
+    ctx.set_candidates(torch.as_tensor(cand, device="cuda"))
+    out, st = ctx.sparse_iteration(torch.as_tensor(p["grid"].astype(np.float32), device="cuda"))
+    assert st["device_status"] == 0
+    assert rel_l2(out.cpu().numpy().astype(np.float64), want) <= 1e-5
+
+
+def test_all_rotations_as_candidates_is_the_dense_iteration(torch_cuda, small_problem):
+    torch, p = torch_cuda, small_problem
+    nrot, nd = p["quat"].shape[0], p["K"].shape[0]
+    g = torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
+    dense, _ = ctx_for(torch, p, "bf16_split").iteration(g)
+    ctx = ctx_for(torch, p, "bf16_split", n_cand=nrot)
+    ctx.set_candidates(torch.arange(nrot, dtype=torch.int32, device="cuda").repeat(nd, 1))
+    sparse, st = ctx.sparse_iteration(g)
+    assert rel_l2(sparse.cpu().numpy().astype(np.float64),
+                  dense.cpu().numpy().astype(np.float64)) < 1e-6
+
+
+def test_targets_and_missed_mass(torch_cuda, small_problem, dense_ref):
+    from oracle import learned as ol
+    torch, p = torch_cuda, small_problem
+    M, R = 64, 16
+    cand = _candidates(dense_ref, M, seed=10)
+    nd = p["K"].shape[0]
+    ctx = ctx_for(torch, p, "bf16_split", n_cand=M, store_scores=True)
+    ctx.set_candidates(torch.as_tensor(cand, device="cuda"))
+    ctx.iteration(torch.as_tensor(p["grid"].astype(np.float32), device="cuda"))
+    tidx, tprob = ctx.targets_from_scores(R)
+    missed = ctx.missed_mass()
+    torch.cuda.synchronize()
+    ridx, rprob = ol.soft_targets(dense_ref["P"], R)
+    gi, gp = tidx.cpu().numpy(), tprob.cpu().numpy()
+    for k in range(nd):
+        o = np.argsort(gi[k])
+        q = np.argsort(ridx[k])
+        assert np.array_equal(gi[k][o], ridx[k][q])
+        assert np.abs(gp[k][o] - rprob[k][q]).max() < 1e-4
+    mr = ol.missed_mass(dense_ref["P"], cand)
+    assert np.abs(missed.cpu().numpy() - mr).max() < 1e-4
+
+
+def test_trained_proposal_beats_untrained(torch_cuda, oracle):
+    """What the network gains: the responsibility mass its top-M candidates
+    capture on held-out frames, trained vs. the same network untrained."""
+    from paper_1409_4256_gb300 import emc, learned, synth
+    torch = torch_cuda
+    ds = synth.make_dataset(32, 32, 3000, 2.0, radius=8.0)
+    quat, w = emc.quat_generate(3)
+    grid = torch.as_tensor(ds.model_true.astype(np.float32), device="cuda")
+    M = 64
+    ctx = emc.Context(32, ds.q, quat, w, ds.K.shape[0], precision="bf16_split",
+                      w_floor=1e-10 * float(ds.model_true.mean()), n_cand=M, store_scores=True)
+    ctx.set_frames(torch.as_tensor(ds.K, device="cuda"))
+    ctx.iteration(grid)
+    tidx, tprob = ctx.targets_from_scores(16)
+    feat = ctx.features()
+    train, test = learned.split_rows(ds.K.shape[0])
+    nrot = quat.shape[0]
+
+    def recall(prop):
+        cand = prop.propose(feat, M, ds.K.shape[0])
+        ctx.set_candidates(cand)
+        mm = ctx.missed_mass().cpu().numpy()
+        return float(1.0 - mm[test].mean())
+
+    prop = learned.Proposal(nrot)
+    before = recall(prop)
+    hist = prop.train(feat, tidx, tprob, train, epochs=30, batch=256, lr=1e-3)
+    after = recall(prop)
+    assert hist[-1] < hist[0]
+    assert after > before + 0.1 and after > 2 * M / nrot, (before, after, hist[0], hist[-1])
