@@ -42,6 +42,7 @@ WORKLOAD_TEXT = {
               "0.3 photons/pixel",
 }
 DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3"}
+LEARNED_FORMS = ("learned",)
 
 
 def parse_args():
@@ -54,9 +55,12 @@ def parse_args():
     ap.add_argument("--workload", default="emc64", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
     ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
-    ap.add_argument("--forms", default="fp32,bf16",
+    ap.add_argument("--forms", default="fp32,bf16,learned",
                     help="other precisions to time briefly (comma list, '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-iters", type=int, default=30,
+                    help="iterations of the learned-vs-dense model comparison (0 to skip)")
+    ap.add_argument("--n-cand", type=int, default=512, help="candidate rotations per frame")
     ap.add_argument("--recompute", action="store_true",
                     help="two-pass streamed E-step (pass 2 recomputes the scores) instead of "
                          "keeping the pass-1 scores in HBM")
@@ -239,6 +243,98 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
     return ms, {k: v / steps for k, v in phases.items()}, kernels, lls[-1]
 
 
+def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, world):
+    """Learned proposal + sparse Maximize with a dense fallback every 5th
+    iteration (the dense one also measures the missed responsibility mass).
+    Untimed set-up: 2 dense iterations from the start model give the soft
+    targets, the MLP trains on 90% of the frames, candidates = its top-M."""
+    from paper_1409_4256_gb300 import learned
+    n_rot, n_data = quat.shape[0], ds.K.shape[0]
+    M = min(args.n_cand, n_rot)
+    floor = 1e-10 * float(ds.model_start.mean())
+    ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split", w_floor=floor,
+                      store_scores=True, n_cand=M, device=str(grid.device), stream=stream)
+    ctx.set_frames(K_dev, stream=stream)
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        g1, _ = ctx.iteration(grid, stream=stream)
+        g2, _ = ctx.iteration(g1, stream=stream)
+        tidx, tprob = ctx.targets_from_scores(32, stream=stream)
+        feat = ctx.features(stream=stream)
+        train, test = learned.split_rows(n_data)
+        prop = learned.Proposal(n_rot, device=str(grid.device))
+        hist = prop.train(feat, tidx, tprob, train, epochs=8, batch=512, lr=1e-3, stream=stream)
+        cand = prop.propose(feat, M, n_data, stream=stream)
+        ctx.set_candidates(cand, stream=stream)
+        ctx.iteration(g2, stream=stream)  # dense E-step on the current model for the recall
+        mm = ctx.missed_mass(stream=stream).cpu().numpy()
+        stream.synchronize()
+        setup_s = time.perf_counter() - t0
+        # timed: cycles of 4 sparse iterations and 1 dense fallback
+        out = torch.empty_like(grid)
+        for _ in range(2):
+            ctx.sparse_iteration(g2, out, stats=False, stream=stream)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        cycles = max(1, args.steps // 5 + 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(cycles):
+            for _ in range(4):
+                ctx.sparse_iteration(g2, out, stats=False, stream=stream)
+            ctx.iteration(g2, out, stats=False, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / (5 * cycles)
+        e0.record(stream)
+        for _ in range(5):
+            ctx.sparse_iteration(g2, out, stats=False, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms_sparse = e0.elapsed_time(e1) / 5
+    res = {"value": world * n_rot * n_data / (ms * 1e-3), "ms_per_step": ms,
+           "ms_sparse_iteration": ms_sparse,
+           "evaluated_pairs_per_s": world * M * n_data / (ms_sparse * 1e-3),
+           "candidates": M, "schedule": "4 sparse + 1 dense per 5 iterations",
+           "train_loss_first_last": [hist[0], hist[-1]],
+           "heldout_captured_mass": float(1.0 - mm[test].mean()),
+           "train_captured_mass": float(1.0 - mm[train].mean()), "setup_s": setup_s}
+    if args.learned_iters > 0:
+        # model after N iterations, learned schedule vs dense, same start
+        dense_ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split",
+                                w_floor=floor, store_scores=True, device=str(grid.device),
+                                stream=stream)
+        dense_ctx.set_frames(K_dev, stream=stream)
+        with torch.cuda.stream(stream):
+            a, b = g2.clone(), torch.empty_like(g2)
+            for _ in range(args.learned_iters):
+                dense_ctx.iteration(a, b, stats=False, stream=stream)
+                a, b = b, a
+            c, d = g2.clone(), torch.empty_like(g2)
+            missed = []
+            for it in range(args.learned_iters):
+                if it % 5 == 4:
+                    ctx.iteration(c, d, stats=False, stream=stream)
+                    missed.append(float(ctx.missed_mass(stream=stream).mean().item()))
+                else:
+                    ctx.sparse_iteration(c, d, stats=False, stream=stream)
+                c, d = d, c
+            stream.synchronize()
+        ref = a.double()
+        res["iters_compared"] = args.learned_iters
+        res["rel_model_diff_vs_dense"] = float(torch.linalg.norm(c.double() - ref) /
+                                               torch.linalg.norm(ref))
+        truth = torch.as_tensor(ds.model_true, device=grid.device)
+        res["rel_model_err_vs_truth"] = {
+            "dense": float(torch.linalg.norm(ref - truth) / torch.linalg.norm(truth)),
+            "learned": float(torch.linalg.norm(c.double() - truth) / torch.linalg.norm(truth))}
+        res["mean_missed_mass_at_dense_steps"] = missed
+        del dense_ctx
+    del ctx
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -325,6 +421,13 @@ def run_ours(args):
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
     for f in [x for x in args.forms.split(",") if x and x != args.precision]:
+        if f in LEARNED_FORMS:
+            try:
+                forms[f] = learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream,
+                                        dist, world)
+            except Exception as e:
+                forms[f] = {"error": str(e)[:300]}
+            continue
         try:
             c2 = make_ctx(f)
             fms, fph, _, fll = time_form(torch, emc, c2, grid, 2, 1, stream, dist)
