@@ -218,7 +218,8 @@ cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t
 
 // ------------------------------------------------------ sparse contractions --
 // One CTA per rotation row: log W_j split into (hi on the 1/8 grid, rest) in
-// shared memory; each warp takes one (frame, slot) pair of the row's list.
+// shared memory; each warp takes pairs (frame, slot) of the row's list, two
+// at a time, reading the frames' K rows 8 pixels (16 bytes) per lane.
 template <int PREC>
 __global__ void __launch_bounds__(256)
     sparse_scores_kernel(const void* __restrict__ L, int64_t plane_stride, int64_t ld_pix,
@@ -228,9 +229,9 @@ __global__ void __launch_bounds__(256)
   const int64_t j = blockIdx.x;
   const int64_t e0 = off[j], e1 = off[j + 1];
   if (e0 == e1) return;
-  extern __shared__ float sm[];
-  float* Lh = sm;
-  float* Lr = sm + ld_pix;
+  extern __shared__ float4 sm4[];
+  float* Lh = reinterpret_cast<float*>(sm4);
+  float* Lr = Lh + ld_pix;
   for (int64_t i = threadIdx.x; i < ld_pix; i += blockDim.x) {
     float h, r;
     if (PREC == EMC_PREC_FP32) {
@@ -248,24 +249,48 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   const double bj = bias[j];
-  const int lane = threadIdx.x & 31;
-  for (int64_t e = e0 + (threadIdx.x >> 5); e < e1; e += blockDim.x >> 5) {
-    const int2 km = ent[e];
-    const uint32_t* Kr = reinterpret_cast<const uint32_t*>(Kb + (int64_t)km.x * ld_pix);
-    float ah = 0.f, ar = 0.f;
-    for (int64_t i2 = lane; i2 < ld_pix / 2; i2 += 32) {
-      const uint32_t w = Kr[i2];
-      const float k0 = __uint_as_float(w << 16), k1 = __uint_as_float(w & 0xffff0000u);
-      ah = fmaf(k0, Lh[2 * i2], ah);
-      ah = fmaf(k1, Lh[2 * i2 + 1], ah);
-      ar = fmaf(k0, Lr[2 * i2], ar);
-      ar = fmaf(k1, Lr[2 * i2 + 1], ar);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t n8 = ld_pix / 8;
+  for (int64_t e = e0 + 2 * wid; e < e1; e += 2 * nw) {
+    const bool two = e + 1 < e1;
+    const int2 ka = ent[e];
+    const int2 kb = two ? ent[e + 1] : ka;
+    const uint4* Ka = reinterpret_cast<const uint4*>(Kb + (int64_t)ka.x * ld_pix);
+    const uint4* Kc = reinterpret_cast<const uint4*>(Kb + (int64_t)kb.x * ld_pix);
+    float ah = 0.f, ar = 0.f, bh = 0.f, br = 0.f;
+    for (int64_t g = lane; g < n8; g += 32) {
+      const uint4 wa = Ka[g], wb = Kc[g];
+      const float4 h0 = reinterpret_cast<const float4*>(Lh)[2 * g];
+      const float4 h1 = reinterpret_cast<const float4*>(Lh)[2 * g + 1];
+      const float4 r0 = reinterpret_cast<const float4*>(Lr)[2 * g];
+      const float4 r1 = reinterpret_cast<const float4*>(Lr)[2 * g + 1];
+      const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+      const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+      const uint32_t ua[4] = {wa.x, wa.y, wa.z, wa.w}, ub[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const float a0 = __uint_as_float(ua[c] << 16), a1 = __uint_as_float(ua[c] & 0xffff0000u);
+        const float b0 = __uint_as_float(ub[c] << 16), b1 = __uint_as_float(ub[c] & 0xffff0000u);
+        ah = fmaf(a0, hv[2 * c], ah);
+        ah = fmaf(a1, hv[2 * c + 1], ah);
+        ar = fmaf(a0, rv[2 * c], ar);
+        ar = fmaf(a1, rv[2 * c + 1], ar);
+        bh = fmaf(b0, hv[2 * c], bh);
+        bh = fmaf(b1, hv[2 * c + 1], bh);
+        br = fmaf(b0, rv[2 * c], br);
+        br = fmaf(b1, rv[2 * c + 1], br);
+      }
     }
     for (int o = 16; o; o >>= 1) {
       ah += __shfl_xor_sync(0xffffffffu, ah, o);
       ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      bh += __shfl_xor_sync(0xffffffffu, bh, o);
+      br += __shfl_xor_sync(0xffffffffu, br, o);
     }
-    if (lane == 0) Sc[(int64_t)km.x * M + km.y] = ((double)ah + (double)ar) + bj;
+    if (lane == 0) {
+      Sc[(int64_t)ka.x * M + ka.y] = ((double)ah + (double)ar) + bj;
+      if (two) Sc[(int64_t)kb.x * M + kb.y] = ((double)bh + (double)br) + bj;
+    }
   }
 }
 
@@ -295,7 +320,9 @@ __global__ void sparse_lse_kernel(const double* __restrict__ Sc, int64_t n_data,
 }
 
 // One CTA per rotation row: Num_j = sum over the row's list of P_jk K_k; the
-// K column of ones at n_pix gives den_j. Rows without candidates are zeroed.
+// K column of ones at n_pix gives den_j. Each thread owns 8 consecutive pixels
+// (one 16-byte load of a K row per pair), the list is staged in shared memory
+// in segments and walked four pairs at a time. Rows without pairs are zeroed.
 __global__ void __launch_bounds__(256)
     sparse_update_kernel(const uint16_t* __restrict__ Kb, int64_t ld_pix, int64_t n_pix,
                          const int64_t* __restrict__ off, const int2* __restrict__ ent, int M,
@@ -304,12 +331,13 @@ __global__ void __launch_bounds__(256)
   const int64_t j = blockIdx.x;
   const int64_t e0 = off[j], e1 = off[j + 1];
   float* out = Num + j * ld_pix;
-  constexpr int kSeg = 512;
+  constexpr int kSeg = 1024;
   __shared__ int sk[kSeg];
   __shared__ float sp[kSeg];
-  for (int64_t i0 = 0; i0 < ld_pix; i0 += 256) {
-    const int64_t i = i0 + threadIdx.x;
-    float acc = 0.f;
+  const int64_t n8 = ld_pix / 8;
+  for (int64_t g0 = 0; g0 < n8; g0 += 256) {
+    const int64_t g = g0 + threadIdx.x;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int64_t s0 = e0; s0 < e1; s0 += kSeg) {
       const int ns = (int)min((int64_t)kSeg, e1 - s0);
       __syncthreads();
@@ -319,12 +347,45 @@ __global__ void __launch_bounds__(256)
         sp[t] = Pc[(int64_t)km.x * M + km.y];
       }
       __syncthreads();
-      if (i < ld_pix)
-        for (int t = 0; t < ns; t++) acc = fmaf(sp[t], bf16_val(Kb[(int64_t)sk[t] * ld_pix + i]), acc);
+      if (g < n8) {
+        int t = 0;
+        for (; t + 4 <= ns; t += 4) {
+          uint4 w[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++)
+            w[u] = reinterpret_cast<const uint4*>(Kb + (int64_t)sk[t + u] * ld_pix)[g];
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const float p = sp[t + u];
+            const uint32_t wv[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+              acc[2 * c] = fmaf(p, __uint_as_float(wv[c] << 16), acc[2 * c]);
+              acc[2 * c + 1] = fmaf(p, __uint_as_float(wv[c] & 0xffff0000u), acc[2 * c + 1]);
+            }
+          }
+        }
+        for (; t < ns; t++) {
+          const uint4 w = reinterpret_cast<const uint4*>(Kb + (int64_t)sk[t] * ld_pix)[g];
+          const float p = sp[t];
+          const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            acc[2 * c] = fmaf(p, __uint_as_float(wv[c] << 16), acc[2 * c]);
+            acc[2 * c + 1] = fmaf(p, __uint_as_float(wv[c] & 0xffff0000u), acc[2 * c + 1]);
+          }
+        }
+      }
     }
-    if (i < ld_pix) {
-      out[i] = acc;
-      if (i == n_pix) den[j] = acc;
+    if (g < n8) {
+      float4* o4 = reinterpret_cast<float4*>(out + 8 * g);
+      o4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      o4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      if (n_pix >= 8 * g && n_pix < 8 * g + 8) {
+#pragma unroll
+        for (int c = 0; c < 8; c++)
+          if (8 * g + c == n_pix) den[j] = acc[c];
+      }
     }
   }
 }

@@ -42,7 +42,7 @@ namespace {
 
 enum { MODE_PASS1 = 0, MODE_NORMALIZE = 1, MODE_UPDATE = 2 };
 
-constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int BM = 128, BN = 256;
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
@@ -51,19 +51,30 @@ constexpr int kSmemBudget = 220 * 1024;
 constexpr int kScratchBytes = 8 * 1024;
 constexpr float kSentinel = -3.0e38f;
 
+// K-block width: 64 elements with 128-byte swizzle, or 32 with 64-byte swizzle
+// for the three-plane score contractions, whose 80 KB stages would otherwise
+// leave room for only two in flight (too shallow to hide the load latency).
 template <int MODE, int NA>
 struct TcCfg {
-  static constexpr int A_BYTES = BM * BK * 2;  // one 128 x 64 BF16 plane
-  static constexpr int B_BYTES = BN * BK * 2;  // 256 x 64 BF16
+  static constexpr int BK = (MODE != MODE_UPDATE && NA == 3) ? 32 : 64;
+  static constexpr int A_BYTES = BM * BK * 2;  // one 128 x BK BF16 plane
+  static constexpr int B_BYTES = BN * BK * 2;  // 256 x BK BF16
   static constexpr int STAGE = NA * A_BYTES + B_BYTES;
   static constexpr int NACC = (MODE != MODE_UPDATE && NA == 3) ? 2 : 1;
   static constexpr int STAGES_RAW = (kSmemBudget - kScratchBytes - 1024 - 256) / STAGE;
-  static constexpr int STAGES = STAGES_RAW > 4 ? 4 : STAGES_RAW;
+  static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
   static constexpr uint32_t TMEM_COLS = NACC * BN;
   static constexpr int SMEM = 1024 + STAGES * STAGE + 256 + kScratchBytes;
   static constexpr uint32_t IDESC = idesc_bf16(BM, BN, MODE == MODE_UPDATE ? 1 : 0);
   static_assert(STAGES >= 2, "shared memory too small for two stages");
 };
+
+// K-major operand descriptor for k-step kk (16 elements) inside a K block
+template <int BK>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t base, int kk) {
+  if (BK == 64) return sdesc_sw128(base + kk * 32, 16, 1024);
+  return sdesc_sw64(base + kk * 32, 512);
+}
 
 struct TcArgs {
   int n_mtiles, n_ntiles, group, kblocks;
@@ -178,14 +189,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t* st = stages + s * C::STAGE;
 #pragma unroll
           for (int p = 0; p < NA; p++)
-            tma_load_3d(st + p * C::A_BYTES, &mapA, full + s, kb * BK, mt * BM, p);
+            tma_load_3d(st + p * C::A_BYTES, &mapA, full + s, kb * C::BK, mt * BM, p);
           uint8_t* sb = st + NA * C::A_BYTES;
           if (MODE != MODE_UPDATE) {
-            tma_load_2d(sb, &mapB, full + s, kb * BK, nt * BN);
+            tma_load_2d(sb, &mapB, full + s, kb * C::BK, nt * BN);
           } else {
 #pragma unroll
             for (int j = 0; j < BN / 64; j++)
-              tma_load_2d(sb + j * (64 * BK * 2), &mapB, full + s, nt * BN + j * 64, kb * BK);
+              tma_load_2d(sb + j * (64 * C::BK * 2), &mapB, full + s, nt * BN + j * 64, kb * C::BK);
           }
         }
       }
@@ -220,12 +231,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t sA = smem_u32(stages + s * C::STAGE);
           const uint32_t sB = sA + NA * C::A_BYTES;
 #pragma unroll
-          for (int k = 0; k < BK / 16; k++) {
+          for (int k = 0; k < C::BK / 16; k++) {
             if (MODE != MODE_UPDATE) {
-              const uint64_t bdesc = sdesc_sw128(sB + k * 32, 16, 1024);
+              const uint64_t bdesc = kmajor_desc<C::BK>(sB, k);
 #pragma unroll
               for (int p = 0; p < NA; p++) {
-                const uint64_t adesc = sdesc_sw128(sA + p * C::A_BYTES + k * 32, 16, 1024);
+                const uint64_t adesc = kmajor_desc<C::BK>(sA + p * C::A_BYTES, k);
                 const int acc = (NA == 3 && p > 0) ? 1 : 0;
                 const bool first = (kb == 0 && k == 0 && p <= 1);
                 umma_bf16(tmem + acc * BN, adesc, bdesc, C::IDESC, first ? 0u : 1u);
@@ -233,10 +244,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
               // B is MN-major: 64-pixel chunks 8 KB apart (LBO), 8-frame groups
               // 1 KB apart (SBO); 16 frames per instruction advance 2 KB.
-              const uint64_t bdesc = sdesc_sw128(sB + k * 2048, 64 * BK * 2, 1024);
+              const uint64_t bdesc = sdesc_sw128(sB + k * 2048, 64 * C::BK * 2, 1024);
 #pragma unroll
               for (int p = 0; p < NA; p++) {
-                const uint64_t adesc = sdesc_sw128(sA + p * C::A_BYTES + k * 32, 16, 1024);
+                const uint64_t adesc = kmajor_desc<C::BK>(sA + p * C::A_BYTES, k);
                 const bool first = (kb == 0 && k == 0 && p == 0);
                 umma_bf16(tmem, adesc, bdesc, C::IDESC, first ? 0u : 1u);
               }
@@ -421,9 +432,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// BF16 tensor map, 128-byte swizzle; dims innermost first, strides in bytes.
+// BF16 tensor map (128- or 64-byte swizzle); dims innermost first, strides in bytes.
 bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
-              const uint64_t* strides, const uint32_t* box) {
+              const uint64_t* strides, const uint32_t* box, int swizzle_bytes = 128) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t d[3], st[2];
@@ -434,7 +445,8 @@ bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
   }
   for (int i = 0; i < rank - 1; i++) st[i] = strides[i];
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st,
-            b, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            b, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -464,13 +476,15 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs a, cudaS
 
 bool maps_scores(const Planes& L, int nterms, int64_t rows, const uint16_t* Kb, int64_t ld_data,
                  int64_t ld_pix, CUtensorMap* mA, CUtensorMap* mB) {
+  const uint32_t bk = nterms == 3 ? 32 : 64;  // TcCfg<scores, NA>::BK
+  const int sw = nterms == 3 ? 64 : 128;
   const uint64_t dA[3] = {(uint64_t)ld_pix, (uint64_t)rows, (uint64_t)nterms};
   const uint64_t sA[2] = {(uint64_t)L.ld * 2, (uint64_t)L.plane_stride * 2};
-  const uint32_t bA[3] = {BK, BM, 1};
+  const uint32_t bA[3] = {bk, BM, 1};
   const uint64_t dB[2] = {(uint64_t)ld_pix, (uint64_t)ld_data};
   const uint64_t sB[1] = {(uint64_t)ld_pix * 2};
-  const uint32_t bB[2] = {BK, BN};
-  return make_map(mA, L.base, 3, dA, sA, bA) && make_map(mB, Kb, 2, dB, sB, bB);
+  const uint32_t bB[2] = {bk, BN};
+  return make_map(mA, L.base, 3, dA, sA, bA, sw) && make_map(mB, Kb, 2, dB, sB, bB, sw);
 }
 
 TcArgs base_args(int64_t rows, int n_ntiles, int kblocks) {
@@ -492,7 +506,7 @@ cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int
                             int32_t* status, cudaStream_t s) {
   CUtensorMap mA, mB;
   if (!maps_scores(L, nterms, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
-  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / BK));
+  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / (nterms == 3 ? 32 : 64)));
   a.nrot = rows;  // validity comes from the bias (-inf on padding rows)
   a.n_data = n_data;
   a.ld_data = ld_data;
@@ -514,7 +528,7 @@ cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias,
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if (!maps_scores(L, nterms, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
-  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / BK));
+  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / (nterms == 3 ? 32 : 64)));
   a.nrot = nrot;
   a.n_data = n_data;
   a.ld_data = ld_data;
@@ -534,13 +548,13 @@ cudaError_t launch_tc_update(const Planes& P, int nterms, int64_t rows, const ui
   CUtensorMap mA, mB;
   const uint64_t dA[3] = {(uint64_t)ld_data, (uint64_t)rows, (uint64_t)nterms};
   const uint64_t sA[2] = {(uint64_t)P.ld * 2, (uint64_t)P.plane_stride * 2};
-  const uint32_t bA[3] = {BK, BM, 1};
+  const uint32_t bA[3] = {64, BM, 1};
   const uint64_t dB[2] = {(uint64_t)ld_pix, (uint64_t)ld_data};
   const uint64_t sB[1] = {(uint64_t)ld_pix * 2};
-  const uint32_t bB[2] = {64, BK};
+  const uint32_t bB[2] = {64, 64};
   if (!make_map(&mA, P.base, 3, dA, sA, bA) || !make_map(&mB, Kb, 2, dB, sB, bB))
     return cudaErrorInvalidValue;
-  TcArgs a = base_args(rows, (int)((ld_pix + BN - 1) / BN), (int)(ld_data / BK));
+  TcArgs a = base_args(rows, (int)((ld_pix + BN - 1) / BN), (int)(ld_data / 64));
   a.nrot = rows;
   a.ld_pix = ld_pix;
   a.n_pix = n_pix;

@@ -134,6 +134,18 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo, ui
   return d;
 }
 
+// Shared-memory matrix descriptor, 64-byte swizzle (layout type 4), K-major:
+// rows of 64 bytes, 8-row atoms of 512 bytes (SBO), sm_100 descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;  // LBO unused for swizzled K-major layouts
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
 // Instruction descriptor of tcgen05.mma.kind::f16: BF16 x BF16 -> FP32,
 // M x N tile, A K-major, B K-major (b_mn_major = 0) or MN-major (1).
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn_major) {
