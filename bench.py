@@ -41,7 +41,7 @@ WORKLOAD_TEXT = {
     "emc128": "128^3 grid, 128x128 detector, n=16 -> 204960 rotations, 100000 Poisson frames, "
               "0.3 photons/pixel",
 }
-DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3"}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3", "fp16_split": "f16x2"}
 LEARNED_FORMS = ("learned",)
 
 
@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--workload", default="emc64", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
     ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
-    ap.add_argument("--forms", default="fp32,bf16,learned",
+    ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned",
                     help="other precisions to time briefly (comma list, '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-iters", type=int, default=30,

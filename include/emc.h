@@ -59,7 +59,12 @@ typedef enum emc_precision {
   EMC_PREC_BF16 = 1,
   /* log W = hi + mid + lo in BF16 with hi on a fixed 1/8 grid (accumulated
    * exactly), tcgen05 BF16 MMA; P = hi + lo in BF16 for the update */
-  EMC_PREC_BF16_SPLIT = 2
+  EMC_PREC_BF16_SPLIT = 2,
+  /* log W = hi + rest in FP16 with hi on a fixed 1/64 grid (accumulated
+   * exactly), frames in FP16 (counts <= 2048 exact), tcgen05 FP16 MMA;
+   * P = (hi + lo) / 2^14 in FP16 for the update. Two MMAs per K step where
+   * the BF16 split needs three. Frames must keep sum_i K_ik below 8192. */
+  EMC_PREC_FP16_SPLIT = 3
 } emc_precision;
 
 typedef enum emc_compress_mode {
@@ -148,9 +153,10 @@ int emc_ctx_destroy(emc_ctx* ctx);
 int emc_ctx_status(emc_ctx* ctx, int* device_status);
 
 /* Load frames K (Sec. 2.1, photon counts): device int32 [n_data][ld_k],
- * ld_k >= n_pix, into the context's padded BF16 frame buffer. Counts must lie
- * in [0, 256] (exact in BF16) and sum to below 65536 per frame; otherwise the
- * device status becomes EMC_ERR_UNSUPPORTED. */
+ * ld_k >= n_pix, into the context's padded frame buffer (BF16, or FP16 for
+ * EMC_PREC_FP16_SPLIT). Counts must lie in [0, 256] (exact in BF16; [0, 2048]
+ * in FP16) and sum to below 65536 per frame (8192 for FP16_SPLIT); otherwise
+ * the device status becomes EMC_ERR_UNSUPPORTED. */
 int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stream);
 
 /* e-step, Eq. 2.9, for rotations [rot0, rot0 + nrot):
@@ -158,6 +164,7 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
  * L (device): FP32 -> float[rows][ld_pix] = log W;
  *             BF16 -> bf16[rows][ld_pix];
  *             BF16_SPLIT -> bf16[3][rows][ld_pix] (hi, mid, lo planes);
+ *             FP16_SPLIT -> fp16[2][rows][ld_pix] (hi, rest planes);
  *             padding columns and rows are written as 0.
  * bias (device double[rows]) = log w_j - sum_i W_ij (-inf on padding rows). */
 int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void* L,
@@ -179,7 +186,8 @@ int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, do
  * size rotations x frames kept); otherwise they are read from the buffer
  * emc_loglik filled (L and bias are then not read and may be NULL).
  * P (device): FP32 -> float[rows][ld_data]; BF16 / BF16_SPLIT ->
- * bf16[2][rows][ld_data] (hi, lo planes, P = hi + lo; lo is 0 for BF16).
+ * bf16[2][rows][ld_data] (hi, lo planes, P = hi + lo; lo is 0 for BF16);
+ * FP16_SPLIT -> fp16[2][rows][ld_data], P = (hi + lo) / 2^14.
  * Padding frames and rows are written as 0. */
 int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
                   const double* lse_m, const double* lse_s, const void* scores, void* P,
@@ -196,9 +204,10 @@ int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
  * library, and allocates nothing at call time.
  *  cfg: N, precision, n_pix, n_rot, n_data are read (host).
  *  L, bias: device, as emc_expand writes them for nrot rotations.
- *  frames: device BF16 [ld_data][ld_pix] (ld_pix = round_up(n_pix + 1, 64),
- *          ld_data = round_up(n_data, 256)): counts in columns < n_pix, 1 in
- *          column n_pix for every real frame, 0 everywhere else.
+ *  frames: device BF16 (FP16 for EMC_PREC_FP16_SPLIT) [ld_data][ld_pix]
+ *          (ld_pix = round_up(n_pix + 1, 64), ld_data = round_up(n_data, 256)):
+ *          counts in columns < n_pix, 1 in column n_pix for every real frame,
+ *          0 everywhere else.
  *  lse_m, lse_s, accumulate: as emc_loglik.
  *  device_status: optional device int32; a bounded wait that gives up or a
  *          non-finite merge writes a negative emc_status there (first wins).

@@ -26,7 +26,9 @@ size_t score_bytes(int64_t rows, int64_t ld_data) {
   return sizeof(float) * (size_t)(rows + rows / 32) * ld_data;
 }
 
-int planes_L(int prec) { return prec == EMC_PREC_BF16_SPLIT ? 3 : 1; }
+int planes_L(int prec) {
+  return prec == EMC_PREC_BF16_SPLIT ? 3 : (prec == EMC_PREC_FP16_SPLIT ? 2 : 1);
+}
 size_t elem_L(int prec) { return prec == EMC_PREC_FP32 ? 4 : 2; }
 int planes_P(int prec) { return prec == EMC_PREC_FP32 ? 1 : 2; }
 size_t elem_P(int prec) { return prec == EMC_PREC_FP32 ? 4 : 2; }
@@ -37,11 +39,12 @@ int check_config(const emc_config* c) {
   if (c->n_pix < 1 || c->n_rot < 1 || c->n_data < 1) return EMC_ERR_ARG;
   if (c->n_pix > (1LL << 24) || c->n_rot > (1LL << 31) || c->n_data > (1LL << 31))
     return EMC_ERR_ARG;
-  if (c->precision < EMC_PREC_FP32 || c->precision > EMC_PREC_BF16_SPLIT) return EMC_ERR_ARG;
+  if (c->precision < EMC_PREC_FP32 || c->precision > EMC_PREC_FP16_SPLIT) return EMC_ERR_ARG;
   if (c->compress_mode != EMC_COMPRESS_DEFERRED && c->compress_mode != EMC_COMPRESS_IDW)
     return EMC_ERR_ARG;
   if (!(c->w_floor > 0.0) || !isfinite(c->w_floor)) return EMC_ERR_ARG;
-  if (c->precision == EMC_PREC_BF16_SPLIT && log(c->w_floor) < (double)kHiMin)
+  if ((c->precision == EMC_PREC_BF16_SPLIT || c->precision == EMC_PREC_FP16_SPLIT) &&
+      log(c->w_floor) < (double)kHiMin)
     return EMC_ERR_UNSUPPORTED;
   if (c->rot_chunk < 0 || (c->flags & ~EMC_FLAG_STORE_SCORES) != 0) return EMC_ERR_ARG;
   if (c->n_cand < 0 || c->n_cand > c->n_rot || c->n_cand > 4096) return EMC_ERR_ARG;
@@ -297,7 +300,8 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
   if (!ctx || !K || ld_k < ctx->cfg.n_pix) return EMC_ERR_ARG;
   const Layout& y = ctx->lay;
   CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb,
-                        ctx->status, (cudaStream_t)stream));
+                        ctx->cfg.precision == EMC_PREC_FP16_SPLIT, ctx->status,
+                        (cudaStream_t)stream));
   ctx->frames_loaded = true;
   return EMC_OK;
 }
@@ -339,8 +343,7 @@ int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const d
     tiles = simt_pass1_tiles(rows);
   } else {
     Planes p{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
-    int nterms = c->cfg.precision == EMC_PREC_BF16_SPLIT ? 3 : 1;
-    CU(launch_tc_pass1(p, nterms, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix, pm, ps,
+    CU(launch_tc_pass1(p, c->cfg.precision, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix, pm, ps,
                        S, Sref, c->status, s));
     tiles = tc_pass1_tiles(rows);
   }
@@ -369,8 +372,7 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
   } else {
     Planes lp{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
     Planes pp{P, Prows * y.ld_data, y.ld_data};
-    int nterms = c->cfg.precision == EMC_PREC_BF16_SPLIT ? 3 : 1;
-    CU(launch_tc_normalize(lp, nterms, bias, rows, nrot, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix,
+    CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix,
                            lse_m, lse_s, (float2*)(c->ws + y.lse2), pp, c->status, s));
   }
   return EMC_OK;
@@ -385,8 +387,7 @@ int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num
                           den, s));
   } else {
     Planes pp{(void*)P, Prows * y.ld_data, y.ld_data};
-    const int nterms = c->cfg.precision == EMC_PREC_BF16_SPLIT ? 2 : 1;
-    CU(launch_tc_update(pp, nterms, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num, den,
+    CU(launch_tc_update(pp, c->cfg.precision, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num, den,
                         c->status, s));
   }
   return EMC_OK;
@@ -563,7 +564,8 @@ extern "C" {
 int emc_features(emc_ctx* ctx, float* feat, emc_stream stream) {
   if (!ctx || !feat || !ctx->frames_loaded) return EMC_ERR_ARG;
   const Layout& y = ctx->lay;
-  CU(launch_features(ctx->Kb, y.ld_pix, ctx->cfg.n_pix, ctx->cfg.n_data, y.ld_data,
+  CU(launch_features(ctx->Kb, ctx->cfg.precision == EMC_PREC_FP16_SPLIT, y.ld_pix,
+                     ctx->cfg.n_pix, ctx->cfg.n_data, y.ld_data,
                      (const int16_t*)(ctx->ws + y.fbin), (const float*)(ctx->ws + y.finv), feat,
                      (cudaStream_t)stream));
   return EMC_OK;
@@ -656,7 +658,8 @@ int emc_sparse_estep(emc_ctx* ctx, const void* L, const double* bias, float* P, 
 int emc_sparse_update(emc_ctx* ctx, const float* P, float* Num, float* den, emc_stream stream) {
   if (!ctx || !P || !Num || !den || !ctx->frames_loaded || !ctx->cand_loaded) return EMC_ERR_ARG;
   const Layout& y = ctx->lay;
-  CU(launch_sparse_update(ctx->Kb, y.ld_pix, ctx->cfg.n_pix, (const int64_t*)(ctx->ws + y.coff),
+  CU(launch_sparse_update(ctx->Kb, ctx->cfg.precision == EMC_PREC_FP16_SPLIT, y.ld_pix,
+                          ctx->cfg.n_pix, (const int64_t*)(ctx->ws + y.coff),
                           (const int2*)(ctx->ws + y.cent), ctx->cfg.n_cand, P, y.rows, Num, den,
                           (cudaStream_t)stream));
   return EMC_OK;

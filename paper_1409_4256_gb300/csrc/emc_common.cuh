@@ -1,6 +1,7 @@
 // emc_common.cuh -- device helpers shared by the libemc kernels (sm_103a).
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -107,12 +108,35 @@ __device__ __forceinline__ float bf16_val(uint16_t u) {
   return __uint_as_float(((uint32_t)u) << 16);
 }
 
-// The fixed grid of the hi term of the three-term split: multiples of 1/8 in
-// [-32, 32); every such value has at most 8 significant bits (exact in BF16)
-// and sums of (integer count <= 256) x (hi) stay on the 1/8 grid, so FP32
-// accumulates them exactly while |sum| < 2^21.
+// FP16 helpers (round to nearest even).
+__device__ __forceinline__ uint16_t fp16_bits(float x) {
+  __half h = __float2half_rn(x);
+  return *reinterpret_cast<uint16_t*>(&h);
+}
+__device__ __forceinline__ float fp16_val(uint16_t u) {
+  return __half2float(*reinterpret_cast<const __half*>(&u));
+}
+
+// The fixed grid of the hi term of the BF16 three-term split: multiples of
+// 1/8 in [-32, 32); every such value has at most 8 significant bits (exact in
+// BF16) and sums of (integer count <= 256) x (hi) stay on the 1/8 grid, so
+// FP32 accumulates them exactly while |sum| < 2^21.
 constexpr float kHiScale = 8.0f;
 constexpr float kHiMin = -32.0f;
 constexpr float kHiMax = 32.0f - 0.125f;
+// The FP16 two-term split: hi on the 1/64 grid in [-32, 32) (at most 11
+// significant bits, exact in FP16); counts <= 2048 are exact in FP16 and the
+// products and partial sums stay on the 1/64 grid, exact in FP32 while
+// |sum| < 2^18.
+constexpr float kHi16Scale = 64.0f;
+constexpr float kHi16Max = 32.0f - 1.0f / 64.0f;
+// Scores are split for the epilogues into a part on the 1/64 grid (every
+// 1/8-grid value lies on it) and a small rest; references (maxima, lse) use
+// the same grid so that subtracting them is exact.
+constexpr float kGrid = 64.0f;
+constexpr double kGridD = 64.0;
+// FP16 responsibilities are stored scaled by 2^14 (P <= 1 stays below the
+// FP16 maximum, P down to ~4e-9 stays normal); the update removes the scale.
+constexpr float kP16Scale = 16384.0f;
 
 }  // namespace emc

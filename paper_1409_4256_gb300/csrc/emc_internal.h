@@ -24,9 +24,10 @@ struct Planes {
   int64_t ld;            // elements between rows
 };
 
+// fp16 != 0: frames in FP16 (EMC_PREC_FP16_SPLIT), else BF16
 cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
-                               int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int32_t* status,
-                               cudaStream_t s);
+                               int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int fp16,
+                               int32_t* status, cudaStream_t s);
 
 cudaError_t launch_expand(const Geom& g, const float* grid, const double* quat,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
@@ -61,18 +62,18 @@ cudaError_t launch_normalize_scores(const float* S, const float* Sref, const flo
 cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
                               double* out, cudaStream_t s);
 
-// tcgen05 forms (precision EMC_PREC_BF16 / EMC_PREC_BF16_SPLIT).
-cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int64_t rows,
+// tcgen05 forms (precision EMC_PREC_BF16 / BF16_SPLIT / FP16_SPLIT).
+cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
                             int32_t* status, cudaStream_t s);
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
-cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias, int64_t rows,
+cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bias, int64_t rows,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
                                 float2* lse2, Planes P, int32_t* status, cudaStream_t s);
-// nterms: 2 (P = hi + lo planes) or 1 (hi plane only).
-cudaError_t launch_tc_update(const Planes& P, int nterms, int64_t rows, const uint16_t* Kb,
+// P planes: hi + lo (BF16 split, FP16 split) or hi only (BF16).
+cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
                              int32_t* status, cudaStream_t s);
 int64_t tc_pass1_tiles(int64_t rows);
@@ -95,9 +96,10 @@ struct MlpLayout {
   int64_t work_floats;
 };
 MlpLayout mlp_layout(int64_t n_out, int64_t B);
-cudaError_t launch_features(const uint16_t* Kb, int64_t ld_pix, int64_t n_pix, int64_t n_data,
-                            int64_t ld_data, const int16_t* bin, const float* inv_count,
-                            float* feat, cudaStream_t s);
+// kf16 != 0: frames in FP16, else BF16 (likewise for the sparse update)
+cudaError_t launch_features(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
+                            int64_t n_data, int64_t ld_data, const int16_t* bin,
+                            const float* inv_count, float* feat, cudaStream_t s);
 cudaError_t mlp_forward(const MlpLayout& y, const float* params, const float* X, int B,
                         float* work, float* logits, cudaStream_t s);
 cudaError_t mlp_train_step(const MlpLayout& y, float* params, float* grads, float* adam_m,
@@ -119,7 +121,7 @@ cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, c
                                  const int2* ent, int M, double* Sc, cudaStream_t s);
 cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data, int M, float* Pc,
                               double* lse_c, int32_t* status, cudaStream_t s);
-cudaError_t launch_sparse_update(const uint16_t* Kb, int64_t ld_pix, int64_t n_pix,
+cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
                                  const int64_t* off, const int2* ent, int M, const float* Pc,
                                  int64_t rows, float* Num, float* den, cudaStream_t s);
 cudaError_t launch_missed_mass(const float* S, const float* Sref, int64_t ld_data,

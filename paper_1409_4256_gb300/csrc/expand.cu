@@ -9,7 +9,7 @@
 //   bias_j = log w_j - sum_i W_ij,
 // the rotation-only part of S_jk = sum_i K_ik log W_ij - W_ij + log w_j.
 // Writes are coalesced along pixels; HBM traffic is the L write (4 B/(i,j)
-// for FP32, 2 B for BF16, 6 B for the three-term split).
+// for FP32, 2 B for BF16, 6 B for the three-term split, 4 B for the FP16 split).
 #include "emc_common.cuh"
 #include "emc_internal.h"
 
@@ -66,6 +66,13 @@ __global__ void __launch_bounds__(kExpandThreads)
       Lf[i] = L;
     } else if (PREC == EMC_PREC_BF16) {
       Lb[i] = bf16_bits(L);
+    } else if (PREC == EMC_PREC_FP16_SPLIT) {
+      // two-term FP16 split: hi on the 1/64 grid, rest r (|r| <= 1/128)
+      float hi = rintf(L * kHi16Scale) * (1.0f / kHi16Scale);
+      if (used && (hi < kHiMin || hi > kHi16Max)) bad = 1;
+      hi = fminf(fmaxf(hi, kHiMin), kHi16Max);
+      Lb[i] = fp16_bits(hi);
+      Lb[i + plane_stride] = fp16_bits(L - hi);
     } else {
       // three-term split: hi on the 1/8 grid, residual r = mid + lo
       float hi = rintf(L * kHiScale) * (1.0f / kHiScale);
@@ -107,6 +114,11 @@ cudaError_t launch_expand(const Geom& g, const float* grid, const double* quat,
       expand_kernel<EMC_PREC_BF16><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid,
                                                        quat, logw, nrot, w_floor, L.base,
                                                        L.plane_stride, bias, status);
+      break;
+    case EMC_PREC_FP16_SPLIT:
+      expand_kernel<EMC_PREC_FP16_SPLIT><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
+                                                             grid, quat, logw, nrot, w_floor,
+                                                             L.base, L.plane_stride, bias, status);
       break;
     default:
       expand_kernel<EMC_PREC_BF16_SPLIT><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,

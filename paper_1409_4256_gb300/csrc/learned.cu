@@ -20,7 +20,8 @@ namespace emc {
 // ---------------------------------------------------------------- features --
 // One CTA per frame: per-bin sums of the counts in shared memory, then
 // log(1 + sum / pixels-in-bin); bins with no pixel give 0.
-__global__ void features_kernel(const uint16_t* __restrict__ Kb, int64_t ld_pix, int64_t n_pix,
+__global__ void features_kernel(const uint16_t* __restrict__ Kb, int kf16, int64_t ld_pix,
+                                int64_t n_pix,
                                 int64_t n_data, const int16_t* __restrict__ bin,
                                 const float* __restrict__ inv_count, float* __restrict__ feat) {
   const int64_t k = blockIdx.x;
@@ -29,7 +30,8 @@ __global__ void features_kernel(const uint16_t* __restrict__ Kb, int64_t ld_pix,
   __syncthreads();
   if (k < n_data)
     for (int64_t i = threadIdx.x; i < n_pix; i += blockDim.x) {
-      const float c = bf16_val(Kb[k * ld_pix + i]);
+      const uint16_t u = Kb[k * ld_pix + i];
+      const float c = kf16 ? fp16_val(u) : bf16_val(u);
       if (c != 0.f) atomicAdd(&acc[bin[i]], c);
     }
   __syncthreads();
@@ -37,10 +39,11 @@ __global__ void features_kernel(const uint16_t* __restrict__ Kb, int64_t ld_pix,
     feat[k * kFeat + b] = k < n_data ? log1pf(acc[b] * inv_count[b]) : 0.f;
 }
 
-cudaError_t launch_features(const uint16_t* Kb, int64_t ld_pix, int64_t n_pix, int64_t n_data,
-                            int64_t ld_data, const int16_t* bin, const float* inv_count,
-                            float* feat, cudaStream_t s) {
-  features_kernel<<<(unsigned)ld_data, 256, 0, s>>>(Kb, ld_pix, n_pix, n_data, bin, inv_count, feat);
+cudaError_t launch_features(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
+                            int64_t n_data, int64_t ld_data, const int16_t* bin,
+                            const float* inv_count, float* feat, cudaStream_t s) {
+  features_kernel<<<(unsigned)ld_data, 256, 0, s>>>(Kb, kf16, ld_pix, n_pix, n_data, bin,
+                                                    inv_count, feat);
   return cudaGetLastError();
 }
 

@@ -4,14 +4,15 @@
 
 namespace emc {
 
-// Frames K (Sec. 2.1) int32 [n_data][ld_k] -> BF16 [ld_data][ld_pix]:
+// Frames K (Sec. 2.1) int32 [n_data][ld_k] -> BF16 (or FP16) [ld_data][ld_pix]:
 // columns < n_pix hold the counts, column n_pix holds 1 for every real frame
 // (so that the M-step contraction also yields den_j = sum_k P_jk), everything
-// else 0. Counts outside [0, 256] or a frame total >= 65536 would break the
-// exact BF16 / exact hi-term accumulation and are flagged.
+// else 0. Counts outside [0, 256] (BF16; [0, 2048] FP16) or a frame total at or
+// above 65536 (8192 for FP16) would break the exact conversion or the exact
+// hi-term accumulation and are flagged.
 __global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, int64_t n_data,
                                    int64_t n_pix, int64_t ld_pix, uint16_t* __restrict__ Kb,
-                                   int32_t* status) {
+                                   int fp16, int32_t* status) {
   const int64_t k = blockIdx.x;
   __shared__ long long red[8];
   long long tot = 0;
@@ -21,14 +22,14 @@ __global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, 
     if (k < n_data) {
       if (i < n_pix) {
         int32_t c = K[k * ld_k + i];
-        if (c < 0 || c > 256) bad = 1;
+        if (c < 0 || c > (fp16 ? 2048 : 256)) bad = 1;
         tot += c;
         v = (float)c;
       } else if (i == n_pix) {
         v = 1.f;
       }
     }
-    Kb[k * ld_pix + i] = bf16_bits(v);
+    Kb[k * ld_pix + i] = fp16 ? fp16_bits(v) : bf16_bits(v);
   }
   for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
@@ -36,15 +37,16 @@ __global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, 
   if (threadIdx.x == 0) {
     long long s = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
-    if (s >= 65536) bad = 1;
+    if (s >= (fp16 ? 8192 : 65536)) bad = 1;
   }
   if (bad) set_status(status, EMC_ERR_UNSUPPORTED);
 }
 
 cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
-                               int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int32_t* status,
-                               cudaStream_t s) {
-  prep_frames_kernel<<<(unsigned)ld_data, 256, 0, s>>>(K, ld_k, n_data, n_pix, ld_pix, Kb, status);
+                               int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int fp16,
+                               int32_t* status, cudaStream_t s) {
+  prep_frames_kernel<<<(unsigned)ld_data, 256, 0, s>>>(K, ld_k, n_data, n_pix, ld_pix, Kb, fp16,
+                                                       status);
   return cudaGetLastError();
 }
 
@@ -116,7 +118,7 @@ cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t 
   return cudaGetLastError();
 }
 
-// lse_k = m_k + log s_k (FP64) split into a part on the 1/8 grid and a small
+// lse_k = m_k + log s_k (FP64) split into a part on the 1/64 grid and a small
 // FP32 rest, so that kernels can subtract it from grid-aligned scores exactly.
 __global__ void lse_split_kernel(const double* __restrict__ lse_m, const double* __restrict__ lse_s,
                                  int64_t n_data, int64_t ld_data, float2* __restrict__ out) {
@@ -127,7 +129,7 @@ __global__ void lse_split_kernel(const double* __restrict__ lse_m, const double*
     return;
   }
   const double l = lse_m[k] + log(lse_s[k]);
-  const double h = rint(l * 8.0) * 0.125;
+  const double h = rint(l * kGridD) / kGridD;
   out[k] = make_float2((float)h, (float)(l - h));
 }
 
@@ -140,12 +142,12 @@ cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n
 
 // E-step pass 2 from stored scores (Eq. 2.4): P_jk = exp(S_jk - lse_k) with
 // S_jk held as d_jk (relative to its 32-row group maximum r_gk, which lies on
-// the 1/8 grid); r_gk - hi(lse_k) is exact, so
+// the 1/64 grid); r_gk - hi(lse_k) is exact, so
 //   P_jk = exp(d_jk + ((r_gk - hi_k) - lo_k)).
 // One thread per 4 consecutive frames of one row: 16-byte loads of d,
 // 8-byte (BF16 x4) or 16-byte (FP32 x4) stores of P. HBM-bound: 4 B read and
 // 4 B written per (j, k).
-template <int OUT>  // 0: FP32 P; 1: BF16 hi plane only; 2: BF16 hi + lo planes
+template <int OUT>  // 0: FP32 P; 1: BF16 hi plane only; 2: BF16 hi + lo; 3: FP16 hi + lo of 2^14 P
 __global__ void normalize_scores_kernel(const float* __restrict__ S, const float* __restrict__ Sref,
                                         const float2* __restrict__ lse2, int64_t rows,
                                         int64_t nrot, int64_t ld_data, int64_t n_data,
@@ -172,8 +174,14 @@ __global__ void normalize_scores_kernel(const float* __restrict__ S, const float
     uint16_t h[4], l[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      h[u] = bf16_bits(p[u]);
-      l[u] = OUT == 2 ? bf16_bits(p[u] - bf16_val(h[u])) : (uint16_t)0;
+      if (OUT == 3) {
+        const float ps = p[u] * kP16Scale;
+        h[u] = fp16_bits(ps);
+        l[u] = fp16_bits(ps - fp16_val(h[u]));
+      } else {
+        h[u] = bf16_bits(p[u]);
+        l[u] = OUT == 2 ? bf16_bits(p[u] - bf16_val(h[u])) : (uint16_t)0;
+      }
     }
     uint16_t* ph = reinterpret_cast<uint16_t*>(P) + j * ld_data + k;
     *reinterpret_cast<uint2*>(ph) = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16),
@@ -190,6 +198,9 @@ cudaError_t launch_normalize_scores(const float* S, const float* Sref, const flo
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (precision == EMC_PREC_FP32)
     normalize_scores_kernel<0><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
+                                                       P_plane);
+  else if (precision == EMC_PREC_FP16_SPLIT)
+    normalize_scores_kernel<3><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
                                                        P_plane);
   else if (precision == EMC_PREC_BF16)
     normalize_scores_kernel<1><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,

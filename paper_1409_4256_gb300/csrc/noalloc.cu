@@ -64,7 +64,7 @@ extern "C" int emc_loglik_static(const emc_config* cfg, const void* L, const dou
                                  emc_stream stream) {
   if (!cfg || !L || !bias || !frames || !lse_m || !lse_s) return EMC_ERR_ARG;
   if (cfg->n_pix < 1 || cfg->n_data < 1 || nrot < 1 || nrot > cfg->n_rot) return EMC_ERR_ARG;
-  if (cfg->precision < EMC_PREC_FP32 || cfg->precision > EMC_PREC_BF16_SPLIT) return EMC_ERR_ARG;
+  if (cfg->precision < EMC_PREC_FP32 || cfg->precision > EMC_PREC_FP16_SPLIT) return EMC_ERR_ARG;
   const int64_t ld_pix = up(cfg->n_pix + 1, 64);
   const int64_t ld_data = up(cfg->n_data, 256);
   const int64_t rows = up(nrot, 128);
@@ -79,7 +79,6 @@ extern "C" int emc_loglik_static(const emc_config* cfg, const void* L, const dou
   double* part_m = reinterpret_cast<double*>(base);
   float* part_s = reinterpret_cast<float*>(part_m + (block / 64) * ld_data);
   cudaStream_t s = (cudaStream_t)stream;
-  const int nterms = cfg->precision == EMC_PREC_BF16_SPLIT ? 3 : 1;
   const size_t elem = cfg->precision == EMC_PREC_FP32 ? 4 : 2;
   for (int64_t r0 = 0; r0 < rows; r0 += block) {
     const int64_t nb = block < rows - r0 ? block : rows - r0;
@@ -92,7 +91,7 @@ extern "C" int emc_loglik_static(const emc_config* cfg, const void* L, const dou
       tiles = simt_pass1_tiles(nb);
     } else {
       Planes p{const_cast<char*>(Lb), rows * ld_pix, ld_pix};
-      e = launch_tc_pass1(p, nterms, bias + r0, nb, frames, ld_data, cfg->n_data, ld_pix, part_m,
+      e = launch_tc_pass1(p, cfg->precision, bias + r0, nb, frames, ld_data, cfg->n_data, ld_pix, part_m,
                           part_s, nullptr, nullptr, device_status, s);
       tiles = tc_pass1_tiles(nb);
     }

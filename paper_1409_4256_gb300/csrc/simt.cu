@@ -123,11 +123,11 @@ __global__ void __launch_bounds__(S_THREADS)
   }
   __syncthreads();
   if (S) {
-    // scores relative to the tile's column maximum rounded to the 1/8 grid
+    // scores relative to the tile's column maximum rounded to the 1/64 grid
     float ref[8];
 #pragma unroll
     for (int j = 0; j < 8; j++)
-      ref[j] = mcol[j] == -INFINITY ? -3.0e38f : (float)(rint(mcol[j] * 8.0) * 0.125);
+      ref[j] = mcol[j] == -INFINITY ? -3.0e38f : (float)(rint(mcol[j] * kGridD) / kGridD);
 #pragma unroll
     for (int i = 0; i < 4; i++) {
       float v[8];

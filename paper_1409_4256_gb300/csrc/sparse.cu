@@ -217,6 +217,18 @@ cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t
 }
 
 // ------------------------------------------------------ sparse contractions --
+// two frame counts packed in 32 bits (BF16 or FP16 frames)
+template <bool KF16>
+__device__ __forceinline__ void unpack2(uint32_t w, float& lo, float& hi) {
+  if (KF16) {
+    lo = fp16_val((uint16_t)(w & 0xffffu));
+    hi = fp16_val((uint16_t)(w >> 16));
+  } else {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xffff0000u);
+  }
+}
+
 // One CTA per rotation row: log W_j split into (hi on the 1/8 grid, rest) in
 // shared memory; each warp takes pairs (frame, slot) of the row's list, two
 // at a time, reading the frames' K rows 8 pixels (16 bytes) per lane.
@@ -238,6 +250,10 @@ __global__ void __launch_bounds__(256)
       const float x = reinterpret_cast<const float*>(L)[j * ld_pix + i];
       h = rintf(x * 8.f) * 0.125f;
       r = x - h;
+    } else if (PREC == EMC_PREC_FP16_SPLIT) {
+      const uint16_t* Lb = reinterpret_cast<const uint16_t*>(L) + j * ld_pix + i;
+      h = fp16_val(Lb[0]);
+      r = fp16_val(Lb[plane_stride]);
     } else {
       const uint16_t* Lb = reinterpret_cast<const uint16_t*>(L) + j * ld_pix + i;
       h = bf16_val(Lb[0]);
@@ -269,8 +285,9 @@ __global__ void __launch_bounds__(256)
       const uint32_t ua[4] = {wa.x, wa.y, wa.z, wa.w}, ub[4] = {wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
       for (int c = 0; c < 4; c++) {
-        const float a0 = __uint_as_float(ua[c] << 16), a1 = __uint_as_float(ua[c] & 0xffff0000u);
-        const float b0 = __uint_as_float(ub[c] << 16), b1 = __uint_as_float(ub[c] & 0xffff0000u);
+        float a0, a1, b0, b1;
+        unpack2<PREC == EMC_PREC_FP16_SPLIT>(ua[c], a0, a1);
+        unpack2<PREC == EMC_PREC_FP16_SPLIT>(ub[c], b0, b1);
         ah = fmaf(a0, hv[2 * c], ah);
         ah = fmaf(a1, hv[2 * c + 1], ah);
         ar = fmaf(a0, rv[2 * c], ar);
@@ -323,6 +340,7 @@ __global__ void sparse_lse_kernel(const double* __restrict__ Sc, int64_t n_data,
 // K column of ones at n_pix gives den_j. Each thread owns 8 consecutive pixels
 // (one 16-byte load of a K row per pair), the list is staged in shared memory
 // in segments and walked four pairs at a time. Rows without pairs are zeroed.
+template <bool KF16>
 __global__ void __launch_bounds__(256)
     sparse_update_kernel(const uint16_t* __restrict__ Kb, int64_t ld_pix, int64_t n_pix,
                          const int64_t* __restrict__ off, const int2* __restrict__ ent, int M,
@@ -360,8 +378,10 @@ __global__ void __launch_bounds__(256)
             const uint32_t wv[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-              acc[2 * c] = fmaf(p, __uint_as_float(wv[c] << 16), acc[2 * c]);
-              acc[2 * c + 1] = fmaf(p, __uint_as_float(wv[c] & 0xffff0000u), acc[2 * c + 1]);
+              float k0, k1;
+              unpack2<KF16>(wv[c], k0, k1);
+              acc[2 * c] = fmaf(p, k0, acc[2 * c]);
+              acc[2 * c + 1] = fmaf(p, k1, acc[2 * c + 1]);
             }
           }
         }
@@ -371,8 +391,10 @@ __global__ void __launch_bounds__(256)
           const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
           for (int c = 0; c < 4; c++) {
-            acc[2 * c] = fmaf(p, __uint_as_float(wv[c] << 16), acc[2 * c]);
-            acc[2 * c + 1] = fmaf(p, __uint_as_float(wv[c] & 0xffff0000u), acc[2 * c + 1]);
+            float k0, k1;
+            unpack2<KF16>(wv[c], k0, k1);
+            acc[2 * c] = fmaf(p, k0, acc[2 * c]);
+            acc[2 * c + 1] = fmaf(p, k1, acc[2 * c + 1]);
           }
         }
       }
@@ -427,6 +449,13 @@ cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, c
       sparse_scores_kernel<EMC_PREC_BF16><<<(unsigned)rows, 256, smem, s>>>(
           L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
       break;
+    case EMC_PREC_FP16_SPLIT:
+      e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_FP16_SPLIT>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      sparse_scores_kernel<EMC_PREC_FP16_SPLIT><<<(unsigned)rows, 256, smem, s>>>(
+          L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
+      break;
     default:
       e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_BF16_SPLIT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -445,10 +474,15 @@ cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data,
   return cudaGetLastError();
 }
 
-cudaError_t launch_sparse_update(const uint16_t* Kb, int64_t ld_pix, int64_t n_pix,
+cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
                                  const int64_t* off, const int2* ent, int M, const float* Pc,
                                  int64_t rows, float* Num, float* den, cudaStream_t s) {
-  sparse_update_kernel<<<(unsigned)rows, 256, 0, s>>>(Kb, ld_pix, n_pix, off, ent, M, Pc, Num, den);
+  if (kf16)
+    sparse_update_kernel<true><<<(unsigned)rows, 256, 0, s>>>(Kb, ld_pix, n_pix, off, ent, M, Pc,
+                                                              Num, den);
+  else
+    sparse_update_kernel<false><<<(unsigned)rows, 256, 0, s>>>(Kb, ld_pix, n_pix, off, ent, M, Pc,
+                                                               Num, den);
   return cudaGetLastError();
 }
 

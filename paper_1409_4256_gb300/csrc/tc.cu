@@ -52,20 +52,21 @@ constexpr int kScratchBytes = 8 * 1024;
 constexpr float kSentinel = -3.0e38f;
 
 // K-block width: 64 elements with 128-byte swizzle, or 32 with 64-byte swizzle
-// for the three-plane score contractions, whose 80 KB stages would otherwise
-// leave room for only two in flight (too shallow to hide the load latency).
-template <int MODE, int NA>
+// for the multi-plane score contractions, whose 64-80 KB stages would
+// otherwise leave room for only two or three in flight (too shallow to hide
+// the load latency). F16: FP16 operands (FP16 split) instead of BF16.
+template <int MODE, int NA, bool F16>
 struct TcCfg {
-  static constexpr int BK = (MODE != MODE_UPDATE && NA == 3) ? 32 : 64;
+  static constexpr int BK = (MODE != MODE_UPDATE && NA >= 2) ? 32 : 64;
   static constexpr int A_BYTES = BM * BK * 2;  // one 128 x BK BF16 plane
   static constexpr int B_BYTES = BN * BK * 2;  // 256 x BK BF16
   static constexpr int STAGE = NA * A_BYTES + B_BYTES;
-  static constexpr int NACC = (MODE != MODE_UPDATE && NA == 3) ? 2 : 1;
+  static constexpr int NACC = (MODE != MODE_UPDATE && NA >= 2) ? 2 : 1;
   static constexpr int STAGES_RAW = (kSmemBudget - kScratchBytes - 1024 - 256) / STAGE;
   static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
   static constexpr uint32_t TMEM_COLS = NACC * BN;
   static constexpr int SMEM = 1024 + STAGES * STAGE + 256 + kScratchBytes;
-  static constexpr uint32_t IDESC = idesc_bf16(BM, BN, MODE == MODE_UPDATE ? 1 : 0);
+  static constexpr uint32_t IDESC = idesc_f16kind(BM, BN, MODE == MODE_UPDATE ? 1 : 0, F16);
   static_assert(STAGES >= 2, "shared memory too small for two stages");
 };
 
@@ -125,11 +126,11 @@ __device__ __forceinline__ void fail(volatile int* abort, int32_t* status) {
   set_status(status, EMC_ERR_TIMEOUT);
 }
 
-template <int MODE, int NA>
+template <int MODE, int NA, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const TcArgs a) {
-  using C = TcCfg<MODE, NA>;
+  using C = TcCfg<MODE, NA, F16>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int p = 0; p < NA; p++) {
                 const uint64_t adesc = kmajor_desc<C::BK>(sA + p * C::A_BYTES, k);
-                const int acc = (NA == 3 && p > 0) ? 1 : 0;
+                const int acc = (NA >= 2 && p > 0) ? 1 : 0;
                 const bool first = (kb == 0 && k == 0 && p <= 1);
                 umma_bf16(tmem + acc * BN, adesc, bdesc, C::IDESC, first ? 0u : 1u);
               }
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const double b = a.bias[row];
         valid = valid && b > -INFINITY;
         if (valid) {
-          const double h = rint(b * 8.0) * 0.125;
+          const double h = rint(b * kGridD) / kGridD;
           bh = (float)h;
           bl = (float)(b - h);
         }
@@ -310,6 +311,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (MODE == MODE_UPDATE) {
           const int64_t n0 = (int64_t)nt * BN + col0;
           if (n0 < a.ld_pix) {
+            if (F16) {  // FP16 responsibilities carry a 2^14 scale
+#pragma unroll
+              for (int i = 0; i < 32; i++)
+                v0[i] = __float_as_uint(__uint_as_float(v0[i]) * (1.0f / kP16Scale));
+            }
             float* dst = a.Num + row * a.ld_pix + n0;
 #pragma unroll
             for (int i = 0; i < 32; i += 4)
@@ -322,16 +328,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           continue;
         }
-        // scores: exact part xh (multiples of 1/8), small part xl
+        // scores: exact part xh (multiples of 1/64), small part xl
         float xh[32], xl[32];
 #pragma unroll
         for (int i = 0; i < 32; i++) {
           float h = __uint_as_float(v0[i]) + bh;
           float l = (C::NACC == 2 ? __uint_as_float(v1[i]) : 0.f) + bl;
-          const float rr = rintf(l * 8.f) * 0.125f;
+          const float rr = rintf(l * kGrid) * (1.0f / kGrid);
           h += rr;
           l -= rr;
-          big |= fabsf(h) > 1048576.f;
+          big |= fabsf(h) > 131072.f;
           xh[i] = valid ? h : kSentinel;
           xl[i] = valid ? l : 0.f;
         }
@@ -370,14 +376,22 @@ __global__ void __launch_bounds__(kThreads, 1)
               const float d = (xh[i + u] - L.x) + (xl[i + u] - L.y);
               pr[u] = (valid && k0 + i + u < a.n_data) ? __expf(d) : 0.f;
             }
-            const uint16_t h0 = bf16_bits(pr[0]), h1 = bf16_bits(pr[1]);
-            ph[i / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-            if (NA == 3) {
-              const uint16_t l0 = bf16_bits(pr[0] - bf16_val(h0));
-              const uint16_t l1 = bf16_bits(pr[1] - bf16_val(h1));
+            if (F16) {  // FP16 hi + lo of 2^14 P
+              const float s0 = pr[0] * kP16Scale, s1 = pr[1] * kP16Scale;
+              const uint16_t h0 = fp16_bits(s0), h1 = fp16_bits(s1);
+              ph[i / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+              const uint16_t l0 = fp16_bits(s0 - fp16_val(h0)), l1 = fp16_bits(s1 - fp16_val(h1));
               pl[i / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
             } else {
-              pl[i / 2] = 0u;
+              const uint16_t h0 = bf16_bits(pr[0]), h1 = bf16_bits(pr[1]);
+              ph[i / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+              if (NA == 3) {
+                const uint16_t l0 = bf16_bits(pr[0] - bf16_val(h0));
+                const uint16_t l1 = bf16_bits(pr[1] - bf16_val(h1));
+                pl[i / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+              } else {
+                pl[i / 2] = 0u;
+              }
             }
           }
           uint16_t* dh = a.P + row * a.ld_data + k0;
@@ -389,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      if (NA == 3 && big && valid) set_status(a.status, EMC_ERR_NUMERIC);
+      if (NA >= 2 && big && valid) set_status(a.status, EMC_ERR_NUMERIC);
       if (MODE == MODE_PASS1) {
         named_bar(1, kEpiThreads);
         const int col = et;  // one frame column per epilogue thread
@@ -434,7 +448,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // BF16 tensor map (128- or 64-byte swizzle); dims innermost first, strides in bytes.
 bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
-              const uint64_t* strides, const uint32_t* box, int swizzle_bytes = 128) {
+              const uint64_t* strides, const uint32_t* box, int swizzle_bytes = 128,
+              bool fp16 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t d[3], st[2];
@@ -444,7 +459,8 @@ bool make_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
     b[i] = box[i];
   }
   for (int i = 0; i < rank - 1; i++) st[i] = strides[i];
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st,
+  return fn(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+            (cuuint32_t)rank, const_cast<void*>(base), d, st,
             b, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -457,12 +473,12 @@ int num_sms() {
   return n > 0 ? n : 148;
 }
 
-template <int MODE, int NA>
+template <int MODE, int NA, bool F16>
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs a, cudaStream_t s) {
-  using C = TcCfg<MODE, NA>;
+  using C = TcCfg<MODE, NA, F16>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel<MODE, NA>,
+    cudaError_t e = cudaFuncSetAttribute(tc_kernel<MODE, NA, F16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -470,21 +486,28 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs a, cudaS
   const int T = a.n_mtiles * a.n_ntiles;
   if (T <= 0) return cudaSuccess;
   const int grid = T < num_sms() ? T : num_sms();
-  tc_kernel<MODE, NA><<<grid, kThreads, C::SMEM, s>>>(mA, mB, a);
+  tc_kernel<MODE, NA, F16><<<grid, kThreads, C::SMEM, s>>>(mA, mB, a);
   return cudaGetLastError();
 }
 
-bool maps_scores(const Planes& L, int nterms, int64_t rows, const uint16_t* Kb, int64_t ld_data,
+// planes of log W and operand type of each tensor-core precision
+int score_planes(int precision) {
+  return precision == EMC_PREC_BF16_SPLIT ? 3 : (precision == EMC_PREC_FP16_SPLIT ? 2 : 1);
+}
+
+bool maps_scores(const Planes& L, int precision, int64_t rows, const uint16_t* Kb, int64_t ld_data,
                  int64_t ld_pix, CUtensorMap* mA, CUtensorMap* mB) {
-  const uint32_t bk = nterms == 3 ? 32 : 64;  // TcCfg<scores, NA>::BK
-  const int sw = nterms == 3 ? 64 : 128;
+  const int nterms = score_planes(precision);
+  const bool f16 = precision == EMC_PREC_FP16_SPLIT;
+  const uint32_t bk = nterms >= 2 ? 32 : 64;  // TcCfg<scores, NA, F16>::BK
+  const int sw = nterms >= 2 ? 64 : 128;
   const uint64_t dA[3] = {(uint64_t)ld_pix, (uint64_t)rows, (uint64_t)nterms};
   const uint64_t sA[2] = {(uint64_t)L.ld * 2, (uint64_t)L.plane_stride * 2};
   const uint32_t bA[3] = {bk, BM, 1};
   const uint64_t dB[2] = {(uint64_t)ld_pix, (uint64_t)ld_data};
   const uint64_t sB[1] = {(uint64_t)ld_pix * 2};
   const uint32_t bB[2] = {bk, BN};
-  return make_map(mA, L.base, 3, dA, sA, bA, sw) && make_map(mB, Kb, 2, dB, sB, bB, sw);
+  return make_map(mA, L.base, 3, dA, sA, bA, sw, f16) && make_map(mB, Kb, 2, dB, sB, bB, sw, f16);
 }
 
 TcArgs base_args(int64_t rows, int n_ntiles, int kblocks) {
@@ -500,13 +523,15 @@ TcArgs base_args(int64_t rows, int n_ntiles, int kblocks) {
 
 int64_t tc_pass1_tiles(int64_t rows) { return rows / BM; }
 
-cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int64_t rows,
+cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
                             int32_t* status, cudaStream_t s) {
   CUtensorMap mA, mB;
-  if (!maps_scores(L, nterms, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
-  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / (nterms == 3 ? 32 : 64)));
+  if (!maps_scores(L, precision, rows, Kb, ld_data, ld_pix, &mA, &mB))
+    return cudaErrorInvalidValue;
+  const int nterms = score_planes(precision);
+  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / (nterms >= 2 ? 32 : 64)));
   a.nrot = rows;  // validity comes from the bias (-inf on padding rows)
   a.n_data = n_data;
   a.ld_data = ld_data;
@@ -517,18 +542,22 @@ cudaError_t launch_tc_pass1(const Planes& L, int nterms, const double* bias, int
   a.S = S;
   a.Sref = Sref;
   a.status = status;
-  return nterms == 3 ? launch<MODE_PASS1, 3>(mA, mB, a, s) : launch<MODE_PASS1, 1>(mA, mB, a, s);
+  if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_PASS1, 2, true>(mA, mB, a, s);
+  return nterms == 3 ? launch<MODE_PASS1, 3, false>(mA, mB, a, s)
+                     : launch<MODE_PASS1, 1, false>(mA, mB, a, s);
 }
 
-cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias, int64_t rows,
+cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bias, int64_t rows,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
                                 float2* lse2, Planes P, int32_t* status, cudaStream_t s) {
   cudaError_t e = launch_lse_split(lse_m, lse_s, n_data, ld_data, lse2, s);
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
-  if (!maps_scores(L, nterms, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
-  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / (nterms == 3 ? 32 : 64)));
+  if (!maps_scores(L, precision, rows, Kb, ld_data, ld_pix, &mA, &mB))
+    return cudaErrorInvalidValue;
+  const int nterms = score_planes(precision);
+  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / (nterms >= 2 ? 32 : 64)));
   a.nrot = nrot;
   a.n_data = n_data;
   a.ld_data = ld_data;
@@ -538,13 +567,16 @@ cudaError_t launch_tc_normalize(const Planes& L, int nterms, const double* bias,
   a.P = reinterpret_cast<uint16_t*>(P.base);
   a.P_plane = P.plane_stride;
   a.status = status;
-  return nterms == 3 ? launch<MODE_NORMALIZE, 3>(mA, mB, a, s)
-                     : launch<MODE_NORMALIZE, 1>(mA, mB, a, s);
+  if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_NORMALIZE, 2, true>(mA, mB, a, s);
+  return nterms == 3 ? launch<MODE_NORMALIZE, 3, false>(mA, mB, a, s)
+                     : launch<MODE_NORMALIZE, 1, false>(mA, mB, a, s);
 }
 
-cudaError_t launch_tc_update(const Planes& P, int nterms, int64_t rows, const uint16_t* Kb,
+cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
                              int32_t* status, cudaStream_t s) {
+  const int nterms = precision == EMC_PREC_BF16 ? 1 : 2;
+  const bool f16 = precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
   const uint64_t dA[3] = {(uint64_t)ld_data, (uint64_t)rows, (uint64_t)nterms};
   const uint64_t sA[2] = {(uint64_t)P.ld * 2, (uint64_t)P.plane_stride * 2};
@@ -552,7 +584,7 @@ cudaError_t launch_tc_update(const Planes& P, int nterms, int64_t rows, const ui
   const uint64_t dB[2] = {(uint64_t)ld_pix, (uint64_t)ld_data};
   const uint64_t sB[1] = {(uint64_t)ld_pix * 2};
   const uint32_t bB[2] = {64, 64};
-  if (!make_map(&mA, P.base, 3, dA, sA, bA) || !make_map(&mB, Kb, 2, dB, sB, bB))
+  if (!make_map(&mA, P.base, 3, dA, sA, bA, 128, f16) || !make_map(&mB, Kb, 2, dB, sB, bB, 128, f16))
     return cudaErrorInvalidValue;
   TcArgs a = base_args(rows, (int)((ld_pix + BN - 1) / BN), (int)(ld_data / 64));
   a.nrot = rows;
@@ -562,7 +594,9 @@ cudaError_t launch_tc_update(const Planes& P, int nterms, int64_t rows, const ui
   a.Num = Num;
   a.den = den;
   a.status = status;
-  return nterms == 2 ? launch<MODE_UPDATE, 2>(mA, mB, a, s) : launch<MODE_UPDATE, 1>(mA, mB, a, s);
+  if (f16) return launch<MODE_UPDATE, 2, true>(mA, mB, a, s);
+  return nterms == 2 ? launch<MODE_UPDATE, 2, false>(mA, mB, a, s)
+                     : launch<MODE_UPDATE, 1, false>(mA, mB, a, s);
 }
 
 }  // namespace emc

@@ -146,12 +146,12 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr, uint32_t sbo) {
   return d;
 }
 
-// Instruction descriptor of tcgen05.mma.kind::f16: BF16 x BF16 -> FP32,
-// M x N tile, A K-major, B K-major (b_mn_major = 0) or MN-major (1).
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn_major) {
+// Instruction descriptor of tcgen05.mma.kind::f16: BF16 x BF16 (or FP16 x
+// FP16) -> FP32, M x N tile, A K-major, B K-major (b_mn_major = 0) or MN-major (1).
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, int b_mn_major, bool fp16) {
   return (1u << 4)                       // D format: F32
-         | (1u << 7)                     // A format: BF16
-         | (1u << 10)                    // B format: BF16
+         | ((fp16 ? 0u : 1u) << 7)       // A format: F16 (0) or BF16 (1)
+         | ((fp16 ? 0u : 1u) << 10)      // B format, same as A
          | ((uint32_t)b_mn_major << 16)  // B major-ness
          | ((uint32_t)(N >> 3) << 17)    // N / 8
          | ((uint32_t)(M >> 4) << 24);   // M / 16

@@ -16,8 +16,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libemc.so")
 
-PREC_FP32, PREC_BF16, PREC_BF16_SPLIT = 0, 1, 2
-PRECISIONS = {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16_split": PREC_BF16_SPLIT}
+PREC_FP32, PREC_BF16, PREC_BF16_SPLIT, PREC_FP16_SPLIT = 0, 1, 2, 3
+PRECISIONS = {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16_split": PREC_BF16_SPLIT,
+              "fp16_split": PREC_FP16_SPLIT}
 COMPRESS_DEFERRED, COMPRESS_IDW = 0, 1
 FLAG_STORE_SCORES = 1
 

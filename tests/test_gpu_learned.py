@@ -42,10 +42,11 @@ def ctx_for(torch, p, precision="bf16_split", n_cand=0, store_scores=False):
     return c
 
 
-def test_features(torch_cuda, small_problem):
+@pytest.mark.parametrize("precision", ["bf16_split", "fp16_split"])
+def test_features(torch_cuda, small_problem, precision):
     from oracle import learned as ol
     torch, p = torch_cuda, small_problem
-    ctx = ctx_for(torch, p)
+    ctx = ctx_for(torch, p, precision)
     f = ctx.features()
     torch.cuda.synchronize()
     nd = p["K"].shape[0]
@@ -158,7 +159,7 @@ def _candidates(dense_ref, M, seed=8):
     return np.array(out, dtype=np.int32)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16_split"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16_split", "fp16_split"])
 def test_sparse_steps(torch_cuda, small_problem, dense_ref, precision):
     from oracle import learned as ol
     torch, p = torch_cuda, small_problem
@@ -173,8 +174,9 @@ def test_sparse_steps(torch_cuda, small_problem, dense_ref, precision):
     torch.cuda.synchronize()
     assert ctx.status() == 0
     Pr, lser = ol.sparse_estep(dense_ref["S"], cand)
-    assert np.abs(P.cpu().numpy()[:nd] - Pr).max() <= 1e-4
-    assert np.abs(lse.cpu().numpy()[:nd] - lser).max() <= 1e-4
+    tol = 1e-3 if precision == "fp16_split" else 1e-4  # FP16 rest term, see test_gpu_parity
+    assert np.abs(P.cpu().numpy()[:nd] - Pr).max() <= tol
+    assert np.abs(lse.cpu().numpy()[:nd] - lser).max() <= tol
     Nr, dr = ol.sparse_mstep(Pr, cand, p["K"], nrot)
     assert rel_l2(Num.cpu().numpy()[:nrot, :p["q"].shape[0]], Nr) <= 1e-4
     assert rel_l2(den.cpu().numpy()[:nrot], dr) <= 1e-4

@@ -10,13 +10,19 @@ design notes):
   max |dP| <= 1e-4, rel-L2(model) <= 1e-5  for FP32 and the BF16 split form;
   log W within 2e-6 + 2e-7 |log W| (FP32 trilinear + logf);
   lse within 1e-4 absolute (an lse error d scales all P of a frame by e^-d).
+The FP16 split keeps log W to 2^-19 absolute (its FP16 rest term), which moves
+S by ~sqrt(sum_i K_ik^2) * 2^-19: it meets the model bar (1e-5) but holds lse
+and P only to 1e-3, and log W to 4e-6 + 2e-7 |log W|.
 """
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
-EXACT_PRECISIONS = ["fp32", "bf16_split"]
+EXACT_PRECISIONS = ["fp32", "bf16_split", "fp16_split"]
+# per-element tolerances of each form: (log W absolute, lse, P)
+TOL = {"fp32": (2e-6, 1e-4, 1e-4), "bf16_split": (2e-6, 1e-4, 1e-4),
+       "fp16_split": (4e-6, 1e-3, 1e-3)}
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +66,8 @@ def decode_L(torch, ctx, L, nrot, precision):
     b = ctx.buffer_sizes(nrot)
     if precision == "fp32":
         return L.view(torch.float32).view(b.rows, b.ld_pix).double().cpu().numpy()
-    planes = L.view(torch.bfloat16).view(-1, b.rows, b.ld_pix).double().cpu().numpy()
+    dt = torch.float16 if precision == "fp16_split" else torch.bfloat16
+    planes = L.view(dt).view(-1, b.rows, b.ld_pix).double().cpu().numpy()
     return planes.sum(0)
 
 
@@ -68,6 +75,9 @@ def decode_P(torch, ctx, P, nrot, precision):
     b = ctx.buffer_sizes(nrot)
     if precision == "fp32":
         return P.view(torch.float32).view(b.rows, b.ld_data).double().cpu().numpy()
+    if precision == "fp16_split":  # FP16 hi + lo of 2^14 P
+        planes = P.view(torch.float16).view(2, b.rows, b.ld_data).double().cpu().numpy()
+        return (planes[0] + planes[1]) / 16384.0
     planes = P.view(torch.bfloat16).view(2, b.rows, b.ld_data).double().cpu().numpy()
     return planes[0] + planes[1]
 
@@ -87,7 +97,7 @@ def test_expand(torch_cuda, small_problem, ref, precision):
     Lg = decode_L(torch, ctx, L, nrot, precision)
     Lo = np.log(ref["W"])
     err = np.abs(Lg[:nrot, :npix] - Lo)
-    assert np.all(err <= 2e-6 + 2e-7 * np.abs(Lo)), err.max()
+    assert np.all(err <= TOL[precision][0] + 2e-7 * np.abs(Lo)), err.max()
     assert np.all(Lg[:, npix:] == 0) and np.all(Lg[nrot:] == 0)
     bg = bias.cpu().numpy()
     assert np.abs(bg[:nrot] - ref["bias"]).max() < 1e-6 * np.abs(ref["bias"]).max()
@@ -105,10 +115,10 @@ def test_estep_two_passes(torch_cuda, small_problem, ref, precision):
     torch.cuda.synchronize()
     assert ctx.status() == 0
     lse = (lse_m + torch.log(lse_s)).cpu().numpy()[:nd]
-    assert np.abs(lse - ref["lse"]).max() <= 1e-4
+    assert np.abs(lse - ref["lse"]).max() <= TOL[precision][1]
     Pg = decode_P(torch, ctx, P, nrot, precision)
     dP = np.abs(Pg[:nrot, :nd] - ref["P"]).max()
-    assert dP <= 1e-4, dP
+    assert dP <= TOL[precision][2], dP
     assert np.all(Pg[nrot:] == 0) and np.all(Pg[:, nd:] == 0)
     assert np.allclose(Pg[:nrot, :nd].sum(0), 1.0, atol=1e-3)
 
@@ -127,7 +137,7 @@ def test_estep_from_stored_scores(torch_cuda, small_problem, ref, precision):
     torch.cuda.synchronize()
     assert ctx.status() == 0
     Pg = decode_P(torch, ctx, P, nrot, precision)
-    assert np.abs(Pg[:nrot, :nd] - ref["P"]).max() <= 1e-4
+    assert np.abs(Pg[:nrot, :nd] - ref["P"]).max() <= TOL[precision][2]
     assert np.all(Pg[nrot:] == 0) and np.all(Pg[:, nd:] == 0)
     # the stored scores reproduce the oracle's S_jk
     b = ctx.buffer_sizes(nrot)
@@ -136,7 +146,7 @@ def test_estep_from_stored_scores(torch_cuda, small_problem, ref, precision):
     r = Sf[b.rows * b.ld_data:].reshape(b.rows // 32, b.ld_data)
     S = d + np.repeat(r, 32, axis=0)
     sel = ref["P"] > 1e-6
-    assert np.abs(S[:nrot, :nd][sel] - ref["S"][sel]).max() < 1e-3
+    assert np.abs(S[:nrot, :nd][sel] - ref["S"][sel]).max() < 10 * TOL[precision][1]
     # both pass-2 forms agree
     assert np.abs(decode_P(torch, ctx, P2, nrot, precision) - Pg).max() < 1e-5
 
@@ -167,7 +177,7 @@ def test_loglik_accumulates_over_rotation_blocks(torch_cuda, small_problem, ref,
     m, s = ctx.loglik(Lb, bb, 680, m, s, accumulate=True)
     torch.cuda.synchronize()
     lse = (m + torch.log(s)).cpu().numpy()[:nd]
-    assert np.abs(lse - ref["lse"]).max() <= 1e-4
+    assert np.abs(lse - ref["lse"]).max() <= TOL[precision][1]
 
 
 @pytest.mark.parametrize("precision", EXACT_PRECISIONS)

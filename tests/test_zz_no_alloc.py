@@ -25,16 +25,17 @@ def torch_cuda():
     return torch
 
 
-def frames_bf16(torch, K, ld_data, ld_pix):
-    """The documented frame layout: counts, a column of ones at n_pix, zeros."""
+def frames_bf16(torch, K, ld_data, ld_pix, fp16=False):
+    """The documented frame layout: counts, a column of ones at n_pix, zeros
+    (BF16, or FP16 for the FP16 split)."""
     n_data, n_pix = K.shape
     F = torch.zeros((ld_data, ld_pix), dtype=torch.float32, device="cuda")
     F[:n_data, :n_pix] = torch.as_tensor(K, dtype=torch.float32, device="cuda")
     F[:n_data, n_pix] = 1.0
-    return F.to(torch.bfloat16).contiguous()
+    return F.to(torch.float16 if fp16 else torch.bfloat16).contiguous()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16_split"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16_split", "fp16_split"])
 def test_loglik_static_matches_workspace_call(torch_cuda, small_problem, precision):
     torch, p = torch_cuda, small_problem
     from paper_1409_4256_gb300 import emc
@@ -47,7 +48,7 @@ def test_loglik_static_matches_workspace_call(torch_cuda, small_problem, precisi
     m_ref, s_ref = ctx.loglik(L, bias, nrot)
     torch.cuda.synchronize()
     lse_ref = (m_ref + torch.log(s_ref)).cpu().numpy()[:nd]
-    frames = frames_bf16(torch, p["K"], ctx.ld_data, ctx.ld_pix)
+    frames = frames_bf16(torch, p["K"], ctx.ld_data, ctx.ld_pix, fp16=precision == "fp16_split")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     for call in range(2):  # two calls in a row share the static scratch
         m = torch.full((ctx.ld_data,), float("nan"), dtype=torch.float64, device="cuda")
@@ -56,6 +57,7 @@ def test_loglik_static_matches_workspace_call(torch_cuda, small_problem, precisi
         torch.cuda.synchronize()
         assert int(status.item()) == 0
         lse = (m + torch.log(s)).cpu().numpy()[:nd]
+        # same kernels and inputs as the workspace call: the parity tolerance
         assert np.abs(lse - lse_ref).max() <= 1e-4, (call, np.abs(lse - lse_ref).max())
 
 
