@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
     ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
     ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned",
-                    help="other precisions to time briefly (comma list, '' for none)")
+                    help="other forms to time briefly (comma list, or 'none')")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-iters", type=int, default=30,
                     help="iterations of the learned-vs-dense model comparison (0 to skip)")
@@ -420,7 +420,7 @@ def run_ours(args):
 
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
-    for f in [x for x in args.forms.split(",") if x and x != args.precision]:
+    for f in [x for x in args.forms.split(",") if x and x not in (args.precision, "none")]:
         if f in LEARNED_FORMS:
             try:
                 forms[f] = learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream,

@@ -5,7 +5,7 @@
 // that expansion used) and scatters f * Num_ij into g_num and f * den_j into
 // g_den with FP64 atomics resolved in L2 (the N^3 FP64 grids, 2 MB at 64^3,
 // stay L2-resident). The paper's insert_slices kernel also used one block
-// per slice.
+// per slice. Rotations without responsibility mass (den_j = 0) are skipped.
 #include "emc_common.cuh"
 #include "emc_internal.h"
 
@@ -15,7 +15,7 @@ constexpr int kCompressThreads = 256;
 
 __global__ void __launch_bounds__(kCompressThreads)
     compress_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
-                    int64_t ld_pix, int N, const double* __restrict__ quat,
+                    int64_t ld_pix, int N, const RotDF* __restrict__ rot,
                     const float* __restrict__ Num, const float* __restrict__ den, int mode,
                     double* __restrict__ g_num, double* __restrict__ g_den) {
   const int64_t row = blockIdx.x;
@@ -24,7 +24,8 @@ __global__ void __launch_bounds__(kCompressThreads)
   // a rotation without responsibility mass has Num = 0 and den = 0 (both
   // modes): it adds nothing, and sparse iterations leave most rows so
   if (!(dj > 0.f)) return;
-  if (threadIdx.x == 0) quat_to_rot_df(quat + 4 * row, &R);
+  if (threadIdx.x < 18)
+    reinterpret_cast<float*>(&R)[threadIdx.x] = reinterpret_cast<const float*>(rot + row)[threadIdx.x];
   __syncthreads();
   const float half_n = 0.5f * (float)N;
   const int64_t nn = (int64_t)N * N;
@@ -46,18 +47,19 @@ __global__ void __launch_bounds__(kCompressThreads)
                 ((c & 1) ? t[2] : 1.f - t[2]);
       if (w == 0.f) continue;
       int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
-      atomicAdd(g_num + l, (double)w * (double)v);
-      atomicAdd(g_den + l, (double)w * (double)dv);
+      // FP32 products (relative error 6e-8), FP64 accumulation in L2
+      atomicAdd(g_num + l, (double)(w * v));
+      atomicAdd(g_den + l, (double)(w * dv));
     }
   }
 }
 
-cudaError_t launch_compress(const Geom& g, const double* quat, int64_t nrot, const float* Num,
+cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const float* Num,
                             const float* den, int mode, double* g_num, double* g_den,
                             cudaStream_t s) {
   if (nrot <= 0) return cudaSuccess;
   compress_kernel<<<(unsigned)nrot, kCompressThreads, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
-                                                             quat, Num, den, mode, g_num, g_den);
+                                                             rot, Num, den, mode, g_num, g_den);
   return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
-  size_t qh, ql, quat, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
+  size_t qh, ql, quat, rot, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
       Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, total;
 };
 
@@ -69,6 +69,7 @@ Layout make_layout(const emc_config* c) {
   y.qh = take(sizeof(float4) * y.ld_pix);
   y.ql = take(sizeof(float4) * y.ld_pix);
   y.quat = take(sizeof(double) * 4 * c->n_rot);
+  y.rot = take(sizeof(RotDF) * c->n_rot);
   y.logw = take(sizeof(double) * c->n_rot);
   y.Kb = take(2 * (size_t)y.ld_data * y.ld_pix);
   y.status = take(256);
@@ -114,6 +115,7 @@ struct emc_ctx {
   size_t ws_bytes;
   Geom geom;
   double* quat;
+  const RotDF* rot;
   double* logw;
   uint16_t* Kb;
   int32_t* status;
@@ -212,6 +214,8 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   }
   std::vector<double> lw(cfg->n_rot);
   for (int64_t j = 0; j < cfg->n_rot; j++) lw[j] = log(weight[j]);
+  std::vector<RotDF> rot(cfg->n_rot);
+  for (int64_t j = 0; j < cfg->n_rot; j++) quat_to_rot_df(quat + 4 * j, &rot[j]);
   // feature bins of the learned proposal: radial floor(32 |q| / max|q|),
   // angular floor(16 (atan2(q_y, q_x) + pi) / (2 pi)); both capped at the top bin
   std::vector<int16_t> fbin(y.ld_pix, 0);
@@ -249,6 +253,7 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   c->geom.ld_pix = y.ld_pix;
   c->geom.N = cfg->N;
   c->quat = (double*)(c->ws + y.quat);
+  c->rot = (const RotDF*)(c->ws + y.rot);
   c->logw = (double*)(c->ws + y.logw);
   c->Kb = (uint16_t*)(c->ws + y.Kb);
   c->status = (int32_t*)(c->ws + y.status);
@@ -262,6 +267,8 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
                         s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->logw, lw.data(), sizeof(double) * cfg->n_rot, cudaMemcpyHostToDevice,
                         s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.rot, rot.data(), sizeof(RotDF) * cfg->n_rot,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= cudaMemsetAsync(c->status, 0, 256, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->ws + y.fbin, fbin.data(), sizeof(int16_t) * y.ld_pix,
                         cudaMemcpyHostToDevice, s) == cudaSuccess;
@@ -318,7 +325,7 @@ int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L
               cudaStream_t s) {
   const int64_t rows = round_up(nrot, 128);
   Planes p{L, rows * c->lay.ld_pix, c->lay.ld_pix};
-  CU(launch_expand(c->geom, grid, c->quat + 4 * rot0, c->logw + rot0, nrot, rows,
+  CU(launch_expand(c->geom, grid, c->rot + rot0, c->logw + rot0, nrot, rows,
                    c->cfg.precision, (float)c->cfg.w_floor, p, bias, c->status, s));
   return EMC_OK;
 }
@@ -352,16 +359,17 @@ int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const d
   return EMC_OK;
 }
 
-// S, Sref: stored scores of these rows (NULL: recompute from L and bias).
+// S, Sref: stored scores of these rows, S frame-major with leading dimension
+// ldS (NULL: recompute from L and bias).
 int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const double* bias,
                  int64_t nrot, const double* lse_m, const double* lse_s, const float* S,
-                 const float* Sref, void* P, int64_t Prows, cudaStream_t s) {
+                 int64_t ldS, const float* Sref, void* P, int64_t Prows, cudaStream_t s) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
   if (S) {
     float2* lse2 = (float2*)(c->ws + y.lse2);
     CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s));
-    CU(launch_normalize_scores(S, Sref, lse2, rows, nrot, y.ld_data, c->cfg.n_data,
+    CU(launch_normalize_scores(S, ldS, Sref, lse2, rows, nrot, y.ld_data, c->cfg.n_data,
                                c->cfg.precision, P, Prows * y.ld_data, s));
     return EMC_OK;
   }
@@ -430,7 +438,7 @@ int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
   const int64_t rows = round_up(nrot, 128);
   const float* S = (const float*)scores;
   const float* Sref = S ? S + rows * ctx->lay.ld_data : nullptr;
-  return do_normalize(ctx, L, rows, 0, bias, nrot, lse_m, lse_s, S, Sref, P, rows,
+  return do_normalize(ctx, L, rows, 0, bias, nrot, lse_m, lse_s, S, rows, Sref, P, rows,
                       (cudaStream_t)stream);
 }
 
@@ -452,7 +460,7 @@ int emc_compress(emc_ctx* ctx, int64_t rot0, int64_t nrot, const float* Num, con
     CU(cudaMemsetAsync(g_num, 0, gb, s));
     CU(cudaMemsetAsync(g_den, 0, gb, s));
   }
-  CU(launch_compress(ctx->geom, ctx->quat + 4 * rot0, nrot, Num, den, ctx->cfg.compress_mode,
+  CU(launch_compress(ctx->geom, ctx->rot + rot0, nrot, Num, den, ctx->cfg.compress_mode,
                      g_num, g_den, s));
   return EMC_OK;
 }
@@ -503,14 +511,15 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     const int64_t nr = std::min(y.chunk_rows, n_rot - r0);
     const int64_t crows = round_up(nr, 128);
     if (stats) CU(cudaEventRecord(c->ev[3], s));
-    const float* Sc = S ? S + r0 * y.ld_data : nullptr;
+    const float* Sc = S ? S + r0 : nullptr;  // frame-major: rows r0.. of every frame
     const float* Sr = S ? S + y.rows * y.ld_data + (r0 / 32) * y.ld_data : nullptr;
-    if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lse_m, lse_s, Sc, Sr, P, crows, s)))
+    if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lse_m, lse_s, Sc, y.rows, Sr, P, crows,
+                           s)))
       return st;
     if (stats) CU(cudaEventRecord(c->ev[4], s));
     if ((st = do_update(c, P, crows, nr, Num, den, s))) return st;
     if (stats) CU(cudaEventRecord(c->ev[5], s));
-    CU(launch_compress(c->geom, c->quat + 4 * r0, nr, Num, den, c->cfg.compress_mode, gn, gd, s));
+    CU(launch_compress(c->geom, c->rot + r0, nr, Num, den, c->cfg.compress_mode, gn, gd, s));
     if (stats) CU(cudaEventRecord(c->ev[6], s));
     kernels += 3;
     if (stats) {
@@ -619,8 +628,8 @@ int emc_targets_from_scores(emc_ctx* ctx, const void* scores, int R, int32_t* ti
     scores = ctx->ws + y.S;
   }
   const float* S = (const float*)scores;
-  CU(launch_topr_columns(S, S + y.rows * y.ld_data, y.ld_data, ctx->cfg.n_rot, ctx->cfg.n_data, R,
-                         tidx, tprob, (cudaStream_t)stream));
+  CU(launch_topr_columns(S, y.rows, S + y.rows * y.ld_data, y.ld_data, ctx->cfg.n_rot,
+                         ctx->cfg.n_data, R, tidx, tprob, (cudaStream_t)stream));
   return EMC_OK;
 }
 
@@ -693,7 +702,7 @@ int emc_sparse_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_
   if (stats) CU(cudaEventRecord(c->ev[3], s));
   CU(cudaMemsetAsync(gn, 0, gb, s));
   CU(cudaMemsetAsync(gd, 0, gb, s));
-  CU(launch_compress(c->geom, c->quat, c->cfg.n_rot, Num, den, c->cfg.compress_mode, gn, gd, s));
+  CU(launch_compress(c->geom, c->rot, c->cfg.n_rot, Num, den, c->cfg.compress_mode, gn, gd, s));
   CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, grid_in, grid_out, s));
   if (stats) CU(cudaEventRecord(c->ev[4], s));
   if (stats) {
@@ -733,7 +742,7 @@ int emc_missed_mass(emc_ctx* ctx, const void* scores, const double* lse_m, const
   float2* lse2 = (float2*)(ctx->ws + y.lse2);
   CU(launch_lse_split(lse_m, lse_s, ctx->cfg.n_data, y.ld_data, lse2, s));
   const float* S = (const float*)scores;
-  CU(launch_missed_mass(S, S + y.rows * y.ld_data, y.ld_data, lse2,
+  CU(launch_missed_mass(S, y.rows, S + y.rows * y.ld_data, y.ld_data, lse2,
                         (const int32_t*)(ctx->ws + y.cand), ctx->cfg.n_cand, ctx->cfg.n_data,
                         missed, s));
   return EMC_OK;

@@ -60,7 +60,7 @@ struct RotDF {
 };
 
 // Hamilton rotation matrix of a unit quaternion (w, x, y, z), in FP64, split.
-__device__ __forceinline__ void quat_to_rot_df(const double* q, RotDF* out) {
+__host__ __device__ __forceinline__ void quat_to_rot_df(const double* q, RotDF* out) {
   double w = q[0], x = q[1], y = q[2], z = q[3];
   double R[9];
   R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);

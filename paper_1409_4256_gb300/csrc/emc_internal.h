@@ -7,6 +7,10 @@
 
 namespace emc {
 
+// Rotation matrix R_j (row-major 3x3) as double-float pairs (h, l) of FP32,
+// computed once per context on the host in FP64.
+struct RotDF;
+
 // Pixel geometry as stored in the workspace: positions q_i split into FP32
 // hi/lo pairs, w component 1 for a used pixel and 0 for padding.
 struct Geom {
@@ -29,13 +33,13 @@ cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, i
                                int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int fp16,
                                int32_t* status, cudaStream_t s);
 
-cudaError_t launch_expand(const Geom& g, const float* grid, const double* quat,
+cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
                           float w_floor, Planes L, double* bias, int32_t* status, cudaStream_t s);
 
 // FP32 SIMT forms (precision EMC_PREC_FP32).
-// S, Sref (optional, both or neither): scores relative to 32-row group maxima
-// [rows][ld_data] and the maxima (on the 1/8 grid) [rows / 32][ld_data].
+// S, Sref (optional, both or neither): scores relative to 32-row group maxima,
+// frame-major [ld_data][rows], and the maxima (on the 1/64 grid) [rows / 32][ld_data].
 cudaError_t launch_simt_pass1(const float* L, int64_t ld_pix, const double* bias, int64_t rows,
                               const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                               double* part_m, float* part_s, float* S, float* Sref,
@@ -55,10 +59,12 @@ cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t 
                              int accumulate, int32_t* status, cudaStream_t s);
 cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n_data,
                              int64_t ld_data, float2* out, cudaStream_t s);
-// E-step pass 2 from stored scores; P layout as emc_normalize documents.
-cudaError_t launch_normalize_scores(const float* S, const float* Sref, const float2* lse2,
-                                    int64_t rows, int64_t nrot, int64_t ld_data, int64_t n_data,
-                                    int precision, void* P, int64_t P_plane, cudaStream_t s);
+// E-step pass 2 from stored scores (frame-major, ld ldS); P layout as
+// emc_normalize documents.
+cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sref,
+                                    const float2* lse2, int64_t rows, int64_t nrot,
+                                    int64_t ld_data, int64_t n_data, int precision, void* P,
+                                    int64_t P_plane, cudaStream_t s);
 cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
                               double* out, cudaStream_t s);
 
@@ -78,7 +84,7 @@ cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const
                              int32_t* status, cudaStream_t s);
 int64_t tc_pass1_tiles(int64_t rows);
 
-cudaError_t launch_compress(const Geom& g, const double* quat, int64_t nrot, const float* Num,
+cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const float* Num,
                             const float* den, int mode, double* g_num, double* g_den,
                             cudaStream_t s);
 cudaError_t launch_finalize(int64_t n_vox, const double* g_num, const double* g_den,
@@ -110,7 +116,7 @@ cudaError_t mlp_train_step(const MlpLayout& y, float* params, float* grads, floa
 // ---- candidates and the sparse Maximize (sparse.cu) ----
 cudaError_t launch_topm(const float* logits, int64_t B, int64_t n, int64_t ld, int M,
                         int32_t* cand, cudaStream_t s);
-cudaError_t launch_topr_columns(const float* S, const float* Sref, int64_t ld, int64_t nrot,
+cudaError_t launch_topr_columns(const float* S, int64_t ldS, const float* Sref, int64_t ld, int64_t nrot,
                                 int64_t n_data, int R, int32_t* tidx, float* tprob,
                                 cudaStream_t s);
 cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t n_rot,
@@ -124,7 +130,7 @@ cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data,
 cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
                                  const int64_t* off, const int2* ent, int M, const float* Pc,
                                  int64_t rows, float* Num, float* den, cudaStream_t s);
-cudaError_t launch_missed_mass(const float* S, const float* Sref, int64_t ld_data,
+cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, int64_t ld_data,
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
                                float* missed, cudaStream_t s);
 

@@ -1,13 +1,15 @@
 // expand.cu -- e-step of EMC (Eq. 2.9) and the per-rotation bias of Eq. 2.3.
 //
 // One CTA per rotation row j, threads striding over pixels. For every pixel
-// the grid point p = R_j q_i + N/2 is formed in double-float, the trilinear
+// the grid point p = R_j q_i + N/2 is formed in double-float (R_j from the
+// context's table of double-float rotation matrices), the trilinear
 // weights f(p_l - p) of the eight surrounding voxels (Eq. 2.8, tent kernel)
 // blend the L2-resident grid, W_ij = max(W, w_floor) and log W_ij is stored in
 // the layout the contraction of the chosen precision reads. The same CTA sums
 // W_ij over pixels in FP64 (block reduction) and writes
 //   bias_j = log w_j - sum_i W_ij,
-// the rotation-only part of S_jk = sum_i K_ik log W_ij - W_ij + log w_j.
+// the rotation-only part of S_jk = sum_i K_ik log W_ij - W_ij + log w_j
+// (per-thread compensated FP32 sums, FP64 across the block).
 // Writes are coalesced along pixels; HBM traffic is the L write (4 B/(i,j)
 // for FP32, 2 B for BF16, 6 B for the three-term split, 4 B for the FP16 split).
 #include "emc_common.cuh"
@@ -21,21 +23,22 @@ template <int PREC>
 __global__ void __launch_bounds__(kExpandThreads)
     expand_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
                   int64_t ld_pix, int N, const float* __restrict__ grid,
-                  const double* __restrict__ quat, const double* __restrict__ logw, int64_t nrot,
+                  const RotDF* __restrict__ rot, const double* __restrict__ logw, int64_t nrot,
                   float w_floor, void* __restrict__ Lbase, int64_t plane_stride,
                   double* __restrict__ bias, int32_t* status) {
   const int64_t row = blockIdx.x;
   __shared__ RotDF R;
   __shared__ double red[kExpandThreads / 32];
   const bool valid_row = row < nrot;
-  if (threadIdx.x == 0 && valid_row) quat_to_rot_df(quat + 4 * row, &R);
+  if (threadIdx.x < 18 && valid_row)
+    reinterpret_cast<float*>(&R)[threadIdx.x] = reinterpret_cast<const float*>(rot + row)[threadIdx.x];
   __syncthreads();
 
   float* Lf = reinterpret_cast<float*>(Lbase) + row * ld_pix;
   uint16_t* Lb = reinterpret_cast<uint16_t*>(Lbase) + row * ld_pix;
   const float half_n = 0.5f * (float)N;
   const int64_t nn = (int64_t)N * N;
-  double wsum = 0.0;
+  float wsum = 0.f, wcomp = 0.f;  // Kahan-compensated sum of W over this thread's pixels
   int bad = 0;
 
   for (int64_t i = threadIdx.x; i < ld_pix; i += kExpandThreads) {
@@ -58,7 +61,10 @@ __global__ void __launch_bounds__(kExpandThreads)
           W = fmaf(w, __ldg(grid + (int64_t)x * nn + (int64_t)y * N + z), W);
         }
         W = fmaxf(W, w_floor);
-        wsum += (double)W;
+        const float ky = W - wcomp;
+        const float kt = wsum + ky;
+        wcomp = (kt - wsum) - ky;
+        wsum = kt;
         L = logf(W);
       }
     }
@@ -89,8 +95,9 @@ __global__ void __launch_bounds__(kExpandThreads)
   if (bad) set_status(status, EMC_ERR_UNSUPPORTED);
 
   // FP64 block reduction of sum_i W_ij
-  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wsum;
+  double ws = (double)wsum - (double)wcomp;
+  for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ws;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -99,7 +106,7 @@ __global__ void __launch_bounds__(kExpandThreads)
   }
 }
 
-cudaError_t launch_expand(const Geom& g, const float* grid, const double* quat,
+cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
                           float w_floor, Planes L, double* bias, int32_t* status, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
@@ -107,22 +114,22 @@ cudaError_t launch_expand(const Geom& g, const float* grid, const double* quat,
   switch (precision) {
     case EMC_PREC_FP32:
       expand_kernel<EMC_PREC_FP32><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid,
-                                                       quat, logw, nrot, w_floor, L.base,
+                                                       rot, logw, nrot, w_floor, L.base,
                                                        L.plane_stride, bias, status);
       break;
     case EMC_PREC_BF16:
       expand_kernel<EMC_PREC_BF16><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid,
-                                                       quat, logw, nrot, w_floor, L.base,
+                                                       rot, logw, nrot, w_floor, L.base,
                                                        L.plane_stride, bias, status);
       break;
     case EMC_PREC_FP16_SPLIT:
       expand_kernel<EMC_PREC_FP16_SPLIT><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
-                                                             grid, quat, logw, nrot, w_floor,
+                                                             grid, rot, logw, nrot, w_floor,
                                                              L.base, L.plane_stride, bias, status);
       break;
     default:
       expand_kernel<EMC_PREC_BF16_SPLIT><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
-                                                             grid, quat, logw, nrot, w_floor,
+                                                             grid, rot, logw, nrot, w_floor,
                                                              L.base, L.plane_stride, bias, status);
       break;
   }

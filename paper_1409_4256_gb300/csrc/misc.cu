@@ -141,73 +141,87 @@ cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n
 }
 
 // E-step pass 2 from stored scores (Eq. 2.4): P_jk = exp(S_jk - lse_k) with
-// S_jk held as d_jk (relative to its 32-row group maximum r_gk, which lies on
-// the 1/64 grid); r_gk - hi(lse_k) is exact, so
-//   P_jk = exp(d_jk + ((r_gk - hi_k) - lo_k)).
-// One thread per 4 consecutive frames of one row: 16-byte loads of d,
-// 8-byte (BF16 x4) or 16-byte (FP32 x4) stores of P. HBM-bound: 4 B read and
-// 4 B written per (j, k).
+// S_jk held frame-major as d[k][j] (ld = ldS) relative to its 32-row group
+// maximum r[j/32][k], which lies on the 1/64 grid; r - hi(lse_k) is exact, so
+//   P_jk = exp(d_kj + ((r_gk - hi_k) - lo_k)).
+// One CTA per 32 rows x 64 frames: coalesced 128-byte reads of d along j,
+// a shared-memory transpose, coalesced writes of P along k. HBM-bound: 4 B read
+// and 4 B written per (j, k).
 template <int OUT>  // 0: FP32 P; 1: BF16 hi plane only; 2: BF16 hi + lo; 3: FP16 hi + lo of 2^14 P
-__global__ void normalize_scores_kernel(const float* __restrict__ S, const float* __restrict__ Sref,
-                                        const float2* __restrict__ lse2, int64_t rows,
-                                        int64_t nrot, int64_t ld_data, int64_t n_data,
-                                        void* __restrict__ P, int64_t P_plane) {
-  const int64_t q4 = ld_data / 4;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * q4) return;
-  const int64_t j = idx / q4, k = (idx % q4) * 4;
-  const float4 d = *reinterpret_cast<const float4*>(S + j * ld_data + k);
-  const float4 r = *reinterpret_cast<const float4*>(Sref + (j >> 5) * ld_data + k);
-  const float dv[4] = {d.x, d.y, d.z, d.w};
-  const float rv[4] = {r.x, r.y, r.z, r.w};
-  float p[4];
+__global__ void __launch_bounds__(256)
+    normalize_scores_kernel(const float* __restrict__ S, int64_t ldS,
+                            const float* __restrict__ Sref, const float2* __restrict__ lse2,
+                            int64_t nrot, int64_t ld_data, int64_t n_data, void* __restrict__ P,
+                            int64_t P_plane) {
+  __shared__ float tile[64][33];
+  const int64_t j0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
 #pragma unroll
-  for (int u = 0; u < 4; u++) {
+  for (int r = 0; r < 8; r++) {  // frames k0 + ty + 8r, rows j0 + tx
+    const int kk = ty + 8 * r;
+    tile[kk][tx] = S[(k0 + kk) * ldS + j0 + tx];
+  }
+  __syncthreads();
+  // thread: row j0 + (threadIdx.x >> 3), frames k0 + 8 * (threadIdx.x & 7) .. + 8
+  const int jj = threadIdx.x >> 3, kb = (threadIdx.x & 7) * 8;
+  const int64_t j = j0 + jj, k = k0 + kb;
+  const float4* rs = reinterpret_cast<const float4*>(Sref + (j >> 5) * ld_data + k);
+  const float4 r0 = rs[0], r1 = rs[1];
+  const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+  float p[8];
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
     const float2 L = lse2[k + u];
-    const float e = dv[u] + ((rv[u] - L.x) - L.y);
-    p[u] = (j < nrot && k + u < n_data) ? __expf(e) : 0.f;
+    const float ex = tile[kb + u][jj] + ((rv[u] - L.x) - L.y);
+    p[u] = (j < nrot && k + u < n_data) ? __expf(ex) : 0.f;
   }
   if (OUT == 0) {
-    *reinterpret_cast<float4*>(reinterpret_cast<float*>(P) + j * ld_data + k) =
-        make_float4(p[0], p[1], p[2], p[3]);
+    float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(P) + j * ld_data + k);
+    o[0] = make_float4(p[0], p[1], p[2], p[3]);
+    o[1] = make_float4(p[4], p[5], p[6], p[7]);
   } else {
-    uint16_t h[4], l[4];
+    uint32_t h[4], l[4];
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
+    for (int u = 0; u < 8; u += 2) {
+      uint16_t h0, h1, l0, l1;
       if (OUT == 3) {
-        const float ps = p[u] * kP16Scale;
-        h[u] = fp16_bits(ps);
-        l[u] = fp16_bits(ps - fp16_val(h[u]));
+        const float s0 = p[u] * kP16Scale, s1 = p[u + 1] * kP16Scale;
+        h0 = fp16_bits(s0);
+        h1 = fp16_bits(s1);
+        l0 = fp16_bits(s0 - fp16_val(h0));
+        l1 = fp16_bits(s1 - fp16_val(h1));
       } else {
-        h[u] = bf16_bits(p[u]);
-        l[u] = OUT == 2 ? bf16_bits(p[u] - bf16_val(h[u])) : (uint16_t)0;
+        h0 = bf16_bits(p[u]);
+        h1 = bf16_bits(p[u + 1]);
+        l0 = OUT == 2 ? bf16_bits(p[u] - bf16_val(h0)) : (uint16_t)0;
+        l1 = OUT == 2 ? bf16_bits(p[u + 1] - bf16_val(h1)) : (uint16_t)0;
       }
+      h[u / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+      l[u / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
     }
     uint16_t* ph = reinterpret_cast<uint16_t*>(P) + j * ld_data + k;
-    *reinterpret_cast<uint2*>(ph) = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16),
-                                               (uint32_t)h[2] | ((uint32_t)h[3] << 16));
-    *reinterpret_cast<uint2*>(ph + P_plane) = make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16),
-                                                         (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+    *reinterpret_cast<uint4*>(ph) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(ph + P_plane) = make_uint4(l[0], l[1], l[2], l[3]);
   }
 }
 
-cudaError_t launch_normalize_scores(const float* S, const float* Sref, const float2* lse2,
-                                    int64_t rows, int64_t nrot, int64_t ld_data, int64_t n_data,
-                                    int precision, void* P, int64_t P_plane, cudaStream_t s) {
-  const int64_t n = rows * (ld_data / 4);
-  const unsigned blocks = (unsigned)((n + 255) / 256);
+cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sref,
+                                    const float2* lse2, int64_t rows, int64_t nrot,
+                                    int64_t ld_data, int64_t n_data, int precision, void* P,
+                                    int64_t P_plane, cudaStream_t s) {
+  dim3 grid((unsigned)(ld_data / 64), (unsigned)(rows / 32));
   if (precision == EMC_PREC_FP32)
-    normalize_scores_kernel<0><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
-                                                       P_plane);
+    normalize_scores_kernel<0><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
+                                                    P_plane);
   else if (precision == EMC_PREC_FP16_SPLIT)
-    normalize_scores_kernel<3><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
-                                                       P_plane);
+    normalize_scores_kernel<3><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
+                                                    P_plane);
   else if (precision == EMC_PREC_BF16)
-    normalize_scores_kernel<1><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
-                                                       P_plane);
+    normalize_scores_kernel<1><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
+                                                    P_plane);
   else
-    normalize_scores_kernel<2><<<blocks, 256, 0, s>>>(S, Sref, lse2, rows, nrot, ld_data, n_data, P,
-                                                       P_plane);
+    normalize_scores_kernel<2><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
+                                                    P_plane);
   return cudaGetLastError();
 }
 

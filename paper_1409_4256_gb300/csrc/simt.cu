@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(S_THREADS)
     simt_pass1_kernel(const float* __restrict__ L, int64_t ld_pix, const double* __restrict__ bias,
                       const uint16_t* __restrict__ Kb, int64_t ld_data,
                       double* __restrict__ part_m, float* __restrict__ part_s,
-                      float* __restrict__ S, float* __restrict__ Sref) {
+                      float* __restrict__ S, float* __restrict__ Sref, int64_t rows) {
   __shared__ __align__(16) float Ah[SB_K][SA_LD];
   __shared__ __align__(16) float Ar[SB_K][SA_LD];
   __shared__ __align__(16) float Bs[SB_K][SBN_LD];
@@ -128,14 +128,15 @@ __global__ void __launch_bounds__(S_THREADS)
 #pragma unroll
     for (int j = 0; j < 8; j++)
       ref[j] = mcol[j] == -INFINITY ? -3.0e38f : (float)(rint(mcol[j] * kGridD) / kGridD);
+    // frame-major: 4 consecutive rows of one column per float4
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-      float v[8];
-#pragma unroll
-      for (int j = 0; j < 8; j++) v[j] = (float)(x[i][j] - (double)ref[j]);
-      float4* dst = reinterpret_cast<float4*>(S + (r0 + ty * 4 + i) * ld_data + c0 + tx * 8);
-      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+    for (int j = 0; j < 8; j++) {
+      float4 v;
+      v.x = (float)(x[0][j] - (double)ref[j]);
+      v.y = (float)(x[1][j] - (double)ref[j]);
+      v.z = (float)(x[2][j] - (double)ref[j]);
+      v.w = (float)(x[3][j] - (double)ref[j]);
+      *reinterpret_cast<float4*>(S + (c0 + tx * 8 + j) * rows + r0 + ty * 4) = v;
     }
     if (ty == 0) {
 #pragma unroll
@@ -277,7 +278,7 @@ cudaError_t launch_simt_pass1(const float* L, int64_t ld_pix, const double* bias
   (void)n_data;
   dim3 grd((unsigned)(ld_data / SB_N), (unsigned)(rows / SB_M));
   simt_pass1_kernel<<<grd, S_THREADS, 0, s>>>(L, ld_pix, bias, Kb, ld_data, part_m, part_s, S,
-                                              Sref);
+                                              Sref, rows);
   return cudaGetLastError();
 }
 

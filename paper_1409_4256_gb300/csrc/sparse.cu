@@ -103,11 +103,12 @@ cudaError_t launch_topm(const float* logits, int64_t B, int64_t n, int64_t ld, i
 }
 
 // ------------------------------------------------- training targets (top R) --
-// Per frame (one thread, threads on consecutive frames so row reads coalesce):
-// the R largest stored dense scores over rows [0, nrot) and their softmax
+// Per frame (one thread, reading its frame-major scores sequentially): the R
+// largest stored dense scores over rows [0, nrot) and their softmax
 // (targets proportional to the dense responsibilities).
-__global__ void topr_columns_kernel(const float* __restrict__ S, const float* __restrict__ Sref,
-                                    int64_t ld, int64_t nrot, int64_t n_data, int R,
+__global__ void topr_columns_kernel(const float* __restrict__ S, int64_t ldS,
+                                    const float* __restrict__ Sref, int64_t ld, int64_t nrot,
+                                    int64_t n_data, int R,
                                     int32_t* __restrict__ tidx, float* __restrict__ tprob) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_data) return;
@@ -120,7 +121,7 @@ __global__ void topr_columns_kernel(const float* __restrict__ S, const float* __
   int mpos = 0;
   float mval = -INFINITY;
   for (int64_t j = 0; j < nrot; j++) {
-    const float v = S[j * ld + k] + Sref[(j >> 5) * ld + k];
+    const float v = S[k * ldS + j] + Sref[(j >> 5) * ld + k];
     if (v > mval) {
       val[mpos] = v;
       idx[mpos] = (int)j;
@@ -143,12 +144,12 @@ __global__ void topr_columns_kernel(const float* __restrict__ S, const float* __
   }
 }
 
-cudaError_t launch_topr_columns(const float* S, const float* Sref, int64_t ld, int64_t nrot,
-                                int64_t n_data, int R, int32_t* tidx, float* tprob,
+cudaError_t launch_topr_columns(const float* S, int64_t ldS, const float* Sref, int64_t ld,
+                                int64_t nrot, int64_t n_data, int R, int32_t* tidx, float* tprob,
                                 cudaStream_t s) {
   if (R < 1 || R > kMaxTargets) return cudaErrorInvalidValue;
-  topr_columns_kernel<<<(unsigned)((n_data + 127) / 128), 128, 0, s>>>(S, Sref, ld, nrot, n_data,
-                                                                       R, tidx, tprob);
+  topr_columns_kernel<<<(unsigned)((n_data + 127) / 128), 128, 0, s>>>(S, ldS, Sref, ld, nrot,
+                                                                       n_data, R, tidx, tprob);
   return cudaGetLastError();
 }
 
@@ -413,8 +414,8 @@ __global__ void __launch_bounds__(256)
 }
 
 // 1 - sum_{j in C_k} P_jk of a dense E-step, from its stored scores.
-__global__ void missed_mass_kernel(const float* __restrict__ S, const float* __restrict__ Sref,
-                                   int64_t ld_data, const float2* __restrict__ lse2,
+__global__ void missed_mass_kernel(const float* __restrict__ S, int64_t ldS,
+                                   const float* __restrict__ Sref, int64_t ld_data, const float2* __restrict__ lse2,
                                    const int32_t* __restrict__ cand, int M, int64_t n_data,
                                    float* __restrict__ missed) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -423,7 +424,7 @@ __global__ void missed_mass_kernel(const float* __restrict__ S, const float* __r
   double sum = 0.0;
   for (int m = 0; m < M; m++) {
     const int64_t j = cand[k * M + m];
-    const float e = S[j * ld_data + k] + ((Sref[(j >> 5) * ld_data + k] - L.x) - L.y);
+    const float e = S[k * ldS + j] + ((Sref[(j >> 5) * ld_data + k] - L.x) - L.y);
     sum += (double)__expf(e);
   }
   missed[k] = (float)(1.0 - sum);
@@ -486,11 +487,11 @@ cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_missed_mass(const float* S, const float* Sref, int64_t ld_data,
+cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, int64_t ld_data,
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
                                float* missed, cudaStream_t s) {
-  missed_mass_kernel<<<(unsigned)((n_data + 255) / 256), 256, 0, s>>>(S, Sref, ld_data, lse2, cand,
-                                                                     M, n_data, missed);
+  missed_mass_kernel<<<(unsigned)((n_data + 255) / 256), 256, 0, s>>>(S, ldS, Sref, ld_data, lse2,
+                                                                     cand, M, n_data, missed);
   return cudaGetLastError();
 }
 

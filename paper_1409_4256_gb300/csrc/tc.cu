@@ -79,13 +79,14 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t base, int kk) {
 
 struct TcArgs {
   int n_mtiles, n_ntiles, group, kblocks;
+  int64_t rows;      // rows of A (leading dimension of the frame-major stored scores)
   int64_t nrot;      // valid rows of A
   int64_t n_data, ld_data, ld_pix, n_pix;
   const double* bias;      // scores: [rows]
   const float2* lse2;      // normalize: [ld_data] (hi on the 1/8 grid, lo)
   double* part_m;          // pass 1: [n_mtiles][ld_data]
   float* part_s;
-  float* S;                // pass 1, optional: shifted scores [rows][ld_data]
+  float* S;                // pass 1, optional: shifted scores, frame-major [ld_data][rows]
   float* Sref;             // pass 1, optional: 32-row group maxima [rows / 32][ld_data]
   uint16_t* P;             // normalize: planes [2][rows][ld_data]
   int64_t P_plane;
@@ -347,7 +348,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int i = 0; i < 32; i++) v[i] = xh[i];
           const float mcol = warp_transpose_reduce<true>(v, lane);
           const int64_t k0 = (int64_t)nt * BN + col0;
-          float* Srow = a.S ? a.S + row * a.ld_data + k0 : nullptr;
 #pragma unroll
           for (int i = 0; i < 32; i++) {
             const float mi = __shfl_sync(0xffffffffu, mcol, i);
@@ -355,11 +355,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             v[i] = valid ? __expf(d) : 0.f;
             xl[i] = d;
           }
-          if (Srow) {
-            // S_jk relative to the 32-row group maximum of column k
+          if (a.S) {
+            // S_jk relative to the 32-row group maximum of column k, frame-major:
+            // the warp's 32 lanes (consecutive rows) write one 128-byte segment per column
+            float* Scol = a.S + k0 * a.rows + row;
 #pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(Srow + i) = make_float4(xl[i], xl[i + 1], xl[i + 2], xl[i + 3]);
+            for (int i = 0; i < 32; i++) Scol[(int64_t)i * a.rows] = xl[i];
             a.Sref[((int64_t)mt * 4 + q) * a.ld_data + k0 + lane] = mcol;
           }
           const float scol = warp_transpose_reduce<false>(v, lane);
@@ -513,6 +514,7 @@ bool maps_scores(const Planes& L, int precision, int64_t rows, const uint16_t* K
 TcArgs base_args(int64_t rows, int n_ntiles, int kblocks) {
   TcArgs a{};
   a.n_mtiles = (int)(rows / BM);
+  a.rows = rows;
   a.n_ntiles = n_ntiles;
   a.group = 8;
   a.kblocks = kblocks;

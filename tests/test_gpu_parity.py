@@ -142,7 +142,7 @@ def test_estep_from_stored_scores(torch_cuda, small_problem, ref, precision):
     # the stored scores reproduce the oracle's S_jk
     b = ctx.buffer_sizes(nrot)
     Sf = Sbuf.view(torch.float32).cpu().numpy().astype(np.float64)
-    d = Sf[:b.rows * b.ld_data].reshape(b.rows, b.ld_data)
+    d = Sf[:b.rows * b.ld_data].reshape(b.ld_data, b.rows).T  # stored frame-major
     r = Sf[b.rows * b.ld_data:].reshape(b.rows // 32, b.ld_data)
     S = d + np.repeat(r, 32, axis=0)
     sel = ref["P"] > 1e-6
