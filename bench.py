@@ -43,6 +43,7 @@ WORKLOAD_TEXT = {
 }
 DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3", "fp16_split": "f16x2"}
 LEARNED_FORMS = ("learned",)
+ADAPTIVE_FORMS = ("adaptive",)
 
 
 def parse_args():
@@ -55,11 +56,13 @@ def parse_args():
     ap.add_argument("--workload", default="emc64", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
     ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
-    ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned",
+    ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned,adaptive",
                     help="other forms to time briefly (comma list, or 'none')")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-iters", type=int, default=30,
                     help="iterations of the learned-vs-dense model comparison (0 to skip)")
+    ap.add_argument("--adaptive-iters", type=int, default=12,
+                    help="iterations of the adaptive-sampling schedule")
     ap.add_argument("--n-cand", type=int, default=512, help="candidate rotations per frame")
     ap.add_argument("--recompute", action="store_true",
                     help="two-pass streamed E-step (pass 2 recomputes the scores) instead of "
@@ -335,6 +338,44 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
     return res
 
 
+def adaptive_form(torch, args, cfg, ds, grid, K_dev, stream, ctx, fixed_ms):
+    """Adaptive rotation sampling (Sec. 3.4, Eq. 3.1) from the start model:
+    d rises from n_quat - 5 to n_quat as the likelihood settles. Reports every
+    level's iterations and device time, against the same number of iterations
+    at the final d (fixed_ms each), and the likelihoods both schedules reach."""
+    from paper_1409_4256_gb300 import adaptive
+    d_max = cfg["n_quat"]
+    d0 = max(1, d_max - 5)
+    iters = args.adaptive_iters
+    floor = 1e-10 * float(ds.model_start.mean())
+    t0 = time.perf_counter()
+    g, hist = adaptive.run(cfg["N"], ds.q, K_dev, grid, d0, d_max, iters, precision=args.precision,
+                           w_floor=floor, store_scores=not args.recompute, device=str(grid.device),
+                           K_host=ds.K, stream=stream)
+    wall = time.perf_counter() - t0
+    levels = {}
+    for h in hist:
+        lv = levels.setdefault(h.d, {"d": h.d, "rotations": h.n_rot, "iterations": 0, "ms": 0.0})
+        lv["iterations"] += 1
+        lv["ms"] += h.ms
+    for lv in levels.values():
+        lv["pairs_per_s"] = lv["rotations"] * ds.K.shape[0] * lv["iterations"] / (lv["ms"] * 1e-3)
+    # the same number of iterations at the final d (the benchmark's context)
+    const = adaptive.log_factorial_sum(ds.K)
+    fixed_ll = []
+    with torch.cuda.stream(stream):
+        a, b = grid.clone(), torch.empty_like(grid)
+        for _ in range(iters):
+            _, st = ctx.iteration(a, b, stream=stream)
+            fixed_ll.append(st["loglik"] - const)
+            a, b = b, a
+    return {"schedule": f"d {d0} -> {d_max}, refine when |dL| <= 0.01 |L|", "iterations": iters,
+            "levels": list(levels.values()), "device_ms_total": sum(h.ms for h in hist),
+            "fixed_d_ms_total": iters * fixed_ms, "wall_s_with_setup": wall,
+            "loglik_per_iteration": [h.loglik for h in hist], "reached_d": hist[-1].d,
+            "fixed_d_loglik_per_iteration": fixed_ll}
+
+
 def run_ours(args):
     import torch
 
@@ -421,6 +462,12 @@ def run_ours(args):
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
     for f in [x for x in args.forms.split(",") if x and x not in (args.precision, "none")]:
+        if f in ADAPTIVE_FORMS:
+            try:
+                forms[f] = adaptive_form(torch, args, cfg, ds, grid, K_dev, stream, ctx, ms)
+            except Exception as e:
+                forms[f] = {"error": str(e)[:300]}
+            continue
         if f in LEARNED_FORMS:
             try:
                 forms[f] = learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream,
