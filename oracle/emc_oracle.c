@@ -25,6 +25,7 @@
  *    projection to the unit sphere (Jacobian of radial projection of a flat
  *    tetrahedral cell onto S^3), normalised to sum 1.
  *  - Eq. 2.12 voxels with zero denominator keep their previous value.
+ *  - Gaussian model: see the block before oracle_fluence.
  */
 #include <math.h>
 #include <stdint.h>
@@ -473,6 +474,111 @@ double oracle_iteration(int N, const double* grid, long n_rot, const double* qua
     oracle_compress(N, n_rot, quat, n_pix, q, Num, den, mode, grid, gn, gd, grid_out);
   }
   free(W); free(S); free(Num); free(den); free(gn); free(gd);
+  return L;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian noise model (Sec. 2.2, Eqs. 2.2-2.3, 2.5-2.6).                    */
+/*                                                                           */
+/* Reading (the paper's superscripts put phi^(n+1) = f(W^(n)) in the M-step   */
+/* and phi^(n) in the E-step): the fluence of Eq. 2.6 is evaluated on the     */
+/* model W^(n) of the current iteration and used in that iteration's E-step   */
+/* and M-step. Eq. 2.6 is the least-squares optimum of Eq. 2.2 over phi for   */
+/* fixed W, so each rotation is scored at its best-fitting fluence.           */
+/* K/phi with phi infinite (sum_i W_ij K_ik = 0) or undefined (a frame with   */
+/* no photons) is read as 0.                                                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * 1/phi_jk of Eq. 2.6: (sum_i W_ij K_ik) / (sum_i K_ik^2), 0 for an empty frame.
+ * W[n_rot][n_pix], K[n_data][n_pix] -> inv_phi[n_rot][n_data].
+ */
+void oracle_fluence(long n_rot, long n_pix, long n_data, const double* W, const double* K,
+                    double* inv_phi) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long j = 0; j < n_rot; j++) {
+    for (long k = 0; k < n_data; k++) {
+      double kk = 0.0, wk = 0.0;
+      for (long i = 0; i < n_pix; i++) {
+        kk += K[k * n_pix + i] * K[k * n_pix + i];
+        wk += W[j * n_pix + i] * K[k * n_pix + i];
+      }
+      inv_phi[j * n_data + k] = kk > 0.0 ? wk / kk : 0.0;
+    }
+  }
+}
+
+/*
+ * Eqs. 2.2-2.3 with the log prior weight of Eq. 2.4:
+ *   S_jk = -sum_i (K_ik / phi_jk - W_ij)^2 / (2 sigma^2) + log w_j.
+ */
+void oracle_scores_gauss(long n_rot, long n_pix, long n_data, const double* W,
+                         const double* weight, const double* K, double sigma,
+                         const double* inv_phi, double* S) {
+  const double s2 = 2.0 * sigma * sigma;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long j = 0; j < n_rot; j++) {
+    for (long k = 0; k < n_data; k++) {
+      const double f = inv_phi[j * n_data + k];
+      double q = 0.0;
+      for (long i = 0; i < n_pix; i++) {
+        const double r = K[k * n_pix + i] * f - W[j * n_pix + i];
+        q += r * r;
+      }
+      S[j * n_data + k] = -q / s2 + log(weight[j]);
+    }
+  }
+}
+
+/*
+ * M-step of the Gaussian model, Eq. 2.5 with the frames scaled by their
+ * fluence, split into the numerator and denominator Eq. 2.12 consumes:
+ *   Num_ij = sum_k P_jk K_ik / phi_jk,   den_j = sum_k P_jk.
+ */
+void oracle_mstep_gauss(long n_rot, long n_pix, long n_data, const double* P, const double* K,
+                        const double* inv_phi, double* Num, double* den) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long j = 0; j < n_rot; j++) {
+    double d = 0.0;
+    for (long k = 0; k < n_data; k++) d += P[j * n_data + k];
+    den[j] = d;
+    for (long i = 0; i < n_pix; i++) {
+      double s = 0.0;
+      for (long k = 0; k < n_data; k++)
+        s += P[j * n_data + k] * K[k * n_pix + i] * inv_phi[j * n_data + k];
+      Num[j * n_pix + i] = s;
+    }
+  }
+}
+
+/*
+ * One pass of Algorithm 2.1 under the Gaussian model: expand (no floor: the
+ * model has no logarithm), fluence, scores, E-step, M-step, compress.
+ * Returns sum_k lse_k.
+ */
+double oracle_iteration_gauss(int N, const double* grid, long n_rot, const double* quat,
+                              const double* weight, long n_pix, const double* q, long n_data,
+                              const double* K, double sigma, int mode, double* grid_out,
+                              double* P_out, double* lse_out) {
+  long M = (long)N * N * N;
+  double* W = malloc(sizeof(double) * (size_t)(n_rot * n_pix));
+  double* F = malloc(sizeof(double) * (size_t)(n_rot * n_data));
+  double* S = malloc(sizeof(double) * (size_t)(n_rot * n_data));
+  double* Num = malloc(sizeof(double) * (size_t)(n_rot * n_pix));
+  double* den = malloc(sizeof(double) * (size_t)n_rot);
+  double* gn = malloc(sizeof(double) * (size_t)M);
+  double* gd = malloc(sizeof(double) * (size_t)M);
+  double L = NAN;
+  if (W && F && S && Num && den && gn && gd) {
+    oracle_expand(N, grid, n_rot, quat, n_pix, q, 0.0, W);
+    oracle_fluence(n_rot, n_pix, n_data, W, K, F);
+    oracle_scores_gauss(n_rot, n_pix, n_data, W, weight, K, sigma, F, S);
+    L = oracle_estep(n_rot, n_data, S, S, lse_out); /* S now holds P */
+    if (P_out) memcpy(P_out, S, sizeof(double) * (size_t)(n_rot * n_data));
+    oracle_mstep_gauss(n_rot, n_pix, n_data, S, K, F, Num, den);
+    oracle_compress(N, n_rot, quat, n_pix, q, Num, den, mode, grid, gn, gd, grid_out);
+  }
+  free(W); free(F); free(S); free(Num); free(den); free(gn); free(gd);
   return L;
 }
 

@@ -55,6 +55,14 @@ def lib():
             L.oracle_iteration.argtypes = [ctypes.c_int, _dp, ctypes.c_long, _dp, _dp, ctypes.c_long,
                                            _dp, ctypes.c_long, _dp, ctypes.c_double, ctypes.c_int,
                                            _dp, _dp, _dp]
+            L.oracle_fluence.argtypes = [ctypes.c_long] * 3 + [_dp] * 3
+            L.oracle_scores_gauss.argtypes = [ctypes.c_long] * 3 + [_dp] * 3 + [ctypes.c_double,
+                                                                                _dp, _dp]
+            L.oracle_mstep_gauss.argtypes = [ctypes.c_long] * 3 + [_dp] * 5
+            L.oracle_iteration_gauss.restype = ctypes.c_double
+            L.oracle_iteration_gauss.argtypes = [ctypes.c_int, _dp, ctypes.c_long, _dp, _dp,
+                                                 ctypes.c_long, _dp, ctypes.c_long, _dp,
+                                                 ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
             L.oracle_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -156,6 +164,54 @@ def iteration(grid, quat, weight, q, K, w_floor: float, mode: int = 0, want_P: b
     P = np.empty((quat.shape[0], K.shape[0])) if want_P else None
     L = lib().oracle_iteration(N, _p(grid), quat.shape[0], _p(quat), _p(weight), q.shape[0], _p(q),
                                K.shape[0], _p(K), w_floor, mode, _p(out), _p(P), _p(lse))
+    if want_P:
+        return out, lse, L, P
+    return out, lse, L
+
+
+# ----------------------------------------------------------------------------
+# Gaussian noise model (Eqs. 2.2-2.3, 2.5-2.6)
+# ----------------------------------------------------------------------------
+
+def fluence(W, K) -> np.ndarray:
+    """1/phi_jk of Eq. 2.6 (0 for an empty frame): [n_rot, n_data]."""
+    W, K = _f64(W), _f64(K)
+    F = np.empty((W.shape[0], K.shape[0]))
+    lib().oracle_fluence(W.shape[0], W.shape[1], K.shape[0], _p(W), _p(K), _p(F))
+    return F
+
+
+def scores_gauss(W, weight, K, sigma: float, inv_phi=None) -> np.ndarray:
+    """S_jk = -sum_i (K_ik / phi_jk - W_ij)^2 / (2 sigma^2) + log w_j."""
+    W, weight, K = _f64(W), _f64(weight), _f64(K)
+    F = fluence(W, K) if inv_phi is None else _f64(inv_phi)
+    S = np.empty((W.shape[0], K.shape[0]))
+    lib().oracle_scores_gauss(W.shape[0], W.shape[1], K.shape[0], _p(W), _p(weight), _p(K),
+                              float(sigma), _p(F), _p(S))
+    return S
+
+
+def mstep_gauss(P, K, inv_phi) -> tuple[np.ndarray, np.ndarray]:
+    """(Num_ij = sum_k P_jk K_ik / phi_jk, den_j = sum_k P_jk)."""
+    P, K, F = _f64(P), _f64(K), _f64(inv_phi)
+    Num = np.empty((P.shape[0], K.shape[1]))
+    den = np.empty(P.shape[0])
+    lib().oracle_mstep_gauss(P.shape[0], K.shape[1], P.shape[1], _p(P), _p(K), _p(F), _p(Num),
+                             _p(den))
+    return Num, den
+
+
+def iteration_gauss(grid, quat, weight, q, K, sigma: float, mode: int = 0,
+                    want_P: bool = False):
+    """Algorithm 2.1 under the Gaussian model: (grid_out, lse, sum lse[, P])."""
+    grid, quat, weight, q, K = _f64(grid), _f64(quat), _f64(weight), _f64(q), _f64(K)
+    N = grid.shape[0]
+    out = np.empty_like(grid)
+    lse = np.empty(K.shape[0])
+    P = np.empty((quat.shape[0], K.shape[0])) if want_P else None
+    L = lib().oracle_iteration_gauss(N, _p(grid), quat.shape[0], _p(quat), _p(weight),
+                                     q.shape[0], _p(q), K.shape[0], _p(K), float(sigma), mode,
+                                     _p(out), _p(P), _p(lse))
     if want_P:
         return out, lse, L, P
     return out, lse, L
