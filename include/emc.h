@@ -67,6 +67,23 @@ typedef enum emc_precision {
   EMC_PREC_FP16_SPLIT = 3
 } emc_precision;
 
+/* Noise model of the frames given W_ij (Sec. 2.2). */
+typedef enum emc_model {
+  /* Poisson: log P(K_ik | W_ij) = K_ik log W_ij - W_ij - log K_ik! */
+  EMC_MODEL_POISSON = 0,
+  /* Gaussian with per-(j,k) fluence (Eqs. 2.2-2.3, 2.5-2.6):
+   * log P = -(K_ik / phi_jk - W_ij)^2 / (2 sigma^2) + const, with
+   * phi_jk = sum_i K_ik^2 / sum_i W_ij K_ik evaluated on the model of the
+   * current iteration (its least-squares optimum) and used in that
+   * iteration's E- and M-step. Then
+   *   S_jk = (G_jk^2 / A_k - B_j) / (2 sigma^2) + log w_j,
+   *   G_jk = sum_i W_ij K_ik, A_k = sum_i K_ik^2, B_j = sum_i W_ij^2,
+   * so the E-step is the same contraction over pixels with W in place of
+   * log W. Needs precision EMC_PREC_FP16_SPLIT and EMC_FLAG_STORE_SCORES;
+   * the sparse Maximize and emc_loglik_static are Poisson only. */
+  EMC_MODEL_GAUSSIAN = 1
+} emc_model;
+
 typedef enum emc_compress_mode {
   EMC_COMPRESS_DEFERRED = 0, /* Eq. 2.11-2.12: normalise after compression */
   EMC_COMPRESS_IDW = 1       /* Eq. 2.5 per slice, then Eq. 2.10 */
@@ -91,7 +108,9 @@ typedef struct emc_config {
                             0 = all rotations in one chunk */
   int32_t n_cand;        /* candidate rotations per frame for the sparse
                             Maximize (0 = none; at most min(n_rot, 4096)) */
-  int32_t reserved;      /* 0 */
+  int32_t model;         /* emc_model (0 = Poisson) */
+  double sigma;          /* sigma of Eq. 2.2 (> 0) for EMC_MODEL_GAUSSIAN;
+                            not read for the Poisson model */
 } emc_config;
 
 /* Per-call buffer sizes in bytes for a block of nrot rotations. */
@@ -110,7 +129,9 @@ typedef struct emc_buffer_sizes {
 } emc_buffer_sizes;
 
 typedef struct emc_iter_stats {
-  double loglik;       /* sum_k lse_k (Poisson log-likelihood without log K!) */
+  double loglik;       /* sum_k lse_k (Poisson: the log-likelihood without
+                          sum log K!; Gaussian: without the per-frame
+                          normal-density constants) */
   double ms_expand, ms_loglik, ms_normalize, ms_update, ms_compress, ms_total;
   int32_t device_status; /* emc_status recorded on the device (0 = OK) */
   int32_t kernels;       /* kernel launches made by the call */
@@ -156,7 +177,10 @@ int emc_ctx_status(emc_ctx* ctx, int* device_status);
  * ld_k >= n_pix, into the context's padded frame buffer (BF16, or FP16 for
  * EMC_PREC_FP16_SPLIT). Counts must lie in [0, 256] (exact in BF16; [0, 2048]
  * in FP16) and sum to below 65536 per frame (8192 for FP16_SPLIT); otherwise
- * the device status becomes EMC_ERR_UNSUPPORTED. */
+ * the device status becomes EMC_ERR_UNSUPPORTED. The Gaussian model keeps an
+ * FP16 copy (the E-step operand) and a BF16 copy (the M-step operand), so its
+ * counts must lie in [0, 256]; frame totals are not limited. It also records
+ * A_k = sum_i K_ik^2 and the largest frame total. */
 int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stream);
 
 /* e-step, Eq. 2.9, for rotations [rot0, rot0 + nrot):
@@ -166,7 +190,14 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
  *             BF16_SPLIT -> bf16[3][rows][ld_pix] (hi, mid, lo planes);
  *             FP16_SPLIT -> fp16[2][rows][ld_pix] (hi, rest planes);
  *             padding columns and rows are written as 0.
- * bias (device double[rows]) = log w_j - sum_i W_ij (-inf on padding rows). */
+ * bias (device double[rows]) = log w_j - sum_i W_ij (-inf on padding rows).
+ * Gaussian model: W_ij = max(trilinear(grid, R_j q_i), 0) (w_floor is not
+ * used); L = fp16[3][rows][ld_pix] holding s W = hi + mid + lo, hi integral,
+ * with s = 2^e chosen from max(grid) and the largest frame total so that
+ * every partial sum of hi K stays below 2^24 (exact in FP32); bias_j =
+ * log w_j - sum_i W_ij^2 / (2 sigma^2). The call records s in the context;
+ * emc_loglik, emc_normalize and emc_update use the scale of the last
+ * emc_expand. */
 int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void* L,
                double* bias, emc_stream stream);
 
@@ -175,9 +206,15 @@ int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void
  * S_jk = sum_i K_ik log W_ij + bias_j. lse_m, lse_s: device double[ld_data];
  * accumulate = 0 starts from (m, s) = (-inf, 0), else merges into them.
  * scores (device, score_bytes, may be NULL): when given, the scores are also
- * stored, as float d[rows][ld_data] relative to float r[rows/32][ld_data]
- * (the maximum of each 32-row group of a column, on the 1/8 grid; d follows
- * directly after d in the same buffer): S_jk = d_jk + r_(j/32)k. */
+ * stored, frame-major, as float d[ld_data][rows] relative to float
+ * r[rows/32][ld_data] (the maximum of each 32-row group of a column, on the
+ * 1/64 grid; r follows directly after d in the same buffer):
+ * S_jk = d[k][j] + r[j/32][k].
+ * Gaussian model: S_jk = (G_jk^2 / A_k - B_j) / (2 sigma^2) + log w_j from
+ * the FP16 three-plane L (see emc_model); scores more than about 1.2e5 below
+ * zero are clamped there (their exp is 0 next to any frame's best rotation),
+ * and a frame whose best score lies below that makes the device status
+ * EMC_ERR_NUMERIC (sigma too small for the data). */
 int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, double* lse_m,
                double* lse_s, int accumulate, void* scores, emc_stream stream);
 
@@ -188,7 +225,12 @@ int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, do
  * P (device): FP32 -> float[rows][ld_data]; BF16 / BF16_SPLIT ->
  * bf16[2][rows][ld_data] (hi, lo planes, P = hi + lo; lo is 0 for BF16);
  * FP16_SPLIT -> fp16[2][rows][ld_data], P = (hi + lo) / 2^14.
- * Padding frames and rows are written as 0. */
+ * Padding frames and rows are written as 0.
+ * Gaussian model (scores and bias required): the planes hold P_jk / phi_jk,
+ * the responsibility already divided by the fluence that Eq. 2.5 applies to
+ * frame k (1/phi_jk = sqrt(2 sigma^2 (S_jk - bias_j) / A_k)), as
+ * bf16[2][rows][ld_data] hi + lo; after the planes the buffer holds
+ * float den[rows] = sum_k P_jk (prob_bytes counts it). */
 int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
                   const double* lse_m, const double* lse_s, const void* scores, void* P,
                   emc_stream stream);
@@ -225,7 +267,10 @@ int emc_loglik_static(const emc_config* cfg, const void* L, const double* bias,
                       int accumulate, int32_t* device_status, emc_stream stream);
 
 /* M-step, Eq. 2.11: Num (device float[rows][ld_pix]) = P K over frames;
- * den (device float[rows]) = sum_k P_jk. */
+ * den (device float[rows]) = sum_k P_jk.
+ * Gaussian model: Num_ij = sum_k P_jk K_ik / phi_jk (Eq. 2.5 before the
+ * division) from the planes emc_normalize wrote; den is copied from the end
+ * of the P buffer. */
 int emc_update(emc_ctx* ctx, const void* P, int64_t nrot, float* Num, float* den,
                emc_stream stream);
 

@@ -19,19 +19,35 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
   size_t qh, ql, quat, rot, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
-      Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, total;
+      Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, gk, gauss,
+      Kb2, total;
 };
+
+// Gaussian scalars inside the 256-byte block at Layout::gauss
+constexpr size_t kGaussMaxOff = 0;    // unsigned: bits of max(grid)
+constexpr size_t kGaussNmaxOff = 8;   // unsigned long long: largest frame total
+constexpr size_t kGaussScaleOff = 16; // float4: (s, 1/s^2, ps, 1/ps)
 
 size_t score_bytes(int64_t rows, int64_t ld_data) {
   return sizeof(float) * (size_t)(rows + rows / 32) * ld_data;
 }
 
-int planes_L(int prec) {
-  return prec == EMC_PREC_BF16_SPLIT ? 3 : (prec == EMC_PREC_FP16_SPLIT ? 2 : 1);
+bool is_gauss(const emc_config* c) { return c->model == EMC_MODEL_GAUSSIAN; }
+
+// bytes of L (emc_expand) and P (emc_normalize) for `rows` rotations
+size_t L_bytes(const emc_config* c, int64_t rows, int64_t ld_pix) {
+  const int p = c->precision;
+  const int planes = is_gauss(c) ? 3 : (p == EMC_PREC_BF16_SPLIT ? 3 : (p == EMC_PREC_FP16_SPLIT ? 2 : 1));
+  return (size_t)planes * (p == EMC_PREC_FP32 ? 4 : 2) * (size_t)rows * ld_pix;
 }
-size_t elem_L(int prec) { return prec == EMC_PREC_FP32 ? 4 : 2; }
-int planes_P(int prec) { return prec == EMC_PREC_FP32 ? 1 : 2; }
-size_t elem_P(int prec) { return prec == EMC_PREC_FP32 ? 4 : 2; }
+// Gaussian: after the planes, den[rows] (float)
+size_t P_plane_bytes(const emc_config* c, int64_t rows, int64_t ld_data) {
+  const int p = c->precision;
+  return (size_t)(p == EMC_PREC_FP32 ? 1 : 2) * (p == EMC_PREC_FP32 ? 4 : 2) * (size_t)rows * ld_data;
+}
+size_t P_bytes(const emc_config* c, int64_t rows, int64_t ld_data) {
+  return P_plane_bytes(c, rows, ld_data) + (is_gauss(c) ? align256(sizeof(float) * rows) : 0);
+}
 
 int check_config(const emc_config* c) {
   if (!c) return EMC_ERR_ARG;
@@ -43,9 +59,16 @@ int check_config(const emc_config* c) {
   if (c->compress_mode != EMC_COMPRESS_DEFERRED && c->compress_mode != EMC_COMPRESS_IDW)
     return EMC_ERR_ARG;
   if (!(c->w_floor > 0.0) || !isfinite(c->w_floor)) return EMC_ERR_ARG;
-  if ((c->precision == EMC_PREC_BF16_SPLIT || c->precision == EMC_PREC_FP16_SPLIT) &&
-      log(c->w_floor) < (double)kHiMin)
+  if (c->model != EMC_MODEL_POISSON && c->model != EMC_MODEL_GAUSSIAN) return EMC_ERR_ARG;
+  if (is_gauss(c)) {
+    if (!(c->sigma > 0.0) || !isfinite(c->sigma)) return EMC_ERR_ARG;
+    if (c->precision != EMC_PREC_FP16_SPLIT || !(c->flags & EMC_FLAG_STORE_SCORES) ||
+        c->n_cand != 0)
+      return EMC_ERR_UNSUPPORTED;
+  } else if ((c->precision == EMC_PREC_BF16_SPLIT || c->precision == EMC_PREC_FP16_SPLIT) &&
+             log(c->w_floor) < (double)kHiMin) {
     return EMC_ERR_UNSUPPORTED;
+  }
   if (c->rot_chunk < 0 || (c->flags & ~EMC_FLAG_STORE_SCORES) != 0) return EMC_ERR_ARG;
   if (c->n_cand < 0 || c->n_cand > c->n_rot || c->n_cand > 4096) return EMC_ERR_ARG;
   return EMC_OK;
@@ -58,7 +81,6 @@ Layout make_layout(const emc_config* c) {
   y.rows = round_up(c->n_rot, 128);
   y.chunk_rows = c->rot_chunk > 0 ? std::min(round_up(c->rot_chunk, 128), y.rows) : y.rows;
   y.part_tiles = y.rows / 64;
-  const int p = c->precision;
   const int64_t nvox = (int64_t)c->N * c->N * c->N;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -73,7 +95,7 @@ Layout make_layout(const emc_config* c) {
   y.logw = take(sizeof(double) * c->n_rot);
   y.Kb = take(2 * (size_t)y.ld_data * y.ld_pix);
   y.status = take(256);
-  y.L = take(planes_L(p) * elem_L(p) * (size_t)y.rows * y.ld_pix);
+  y.L = take(L_bytes(c, y.rows, y.ld_pix));
   y.bias = take(sizeof(double) * y.rows);
   y.lse_m = take(sizeof(double) * y.ld_data);
   y.lse_s = take(sizeof(double) * y.ld_data);
@@ -81,7 +103,7 @@ Layout make_layout(const emc_config* c) {
   y.part_m = take(sizeof(double) * (size_t)y.part_tiles * y.ld_data);
   y.part_s = take(sizeof(float) * (size_t)y.part_tiles * y.ld_data);
   y.S = (c->flags & EMC_FLAG_STORE_SCORES) ? take(score_bytes(y.rows, y.ld_data)) : 0;
-  y.P = take(planes_P(p) * elem_P(p) * (size_t)y.chunk_rows * y.ld_data);
+  y.P = take(P_bytes(c, y.chunk_rows, y.ld_data));
   y.Num = take(sizeof(float) * (size_t)y.chunk_rows * y.ld_pix);
   y.den = take(sizeof(float) * y.chunk_rows);
   y.gnum = take(sizeof(double) * nvox);
@@ -97,6 +119,9 @@ Layout make_layout(const emc_config* c) {
   y.Sc = M ? take(sizeof(double) * (size_t)y.ld_data * M) : 0;
   y.Pc = M ? take(sizeof(float) * (size_t)y.ld_data * M) : 0;
   y.lsec = M ? take(sizeof(double) * (size_t)y.ld_data) : 0;
+  y.gk = is_gauss(c) ? take(sizeof(float4) * (size_t)y.ld_data) : 0;
+  y.gauss = take(256);
+  y.Kb2 = is_gauss(c) ? take(2 * (size_t)y.ld_data * y.ld_pix) : 0;
   y.total = o;
   return y;
 }
@@ -119,6 +144,11 @@ struct emc_ctx {
   double* logw;
   uint16_t* Kb;
   int32_t* status;
+  uint16_t* Kb2;              // Gaussian: BF16 copy of the frames (the update operand)
+  float4* gk;                 // Gaussian per-frame constants
+  unsigned* gmax;             // Gaussian: bits of max(grid) of the last emc_expand
+  unsigned long long* nmax;   // Gaussian: largest frame total
+  float4* gsc;                // Gaussian scales of the last emc_expand
   bool frames_loaded;
   bool cand_loaded;
   cudaEvent_t ev[8];
@@ -154,13 +184,12 @@ int emc_buffer_sizes_for(const emc_config* cfg, int64_t nrot, emc_buffer_sizes* 
   if (st) return st;
   if (!out || nrot < 1 || nrot > cfg->n_rot) return EMC_ERR_ARG;
   Layout y = make_layout(cfg);
-  const int p = cfg->precision;
   out->ld_pix = y.ld_pix;
   out->ld_data = y.ld_data;
   out->rows = round_up(nrot, 128);
-  out->logw_bytes = planes_L(p) * elem_L(p) * (size_t)out->rows * y.ld_pix;
+  out->logw_bytes = L_bytes(cfg, out->rows, y.ld_pix);
   out->bias_bytes = sizeof(double) * out->rows;
-  out->prob_bytes = planes_P(p) * elem_P(p) * (size_t)out->rows * y.ld_data;
+  out->prob_bytes = P_bytes(cfg, out->rows, y.ld_data);
   out->num_bytes = sizeof(float) * (size_t)out->rows * y.ld_pix;
   out->den_bytes = sizeof(float) * out->rows;
   out->lse_bytes = sizeof(double) * y.ld_data;
@@ -257,6 +286,11 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   c->logw = (double*)(c->ws + y.logw);
   c->Kb = (uint16_t*)(c->ws + y.Kb);
   c->status = (int32_t*)(c->ws + y.status);
+  c->gk = y.gk ? (float4*)(c->ws + y.gk) : nullptr;
+  c->Kb2 = y.Kb2 ? (uint16_t*)(c->ws + y.Kb2) : nullptr;
+  c->gmax = (unsigned*)(c->ws + y.gauss + kGaussMaxOff);
+  c->nmax = (unsigned long long*)(c->ws + y.gauss + kGaussNmaxOff);
+  c->gsc = (float4*)(c->ws + y.gauss + kGaussScaleOff);
   cudaStream_t s = (cudaStream_t)stream;
   bool ok = true;
   ok &= cudaMemcpyAsync(c->ws + y.qh, qh.data(), sizeof(float4) * y.ld_pix,
@@ -270,6 +304,7 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   ok &= cudaMemcpyAsync(c->ws + y.rot, rot.data(), sizeof(RotDF) * cfg->n_rot,
                         cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= cudaMemsetAsync(c->status, 0, 256, s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->ws + y.gauss, 0, 256, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->ws + y.fbin, fbin.data(), sizeof(int16_t) * y.ld_pix,
                         cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->ws + y.finv, finv.data(), sizeof(float) * kFeat, cudaMemcpyHostToDevice,
@@ -306,9 +341,16 @@ int emc_ctx_status(emc_ctx* ctx, int* device_status) {
 int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stream) {
   if (!ctx || !K || ld_k < ctx->cfg.n_pix) return EMC_ERR_ARG;
   const Layout& y = ctx->lay;
+  const bool g = is_gauss(&ctx->cfg);
   CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb,
-                        ctx->cfg.precision == EMC_PREC_FP16_SPLIT, ctx->status,
+                        g ? 3 : (ctx->cfg.precision == EMC_PREC_FP16_SPLIT ? 1 : 0), ctx->status,
                         (cudaStream_t)stream));
+  if (g) {
+    CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb2,
+                          2, ctx->status, (cudaStream_t)stream));
+    CU(launch_gauss_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, ctx->cfg.sigma,
+                           ctx->gk, ctx->nmax, (cudaStream_t)stream));
+  }
   ctx->frames_loaded = true;
   return EMC_OK;
 }
@@ -325,8 +367,13 @@ int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L
               cudaStream_t s) {
   const int64_t rows = round_up(nrot, 128);
   Planes p{L, rows * c->lay.ld_pix, c->lay.ld_pix};
+  const bool g = is_gauss(&c->cfg);
+  if (g)
+    CU(launch_gauss_scales(grid, (int64_t)c->cfg.N * c->cfg.N * c->cfg.N, c->gmax, c->nmax,
+                           c->gsc, c->status, s));
   CU(launch_expand(c->geom, grid, c->rot + rot0, c->logw + rot0, nrot, rows,
-                   c->cfg.precision, (float)c->cfg.w_floor, p, bias, c->status, s));
+                   c->cfg.precision, (float)c->cfg.w_floor, p, bias, g ? c->gsc : nullptr,
+                   c->cfg.sigma, c->status, s));
   return EMC_OK;
 }
 
@@ -350,11 +397,13 @@ int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const d
     tiles = simt_pass1_tiles(rows);
   } else {
     Planes p{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
+    const bool g = is_gauss(&c->cfg);
     CU(launch_tc_pass1(p, c->cfg.precision, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix, pm, ps,
-                       S, Sref, c->status, s));
+                       S, Sref, g ? c->gk : nullptr, g ? c->gsc : nullptr, c->status, s));
     tiles = tc_pass1_tiles(rows);
   }
   CU(launch_lse_merge(pm, ps, tiles, y.ld_data, c->cfg.n_data, lse_m, lse_s, accumulate,
+                      is_gauss(&c->cfg),
                       c->status, s));
   return EMC_OK;
 }
@@ -366,6 +415,16 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
                  int64_t ldS, const float* Sref, void* P, int64_t Prows, cudaStream_t s) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
+  if (is_gauss(&c->cfg)) {
+    if (!S || !bias) return EMC_ERR_UNSUPPORTED;
+    float2* lse2 = (float2*)(c->ws + y.lse2);
+    float* den = (float*)((char*)P + P_plane_bytes(&c->cfg, Prows, y.ld_data));
+    CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s));
+    CU(launch_normalize_scores_gauss(S, ldS, Sref, lse2, bias, c->gk, rows, nrot,
+                                     y.ld_data, c->cfg.n_data, (uint16_t*)P, Prows * y.ld_data,
+                                     den, s));
+    return EMC_OK;
+  }
   if (S) {
     float2* lse2 = (float2*)(c->ws + y.lse2);
     CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s));
@@ -395,8 +454,16 @@ int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num
                           den, s));
   } else {
     Planes pp{(void*)P, Prows * y.ld_data, y.ld_data};
-    CU(launch_tc_update(pp, c->cfg.precision, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num, den,
-                        c->status, s));
+    if (is_gauss(&c->cfg)) {
+      // BF16 hi + lo planes of P / phi against the BF16 copy of the frames
+      CU(launch_tc_update(pp, EMC_PREC_BF16_SPLIT, rows, c->Kb2, y.ld_data, y.ld_pix, c->cfg.n_pix,
+                          Num, nullptr, c->status, s));
+      const char* tail = (const char*)P + P_plane_bytes(&c->cfg, Prows, y.ld_data);
+      CU(cudaMemcpyAsync(den, tail, sizeof(float) * rows, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CU(launch_tc_update(pp, c->cfg.precision, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num,
+                          den, c->status, s));
+    }
   }
   return EMC_OK;
 }
@@ -432,6 +499,8 @@ int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
                   emc_stream stream) {
   if (!ctx || !lse_m || !lse_s || !P) return EMC_ERR_ARG;
   if (!scores && (!L || !bias)) return EMC_ERR_ARG;
+  if (is_gauss(&ctx->cfg) && !scores) return EMC_ERR_UNSUPPORTED;
+  if (is_gauss(&ctx->cfg) && !bias) return EMC_ERR_ARG;
   if (check_rot_range(ctx, 0, nrot)) return EMC_ERR_ARG;
   if (!ctx->frames_loaded) return EMC_ERR_ARG;
   if (((uintptr_t)scores) & 15) return EMC_ERR_ARG;
@@ -491,13 +560,12 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   double* gd = (double*)(c->ws + y.gden);
   double* ll = (double*)(c->ws + y.scalar);
   const size_t gb = sizeof(double) * (size_t)c->cfg.N * c->cfg.N * c->cfg.N;
-  const size_t Lelem = elem_L(c->cfg.precision);
   int kernels = 0;
   int st;
 
   if (stats) CU(cudaEventRecord(c->ev[0], s));
   if ((st = do_expand(c, grid_in, 0, n_rot, L, bias, s))) return st;
-  kernels++;
+  kernels += is_gauss(&c->cfg) ? 3 : 1;  // Gaussian: grid maximum and scales first
   if (stats) CU(cudaEventRecord(c->ev[1], s));
   float* S = (c->cfg.flags & EMC_FLAG_STORE_SCORES) ? (float*)(c->ws + y.S) : nullptr;
   if ((st = do_loglik(c, L, y.rows, 0, bias, n_rot, lse_m, lse_s, 0, S, s))) return st;
@@ -521,7 +589,8 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     if (stats) CU(cudaEventRecord(c->ev[5], s));
     CU(launch_compress(c->geom, c->rot + r0, nr, Num, den, c->cfg.compress_mode, gn, gd, s));
     if (stats) CU(cudaEventRecord(c->ev[6], s));
-    kernels += 3;
+    // normalize: lse split + the pass (one SIMT kernel when recomputing in FP32)
+    kernels += (S || c->cfg.precision != EMC_PREC_FP32 ? 2 : 1) + 2;
     if (stats) {
       // chunk timings need a host wait per chunk; only when stats are asked for
       float a = 0, b = 0, d = 0;
@@ -534,7 +603,6 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
       t_cmp += d;
     }
   }
-  (void)Lelem;
   if (stats) CU(cudaEventRecord(c->ev[3], s));
   CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, grid_in, grid_out, s));
   kernels++;

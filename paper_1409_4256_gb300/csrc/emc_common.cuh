@@ -139,4 +139,26 @@ constexpr double kGridD = 64.0;
 // FP16 maximum, P down to ~4e-9 stays normal); the update removes the scale.
 constexpr float kP16Scale = 16384.0f;
 
+// Gaussian model (Eqs. 2.2-2.3): S_jk <= log w_j < 0, and scores further than
+// kGaussClamp below zero are clamped -- their exp vanishes next to any
+// frame's best rotation, and the clamp keeps every score's 1/64-grid part
+// exact in FP32.
+constexpr float kGaussClamp = 120000.0f;
+
+// Scale of the Gaussian contraction, from the grid maximum Wmax and the
+// largest frame total Nmax (x: s, y: 1/s^2):
+//   s  = the largest power of two with s Wmax Nmax <= 2^23 and s Wmax <= 2^15.
+//        The integral hi part of s W is at most s Wmax + 1/2, so every partial
+//        sum of hi K over a frame stays below 2^24 (exact in FP32) and hi
+//        stays far inside the FP16 range.
+__host__ __device__ inline float4 gauss_scales(float wmax, long long nmax) {
+  if (!(wmax > 0.f) || !(wmax < 3.0e38f)) return make_float4(1.f, 1.f, 0.f, 0.f);
+  const double w = (double)wmax, n = (double)(nmax > 0 ? nmax : 1);
+  int e = ilogb(8388608.0 / (w * n));
+  const int e2 = ilogb(32768.0 / w);
+  e = e < e2 ? e : e2;
+  e = e < -60 ? -60 : (e > 60 ? 60 : e);
+  return make_float4((float)ldexp(1.0, e), (float)ldexp(1.0, -2 * e), 0.f, 0.f);
+}
+
 }  // namespace emc

@@ -28,14 +28,35 @@ struct Planes {
   int64_t ld;            // elements between rows
 };
 
-// fp16 != 0: frames in FP16 (EMC_PREC_FP16_SPLIT), else BF16
+// fp16: bit 0 FP16 frames (EMC_PREC_FP16_SPLIT), else BF16; bit 1 no limit on
+// the frame total (the Gaussian model's two copies)
 cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
                                int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int fp16,
                                int32_t* status, cudaStream_t s);
 
+// gsc != NULL: Gaussian model (FP16 three-plane s W, bias log w - sum W^2 / 2 sigma^2)
 cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
-                          float w_floor, Planes L, double* bias, int32_t* status, cudaStream_t s);
+                          float w_floor, Planes L, double* bias, const float4* gsc, double sigma,
+                          int32_t* status, cudaStream_t s);
+
+// ---- Gaussian model (misc.cu) ----
+// Per-frame constants gk[ld_data] = (c_k hi, c_k lo, 2 sigma^2 / A_k, 0) and the
+// largest frame total (*nmax).
+cudaError_t launch_gauss_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                                int64_t ld_data, double sigma, float4* gk,
+                                unsigned long long* nmax, cudaStream_t s);
+// max(grid) into *gmax, then the scales (s, 1/s^2, 0, 0) into *gsc.
+cudaError_t launch_gauss_scales(const float* grid, int64_t n_vox, unsigned* gmax,
+                                const unsigned long long* nmax, float4* gsc, int32_t* status,
+                                cudaStream_t s);
+// Pass 2 from stored scores: BF16 hi + lo planes of P / phi, den[rows] = sum_k P.
+cudaError_t launch_normalize_scores_gauss(const float* S, int64_t ldS, const float* Sref,
+                                          const float2* lse2, const double* bias,
+                                          const float4* gk, int64_t rows,
+                                          int64_t nrot, int64_t ld_data, int64_t n_data,
+                                          uint16_t* P, int64_t P_plane, float* den,
+                                          cudaStream_t s);
 
 // FP32 SIMT forms (precision EMC_PREC_FP32).
 // S, Sref (optional, both or neither): scores relative to 32-row group maxima,
@@ -56,7 +77,7 @@ int64_t simt_pass1_tiles(int64_t rows);
 // Merge of per-tile (max, sum) pairs into the running per-frame (m, s).
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
-                             int accumulate, int32_t* status, cudaStream_t s);
+                             int accumulate, int gauss, int32_t* status, cudaStream_t s);
 cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n_data,
                              int64_t ld_data, float2* out, cudaStream_t s);
 // E-step pass 2 from stored scores (frame-major, ld ldS); P layout as
@@ -69,16 +90,19 @@ cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t 
                               double* out, cudaStream_t s);
 
 // tcgen05 forms (precision EMC_PREC_BF16 / BF16_SPLIT / FP16_SPLIT).
+// gk, gsc != NULL: the Gaussian model's pass 1 (three FP16 planes of s W).
 cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
-                            int32_t* status, cudaStream_t s);
+                            const float4* gk, const float4* gsc, int32_t* status,
+                            cudaStream_t s);
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
 cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bias, int64_t rows,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
                                 float2* lse2, Planes P, int32_t* status, cudaStream_t s);
-// P planes: hi + lo (BF16 split, FP16 split) or hi only (BF16).
+// P planes: hi + lo (BF16 split, FP16 split) or hi only (BF16); FP16 planes
+// carry the scale 2^14. den NULL: not written.
 cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
                              int32_t* status, cudaStream_t s);

@@ -12,6 +12,12 @@
 // (per-thread compensated FP32 sums, FP64 across the block).
 // Writes are coalesced along pixels; HBM traffic is the L write (4 B/(i,j)
 // for FP32, 2 B for BF16, 6 B for the three-term split, 4 B for the FP16 split).
+//
+// Gaussian model (GAUSS): no floor and no logarithm. s W_ij (s = 2^e from the
+// context's scales) is split into three FP16 terms: hi integral (rint below
+// 2048, else the FP16 rounding, itself integral there), mid = fp16(s W - hi),
+// lo = fp16(s W - hi - mid); the representation error is below 2^-23 s^-1 W
+// units. The CTA sums W_ij^2 instead, bias_j = log w_j - sum_i W_ij^2 / (2 sigma^2).
 #include "emc_common.cuh"
 #include "emc_internal.h"
 
@@ -19,13 +25,14 @@ namespace emc {
 
 constexpr int kExpandThreads = 256;
 
-template <int PREC>
+template <int PREC, bool GAUSS>
 __global__ void __launch_bounds__(kExpandThreads)
     expand_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
                   int64_t ld_pix, int N, const float* __restrict__ grid,
                   const RotDF* __restrict__ rot, const double* __restrict__ logw, int64_t nrot,
                   float w_floor, void* __restrict__ Lbase, int64_t plane_stride,
-                  double* __restrict__ bias, int32_t* status) {
+                  double* __restrict__ bias, const float4* __restrict__ gsc, double inv2s2,
+                  int32_t* status) {
   const int64_t row = blockIdx.x;
   __shared__ RotDF R;
   __shared__ double red[kExpandThreads / 32];
@@ -38,8 +45,9 @@ __global__ void __launch_bounds__(kExpandThreads)
   uint16_t* Lb = reinterpret_cast<uint16_t*>(Lbase) + row * ld_pix;
   const float half_n = 0.5f * (float)N;
   const int64_t nn = (int64_t)N * N;
-  float wsum = 0.f, wcomp = 0.f;  // Kahan-compensated sum of W over this thread's pixels
+  float wsum = 0.f, wcomp = 0.f;  // Kahan-compensated sum of W (W^2) over this thread's pixels
   int bad = 0;
+  const float gs = GAUSS ? gsc->x : 1.f;
 
   for (int64_t i = threadIdx.x; i < ld_pix; i += kExpandThreads) {
     float L = 0.f;
@@ -60,15 +68,22 @@ __global__ void __launch_bounds__(kExpandThreads)
                     ((c & 1) ? t[2] : 1.f - t[2]);
           W = fmaf(w, __ldg(grid + (int64_t)x * nn + (int64_t)y * N + z), W);
         }
-        W = fmaxf(W, w_floor);
-        const float ky = W - wcomp;
+        W = fmaxf(W, GAUSS ? 0.f : w_floor);
+        const float ky = (GAUSS ? W * W : W) - wcomp;
         const float kt = wsum + ky;
         wcomp = (kt - wsum) - ky;
         wsum = kt;
-        L = logf(W);
+        L = GAUSS ? W * gs : logf(W);
       }
     }
-    if (PREC == EMC_PREC_FP32) {
+    if (GAUSS) {
+      const float hi = L < 2048.f ? rintf(L) : fp16_val(fp16_bits(L));
+      const float r = L - hi;  // exact
+      const uint16_t mid = fp16_bits(r);
+      Lb[i] = fp16_bits(hi);
+      Lb[i + plane_stride] = mid;
+      Lb[i + 2 * plane_stride] = fp16_bits(r - fp16_val(mid));
+    } else if (PREC == EMC_PREC_FP32) {
       Lf[i] = L;
     } else if (PREC == EMC_PREC_BF16) {
       Lb[i] = bf16_bits(L);
@@ -102,37 +117,31 @@ __global__ void __launch_bounds__(kExpandThreads)
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kExpandThreads / 32; w++) s += red[w];
-    bias[row] = valid_row ? logw[row] - s : -INFINITY;
+    bias[row] = valid_row ? logw[row] - (GAUSS ? s * inv2s2 : s) : -INFINITY;
   }
 }
 
 cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
-                          float w_floor, Planes L, double* bias, int32_t* status, cudaStream_t s) {
+                          float w_floor, Planes L, double* bias, const float4* gsc, double sigma,
+                          int32_t* status, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
   dim3 grd((unsigned)rows), blk(kExpandThreads);
-  switch (precision) {
-    case EMC_PREC_FP32:
-      expand_kernel<EMC_PREC_FP32><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid,
-                                                       rot, logw, nrot, w_floor, L.base,
-                                                       L.plane_stride, bias, status);
-      break;
-    case EMC_PREC_BF16:
-      expand_kernel<EMC_PREC_BF16><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid,
-                                                       rot, logw, nrot, w_floor, L.base,
-                                                       L.plane_stride, bias, status);
-      break;
-    case EMC_PREC_FP16_SPLIT:
-      expand_kernel<EMC_PREC_FP16_SPLIT><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
-                                                             grid, rot, logw, nrot, w_floor,
-                                                             L.base, L.plane_stride, bias, status);
-      break;
-    default:
-      expand_kernel<EMC_PREC_BF16_SPLIT><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
-                                                             grid, rot, logw, nrot, w_floor,
-                                                             L.base, L.plane_stride, bias, status);
-      break;
+#define EMC_EXPAND(P, G)                                                                     \
+  expand_kernel<P, G><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid, rot, logw, \
+                                          nrot, w_floor, L.base, L.plane_stride, bias, gsc,     \
+                                          gsc ? 1.0 / (2.0 * sigma * sigma) : 0.0, status)
+  if (gsc) {
+    EMC_EXPAND(EMC_PREC_FP16_SPLIT, true);
+  } else {
+    switch (precision) {
+      case EMC_PREC_FP32: EMC_EXPAND(EMC_PREC_FP32, false); break;
+      case EMC_PREC_BF16: EMC_EXPAND(EMC_PREC_BF16, false); break;
+      case EMC_PREC_FP16_SPLIT: EMC_EXPAND(EMC_PREC_FP16_SPLIT, false); break;
+      default: EMC_EXPAND(EMC_PREC_BF16_SPLIT, false); break;
+    }
   }
+#undef EMC_EXPAND
   return cudaGetLastError();
 }
 

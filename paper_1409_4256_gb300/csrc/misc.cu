@@ -9,7 +9,9 @@ namespace emc {
 // (so that the M-step contraction also yields den_j = sum_k P_jk), everything
 // else 0. Counts outside [0, 256] (BF16; [0, 2048] FP16) or a frame total at or
 // above 65536 (8192 for FP16) would break the exact conversion or the exact
-// hi-term accumulation and are flagged.
+// hi-term accumulation and are flagged. fp16 is a bit set: bit 0 FP16 (else
+// BF16), bit 1 no limit on the total (the Gaussian model scales its operand
+// to the largest total).
 __global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, int64_t n_data,
                                    int64_t n_pix, int64_t ld_pix, uint16_t* __restrict__ Kb,
                                    int fp16, int32_t* status) {
@@ -22,14 +24,14 @@ __global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, 
     if (k < n_data) {
       if (i < n_pix) {
         int32_t c = K[k * ld_k + i];
-        if (c < 0 || c > (fp16 ? 2048 : 256)) bad = 1;
+        if (c < 0 || c > ((fp16 & 1) ? 2048 : 256)) bad = 1;
         tot += c;
         v = (float)c;
       } else if (i == n_pix) {
         v = 1.f;
       }
     }
-    Kb[k * ld_pix + i] = fp16 ? fp16_bits(v) : bf16_bits(v);
+    Kb[k * ld_pix + i] = (fp16 & 1) ? fp16_bits(v) : bf16_bits(v);
   }
   for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
@@ -37,7 +39,7 @@ __global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, 
   if (threadIdx.x == 0) {
     long long s = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
-    if (s >= (fp16 ? 8192 : 65536)) bad = 1;
+    if (!(fp16 & 2) && s >= ((fp16 & 1) ? 8192 : 65536)) bad = 1;
   }
   if (bad) set_status(status, EMC_ERR_UNSUPPORTED);
 }
@@ -50,6 +52,95 @@ cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, i
   return cudaGetLastError();
 }
 
+// Gaussian model, per frame k: A_k = sum_i K_ik^2 and the constants the
+// kernels need, gk[k] = (c_k hi, c_k lo, 2 sigma^2 / A_k, 0) with
+// c_k = 1 / (2 sigma^2 A_k) split into two FP32 (0 for an empty or padding
+// frame: its score is -B_j / (2 sigma^2) whatever the fluence); the largest
+// frame total goes to *nmax (atomic maximum; zeroed by the caller).
+__global__ void gauss_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, int64_t n_data,
+                                    int64_t n_pix, double inv2s2, float4* __restrict__ gk,
+                                    unsigned long long* nmax) {
+  const int64_t k = blockIdx.x;
+  __shared__ long long ra[8], rn[8];
+  long long a = 0, n = 0;
+  if (k < n_data) {
+    for (int64_t i = threadIdx.x; i < n_pix; i += blockDim.x) {
+      const long long c = K[k * ld_k + i];
+      a += c * c;
+      n += c;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ra[threadIdx.x >> 5] = a;
+    rn[threadIdx.x >> 5] = n;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long A = 0, Nk = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      A += ra[w];
+      Nk += rn[w];
+    }
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (A > 0) {
+      const double c = inv2s2 / (double)A;
+      const float ch = (float)c;
+      g = make_float4(ch, (float)(c - (double)ch), (float)(1.0 / (inv2s2 * (double)A)), 0.f);
+    }
+    gk[k] = g;
+    if (Nk > 0) atomicMax(nmax, (unsigned long long)Nk);
+  }
+}
+
+cudaError_t launch_gauss_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                                int64_t ld_data, double sigma, float4* gk,
+                                unsigned long long* nmax, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(nmax, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  gauss_frames_kernel<<<(unsigned)ld_data, 256, 0, s>>>(K, ld_k, n_data, n_pix,
+                                                        1.0 / (2.0 * sigma * sigma), gk, nmax);
+  return cudaGetLastError();
+}
+
+// Largest grid value (for the Gaussian scales). Non-negative floats order
+// like their bit patterns, so an integer atomic maximum suffices; a
+// non-finite voxel counts as +inf.
+__global__ void grid_max_kernel(const float* __restrict__ grid, int64_t n, unsigned* out) {
+  unsigned m = 0u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = grid[i];
+    const unsigned b = isfinite(v) ? __float_as_uint(fmaxf(v, 0.f)) : 0x7f800000u;
+    m = b > m ? b : m;
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void gauss_scales_kernel(const unsigned* gmax, const unsigned long long* nmax,
+                                    float4* gsc, int32_t* status) {
+  const float w = __uint_as_float(*gmax);
+  if (!isfinite(w)) set_status(status, EMC_ERR_NUMERIC);
+  *gsc = gauss_scales(w, (long long)*nmax);
+}
+
+// scratch: 16 bytes for the maximum, then the float4 scales at gsc
+cudaError_t launch_gauss_scales(const float* grid, int64_t n_vox, unsigned* gmax,
+                                const unsigned long long* nmax, float4* gsc, int32_t* status,
+                                cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(gmax, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (n_vox + 255) / 256;
+  blocks = blocks < 1024 ? blocks : 1024;
+  grid_max_kernel<<<(unsigned)blocks, 256, 0, s>>>(grid, n_vox, gmax);
+  gauss_scales_kernel<<<1, 1, 0, s>>>(gmax, nmax, gsc, status);
+  return cudaGetLastError();
+}
+
 // Per frame k: fold the per-tile pairs (m_t, s_t) -- each meaning
 // sum over the tile's rotations of exp(S_jk) = s_t exp(m_t) -- into the running
 // (m_k, s_k) in FP64 (Eq. 2.4's denominator; only maxima and sums travel, as
@@ -57,7 +148,7 @@ cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, i
 __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float* __restrict__ part_s,
                                  int64_t n_tiles, int64_t ld_data, int64_t n_data,
                                  double* __restrict__ lse_m, double* __restrict__ lse_s,
-                                 int accumulate, int32_t* status) {
+                                 int accumulate, double clamp, int32_t* status) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_data) return;
   double M = accumulate ? lse_m[k] : -INFINITY;
@@ -79,17 +170,20 @@ __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float*
     float sv = part_s[t * ld_data + k];
     if (sv > 0.f) acc += (double)(sv * __expf((float)(m - Mn)));
   }
-  if (!isfinite(Mn) || !(acc > 0.0) || !isfinite(acc)) set_status(status, EMC_ERR_NUMERIC);
+  // a best score at the clamp (Gaussian model) means every rotation was clamped
+  if (!isfinite(Mn) || !(acc > 0.0) || !isfinite(acc) || Mn <= clamp)
+    set_status(status, EMC_ERR_NUMERIC);
   lse_m[k] = Mn;
   lse_s[k] = acc;
 }
 
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
-                             int accumulate, int32_t* status, cudaStream_t s) {
+                             int accumulate, int gauss, int32_t* status, cudaStream_t s) {
   unsigned blocks = (unsigned)((n_data + 255) / 256);
   lse_merge_kernel<<<blocks, 256, 0, s>>>(part_m, part_s, n_tiles, ld_data, n_data, lse_m, lse_s,
-                                          accumulate, status);
+                                          accumulate, gauss ? -(double)kGaussClamp : -INFINITY,
+                                          status);
   return cudaGetLastError();
 }
 
@@ -222,6 +316,88 @@ cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sr
   else
     normalize_scores_kernel<2><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
                                                     P_plane);
+  return cudaGetLastError();
+}
+
+// Gaussian model, pass 2 from stored scores: P_jk = exp(S_jk - lse_k) as in
+// normalize_scores_kernel, then the M-step operand of Eq. 2.5 with the
+// fluence of Eq. 2.6, P_jk / phi_jk, where
+//   1/phi_jk = G_jk / A_k = sqrt((S_jk - bias_j) 2 sigma^2 / A_k)
+// and S_jk - bias_j = G_jk^2 / (2 sigma^2 A_k) >= 0 is formed as
+// d + (r - hi(bias_j)) - lo(bias_j) (r and hi(bias) on the 1/64 grid, so the
+// large parts cancel exactly). Written as BF16 hi + lo of P / phi (relative
+// precision 2^-17 over the whole FP32 range, which a single FP16 scale cannot
+// give rows of small responsibility); den_j = sum_k P_jk is added to den with
+// one FP32 atomic per row and 64 frames (den zeroed by the caller).
+__global__ void __launch_bounds__(256)
+    normalize_scores_gauss_kernel(const float* __restrict__ S, int64_t ldS,
+                                  const float* __restrict__ Sref, const float2* __restrict__ lse2,
+                                  const double* __restrict__ bias, const float4* __restrict__ gk,
+                                  int64_t nrot, int64_t ld_data,
+                                  int64_t n_data, uint16_t* __restrict__ P, int64_t P_plane,
+                                  float* __restrict__ den) {
+  __shared__ float tile[64][33];
+  const int64_t j0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < 8; r++) {
+    const int kk = ty + 8 * r;
+    tile[kk][tx] = S[(k0 + kk) * ldS + j0 + tx];
+  }
+  __syncthreads();
+  const int jj = threadIdx.x >> 3, kb = (threadIdx.x & 7) * 8;
+  const int64_t j = j0 + jj, k = k0 + kb;
+  const bool row_ok = j < nrot;
+  float bh = 0.f, bl = 0.f;
+  if (row_ok) {
+    const double b = bias[j];
+    const double h = rint(b * kGridD) / kGridD;
+    bh = (float)h;
+    bl = (float)(b - h);
+  }
+  const float4* rs = reinterpret_cast<const float4*>(Sref + (j >> 5) * ld_data + k);
+  const float4 r0 = rs[0], r1 = rs[1];
+  const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+  float p[8], dsum = 0.f;
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
+    const float2 L = lse2[k + u];
+    const float d = tile[kb + u][jj];
+    const bool ok = row_ok && k + u < n_data;
+    const float pr = ok ? __expf(d + ((rv[u] - L.x) - L.y)) : 0.f;
+    dsum += pr;
+    const float q = fmaxf(d + ((rv[u] - bh) - bl), 0.f);
+    p[u] = ok ? pr * sqrtf(q * gk[k + u].z) : 0.f;
+  }
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int u = 0; u < 8; u += 2) {
+    const uint16_t h0 = bf16_bits(p[u]), h1 = bf16_bits(p[u + 1]);
+    const uint16_t l0 = bf16_bits(p[u] - bf16_val(h0)), l1 = bf16_bits(p[u + 1] - bf16_val(h1));
+    h[u / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+    l[u / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+  }
+  uint16_t* ph = P + j * ld_data + k;
+  *reinterpret_cast<uint4*>(ph) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(ph + P_plane) = make_uint4(l[0], l[1], l[2], l[3]);
+  // the 8 threads of one row are consecutive lanes
+  dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
+  dsum += __shfl_xor_sync(0xffffffffu, dsum, 2);
+  dsum += __shfl_xor_sync(0xffffffffu, dsum, 4);
+  if ((threadIdx.x & 7) == 0 && row_ok && dsum > 0.f) atomicAdd(den + j, dsum);
+}
+
+cudaError_t launch_normalize_scores_gauss(const float* S, int64_t ldS, const float* Sref,
+                                          const float2* lse2, const double* bias,
+                                          const float4* gk, int64_t rows,
+                                          int64_t nrot, int64_t ld_data, int64_t n_data,
+                                          uint16_t* P, int64_t P_plane, float* den,
+                                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(den, 0, sizeof(float) * rows, s);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(ld_data / 64), (unsigned)(rows / 32));
+  normalize_scores_gauss_kernel<<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, bias, gk, nrot,
+                                                     ld_data, n_data, P, P_plane, den);
   return cudaGetLastError();
 }
 

@@ -65,6 +65,7 @@ extern "C" int emc_loglik_static(const emc_config* cfg, const void* L, const dou
   if (!cfg || !L || !bias || !frames || !lse_m || !lse_s) return EMC_ERR_ARG;
   if (cfg->n_pix < 1 || cfg->n_data < 1 || nrot < 1 || nrot > cfg->n_rot) return EMC_ERR_ARG;
   if (cfg->precision < EMC_PREC_FP32 || cfg->precision > EMC_PREC_FP16_SPLIT) return EMC_ERR_ARG;
+  if (cfg->model != EMC_MODEL_POISSON) return EMC_ERR_UNSUPPORTED;
   const int64_t ld_pix = up(cfg->n_pix + 1, 64);
   const int64_t ld_data = up(cfg->n_data, 256);
   const int64_t rows = up(nrot, 128);
@@ -92,12 +93,12 @@ extern "C" int emc_loglik_static(const emc_config* cfg, const void* L, const dou
     } else {
       Planes p{const_cast<char*>(Lb), rows * ld_pix, ld_pix};
       e = launch_tc_pass1(p, cfg->precision, bias + r0, nb, frames, ld_data, cfg->n_data, ld_pix, part_m,
-                          part_s, nullptr, nullptr, device_status, s);
+                          part_s, nullptr, nullptr, nullptr, nullptr, device_status, s);
       tiles = tc_pass1_tiles(nb);
     }
     if (e != cudaSuccess) return EMC_ERR_CUDA;
     e = launch_lse_merge(part_m, part_s, tiles, ld_data, cfg->n_data, lse_m, lse_s,
-                         (accumulate || r0 > 0) ? 1 : 0, device_status, s);
+                         (accumulate || r0 > 0) ? 1 : 0, 0, device_status, s);
     if (e != cudaSuccess) return EMC_ERR_CUDA;
   }
   return EMC_OK;

@@ -27,6 +27,13 @@
 // multiples of 1/8 into the exact part and only then subtracts the reference
 // (running max in pass 1, lse_k in pass 2), so the exponent is accurate to a
 // few FP32 ulps of a number of order one.
+//
+// Gaussian model (pass 1 with three FP16 planes): the accumulators hold
+// s G_jk = gh + gl, gh integral and exact (every partial sum below 2^24), and
+// the epilogue forms S_jk = c'_k (gh + gl)^2 + bias_j, c'_k = 1/(2 sigma^2 A_k s^2),
+// in double-float: gh^2 as an exact two-product, c' gh^2 with its FMA
+// remainder, the 1/64-grid part of the product added to that of the bias
+// exactly and every remainder gathered in the small part.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -48,7 +55,7 @@ constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a tile takes tens of microseconds
 constexpr int kSmemBudget = 220 * 1024;
-constexpr int kScratchBytes = 8 * 1024;
+constexpr int kScratchBytes = 10 * 1024;
 constexpr float kSentinel = -3.0e38f;
 
 // K-block width: 64 elements with 128-byte swizzle, or 32 with 64-byte swizzle
@@ -88,6 +95,8 @@ struct TcArgs {
   float* part_s;
   float* S;                // pass 1, optional: shifted scores, frame-major [ld_data][rows]
   float* Sref;             // pass 1, optional: 32-row group maxima [rows / 32][ld_data]
+  const float4* gk;        // Gaussian pass 1: per frame (c_k hi, c_k lo, 2 sigma^2 / A_k, 0)
+  const float4* gsc;       // Gaussian pass 1: scales (s, 1/s^2, 0, 0)
   uint16_t* P;             // normalize: planes [2][rows][ld_data]
   int64_t P_plane;
   float* Num;              // update: [rows][ld_pix]
@@ -132,6 +141,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const TcArgs a) {
   using C = TcCfg<MODE, NA, F16>;
+  constexpr bool GAUSS = (MODE == MODE_PASS1 && NA == 3 && F16);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
@@ -282,10 +292,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const double b = a.bias[row];
         valid = valid && b > -INFINITY;
         if (valid) {
-          const double h = rint(b * kGridD) / kGridD;
-          bh = (float)h;
-          bl = (float)(b - h);
+          bh = (float)(rint(b * kGridD) / kGridD);  // on the 1/64 grid (coarser beyond 2^18)
+          bl = (float)(b - (double)bh);
         }
+      }
+      float2* cs = scratch + 4 * BN;  // Gaussian: c'_k of the tile's frames
+      if (GAUSS) {
+        const float4 g = a.gk[(int64_t)nt * BN + et];
+        const float is2 = a.gsc->y;
+        cs[et] = make_float2(g.x * is2, g.y * is2);
+        named_bar(1, kEpiThreads);
       }
       if (MODE == MODE_NORMALIZE) {
         scratch[et] = a.lse2[(int64_t)nt * BN + et];
@@ -321,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < 32; i += 4)
               *reinterpret_cast<uint4*>(dst + i) = make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
-            if (a.n_pix >= n0 && a.n_pix < n0 + 32) {
+            if (a.den && a.n_pix >= n0 && a.n_pix < n0 + 32) {
 #pragma unroll
               for (int i = 0; i < 32; i++)
                 if (n0 + i == a.n_pix) a.den[row] = __uint_as_float(v0[i]);
@@ -333,12 +349,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         float xh[32], xl[32];
 #pragma unroll
         for (int i = 0; i < 32; i++) {
-          float h = __uint_as_float(v0[i]) + bh;
-          float l = (C::NACC == 2 ? __uint_as_float(v1[i]) : 0.f) + bl;
+          float h, l;
+          if (GAUSS) {
+            const float gh = __uint_as_float(v0[i]), gl = __uint_as_float(v1[i]);
+            const float2 c = cs[col0 + i];
+            const float t = gh * gh;
+            const float r = fmaf(gh, gh, -t) + gl * (2.f * gh + gl);  // (gh + gl)^2 - t
+            const float x = c.x * t;
+            const float rest = fmaf(c.x, t, -x) + fmaf(c.x, r, c.y * t);
+            const float xg = rintf(x * kGrid) * (1.0f / kGrid);
+            h = xg + bh;  // exact wherever |h| < 2^18
+            l = ((x - xg) + rest) + bl;
+          } else {
+            h = __uint_as_float(v0[i]) + bh;
+            l = (C::NACC == 2 ? __uint_as_float(v1[i]) : 0.f) + bl;
+          }
           const float rr = rintf(l * kGrid) * (1.0f / kGrid);
           h += rr;
           l -= rr;
-          big |= fabsf(h) > 131072.f;
+          if (GAUSS) {
+            if (h < -kGaussClamp) {
+              h = -kGaussClamp;
+              l = 0.f;
+            }
+            big |= !(h <= 131072.f);  // also NaN
+          } else {
+            big |= fabsf(h) > 131072.f;
+          }
           xh[i] = valid ? h : kSentinel;
           xl[i] = valid ? l : 0.f;
         }
@@ -496,10 +533,8 @@ int score_planes(int precision) {
   return precision == EMC_PREC_BF16_SPLIT ? 3 : (precision == EMC_PREC_FP16_SPLIT ? 2 : 1);
 }
 
-bool maps_scores(const Planes& L, int precision, int64_t rows, const uint16_t* Kb, int64_t ld_data,
-                 int64_t ld_pix, CUtensorMap* mA, CUtensorMap* mB) {
-  const int nterms = score_planes(precision);
-  const bool f16 = precision == EMC_PREC_FP16_SPLIT;
+bool maps_scores(const Planes& L, int nterms, bool f16, int64_t rows, const uint16_t* Kb,
+                 int64_t ld_data, int64_t ld_pix, CUtensorMap* mA, CUtensorMap* mB) {
   const uint32_t bk = nterms >= 2 ? 32 : 64;  // TcCfg<scores, NA, F16>::BK
   const int sw = nterms >= 2 ? 64 : 128;
   const uint64_t dA[3] = {(uint64_t)ld_pix, (uint64_t)rows, (uint64_t)nterms};
@@ -528,11 +563,14 @@ int64_t tc_pass1_tiles(int64_t rows) { return rows / BM; }
 cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
-                            int32_t* status, cudaStream_t s) {
+                            const float4* gk, const float4* gsc, int32_t* status,
+                            cudaStream_t s) {
+  const bool gauss = gk != nullptr;
+  const int nterms = gauss ? 3 : score_planes(precision);
+  const bool f16 = gauss || precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
-  if (!maps_scores(L, precision, rows, Kb, ld_data, ld_pix, &mA, &mB))
+  if (!maps_scores(L, nterms, f16, rows, Kb, ld_data, ld_pix, &mA, &mB))
     return cudaErrorInvalidValue;
-  const int nterms = score_planes(precision);
   TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / (nterms >= 2 ? 32 : 64)));
   a.nrot = rows;  // validity comes from the bias (-inf on padding rows)
   a.n_data = n_data;
@@ -543,7 +581,10 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
   a.part_s = part_s;
   a.S = S;
   a.Sref = Sref;
+  a.gk = gk;
+  a.gsc = gsc;
   a.status = status;
+  if (gauss) return launch<MODE_PASS1, 3, true>(mA, mB, a, s);
   if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_PASS1, 2, true>(mA, mB, a, s);
   return nterms == 3 ? launch<MODE_PASS1, 3, false>(mA, mB, a, s)
                      : launch<MODE_PASS1, 1, false>(mA, mB, a, s);
@@ -555,10 +596,11 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
                                 float2* lse2, Planes P, int32_t* status, cudaStream_t s) {
   cudaError_t e = launch_lse_split(lse_m, lse_s, n_data, ld_data, lse2, s);
   if (e != cudaSuccess) return e;
-  CUtensorMap mA, mB;
-  if (!maps_scores(L, precision, rows, Kb, ld_data, ld_pix, &mA, &mB))
-    return cudaErrorInvalidValue;
   const int nterms = score_planes(precision);
+  CUtensorMap mA, mB;
+  if (!maps_scores(L, nterms, precision == EMC_PREC_FP16_SPLIT, rows, Kb, ld_data, ld_pix, &mA,
+                   &mB))
+    return cudaErrorInvalidValue;
   TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / (nterms >= 2 ? 32 : 64)));
   a.nrot = nrot;
   a.n_data = n_data;

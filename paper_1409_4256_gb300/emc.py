@@ -21,6 +21,8 @@ PRECISIONS = {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16_split": PREC_BF16_SPLI
               "fp16_split": PREC_FP16_SPLIT}
 COMPRESS_DEFERRED, COMPRESS_IDW = 0, 1
 FLAG_STORE_SCORES = 1
+MODEL_POISSON, MODEL_GAUSSIAN = 0, 1
+MODELS = {"poisson": MODEL_POISSON, "gaussian": MODEL_GAUSSIAN}
 
 _lock = threading.Lock()
 _lib = None
@@ -36,7 +38,7 @@ class Config(ctypes.Structure):
                 ("n_data", ctypes.c_int64), ("w_floor", ctypes.c_double),
                 ("compress_mode", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("rot_chunk", ctypes.c_int64), ("n_cand", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("model", ctypes.c_int32), ("sigma", ctypes.c_double)]
 
 
 class BufferSizes(ctypes.Structure):
@@ -189,11 +191,15 @@ class Context:
     """An emc_ctx plus its caller-owned workspace (a torch uint8 tensor)."""
 
     def __init__(self, N: int, q: np.ndarray, quat: np.ndarray, weight: np.ndarray, n_data: int,
-                 precision="bf16_split", w_floor: float = 1e-10, compress_mode: int = 0,
+                 precision=None, w_floor: float = 1e-10, compress_mode: int = 0,
                  rot_chunk: int = 0, store_scores: bool = False, n_cand: int = 0,
-                 device: str = "cuda", stream=None):
+                 device: str = "cuda", stream=None, model: str = "poisson", sigma: float = 1.0):
         import torch
         self.torch = torch
+        gauss = MODELS[model] == MODEL_GAUSSIAN
+        if precision is None:
+            precision = "fp16_split" if gauss else "bf16_split"
+        store_scores = store_scores or gauss  # the Gaussian pass 2 reads the stored scores
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         q = np.ascontiguousarray(q, dtype=np.float64)
@@ -202,7 +208,7 @@ class Context:
         self.cfg = Config(N=N, precision=precision, n_pix=q.shape[0], n_rot=quat.shape[0],
                           n_data=n_data, w_floor=w_floor, compress_mode=compress_mode,
                           flags=FLAG_STORE_SCORES if store_scores else 0, rot_chunk=rot_chunk,
-                          n_cand=n_cand, reserved=0)
+                          n_cand=n_cand, model=MODELS[model], sigma=float(sigma))
         L = lib()
         nb = ctypes.c_size_t()
         _check(L.emc_workspace_size(ctypes.byref(self.cfg), ctypes.byref(nb)), "emc_workspace_size")

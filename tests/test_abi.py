@@ -71,3 +71,21 @@ def test_status_strings_and_config_checks(libemc):
     assert b.ld_pix == 128 and b.ld_data == 256 and b.rows == 128
     assert b.logw_bytes == 3 * 2 * 128 * 128
     assert libemc.emc_buffer_sizes_for(ctypes.byref(cfg), 51, ctypes.byref(b)) == -1
+
+
+def test_gaussian_config_checks(libemc):
+    # the Gaussian model needs the FP16 split, stored scores, sigma > 0 and no
+    # candidate sets; the checks run before anything touches a device
+    from paper_1409_4256_gb300 import emc
+    nb = ctypes.c_size_t()
+
+    def ws(**kw):
+        base = dict(N=32, precision=3, n_pix=100, n_rot=50, n_data=10, w_floor=1e-10,
+                    compress_mode=0, flags=1, rot_chunk=0, n_cand=0, model=1, sigma=1.0)
+        base.update(kw)
+        return libemc.emc_workspace_size(ctypes.byref(emc.Config(**base)), ctypes.byref(nb))
+
+    assert ws() == 0
+    assert ws(precision=2) == -4 and ws(flags=0) == -4 and ws(n_cand=8) == -4
+    assert ws(sigma=0.0) == -1 and ws(sigma=float("nan")) == -1 and ws(model=2) == -1
+    assert ws(model=0, sigma=0.0) == 0  # sigma is not read for the Poisson model
