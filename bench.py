@@ -44,6 +44,7 @@ WORKLOAD_TEXT = {
 DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3", "fp16_split": "f16x2"}
 LEARNED_FORMS = ("learned",)
 ADAPTIVE_FORMS = ("adaptive",)
+GAUSS_FORMS = ("gaussian",)
 
 
 def parse_args():
@@ -56,13 +57,15 @@ def parse_args():
     ap.add_argument("--workload", default="emc64", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
     ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
-    ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned,adaptive",
+    ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned,adaptive,gaussian",
                     help="other forms to time briefly (comma list, or 'none')")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-iters", type=int, default=30,
                     help="iterations of the learned-vs-dense model comparison (0 to skip)")
     ap.add_argument("--adaptive-iters", type=int, default=12,
                     help="iterations of the adaptive-sampling schedule")
+    ap.add_argument("--sigma", type=float, default=1.0,
+                    help="sigma of the Gaussian noise model form (photon units)")
     ap.add_argument("--n-cand", type=int, default=512, help="candidate rotations per frame")
     ap.add_argument("--recompute", action="store_true",
                     help="two-pass streamed E-step (pass 2 recomputes the scores) instead of "
@@ -248,16 +251,26 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
 
 def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, world):
     """Learned proposal + sparse Maximize with a dense fallback every 5th
-    iteration (the dense one also measures the missed responsibility mass).
-    Untimed set-up: 2 dense iterations from the start model give the soft
-    targets, the MLP trains on 90% of the frames, candidates = its top-M."""
+    iteration. Untimed set-up: 2 dense iterations from the start model give the
+    soft targets (top 32 per frame), the MLP trains on 90% of the frames. Each
+    frame's candidate set is the top R = 32 rotations of the last dense E-step
+    followed by the network's best rotations not among them (M in all); every
+    dense fallback refreshes the dense part. Reported separately: the mass the
+    network's own top M captures on held-out and training frames."""
     from paper_1409_4256_gb300 import learned
     n_rot, n_data = quat.shape[0], ds.K.shape[0]
     M = min(args.n_cand, n_rot)
+    R = min(32, M)
     floor = 1e-10 * float(ds.model_start.mean())
     ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split", w_floor=floor,
                       store_scores=True, n_cand=M, device=str(grid.device), stream=stream)
     ctx.set_frames(K_dev, stream=stream)
+
+    def refresh(net):
+        # candidates = top R of the last dense E-step + the network's best others
+        ti, _ = ctx.targets_from_scores(R, stream=stream)
+        ctx.set_candidates(emc.merge_candidates(ti, net, M, stream=stream), stream=stream)
+
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
         g1, _ = ctx.iteration(grid, stream=stream)
@@ -267,13 +280,16 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
         train, test = learned.split_rows(n_data)
         prop = learned.Proposal(n_rot, device=str(grid.device))
         hist = prop.train(feat, tidx, tprob, train, epochs=8, batch=512, lr=1e-3, stream=stream)
-        cand = prop.propose(feat, M, n_data, stream=stream)
-        ctx.set_candidates(cand, stream=stream)
-        ctx.iteration(g2, stream=stream)  # dense E-step on the current model for the recall
+        net = prop.propose(feat, M, n_data, stream=stream)
+        # recall at the current model: the network's own sets, then the merged ones
+        ctx.set_candidates(net, stream=stream)
+        ctx.iteration(g2, stream=stream)  # dense E-step on the current model
+        mm_net = ctx.missed_mass(stream=stream).cpu().numpy()
+        refresh(net)
         mm = ctx.missed_mass(stream=stream).cpu().numpy()
         stream.synchronize()
         setup_s = time.perf_counter() - t0
-        # timed: cycles of 4 sparse iterations and 1 dense fallback
+        # timed: cycles of 4 sparse iterations, 1 dense fallback and the refresh
         out = torch.empty_like(grid)
         for _ in range(2):
             ctx.sparse_iteration(g2, out, stats=False, stream=stream)
@@ -287,6 +303,7 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
             for _ in range(4):
                 ctx.sparse_iteration(g2, out, stats=False, stream=stream)
             ctx.iteration(g2, out, stats=False, stream=stream)
+            refresh(net)
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / (5 * cycles)
@@ -299,10 +316,15 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
     res = {"value": world * n_rot * n_data / (ms * 1e-3), "ms_per_step": ms,
            "ms_sparse_iteration": ms_sparse,
            "evaluated_pairs_per_s": world * M * n_data / (ms_sparse * 1e-3),
-           "candidates": M, "schedule": "4 sparse + 1 dense per 5 iterations",
+           "candidates": M, "dense_top_kept": R,
+           "schedule": "4 sparse + 1 dense per 5 iterations; candidates = dense top 32 + "
+                       "network's best others, refreshed at every dense step",
            "train_loss_first_last": [hist[0], hist[-1]],
-           "heldout_captured_mass": float(1.0 - mm[test].mean()),
-           "train_captured_mass": float(1.0 - mm[train].mean()), "setup_s": setup_s}
+           "network_heldout_captured_mass": float(1.0 - mm_net[test].mean()),
+           "network_train_captured_mass": float(1.0 - mm_net[train].mean()),
+           "random_sets_captured_mass_expected": M / n_rot,
+           "merged_heldout_captured_mass": float(1.0 - mm[test].mean()),
+           "merged_train_captured_mass": float(1.0 - mm[train].mean()), "setup_s": setup_s}
     if args.learned_iters > 0:
         # model after N iterations, learned schedule vs dense, same start
         dense_ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split",
@@ -314,12 +336,15 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
             for _ in range(args.learned_iters):
                 dense_ctx.iteration(a, b, stats=False, stream=stream)
                 a, b = b, a
+            ctx.iteration(g2, stream=stream)  # the schedule starts from a dense E-step's sets
+            refresh(net)
             c, d = g2.clone(), torch.empty_like(g2)
             missed = []
             for it in range(args.learned_iters):
                 if it % 5 == 4:
                     ctx.iteration(c, d, stats=False, stream=stream)
                     missed.append(float(ctx.missed_mass(stream=stream).mean().item()))
+                    refresh(net)
                 else:
                     ctx.sparse_iteration(c, d, stats=False, stream=stream)
                 c, d = d, c
@@ -402,9 +427,9 @@ def run_ours(args):
     K_dev = torch.as_tensor(ds.K, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
-    def make_ctx(prec):
+    def make_ctx(prec, **kw):
         c = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision=prec, w_floor=floor,
-                        store_scores=not args.recompute, device=str(dev), stream=stream)
+                        store_scores=not args.recompute, device=str(dev), stream=stream, **kw)
         c.set_frames(K_dev, stream=stream)
         return c
 
@@ -476,10 +501,14 @@ def run_ours(args):
                 forms[f] = {"error": str(e)[:300]}
             continue
         try:
-            c2 = make_ctx(f)
+            gauss = f in GAUSS_FORMS
+            c2 = (make_ctx(None, model="gaussian", sigma=args.sigma) if gauss else make_ctx(f))
             fms, fph, _, fll = time_form(torch, emc, c2, grid, 2, 1, stream, dist)
             forms[f] = {"value": world * pairs / (fms * 1e-3), "ms_per_step": fms, "loglik": fll,
                         "ms_loglik": fph["ms_loglik"]}
+            if gauss:
+                forms[f].update({"model": "Gaussian, per-(j,k) fluence (Eqs. 2.2-2.6)",
+                                 "sigma": args.sigma, "phases_ms": fph})
             del c2
         except Exception as e:  # a form that is not built yet is reported, not hidden
             forms[f] = {"error": str(e)[:200]}

@@ -348,6 +348,16 @@ int emc_topm(const float* logits, int64_t batch, int64_t n, int64_t ld, int M, i
 int emc_targets_from_scores(emc_ctx* ctx, const void* scores, int R, int32_t* tidx, float* tprob,
                             emc_stream stream);
 
+/* Candidate sets from two ranked lists (no counterpart in the paper: the
+ * learned proposal's schedule). For each of n frames: the R rotations of
+ * first (device int32[n][R], distinct, e.g. tidx of emc_targets_from_scores
+ * after a dense iteration), then the entries of rest (device int32[n][M_rest],
+ * e.g. emc_topm of the network's logits) that are not among them, in their
+ * order, until M are written to out (device int32[n][M]). Needs
+ * 0 <= R <= 64 and M_rest >= M (so that M distinct entries exist). */
+int emc_merge_candidates(const int32_t* first, int R, const int32_t* rest, int M_rest, int64_t n,
+                         int M, int32_t* out, emc_stream stream);
+
 /* Load candidate sets cand (device int32[n_data][n_cand], rotation indices)
  * and build the per-rotation pair lists the sparse calls use. An index outside
  * [0, n_rot) sets EMC_ERR_ARG in the device status. */

@@ -148,6 +148,25 @@ def topm(logits: np.ndarray, M: int) -> np.ndarray:
     return np.sort(order, axis=1)
 
 
+def merge_candidates(first: np.ndarray, rest: np.ndarray, M: int) -> np.ndarray:
+    """Candidate sets from two ranked lists per frame: every entry of `first`
+    (the dense E-step's top R, distinct), then the entries of `rest` (the
+    network's top list) not already taken, in order, until M: [B, M]."""
+    out = np.empty((first.shape[0], M), dtype=np.int64)
+    for k in range(first.shape[0]):
+        row = list(first[k][:M])
+        seen = set(row)
+        for c in rest[k]:
+            if len(row) == M:
+                break
+            if c not in seen:
+                row.append(c)
+                seen.add(c)
+        assert len(row) == M, "rest too short"
+        out[k] = row
+    return out
+
+
 def sparse_estep(S: np.ndarray, cand: np.ndarray):
     """Eq. 2.4 over candidate sets. S: dense scores [n_rot, n_data];
     cand [n_data, M]. Returns (P_c [n_data, M], lse_c [n_data])."""

@@ -701,6 +701,14 @@ int emc_targets_from_scores(emc_ctx* ctx, const void* scores, int R, int32_t* ti
   return EMC_OK;
 }
 
+int emc_merge_candidates(const int32_t* first, int R, const int32_t* rest, int M_rest, int64_t n,
+                         int M, int32_t* out, emc_stream stream) {
+  if (!rest || !out || n < 0 || M < 1 || R < 0 || R > kMaxTargets || M_rest < M) return EMC_ERR_ARG;
+  if (R > 0 && !first) return EMC_ERR_ARG;
+  CU(launch_merge_candidates(first, R, rest, M_rest, n, M, out, (cudaStream_t)stream));
+  return EMC_OK;
+}
+
 int emc_set_candidates(emc_ctx* ctx, const int32_t* cand, emc_stream stream) {
   if (!ctx || !cand || ctx->cfg.n_cand < 1) return EMC_ERR_ARG;
   const Layout& y = ctx->lay;

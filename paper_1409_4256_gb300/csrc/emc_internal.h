@@ -143,6 +143,8 @@ cudaError_t launch_topm(const float* logits, int64_t B, int64_t n, int64_t ld, i
 cudaError_t launch_topr_columns(const float* S, int64_t ldS, const float* Sref, int64_t ld, int64_t nrot,
                                 int64_t n_data, int R, int32_t* tidx, float* tprob,
                                 cudaStream_t s);
+cudaError_t launch_merge_candidates(const int32_t* first, int R, const int32_t* rest, int M_rest,
+                                    int64_t n, int M, int32_t* out, cudaStream_t s);
 cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t n_rot,
                              int64_t rows, int32_t* cnt, int64_t* off, int2* ent,
                              int32_t* status, cudaStream_t s);

@@ -203,6 +203,47 @@ __global__ void csr_fill_kernel(const int32_t* __restrict__ cand, int64_t n_pair
   ent[pos] = make_int2((int)(e / M), (int)(e % M));
 }
 
+// Candidate sets from two ranked lists per frame: the R entries of `first`
+// (distinct; the dense E-step's top R), then the entries of `rest` (the
+// network's top list) that are not among them, in order, until M are written.
+// With M_rest >= M at most R entries of rest repeat first, so M are always
+// found. One warp per frame; membership by broadcasting first's entries.
+__global__ void merge_candidates_kernel(const int32_t* __restrict__ first, int R,
+                                        const int32_t* __restrict__ rest, int M_rest,
+                                        int64_t n, int M, int32_t* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= n) return;
+  const int32_t* f = first + k * R;
+  const int32_t* r = rest + k * M_rest;
+  int32_t* o = out + k * M;
+  const int32_t f0 = lane < R ? f[lane] : -1;
+  const int32_t f1 = lane + 32 < R ? f[lane + 32] : -1;
+  const int nf = R < M ? R : M;
+  for (int t = lane; t < nf; t += 32) o[t] = f[t];
+  int filled = nf;
+  for (int base = 0; base < M_rest && filled < M; base += 32) {
+    const int32_t c = base + lane < M_rest ? r[base + lane] : -1;
+    bool dup = c < 0;
+    for (int t = 0; t < R; t++) {
+      const int32_t v = __shfl_sync(0xffffffffu, t < 32 ? f0 : f1, t & 31);
+      dup |= v == c;
+    }
+    const unsigned keep = __ballot_sync(0xffffffffu, !dup);
+    const int pos = filled + __popc(keep & ((1u << lane) - 1u));
+    if (!dup && pos < M) o[pos] = c;
+    filled += __popc(keep);
+  }
+}
+
+cudaError_t launch_merge_candidates(const int32_t* first, int R, const int32_t* rest, int M_rest,
+                                    int64_t n, int M, int32_t* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  merge_candidates_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(first, R, rest, M_rest, n, M,
+                                                                  out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t n_rot,
                              int64_t rows, int32_t* cnt, int64_t* off, int2* ent,
                              int32_t* status, cudaStream_t s) {

@@ -87,6 +87,7 @@ _SIGS = {
     "emc_mlp_forward": (_i32, [_i64, _vp, _vp, _i64, _vp, _vp, _vp]),
     "emc_mlp_train_step": (_i32, [_i64, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp, _vp,
                                   _i64, _i32, _vp, _vp, _vp]),
+    "emc_merge_candidates": (_i32, [_vp, _i32, _vp, _i32, _i64, _i32, _vp, _vp]),
     "emc_topm": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "emc_targets_from_scores": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
     "emc_set_candidates": (_i32, [_vp, _vp, _vp]),
@@ -174,6 +175,18 @@ def mlp_train_step(n_out: int, params, grads, m, v, step: int, lr: float, X, tid
 
 def topm(logits, batch: int, n: int, ld: int, M: int, cand, stream=None) -> None:
     _check(lib().emc_topm(_ptr(logits), batch, n, ld, M, _ptr(cand), _stream(stream)), "emc_topm")
+
+
+def merge_candidates(first, rest, M: int, out=None, stream=None):
+    """first int32 [n, R] (or None), rest int32 [n, M_rest >= M] -> int32 [n, M]."""
+    import torch
+    n = rest.shape[0]
+    if out is None:
+        out = torch.empty((n, M), dtype=torch.int32, device=rest.device)
+    R = 0 if first is None else first.shape[1]
+    _check(lib().emc_merge_candidates(_ptr(first), R, _ptr(rest), rest.shape[1], n, M, _ptr(out),
+                                      _stream(stream)), "emc_merge_candidates")
+    return out
 
 
 def _ptr(t) -> int:

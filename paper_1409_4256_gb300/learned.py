@@ -83,9 +83,14 @@ class Proposal:
             emc.mlp_forward(self.n_out, self.params, feat[s:s + b], b, work, out[s:s + b], stream)
         return out
 
-    def propose(self, feat, M: int, n_frames: int, batch: int = 2048, stream=None):
-        """Top-M rotations per frame: int32 [n_frames, M]."""
+    def propose(self, feat, M: int, n_frames: int, batch: int = 2048, first=None, stream=None):
+        """Top-M rotations per frame: int32 [n_frames, M]. With `first`
+        (int32 [n_frames, R], e.g. the top R of the last dense E-step), each set
+        is those R followed by the network's best rotations not among them."""
         torch = self.torch
+        if first is not None:
+            net = self.propose(feat, M, n_frames, batch, stream=stream)
+            return emc.merge_candidates(first, net, M, stream=stream)
         cand = torch.empty((n_frames, M), dtype=torch.int32, device=self.device)
         work = torch.empty(emc.mlp_work_size(self.n_out, batch), dtype=torch.uint8,
                            device=self.device)

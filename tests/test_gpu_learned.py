@@ -147,6 +147,25 @@ def test_topm_matches_sorting(torch_cuda):
     assert np.array_equal(got, ref)
 
 
+def test_merge_candidates_matches_oracle(torch_cuda):
+    # integer work: bit-exact, including the order of the merged entries
+    from oracle import learned as ol
+    from paper_1409_4256_gb300 import emc
+    torch = torch_cuda
+    rng = np.random.default_rng(9)
+    n, n_rot = 300, 4000
+    for R, M_rest, M in ((32, 512, 512), (64, 100, 100), (5, 40, 33), (0, 64, 64)):
+        first = np.stack([rng.permutation(n_rot)[:R] for _ in range(n)]).astype(np.int32)
+        # rest overlaps first heavily: its head repeats part of first
+        rest = np.stack([np.concatenate([f[:R // 2], np.setdiff1d(rng.permutation(n_rot), f)
+                                         [:M_rest - R // 2]]) for f in first]).astype(np.int32)
+        got = emc.merge_candidates(torch.as_tensor(first, device="cuda") if R else None,
+                                   torch.as_tensor(rest, device="cuda"), M).cpu().numpy()
+        assert np.array_equal(got, ol.merge_candidates(first, rest, M))
+    with pytest.raises(emc.EmcError):  # rest shorter than M
+        emc.merge_candidates(None, torch.zeros((4, 8), dtype=torch.int32, device="cuda"), 9)
+
+
 def _candidates(dense_ref, M, seed=8):
     # the top M/2 dense scores plus M/2 random others, sorted per frame
     S = dense_ref["S"]

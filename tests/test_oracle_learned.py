@@ -117,3 +117,19 @@ def test_soft_targets_renormalised():
     idx, prob = ol.soft_targets(P, 4)
     assert idx.shape == (6, 4) and np.allclose(prob.sum(axis=1), 1.0)
     assert np.all(P.T[np.arange(6), idx[:, 0]] == P.max(axis=0))
+
+
+def test_merge_candidates_hand_cases():
+    from oracle import learned as ol
+    first = np.array([[5, 2], [0, 1]])
+    rest = np.array([[2, 7, 5, 9, 3], [4, 3, 2, 1, 0]])
+    out = ol.merge_candidates(first, rest, 4)
+    assert out.tolist() == [[5, 2, 7, 9], [0, 1, 4, 3]]
+    # every merged set holds all of `first` and M distinct entries
+    rng = np.random.default_rng(40)
+    first = np.stack([rng.permutation(50)[:6] for _ in range(20)])
+    rest = np.stack([rng.permutation(50)[:16] for _ in range(20)])
+    out = ol.merge_candidates(first, rest, 16)
+    for k in range(20):
+        assert set(first[k]) <= set(out[k]) and len(set(out[k])) == 16
+        assert set(out[k]) <= set(first[k]) | set(rest[k])
