@@ -238,166 +238,160 @@ cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n
 // S_jk held frame-major as d[k][j] (ld = ldS) relative to its 32-row group
 // maximum r[j/32][k], which lies on the 1/64 grid; r - hi(lse_k) is exact, so
 //   P_jk = exp(d_kj + ((r_gk - hi_k) - lo_k)).
-// One CTA per 32 rows x 64 frames: coalesced 128-byte reads of d along j,
-// a shared-memory transpose, coalesced writes of P along k. HBM-bound: 4 B read
-// and 4 B written per (j, k).
-template <int OUT>  // 0: FP32 P; 1: BF16 hi plane only; 2: BF16 hi + lo; 3: FP16 hi + lo of 2^14 P
-__global__ void __launch_bounds__(256)
-    normalize_scores_kernel(const float* __restrict__ S, int64_t ldS,
-                            const float* __restrict__ Sref, const float2* __restrict__ lse2,
-                            int64_t nrot, int64_t ld_data, int64_t n_data, void* __restrict__ P,
-                            int64_t P_plane) {
-  __shared__ float tile[64][33];
-  const int64_t j0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-#pragma unroll
-  for (int r = 0; r < 8; r++) {  // frames k0 + ty + 8r, rows j0 + tx
-    const int kk = ty + 8 * r;
-    tile[kk][tx] = S[(k0 + kk) * ldS + j0 + tx];
-  }
-  __syncthreads();
-  // thread: row j0 + (threadIdx.x >> 3), frames k0 + 8 * (threadIdx.x & 7) .. + 8
-  const int jj = threadIdx.x >> 3, kb = (threadIdx.x & 7) * 8;
-  const int64_t j = j0 + jj, k = k0 + kb;
-  const float4* rs = reinterpret_cast<const float4*>(Sref + (j >> 5) * ld_data + k);
-  const float4 r0 = rs[0], r1 = rs[1];
-  const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-  float p[8];
-#pragma unroll
-  for (int u = 0; u < 8; u++) {
-    const float2 L = lse2[k + u];
-    const float ex = tile[kb + u][jj] + ((rv[u] - L.x) - L.y);
-    p[u] = (j < nrot && k + u < n_data) ? __expf(ex) : 0.f;
-  }
-  if (OUT == 0) {
-    float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(P) + j * ld_data + k);
-    o[0] = make_float4(p[0], p[1], p[2], p[3]);
-    o[1] = make_float4(p[4], p[5], p[6], p[7]);
-  } else {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      uint16_t h0, h1, l0, l1;
-      if (OUT == 3) {
-        const float s0 = p[u] * kP16Scale, s1 = p[u + 1] * kP16Scale;
-        h0 = fp16_bits(s0);
-        h1 = fp16_bits(s1);
-        l0 = fp16_bits(s0 - fp16_val(h0));
-        l1 = fp16_bits(s1 - fp16_val(h1));
-      } else {
-        h0 = bf16_bits(p[u]);
-        h1 = bf16_bits(p[u + 1]);
-        l0 = OUT == 2 ? bf16_bits(p[u] - bf16_val(h0)) : (uint16_t)0;
-        l1 = OUT == 2 ? bf16_bits(p[u + 1] - bf16_val(h1)) : (uint16_t)0;
-      }
-      h[u / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-      l[u / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-    }
-    uint16_t* ph = reinterpret_cast<uint16_t*>(P) + j * ld_data + k;
-    *reinterpret_cast<uint4*>(ph) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(ph + P_plane) = make_uint4(l[0], l[1], l[2], l[3]);
-  }
-}
-
-cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sref,
-                                    const float2* lse2, int64_t rows, int64_t nrot,
-                                    int64_t ld_data, int64_t n_data, int precision, void* P,
-                                    int64_t P_plane, cudaStream_t s) {
-  dim3 grid((unsigned)(ld_data / 64), (unsigned)(rows / 32));
-  if (precision == EMC_PREC_FP32)
-    normalize_scores_kernel<0><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
-                                                    P_plane);
-  else if (precision == EMC_PREC_FP16_SPLIT)
-    normalize_scores_kernel<3><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
-                                                    P_plane);
-  else if (precision == EMC_PREC_BF16)
-    normalize_scores_kernel<1><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
-                                                    P_plane);
-  else
-    normalize_scores_kernel<2><<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, nrot, ld_data, n_data, P,
-                                                    P_plane);
-  return cudaGetLastError();
-}
-
-// Gaussian model, pass 2 from stored scores: P_jk = exp(S_jk - lse_k) as in
-// normalize_scores_kernel, then the M-step operand of Eq. 2.5 with the
+// One CTA per 128 rows x 64 frames: every thread has eight 16-byte loads of d
+// in flight (512 contiguous bytes per warp and frame), the tile is transposed
+// through shared memory with its columns XOR-swizzled by 4 (k / 8 mod 8), so
+// that the reads along k are free of bank conflicts, and P is written along k
+// (128 contiguous bytes per row and plane). The lse split and the group maxima
+// of the tile are staged in shared memory. HBM-bound: 4 B read and 4 B written
+// per (j, k).
+//
+// Gaussian model (OUT 4): after P, the M-step operand of Eq. 2.5 with the
 // fluence of Eq. 2.6, P_jk / phi_jk, where
 //   1/phi_jk = G_jk / A_k = sqrt((S_jk - bias_j) 2 sigma^2 / A_k)
 // and S_jk - bias_j = G_jk^2 / (2 sigma^2 A_k) >= 0 is formed as
 // d + (r - hi(bias_j)) - lo(bias_j) (r and hi(bias) on the 1/64 grid, so the
-// large parts cancel exactly). Written as BF16 hi + lo of P / phi (relative
-// precision 2^-17 over the whole FP32 range, which a single FP16 scale cannot
-// give rows of small responsibility); den_j = sum_k P_jk is added to den with
-// one FP32 atomic per row and 64 frames (den zeroed by the caller).
-__global__ void __launch_bounds__(256)
-    normalize_scores_gauss_kernel(const float* __restrict__ S, int64_t ldS,
-                                  const float* __restrict__ Sref, const float2* __restrict__ lse2,
-                                  const double* __restrict__ bias, const float4* __restrict__ gk,
-                                  int64_t nrot, int64_t ld_data,
-                                  int64_t n_data, uint16_t* __restrict__ P, int64_t P_plane,
-                                  float* __restrict__ den) {
-  __shared__ float tile[64][33];
-  const int64_t j0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 64;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+// large parts cancel exactly). Written as BF16 hi + lo (relative precision
+// 2^-17 over the whole FP32 range, which a single FP16 scale cannot give rows
+// of small responsibility); den_j = sum_k P_jk is added to den with one FP32
+// atomic per row and 8 frames (den zeroed by the caller).
+struct NormArgs {
+  const float* S;
+  int64_t ldS;
+  const float* Sref;
+  const float2* lse2;
+  int64_t nrot, ld_data, n_data;
+  void* P;
+  int64_t P_plane;
+  const double* bias;  // Gaussian
+  const float4* gk;    // Gaussian: .z = 2 sigma^2 / A_k
+  float* den;          // Gaussian
+};
+
+constexpr int kNormRows = 128, kNormFrames = 64;
+
+// OUT: 0 FP32 P; 1 BF16 hi plane only; 2 BF16 hi + lo; 3 FP16 hi + lo of 2^14 P;
+// 4 Gaussian BF16 hi + lo of P / phi plus den
+template <int OUT>
+__global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a) {
+  __shared__ __align__(16) float tile[kNormFrames][kNormRows];
+  __shared__ float2 sl[kNormFrames];
+  __shared__ float sr[kNormRows / 32][kNormFrames];
+  __shared__ float sg[kNormFrames];
+  const int64_t j0 = (int64_t)blockIdx.y * kNormRows, k0 = (int64_t)blockIdx.x * kNormFrames;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4 v[8];
+#pragma unroll
+  for (int r = 0; r < 8; r++) {  // warp w: frames w + 8 r; lane: rows 4 lane .. 4 lane + 3
+    const int k = warp + 8 * r;
+    v[r] = __ldcs(reinterpret_cast<const float4*>(a.S + (k0 + k) * a.ldS + j0) + lane);
+  }
+  if (tid < kNormFrames) {
+    sl[tid] = a.lse2[k0 + tid];
+    if (OUT == 4) sg[tid] = a.gk[k0 + tid].z;
+  }
+  sr[tid >> 6][tid & 63] = a.Sref[((j0 >> 5) + (tid >> 6)) * a.ld_data + k0 + (tid & 63)];
 #pragma unroll
   for (int r = 0; r < 8; r++) {
-    const int kk = ty + 8 * r;
-    tile[kk][tx] = S[(k0 + kk) * ldS + j0 + tx];
+    const int k = warp + 8 * r;  // (k >> 3) & 7 == r
+    *reinterpret_cast<float4*>(&tile[k][(4 * lane) ^ (4 * r)]) = v[r];
   }
   __syncthreads();
-  const int jj = threadIdx.x >> 3, kb = (threadIdx.x & 7) * 8;
-  const int64_t j = j0 + jj, k = k0 + kb;
-  const bool row_ok = j < nrot;
-  float bh = 0.f, bl = 0.f;
-  if (row_ok) {
-    const double b = bias[j];
-    const double h = rint(b * kGridD) / kGridD;
-    bh = (float)h;
-    bl = (float)(b - h);
-  }
-  const float4* rs = reinterpret_cast<const float4*>(Sref + (j >> 5) * ld_data + k);
-  const float4 r0 = rs[0], r1 = rs[1];
-  const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-  float p[8], dsum = 0.f;
+  const int kq = tid & 7, kb = 8 * kq, sw = 4 * kq;  // frames kb .. kb + 7
+  float2 L[8];
 #pragma unroll
-  for (int u = 0; u < 8; u++) {
-    const float2 L = lse2[k + u];
-    const float d = tile[kb + u][jj];
-    const bool ok = row_ok && k + u < n_data;
-    const float pr = ok ? __expf(d + ((rv[u] - L.x) - L.y)) : 0.f;
-    dsum += pr;
-    const float q = fmaxf(d + ((rv[u] - bh) - bl), 0.f);
-    p[u] = ok ? pr * sqrtf(q * gk[k + u].z) : 0.f;
-  }
-  uint32_t h[4], l[4];
+  for (int u = 0; u < 8; u++) L[u] = sl[kb + u];
+#pragma unroll 1
+  for (int pass = 0; pass < kNormRows / 32; pass++) {
+    const int jj = (tid >> 3) + 32 * pass;
+    const int64_t j = j0 + jj, k = k0 + kb;
+    const bool row_ok = j < a.nrot;
+    float bh = 0.f, bl = 0.f;
+    if (OUT == 4 && row_ok) {
+      const double b = a.bias[j];
+      bh = (float)(rint(b * kGridD) / kGridD);
+      bl = (float)(b - (double)bh);
+    }
+    float p[8], dsum = 0.f;
 #pragma unroll
-  for (int u = 0; u < 8; u += 2) {
-    const uint16_t h0 = bf16_bits(p[u]), h1 = bf16_bits(p[u + 1]);
-    const uint16_t l0 = bf16_bits(p[u] - bf16_val(h0)), l1 = bf16_bits(p[u + 1] - bf16_val(h1));
-    h[u / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-    l[u / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    for (int u = 0; u < 8; u++) {
+      const float d = tile[kb + u][jj ^ sw];
+      const float r = sr[pass][kb + u];
+      const bool ok = row_ok && k + u < a.n_data;
+      const float pr = ok ? __expf(d + ((r - L[u].x) - L[u].y)) : 0.f;
+      if (OUT == 4) {
+        dsum += pr;
+        const float q = fmaxf(d + ((r - bh) - bl), 0.f);
+        p[u] = ok ? pr * sqrtf(q * sg[kb + u]) : 0.f;
+      } else {
+        p[u] = pr;
+      }
+    }
+    if (OUT == 0) {
+      float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.P) + j * a.ld_data + k);
+      o[0] = make_float4(p[0], p[1], p[2], p[3]);
+      o[1] = make_float4(p[4], p[5], p[6], p[7]);
+    } else {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        uint16_t h0, h1, l0, l1;
+        if (OUT == 3) {
+          const float s0 = p[u] * kP16Scale, s1 = p[u + 1] * kP16Scale;
+          h0 = fp16_bits(s0);
+          h1 = fp16_bits(s1);
+          l0 = fp16_bits(s0 - fp16_val(h0));
+          l1 = fp16_bits(s1 - fp16_val(h1));
+        } else {
+          h0 = bf16_bits(p[u]);
+          h1 = bf16_bits(p[u + 1]);
+          l0 = OUT != 1 ? bf16_bits(p[u] - bf16_val(h0)) : (uint16_t)0;
+          l1 = OUT != 1 ? bf16_bits(p[u + 1] - bf16_val(h1)) : (uint16_t)0;
+        }
+        h[u / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+        l[u / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+      }
+      uint16_t* ph = reinterpret_cast<uint16_t*>(a.P) + j * a.ld_data + k;
+      *reinterpret_cast<uint4*>(ph) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(ph + a.P_plane) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    if (OUT == 4) {  // the 8 threads of a row are consecutive lanes
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, 2);
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, 4);
+      if (kq == 0 && row_ok && dsum > 0.f) atomicAdd(a.den + j, dsum);
+    }
   }
-  uint16_t* ph = P + j * ld_data + k;
-  *reinterpret_cast<uint4*>(ph) = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4*>(ph + P_plane) = make_uint4(l[0], l[1], l[2], l[3]);
-  // the 8 threads of one row are consecutive lanes
-  dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
-  dsum += __shfl_xor_sync(0xffffffffu, dsum, 2);
-  dsum += __shfl_xor_sync(0xffffffffu, dsum, 4);
-  if ((threadIdx.x & 7) == 0 && row_ok && dsum > 0.f) atomicAdd(den + j, dsum);
+}
+
+// rows: multiple of 128 (the stored-score blocks are); ld_data: multiple of 256
+cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sref,
+                                    const float2* lse2, int64_t rows, int64_t nrot,
+                                    int64_t ld_data, int64_t n_data, int precision, void* P,
+                                    int64_t P_plane, cudaStream_t s) {
+  NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane, nullptr, nullptr, nullptr};
+  dim3 grid((unsigned)(ld_data / kNormFrames), (unsigned)(rows / kNormRows));
+  if (precision == EMC_PREC_FP32)
+    normalize_scores_kernel<0><<<grid, 256, 0, s>>>(a);
+  else if (precision == EMC_PREC_FP16_SPLIT)
+    normalize_scores_kernel<3><<<grid, 256, 0, s>>>(a);
+  else if (precision == EMC_PREC_BF16)
+    normalize_scores_kernel<1><<<grid, 256, 0, s>>>(a);
+  else
+    normalize_scores_kernel<2><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_normalize_scores_gauss(const float* S, int64_t ldS, const float* Sref,
                                           const float2* lse2, const double* bias,
-                                          const float4* gk, int64_t rows,
-                                          int64_t nrot, int64_t ld_data, int64_t n_data,
-                                          uint16_t* P, int64_t P_plane, float* den,
-                                          cudaStream_t s) {
+                                          const float4* gk, int64_t rows, int64_t nrot,
+                                          int64_t ld_data, int64_t n_data, uint16_t* P,
+                                          int64_t P_plane, float* den, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(den, 0, sizeof(float) * rows, s);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(ld_data / 64), (unsigned)(rows / 32));
-  normalize_scores_gauss_kernel<<<grid, 256, 0, s>>>(S, ldS, Sref, lse2, bias, gk, nrot,
-                                                     ld_data, n_data, P, P_plane, den);
+  NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane, bias, gk, den};
+  dim3 grid((unsigned)(ld_data / kNormFrames), (unsigned)(rows / kNormRows));
+  normalize_scores_kernel<4><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
