@@ -480,9 +480,18 @@ def run_ours(args):
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "peak_source": f"{pk_src} bf16 sustained"}
     achieved = flops / (dom_ms * 1e-3) / 1e12
+    # DRAM bytes of pass 1 from one ncu capture of this exact configuration
+    # (profiles/tc_pass1_update_emc64_dram_bytes.md); other configurations: unmeasured
+    traffic = None
+    if (args.workload == "emc64" and args.precision == "bf16_split" and n_data == 20000
+            and n_rot == 50100 and not args.recompute):
+        traffic = 6.82e9 + 4.25e9
     roof.update({"kernel": "E-step pass 1 (scores + online log-sum-exp)", "achieved": achieved,
                  "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": None, "algorithmic_flops_per_launch": flops})
+                 "traffic": traffic, "traffic_unit": "bytes per launch",
+                 "algorithmic_flops_per_launch": flops,
+                 "executed_flops_per_launch": flops * (3 if args.precision == "bf16_split" else
+                                                       2 if args.precision == "fp16_split" else 1)})
 
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
