@@ -13,6 +13,9 @@ namespace emc {
 
 constexpr int kCompressThreads = 256;
 
+// INTERIOR: all trilinear corners of every pixel lie inside the grid (checked
+// on the host from max |q_i|), so no bounds checks and one base index.
+template <bool INTERIOR>
 __global__ void __launch_bounds__(kCompressThreads)
     compress_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
                     int64_t ld_pix, int N, const RotDF* __restrict__ rot,
@@ -39,6 +42,21 @@ __global__ void __launch_bounds__(kCompressThreads)
     float t[3];
     rotate_to_grid(R, a, b, half_n, f, t);
     const float v = Nr[i] * inv_d;
+    if (INTERIOR) {
+      const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
+      const int nn32 = N * N;
+      const int base = f[0] * nn32 + f[1] * N + f[2];
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
+        const float w = wx[cx] * wy[cy] * wz[cz];
+        if (w == 0.f) continue;
+        const int l = base + cx * nn32 + cy * N + cz;
+        atomicAdd(g_num + l, (double)(w * v));
+        atomicAdd(g_den + l, (double)(w * dv));
+      }
+      continue;
+    }
 #pragma unroll
     for (int c = 0; c < 8; c++) {
       int x = f[0] + ((c >> 2) & 1), y = f[1] + ((c >> 1) & 1), z = f[2] + (c & 1);
@@ -58,8 +76,12 @@ cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const
                             const float* den, int mode, double* g_num, double* g_den,
                             cudaStream_t s) {
   if (nrot <= 0) return cudaSuccess;
-  compress_kernel<<<(unsigned)nrot, kCompressThreads, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N,
-                                                             rot, Num, den, mode, g_num, g_den);
+  if (g.interior)
+    compress_kernel<true><<<(unsigned)nrot, kCompressThreads, 0, s>>>(
+        g.qh, g.ql, g.n_pix, g.ld_pix, g.N, rot, Num, den, mode, g_num, g_den);
+  else
+    compress_kernel<false><<<(unsigned)nrot, kCompressThreads, 0, s>>>(
+        g.qh, g.ql, g.n_pix, g.ld_pix, g.N, rot, Num, den, mode, g_num, g_den);
   return cudaGetLastError();
 }
 

@@ -281,6 +281,18 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   c->geom.n_pix = cfg->n_pix;
   c->geom.ld_pix = y.ld_pix;
   c->geom.N = cfg->N;
+  {
+    // |R q| = |q|: with every |q_i| below N/2 - 1 (less a margin far above the
+    // 1e-9-voxel error of the rotation) each p = R q + N/2 has floor in
+    // [1, N - 2], so the trilinear corners need no bounds checks
+    double r2max = 0.0;
+    for (int64_t i = 0; i < cfg->n_pix; i++) {
+      const double* qi = q + 3 * i;
+      const double r2 = qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2];
+      r2max = r2 > r2max ? r2 : r2max;
+    }
+    c->geom.interior = sqrt(r2max) < 0.5 * cfg->N - 1.0 - 1e-4 ? 1 : 0;
+  }
   c->quat = (double*)(c->ws + y.quat);
   c->rot = (const RotDF*)(c->ws + y.rot);
   c->logw = (double*)(c->ws + y.logw);

@@ -75,16 +75,26 @@ __host__ __device__ __forceinline__ void quat_to_rot_df(const double* q, RotDF* 
 
 // Grid coordinate p = R q + N/2 of one pixel, split into the integer corner
 // f (floor) and the fraction t in [0, 1], both accurate to ~1e-9 voxel.
+// Compensated dot product: with R = Rh + Rl and q = qh + ql,
+//   p = N/2 + sum_b Rh_b qh_b + sum_b (Rh_b ql_b + Rl_b qh_b) + O(2^-40),
+// the products Rh_b qh_b are split exactly (FMA), summed onto N/2 with exact
+// two-sums, and every remainder is gathered in one small FP32 term.
 __device__ __forceinline__ void rotate_to_grid(const RotDF& R, float4 qh, float4 ql, float half_n,
                                                int* f, float* t) {
-  f2 qv[3] = {{qh.x, ql.x}, {qh.y, ql.y}, {qh.z, ql.z}};
+  const float qhv[3] = {qh.x, qh.y, qh.z}, qlv[3] = {ql.x, ql.y, ql.z};
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    f2 s = {half_n, 0.f};
+    float S = half_n, L = 0.f;
 #pragma unroll
-    for (int b = 0; b < 3; b++) s = df_add(s, df_mul(R.r[3 * a + b], qv[b]));
-    float fl = floorf(s.h);
-    float fr = (s.h - fl) + s.l;  // s.h - fl is exact
+    for (int b = 0; b < 3; b++) {
+      const f2 r = R.r[3 * a + b];
+      const f2 p = two_prod(r.h, qhv[b]);
+      const f2 s = two_sum(S, p.h);
+      S = s.h;
+      L += s.l + fmaf(r.h, qlv[b], fmaf(r.l, qhv[b], p.l));
+    }
+    float fl = floorf(S);
+    float fr = (S - fl) + L;  // S - fl is exact
     if (fr < 0.f) {
       fl -= 1.f;
       fr += 1.f;

@@ -19,6 +19,7 @@ struct Geom {
   int64_t n_pix;
   int64_t ld_pix;
   int N;
+  int interior;  // every |q_i| < N/2 - 1 with margin: all 8 corners of every R_j q_i lie in the grid
 };
 
 // A block of rows of a (possibly multi-plane) row-major matrix.

@@ -25,7 +25,40 @@ namespace emc {
 
 constexpr int kExpandThreads = 256;
 
-template <int PREC, bool GAUSS>
+// Trilinear value of the grid at p = f + t (Eq. 2.8 tent weights). INTERIOR:
+// all eight corners are known to lie inside the grid (no bounds checks, one
+// base index); otherwise corners outside [0, N) carry no value.
+template <bool INTERIOR>
+__device__ __forceinline__ float trilinear(const float* __restrict__ grid, int N, const int* f,
+                                           const float* t) {
+  const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
+  float W = 0.f;
+  if (INTERIOR) {
+    const int nn = N * N;
+    const float* g = grid + (f[0] * nn + f[1] * N + f[2]);
+#pragma unroll
+    for (int cx = 0; cx < 2; cx++)
+#pragma unroll
+      for (int cy = 0; cy < 2; cy++) {
+        const float wxy = wx[cx] * wy[cy];
+        const float* gr = g + cx * nn + cy * N;
+        W = fmaf(wxy * wz[0], __ldg(gr), W);
+        W = fmaf(wxy * wz[1], __ldg(gr + 1), W);
+      }
+    return W;
+  }
+  const int64_t nn = (int64_t)N * N;
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    int x = f[0] + ((c >> 2) & 1), y = f[1] + ((c >> 1) & 1), z = f[2] + (c & 1);
+    if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= N) continue;
+    const float w = wx[(c >> 2) & 1] * wy[(c >> 1) & 1] * wz[c & 1];
+    W = fmaf(w, __ldg(grid + (int64_t)x * nn + (int64_t)y * N + z), W);
+  }
+  return W;
+}
+
+template <int PREC, bool GAUSS, bool INTERIOR>
 __global__ void __launch_bounds__(kExpandThreads)
     expand_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
                   int64_t ld_pix, int N, const float* __restrict__ grid,
@@ -44,7 +77,6 @@ __global__ void __launch_bounds__(kExpandThreads)
   float* Lf = reinterpret_cast<float*>(Lbase) + row * ld_pix;
   uint16_t* Lb = reinterpret_cast<uint16_t*>(Lbase) + row * ld_pix;
   const float half_n = 0.5f * (float)N;
-  const int64_t nn = (int64_t)N * N;
   float wsum = 0.f, wcomp = 0.f;  // Kahan-compensated sum of W (W^2) over this thread's pixels
   int bad = 0;
   const float gs = GAUSS ? gsc->x : 1.f;
@@ -59,15 +91,7 @@ __global__ void __launch_bounds__(kExpandThreads)
         int f[3];
         float t[3];
         rotate_to_grid(R, a, b, half_n, f, t);
-        float W = 0.f;
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-          int x = f[0] + ((c >> 2) & 1), y = f[1] + ((c >> 1) & 1), z = f[2] + (c & 1);
-          if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= N) continue;
-          float w = (((c >> 2) & 1) ? t[0] : 1.f - t[0]) * (((c >> 1) & 1) ? t[1] : 1.f - t[1]) *
-                    ((c & 1) ? t[2] : 1.f - t[2]);
-          W = fmaf(w, __ldg(grid + (int64_t)x * nn + (int64_t)y * N + z), W);
-        }
+        float W = trilinear<INTERIOR>(grid, N, f, t);
         W = fmaxf(W, GAUSS ? 0.f : w_floor);
         const float ky = (GAUSS ? W * W : W) - wcomp;
         const float kt = wsum + ky;
@@ -127,10 +151,16 @@ cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
                           int32_t* status, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
   dim3 grd((unsigned)rows), blk(kExpandThreads);
-#define EMC_EXPAND(P, G)                                                                     \
-  expand_kernel<P, G><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid, rot, logw, \
-                                          nrot, w_floor, L.base, L.plane_stride, bias, gsc,     \
-                                          gsc ? 1.0 / (2.0 * sigma * sigma) : 0.0, status)
+#define EMC_EXPAND_I(P, G, I)                                                                \
+  expand_kernel<P, G, I><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid, rot,     \
+                                             logw, nrot, w_floor, L.base, L.plane_stride, bias, \
+                                             gsc, gsc ? 1.0 / (2.0 * sigma * sigma) : 0.0, status)
+#define EMC_EXPAND(P, G)        \
+  if (g.interior) {             \
+    EMC_EXPAND_I(P, G, true);   \
+  } else {                      \
+    EMC_EXPAND_I(P, G, false);  \
+  }
   if (gsc) {
     EMC_EXPAND(EMC_PREC_FP16_SPLIT, true);
   } else {
@@ -142,6 +172,7 @@ cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
     }
   }
 #undef EMC_EXPAND
+#undef EMC_EXPAND_I
   return cudaGetLastError();
 }
 

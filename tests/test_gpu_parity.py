@@ -241,6 +241,36 @@ def test_single_rotation(torch_cuda, small_problem, oracle):
     assert np.all(Pg[0, :p["K"].shape[0]] == 1.0)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16_split"])
+def test_pixels_reaching_the_grid_edge(torch_cuda, small_problem, oracle, precision):
+    # pixels stretched to |q| = N/2 - 0.4: some trilinear corners fall outside
+    # the grid, so the bounds-checked expand and compress paths run (the
+    # workloads' own pixels keep every corner inside)
+    torch, p = torch_cuda, small_problem
+    N = p["N"]
+    r = np.linalg.norm(p["q"], axis=1)
+    q = p["q"] * ((N / 2 - 0.4) / r.max())
+    e = dict(p, q=q, quat=p["quat"][:300], w=p["w"][:300] / p["w"][:300].sum())
+    K = p["K"].astype(np.float64)
+    W = oracle.expand(e["grid"], e["quat"], q, e["w_floor"])
+    P, lse, _ = oracle.estep(oracle.scores(W, e["w"], K))
+    Num, den = oracle.mstep(P, K)
+    out, _, gd = oracle.compress(N, e["quat"], q, Num, den, e["grid"])
+    ctx = make_ctx(torch, e, precision)
+    nrot, npix = e["quat"].shape[0], q.shape[0]
+    L, bias = ctx.expand(grid_dev(torch, e), 0, nrot)
+    got, st = ctx.iteration(grid_dev(torch, e))
+    torch.cuda.synchronize()
+    assert ctx.status() == 0 and st["device_status"] == 0
+    # where the corners left inside the grid carry small trilinear weights, the
+    # FP32 rounding of the fraction t (<= 2^-25 absolute) bounds W's error:
+    # |dW| <= 8 * 2^-25 * max(grid) on top of the relative error of the values
+    Wg = np.exp(decode_L(torch, ctx, L, nrot, precision)[:nrot, :npix])
+    tol = (TOL[precision][0] + 2e-7 * np.abs(np.log(W))) * W + 8 * 2.0 ** -25 * e["grid"].max()
+    assert np.all(np.abs(Wg - W) <= tol)
+    assert rel_l2(got.cpu().numpy().astype(np.float64), out) <= 1e-5
+
+
 def test_counts_out_of_range_are_flagged(torch_cuda, small_problem):
     torch, p = torch_cuda, small_problem
     from paper_1409_4256_gb300 import emc
