@@ -45,6 +45,7 @@ DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3", "fp16_split": "f
 LEARNED_FORMS = ("learned",)
 ADAPTIVE_FORMS = ("adaptive",)
 GAUSS_FORMS = ("gaussian",)
+SPARSE_K_FORMS = ("sparse_k",)
 
 
 def parse_args():
@@ -57,7 +58,7 @@ def parse_args():
     ap.add_argument("--workload", default="emc64", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
     ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
-    ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned,adaptive,gaussian",
+    ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned,adaptive,gaussian,sparse_k",
                     help="other forms to time briefly (comma list, or 'none')")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-iters", type=int, default=30,
@@ -249,6 +250,16 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
     return ms, {k: v / steps for k, v in phases.items()}, kernels, lls[-1]
 
 
+def rot_chunk_for(n_rot: int, n_data: int, cap: float = 8e9) -> int:
+    """Rotations per pass-2 chunk keeping the P chunk (2 x 2 B per pair) below
+    `cap` bytes; 0 (one chunk) when everything fits."""
+    ld_data = -(-n_data // 256) * 256
+    rows = -(-n_rot // 128) * 128
+    if 4.0 * ld_data * rows <= cap:
+        return 0
+    return max(128, int(cap // (4 * ld_data)) // 128 * 128)
+
+
 def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, world):
     """Learned proposal + sparse Maximize with a dense fallback every 5th
     iteration. Untimed set-up: 2 dense iterations from the start model give the
@@ -263,7 +274,8 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
     R = min(32, M)
     floor = 1e-10 * float(ds.model_start.mean())
     ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split", w_floor=floor,
-                      store_scores=True, n_cand=M, device=str(grid.device), stream=stream)
+                      store_scores=True, n_cand=M, device=str(grid.device), stream=stream,
+                      rot_chunk=rot_chunk_for(n_rot, n_data))
     ctx.set_frames(K_dev, stream=stream)
 
     def refresh(net):
@@ -329,7 +341,7 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
         # model after N iterations, learned schedule vs dense, same start
         dense_ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split",
                                 w_floor=floor, store_scores=True, device=str(grid.device),
-                                stream=stream)
+                                stream=stream, rot_chunk=rot_chunk_for(n_rot, n_data))
         dense_ctx.set_frames(K_dev, stream=stream)
         with torch.cuda.stream(stream):
             a, b = g2.clone(), torch.empty_like(g2)
@@ -360,6 +372,44 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
         res["mean_missed_mass_at_dense_steps"] = missed
         del dense_ctx
     del ctx
+    return res
+
+
+def sparse_k_form(torch, emc, cfg, ds, quat, w, grid, K_dev, stream, tensor_pass1_ms):
+    """E-step pass 1 gathered over each frame's non-zero pixels (FP32 log W),
+    timed beside the same pass as a dense FP32 SIMT contraction and the
+    tensor-core pass of the headline form."""
+    n_rot, n_data = quat.shape[0], ds.K.shape[0]
+    floor = 1e-10 * float(ds.model_start.mean())
+    ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="fp32", w_floor=floor,
+                      sparse_k=True, device=str(grid.device), stream=stream)
+    ctx.set_frames(K_dev, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        L, bias = ctx.expand(grid, 0, n_rot, stream=stream)
+        m, s_ = ctx.loglik_sparse_k(L, bias, n_rot, stream=stream)  # warm-up
+        ev[0].record(stream)
+        for _ in range(2):
+            ctx.loglik_sparse_k(L, bias, n_rot, m, s_, stream=stream)
+        ev[1].record(stream)
+        md, sd = ctx.loglik(L, bias, n_rot, stream=stream)
+        ev[2].record(stream)
+        ctx.loglik(L, bias, n_rot, md, sd, stream=stream)
+        ev[3].record(stream)
+        ev[3].synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError("device status set by the sparse-K pass")
+    ms = ev[0].elapsed_time(ev[1]) / 2
+    ms_dense = ev[2].elapsed_time(ev[3])
+    lse_diff = float((m + torch.log(s_) - md - torch.log(sd))[:n_data].abs().max())
+    nz = float(np.count_nonzero(ds.K)) / ds.K.size
+    res = {"ms_pass1": ms, "pairs_per_s": n_rot * n_data / (ms * 1e-3),
+           "nonzero_fraction": nz, "fp32_dense_pass1_ms": ms_dense,
+           "tensor_pass1_ms": tensor_pass1_ms, "max_lse_diff_vs_dense_fp32": lse_diff,
+           # cost scales with the non-zero count: the density where it would match the
+           # tensor-core pass on this geometry
+           "break_even_nonzero_fraction": nz * tensor_pass1_ms / ms}
+    del ctx, L, bias
     return res
 
 
@@ -429,7 +479,8 @@ def run_ours(args):
 
     def make_ctx(prec, **kw):
         c = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision=prec, w_floor=floor,
-                        store_scores=not args.recompute, device=str(dev), stream=stream, **kw)
+                        store_scores=not args.recompute, device=str(dev), stream=stream,
+                        rot_chunk=rot_chunk_for(n_rot, n_data), **kw)
         c.set_frames(K_dev, stream=stream)
         return c
 
@@ -495,10 +546,19 @@ def run_ours(args):
 
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
-    for f in [x for x in args.forms.split(",") if x and x not in (args.precision, "none")]:
-        if f in ADAPTIVE_FORMS:
+    others = [x for x in args.forms.split(",") if x and x not in (args.precision, "none")]
+    for f in [x for x in others if x in ADAPTIVE_FORMS]:  # the one form that reuses ctx
+        try:
+            forms[f] = adaptive_form(torch, args, cfg, ds, grid, K_dev, stream, ctx, ms)
+        except Exception as e:
+            forms[f] = {"error": str(e)[:300]}
+    del ctx  # every other form builds its own context
+    torch.cuda.empty_cache()
+    for f in [x for x in others if x not in ADAPTIVE_FORMS]:
+        if f in SPARSE_K_FORMS:
             try:
-                forms[f] = adaptive_form(torch, args, cfg, ds, grid, K_dev, stream, ctx, ms)
+                forms[f] = sparse_k_form(torch, emc, cfg, ds, quat, w, grid, K_dev, stream,
+                                         phases["ms_loglik"])
             except Exception as e:
                 forms[f] = {"error": str(e)[:300]}
             continue

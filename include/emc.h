@@ -94,6 +94,10 @@ typedef enum emc_compress_mode {
                                    workspace (rows x ld_data x 4 B plus 1/32 of
                                    that) and derives P from them instead of
                                    recomputing the contraction */
+#define EMC_FLAG_SPARSE_K 2     /* emc_set_frames also lists every frame's
+                                   non-zero pixels (n_data x n_pix x 4 B of
+                                   workspace at most) for emc_loglik_sparse_k;
+                                   needs n_pix <= 65536 */
 
 typedef struct emc_config {
   int32_t N;             /* grid side, 4 <= N <= 1024 */
@@ -217,6 +221,18 @@ int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void
  * EMC_ERR_NUMERIC (sigma too small for the data). */
 int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, double* lse_m,
                double* lse_s, int accumulate, void* scores, emc_stream stream);
+
+/* Sparse-K form of the E-step pass 1 (no counterpart in the paper: an
+ * alternative contraction for frames with few photons). Same result as
+ * emc_loglik -- (m_k, s_k) over the block's rotations of
+ * S_jk = sum_i K_ik log W_ij + bias_j -- but the sum runs over each frame's
+ * non-zero pixels only, gathering log W there instead of contracting densely
+ * on the tensor cores. Needs EMC_FLAG_SPARSE_K and precision EMC_PREC_FP32 (L =
+ * FP32 log W of emc_expand); the Poisson model only; no stored scores.
+ * Returns EMC_ERR_UNSUPPORTED if one log W row (2 x 4 B x ld_pix) does not
+ * fit the kernel's shared memory (ld_pix above ~27000). */
+int emc_loglik_sparse_k(emc_ctx* ctx, const float* L, const double* bias, int64_t nrot,
+                        double* lse_m, double* lse_s, int accumulate, emc_stream stream);
 
 /* E-step pass 2 (Eq. 2.4): P_jk = exp(S_jk - lse_k). With scores == NULL the
  * scores are recomputed from L and bias (two-pass streamed form, nothing of
@@ -374,8 +390,8 @@ int emc_sparse_estep(emc_ctx* ctx, const void* L, const double* bias, float* P, 
 int emc_sparse_update(emc_ctx* ctx, const float* P, float* Num, float* den, emc_stream stream);
 
 /* One pass of Algorithm 2.1 with the Maximize step over the candidate sets
- * (e-step, sparse E- and M-steps, c-step); needs rot_chunk 0. stats->loglik is
- * sum_k of the candidate-set lse_k. */
+ * (e-step, sparse E- and M-steps, c-step). stats->loglik is sum_k of the
+ * candidate-set lse_k. */
 int emc_sparse_iteration(emc_ctx* ctx, const float* grid_in, float* grid_out,
                          emc_iter_stats* stats, emc_stream stream);
 

@@ -20,7 +20,7 @@ struct Layout {
   int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
   size_t qh, ql, quat, rot, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
       Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, gk, gauss,
-      Kb2, total;
+      Kb2, skcnt, skoff, skent, total;
 };
 
 // Gaussian scalars inside the 256-byte block at Layout::gauss
@@ -63,13 +63,15 @@ int check_config(const emc_config* c) {
   if (is_gauss(c)) {
     if (!(c->sigma > 0.0) || !isfinite(c->sigma)) return EMC_ERR_ARG;
     if (c->precision != EMC_PREC_FP16_SPLIT || !(c->flags & EMC_FLAG_STORE_SCORES) ||
-        c->n_cand != 0)
+        c->n_cand != 0 || (c->flags & EMC_FLAG_SPARSE_K))
       return EMC_ERR_UNSUPPORTED;
   } else if ((c->precision == EMC_PREC_BF16_SPLIT || c->precision == EMC_PREC_FP16_SPLIT) &&
              log(c->w_floor) < (double)kHiMin) {
     return EMC_ERR_UNSUPPORTED;
   }
-  if (c->rot_chunk < 0 || (c->flags & ~EMC_FLAG_STORE_SCORES) != 0) return EMC_ERR_ARG;
+  if (c->rot_chunk < 0 || (c->flags & ~(EMC_FLAG_STORE_SCORES | EMC_FLAG_SPARSE_K)) != 0)
+    return EMC_ERR_ARG;
+  if ((c->flags & EMC_FLAG_SPARSE_K) && c->n_pix > 65536) return EMC_ERR_UNSUPPORTED;
   if (c->n_cand < 0 || c->n_cand > c->n_rot || c->n_cand > 4096) return EMC_ERR_ARG;
   return EMC_OK;
 }
@@ -104,8 +106,10 @@ Layout make_layout(const emc_config* c) {
   y.part_s = take(sizeof(float) * (size_t)y.part_tiles * y.ld_data);
   y.S = (c->flags & EMC_FLAG_STORE_SCORES) ? take(score_bytes(y.rows, y.ld_data)) : 0;
   y.P = take(P_bytes(c, y.chunk_rows, y.ld_data));
-  y.Num = take(sizeof(float) * (size_t)y.chunk_rows * y.ld_pix);
-  y.den = take(sizeof(float) * y.chunk_rows);
+  // the sparse update (n_cand > 0) writes Num and den for every rotation at once
+  const int64_t num_rows = c->n_cand > 0 ? y.rows : y.chunk_rows;
+  y.Num = take(sizeof(float) * (size_t)num_rows * y.ld_pix);
+  y.den = take(sizeof(float) * num_rows);
   y.gnum = take(sizeof(double) * nvox);
   y.gden = take(sizeof(double) * nvox);
   y.scalar = take(256);
@@ -122,6 +126,10 @@ Layout make_layout(const emc_config* c) {
   y.gk = is_gauss(c) ? take(sizeof(float4) * (size_t)y.ld_data) : 0;
   y.gauss = take(256);
   y.Kb2 = is_gauss(c) ? take(2 * (size_t)y.ld_data * y.ld_pix) : 0;
+  const bool sk = (c->flags & EMC_FLAG_SPARSE_K) != 0;
+  y.skcnt = sk ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
+  y.skoff = sk ? take(sizeof(int64_t) * (size_t)(y.ld_data + 1)) : 0;
+  y.skent = sk ? take(sizeof(uint32_t) * (size_t)c->n_data * c->n_pix) : 0;
   y.total = o;
   return y;
 }
@@ -357,6 +365,10 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
   CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb,
                         g ? 3 : (ctx->cfg.precision == EMC_PREC_FP16_SPLIT ? 1 : 0), ctx->status,
                         (cudaStream_t)stream));
+  if (ctx->cfg.flags & EMC_FLAG_SPARSE_K)
+    CU(launch_sparse_k_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data,
+                              (int32_t*)(ctx->ws + y.skcnt), (int64_t*)(ctx->ws + y.skoff),
+                              (uint32_t*)(ctx->ws + y.skent), (cudaStream_t)stream));
   if (g) {
     CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb2,
                           2, ctx->status, (cudaStream_t)stream));
@@ -504,6 +516,27 @@ int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, do
   if (((uintptr_t)scores) & 15) return EMC_ERR_ARG;
   return do_loglik(ctx, L, round_up(nrot, 128), 0, bias, nrot, lse_m, lse_s, accumulate, scores,
                    (cudaStream_t)stream);
+}
+
+int emc_loglik_sparse_k(emc_ctx* ctx, const float* L, const double* bias, int64_t nrot,
+                        double* lse_m, double* lse_s, int accumulate, emc_stream stream) {
+  if (!ctx || !L || !bias || !lse_m || !lse_s) return EMC_ERR_ARG;
+  if (check_rot_range(ctx, 0, nrot)) return EMC_ERR_ARG;
+  if (!ctx->frames_loaded) return EMC_ERR_ARG;
+  if (!(ctx->cfg.flags & EMC_FLAG_SPARSE_K) || ctx->cfg.precision != EMC_PREC_FP32)
+    return EMC_ERR_UNSUPPORTED;
+  const Layout& y = ctx->lay;
+  if (sparse_k_smem(y.ld_pix) > 220u * 1024u) return EMC_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t rows = round_up(nrot, 128);
+  double* pm = (double*)(ctx->ws + y.part_m);
+  float* ps = (float*)(ctx->ws + y.part_s);
+  CU(launch_sparse_k_pass1(L, y.ld_pix, ctx->cfg.n_pix, bias, rows, (int64_t*)(ctx->ws + y.skoff),
+                           (uint32_t*)(ctx->ws + y.skent), y.ld_data, ctx->cfg.n_data, pm, ps,
+                           s));
+  CU(launch_lse_merge(pm, ps, rows / 128, y.ld_data, ctx->cfg.n_data, lse_m, lse_s, accumulate, 0,
+                      ctx->status, s));
+  return EMC_OK;
 }
 
 int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
@@ -766,7 +799,6 @@ int emc_sparse_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_
                          emc_stream stream) {
   if (!c || !grid_in || !grid_out || grid_in == grid_out) return EMC_ERR_ARG;
   if (!c->frames_loaded || !c->cand_loaded) return EMC_ERR_ARG;
-  if (c->lay.chunk_rows != c->lay.rows) return EMC_ERR_UNSUPPORTED;  // Num holds every row
   cudaStream_t s = (cudaStream_t)stream;
   const Layout& y = c->lay;
   void* L = c->ws + y.L;

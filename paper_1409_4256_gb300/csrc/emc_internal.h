@@ -161,6 +161,22 @@ cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, i
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
                                float* missed, cudaStream_t s);
 
+// exclusive scan of cnt[0, n) into off[0, n] (off[n] = total), one CTA
+cudaError_t launch_scan_counts(const int32_t* cnt, int64_t n, int64_t* off, cudaStream_t s);
+
+// ---- sparse-K pass 1 (sparse_k.cu) ----
+// non-zero pixels of every frame: cnt[ld_data], off[ld_data + 1],
+// ent[] = pixel | count << 16 in pixel order
+cudaError_t launch_sparse_k_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                                   int64_t ld_data, int32_t* cnt, int64_t* off, uint32_t* ent,
+                                   cudaStream_t s);
+// per 128-row tile (max, sum) pairs like the dense pass 1, from FP32 log W
+cudaError_t launch_sparse_k_pass1(const float* L, int64_t ld_pix, int64_t n_pix, const double* bias,
+                                  int64_t rows, const int64_t* off, const uint32_t* ent,
+                                  int64_t ld_data, int64_t n_data, double* part_m, float* part_s,
+                                  cudaStream_t s);
+size_t sparse_k_smem(int64_t ld_pix);
+
 // Host side of Eq. 2.7 (emc_quat.cpp).
 int64_t quat_generate(int n, int uniform, double* quat, double* weight, int64_t cap);
 

@@ -244,6 +244,11 @@ cudaError_t launch_merge_candidates(const int32_t* first, int R, const int32_t* 
   return cudaGetLastError();
 }
 
+cudaError_t launch_scan_counts(const int32_t* cnt, int64_t n, int64_t* off, cudaStream_t s) {
+  csr_scan_kernel<<<1, 1024, 0, s>>>(cnt, n, off);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t n_rot,
                              int64_t rows, int32_t* cnt, int64_t* off, int2* ent,
                              int32_t* status, cudaStream_t s) {

@@ -21,6 +21,7 @@ PRECISIONS = {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16_split": PREC_BF16_SPLI
               "fp16_split": PREC_FP16_SPLIT}
 COMPRESS_DEFERRED, COMPRESS_IDW = 0, 1
 FLAG_STORE_SCORES = 1
+FLAG_SPARSE_K = 2
 MODEL_POISSON, MODEL_GAUSSIAN = 0, 1
 MODELS = {"poisson": MODEL_POISSON, "gaussian": MODEL_GAUSSIAN}
 
@@ -87,6 +88,7 @@ _SIGS = {
     "emc_mlp_forward": (_i32, [_i64, _vp, _vp, _i64, _vp, _vp, _vp]),
     "emc_mlp_train_step": (_i32, [_i64, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp, _vp,
                                   _i64, _i32, _vp, _vp, _vp]),
+    "emc_loglik_sparse_k": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "emc_merge_candidates": (_i32, [_vp, _i32, _vp, _i32, _i64, _i32, _vp, _vp]),
     "emc_topm": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "emc_targets_from_scores": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
@@ -206,7 +208,8 @@ class Context:
     def __init__(self, N: int, q: np.ndarray, quat: np.ndarray, weight: np.ndarray, n_data: int,
                  precision=None, w_floor: float = 1e-10, compress_mode: int = 0,
                  rot_chunk: int = 0, store_scores: bool = False, n_cand: int = 0,
-                 device: str = "cuda", stream=None, model: str = "poisson", sigma: float = 1.0):
+                 device: str = "cuda", stream=None, model: str = "poisson", sigma: float = 1.0,
+                 sparse_k: bool = False):
         import torch
         self.torch = torch
         gauss = MODELS[model] == MODEL_GAUSSIAN
@@ -220,7 +223,8 @@ class Context:
         weight = np.ascontiguousarray(weight, dtype=np.float64)
         self.cfg = Config(N=N, precision=precision, n_pix=q.shape[0], n_rot=quat.shape[0],
                           n_data=n_data, w_floor=w_floor, compress_mode=compress_mode,
-                          flags=FLAG_STORE_SCORES if store_scores else 0, rot_chunk=rot_chunk,
+                          flags=(FLAG_STORE_SCORES if store_scores else 0) |
+                          (FLAG_SPARSE_K if sparse_k else 0), rot_chunk=rot_chunk,
                           n_cand=n_cand, model=MODELS[model], sigma=float(sigma))
         L = lib()
         nb = ctypes.c_size_t()
@@ -299,6 +303,16 @@ class Context:
             lse_s = self.torch.empty(self.ld_data, dtype=self.torch.float64, device=self.device)
         _check(lib().emc_loglik(self.h, _ptr(L), _ptr(bias), nrot, _ptr(lse_m), _ptr(lse_s),
                                 int(accumulate), _ptr(scores), _stream(stream)), "emc_loglik")
+        return lse_m, lse_s
+
+    def loglik_sparse_k(self, L, bias, nrot: int, lse_m=None, lse_s=None,
+                        accumulate: bool = False, stream=None):
+        if lse_m is None:
+            lse_m = self.torch.empty(self.ld_data, dtype=self.torch.float64, device=self.device)
+            lse_s = self.torch.empty(self.ld_data, dtype=self.torch.float64, device=self.device)
+        _check(lib().emc_loglik_sparse_k(self.h, _ptr(L), _ptr(bias), nrot, _ptr(lse_m),
+                                         _ptr(lse_s), int(accumulate), _stream(stream)),
+               "emc_loglik_sparse_k")
         return lse_m, lse_s
 
     def normalize(self, L, bias, nrot: int, lse_m, lse_s, scores=None, stream=None):

@@ -89,3 +89,21 @@ def test_gaussian_config_checks(libemc):
     assert ws(precision=2) == -4 and ws(flags=0) == -4 and ws(n_cand=8) == -4
     assert ws(sigma=0.0) == -1 and ws(sigma=float("nan")) == -1 and ws(model=2) == -1
     assert ws(model=0, sigma=0.0) == 0  # sigma is not read for the Poisson model
+
+
+def test_sparse_k_config_checks(libemc):
+    from paper_1409_4256_gb300 import emc
+    nb = ctypes.c_size_t()
+
+    def ws(**kw):
+        base = dict(N=32, precision=0, n_pix=100, n_rot=50, n_data=10, w_floor=1e-10,
+                    compress_mode=0, flags=2, rot_chunk=0, n_cand=0, model=0, sigma=1.0)
+        base.update(kw)
+        return libemc.emc_workspace_size(ctypes.byref(emc.Config(**base)), ctypes.byref(nb))
+
+    assert ws() == 0
+    small = nb.value
+    assert ws(flags=0) == 0 and nb.value < small  # the non-zero lists take workspace
+    assert ws(n_pix=70000) == -4  # pixel indices must fit 16 bits
+    assert ws(flags=4) == -1
+    assert ws(model=1, precision=3, flags=3) == -4  # Poisson only
