@@ -94,6 +94,18 @@ typedef enum emc_compress_mode {
                                    workspace (rows x ld_data x 4 B plus 1/32 of
                                    that) and derives P from them instead of
                                    recomputing the contraction */
+#define EMC_FLAG_WIDE_COUNTS 4  /* counts above 256 (the largest integer range
+                                   BF16 holds exactly): ld_pix reserves 64
+                                   more columns, and emc_set_frames gives every
+                                   pixel whose count exceeds 256 in some frame
+                                   duplicate columns (same q_i) carrying the
+                                   count in parts of at most 256; expansion
+                                   leaves duplicates out of sum_i W_ij and
+                                   compression out of the denominators, so every
+                                   result is unchanged. More than 64 duplicate
+                                   columns needed: EMC_ERR_UNSUPPORTED in the
+                                   device status. Frame totals keep their
+                                   limits. Not for emc_loglik_static. */
 #define EMC_FLAG_SPARSE_K 2     /* emc_set_frames also lists every frame's
                                    non-zero pixels (n_data x n_pix x 4 B of
                                    workspace at most) for emc_loglik_sparse_k;

@@ -35,13 +35,16 @@ __global__ void __launch_bounds__(kCompressThreads)
   const float* Nr = Num + row * ld_pix;
   const float inv_d = (mode == EMC_COMPRESS_IDW) ? 1.0f / dj : 1.0f;
   const float dv = (mode == EMC_COMPRESS_IDW) ? 1.0f : dj;
-  for (int64_t i = threadIdx.x; i < n_pix; i += kCompressThreads) {
+  // every column with geometry: pixels (w = 1) and duplicate columns carrying
+  // counts above 256 (w = kDupMark), which add numerator but no denominator
+  for (int64_t i = threadIdx.x; i < ld_pix; i += kCompressThreads) {
     float4 a = qh[i], b = ql[i];
     if (a.w == 0.f) continue;
     int f[3];
     float t[3];
     rotate_to_grid(R, a, b, half_n, f, t);
     const float v = Nr[i] * inv_d;
+    const float dvi = a.w == 1.f ? dv : 0.f;
     if (INTERIOR) {
       const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
       const int nn32 = N * N;
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(kCompressThreads)
         if (w == 0.f) continue;
         const int l = base + cx * nn32 + cy * N + cz;
         atomicAdd(g_num + l, (double)(w * v));
-        atomicAdd(g_den + l, (double)(w * dv));
+        if (dvi != 0.f) atomicAdd(g_den + l, (double)(w * dvi));
       }
       continue;
     }
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(kCompressThreads)
       int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
       // FP32 products (relative error 6e-8), FP64 accumulation in L2
       atomicAdd(g_num + l, (double)(w * v));
-      atomicAdd(g_den + l, (double)(w * dv));
+      if (dvi != 0.f) atomicAdd(g_den + l, (double)(w * dvi));
     }
   }
 }

@@ -20,7 +20,7 @@ struct Layout {
   int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
   size_t qh, ql, quat, rot, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
       Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, gk, gauss,
-      Kb2, skcnt, skoff, skent, total;
+      Kb2, skcnt, skoff, skent, dupsrc, duprank, pixmax, total;
 };
 
 // Gaussian scalars inside the 256-byte block at Layout::gauss
@@ -69,7 +69,8 @@ int check_config(const emc_config* c) {
              log(c->w_floor) < (double)kHiMin) {
     return EMC_ERR_UNSUPPORTED;
   }
-  if (c->rot_chunk < 0 || (c->flags & ~(EMC_FLAG_STORE_SCORES | EMC_FLAG_SPARSE_K)) != 0)
+  if (c->rot_chunk < 0 ||
+      (c->flags & ~(EMC_FLAG_STORE_SCORES | EMC_FLAG_SPARSE_K | EMC_FLAG_WIDE_COUNTS)) != 0)
     return EMC_ERR_ARG;
   if ((c->flags & EMC_FLAG_SPARSE_K) && c->n_pix > 65536) return EMC_ERR_UNSUPPORTED;
   if (c->n_cand < 0 || c->n_cand > c->n_rot || c->n_cand > 4096) return EMC_ERR_ARG;
@@ -78,7 +79,9 @@ int check_config(const emc_config* c) {
 
 Layout make_layout(const emc_config* c) {
   Layout y;
-  y.ld_pix = round_up(c->n_pix + 1, 64);
+  const bool wide = (c->flags & EMC_FLAG_WIDE_COUNTS) != 0;
+  // pixels, the column of ones, and (wide counts) the duplicate columns
+  y.ld_pix = round_up(c->n_pix + 1 + (wide ? kDupCols : 0), 64);
   y.ld_data = round_up(c->n_data, 256);
   y.rows = round_up(c->n_rot, 128);
   y.chunk_rows = c->rot_chunk > 0 ? std::min(round_up(c->rot_chunk, 128), y.rows) : y.rows;
@@ -130,6 +133,9 @@ Layout make_layout(const emc_config* c) {
   y.skcnt = sk ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
   y.skoff = sk ? take(sizeof(int64_t) * (size_t)(y.ld_data + 1)) : 0;
   y.skent = sk ? take(sizeof(uint32_t) * (size_t)c->n_data * c->n_pix) : 0;
+  y.dupsrc = wide ? take(sizeof(int32_t) * kDupCols) : 0;
+  y.duprank = wide ? take(sizeof(int32_t) * kDupCols) : 0;
+  y.pixmax = wide ? take(sizeof(int32_t) * (size_t)c->n_pix) : 0;
   y.total = o;
   return y;
 }
@@ -362,16 +368,29 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
   if (!ctx || !K || ld_k < ctx->cfg.n_pix) return EMC_ERR_ARG;
   const Layout& y = ctx->lay;
   const bool g = is_gauss(&ctx->cfg);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t* dsrc = nullptr;
+  const int32_t* drank = nullptr;
+  if (ctx->cfg.flags & EMC_FLAG_WIDE_COUNTS) {
+    // duplicate columns for counts above 256 (geometry and bins rewritten)
+    dsrc = (const int32_t*)(ctx->ws + y.dupsrc);
+    drank = (const int32_t*)(ctx->ws + y.duprank);
+    CU(launch_assign_duplicates(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data,
+                                (int32_t*)(ctx->ws + y.pixmax), (float4*)(ctx->ws + y.qh),
+                                (float4*)(ctx->ws + y.ql), (int16_t*)(ctx->ws + y.fbin),
+                                (int32_t*)(ctx->ws + y.dupsrc), (int32_t*)(ctx->ws + y.duprank),
+                                ctx->status, s));
+  }
   CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb,
-                        g ? 3 : (ctx->cfg.precision == EMC_PREC_FP16_SPLIT ? 1 : 0), ctx->status,
-                        (cudaStream_t)stream));
+                        g ? 3 : (ctx->cfg.precision == EMC_PREC_FP16_SPLIT ? 1 : 0), dsrc, drank,
+                        ctx->status, s));
   if (ctx->cfg.flags & EMC_FLAG_SPARSE_K)
     CU(launch_sparse_k_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data,
                               (int32_t*)(ctx->ws + y.skcnt), (int64_t*)(ctx->ws + y.skoff),
                               (uint32_t*)(ctx->ws + y.skent), (cudaStream_t)stream));
   if (g) {
     CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb2,
-                          2, ctx->status, (cudaStream_t)stream));
+                          2, dsrc, drank, ctx->status, s));
     CU(launch_gauss_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, ctx->cfg.sigma,
                            ctx->gk, ctx->nmax, (cudaStream_t)stream));
   }

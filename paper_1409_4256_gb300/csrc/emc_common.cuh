@@ -149,6 +149,13 @@ constexpr double kGridD = 64.0;
 // FP16 maximum, P down to ~4e-9 stays normal); the update removes the scale.
 constexpr float kP16Scale = 16384.0f;
 
+// Duplicate pixel columns for counts above 256 (EMC_FLAG_WIDE_COUNTS): at most
+// this many, each carrying up to kDupCount photons of its source pixel; their
+// geometry entry has w = kDupMark (used pixels 1, padding 0).
+constexpr int kDupCols = 64;
+constexpr int kDupCount = 256;
+constexpr float kDupMark = 2.0f;
+
 // Gaussian model (Eqs. 2.2-2.3): S_jk <= log w_j < 0, and scores further than
 // kGaussClamp below zero are clamped -- their exp vanishes next to any
 // frame's best rotation, and the clamp keeps every score's 1/64-grid part

@@ -31,9 +31,20 @@ struct Planes {
 
 // fp16: bit 0 FP16 frames (EMC_PREC_FP16_SPLIT), else BF16; bit 1 no limit on
 // the frame total (the Gaussian model's two copies)
+// dup_src/dup_rank (device int32[kDupCols], NULL without duplicates): source
+// pixel of each duplicate column n_pix + 1 + d and its rank among that pixel's
+// duplicates; counts are then split in parts of at most kDupCount.
 cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
                                int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int fp16,
+                               const int32_t* dup_src, const int32_t* dup_rank,
                                int32_t* status, cudaStream_t s);
+// Duplicate columns for counts above kDupCount: per-pixel maxima over the
+// frames, then one thread assigns columns in pixel order and writes their
+// geometry (w = kDupMark) and feature bins. pixmax: int32[n_pix] scratch.
+cudaError_t launch_assign_duplicates(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                                     int64_t ld_data, int32_t* pixmax, float4* qh, float4* ql,
+                                     int16_t* fbin, int32_t* dup_src, int32_t* dup_rank,
+                                     int32_t* status, cudaStream_t s);
 
 // gsc != NULL: Gaussian model (FP16 three-plane s W, bias log w - sum W^2 / 2 sigma^2)
 cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kExpandThreads)
   for (int64_t i = threadIdx.x; i < ld_pix; i += kExpandThreads) {
     float L = 0.f;
     bool used = false;
-    if (valid_row && i < n_pix) {
+    if (valid_row) {  // geometry w: 1 pixel, kDupMark duplicate column, 0 padding / ones
       float4 a = qh[i], b = ql[i];
       if (a.w != 0.f) {
         used = true;
@@ -93,10 +93,12 @@ __global__ void __launch_bounds__(kExpandThreads)
         rotate_to_grid(R, a, b, half_n, f, t);
         float W = trilinear<INTERIOR>(grid, N, f, t);
         W = fmaxf(W, GAUSS ? 0.f : w_floor);
-        const float ky = (GAUSS ? W * W : W) - wcomp;
-        const float kt = wsum + ky;
-        wcomp = (kt - wsum) - ky;
-        wsum = kt;
+        if (a.w == 1.f) {  // duplicate columns (counts above 256) repeat a pixel: not summed
+          const float ky = (GAUSS ? W * W : W) - wcomp;
+          const float kt = wsum + ky;
+          wcomp = (kt - wsum) - ky;
+          wsum = kt;
+        }
         L = GAUSS ? W * gs : logf(W);
       }
     }

@@ -29,7 +29,8 @@ __global__ void features_kernel(const uint16_t* __restrict__ Kb, int kf16, int64
   for (int b = threadIdx.x; b < kFeat; b += blockDim.x) acc[b] = 0.f;
   __syncthreads();
   if (k < n_data)
-    for (int64_t i = threadIdx.x; i < n_pix; i += blockDim.x) {
+    for (int64_t i = threadIdx.x; i < ld_pix; i += blockDim.x) {  // pixels + duplicate columns
+      if (i == n_pix) continue;  // the column of ones
       const uint16_t u = Kb[k * ld_pix + i];
       const float c = kf16 ? fp16_val(u) : bf16_val(u);
       if (c != 0.f) atomicAdd(&acc[bin[i]], c);

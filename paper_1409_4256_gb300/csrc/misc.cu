@@ -14,21 +14,32 @@ namespace emc {
 // to the largest total).
 __global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, int64_t n_data,
                                    int64_t n_pix, int64_t ld_pix, uint16_t* __restrict__ Kb,
-                                   int fp16, int32_t* status) {
+                                   int fp16, const int32_t* __restrict__ dup_src,
+                                   const int32_t* __restrict__ dup_rank, int32_t* status) {
   const int64_t k = blockIdx.x;
   __shared__ long long red[8];
   long long tot = 0;
   int bad = 0;
+  const bool wide = dup_src != nullptr;
   for (int64_t i = threadIdx.x; i < ld_pix; i += blockDim.x) {
     float v = 0.f;
     if (k < n_data) {
       if (i < n_pix) {
         int32_t c = K[k * ld_k + i];
-        if (c < 0 || c > ((fp16 & 1) ? 2048 : 256)) bad = 1;
+        if (c < 0 || (!wide && c > ((fp16 & 1) ? 2048 : 256))) bad = 1;
         tot += c;
-        v = (float)c;
+        v = (float)(wide ? min(c, kDupCount) : c);
       } else if (i == n_pix) {
         v = 1.f;
+      } else if (wide && i - n_pix - 1 < kDupCols) {
+        // duplicate column: the part of its source pixel's count beyond the
+        // parts the source column and the lower-ranked duplicates carry
+        const int d = (int)(i - n_pix - 1);
+        const int32_t src = dup_src[d];
+        if (src >= 0) {
+          const int32_t c = K[k * ld_k + src] - kDupCount * (dup_rank[d] + 1);
+          v = (float)max(0, min(c, kDupCount));
+        }
       }
     }
     Kb[k * ld_pix + i] = (fp16 & 1) ? fp16_bits(v) : bf16_bits(v);
@@ -46,9 +57,69 @@ __global__ void prep_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, 
 
 cudaError_t launch_prep_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
                                int64_t ld_data, int64_t ld_pix, uint16_t* Kb, int fp16,
+                               const int32_t* dup_src, const int32_t* dup_rank,
                                int32_t* status, cudaStream_t s) {
   prep_frames_kernel<<<(unsigned)ld_data, 256, 0, s>>>(K, ld_k, n_data, n_pix, ld_pix, Kb, fp16,
-                                                       status);
+                                                       dup_src, dup_rank, status);
+  return cudaGetLastError();
+}
+
+// largest count of every pixel over the frames, where it exceeds kDupCount
+__global__ void pixel_max_kernel(const int32_t* __restrict__ K, int64_t ld_k, int64_t n_data,
+                                 int64_t n_pix, int32_t* __restrict__ pixmax) {
+  const int64_t k = blockIdx.x;
+  if (k >= n_data) return;
+  for (int64_t i = threadIdx.x; i < n_pix; i += blockDim.x) {
+    const int32_t c = K[k * ld_k + i];
+    if (c > kDupCount) atomicMax(&pixmax[i], c);
+  }
+}
+
+// One thread, pixels in order: ceil(max / kDupCount) - 1 duplicate columns
+// per pixel, geometry copied with w = kDupMark; unused columns reset.
+__global__ void assign_duplicates_kernel(const int32_t* __restrict__ pixmax, int64_t n_pix,
+                                         float4* qh, float4* ql, int16_t* fbin,
+                                         int32_t* dup_src, int32_t* dup_rank, int32_t* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int nd = 0;
+  for (int64_t i = 0; i < n_pix; i++) {
+    const int32_t m = pixmax[i];
+    if (m <= kDupCount) continue;
+    const int need = (m - 1) / kDupCount;
+    for (int t = 0; t < need; t++) {
+      if (nd >= kDupCols) {
+        set_status(status, EMC_ERR_UNSUPPORTED);
+        break;
+      }
+      const int64_t col = n_pix + 1 + nd;
+      const float4 a = qh[i];
+      qh[col] = make_float4(a.x, a.y, a.z, kDupMark);
+      ql[col] = ql[i];
+      fbin[col] = fbin[i];
+      dup_src[nd] = (int32_t)i;
+      dup_rank[nd] = t;
+      nd++;
+    }
+  }
+  for (; nd < kDupCols; nd++) {
+    const int64_t col = n_pix + 1 + nd;
+    qh[col] = make_float4(0.f, 0.f, 0.f, 0.f);
+    ql[col] = make_float4(0.f, 0.f, 0.f, 0.f);
+    fbin[col] = 0;
+    dup_src[nd] = -1;
+    dup_rank[nd] = 0;
+  }
+}
+
+cudaError_t launch_assign_duplicates(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                                     int64_t ld_data, int32_t* pixmax, float4* qh, float4* ql,
+                                     int16_t* fbin, int32_t* dup_src, int32_t* dup_rank,
+                                     int32_t* status, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(pixmax, 0, sizeof(int32_t) * n_pix, s);
+  if (e != cudaSuccess) return e;
+  pixel_max_kernel<<<(unsigned)ld_data, 256, 0, s>>>(K, ld_k, n_data, n_pix, pixmax);
+  assign_duplicates_kernel<<<1, 32, 0, s>>>(pixmax, n_pix, qh, ql, fbin, dup_src, dup_rank,
+                                            status);
   return cudaGetLastError();
 }
 

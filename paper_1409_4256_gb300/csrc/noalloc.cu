@@ -65,7 +65,8 @@ extern "C" int emc_loglik_static(const emc_config* cfg, const void* L, const dou
   if (!cfg || !L || !bias || !frames || !lse_m || !lse_s) return EMC_ERR_ARG;
   if (cfg->n_pix < 1 || cfg->n_data < 1 || nrot < 1 || nrot > cfg->n_rot) return EMC_ERR_ARG;
   if (cfg->precision < EMC_PREC_FP32 || cfg->precision > EMC_PREC_FP16_SPLIT) return EMC_ERR_ARG;
-  if (cfg->model != EMC_MODEL_POISSON) return EMC_ERR_UNSUPPORTED;
+  if (cfg->model != EMC_MODEL_POISSON || (cfg->flags & EMC_FLAG_WIDE_COUNTS))
+    return EMC_ERR_UNSUPPORTED;
   const int64_t ld_pix = up(cfg->n_pix + 1, 64);
   const int64_t ld_data = up(cfg->n_data, 256);
   const int64_t rows = up(nrot, 128);

@@ -22,6 +22,7 @@ PRECISIONS = {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16_split": PREC_BF16_SPLI
 COMPRESS_DEFERRED, COMPRESS_IDW = 0, 1
 FLAG_STORE_SCORES = 1
 FLAG_SPARSE_K = 2
+FLAG_WIDE_COUNTS = 4
 MODEL_POISSON, MODEL_GAUSSIAN = 0, 1
 MODELS = {"poisson": MODEL_POISSON, "gaussian": MODEL_GAUSSIAN}
 
@@ -209,7 +210,7 @@ class Context:
                  precision=None, w_floor: float = 1e-10, compress_mode: int = 0,
                  rot_chunk: int = 0, store_scores: bool = False, n_cand: int = 0,
                  device: str = "cuda", stream=None, model: str = "poisson", sigma: float = 1.0,
-                 sparse_k: bool = False):
+                 sparse_k: bool = False, wide_counts: bool = False):
         import torch
         self.torch = torch
         gauss = MODELS[model] == MODEL_GAUSSIAN
@@ -224,7 +225,8 @@ class Context:
         self.cfg = Config(N=N, precision=precision, n_pix=q.shape[0], n_rot=quat.shape[0],
                           n_data=n_data, w_floor=w_floor, compress_mode=compress_mode,
                           flags=(FLAG_STORE_SCORES if store_scores else 0) |
-                          (FLAG_SPARSE_K if sparse_k else 0), rot_chunk=rot_chunk,
+                          (FLAG_SPARSE_K if sparse_k else 0) |
+                          (FLAG_WIDE_COUNTS if wide_counts else 0), rot_chunk=rot_chunk,
                           n_cand=n_cand, model=MODELS[model], sigma=float(sigma))
         L = lib()
         nb = ctypes.c_size_t()

@@ -105,5 +105,16 @@ def test_sparse_k_config_checks(libemc):
     small = nb.value
     assert ws(flags=0) == 0 and nb.value < small  # the non-zero lists take workspace
     assert ws(n_pix=70000) == -4  # pixel indices must fit 16 bits
-    assert ws(flags=4) == -1
+    assert ws(flags=8) == -1
     assert ws(model=1, precision=3, flags=3) == -4  # Poisson only
+
+
+def test_wide_counts_reserve_duplicate_columns(libemc):
+    # EMC_FLAG_WIDE_COUNTS: 64 more columns in the pixel stride for duplicates
+    from paper_1409_4256_gb300 import emc
+    b = emc.BufferSizes()
+    for flags, want in ((0, 128), (4, 192)):
+        cfg = emc.Config(N=32, precision=2, n_pix=100, n_rot=50, n_data=10, w_floor=1e-10,
+                         compress_mode=0, flags=flags, rot_chunk=0, n_cand=0, model=0, sigma=1.0)
+        assert libemc.emc_buffer_sizes_for(ctypes.byref(cfg), 50, ctypes.byref(b)) == 0
+        assert b.ld_pix == want

@@ -1,11 +1,17 @@
 """Parity at the workloads' full sizes, on outputs the oracle can compute one
 by one and on identities that hold at any size.
 
+* emc32 (32^3, 32x32 detector, n=4 -> 3240 rotations, 1000 frames): small
+  enough for the oracle to compute everything; every P_jk and the model.
 * emc64 (64^3, 64x64 detector with 10% masked, n=10 -> 50100 rotations, 20000
   frames), the benchmark's configuration: every step over all rotations at
   once (the tile and launch shapes emc_iteration uses, scores stored).
 * emc128 (128^3, 128x128 detector, n=16 -> 204960 rotations, 100000 frames):
-  the same steps over rotation blocks of 8192 (merging lse across blocks).
+  the same steps over rotation blocks of 8192 (merging lse across blocks);
+  and the sparse E-step over 512 candidates per frame (seeded sets made on
+  the host) against the oracle's scores over the same candidates.
+* emc160 (160^3, 160x160 detector, n=20 -> 400200 rotations, 200000 frames
+  with log-normal fluence): the dense steps over rotation blocks of 8192.
 
 Sampled outputs: lse_k and the column P_{.k} of a few frames, against the FP64
 oracle's scores of those frames over every rotation. Identities (exact in
@@ -42,17 +48,24 @@ def _oracle_columns(oracle, grid, quat, w, q, Ks, floor, chunk=4096):
     return lse, P
 
 
-def _run(torch, oracle, name, block, sample):
-    from paper_1409_4256_gb300 import emc, synth
+def _dataset(name):
+    from paper_1409_4256_gb300 import synth
     cfg = synth.WORKLOADS[name]
-    ds = synth.make_dataset(cfg["N"], cfg["D"], cfg["n_data"], cfg["mean_photons"],
-                            masked_fraction=cfg["masked_fraction"], device="cuda")
-    quat, w = emc.quat_generate(cfg["n_quat"])
+    return cfg, synth.make_dataset(cfg["N"], cfg["D"], cfg["n_data"], cfg["mean_photons"],
+                                   masked_fraction=cfg["masked_fraction"],
+                                   fluence_sigma=cfg["fluence_sigma"], device="cuda")
+
+
+def _run(torch, oracle, name, block, sample, wide=False):
+    from paper_1409_4256_gb300 import emc
+    cfg, ds = _dataset(name)
+    quat, w = emc.quat_generate(cfg["n_quat"])       # the library's sampling
+    quat_o, w_o = oracle.quat_generate(cfg["n_quat"])  # the oracle's own (same order)
     nrot, nd, npix = quat.shape[0], ds.K.shape[0], ds.q.shape[0]
     grid32 = ds.model_start.astype(np.float32)
     floor = 1e-10 * float(ds.model_start.mean())
     ctx = emc.Context(cfg["N"], ds.q, quat, w, nd, precision="bf16_split", w_floor=floor,
-                      rot_chunk=block)
+                      rot_chunk=block, wide_counts=wide)
     ctx.set_frames(torch.as_tensor(ds.K, device="cuda"))
     g = torch.as_tensor(grid32, device="cuda")
     lse_m = torch.empty(ctx.ld_data, dtype=torch.float64, device="cuda")
@@ -84,13 +97,14 @@ def _run(torch, oracle, name, block, sample):
                              planes[1].index_select(1, sidx).double())[:nb].cpu().numpy()
         Num, den = ctx.update(P, nb)
         den_sum += float(den[:nb].double().sum())
-        num_sum += float(Num[:nb, :npix].double().sum())
+        # pixel columns and duplicate columns (counts above 256), not the ones column
+        num_sum += float(Num[:nb, :npix].double().sum() + Num[:nb, npix + 1:].double().sum())
         ctx.compress(r0, nb, Num, den, g_num, g_den, accumulate=True)
         del L, bias, Sb, P, Num, den
     torch.cuda.synchronize()
     assert ctx.status() == 0
     lse = (lse_m + torch.log(lse_s)).cpu().numpy()
-    lse_o, P_o = _oracle_columns(oracle, grid32.astype(np.float64), quat, w, ds.q,
+    lse_o, P_o = _oracle_columns(oracle, grid32.astype(np.float64), quat_o, w_o, ds.q,
                                  ds.K[sample].astype(np.float64), floor)
     return dict(lse=lse[:nd], lse_o=lse_o, P=Pcols, P_o=P_o, den_sum=den_sum, num_sum=num_sum,
                 photons=float(ds.K.astype(np.float64).sum()), nd=nd, npix=npix,
@@ -116,3 +130,76 @@ def test_fullsize_emc128(torch_cuda, oracle):
     sample = np.array([3, 54321, 99999])
     r = _run(torch_cuda, oracle, "emc128", 8192, sample)
     _check(r, sample)
+
+
+def test_fullsize_emc160(torch_cuda, oracle):
+    sample = np.array([1, 123456, 199999])
+    # a few pixels of the brightest frames exceed 256 photons: duplicate columns
+    r = _run(torch_cuda, oracle, "emc160", 8192, sample, wide=True)
+    _check(r, sample)
+
+
+def test_fullsize_emc32_every_output(torch_cuda, oracle):
+    # 3240 rotations x 1000 frames: every responsibility, the lse of every
+    # frame and the model after one iteration, against the oracle's full chain
+    torch = torch_cuda
+    from paper_1409_4256_gb300 import emc
+    cfg, ds = _dataset("emc32")
+    quat, w = emc.quat_generate(cfg["n_quat"])
+    quat_o, w_o = oracle.quat_generate(cfg["n_quat"])
+    nrot, nd = quat.shape[0], ds.K.shape[0]
+    grid32 = ds.model_start.astype(np.float32)
+    floor = 1e-10 * float(ds.model_start.mean())
+    out_o, lse_o, L_o, P_o = oracle.iteration(grid32.astype(np.float64), quat_o, w_o, ds.q,
+                                              ds.K.astype(np.float64), floor, want_P=True)
+    ctx = emc.Context(cfg["N"], ds.q, quat, w, nd, precision="bf16_split", w_floor=floor,
+                      store_scores=True)
+    ctx.set_frames(torch.as_tensor(ds.K, device="cuda"))
+    g = torch.as_tensor(grid32, device="cuda")
+    L, bias = ctx.expand(g, 0, nrot)
+    Sb = ctx.scores_buffer(nrot)
+    m, s = ctx.loglik(L, bias, nrot, scores=Sb)
+    P = ctx.normalize(None, None, nrot, m, s, scores=Sb)
+    out, st = ctx.iteration(g)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0 and st["device_status"] == 0
+    b = ctx.buffer_sizes(nrot)
+    planes = P.view(torch.bfloat16).view(2, b.rows, b.ld_data).double().cpu().numpy()
+    Pg = (planes[0] + planes[1])[:nrot, :nd]
+    assert np.abs(Pg - P_o).max() <= 1e-4
+    assert np.abs((m + torch.log(s)).cpu().numpy()[:nd] - lse_o).max() <= 1e-4
+    o = out.double().cpu().numpy()
+    assert np.linalg.norm(o - out_o) <= 1e-5 * np.linalg.norm(out_o)
+    assert abs(st["loglik"] - L_o) <= 1e-4 * nd
+
+
+def test_fullsize_sparse_estep_emc128(torch_cuda, oracle):
+    # 100000 frames x 512 candidates of 204960 rotations; the candidate sets are
+    # made on the host (a seeded offset pattern shifted per frame, all distinct)
+    torch = torch_cuda
+    from paper_1409_4256_gb300 import emc
+    cfg, ds = _dataset("emc128")
+    quat, w = emc.quat_generate(cfg["n_quat"])
+    quat_o, w_o = oracle.quat_generate(cfg["n_quat"])
+    nrot, nd, M = quat.shape[0], ds.K.shape[0], 512
+    rng = np.random.default_rng(51)
+    offsets = np.sort(rng.choice(nrot, M, replace=False))
+    base = rng.integers(0, nrot, size=nd)
+    cand = np.sort((base[:, None] + offsets[None, :]) % nrot, axis=1).astype(np.int32)
+    grid32 = ds.model_start.astype(np.float32)
+    floor = 1e-10 * float(ds.model_start.mean())
+    ctx = emc.Context(cfg["N"], ds.q, quat, w, nd, precision="bf16_split", w_floor=floor,
+                      n_cand=M, rot_chunk=8192)
+    ctx.set_frames(torch.as_tensor(ds.K, device="cuda"))
+    ctx.set_candidates(torch.as_tensor(cand, device="cuda"))
+    L, bias = ctx.expand(torch.as_tensor(grid32, device="cuda"), 0, nrot)
+    Pc, lse_c = ctx.sparse_estep(L, bias)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    Pc, lse_c = Pc.cpu().numpy(), lse_c.cpu().numpy()
+    for k in (0, 31337, 99999):
+        W = oracle.expand(grid32.astype(np.float64), quat_o[cand[k]], ds.q, floor)
+        S = oracle.scores(W, w_o[cand[k]], ds.K[k:k + 1].astype(np.float64))
+        P_o, lse_o, _ = oracle.estep(S)
+        assert abs(lse_c[k] - lse_o[0]) <= 1e-4
+        assert np.abs(Pc[k] - P_o[:, 0]).max() <= 1e-4

@@ -271,6 +271,55 @@ def test_pixels_reaching_the_grid_edge(torch_cuda, small_problem, oracle, precis
     assert rel_l2(got.cpu().numpy().astype(np.float64), out) <= 1e-5
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16_split"])
+def test_wide_counts(torch_cuda, small_problem, oracle, precision):
+    # counts above 256 ride on duplicate columns: the iteration equals the
+    # oracle's on the same integer counts, and without the flag they are refused
+    torch, p = torch_cuda, small_problem
+    from paper_1409_4256_gb300 import emc
+    K = p["K"].copy()
+    K[3, 100], K[5, 100], K[8, 200], K[9, 300], K[9, 301] = 700, 300, 1000, 257, 512
+    out_o, _, L_o = oracle.iteration(p["grid"], p["quat"], p["w"], p["q"], K.astype(np.float64),
+                                     p["w_floor"])
+    ctx = emc.Context(p["N"], p["q"], p["quat"], p["w"], K.shape[0], precision=precision,
+                      w_floor=p["w_floor"], wide_counts=True)
+    ctx.set_frames(torch.as_tensor(K, device="cuda"))
+    out, st = ctx.iteration(grid_dev(torch, p))
+    assert st["device_status"] == 0
+    assert rel_l2(out.cpu().numpy().astype(np.float64), out_o) <= 1e-5
+    assert abs(st["loglik"] - L_o) <= 1e-4 * K.shape[0]
+    plain = make_ctx(torch, dict(p, K=K), precision)
+    torch.cuda.synchronize()
+    assert plain.status() == -4
+
+
+def test_wide_counts_gaussian(torch_cuda, small_problem, oracle):
+    torch, p = torch_cuda, small_problem
+    from paper_1409_4256_gb300 import emc
+    K = p["K"].copy()
+    K[3, 100], K[8, 200] = 900, 400
+    out_o, _, _ = oracle.iteration_gauss(p["grid"], p["quat"], p["w"], p["q"],
+                                         K.astype(np.float64), 1.0)
+    ctx = emc.Context(p["N"], p["q"], p["quat"], p["w"], K.shape[0], model="gaussian", sigma=1.0,
+                      wide_counts=True)
+    ctx.set_frames(torch.as_tensor(K, device="cuda"))
+    out, st = ctx.iteration(grid_dev(torch, p))
+    assert st["device_status"] == 0
+    assert rel_l2(out.cpu().numpy().astype(np.float64), out_o) <= 1e-5
+
+
+def test_too_many_duplicate_columns_are_flagged(torch_cuda, small_problem):
+    torch, p = torch_cuda, small_problem
+    from paper_1409_4256_gb300 import emc
+    K = p["K"].copy()
+    K[0, 0] = 256 * 70  # needs 69 duplicate columns, 64 exist
+    ctx = emc.Context(p["N"], p["q"], p["quat"], p["w"], K.shape[0], precision="bf16_split",
+                      w_floor=p["w_floor"], wide_counts=True)
+    ctx.set_frames(torch.as_tensor(K, device="cuda"))
+    torch.cuda.synchronize()
+    assert ctx.status() == -4
+
+
 def test_counts_out_of_range_are_flagged(torch_cuda, small_problem):
     torch, p = torch_cuda, small_problem
     from paper_1409_4256_gb300 import emc
