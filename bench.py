@@ -585,8 +585,11 @@ def run_ours(args):
     # ---- CPU oracle baseline (rank 0, N = 1) --------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle
+        oracle.build()
+        quat_o, w_o = oracle.quat_generate(cfg["n_quat"])  # the oracle's own sampling
         n_rot_s, n_data_s = sample_sizes(cfg, ds, n_rot)
-        v, dt, cores = oracle_sample(cfg, ds, quat, w, n_rot_s, n_data_s)
+        v, dt, cores = oracle_sample(cfg, ds, quat_o, w_o, n_rot_s, n_data_s)
         cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"one FP64 oracle iteration over {n_rot_s} of {n_rot} rotations x "
                          f"{n_data_s} of {n_data} frames ({dt:.1f} s)"}
