@@ -6,6 +6,10 @@
 // g_den with FP64 atomics resolved in L2 (the N^3 FP64 grids, 2 MB at 64^3,
 // stay L2-resident). The paper's insert_slices kernel also used one block
 // per slice. Rotations without responsibility mass (den_j = 0) are skipped.
+// Every slice passes through the centre of the grid, so concurrent CTAs
+// reduce into the same central voxels; with nrep > 1 the CTA of row j uses
+// grid replica j mod nrep (nrep x N^3 per grid, summed by the final division)
+// to spread those reductions over more addresses.
 #include "emc_common.cuh"
 #include "emc_internal.h"
 
@@ -20,8 +24,12 @@ __global__ void __launch_bounds__(kCompressThreads)
     compress_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
                     int64_t ld_pix, int N, const RotDF* __restrict__ rot,
                     const float* __restrict__ Num, const float* __restrict__ den, int mode,
-                    double* __restrict__ g_num, double* __restrict__ g_den) {
+                    double* __restrict__ g_num, double* __restrict__ g_den, int nrep,
+                    int64_t n_vox) {
   const int64_t row = blockIdx.x;
+  const int64_t rep = (row % nrep) * n_vox;
+  g_num += rep;
+  g_den += rep;
   __shared__ RotDF R;
   const float dj = den[row];
   // a rotation without responsibility mass has Num = 0 and den = 0 (both
@@ -76,15 +84,16 @@ __global__ void __launch_bounds__(kCompressThreads)
 }
 
 cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const float* Num,
-                            const float* den, int mode, double* g_num, double* g_den,
+                            const float* den, int mode, double* g_num, double* g_den, int nrep,
                             cudaStream_t s) {
   if (nrot <= 0) return cudaSuccess;
+  const int64_t n_vox = (int64_t)g.N * g.N * g.N;
   if (g.interior)
     compress_kernel<true><<<(unsigned)nrot, kCompressThreads, 0, s>>>(
-        g.qh, g.ql, g.n_pix, g.ld_pix, g.N, rot, Num, den, mode, g_num, g_den);
+        g.qh, g.ql, g.n_pix, g.ld_pix, g.N, rot, Num, den, mode, g_num, g_den, nrep, n_vox);
   else
     compress_kernel<false><<<(unsigned)nrot, kCompressThreads, 0, s>>>(
-        g.qh, g.ql, g.n_pix, g.ld_pix, g.N, rot, Num, den, mode, g_num, g_den);
+        g.qh, g.ql, g.n_pix, g.ld_pix, g.N, rot, Num, den, mode, g_num, g_den, nrep, n_vox);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   int64_t ld_pix, ld_data, rows, chunk_rows, part_tiles;
+  int nrep;  // grid replicas of the fused iterations' compression
   size_t qh, ql, quat, rot, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
       Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, gk, gauss,
       Kb2, skcnt, skoff, skent, dupsrc, duprank, pixmax, total;
@@ -113,8 +114,12 @@ Layout make_layout(const emc_config* c) {
   const int64_t num_rows = c->n_cand > 0 ? y.rows : y.chunk_rows;
   y.Num = take(sizeof(float) * (size_t)num_rows * y.ld_pix);
   y.den = take(sizeof(float) * num_rows);
-  y.gnum = take(sizeof(double) * nvox);
-  y.gden = take(sizeof(double) * nvox);
+  // replicas spread the reductions into the central voxels every slice crosses;
+  // as many as fit 64 MB for both grids, at most 16 (16 measured best at 64^3,
+  // 8 and 32 slower; one for large grids)
+  y.nrep = (int)std::max<int64_t>(1, std::min<int64_t>(16, (64ll << 20) / (16 * nvox)));
+  y.gnum = take(sizeof(double) * nvox * y.nrep);
+  y.gden = take(sizeof(double) * nvox * y.nrep);
   y.scalar = take(256);
   y.fbin = take(sizeof(int16_t) * y.ld_pix);
   y.finv = take(sizeof(float) * kFeat);
@@ -593,8 +598,8 @@ int emc_compress(emc_ctx* ctx, int64_t rot0, int64_t nrot, const float* Num, con
     CU(cudaMemsetAsync(g_num, 0, gb, s));
     CU(cudaMemsetAsync(g_den, 0, gb, s));
   }
-  CU(launch_compress(ctx->geom, ctx->rot + rot0, nrot, Num, den, ctx->cfg.compress_mode,
-                     g_num, g_den, s));
+  CU(launch_compress(ctx->geom, ctx->rot + rot0, nrot, Num, den, ctx->cfg.compress_mode, g_num,
+                     g_den, 1, s));
   return EMC_OK;
 }
 
@@ -602,7 +607,7 @@ int emc_finalize(emc_ctx* ctx, const double* g_num, const double* g_den, const f
                  float* grid_out, emc_stream stream) {
   if (!ctx || !g_num || !g_den || !grid_prev || !grid_out) return EMC_ERR_ARG;
   const int64_t nvox = (int64_t)ctx->cfg.N * ctx->cfg.N * ctx->cfg.N;
-  CU(launch_finalize(nvox, g_num, g_den, grid_prev, grid_out, (cudaStream_t)stream));
+  CU(launch_finalize(nvox, g_num, g_den, 1, grid_prev, grid_out, (cudaStream_t)stream));
   return EMC_OK;
 }
 
@@ -623,7 +628,7 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   double* gn = (double*)(c->ws + y.gnum);
   double* gd = (double*)(c->ws + y.gden);
   double* ll = (double*)(c->ws + y.scalar);
-  const size_t gb = sizeof(double) * (size_t)c->cfg.N * c->cfg.N * c->cfg.N;
+  const size_t gb = sizeof(double) * (size_t)c->cfg.N * c->cfg.N * c->cfg.N * c->lay.nrep;
   int kernels = 0;
   int st;
 
@@ -651,7 +656,8 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     if (stats) CU(cudaEventRecord(c->ev[4], s));
     if ((st = do_update(c, P, crows, nr, Num, den, s))) return st;
     if (stats) CU(cudaEventRecord(c->ev[5], s));
-    CU(launch_compress(c->geom, c->rot + r0, nr, Num, den, c->cfg.compress_mode, gn, gd, s));
+    CU(launch_compress(c->geom, c->rot + r0, nr, Num, den, c->cfg.compress_mode, gn, gd, y.nrep,
+                       s));
     if (stats) CU(cudaEventRecord(c->ev[6], s));
     // normalize: lse split + the pass (one SIMT kernel when recomputing in FP32)
     kernels += (S || c->cfg.precision != EMC_PREC_FP32 ? 2 : 1) + 2;
@@ -668,7 +674,8 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     }
   }
   if (stats) CU(cudaEventRecord(c->ev[3], s));
-  CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, grid_in, grid_out, s));
+  CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, y.nrep, grid_in, grid_out,
+                     s));
   kernels++;
   if (stats) CU(cudaEventRecord(c->ev[7], s));
   c->kernels = kernels;
@@ -829,7 +836,7 @@ int emc_sparse_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_
   double* gn = (double*)(c->ws + y.gnum);
   double* gd = (double*)(c->ws + y.gden);
   double* ll = (double*)(c->ws + y.scalar);
-  const size_t gb = sizeof(double) * (size_t)c->cfg.N * c->cfg.N * c->cfg.N;
+  const size_t gb = sizeof(double) * (size_t)c->cfg.N * c->cfg.N * c->cfg.N * c->lay.nrep;
   int st;
   if (stats) CU(cudaEventRecord(c->ev[0], s));
   if ((st = do_expand(c, grid_in, 0, c->cfg.n_rot, L, bias, s))) return st;
@@ -841,8 +848,10 @@ int emc_sparse_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_
   if (stats) CU(cudaEventRecord(c->ev[3], s));
   CU(cudaMemsetAsync(gn, 0, gb, s));
   CU(cudaMemsetAsync(gd, 0, gb, s));
-  CU(launch_compress(c->geom, c->rot, c->cfg.n_rot, Num, den, c->cfg.compress_mode, gn, gd, s));
-  CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, grid_in, grid_out, s));
+  CU(launch_compress(c->geom, c->rot, c->cfg.n_rot, Num, den, c->cfg.compress_mode, gn, gd,
+                     y.nrep, s));
+  CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, y.nrep, grid_in, grid_out,
+                     s));
   if (stats) CU(cudaEventRecord(c->ev[4], s));
   if (stats) {
     CU(cudaEventSynchronize(c->ev[4]));

@@ -120,10 +120,12 @@ cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const
                              int32_t* status, cudaStream_t s);
 int64_t tc_pass1_tiles(int64_t rows);
 
+// nrep grid replicas of n_vox each (row j reduces into replica j mod nrep)
 cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const float* Num,
-                            const float* den, int mode, double* g_num, double* g_den,
+                            const float* den, int mode, double* g_num, double* g_den, int nrep,
                             cudaStream_t s);
-cudaError_t launch_finalize(int64_t n_vox, const double* g_num, const double* g_den,
+// grid_out = (sum of nrep numerator replicas) / (sum of denominator replicas)
+cudaError_t launch_finalize(int64_t n_vox, const double* g_num, const double* g_den, int nrep,
                             const float* grid_prev, float* grid_out, cudaStream_t s);
 
 // ---- learned proposal (learned.cu) ----

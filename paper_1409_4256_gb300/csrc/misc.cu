@@ -468,18 +468,22 @@ cudaError_t launch_normalize_scores_gauss(const float* S, int64_t ldS, const flo
 
 // Eq. 2.12's final division (the paper's insert_slices_division), over voxels.
 __global__ void finalize_kernel(int64_t n_vox, const double* __restrict__ g_num,
-                                const double* __restrict__ g_den, const float* grid_prev,
-                                float* grid_out) {
+                                const double* __restrict__ g_den, int nrep,
+                                const float* grid_prev, float* grid_out) {
   int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_vox) return;
-  double d = g_den[l];
-  grid_out[l] = d > 0.0 ? (float)(g_num[l] / d) : grid_prev[l];
+  double n = 0.0, d = 0.0;
+  for (int r = 0; r < nrep; r++) {  // the compression's grid replicas
+    n += g_num[r * n_vox + l];
+    d += g_den[r * n_vox + l];
+  }
+  grid_out[l] = d > 0.0 ? (float)(n / d) : grid_prev[l];
 }
 
-cudaError_t launch_finalize(int64_t n_vox, const double* g_num, const double* g_den,
+cudaError_t launch_finalize(int64_t n_vox, const double* g_num, const double* g_den, int nrep,
                             const float* grid_prev, float* grid_out, cudaStream_t s) {
   unsigned blocks = (unsigned)((n_vox + 255) / 256);
-  finalize_kernel<<<blocks, 256, 0, s>>>(n_vox, g_num, g_den, grid_prev, grid_out);
+  finalize_kernel<<<blocks, 256, 0, s>>>(n_vox, g_num, g_den, nrep, grid_prev, grid_out);
   return cudaGetLastError();
 }
 
