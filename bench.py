@@ -67,6 +67,8 @@ def parse_args():
                     help="iterations of the adaptive-sampling schedule")
     ap.add_argument("--sigma", type=float, default=1.0,
                     help="sigma of the Gaussian noise model form (photon units)")
+    ap.add_argument("--learned-sparse-k", type=int, default=1,
+                    help="sparse Maximize reads the frames' non-zero pixel lists (1) or rows (0)")
     ap.add_argument("--n-cand", type=int, default=512, help="candidate rotations per frame")
     ap.add_argument("--recompute", action="store_true",
                     help="two-pass streamed E-step (pass 2 recomputes the scores) instead of "
@@ -275,7 +277,7 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
     floor = 1e-10 * float(ds.model_start.mean())
     ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split", w_floor=floor,
                       store_scores=True, n_cand=M, device=str(grid.device), stream=stream,
-                      rot_chunk=rot_chunk_for(n_rot, n_data))
+                      rot_chunk=rot_chunk_for(n_rot, n_data), sparse_k=args.learned_sparse_k)
     ctx.set_frames(K_dev, stream=stream)
 
     def refresh(net):
@@ -328,7 +330,7 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
     res = {"value": world * n_rot * n_data / (ms * 1e-3), "ms_per_step": ms,
            "ms_sparse_iteration": ms_sparse,
            "evaluated_pairs_per_s": world * M * n_data / (ms_sparse * 1e-3),
-           "candidates": M, "dense_top_kept": R,
+           "candidates": M, "dense_top_kept": R, "frames_as_nonzero_lists": bool(args.learned_sparse_k),
            "schedule": "4 sparse + 1 dense per 5 iterations; candidates = dense top 32 + "
                        "network's best others, refreshed at every dense step",
            "train_loss_first_last": [hist[0], hist[-1]],

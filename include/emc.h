@@ -109,7 +109,10 @@ typedef enum emc_compress_mode {
 #define EMC_FLAG_SPARSE_K 2     /* emc_set_frames also lists every frame's
                                    non-zero pixels (n_data x n_pix x 4 B of
                                    workspace at most) for emc_loglik_sparse_k;
-                                   needs n_pix <= 65536 */
+                                   the sparse Maximize (emc_sparse_estep,
+                                   emc_sparse_update) then reads those lists
+                                   instead of the frames' rows. Needs
+                                   n_pix <= 65536 */
 
 typedef struct emc_config {
   int32_t N;             /* grid side, 4 <= N <= 1024 */
@@ -162,7 +165,9 @@ const char* emc_status_string(int status);
  * divided n times gives M_rot = 10 (5 n^3 + n) rotations, q ~ -q identified.
  * emc_quat_count returns that number (or -1 for n < 1).
  * emc_quat_generate writes unit quaternions quat[cap][4] (host, w first,
- * first non-zero component positive, sorted by round(q * 2^30)) and prior
+ * first non-zero component positive; ordered along a space-filling curve:
+ * by the 30-bit Morton code of the top 10 bits of round(q_c * 2^30) + 2^30
+ * for c = x, y, z, ties by round(q * 2^30) lexicographically) and prior
  * weights weight[cap] (host, sum 1; w_j ~ 1/|x_j|^4 for the flat lattice point
  * x_j, or equal weights when uniform != 0). Returns the count written, or a
  * negative emc_status (EMC_ERR_ARG if cap is too small). */

@@ -128,13 +128,29 @@ static int cmp_key8(const void* x, const void* y) {
 
 typedef struct {
   int64_t key[4];
+  uint64_t z;  /* Morton code of the (x, y, z) keys, the primary order */
   double q[4];
   double w;
 } qrec;
 
+/* interleave the top 10 bits of key + 2^30 of x, y, z (bit b of axis d goes to
+ * bit 3 b + d) */
+static uint64_t morton_xyz(const int64_t* key) {
+  uint64_t z = 0;
+  for (int d = 0; d < 3; d++) {
+    int64_t u = (key[1 + d] + ((int64_t)1 << 30)) / ((int64_t)1 << 21);
+    if (u < 0) u = 0;
+    if (u > 1023) u = 1023;
+    for (int b = 0; b < 10; b++)
+      if ((u >> b) & 1) z |= (uint64_t)1 << (3 * b + d);
+  }
+  return z;
+}
+
 static int cmp_qrec(const void* x, const void* y) {
   const qrec* a = (const qrec*)x;
   const qrec* b = (const qrec*)y;
+  if (a->z != b->z) return a->z < b->z ? -1 : 1;
   for (int t = 0; t < 4; t++) {
     if (a->key[t] < b->key[t]) return -1;
     if (a->key[t] > b->key[t]) return 1;
@@ -168,8 +184,10 @@ long oracle_600cell_counts(long* n_vertices, long* n_edges) {
  * into quat[cap][4] and prior weights (sum 1) into weight[cap]; either may be
  * NULL to count only. uniform != 0 gives equal weights. Returns the number of
  * rotations, or -1 on allocation failure, -2 if cap is too small.
- * Order: q canonicalised so that its first non-zero component is positive,
- * then sorted lexicographically by round(q_c * 2^30).
+ * Order (a convention shared with the library, not the paper's): q
+ * canonicalised so that its first non-zero component is positive;
+ * k_c = round(q_c * 2^30); sorted by the Morton code of the top 10 bits of
+ * k_x + 2^30, k_y + 2^30, k_z + 2^30, ties by (k_w, k_x, k_y, k_z).
  */
 long oracle_quat_generate(int n, int uniform, double* quat, double* weight, long cap) {
   if (n < 1) return -1;
@@ -242,6 +260,7 @@ long oracle_quat_generate(int n, int uniform, double* quat, double* weight, long
       R->q[t] = x[t] / r;
       R->key[t] = llround(R->q[t] * 1073741824.0);
     }
+    R->z = morton_xyz(R->key);
     R->w = uniform ? 1.0 : 1.0 / (r2 * r2);
     nr++;
   }

@@ -804,9 +804,11 @@ int emc_sparse_estep(emc_ctx* ctx, const void* L, const double* bias, float* P, 
   const int M = ctx->cfg.n_cand;
   Planes lp{(void*)L, y.rows * y.ld_pix, y.ld_pix};
   double* Sc = (double*)(ctx->ws + y.Sc);
+  const bool csr = (ctx->cfg.flags & EMC_FLAG_SPARSE_K) != 0;  // frames' non-zero lists
   CU(launch_sparse_scores(lp, ctx->cfg.precision, y.rows, bias, ctx->Kb, y.ld_pix,
-                          (const int64_t*)(ctx->ws + y.coff), (const int2*)(ctx->ws + y.cent), M, Sc,
-                          s));
+                          (const int64_t*)(ctx->ws + y.coff), (const int2*)(ctx->ws + y.cent), M,
+                          csr ? (const int64_t*)(ctx->ws + y.skoff) : nullptr,
+                          csr ? (const uint32_t*)(ctx->ws + y.skent) : nullptr, Sc, s));
   CU(launch_sparse_lse(Sc, ctx->cfg.n_data, y.ld_data, M, P, lse, ctx->status, s));
   return EMC_OK;
 }
@@ -814,9 +816,12 @@ int emc_sparse_estep(emc_ctx* ctx, const void* L, const double* bias, float* P, 
 int emc_sparse_update(emc_ctx* ctx, const float* P, float* Num, float* den, emc_stream stream) {
   if (!ctx || !P || !Num || !den || !ctx->frames_loaded || !ctx->cand_loaded) return EMC_ERR_ARG;
   const Layout& y = ctx->lay;
+  const bool csr = (ctx->cfg.flags & EMC_FLAG_SPARSE_K) != 0;  // frames' non-zero lists
   CU(launch_sparse_update(ctx->Kb, ctx->cfg.precision == EMC_PREC_FP16_SPLIT, y.ld_pix,
                           ctx->cfg.n_pix, (const int64_t*)(ctx->ws + y.coff),
-                          (const int2*)(ctx->ws + y.cent), ctx->cfg.n_cand, P, y.rows, Num, den,
+                          (const int2*)(ctx->ws + y.cent), ctx->cfg.n_cand, P, y.rows,
+                          csr ? (const int64_t*)(ctx->ws + y.skoff) : nullptr,
+                          csr ? (const uint32_t*)(ctx->ws + y.skent) : nullptr, Num, den,
                           (cudaStream_t)stream));
   return EMC_OK;
 }

@@ -162,14 +162,18 @@ cudaError_t launch_merge_candidates(const int32_t* first, int R, const int32_t* 
 cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t n_rot,
                              int64_t rows, int32_t* cnt, int64_t* off, int2* ent,
                              int32_t* status, cudaStream_t s);
+// koff/kent (non-NULL): the frames' non-zero pixel lists (EMC_FLAG_SPARSE_K)
+// replace their dense rows in both sparse contractions
 cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, const double* bias,
                                  const uint16_t* Kb, int64_t ld_pix, const int64_t* off,
-                                 const int2* ent, int M, double* Sc, cudaStream_t s);
+                                 const int2* ent, int M, const int64_t* koff,
+                                 const uint32_t* kent, double* Sc, cudaStream_t s);
 cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data, int M, float* Pc,
                               double* lse_c, int32_t* status, cudaStream_t s);
 cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
                                  const int64_t* off, const int2* ent, int M, const float* Pc,
-                                 int64_t rows, float* Num, float* den, cudaStream_t s);
+                                 int64_t rows, const int64_t* koff, const uint32_t* kent,
+                                 float* Num, float* den, cudaStream_t s);
 cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, int64_t ld_data,
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
                                float* missed, cudaStream_t s);

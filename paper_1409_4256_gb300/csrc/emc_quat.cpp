@@ -13,8 +13,11 @@
 // the flat point x_j; weights are normalised to sum 1.
 //
 // Output order (an interface convention): sign fixed so that the first
-// non-zero component is positive, then sorted by round(q_c * 2^30),
-// lexicographically over (w, x, y, z).
+// non-zero component is positive; k_c = round(q_c * 2^30); sorted by the
+// 30-bit Morton code of the top 10 bits of k_x + 2^30, k_y + 2^30, k_z + 2^30
+// (a space-filling curve through the rotations, so that consecutive indices --
+// and 128-rotation tiles -- cover compact regions of SO(3)), ties broken by
+// (k_w, k_x, k_y, k_z) lexicographically.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -104,6 +107,7 @@ int64_t quat_generate(int n, int uniform, double* quat, double* weight, int64_t 
 
   struct Rec {
     std::array<int64_t, 4> key;
+    uint64_t code;
     V4 q;
     double w;
   };
@@ -139,7 +143,19 @@ int64_t quat_generate(int n, int uniform, double* quat, double* weight, int64_t 
           rec.w = uniform ? 1.0 : 1.0 / (r2 * r2);
           out.push_back(rec);
         }
-  std::sort(out.begin(), out.end(), [](const Rec& a, const Rec& b) { return a.key < b.key; });
+  auto morton = [](const std::array<int64_t, 4>& k) {
+    uint64_t code = 0;
+    for (int d = 0; d < 3; d++) {
+      int64_t u = (k[1 + d] + (int64_t(1) << 30)) >> 21;  // 10 bits of [0, 2^31]
+      u = u < 0 ? 0 : (u > 1023 ? 1023 : u);
+      for (int b = 0; b < 10; b++) code |= (uint64_t)((u >> b) & 1) << (3 * b + d);
+    }
+    return code;
+  };
+  for (Rec& r : out) r.code = morton(r.key);
+  std::sort(out.begin(), out.end(), [](const Rec& a, const Rec& b) {
+    return a.code != b.code ? a.code < b.code : a.key < b.key;
+  });
   const int64_t count = (int64_t)out.size();
   if (quat == nullptr && weight == nullptr) return count;
   if (count > cap) return EMC_ERR_ARG;

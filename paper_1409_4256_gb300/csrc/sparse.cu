@@ -279,11 +279,16 @@ __device__ __forceinline__ void unpack2(uint32_t w, float& lo, float& hi) {
 // One CTA per rotation row: log W_j split into (hi on the 1/8 grid, rest) in
 // shared memory; each warp takes pairs (frame, slot) of the row's list, two
 // at a time, reading the frames' K rows 8 pixels (16 bytes) per lane.
-template <int PREC>
+// CSR: the frames' non-zero pixel lists (pixel | count << 16, EMC_FLAG_SPARSE_K)
+// are read instead of their rows -- 4 bytes per non-zero pixel rather than 2
+// bytes per pixel -- and gathered against the staged row; the count x hi sums
+// stay exact (integral counts, hi on the 1/8 grid, frame totals below 2^16).
+template <int PREC, bool CSR>
 __global__ void __launch_bounds__(256)
     sparse_scores_kernel(const void* __restrict__ L, int64_t plane_stride, int64_t ld_pix,
                          const double* __restrict__ bias, const uint16_t* __restrict__ Kb,
                          const int64_t* __restrict__ off, const int2* __restrict__ ent, int M,
+                         const int64_t* __restrict__ koff, const uint32_t* __restrict__ kent,
                          double* __restrict__ Sc) {
   const int64_t j = blockIdx.x;
   const int64_t e0 = off[j], e1 = off[j + 1];
@@ -313,6 +318,26 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const double bj = bias[j];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (CSR) {
+    for (int64_t e = e0 + wid; e < e1; e += nw) {
+      const int2 km = ent[e];
+      const int64_t f1 = koff[km.x + 1];
+      float ah = 0.f, ar = 0.f;
+      for (int64_t f = koff[km.x] + lane; f < f1; f += 32) {
+        const uint32_t w = kent[f];
+        const int idx = (int)(w & 0xffffu);
+        const float c = (float)(w >> 16);
+        ah = fmaf(c, Lh[idx], ah);
+        ar = fmaf(c, Lr[idx], ar);
+      }
+      for (int o = 16; o; o >>= 1) {
+        ah += __shfl_xor_sync(0xffffffffu, ah, o);
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      }
+      if (lane == 0) Sc[(int64_t)km.x * M + km.y] = ((double)ah + (double)ar) + bj;
+    }
+    return;
+  }
   const int64_t n8 = ld_pix / 8;
   for (int64_t e = e0 + 2 * wid; e < e1; e += 2 * nw) {
     const bool two = e + 1 < e1;
@@ -459,6 +484,45 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// CSR form of the sparse update: the row Num_j accumulates in shared memory
+// (FP32 atomics; a frame's non-zero pixels are distinct) from every pair's
+// P_jk times the frame's non-zero counts, then is written out whole with
+// den_j = sum of the row's P_jk. Rows without pairs are zeroed.
+__global__ void __launch_bounds__(256)
+    sparse_update_csr_kernel(const int64_t* __restrict__ koff, const uint32_t* __restrict__ kent,
+                             int64_t ld_pix, const int64_t* __restrict__ off,
+                             const int2* __restrict__ ent, int M, const float* __restrict__ Pc,
+                             float* __restrict__ Num, float* __restrict__ den) {
+  const int64_t j = blockIdx.x;
+  const int64_t e0 = off[j], e1 = off[j + 1];
+  extern __shared__ float4 sm4u[];
+  float* srow = reinterpret_cast<float*>(sm4u);
+  __shared__ float sden[8];
+  for (int64_t i = threadIdx.x; i < ld_pix; i += blockDim.x) srow[i] = 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float dsum = 0.f;
+  for (int64_t e = e0 + wid; e < e1; e += nw) {
+    const int2 km = ent[e];
+    const float p = Pc[(int64_t)km.x * M + km.y];
+    dsum += p;
+    const int64_t f1 = koff[km.x + 1];
+    for (int64_t f = koff[km.x] + lane; f < f1; f += 32) {
+      const uint32_t w = kent[f];
+      atomicAdd(&srow[w & 0xffffu], p * (float)(w >> 16));
+    }
+  }
+  if (lane == 0) sden[wid] = dsum;
+  __syncthreads();
+  float* out = Num + j * ld_pix;
+  for (int64_t i = threadIdx.x; i < ld_pix; i += blockDim.x) out[i] = srow[i];
+  if (threadIdx.x == 0) {
+    float d = 0.f;
+    for (int w = 0; w < nw; w++) d += sden[w];
+    den[j] = d;
+  }
+}
+
 // 1 - sum_{j in C_k} P_jk of a dense E-step, from its stored scores.
 __global__ void missed_mass_kernel(const float* __restrict__ S, int64_t ldS,
                                    const float* __restrict__ Sref, int64_t ld_data, const float2* __restrict__ lse2,
@@ -478,39 +542,30 @@ __global__ void missed_mass_kernel(const float* __restrict__ S, int64_t ldS,
 
 cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, const double* bias,
                                  const uint16_t* Kb, int64_t ld_pix, const int64_t* off,
-                                 const int2* ent, int M, double* Sc, cudaStream_t s) {
+                                 const int2* ent, int M, const int64_t* koff,
+                                 const uint32_t* kent, double* Sc, cudaStream_t s) {
   const size_t smem = 2 * sizeof(float) * (size_t)ld_pix;
-  cudaError_t e;
-  switch (precision) {
-    case EMC_PREC_FP32:
-      e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_FP32>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      sparse_scores_kernel<EMC_PREC_FP32><<<(unsigned)rows, 256, smem, s>>>(
-          L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
-      break;
-    case EMC_PREC_BF16:
-      e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_BF16>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      sparse_scores_kernel<EMC_PREC_BF16><<<(unsigned)rows, 256, smem, s>>>(
-          L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
-      break;
-    case EMC_PREC_FP16_SPLIT:
-      e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_FP16_SPLIT>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      sparse_scores_kernel<EMC_PREC_FP16_SPLIT><<<(unsigned)rows, 256, smem, s>>>(
-          L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
-      break;
-    default:
-      e = cudaFuncSetAttribute(sparse_scores_kernel<EMC_PREC_BF16_SPLIT>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      sparse_scores_kernel<EMC_PREC_BF16_SPLIT><<<(unsigned)rows, 256, smem, s>>>(
-          L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, Sc);
-      break;
+  cudaError_t e = cudaSuccess;
+#define EMC_SPARSE_SCORES(P, C)                                                              \
+  e = cudaFuncSetAttribute(sparse_scores_kernel<P, C>,                                       \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+  if (e != cudaSuccess) return e;                                                            \
+  sparse_scores_kernel<P, C><<<(unsigned)rows, 256, smem, s>>>(                              \
+      L.base, L.plane_stride, ld_pix, bias, Kb, off, ent, M, koff, kent, Sc)
+#define EMC_SPARSE_SCORES_P(P)      \
+  if (kent) {                       \
+    EMC_SPARSE_SCORES(P, true);     \
+  } else {                          \
+    EMC_SPARSE_SCORES(P, false);    \
   }
+  switch (precision) {
+    case EMC_PREC_FP32: EMC_SPARSE_SCORES_P(EMC_PREC_FP32); break;
+    case EMC_PREC_BF16: EMC_SPARSE_SCORES_P(EMC_PREC_BF16); break;
+    case EMC_PREC_FP16_SPLIT: EMC_SPARSE_SCORES_P(EMC_PREC_FP16_SPLIT); break;
+    default: EMC_SPARSE_SCORES_P(EMC_PREC_BF16_SPLIT); break;
+  }
+#undef EMC_SPARSE_SCORES_P
+#undef EMC_SPARSE_SCORES
   return cudaGetLastError();
 }
 
@@ -523,7 +578,17 @@ cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data,
 
 cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
                                  const int64_t* off, const int2* ent, int M, const float* Pc,
-                                 int64_t rows, float* Num, float* den, cudaStream_t s) {
+                                 int64_t rows, const int64_t* koff, const uint32_t* kent,
+                                 float* Num, float* den, cudaStream_t s) {
+  if (kent) {
+    const size_t smem = sizeof(float) * (size_t)ld_pix;
+    cudaError_t e = cudaFuncSetAttribute(sparse_update_csr_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sparse_update_csr_kernel<<<(unsigned)rows, 256, smem, s>>>(koff, kent, ld_pix, off, ent, M, Pc,
+                                                               Num, den);
+    return cudaGetLastError();
+  }
   if (kf16)
     sparse_update_kernel<true><<<(unsigned)rows, 256, 0, s>>>(Kb, ld_pix, n_pix, off, ent, M, Pc,
                                                               Num, den);

@@ -34,10 +34,11 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-def ctx_for(torch, p, precision="bf16_split", n_cand=0, store_scores=False):
+def ctx_for(torch, p, precision="bf16_split", n_cand=0, store_scores=False, sparse_k=False):
     from paper_1409_4256_gb300 import emc
     c = emc.Context(p["N"], p["q"], p["quat"], p["w"], p["K"].shape[0], precision=precision,
-                    w_floor=p["w_floor"], n_cand=n_cand, store_scores=store_scores)
+                    w_floor=p["w_floor"], n_cand=n_cand, store_scores=store_scores,
+                    sparse_k=sparse_k)
     c.set_frames(torch.as_tensor(p["K"], device="cuda"))
     return c
 
@@ -178,14 +179,16 @@ def _candidates(dense_ref, M, seed=8):
     return np.array(out, dtype=np.int32)
 
 
+@pytest.mark.parametrize("sparse_k", [False, True])
 @pytest.mark.parametrize("precision", ["fp32", "bf16_split", "fp16_split"])
-def test_sparse_steps(torch_cuda, small_problem, dense_ref, precision):
+def test_sparse_steps(torch_cuda, small_problem, dense_ref, precision, sparse_k):
+    # sparse_k: the frames' non-zero pixel lists replace their rows
     from oracle import learned as ol
     torch, p = torch_cuda, small_problem
     M = 96
     cand = _candidates(dense_ref, M)
     nrot, nd = p["quat"].shape[0], p["K"].shape[0]
-    ctx = ctx_for(torch, p, precision, n_cand=M)
+    ctx = ctx_for(torch, p, precision, n_cand=M, sparse_k=sparse_k)
     ctx.set_candidates(torch.as_tensor(cand, device="cuda"))
     L, bias = ctx.expand(torch.as_tensor(p["grid"].astype(np.float32), device="cuda"), 0, nrot)
     P, lse = ctx.sparse_estep(L, bias)
@@ -201,7 +204,8 @@ def test_sparse_steps(torch_cuda, small_problem, dense_ref, precision):
     assert rel_l2(den.cpu().numpy()[:nrot], dr) <= 1e-4
 
 
-def test_sparse_iteration_matches_oracle(torch_cuda, small_problem, dense_ref, oracle):
+@pytest.mark.parametrize("sparse_k", [False, True])
+def test_sparse_iteration_matches_oracle(torch_cuda, small_problem, dense_ref, oracle, sparse_k):
     from oracle import learned as ol
     torch, p = torch_cuda, small_problem
     M = 96
@@ -210,7 +214,7 @@ def test_sparse_iteration_matches_oracle(torch_cuda, small_problem, dense_ref, o
     Pr, _ = ol.sparse_estep(dense_ref["S"], cand)
     Nr, dr = ol.sparse_mstep(Pr, cand, p["K"], nrot)
     want, _, _ = oracle.compress(p["N"], p["quat"], p["q"], Nr, dr, p["grid"])
-    ctx = ctx_for(torch, p, "bf16_split", n_cand=M)
+    ctx = ctx_for(torch, p, "bf16_split", n_cand=M, sparse_k=sparse_k)
     ctx.set_candidates(torch.as_tensor(cand, device="cuda"))
     out, st = ctx.sparse_iteration(torch.as_tensor(p["grid"].astype(np.float32), device="cuda"))
     assert st["device_status"] == 0
