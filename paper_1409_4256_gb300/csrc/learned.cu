@@ -8,8 +8,13 @@
 // (Eq. 2.4), so that the Maximize step can run over its top-M rotations only.
 //
 // Matrix products use BF16-rounded operands with FP32 accumulation ("BF16
-// matmuls, FP32 master weights"), in a tiled SIMT kernel that serves the three
-// layouts training needs (X W, dY W^T, X^T dY). Parameters live in one FP32
+// matmuls, FP32 master weights"). The output layer (512 x n_out, nearly all
+// of the work) runs on the tensor cores through the update form of the
+// tcgen05 kernel (K-major A, MN-major B, FP32 rows out): Z = H3 W4,
+// dH3 = dZ (W4^T) and dW4 = (H3^T) dZ, from BF16 copies (W4, its transpose,
+// H3^T, dZ) made by the kernels below, whenever the batch is a multiple of
+// 128. The 512 x 512 layers and other batches use a tiled SIMT kernel that
+// serves the three layouts (X W, dY W^T, X^T dY). Parameters live in one FP32
 // array: W1[512][512] b1[512] W2 b2 W3 b3 W4[512][ld_out] b4[ld_out],
 // ld_out = round_up(n_out, 64).
 #include "emc_common.cuh"
@@ -140,6 +145,49 @@ cudaError_t gemm(int M, int N, int K, const float* A, int64_t lda, const float* 
   return cudaGetLastError();
 }
 
+// ------------------------------------------- BF16 operands for the tcgen05 --
+__global__ void to_bf16_kernel(const float* __restrict__ src, int64_t n, uint16_t* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = bf16_bits(src[i]);
+}
+
+// dst[c][r] = bf16(src[r][c]) for r < rows, c < cols (32 x 32 tiles through
+// shared memory; rows and cols multiples of 32)
+__global__ void transpose_bf16_kernel(const float* __restrict__ src, int64_t ld_src, int64_t rows,
+                                      int64_t cols, uint16_t* __restrict__ dst, int64_t ld_dst) {
+  __shared__ float t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) t[k][tx] = src[(r0 + k) * ld_src + c0 + tx];
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) dst[(c0 + k) * ld_dst + r0 + tx] = bf16_bits(t[tx][k]);
+}
+
+__global__ void add_bias_kernel(float* __restrict__ Z, int64_t ld, int64_t rows, int64_t cols,
+                                const float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows * cols) Z[(i / cols) * ld + i % cols] += b[i % cols];
+}
+
+cudaError_t to_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t s) {
+  to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, dst);
+  return cudaGetLastError();
+}
+cudaError_t transpose_bf16(const float* src, int64_t ld_src, int64_t rows, int64_t cols,
+                           uint16_t* dst, int64_t ld_dst, cudaStream_t s) {
+  dim3 grid((unsigned)(cols / 32), (unsigned)(rows / 32));
+  transpose_bf16_kernel<<<grid, 256, 0, s>>>(src, ld_src, rows, cols, dst, ld_dst);
+  return cudaGetLastError();
+}
+
+// C[M][N] (FP32, row stride N) = A[M][K] (BF16, K contiguous) B[K][N] (BF16, N
+// contiguous) on the tensor cores; M multiple of 128, K and N multiples of 64
+cudaError_t tc_gemm(const uint16_t* A, int64_t M, int64_t K, const uint16_t* B, int64_t N,
+                    float* C, int32_t* status, cudaStream_t s) {
+  Planes pa{const_cast<uint16_t*>(A), M * K, K};
+  return launch_tc_update(pa, EMC_PREC_BF16, M, B, K, N, INT64_MAX, C, nullptr, status, s);
+}
+
 // ------------------------------------------------- loss and its gradient --
 // Row b of z (n_out logits, stride ld): lse = log sum_j exp(z_j); loss
 // += -sum_r p_r (z_{idx_r} - lse) / B; z is overwritten by
@@ -242,9 +290,13 @@ MlpLayout mlp_layout(int64_t n_out, int64_t B) {
   y.b[3] = o;
   o += y.ld_out;
   y.n_params = o;
-  // work: pre-activations a[3], activations h[3], dh, da (each B x 512), z / dz (B x ld_out)
+  // work: pre-activations a[3], activations h[3], dh, da (each B x 512), z / dz (B x ld_out),
+  // then the tensor-core path's BF16 copies: H3 [B][512], H3^T [512][B], dZ [B][ld_out],
+  // W4 [512][ld_out], W4^T [ld_out][512], each from a 256-byte boundary
   y.B = B;
-  y.work_floats = 8 * B * H + B * y.ld_out;
+  auto up64 = [](int64_t n) { return (n + 63) / 64 * 64; };  // floats to 256 bytes
+  y.work_floats = up64(8 * B * H + B * y.ld_out) + up64(B * H / 2) + up64(B * H / 2) +
+                  up64(B * y.ld_out / 2) + 2 * up64(H * y.ld_out / 2);
   return y;
 }
 
@@ -255,17 +307,30 @@ struct Work {
   float* dh;
   float* da;
   float* z;
+  uint16_t *h3b, *h3t, *dzb, *w4b, *w4t;  // BF16 operands of the tensor-core products
 };
 Work carve(const MlpLayout& y, float* w) {
   Work k;
-  const int64_t BH = y.B * kFeat;
+  const int64_t H = kFeat, BH = y.B * H;
+  auto up64 = [](int64_t n) { return (n + 63) / 64 * 64; };
   for (int l = 0; l < 3; l++) k.a[l] = w + l * BH;
   for (int l = 0; l < 3; l++) k.h[l] = w + (3 + l) * BH;
   k.dh = w + 6 * BH;
   k.da = w + 7 * BH;
   k.z = w + 8 * BH;
+  float* o = w + up64(8 * BH + y.B * y.ld_out);
+  k.h3b = reinterpret_cast<uint16_t*>(o);
+  o += up64(BH / 2);
+  k.h3t = reinterpret_cast<uint16_t*>(o);
+  o += up64(BH / 2);
+  k.dzb = reinterpret_cast<uint16_t*>(o);
+  o += up64(y.B * y.ld_out / 2);
+  k.w4b = reinterpret_cast<uint16_t*>(o);
+  o += up64(H * y.ld_out / 2);
+  k.w4t = reinterpret_cast<uint16_t*>(o);
   return k;
 }
+bool tc_batch(int B) { return B >= 128 && B % 128 == 0; }
 }  // namespace
 
 cudaError_t mlp_forward(const MlpLayout& y, const float* params, const float* X, int B,
@@ -280,8 +345,17 @@ cudaError_t mlp_forward(const MlpLayout& y, const float* params, const float* X,
     if (e != cudaSuccess) return e;
     in = w.h[l];
   }
-  return gemm<false, false, 1>(B, (int)y.n_out, H, in, H, params + y.W[3], y.ld_out, logits,
-                               y.ld_out, params + y.b[3], nullptr, 0, s);
+  if (!tc_batch(B))
+    return gemm<false, false, 1>(B, (int)y.n_out, H, in, H, params + y.W[3], y.ld_out, logits,
+                                 y.ld_out, params + y.b[3], nullptr, 0, s);
+  // output layer on the tensor cores: logits = bf16(H3) bf16(W4) + b4
+  if ((e = to_bf16(in, (int64_t)B * H, w.h3b, s)) != cudaSuccess) return e;
+  if ((e = to_bf16(params + y.W[3], (int64_t)H * y.ld_out, w.w4b, s)) != cudaSuccess) return e;
+  if ((e = tc_gemm(w.h3b, B, H, w.w4b, y.ld_out, logits, nullptr, s)) != cudaSuccess) return e;
+  const int64_t n = (int64_t)B * y.n_out;
+  add_bias_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(logits, y.ld_out, B, y.n_out,
+                                                            params + y.b[3]);
+  return cudaGetLastError();
 }
 
 cudaError_t mlp_train_step(const MlpLayout& y, float* params, float* grads, float* adam_m,
@@ -301,14 +375,31 @@ cudaError_t mlp_train_step(const MlpLayout& y, float* params, float* grads, floa
   for (int l = 3; l >= 0; l--) {
     const float* in = l == 0 ? X : w.h[l - 1];
     const int64_t ldw = l == 3 ? y.ld_out : H;
-    e = gemm<true, false, 0>(H, ncol, B, in, H, g, ldg, grads + y.W[l], ldw, nullptr, nullptr, 0, s);
-    if (e != cudaSuccess) return e;
+    const bool tc = l == 3 && tc_batch(B);
+    if (tc) {
+      // dW4 = bf16(H3)^T bf16(dZ) and dH3 = bf16(dZ) bf16(W4)^T on the tensor cores
+      // (the whole padded width: dZ is 0 beyond n_out)
+      if ((e = to_bf16(g, (int64_t)B * y.ld_out, w.dzb, s)) != cudaSuccess) return e;
+      if ((e = transpose_bf16(in, H, B, H, w.h3t, B, s)) != cudaSuccess) return e;
+      if ((e = tc_gemm(w.h3t, H, B, w.dzb, y.ld_out, grads + y.W[3], nullptr, s)) != cudaSuccess)
+        return e;
+    } else {
+      e = gemm<true, false, 0>(H, ncol, B, in, H, g, ldg, grads + y.W[l], ldw, nullptr, nullptr,
+                               0, s);
+      if (e != cudaSuccess) return e;
+    }
     colsum_kernel<<<(ncol + 255) / 256, 256, 0, s>>>(g, B, ncol, ldg, grads + y.b[l]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (l == 0) break;
-    e = gemm<false, true, 0>(B, H, ncol, g, ldg, params + y.W[l], ldw, w.dh, H, nullptr, nullptr,
-                             0, s);
-    if (e != cudaSuccess) return e;
+    if (tc) {
+      if ((e = transpose_bf16(params + y.W[3], y.ld_out, H, y.ld_out, w.w4t, H, s)) != cudaSuccess)
+        return e;
+      if ((e = tc_gemm(w.dzb, B, y.ld_out, w.w4t, H, w.dh, nullptr, s)) != cudaSuccess) return e;
+    } else {
+      e = gemm<false, true, 0>(B, H, ncol, g, ldg, params + y.W[l], ldw, w.dh, H, nullptr,
+                               nullptr, 0, s);
+      if (e != cudaSuccess) return e;
+    }
     const int64_t n = (int64_t)B * H;
     gelu_backward_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.dh, w.a[l - 1], w.da, n);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -73,11 +73,13 @@ def _oracle_params(torch, prop):
     return ps
 
 
-def test_mlp_forward_and_gradients(torch_cuda):
+@pytest.mark.parametrize("B", [64, 128])
+def test_mlp_forward_and_gradients(torch_cuda, B):
+    # B = 64: SIMT products; B = 128: the output layer on the tensor cores
     from oracle import learned as ol
     from paper_1409_4256_gb300 import emc, learned
     torch = torch_cuda
-    n_out, B, R = 300, 64, 8
+    n_out, R = 300, 8
     prop = learned.Proposal(n_out)
     rng = np.random.default_rng(5)
     X = rng.uniform(0, 2, size=(B, 512)).astype(np.float32)
