@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kCompressThreads)
     rotate_to_grid(R, a, b, half_n, f, t);
     const float v = Nr[i] * inv_d;
     const float dvi = a.w == 1.f ? dv : 0.f;
-    if (INTERIOR) {
+    if constexpr (INTERIOR) {
       const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
       const int nn32 = N * N;
       const int base = f[0] * nn32 + f[1] * N + f[2];
@@ -66,19 +66,19 @@ __global__ void __launch_bounds__(kCompressThreads)
         atomicAdd(g_num + l, (double)(w * v));
         if (dvi != 0.f) atomicAdd(g_den + l, (double)(w * dvi));
       }
-      continue;
-    }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 8; c++) {
-      int x = f[0] + ((c >> 2) & 1), y = f[1] + ((c >> 1) & 1), z = f[2] + (c & 1);
-      if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= N) continue;
-      float w = (((c >> 2) & 1) ? t[0] : 1.f - t[0]) * (((c >> 1) & 1) ? t[1] : 1.f - t[1]) *
-                ((c & 1) ? t[2] : 1.f - t[2]);
-      if (w == 0.f) continue;
-      int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
-      // FP32 products (relative error 6e-8), FP64 accumulation in L2
-      atomicAdd(g_num + l, (double)(w * v));
-      if (dvi != 0.f) atomicAdd(g_den + l, (double)(w * dvi));
+      for (int c = 0; c < 8; c++) {
+        int x = f[0] + ((c >> 2) & 1), y = f[1] + ((c >> 1) & 1), z = f[2] + (c & 1);
+        if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= N) continue;
+        float w = (((c >> 2) & 1) ? t[0] : 1.f - t[0]) * (((c >> 1) & 1) ? t[1] : 1.f - t[1]) *
+                  ((c & 1) ? t[2] : 1.f - t[2]);
+        if (w == 0.f) continue;
+        int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
+        // FP32 products (relative error 6e-8), FP64 accumulation in L2
+        atomicAdd(g_num + l, (double)(w * v));
+        if (dvi != 0.f) atomicAdd(g_den + l, (double)(w * dvi));
+      }
     }
   }
 }
