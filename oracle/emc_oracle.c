@@ -601,6 +601,87 @@ double oracle_iteration_gauss(int N, const double* grid, long n_rot, const doubl
   return L;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Poisson model with a per-(j,k) fluence (the 160^3 workload's frames carry a  */
+/* random intensity scale). Reading: the fluence is the Poisson maximum        */
+/* likelihood phi_jk = N_k / sum_i W_ij (N_k = sum_i K_ik), evaluated on the    */
+/* current model, so each rotation is scored at its best scale; the M-step     */
+/* divides the frames by it as Eq. 2.11 does. The per-frame constant           */
+/* N_k log N_k - N_k that appears with it is left out of the scores, like      */
+/* log K!, since it cancels in Eq. 2.4. An empty frame has phi = 0.           */
+/* ------------------------------------------------------------------------ */
+
+/* 1/phi_jk = sum_i W_ij / N_k (0 for an empty frame) */
+void oracle_fluence_poisson(long n_rot, long n_pix, long n_data, const double* W, const double* K,
+                            double* inv_phi) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long j = 0; j < n_rot; j++) {
+    double sw = 0.0;
+    for (long i = 0; i < n_pix; i++) sw += W[j * n_pix + i];
+    for (long k = 0; k < n_data; k++) {
+      double nk = 0.0;
+      for (long i = 0; i < n_pix; i++) nk += K[k * n_pix + i];
+      inv_phi[j * n_data + k] = nk > 0.0 ? sw / nk : 0.0;
+    }
+  }
+}
+
+/*
+ * S_jk = sum_i (K_ik log(phi_jk W_ij) - phi_jk W_ij) + log w_j
+ *        - (N_k log N_k - N_k)
+ */
+void oracle_scores_poisson_fluence(long n_rot, long n_pix, long n_data, const double* W,
+                                   const double* weight, const double* K,
+                                   const double* inv_phi, double* S) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long j = 0; j < n_rot; j++) {
+    for (long k = 0; k < n_data; k++) {
+      const double f = inv_phi[j * n_data + k];
+      double nk = 0.0;
+      for (long i = 0; i < n_pix; i++) nk += K[k * n_pix + i];
+      double s = 0.0;
+      if (f > 0.0) {
+        const double phi = 1.0 / f;
+        for (long i = 0; i < n_pix; i++) {
+          const double kk = K[k * n_pix + i];
+          const double lam = phi * W[j * n_pix + i];
+          s += (kk > 0.0 ? kk * log(lam) : 0.0) - lam;
+        }
+        s -= nk * log(nk) - nk;
+      }
+      S[j * n_data + k] = s + log(weight[j]);
+    }
+  }
+}
+
+/* One pass of Algorithm 2.1 under the Poisson-fluence model (M-step as in the
+ * Gaussian one: Num_ij = sum_k P_jk K_ik / phi_jk, den_j = sum_k P_jk). */
+double oracle_iteration_poisson_fluence(int N, const double* grid, long n_rot, const double* quat,
+                                        const double* weight, long n_pix, const double* q,
+                                        long n_data, const double* K, double w_floor, int mode,
+                                        double* grid_out, double* P_out, double* lse_out) {
+  long M = (long)N * N * N;
+  double* W = malloc(sizeof(double) * (size_t)(n_rot * n_pix));
+  double* F = malloc(sizeof(double) * (size_t)(n_rot * n_data));
+  double* S = malloc(sizeof(double) * (size_t)(n_rot * n_data));
+  double* Num = malloc(sizeof(double) * (size_t)(n_rot * n_pix));
+  double* den = malloc(sizeof(double) * (size_t)n_rot);
+  double* gn = malloc(sizeof(double) * (size_t)M);
+  double* gd = malloc(sizeof(double) * (size_t)M);
+  double L = NAN;
+  if (W && F && S && Num && den && gn && gd) {
+    oracle_expand(N, grid, n_rot, quat, n_pix, q, w_floor, W);
+    oracle_fluence_poisson(n_rot, n_pix, n_data, W, K, F);
+    oracle_scores_poisson_fluence(n_rot, n_pix, n_data, W, weight, K, F, S);
+    L = oracle_estep(n_rot, n_data, S, S, lse_out); /* S now holds P */
+    if (P_out) memcpy(P_out, S, sizeof(double) * (size_t)(n_rot * n_data));
+    oracle_mstep_gauss(n_rot, n_pix, n_data, S, K, F, Num, den);
+    oracle_compress(N, n_rot, quat, n_pix, q, Num, den, mode, grid, gn, gd, grid_out);
+  }
+  free(W); free(F); free(S); free(Num); free(den); free(gn); free(gd);
+  return L;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

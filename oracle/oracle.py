@@ -63,6 +63,13 @@ def lib():
             L.oracle_iteration_gauss.argtypes = [ctypes.c_int, _dp, ctypes.c_long, _dp, _dp,
                                                  ctypes.c_long, _dp, ctypes.c_long, _dp,
                                                  ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
+            L.oracle_fluence_poisson.argtypes = [ctypes.c_long] * 3 + [_dp] * 3
+            L.oracle_scores_poisson_fluence.argtypes = [ctypes.c_long] * 3 + [_dp] * 5
+            L.oracle_iteration_poisson_fluence.restype = ctypes.c_double
+            L.oracle_iteration_poisson_fluence.argtypes = [ctypes.c_int, _dp, ctypes.c_long, _dp,
+                                                           _dp, ctypes.c_long, _dp, ctypes.c_long,
+                                                           _dp, ctypes.c_double, ctypes.c_int,
+                                                           _dp, _dp, _dp]
             L.oracle_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -212,6 +219,44 @@ def iteration_gauss(grid, quat, weight, q, K, sigma: float, mode: int = 0,
     L = lib().oracle_iteration_gauss(N, _p(grid), quat.shape[0], _p(quat), _p(weight),
                                      q.shape[0], _p(q), K.shape[0], _p(K), float(sigma), mode,
                                      _p(out), _p(P), _p(lse))
+    if want_P:
+        return out, lse, L, P
+    return out, lse, L
+
+
+# ----------------------------------------------------------------------------
+# Poisson model with per-(j,k) fluence (maximum-likelihood scale)
+# ----------------------------------------------------------------------------
+
+def fluence_poisson(W, K) -> np.ndarray:
+    """1/phi_jk = sum_i W_ij / N_k (0 for an empty frame): [n_rot, n_data]."""
+    W, K = _f64(W), _f64(K)
+    F = np.empty((W.shape[0], K.shape[0]))
+    lib().oracle_fluence_poisson(W.shape[0], W.shape[1], K.shape[0], _p(W), _p(K), _p(F))
+    return F
+
+
+def scores_poisson_fluence(W, weight, K, inv_phi=None) -> np.ndarray:
+    """S_jk = sum_i (K log(phi W) - phi W) + log w_j - (N_k log N_k - N_k)."""
+    W, weight, K = _f64(W), _f64(weight), _f64(K)
+    F = fluence_poisson(W, K) if inv_phi is None else _f64(inv_phi)
+    S = np.empty((W.shape[0], K.shape[0]))
+    lib().oracle_scores_poisson_fluence(W.shape[0], W.shape[1], K.shape[0], _p(W), _p(weight),
+                                        _p(K), _p(F), _p(S))
+    return S
+
+
+def iteration_poisson_fluence(grid, quat, weight, q, K, w_floor: float, mode: int = 0,
+                              want_P: bool = False):
+    """Algorithm 2.1 under the Poisson-fluence model: (grid_out, lse, sum lse[, P])."""
+    grid, quat, weight, q, K = _f64(grid), _f64(quat), _f64(weight), _f64(q), _f64(K)
+    N = grid.shape[0]
+    out = np.empty_like(grid)
+    lse = np.empty(K.shape[0])
+    P = np.empty((quat.shape[0], K.shape[0])) if want_P else None
+    L = lib().oracle_iteration_poisson_fluence(N, _p(grid), quat.shape[0], _p(quat), _p(weight),
+                                               q.shape[0], _p(q), K.shape[0], _p(K), w_floor,
+                                               mode, _p(out), _p(P), _p(lse))
     if want_P:
         return out, lse, L, P
     return out, lse, L
