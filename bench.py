@@ -45,6 +45,7 @@ DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3", "fp16_split": "f
 LEARNED_FORMS = ("learned",)
 ADAPTIVE_FORMS = ("adaptive",)
 GAUSS_FORMS = ("gaussian",)
+FLUENCE_FORMS = ("poisson_fluence",)
 SPARSE_K_FORMS = ("sparse_k",)
 
 
@@ -58,7 +59,8 @@ def parse_args():
     ap.add_argument("--workload", default="emc64", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
     ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
-    ap.add_argument("--forms", default="fp32,bf16,fp16_split,learned,adaptive,gaussian,sparse_k",
+    ap.add_argument("--forms",
+                    default="fp32,bf16,fp16_split,learned,adaptive,gaussian,poisson_fluence,sparse_k",
                     help="other forms to time briefly (comma list, or 'none')")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-iters", type=int, default=30,
@@ -572,14 +574,18 @@ def run_ours(args):
                 forms[f] = {"error": str(e)[:300]}
             continue
         try:
-            gauss = f in GAUSS_FORMS
-            c2 = (make_ctx(None, model="gaussian", sigma=args.sigma) if gauss else make_ctx(f))
+            gauss, flu = f in GAUSS_FORMS, f in FLUENCE_FORMS
+            c2 = (make_ctx(None, model="gaussian", sigma=args.sigma) if gauss else
+                  make_ctx("bf16_split", model="poisson_fluence") if flu else make_ctx(f))
             fms, fph, _, fll = time_form(torch, emc, c2, grid, 2, 1, stream, dist)
             forms[f] = {"value": world * pairs / (fms * 1e-3), "ms_per_step": fms, "loglik": fll,
                         "ms_loglik": fph["ms_loglik"]}
             if gauss:
                 forms[f].update({"model": "Gaussian, per-(j,k) fluence (Eqs. 2.2-2.6)",
                                  "sigma": args.sigma, "phases_ms": fph})
+            if flu:
+                forms[f].update({"model": "Poisson, per-(j,k) maximum-likelihood fluence, "
+                                          "BF16 split", "phases_ms": fph})
             del c2
         except Exception as e:  # a form that is not built yet is reported, not hidden
             forms[f] = {"error": str(e)[:200]}

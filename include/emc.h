@@ -81,7 +81,22 @@ typedef enum emc_model {
    * so the E-step is the same contraction over pixels with W in place of
    * log W. Needs precision EMC_PREC_FP16_SPLIT and EMC_FLAG_STORE_SCORES;
    * the sparse Maximize and emc_loglik_static are Poisson only. */
-  EMC_MODEL_GAUSSIAN = 1
+  EMC_MODEL_GAUSSIAN = 1,
+  /* Poisson with a per-(j,k) fluence phi_jk (frames of unequal, unknown
+   * intensity): K_ik ~ Poisson(phi_jk W_ij) with phi_jk its maximum-likelihood
+   * value N_k / B_j (N_k = sum_i K_ik, B_j = sum_i W_ij) on the model of the
+   * current iteration, the Poisson counterpart of Eq. 2.6. Then
+   *   S_jk = sum_i K_ik log(W_ij / B_j) + log w_j
+   * (the per-frame constant N_k log N_k - N_k and log K! left out), and the
+   * M-step divides each frame by its fluence as Eq. 2.5 does:
+   *   Num_ij = sum_k P_jk K_ik B_j / N_k, den_j = sum_k P_jk
+   * (an empty frame contributes only to den). The E-step is the Poisson
+   * contraction on log(W / B_j) in place of log W. Needs precision
+   * EMC_PREC_BF16_SPLIT (the other forms hold one rounded value of
+   * log(W / B_j) per element, whose per-rotation rounding bias the
+   * contraction would multiply by N_k); emc_loglik_static and
+   * emc_loglik_sparse_k are Poisson only. */
+  EMC_MODEL_POISSON_FLUENCE = 2
 } emc_model;
 
 typedef enum emc_compress_mode {
@@ -218,7 +233,15 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
  * every partial sum of hi K stays below 2^24 (exact in FP32); bias_j =
  * log w_j - sum_i W_ij^2 / (2 sigma^2). The call records s in the context;
  * emc_loglik, emc_normalize and emc_update use the scale of the last
- * emc_expand. */
+ * emc_expand.
+ * Poisson-fluence model: L holds log(W_ij / B_j) + c in place of log W
+ * (B_j = sum_i W_ij, c = log n_pix rounded to the 1/8 grid, which keeps the
+ * values and the scores in the range of the exact split); bias is
+ * double[2][rows] (bias_bytes): log w_j, then B_j (0 on padding rows). The
+ * context also keeps B_j of rows [rot0, rot0 + nrot) for the sparse calls
+ * and emc_iteration. The scores are then shifted by c N_k per frame;
+ * emc_loglik removes the shift from lse (in FP64), and the normalisation
+ * adds it back. */
 int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void* L,
                double* bias, emc_stream stream);
 
@@ -235,7 +258,10 @@ int emc_expand(emc_ctx* ctx, const float* grid, int64_t rot0, int64_t nrot, void
  * the FP16 three-plane L (see emc_model); scores more than about 1.2e5 below
  * zero are clamped there (their exp is 0 next to any frame's best rotation),
  * and a frame whose best score lies below that makes the device status
- * EMC_ERR_NUMERIC (sigma too small for the data). */
+ * EMC_ERR_NUMERIC (sigma too small for the data).
+ * Poisson-fluence model: lse_k = m_k + log s_k is that of
+ * S_jk = sum_i K_ik log(W_ij / B_j) + log w_j; the stored scores carry the
+ * per-frame shift c N_k of emc_expand's L (P is unchanged by it). */
 int emc_loglik(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot, double* lse_m,
                double* lse_s, int accumulate, void* scores, emc_stream stream);
 
@@ -263,7 +289,11 @@ int emc_loglik_sparse_k(emc_ctx* ctx, const float* L, const double* bias, int64_
  * the responsibility already divided by the fluence that Eq. 2.5 applies to
  * frame k (1/phi_jk = sqrt(2 sigma^2 (S_jk - bias_j) / A_k)), as
  * bf16[2][rows][ld_data] hi + lo; after the planes the buffer holds
- * float den[rows] = sum_k P_jk (prob_bytes counts it). */
+ * float den[rows] = sum_k P_jk (prob_bytes counts it).
+ * Poisson-fluence model (either form; bias, and without scores L,
+ * required): the planes hold P_jk B_j / N_k (0 for an empty frame) as
+ * bf16[2][rows][ld_data] hi + lo, with B_j read from the second half of
+ * bias, followed by float den[rows] = sum_k P_jk. */
 int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
                   const double* lse_m, const double* lse_s, const void* scores, void* P,
                   emc_stream stream);
@@ -303,7 +333,8 @@ int emc_loglik_static(const emc_config* cfg, const void* L, const double* bias,
  * den (device float[rows]) = sum_k P_jk.
  * Gaussian model: Num_ij = sum_k P_jk K_ik / phi_jk (Eq. 2.5 before the
  * division) from the planes emc_normalize wrote; den is copied from the end
- * of the P buffer. */
+ * of the P buffer. Poisson-fluence model: likewise, Num_ij =
+ * sum_k P_jk K_ik B_j / N_k. */
 int emc_update(emc_ctx* ctx, const void* P, int64_t nrot, float* Num, float* den,
                emc_stream stream);
 
@@ -321,7 +352,10 @@ int emc_finalize(emc_ctx* ctx, const double* g_num, const double* g_den, const f
 
 /* One pass of Algorithm 2.1 on the loaded frames, using the workspace for
  * every intermediate: e-step, E-step (two passes), M-step and c-step over
- * rotation chunks of cfg.rot_chunk. grid_out may not alias grid_in.
+ * rotation chunks of cfg.rot_chunk. grid_out may not alias grid_in. With the
+ * tensor-core forms the M-step contracts only the 128-rotation x 64-frame
+ * blocks of P that the normalisation found non-zero (most underflow to exact
+ * zeros); the result is that of the full contraction.
  * stats (host, may be NULL) is filled after the call synchronises `stream`. */
 int emc_iteration(emc_ctx* ctx, const float* grid_in, float* grid_out, emc_iter_stats* stats,
                   emc_stream stream);
@@ -398,12 +432,16 @@ int emc_set_candidates(emc_ctx* ctx, const int32_t* cand, emc_stream stream);
 
 /* Eq. 2.4 over the candidate sets, from L and bias of emc_expand over all
  * rotations: P (device float[ld_data][n_cand], slot order of the candidates;
- * padding frames 0) and lse (device double[ld_data]). */
+ * padding frames 0) and lse (device double[ld_data]; Poisson-fluence model:
+ * without the per-frame shift of L, as emc_loglik). */
 int emc_sparse_estep(emc_ctx* ctx, const void* L, const double* bias, float* P, double* lse,
                      emc_stream stream);
 
 /* Eq. 2.11 over the candidate sets: Num (device float[rows][ld_pix]) and den
- * (device float[rows]) for every rotation (rows without candidates: 0). */
+ * (device float[rows]) for every rotation (rows without candidates: 0).
+ * Poisson-fluence model: Num_ij = sum_k P_jk K_ik B_j / N_k and
+ * den_j = sum_k P_jk over the candidate pairs, B_j from the last emc_expand
+ * over all rotations. */
 int emc_sparse_update(emc_ctx* ctx, const float* P, float* Num, float* den, emc_stream stream);
 
 /* One pass of Algorithm 2.1 with the Maximize step over the candidate sets

@@ -21,7 +21,8 @@ struct Layout {
   int nrep;  // grid replicas of the fused iterations' compression
   size_t qh, ql, quat, rot, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
       Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, gk, gauss,
-      Kb2, skcnt, skoff, skent, dupsrc, duprank, pixmax, total;
+      Kb2, skcnt, skoff, skent, dupsrc, duprank, pixmax, fcn, finvn, fB, kbflag, kbcnt, kblist,
+      total;
 };
 
 // Gaussian scalars inside the 256-byte block at Layout::gauss
@@ -34,6 +35,10 @@ size_t score_bytes(int64_t rows, int64_t ld_data) {
 }
 
 bool is_gauss(const emc_config* c) { return c->model == EMC_MODEL_GAUSSIAN; }
+bool is_flu(const emc_config* c) { return c->model == EMC_MODEL_POISSON_FLUENCE; }
+// Poisson-fluence model: the constant c of L = log(W / B_j) + c, log n_pix on
+// the 1/8 grid (L is then the log of W over the slice's mean)
+double flu_shift(const emc_config* c) { return rint(8.0 * log((double)c->n_pix)) / 8.0; }
 
 // bytes of L (emc_expand) and P (emc_normalize) for `rows` rotations
 size_t L_bytes(const emc_config* c, int64_t rows, int64_t ld_pix) {
@@ -41,13 +46,14 @@ size_t L_bytes(const emc_config* c, int64_t rows, int64_t ld_pix) {
   const int planes = is_gauss(c) ? 3 : (p == EMC_PREC_BF16_SPLIT ? 3 : (p == EMC_PREC_FP16_SPLIT ? 2 : 1));
   return (size_t)planes * (p == EMC_PREC_FP32 ? 4 : 2) * (size_t)rows * ld_pix;
 }
-// Gaussian: after the planes, den[rows] (float)
+// Gaussian and Poisson-fluence: after the planes, den[rows] (float)
 size_t P_plane_bytes(const emc_config* c, int64_t rows, int64_t ld_data) {
   const int p = c->precision;
   return (size_t)(p == EMC_PREC_FP32 ? 1 : 2) * (p == EMC_PREC_FP32 ? 4 : 2) * (size_t)rows * ld_data;
 }
 size_t P_bytes(const emc_config* c, int64_t rows, int64_t ld_data) {
-  return P_plane_bytes(c, rows, ld_data) + (is_gauss(c) ? align256(sizeof(float) * rows) : 0);
+  return P_plane_bytes(c, rows, ld_data) +
+         (is_gauss(c) || is_flu(c) ? align256(sizeof(float) * rows) : 0);
 }
 
 int check_config(const emc_config* c) {
@@ -60,12 +66,18 @@ int check_config(const emc_config* c) {
   if (c->compress_mode != EMC_COMPRESS_DEFERRED && c->compress_mode != EMC_COMPRESS_IDW)
     return EMC_ERR_ARG;
   if (!(c->w_floor > 0.0) || !isfinite(c->w_floor)) return EMC_ERR_ARG;
-  if (c->model != EMC_MODEL_POISSON && c->model != EMC_MODEL_GAUSSIAN) return EMC_ERR_ARG;
+  if (c->model != EMC_MODEL_POISSON && c->model != EMC_MODEL_GAUSSIAN && !is_flu(c))
+    return EMC_ERR_ARG;
   if (is_gauss(c)) {
     if (!(c->sigma > 0.0) || !isfinite(c->sigma)) return EMC_ERR_ARG;
     if (c->precision != EMC_PREC_FP16_SPLIT || !(c->flags & EMC_FLAG_STORE_SCORES) ||
         c->n_cand != 0 || (c->flags & EMC_FLAG_SPARSE_K))
       return EMC_ERR_UNSUPPORTED;
+  } else if (is_flu(c)) {
+    // one rounded value of log(W / B_j) per element (FP32, FP16 rest, BF16)
+    // carries a per-rotation rounding bias that the contraction multiplies by
+    // N_k; the three-term split carries log B_j's low part exactly
+    if (c->precision != EMC_PREC_BF16_SPLIT) return EMC_ERR_UNSUPPORTED;
   } else if ((c->precision == EMC_PREC_BF16_SPLIT || c->precision == EMC_PREC_FP16_SPLIT) &&
              log(c->w_floor) < (double)kHiMin) {
     return EMC_ERR_UNSUPPORTED;
@@ -102,7 +114,7 @@ Layout make_layout(const emc_config* c) {
   y.Kb = take(2 * (size_t)y.ld_data * y.ld_pix);
   y.status = take(256);
   y.L = take(L_bytes(c, y.rows, y.ld_pix));
-  y.bias = take(sizeof(double) * y.rows);
+  y.bias = take(sizeof(double) * y.rows * (is_flu(c) ? 2 : 1));
   y.lse_m = take(sizeof(double) * y.ld_data);
   y.lse_s = take(sizeof(double) * y.ld_data);
   y.lse2 = take(sizeof(float2) * y.ld_data);
@@ -141,6 +153,16 @@ Layout make_layout(const emc_config* c) {
   y.dupsrc = wide ? take(sizeof(int32_t) * kDupCols) : 0;
   y.duprank = wide ? take(sizeof(int32_t) * kDupCols) : 0;
   y.pixmax = wide ? take(sizeof(int32_t) * (size_t)c->n_pix) : 0;
+  y.fcn = is_flu(c) ? take(sizeof(double) * (size_t)y.ld_data) : 0;
+  y.finvn = is_flu(c) ? take(sizeof(float) * (size_t)y.ld_data) : 0;
+  // B_j at rot0 + row for every padded row of an emc_expand block: one tile beyond rows
+  y.fB = is_flu(c) ? take(sizeof(double) * (size_t)(y.rows + 128)) : 0;
+  // non-zero P blocks of a pass-2 chunk (tensor-core update over those only)
+  const bool tc = c->precision != EMC_PREC_FP32;
+  const int64_t ctiles = y.chunk_rows / 128, kbs = y.ld_data / 64;
+  y.kbflag = tc ? take((size_t)ctiles * kbs) : 0;
+  y.kbcnt = tc ? take(sizeof(int32_t) * (size_t)ctiles) : 0;
+  y.kblist = tc ? take(sizeof(int32_t) * (size_t)ctiles * kbs) : 0;
   y.total = o;
   return y;
 }
@@ -168,6 +190,10 @@ struct emc_ctx {
   unsigned* gmax;             // Gaussian: bits of max(grid) of the last emc_expand
   unsigned long long* nmax;   // Gaussian: largest frame total
   float4* gsc;                // Gaussian scales of the last emc_expand
+  double* flu_cn;             // Poisson-fluence: per-frame score shift c N_k
+  float* flu_invn;            // Poisson-fluence: 1 / N_k (0 for empty frames)
+  double* flu_B;              // Poisson-fluence: B_j = sum_i W_ij of the last emc_expand
+  double flu_c;               // Poisson-fluence: c of L = log(W / B_j) + c
   bool frames_loaded;
   bool cand_loaded;
   cudaEvent_t ev[8];
@@ -207,7 +233,7 @@ int emc_buffer_sizes_for(const emc_config* cfg, int64_t nrot, emc_buffer_sizes* 
   out->ld_data = y.ld_data;
   out->rows = round_up(nrot, 128);
   out->logw_bytes = L_bytes(cfg, out->rows, y.ld_pix);
-  out->bias_bytes = sizeof(double) * out->rows;
+  out->bias_bytes = sizeof(double) * out->rows * (is_flu(cfg) ? 2 : 1);
   out->prob_bytes = P_bytes(cfg, out->rows, y.ld_data);
   out->num_bytes = sizeof(float) * (size_t)out->rows * y.ld_pix;
   out->den_bytes = sizeof(float) * out->rows;
@@ -322,6 +348,10 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   c->gmax = (unsigned*)(c->ws + y.gauss + kGaussMaxOff);
   c->nmax = (unsigned long long*)(c->ws + y.gauss + kGaussNmaxOff);
   c->gsc = (float4*)(c->ws + y.gauss + kGaussScaleOff);
+  c->flu_cn = y.fcn ? (double*)(c->ws + y.fcn) : nullptr;
+  c->flu_invn = y.finvn ? (float*)(c->ws + y.finvn) : nullptr;
+  c->flu_B = y.fB ? (double*)(c->ws + y.fB) : nullptr;
+  c->flu_c = is_flu(cfg) ? flu_shift(cfg) : 0.0;
   cudaStream_t s = (cudaStream_t)stream;
   bool ok = true;
   ok &= cudaMemcpyAsync(c->ws + y.qh, qh.data(), sizeof(float4) * y.ld_pix,
@@ -393,6 +423,9 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
     CU(launch_sparse_k_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data,
                               (int32_t*)(ctx->ws + y.skcnt), (int64_t*)(ctx->ws + y.skoff),
                               (uint32_t*)(ctx->ws + y.skent), (cudaStream_t)stream));
+  if (is_flu(&ctx->cfg))
+    CU(launch_flu_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, ctx->flu_c,
+                         ctx->flu_cn, ctx->flu_invn, s));
   if (g) {
     CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb2,
                           2, dsrc, drank, ctx->status, s));
@@ -416,6 +449,12 @@ int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L
   const int64_t rows = round_up(nrot, 128);
   Planes p{L, rows * c->lay.ld_pix, c->lay.ld_pix};
   const bool g = is_gauss(&c->cfg);
+  if (is_flu(&c->cfg)) {
+    CU(launch_expand_flu(c->geom, grid, c->rot + rot0, c->logw + rot0, nrot, rows,
+                         c->cfg.precision, (float)c->cfg.w_floor, c->flu_c, p, bias,
+                         c->flu_B + rot0, c->status, s));
+    return EMC_OK;
+  }
   if (g)
     CU(launch_gauss_scales(grid, (int64_t)c->cfg.N * c->cfg.N * c->cfg.N, c->gmax, c->nmax,
                            c->gsc, c->status, s));
@@ -451,18 +490,36 @@ int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const d
     tiles = tc_pass1_tiles(rows);
   }
   CU(launch_lse_merge(pm, ps, tiles, y.ld_data, c->cfg.n_data, lse_m, lse_s, accumulate,
-                      is_gauss(&c->cfg),
-                      c->status, s));
+                      is_gauss(&c->cfg), c->status, s, c->flu_cn));
   return EMC_OK;
 }
 
 // S, Sref: stored scores of these rows, S frame-major with leading dimension
-// ldS (NULL: recompute from L and bias).
+// ldS (NULL: recompute from L and bias). Bsum: the rows' B_j (Poisson-fluence model).
 int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const double* bias,
                  int64_t nrot, const double* lse_m, const double* lse_s, const float* S,
-                 int64_t ldS, const float* Sref, void* P, int64_t Prows, cudaStream_t s) {
+                 int64_t ldS, const float* Sref, void* P, int64_t Prows, cudaStream_t s,
+                 const double* Bsum = nullptr, uint8_t* kbf = nullptr) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
+  if (is_flu(&c->cfg)) {
+    if (!bias || !Bsum) return EMC_ERR_ARG;
+    float2* lse2 = (float2*)(c->ws + y.lse2);
+    float* den = (float*)((char*)P + P_plane_bytes(&c->cfg, Prows, y.ld_data));
+    if (S) {
+      CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s, c->flu_cn));
+      CU(launch_normalize_scores_flu(S, ldS, Sref, lse2, Bsum, c->flu_invn, rows, nrot,
+                                     y.ld_data, c->cfg.n_data, (uint16_t*)P, Prows * y.ld_data,
+                                     den, s, kbf));
+    } else {
+      Planes lp{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
+      Planes pp{P, Prows * y.ld_data, y.ld_data};
+      CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, c->Kb, y.ld_data,
+                             c->cfg.n_data, y.ld_pix, lse_m, lse_s, lse2, pp, c->status, s,
+                             c->flu_cn, Bsum, c->flu_invn, den, kbf));
+    }
+    return EMC_OK;
+  }
   if (is_gauss(&c->cfg)) {
     if (!S || !bias) return EMC_ERR_UNSUPPORTED;
     float2* lse2 = (float2*)(c->ws + y.lse2);
@@ -470,14 +527,14 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
     CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s));
     CU(launch_normalize_scores_gauss(S, ldS, Sref, lse2, bias, c->gk, rows, nrot,
                                      y.ld_data, c->cfg.n_data, (uint16_t*)P, Prows * y.ld_data,
-                                     den, s));
+                                     den, s, kbf));
     return EMC_OK;
   }
   if (S) {
     float2* lse2 = (float2*)(c->ws + y.lse2);
     CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s));
     CU(launch_normalize_scores(S, ldS, Sref, lse2, rows, nrot, y.ld_data, c->cfg.n_data,
-                               c->cfg.precision, P, Prows * y.ld_data, s));
+                               c->cfg.precision, P, Prows * y.ld_data, s, kbf));
     return EMC_OK;
   }
   if (c->cfg.precision == EMC_PREC_FP32) {
@@ -488,13 +545,15 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
     Planes lp{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
     Planes pp{P, Prows * y.ld_data, y.ld_data};
     CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix,
-                           lse_m, lse_s, (float2*)(c->ws + y.lse2), pp, c->status, s));
+                           lse_m, lse_s, (float2*)(c->ws + y.lse2), pp, c->status, s, nullptr,
+                           nullptr, nullptr, nullptr, kbf));
   }
   return EMC_OK;
 }
 
+// kbc, kbl (optional): the non-zero 64-frame blocks of each row tile of P
 int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num, float* den,
-              cudaStream_t s) {
+              cudaStream_t s, const int32_t* kbc = nullptr, const int32_t* kbl = nullptr) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
   if (c->cfg.precision == EMC_PREC_FP32) {
@@ -502,15 +561,17 @@ int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num
                           den, s));
   } else {
     Planes pp{(void*)P, Prows * y.ld_data, y.ld_data};
-    if (is_gauss(&c->cfg)) {
-      // BF16 hi + lo planes of P / phi against the BF16 copy of the frames
-      CU(launch_tc_update(pp, EMC_PREC_BF16_SPLIT, rows, c->Kb2, y.ld_data, y.ld_pix, c->cfg.n_pix,
-                          Num, nullptr, c->status, s));
+    if (is_gauss(&c->cfg) || is_flu(&c->cfg)) {
+      // BF16 hi + lo planes of P / phi against the BF16 frames (the Gaussian
+      // model's BF16 copy)
+      CU(launch_tc_update(pp, EMC_PREC_BF16_SPLIT, rows, is_gauss(&c->cfg) ? c->Kb2 : c->Kb,
+                          y.ld_data, y.ld_pix, c->cfg.n_pix, Num, nullptr, c->status, s, kbc,
+                          kbl));
       const char* tail = (const char*)P + P_plane_bytes(&c->cfg, Prows, y.ld_data);
       CU(cudaMemcpyAsync(den, tail, sizeof(float) * rows, cudaMemcpyDeviceToDevice, s));
     } else {
       CU(launch_tc_update(pp, c->cfg.precision, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num,
-                          den, c->status, s));
+                          den, c->status, s, kbc, kbl));
     }
   }
   return EMC_OK;
@@ -569,15 +630,16 @@ int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
   if (!ctx || !lse_m || !lse_s || !P) return EMC_ERR_ARG;
   if (!scores && (!L || !bias)) return EMC_ERR_ARG;
   if (is_gauss(&ctx->cfg) && !scores) return EMC_ERR_UNSUPPORTED;
-  if (is_gauss(&ctx->cfg) && !bias) return EMC_ERR_ARG;
+  if ((is_gauss(&ctx->cfg) || is_flu(&ctx->cfg)) && !bias) return EMC_ERR_ARG;
   if (check_rot_range(ctx, 0, nrot)) return EMC_ERR_ARG;
   if (!ctx->frames_loaded) return EMC_ERR_ARG;
   if (((uintptr_t)scores) & 15) return EMC_ERR_ARG;
   const int64_t rows = round_up(nrot, 128);
   const float* S = (const float*)scores;
   const float* Sref = S ? S + rows * ctx->lay.ld_data : nullptr;
+  // Poisson-fluence model: B_j follows log w_j in the bias buffer
   return do_normalize(ctx, L, rows, 0, bias, nrot, lse_m, lse_s, S, rows, Sref, P, rows,
-                      (cudaStream_t)stream);
+                      (cudaStream_t)stream, is_flu(&ctx->cfg) ? bias + rows : nullptr);
 }
 
 int emc_update(emc_ctx* ctx, const void* P, int64_t nrot, float* Num, float* den,
@@ -650,17 +712,25 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     if (stats) CU(cudaEventRecord(c->ev[3], s));
     const float* Sc = S ? S + r0 : nullptr;  // frame-major: rows r0.. of every frame
     const float* Sr = S ? S + y.rows * y.ld_data + (r0 / 32) * y.ld_data : nullptr;
+    // the tensor-core update contracts only the 128 x 64 blocks of P that the
+    // normalisation found non-zero (skipping blocks of exact zeros changes no sum)
+    uint8_t* kbf = y.kbflag ? (uint8_t*)(c->ws + y.kbflag) : nullptr;
+    const int32_t* kbc = kbf ? (const int32_t*)(c->ws + y.kbcnt) : nullptr;
+    const int32_t* kbl = kbf ? (const int32_t*)(c->ws + y.kblist) : nullptr;
     if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lse_m, lse_s, Sc, y.rows, Sr, P, crows,
-                           s)))
+                           s, c->flu_B ? c->flu_B + r0 : nullptr, kbf)))
       return st;
+    if (kbf)
+      CU(launch_kb_lists(kbf, crows / 128, (int)(y.ld_data / 64), (int32_t*)kbc, (int32_t*)kbl,
+                         s));
     if (stats) CU(cudaEventRecord(c->ev[4], s));
-    if ((st = do_update(c, P, crows, nr, Num, den, s))) return st;
+    if ((st = do_update(c, P, crows, nr, Num, den, s, kbc, kbl))) return st;
     if (stats) CU(cudaEventRecord(c->ev[5], s));
     CU(launch_compress(c->geom, c->rot + r0, nr, Num, den, c->cfg.compress_mode, gn, gd, y.nrep,
                        s));
     if (stats) CU(cudaEventRecord(c->ev[6], s));
     // normalize: lse split + the pass (one SIMT kernel when recomputing in FP32)
-    kernels += (S || c->cfg.precision != EMC_PREC_FP32 ? 2 : 1) + 2;
+    kernels += (S || c->cfg.precision != EMC_PREC_FP32 ? 2 : 1) + 2 + (kbf ? 1 : 0);
     if (stats) {
       // chunk timings need a host wait per chunk; only when stats are asked for
       float a = 0, b = 0, d = 0;
@@ -809,7 +879,7 @@ int emc_sparse_estep(emc_ctx* ctx, const void* L, const double* bias, float* P, 
                           (const int64_t*)(ctx->ws + y.coff), (const int2*)(ctx->ws + y.cent), M,
                           csr ? (const int64_t*)(ctx->ws + y.skoff) : nullptr,
                           csr ? (const uint32_t*)(ctx->ws + y.skent) : nullptr, Sc, s));
-  CU(launch_sparse_lse(Sc, ctx->cfg.n_data, y.ld_data, M, P, lse, ctx->status, s));
+  CU(launch_sparse_lse(Sc, ctx->cfg.n_data, y.ld_data, M, P, lse, ctx->status, s, ctx->flu_cn));
   return EMC_OK;
 }
 
@@ -822,7 +892,7 @@ int emc_sparse_update(emc_ctx* ctx, const float* P, float* Num, float* den, emc_
                           (const int2*)(ctx->ws + y.cent), ctx->cfg.n_cand, P, y.rows,
                           csr ? (const int64_t*)(ctx->ws + y.skoff) : nullptr,
                           csr ? (const uint32_t*)(ctx->ws + y.skent) : nullptr, Num, den,
-                          (cudaStream_t)stream));
+                          (cudaStream_t)stream, ctx->flu_B, ctx->flu_invn));
   return EMC_OK;
 }
 
@@ -893,7 +963,7 @@ int emc_missed_mass(emc_ctx* ctx, const void* scores, const double* lse_m, const
   if (!lse_s) lse_s = (const double*)(ctx->ws + y.lse_s);
   cudaStream_t s = (cudaStream_t)stream;
   float2* lse2 = (float2*)(ctx->ws + y.lse2);
-  CU(launch_lse_split(lse_m, lse_s, ctx->cfg.n_data, y.ld_data, lse2, s));
+  CU(launch_lse_split(lse_m, lse_s, ctx->cfg.n_data, y.ld_data, lse2, s, ctx->flu_cn));
   const float* S = (const float*)scores;
   CU(launch_missed_mass(S, y.rows, S + y.rows * y.ld_data, y.ld_data, lse2,
                         (const int32_t*)(ctx->ws + y.cand), ctx->cfg.n_cand, ctx->cfg.n_data,

@@ -52,6 +52,29 @@ cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
                           float w_floor, Planes L, double* bias, const float4* gsc, double sigma,
                           int32_t* status, cudaStream_t s);
 
+// Poisson-fluence model: L = log(W / B_j) + c as the BF16 three-term split
+// (precision EMC_PREC_BF16_SPLIT only); bias = double[2][rows]: log w_j, then
+// B_j = sum_i W_ij; Bctx[row] = B_j too.
+cudaError_t launch_expand_flu(const Geom& g, const float* grid, const RotDF* rot,
+                              const double* logw, int64_t nrot, int64_t rows, int precision,
+                              float w_floor, double c, Planes L, double* bias, double* Bctx,
+                              int32_t* status, cudaStream_t s);
+// Per frame: cn[k] = c N_k, invn[k] = 1 / N_k (0 for empty and padding frames).
+cudaError_t launch_flu_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                              int64_t ld_data, double c, double* cn, float* invn,
+                              cudaStream_t s);
+// Pass 2 from stored scores: BF16 hi + lo planes of P B_j / N_k, den[rows] = sum_k P.
+cudaError_t launch_normalize_scores_flu(const float* S, int64_t ldS, const float* Sref,
+                                        const float2* lse2, const double* Bsum, const float* invn,
+                                        int64_t rows, int64_t nrot, int64_t ld_data,
+                                        int64_t n_data, uint16_t* P, int64_t P_plane, float* den,
+                                        cudaStream_t s, uint8_t* kb_flag = nullptr);
+// Non-zero P blocks (update over those only): the normalisations set
+// flag[mt * kb_ld + kb] (kb_ld = ld_data / 64) for every 128-row x 64-frame
+// block of P with a non-zero entry; this lists them per row tile.
+cudaError_t launch_kb_lists(const uint8_t* flag, int64_t n_mtiles, int kb_ld, int32_t* cnt,
+                            int32_t* list, cudaStream_t s);
+
 // ---- Gaussian model (misc.cu) ----
 // Per-frame constants gk[ld_data] = (c_k hi, c_k lo, 2 sigma^2 / A_k, 0) and the
 // largest frame total (*nmax).
@@ -68,7 +91,7 @@ cudaError_t launch_normalize_scores_gauss(const float* S, int64_t ldS, const flo
                                           const float4* gk, int64_t rows,
                                           int64_t nrot, int64_t ld_data, int64_t n_data,
                                           uint16_t* P, int64_t P_plane, float* den,
-                                          cudaStream_t s);
+                                          cudaStream_t s, uint8_t* kb_flag = nullptr);
 
 // FP32 SIMT forms (precision EMC_PREC_FP32).
 // S, Sref (optional, both or neither): scores relative to 32-row group maxima,
@@ -87,17 +110,22 @@ cudaError_t launch_simt_update(const float* P, int64_t ld_data, int64_t rows, co
 int64_t simt_pass1_tiles(int64_t rows);
 
 // Merge of per-tile (max, sum) pairs into the running per-frame (m, s).
+// shift (may be NULL): per-frame constant carried by the tiles' scores
+// (double[ld_data]), removed before the merge.
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
-                             int accumulate, int gauss, int32_t* status, cudaStream_t s);
+                             int accumulate, int gauss, int32_t* status, cudaStream_t s,
+                             const double* shift = nullptr);
+// shift (may be NULL): added back to lse before the split.
 cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n_data,
-                             int64_t ld_data, float2* out, cudaStream_t s);
+                             int64_t ld_data, float2* out, cudaStream_t s,
+                             const double* shift = nullptr);
 // E-step pass 2 from stored scores (frame-major, ld ldS); P layout as
 // emc_normalize documents.
 cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sref,
                                     const float2* lse2, int64_t rows, int64_t nrot,
                                     int64_t ld_data, int64_t n_data, int precision, void* P,
-                                    int64_t P_plane, cudaStream_t s);
+                                    int64_t P_plane, cudaStream_t s, uint8_t* kb_flag = nullptr);
 cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
                               double* out, cudaStream_t s);
 
@@ -109,15 +137,24 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
                             const float4* gk, const float4* gsc, int32_t* status,
                             cudaStream_t s);
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
+// Bsum != NULL: Poisson-fluence model -- shift[ld_data] is added back to lse,
+// the planes receive BF16 hi + lo of P B_j invn[k] and den[rows] = sum_k P_jk
+// (zeroed here, then FP32 atomics).
 cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bias, int64_t rows,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
-                                float2* lse2, Planes P, int32_t* status, cudaStream_t s);
+                                float2* lse2, Planes P, int32_t* status, cudaStream_t s,
+                                const double* shift = nullptr, const double* Bsum = nullptr,
+                                const float* invn = nullptr, float* den = nullptr,
+                                uint8_t* kb_flag = nullptr);
 // P planes: hi + lo (BF16 split, FP16 split) or hi only (BF16); FP16 planes
 // carry the scale 2^14. den NULL: not written.
+// kb_cnt, kb_list (optional, from launch_kb_lists): contract only the listed
+// 64-frame blocks of each row tile (the others of P are zero)
 cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
-                             int32_t* status, cudaStream_t s);
+                             int32_t* status, cudaStream_t s, const int32_t* kb_cnt = nullptr,
+                             const int32_t* kb_list = nullptr);
 int64_t tc_pass1_tiles(int64_t rows);
 
 // nrep grid replicas of n_vox each (row j reduces into replica j mod nrep)
@@ -168,12 +205,17 @@ cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, c
                                  const uint16_t* Kb, int64_t ld_pix, const int64_t* off,
                                  const int2* ent, int M, const int64_t* koff,
                                  const uint32_t* kent, double* Sc, cudaStream_t s);
+// shift (may be NULL): per-frame constant of the scores, removed from lse_c
 cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data, int M, float* Pc,
-                              double* lse_c, int32_t* status, cudaStream_t s);
+                              double* lse_c, int32_t* status, cudaStream_t s,
+                              const double* shift = nullptr);
+// Bsum, invn (non-NULL): Poisson-fluence model, Num_j = sum P_jk K_k B_j / N_k
+// and den_j = sum P_jk
 cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
                                  const int64_t* off, const int2* ent, int M, const float* Pc,
                                  int64_t rows, const int64_t* koff, const uint32_t* kent,
-                                 float* Num, float* den, cudaStream_t s);
+                                 float* Num, float* den, cudaStream_t s,
+                                 const double* Bsum = nullptr, const float* invn = nullptr);
 cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, int64_t ld_data,
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
                                float* missed, cudaStream_t s);

@@ -147,6 +147,138 @@ __global__ void __launch_bounds__(kExpandThreads)
   }
 }
 
+// Poisson-fluence model: L_ij = log(W_ij / B_j) + c with B_j = sum_i W_ij,
+// so that sum_i K_ik L_ij = sum_i K_ik log W_ij - N_k log B_j + c N_k, the
+// scores of the maximum-likelihood fluence phi_jk = N_k / B_j up to the
+// per-frame shift c N_k (removed in FP64 by the log-sum-exp merge). B_j is
+// needed before the first L is written, so the CTA runs two phases: W_ij
+// (stashed in shared memory when the row fits, STASH, else interpolated again)
+// and its sum, then the split of log W_ij + a_j, a_j = c - log B_j. a_j is
+// carried as ah (1/8 grid) + al: x + ah is formed with its exact rounding
+// error e (two-sum), hi = rint8(x + ah) and the rest r = ((x + ah - hi) + e) + al
+// goes to mid + lo, so no per-rotation rounding of a_j enters the contraction
+// (it would be multiplied by N_k). bias = double[2][rows]: log w_j, then B_j
+// (FP64); Bctx[row] = B_j as well (the context's copy for the sparse steps).
+template <bool INTERIOR, bool STASH>
+__global__ void __launch_bounds__(kExpandThreads)
+    expand_flu_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql,
+                      int64_t ld_pix, int N, const float* __restrict__ grid,
+                      const RotDF* __restrict__ rot, const double* __restrict__ logw, int64_t nrot,
+                      float w_floor, double c, uint16_t* __restrict__ Lbase, int64_t plane_stride,
+                      double* __restrict__ bias, double* __restrict__ Bctx, int32_t* status) {
+  extern __shared__ float wst[];  // STASH: W of the row's pixels
+  const int64_t row = blockIdx.x;
+  __shared__ RotDF R;
+  __shared__ double red[kExpandThreads / 32];
+  __shared__ float a_split[2];
+  const bool valid_row = row < nrot;
+  if (threadIdx.x < 18 && valid_row)
+    reinterpret_cast<float*>(&R)[threadIdx.x] = reinterpret_cast<const float*>(rot + row)[threadIdx.x];
+  __syncthreads();
+  const float half_n = 0.5f * (float)N;
+  float wsum = 0.f, wcomp = 0.f;
+  if (valid_row) {
+    for (int64_t i = threadIdx.x; i < ld_pix; i += kExpandThreads) {
+      const float4 a = qh[i];
+      if (a.w == 0.f) continue;
+      int f[3];
+      float t[3];
+      rotate_to_grid(R, a, ql[i], half_n, f, t);
+      const float W = fmaxf(trilinear<INTERIOR>(grid, N, f, t), w_floor);
+      if (STASH) wst[i] = W;
+      if (a.w == 1.f) {  // duplicate columns repeat a pixel: not summed
+        const float ky = W - wcomp;
+        const float kt = wsum + ky;
+        wcomp = (kt - wsum) - ky;
+        wsum = kt;
+      }
+    }
+  }
+  double ws = (double)wsum - (double)wcomp;
+  for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double B = 0.0;
+    for (int w = 0; w < kExpandThreads / 32; w++) B += red[w];
+    const double aj = valid_row ? c - log(B) : 0.0;
+    const float ah = (float)(rint(aj * kHiScale) / kHiScale);
+    a_split[0] = ah;
+    a_split[1] = (float)(aj - (double)ah);
+    bias[row] = valid_row ? logw[row] : -INFINITY;
+    bias[gridDim.x + row] = valid_row ? B : 0.0;
+    Bctx[row] = valid_row ? B : 0.0;
+  }
+  __syncthreads();
+  const float ah = a_split[0], al = a_split[1];
+  uint16_t* Lb = Lbase + row * ld_pix;
+  int bad = 0;
+  for (int64_t i = threadIdx.x; i < ld_pix; i += kExpandThreads) {
+    float hi = 0.f, r = 0.f;
+    const float4 a = qh[i];
+    if (valid_row && a.w != 0.f) {
+      float W;
+      if (STASH) {
+        W = wst[i];
+      } else {
+        int f[3];
+        float t[3];
+        rotate_to_grid(R, a, ql[i], half_n, f, t);
+        W = fmaxf(trilinear<INTERIOR>(grid, N, f, t), w_floor);
+      }
+      const float x = logf(W);
+      const float s = x + ah;  // two-sum: s + e = x + ah exactly
+      const float bb = s - x;
+      const float e = (x - (s - bb)) + (ah - bb);
+      hi = rintf(s * kHiScale) * (1.0f / kHiScale);
+      if (hi < kHiMin || hi > kHiMax) bad = 1;
+      hi = fminf(fmaxf(hi, kHiMin), kHiMax);
+      r = ((s - hi) + e) + al;
+    }
+    const uint16_t mid = bf16_bits(r);
+    Lb[i] = bf16_bits(hi);
+    Lb[i + plane_stride] = mid;
+    Lb[i + 2 * plane_stride] = bf16_bits(r - bf16_val(mid));
+  }
+  if (bad) set_status(status, EMC_ERR_UNSUPPORTED);
+}
+
+// shared memory for one stashed row of W: rows up to 96 KB (24576 pixels)
+constexpr size_t kFluStashMax = 96 * 1024;
+
+cudaError_t launch_expand_flu(const Geom& g, const float* grid, const RotDF* rot,
+                              const double* logw, int64_t nrot, int64_t rows, int precision,
+                              float w_floor, double c, Planes L, double* bias, double* Bctx,
+                              int32_t* status, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (precision != EMC_PREC_BF16_SPLIT) return cudaErrorInvalidValue;
+  const size_t stash = sizeof(float) * (size_t)g.ld_pix;
+  const bool use_stash = stash <= kFluStashMax;
+  dim3 grd((unsigned)rows), blk(kExpandThreads);
+  cudaError_t e = cudaSuccess;
+#define EMC_FLU(I, S)                                                                         \
+  do {                                                                                        \
+    const size_t sm = S ? stash : 0;                                                          \
+    if (sm > 48 * 1024)                                                                       \
+      e = cudaFuncSetAttribute(expand_flu_kernel<I, S>,                                       \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);         \
+    if (e == cudaSuccess)                                                                     \
+      expand_flu_kernel<I, S><<<grd, blk, sm, s>>>(                                           \
+          g.qh, g.ql, g.ld_pix, g.N, grid, rot, logw, nrot, w_floor, c,                       \
+          reinterpret_cast<uint16_t*>(L.base), L.plane_stride, bias, Bctx, status);           \
+  } while (0)
+  if (g.interior) {
+    if (use_stash) EMC_FLU(true, true);
+    else EMC_FLU(true, false);
+  } else {
+    if (use_stash) EMC_FLU(false, true);
+    else EMC_FLU(false, false);
+  }
+#undef EMC_FLU
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
                           float w_floor, Planes L, double* bias, const float4* gsc, double sigma,

@@ -177,6 +177,35 @@ cudaError_t launch_gauss_frames(const int32_t* K, int64_t ld_k, int64_t n_data, 
   return cudaGetLastError();
 }
 
+// Poisson-fluence model, per frame k: N_k = sum_i K_ik, the score shift
+// cn[k] = c N_k (exact in FP64: c on the 1/8 grid, N_k an integer) and
+// invn[k] = 1 / N_k (0 for an empty or padding frame).
+__global__ void flu_frames_kernel(const int32_t* __restrict__ K, int64_t ld_k, int64_t n_data,
+                                  int64_t n_pix, double c, double* __restrict__ cn,
+                                  float* __restrict__ invn) {
+  const int64_t k = blockIdx.x;
+  __shared__ long long rn[8];
+  long long n = 0;
+  if (k < n_data)
+    for (int64_t i = threadIdx.x; i < n_pix; i += blockDim.x) n += K[k * ld_k + i];
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) rn[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long Nk = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) Nk += rn[w];
+    cn[k] = c * (double)Nk;
+    invn[k] = Nk > 0 ? (float)(1.0 / (double)Nk) : 0.f;
+  }
+}
+
+cudaError_t launch_flu_frames(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                              int64_t ld_data, double c, double* cn, float* invn,
+                              cudaStream_t s) {
+  flu_frames_kernel<<<(unsigned)ld_data, 256, 0, s>>>(K, ld_k, n_data, n_pix, c, cn, invn);
+  return cudaGetLastError();
+}
+
 // Largest grid value (for the Gaussian scales). Non-negative floats order
 // like their bit patterns, so an integer atomic maximum suffices; a
 // non-finite voxel counts as +inf.
@@ -215,17 +244,21 @@ cudaError_t launch_gauss_scales(const float* grid, int64_t n_vox, unsigned* gmax
 // Per frame k: fold the per-tile pairs (m_t, s_t) -- each meaning
 // sum over the tile's rotations of exp(S_jk) = s_t exp(m_t) -- into the running
 // (m_k, s_k) in FP64 (Eq. 2.4's denominator; only maxima and sums travel, as
-// in Sec. 3.3). Reads are coalesced along k.
+// in Sec. 3.3). Reads are coalesced along k. shift (may be NULL): a per-frame
+// constant the tiles' scores carry (the Poisson-fluence model's c N_k),
+// subtracted from their maxima before the merge.
 __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float* __restrict__ part_s,
                                  int64_t n_tiles, int64_t ld_data, int64_t n_data,
                                  double* __restrict__ lse_m, double* __restrict__ lse_s,
-                                 int accumulate, double clamp, int32_t* status) {
+                                 int accumulate, double clamp, const double* __restrict__ shift,
+                                 int32_t* status) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_data) return;
   double M = accumulate ? lse_m[k] : -INFINITY;
   double S = accumulate ? lse_s[k] : 0.0;
+  const double sh = shift ? shift[k] : 0.0;
   double mt = -INFINITY;
-  for (int64_t t = 0; t < n_tiles; t++) mt = fmax(mt, part_m[t * ld_data + k]);
+  for (int64_t t = 0; t < n_tiles; t++) mt = fmax(mt, part_m[t * ld_data + k] - sh);
   double Mn = fmax(M, mt);
   if (Mn == -INFINITY) {  // nothing seen yet
     lse_m[k] = M;
@@ -237,7 +270,7 @@ __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float*
   // this part and the loop runs over every rotation tile
   double acc = (S > 0.0) ? S * exp(M - Mn) : 0.0;
   for (int64_t t = 0; t < n_tiles; t++) {
-    double m = part_m[t * ld_data + k];
+    double m = part_m[t * ld_data + k] - sh;
     float sv = part_s[t * ld_data + k];
     if (sv > 0.f) acc += (double)(sv * __expf((float)(m - Mn)));
   }
@@ -250,11 +283,12 @@ __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float*
 
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
-                             int accumulate, int gauss, int32_t* status, cudaStream_t s) {
+                             int accumulate, int gauss, int32_t* status, cudaStream_t s,
+                             const double* shift) {
   unsigned blocks = (unsigned)((n_data + 255) / 256);
   lse_merge_kernel<<<blocks, 256, 0, s>>>(part_m, part_s, n_tiles, ld_data, n_data, lse_m, lse_s,
                                           accumulate, gauss ? -(double)kGaussClamp : -INFINITY,
-                                          status);
+                                          shift, status);
   return cudaGetLastError();
 }
 
@@ -285,23 +319,25 @@ cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t 
 
 // lse_k = m_k + log s_k (FP64) split into a part on the 1/64 grid and a small
 // FP32 rest, so that kernels can subtract it from grid-aligned scores exactly.
+// shift (may be NULL): the per-frame constant the scores carry, added back.
 __global__ void lse_split_kernel(const double* __restrict__ lse_m, const double* __restrict__ lse_s,
-                                 int64_t n_data, int64_t ld_data, float2* __restrict__ out) {
+                                 int64_t n_data, int64_t ld_data, const double* __restrict__ shift,
+                                 float2* __restrict__ out) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ld_data) return;
   if (k >= n_data) {
     out[k] = make_float2(0.f, 0.f);
     return;
   }
-  const double l = lse_m[k] + log(lse_s[k]);
+  const double l = lse_m[k] + log(lse_s[k]) + (shift ? shift[k] : 0.0);
   const double h = rint(l * kGridD) / kGridD;
   out[k] = make_float2((float)h, (float)(l - h));
 }
 
 cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n_data,
-                             int64_t ld_data, float2* out, cudaStream_t s) {
+                             int64_t ld_data, float2* out, cudaStream_t s, const double* shift) {
   lse_split_kernel<<<(unsigned)((ld_data + 255) / 256), 256, 0, s>>>(lse_m, lse_s, n_data, ld_data,
-                                                                   out);
+                                                                   shift, out);
   return cudaGetLastError();
 }
 
@@ -326,6 +362,9 @@ cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n
 // 2^-17 over the whole FP32 range, which a single FP16 scale cannot give rows
 // of small responsibility); den_j = sum_k P_jk is added to den with one FP32
 // atomic per row and 8 frames (den zeroed by the caller).
+//
+// Poisson-fluence model (OUT 5): the M-step operand P_jk / phi_jk =
+// P_jk B_j / N_k in BF16 hi + lo (0 for an empty frame) and den_j as for OUT 4.
 struct NormArgs {
   const float* S;
   int64_t ldS;
@@ -336,13 +375,17 @@ struct NormArgs {
   int64_t P_plane;
   const double* bias;  // Gaussian
   const float4* gk;    // Gaussian: .z = 2 sigma^2 / A_k
-  float* den;          // Gaussian
+  float* den;          // Gaussian, Poisson-fluence
+  const double* Bsum;  // Poisson-fluence: B_j
+  const float* invn;   // Poisson-fluence: 1 / N_k
+  uint8_t* kb_flag;    // optional: 1 where the CTA's 128 x 64 block of P is non-zero
+  int64_t kb_ld;
 };
 
 constexpr int kNormRows = 128, kNormFrames = 64;
 
 // OUT: 0 FP32 P; 1 BF16 hi plane only; 2 BF16 hi + lo; 3 FP16 hi + lo of 2^14 P;
-// 4 Gaussian BF16 hi + lo of P / phi plus den
+// 4 Gaussian BF16 hi + lo of P / phi plus den; 5 Poisson-fluence, likewise
 template <int OUT>
 __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a) {
   __shared__ __align__(16) float tile[kNormFrames][kNormRows];
@@ -360,6 +403,7 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
   if (tid < kNormFrames) {
     sl[tid] = a.lse2[k0 + tid];
     if (OUT == 4) sg[tid] = a.gk[k0 + tid].z;
+    if (OUT == 5) sg[tid] = a.invn[k0 + tid];
   }
   sr[tid >> 6][tid & 63] = a.Sref[((j0 >> 5) + (tid >> 6)) * a.ld_data + k0 + (tid & 63)];
 #pragma unroll
@@ -372,6 +416,7 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
   float2 L[8];
 #pragma unroll
   for (int u = 0; u < 8; u++) L[u] = sl[kb + u];
+  int nz = 0;
 #pragma unroll 1
   for (int pass = 0; pass < kNormRows / 32; pass++) {
     const int jj = (tid >> 3) + 32 * pass;
@@ -383,6 +428,7 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
       bh = (float)(rint(b * kGridD) / kGridD);
       bl = (float)(b - (double)bh);
     }
+    const float Bj = (OUT == 5 && row_ok) ? (float)a.Bsum[j] : 0.f;
     float p[8], dsum = 0.f;
 #pragma unroll
     for (int u = 0; u < 8; u++) {
@@ -394,6 +440,9 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
         dsum += pr;
         const float q = fmaxf(d + ((r - bh) - bl), 0.f);
         p[u] = ok ? pr * sqrtf(q * sg[kb + u]) : 0.f;
+      } else if (OUT == 5) {
+        dsum += pr;
+        p[u] = pr * (Bj * sg[kb + u]);
       } else {
         p[u] = pr;
       }
@@ -402,6 +451,8 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
       float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.P) + j * a.ld_data + k);
       o[0] = make_float4(p[0], p[1], p[2], p[3]);
       o[1] = make_float4(p[4], p[5], p[6], p[7]);
+#pragma unroll
+      for (int u = 0; u < 8; u++) nz |= p[u] != 0.f;
     } else {
       uint32_t h[4], l[4];
 #pragma unroll
@@ -425,13 +476,18 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
       uint16_t* ph = reinterpret_cast<uint16_t*>(a.P) + j * a.ld_data + k;
       *reinterpret_cast<uint4*>(ph) = make_uint4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<uint4*>(ph + a.P_plane) = make_uint4(l[0], l[1], l[2], l[3]);
+      nz |= (h[0] | h[1] | h[2] | h[3] | l[0] | l[1] | l[2] | l[3]) != 0u;
     }
-    if (OUT == 4) {  // the 8 threads of a row are consecutive lanes
+    if (OUT == 4 || OUT == 5) {  // the 8 threads of a row are consecutive lanes
       dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
       dsum += __shfl_xor_sync(0xffffffffu, dsum, 2);
       dsum += __shfl_xor_sync(0xffffffffu, dsum, 4);
       if (kq == 0 && row_ok && dsum > 0.f) atomicAdd(a.den + j, dsum);
     }
+  }
+  if (a.kb_flag) {  // uniform: every thread reaches the barrier
+    const int any = __syncthreads_or(nz);
+    if (tid == 0) a.kb_flag[(int64_t)blockIdx.y * a.kb_ld + blockIdx.x] = any ? 1 : 0;
   }
 }
 
@@ -439,8 +495,11 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
 cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sref,
                                     const float2* lse2, int64_t rows, int64_t nrot,
                                     int64_t ld_data, int64_t n_data, int precision, void* P,
-                                    int64_t P_plane, cudaStream_t s) {
-  NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane, nullptr, nullptr, nullptr};
+                                    int64_t P_plane, cudaStream_t s, uint8_t* kb_flag) {
+  NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane,
+             nullptr, nullptr, nullptr, nullptr, nullptr};
+  a.kb_flag = kb_flag;
+  a.kb_ld = ld_data / kNormFrames;
   dim3 grid((unsigned)(ld_data / kNormFrames), (unsigned)(rows / kNormRows));
   if (precision == EMC_PREC_FP32)
     normalize_scores_kernel<0><<<grid, 256, 0, s>>>(a);
@@ -457,12 +516,60 @@ cudaError_t launch_normalize_scores_gauss(const float* S, int64_t ldS, const flo
                                           const float2* lse2, const double* bias,
                                           const float4* gk, int64_t rows, int64_t nrot,
                                           int64_t ld_data, int64_t n_data, uint16_t* P,
-                                          int64_t P_plane, float* den, cudaStream_t s) {
+                                          int64_t P_plane, float* den, cudaStream_t s,
+                                          uint8_t* kb_flag) {
   cudaError_t e = cudaMemsetAsync(den, 0, sizeof(float) * rows, s);
   if (e != cudaSuccess) return e;
-  NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane, bias, gk, den};
+  NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane, bias, gk, den, nullptr,
+             nullptr};
+  a.kb_flag = kb_flag;
+  a.kb_ld = ld_data / kNormFrames;
   dim3 grid((unsigned)(ld_data / kNormFrames), (unsigned)(rows / kNormRows));
   normalize_scores_kernel<4><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_scores_flu(const float* S, int64_t ldS, const float* Sref,
+                                        const float2* lse2, const double* Bsum, const float* invn,
+                                        int64_t rows, int64_t nrot, int64_t ld_data,
+                                        int64_t n_data, uint16_t* P, int64_t P_plane, float* den,
+                                        cudaStream_t s, uint8_t* kb_flag) {
+  cudaError_t e = cudaMemsetAsync(den, 0, sizeof(float) * rows, s);
+  if (e != cudaSuccess) return e;
+  NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane, nullptr, nullptr, den, Bsum,
+             invn};
+  a.kb_flag = kb_flag;
+  a.kb_ld = ld_data / kNormFrames;
+  dim3 grid((unsigned)(ld_data / kNormFrames), (unsigned)(rows / kNormRows));
+  normalize_scores_kernel<5><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Per row tile mt (one warp each): the indices of the 64-frame blocks whose
+// flag is set, in order, into list[mt * kb_ld ..] and their number into cnt[mt]
+// (the update then contracts only those blocks of P).
+__global__ void kb_lists_kernel(const uint8_t* __restrict__ flag, int64_t n_mtiles, int kb_ld,
+                                int32_t* __restrict__ cnt, int32_t* __restrict__ list) {
+  const int64_t mt = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (mt >= n_mtiles) return;
+  const uint8_t* f = flag + mt * kb_ld;
+  int32_t* out = list + mt * kb_ld;
+  int n = 0;
+  for (int b0 = 0; b0 < kb_ld; b0 += 32) {
+    const bool on = b0 + lane < kb_ld && f[b0 + lane] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    if (on) out[n + __popc(m & ((1u << lane) - 1u))] = b0 + lane;
+    n += __popc(m);
+  }
+  if (lane == 0) cnt[mt] = n;
+}
+
+cudaError_t launch_kb_lists(const uint8_t* flag, int64_t n_mtiles, int kb_ld, int32_t* cnt,
+                            int32_t* list, cudaStream_t s) {
+  const int64_t threads = n_mtiles * 32;
+  kb_lists_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(flag, n_mtiles, kb_ld, cnt,
+                                                                   list);
   return cudaGetLastError();
 }
 

@@ -384,9 +384,11 @@ __global__ void __launch_bounds__(256)
 }
 
 // One warp per frame: lse over the frame's M candidates, P = exp(S - lse).
+// shift (may be NULL): per-frame constant the scores carry (Poisson-fluence
+// model), removed from the lse written out.
 __global__ void sparse_lse_kernel(const double* __restrict__ Sc, int64_t n_data, int64_t ld_data,
                                   int M, float* __restrict__ Pc, double* __restrict__ lse_c,
-                                  int32_t* status) {
+                                  const double* __restrict__ shift, int32_t* status) {
   const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= ld_data) return;
@@ -405,25 +407,32 @@ __global__ void sparse_lse_kernel(const double* __restrict__ Sc, int64_t n_data,
   const double lse = mx + log(sum);
   if (!isfinite(lse)) set_status(status, EMC_ERR_NUMERIC);
   for (int m = lane; m < M; m += 32) p[m] = __expf((float)(s[m] - lse));
-  if (lane == 0) lse_c[k] = lse;
+  if (lane == 0) lse_c[k] = lse - (shift ? shift[k] : 0.0);
 }
 
 // One CTA per rotation row: Num_j = sum over the row's list of P_jk K_k; the
 // K column of ones at n_pix gives den_j. Each thread owns 8 consecutive pixels
 // (one 16-byte load of a K row per pair), the list is staged in shared memory
 // in segments and walked four pairs at a time. Rows without pairs are zeroed.
+// Poisson-fluence model (Bsum != NULL): the pairs carry P_jk B_j / N_k and
+// den_j = sum P_jk is summed from the staged pairs instead.
 template <bool KF16>
 __global__ void __launch_bounds__(256)
     sparse_update_kernel(const uint16_t* __restrict__ Kb, int64_t ld_pix, int64_t n_pix,
                          const int64_t* __restrict__ off, const int2* __restrict__ ent, int M,
                          const float* __restrict__ Pc, float* __restrict__ Num,
-                         float* __restrict__ den) {
+                         float* __restrict__ den, const double* __restrict__ Bsum,
+                         const float* __restrict__ invn) {
   const int64_t j = blockIdx.x;
   const int64_t e0 = off[j], e1 = off[j + 1];
   float* out = Num + j * ld_pix;
   constexpr int kSeg = 1024;
   __shared__ int sk[kSeg];
   __shared__ float sp[kSeg];
+  __shared__ float sden[8];
+  const bool flu = Bsum != nullptr;
+  const float Bj = flu ? (float)Bsum[j] : 0.f;
+  float dsum = 0.f;
   const int64_t n8 = ld_pix / 8;
   for (int64_t g0 = 0; g0 < n8; g0 += 256) {
     const int64_t g = g0 + threadIdx.x;
@@ -434,7 +443,13 @@ __global__ void __launch_bounds__(256)
       for (int t = threadIdx.x; t < ns; t += 256) {
         const int2 km = ent[s0 + t];
         sk[t] = km.x;
-        sp[t] = Pc[(int64_t)km.x * M + km.y];
+        const float p = Pc[(int64_t)km.x * M + km.y];
+        if (flu) {
+          if (g0 == 0) dsum += p;
+          sp[t] = p * (Bj * invn[km.x]);
+        } else {
+          sp[t] = p;
+        }
       }
       __syncthreads();
       if (g < n8) {
@@ -475,11 +490,21 @@ __global__ void __launch_bounds__(256)
       float4* o4 = reinterpret_cast<float4*>(out + 8 * g);
       o4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
       o4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-      if (n_pix >= 8 * g && n_pix < 8 * g + 8) {
+      if (!flu && n_pix >= 8 * g && n_pix < 8 * g + 8) {
 #pragma unroll
         for (int c = 0; c < 8; c++)
           if (8 * g + c == n_pix) den[j] = acc[c];
       }
+    }
+  }
+  if (flu) {
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if ((threadIdx.x & 31) == 0) sden[threadIdx.x >> 5] = dsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float d = 0.f;
+      for (int w = 0; w < 8; w++) d += sden[w];
+      den[j] = d;
     }
   }
 }
@@ -487,12 +512,14 @@ __global__ void __launch_bounds__(256)
 // CSR form of the sparse update: the row Num_j accumulates in shared memory
 // (FP32 atomics; a frame's non-zero pixels are distinct) from every pair's
 // P_jk times the frame's non-zero counts, then is written out whole with
-// den_j = sum of the row's P_jk. Rows without pairs are zeroed.
+// den_j = sum of the row's P_jk. Rows without pairs are zeroed. Poisson-
+// fluence model (Bsum != NULL): the counts are weighted by P_jk B_j / N_k.
 __global__ void __launch_bounds__(256)
     sparse_update_csr_kernel(const int64_t* __restrict__ koff, const uint32_t* __restrict__ kent,
                              int64_t ld_pix, const int64_t* __restrict__ off,
                              const int2* __restrict__ ent, int M, const float* __restrict__ Pc,
-                             float* __restrict__ Num, float* __restrict__ den) {
+                             float* __restrict__ Num, float* __restrict__ den,
+                             const double* __restrict__ Bsum, const float* __restrict__ invn) {
   const int64_t j = blockIdx.x;
   const int64_t e0 = off[j], e1 = off[j + 1];
   extern __shared__ float4 sm4u[];
@@ -502,10 +529,12 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   float dsum = 0.f;
+  const float Bj = Bsum ? (float)Bsum[j] : 0.f;
   for (int64_t e = e0 + wid; e < e1; e += nw) {
     const int2 km = ent[e];
-    const float p = Pc[(int64_t)km.x * M + km.y];
-    dsum += p;
+    const float p0 = Pc[(int64_t)km.x * M + km.y];
+    dsum += p0;
+    const float p = Bsum ? p0 * (Bj * invn[km.x]) : p0;
     const int64_t f1 = koff[km.x + 1];
     for (int64_t f = koff[km.x] + lane; f < f1; f += 32) {
       const uint32_t w = kent[f];
@@ -570,31 +599,34 @@ cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, c
 }
 
 cudaError_t launch_sparse_lse(const double* Sc, int64_t n_data, int64_t ld_data, int M, float* Pc,
-                              double* lse_c, int32_t* status, cudaStream_t s) {
+                              double* lse_c, int32_t* status, cudaStream_t s,
+                              const double* shift) {
   sparse_lse_kernel<<<(unsigned)((ld_data * 32 + 255) / 256), 256, 0, s>>>(Sc, n_data, ld_data, M,
-                                                                          Pc, lse_c, status);
+                                                                          Pc, lse_c, shift, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, int64_t n_pix,
                                  const int64_t* off, const int2* ent, int M, const float* Pc,
                                  int64_t rows, const int64_t* koff, const uint32_t* kent,
-                                 float* Num, float* den, cudaStream_t s) {
+                                 float* Num, float* den, cudaStream_t s, const double* Bsum,
+                                 const float* invn) {
+  if (Bsum && !invn) return cudaErrorInvalidValue;
   if (kent) {
     const size_t smem = sizeof(float) * (size_t)ld_pix;
     cudaError_t e = cudaFuncSetAttribute(sparse_update_csr_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     sparse_update_csr_kernel<<<(unsigned)rows, 256, smem, s>>>(koff, kent, ld_pix, off, ent, M, Pc,
-                                                               Num, den);
+                                                               Num, den, Bsum, invn);
     return cudaGetLastError();
   }
   if (kf16)
     sparse_update_kernel<true><<<(unsigned)rows, 256, 0, s>>>(Kb, ld_pix, n_pix, off, ent, M, Pc,
-                                                              Num, den);
+                                                              Num, den, Bsum, invn);
   else
     sparse_update_kernel<false><<<(unsigned)rows, 256, 0, s>>>(Kb, ld_pix, n_pix, off, ent, M, Pc,
-                                                               Num, den);
+                                                               Num, den, Bsum, invn);
   return cudaGetLastError();
 }
 

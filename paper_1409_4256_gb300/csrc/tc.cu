@@ -104,9 +104,31 @@ struct TcArgs {
   uint16_t* P;             // normalize: planes [2][rows][ld_data]
   int64_t P_plane;
   float* Num;              // update: [rows][ld_pix]
-  float* den;              // update: [rows]
+  float* den;              // update: [rows]; Poisson-fluence normalize: sum_k P_jk (atomics)
+  const double* Bsum;      // Poisson-fluence normalize: B_j [rows] (NULL otherwise)
+  const float* invn;       // Poisson-fluence normalize: 1 / N_k [ld_data]
+  // update over the non-zero P blocks only (NULL: every K block): per row tile
+  // mt, kb_cnt[mt] K-block indices (64 frames each) in kb_list[mt * kb_ld ..]
+  const int32_t* kb_cnt;
+  const int32_t* kb_list;
+  // normalize: kb_flag[mt * kb_ld + kb] set to 1 where the block's P is non-zero
+  uint8_t* kb_flag;
+  int kb_ld;
   int32_t* status;
 };
+
+// K blocks a tile contracts: every block, or (update with lists) the row
+// tile's non-zero P blocks -- at least one, so that a tile whose P is zero
+// still clears its accumulator (block 0 of it holds zeros).
+__device__ __forceinline__ int tile_kblocks(const TcArgs& a, int mt) {
+  if (!a.kb_cnt) return a.kblocks;
+  const int n = a.kb_cnt[mt];
+  return n > 0 ? n : 1;
+}
+__device__ __forceinline__ int tile_kblock(const TcArgs& a, int mt, int x) {
+  if (!a.kb_cnt) return x;
+  return a.kb_cnt[mt] > 0 ? a.kb_list[(int64_t)mt * a.kb_ld + x] : 0;
+}
 
 __device__ __forceinline__ void tile_coords(int t, const TcArgs& a, int* mt, int* nt) {
   const int per_group = a.group * a.n_ntiles;
@@ -193,7 +215,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
         int mt, nt;
         tile_coords(t, a, &mt, &nt);
-        for (int kb = 0; kb < a.kblocks; kb++, it++) {
+        const int nkb = tile_kblocks(a, mt);
+        for (int x = 0; x < nkb; x++, it++) {
+          const int kb = tile_kblock(a, mt, x);
           const int s = it % C::STAGES;
           const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
           if (!mbar_wait(empty + s, ph ^ 1u, abort, kWaitLimitNs)) {
@@ -235,7 +259,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        for (int kb = 0; kb < a.kblocks; kb++, it++) {
+        int mt_, nt_;
+        tile_coords(t, a, &mt_, &nt_);
+        const int nkb = tile_kblocks(a, mt_);
+        for (int kb = 0; kb < nkb; kb++, it++) {
           const int s = it % C::STAGES;
           const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
           if (!mbar_wait(full + s, ph, abort, kWaitLimitNs)) {
@@ -307,8 +334,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         cs[et] = make_float2(g.x * is2, g.y * is2);
         named_bar(1, kEpiThreads);
       }
+      // Poisson-fluence normalize: P_jk B_j / N_k into the planes, den_j = sum_k P_jk
+      const bool flu = MODE == MODE_NORMALIZE && a.Bsum != nullptr;
+      float* sinv = reinterpret_cast<float*>(scratch + BN);
+      float Bj = 0.f, dsum = 0.f;
       if (MODE == MODE_NORMALIZE) {
         scratch[et] = a.lse2[(int64_t)nt * BN + et];
+        if (flu) {
+          sinv[et] = a.invn[(int64_t)nt * BN + et];
+          if (valid) Bj = (float)a.Bsum[row];
+        }
         named_bar(1, kEpiThreads);
       }
       if (!mbar_wait(acc_full, (uint32_t)tcount & 1u, abort, kWaitLimitNs)) {
@@ -417,6 +452,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               const float2 L = scratch[col0 + i + u];
               const float d = (xh[i + u] - L.x) + (xl[i + u] - L.y);
               pr[u] = (valid && k0 + i + u < a.n_data) ? __expf(d) : 0.f;
+              if (flu) {
+                dsum += pr[u];
+                pr[u] *= Bj * sinv[col0 + i + u];
+              }
             }
             if (F16) {  // FP16 hi + lo of 2^14 P
               const float s0 = pr[0] * kP16Scale, s1 = pr[1] * kP16Scale;
@@ -427,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
               const uint16_t h0 = bf16_bits(pr[0]), h1 = bf16_bits(pr[1]);
               ph[i / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-              if (NA == 3) {
+              if (NA == 3 || flu) {
                 const uint16_t l0 = bf16_bits(pr[0] - bf16_val(h0));
                 const uint16_t l1 = bf16_bits(pr[1] - bf16_val(h1));
                 pl[i / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
@@ -435,6 +474,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 pl[i / 2] = 0u;
               }
             }
+          }
+          if (a.kb_flag) {  // this warp's 32 rows x 32 frames: any non-zero P?
+            uint32_t any = 0u;
+#pragma unroll
+            for (int i = 0; i < 16; i++) any |= ph[i] | pl[i];
+            if (__any_sync(0xffffffffu, any != 0u) && lane == 0)
+              a.kb_flag[(int64_t)mt * a.kb_ld + (k0 >> 6)] = 1;
           }
           uint16_t* dh = a.P + row * a.ld_data + k0;
           uint16_t* dl = dh + a.P_plane;
@@ -446,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (NA >= 2 && big && valid) set_status(a.status, EMC_ERR_NUMERIC);
+      if (flu && valid && dsum > 0.f) atomicAdd(a.den + row, dsum);
       if (MODE == MODE_PASS1) {
         named_bar(1, kEpiThreads);
         const int col = et;  // one frame column per epilogue thread
@@ -597,9 +644,20 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
 cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bias, int64_t rows,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
-                                float2* lse2, Planes P, int32_t* status, cudaStream_t s) {
-  cudaError_t e = launch_lse_split(lse_m, lse_s, n_data, ld_data, lse2, s);
+                                float2* lse2, Planes P, int32_t* status, cudaStream_t s,
+                                const double* shift, const double* Bsum, const float* invn,
+                                float* den, uint8_t* kb_flag) {
+  cudaError_t e = launch_lse_split(lse_m, lse_s, n_data, ld_data, lse2, s, shift);
   if (e != cudaSuccess) return e;
+  if (kb_flag) {
+    e = cudaMemsetAsync(kb_flag, 0, (size_t)(rows / BM) * (ld_data / 64), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (Bsum) {
+    if (!invn || !den || precision == EMC_PREC_FP16_SPLIT) return cudaErrorInvalidValue;
+    e = cudaMemsetAsync(den, 0, sizeof(float) * rows, s);
+    if (e != cudaSuccess) return e;
+  }
   const int nterms = score_planes(precision);
   CUtensorMap mA, mB;
   if (!maps_scores(L, nterms, precision == EMC_PREC_FP16_SPLIT, rows, Kb, ld_data, ld_pix, &mA,
@@ -614,6 +672,11 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
   a.lse2 = lse2;
   a.P = reinterpret_cast<uint16_t*>(P.base);
   a.P_plane = P.plane_stride;
+  a.Bsum = Bsum;
+  a.invn = invn;
+  a.den = den;
+  a.kb_flag = kb_flag;
+  a.kb_ld = (int)(ld_data / 64);
   a.status = status;
   if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_NORMALIZE, 2, true>(mA, mB, a, s);
   return nterms == 3 ? launch<MODE_NORMALIZE, 3, false>(mA, mB, a, s)
@@ -622,7 +685,8 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
 
 cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
-                             int32_t* status, cudaStream_t s) {
+                             int32_t* status, cudaStream_t s, const int32_t* kb_cnt,
+                             const int32_t* kb_list) {
   const int nterms = precision == EMC_PREC_BF16 ? 1 : 2;
   const bool f16 = precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
@@ -641,6 +705,9 @@ cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const
   a.ld_data = ld_data;
   a.Num = Num;
   a.den = den;
+  a.kb_cnt = kb_cnt;
+  a.kb_list = kb_list;
+  a.kb_ld = (int)(ld_data / 64);
   a.status = status;
   if (f16) return launch<MODE_UPDATE, 2, true>(mA, mB, a, s);
   return nterms == 2 ? launch<MODE_UPDATE, 2, false>(mA, mB, a, s)

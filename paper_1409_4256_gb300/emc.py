@@ -23,8 +23,9 @@ COMPRESS_DEFERRED, COMPRESS_IDW = 0, 1
 FLAG_STORE_SCORES = 1
 FLAG_SPARSE_K = 2
 FLAG_WIDE_COUNTS = 4
-MODEL_POISSON, MODEL_GAUSSIAN = 0, 1
-MODELS = {"poisson": MODEL_POISSON, "gaussian": MODEL_GAUSSIAN}
+MODEL_POISSON, MODEL_GAUSSIAN, MODEL_POISSON_FLUENCE = 0, 1, 2
+MODELS = {"poisson": MODEL_POISSON, "gaussian": MODEL_GAUSSIAN,
+          "poisson_fluence": MODEL_POISSON_FLUENCE}
 
 _lock = threading.Lock()
 _lib = None
@@ -289,7 +290,7 @@ class Context:
     def expand(self, grid, rot0: int, nrot: int, stream=None):
         b = self.buffer_sizes(nrot)
         L = self._bytes(b.logw_bytes)
-        bias = self.torch.empty(b.rows, dtype=self.torch.float64, device=self.device)
+        bias = self.torch.empty(b.bias_bytes // 8, dtype=self.torch.float64, device=self.device)
         _check(lib().emc_expand(self.h, _ptr(grid), rot0, nrot, _ptr(L), _ptr(bias),
                                 _stream(stream)), "emc_expand")
         return L, bias

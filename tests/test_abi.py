@@ -87,8 +87,35 @@ def test_gaussian_config_checks(libemc):
 
     assert ws() == 0
     assert ws(precision=2) == -4 and ws(flags=0) == -4 and ws(n_cand=8) == -4
-    assert ws(sigma=0.0) == -1 and ws(sigma=float("nan")) == -1 and ws(model=2) == -1
+    assert ws(sigma=0.0) == -1 and ws(sigma=float("nan")) == -1 and ws(model=3) == -1
     assert ws(model=0, sigma=0.0) == 0  # sigma is not read for the Poisson model
+
+
+def test_poisson_fluence_config_checks(libemc):
+    # the Poisson-fluence model takes the BF16 split only (one rounded value of
+    # log(W / B_j) per element would bias every rotation's score by a multiple
+    # of N_k); its P buffer carries den[rows] after the planes
+    from paper_1409_4256_gb300 import emc
+    nb = ctypes.c_size_t()
+
+    def cfg(**kw):
+        base = dict(N=32, precision=2, n_pix=100, n_rot=50, n_data=10, w_floor=1e-10,
+                    compress_mode=0, flags=0, rot_chunk=0, n_cand=0, model=2, sigma=0.0)
+        base.update(kw)
+        return emc.Config(**base)
+
+    def ws(**kw):
+        return libemc.emc_workspace_size(ctypes.byref(cfg(**kw)), ctypes.byref(nb))
+
+    assert ws() == 0 and ws(flags=1) == 0 and ws(n_cand=8) == 0
+    assert ws(precision=0) == -4 and ws(precision=1) == -4 and ws(precision=3) == -4
+    # a tiny floor is no error on the host: log(W / B_j) is range-checked on the device
+    assert ws(w_floor=1e-30) == 0
+    b, b0 = emc.BufferSizes(), emc.BufferSizes()
+    assert libemc.emc_buffer_sizes_for(ctypes.byref(cfg()), 50, ctypes.byref(b)) == 0
+    assert libemc.emc_buffer_sizes_for(ctypes.byref(cfg(model=0)), 50, ctypes.byref(b0)) == 0
+    assert b.prob_bytes == b0.prob_bytes + 4 * 128  # float den[128] after the planes
+    assert b.logw_bytes == b0.logw_bytes
 
 
 def test_sparse_k_config_checks(libemc):

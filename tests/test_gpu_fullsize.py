@@ -38,14 +38,20 @@ def torch_cuda():
     return torch
 
 
-def _oracle_columns(oracle, grid, quat, w, q, Ks, floor, chunk=4096):
-    """FP64 scores of the sampled frames Ks against every rotation -> (lse, P)."""
-    S = np.empty((quat.shape[0], Ks.shape[0]))
+def _oracle_columns(oracle, grid, quat, w, q, Ks, floor, chunk=4096, models=("poisson",)):
+    """FP64 scores of the sampled frames Ks against every rotation, for each noise
+    model from the same expansion -> {model: (lse, P)}."""
+    S = {m: np.empty((quat.shape[0], Ks.shape[0])) for m in models}
     for j0 in range(0, quat.shape[0], chunk):
         W = oracle.expand(grid, quat[j0:j0 + chunk], q, floor)
-        S[j0:j0 + chunk] = oracle.scores(W, w[j0:j0 + chunk], Ks)
-    P, lse, _ = oracle.estep(S)
-    return lse, P
+        for m in models:
+            f = oracle.scores_poisson_fluence if m == "poisson_fluence" else oracle.scores
+            S[m][j0:j0 + chunk] = f(W, w[j0:j0 + chunk], Ks)
+    out = {}
+    for m in models:
+        P, lse, _ = oracle.estep(S[m])
+        out[m] = (lse, P)
+    return out
 
 
 def _dataset(name):
@@ -56,16 +62,27 @@ def _dataset(name):
                                    fluence_sigma=cfg["fluence_sigma"], device="cuda")
 
 
-def _run(torch, oracle, name, block, sample, wide=False):
-    from paper_1409_4256_gb300 import emc
+def _run(torch, oracle, name, block, sample, wide=False, models=("poisson",)):
     cfg, ds = _dataset(name)
+    res = {m: _run_model(torch, cfg, ds, block, sample, wide, m) for m in models}
+    quat_o, w_o = oracle.quat_generate(cfg["n_quat"])  # the oracle's own sampling (same order)
+    grid = ds.model_start.astype(np.float32).astype(np.float64)
+    cols = _oracle_columns(oracle, grid, quat_o, w_o, ds.q, ds.K[sample].astype(np.float64),
+                           1e-10 * float(ds.model_start.mean()), models=models)
+    for m in models:
+        res[m]["lse_o"], res[m]["P_o"] = cols[m]
+    return res
+
+
+def _run_model(torch, cfg, ds, block, sample, wide, model):
+    from paper_1409_4256_gb300 import emc
     quat, w = emc.quat_generate(cfg["n_quat"])       # the library's sampling
-    quat_o, w_o = oracle.quat_generate(cfg["n_quat"])  # the oracle's own (same order)
     nrot, nd, npix = quat.shape[0], ds.K.shape[0], ds.q.shape[0]
     grid32 = ds.model_start.astype(np.float32)
     floor = 1e-10 * float(ds.model_start.mean())
+    flu = model == "poisson_fluence"
     ctx = emc.Context(cfg["N"], ds.q, quat, w, nd, precision="bf16_split", w_floor=floor,
-                      rot_chunk=block, wide_counts=wide)
+                      rot_chunk=block, wide_counts=wide, model=model)
     ctx.set_frames(torch.as_tensor(ds.K, device="cuda"))
     g = torch.as_tensor(grid32, device="cuda")
     lse_m = torch.empty(ctx.ld_data, dtype=torch.float64, device="cuda")
@@ -80,6 +97,7 @@ def _run(torch, oracle, name, block, sample, wide=False):
     Pcols = np.empty((nrot, len(sample)))
     den_sum = 0.0
     num_sum = 0.0
+    row_err = 0.0  # fluence model: sum_i Num_ij = B_j den_j for every row
     g_num = torch.zeros((cfg["N"],) * 3, dtype=torch.float64, device="cuda")
     g_den = torch.zeros_like(g_num)
     sidx = torch.as_tensor(sample, device="cuda")
@@ -90,32 +108,45 @@ def _run(torch, oracle, name, block, sample, wide=False):
         m2 = torch.empty_like(lse_m)
         s2 = torch.empty_like(lse_s)
         ctx.loglik(L, bias, nb, m2, s2, scores=Sb)  # the block's stored scores
-        P = ctx.normalize(None, None, nb, lse_m, lse_s, scores=Sb)
+        # (the fluence model reads B_j from the second half of bias)
+        P = ctx.normalize(None, bias if flu else None, nb, lse_m, lse_s, scores=Sb)
         b = ctx.buffer_sizes(nb)
-        planes = P.view(torch.bfloat16).view(2, b.rows, b.ld_data)
-        Pcols[r0:r0 + nb] = (planes[0].index_select(1, sidx).double() +
-                             planes[1].index_select(1, sidx).double())[:nb].cpu().numpy()
+        planes = P[:4 * b.rows * b.ld_data].view(torch.bfloat16).view(2, b.rows, b.ld_data)
+        Pc = (planes[0].index_select(1, sidx).double() +
+              planes[1].index_select(1, sidx).double())[:nb]
+        if flu:  # the planes hold P B_j / N_k
+            B = bias[b.rows:b.rows + nb].view(-1, 1)
+            Nk = torch.as_tensor(ds.K[sample].sum(1), device="cuda").double().view(1, -1)
+            Pc = Pc * Nk / B
+        Pcols[r0:r0 + nb] = Pc.cpu().numpy()
         Num, den = ctx.update(P, nb)
         den_sum += float(den[:nb].double().sum())
         # pixel columns and duplicate columns (counts above 256), not the ones column
-        num_sum += float(Num[:nb, :npix].double().sum() + Num[:nb, npix + 1:].double().sum())
+        rows = Num[:nb, :npix].double().sum(1) + Num[:nb, npix + 1:].double().sum(1)
+        num_sum += float(rows.sum())
+        if flu:  # rows whose responsibilities stay in FP32's normal range
+            d64 = den[:nb].double()
+            want = bias[b.rows:b.rows + nb] * d64
+            ok = d64 >= 1e-20
+            row_err = max(row_err, float(((rows - want).abs()[ok] / want[ok]).max()))
         ctx.compress(r0, nb, Num, den, g_num, g_den, accumulate=True)
         del L, bias, Sb, P, Num, den
     torch.cuda.synchronize()
     assert ctx.status() == 0
     lse = (lse_m + torch.log(lse_s)).cpu().numpy()
-    lse_o, P_o = _oracle_columns(oracle, grid32.astype(np.float64), quat_o, w_o, ds.q,
-                                 ds.K[sample].astype(np.float64), floor)
-    return dict(lse=lse[:nd], lse_o=lse_o, P=Pcols, P_o=P_o, den_sum=den_sum, num_sum=num_sum,
+    return dict(lse=lse[:nd], P=Pcols, den_sum=den_sum, num_sum=num_sum,
                 photons=float(ds.K.astype(np.float64).sum()), nd=nd, npix=npix,
-                g_num=float(g_num.sum()), g_den=float(g_den.sum()))
+                g_num=float(g_num.sum()), g_den=float(g_den.sum()), flu=flu, row_err=row_err)
 
 
 def _check(r, sample):
     assert np.abs(r["lse"][sample] - r["lse_o"]).max() <= 1e-4
     assert np.abs(r["P"] - r["P_o"]).max() <= 1e-4
     assert abs(r["den_sum"] - r["nd"]) <= 1e-4 * r["nd"]
-    assert abs(r["num_sum"] - r["photons"]) <= 1e-4 * r["photons"]
+    if r["flu"]:  # no frame is empty: sum_i Num_ij = sum_k P_jk B_j = B_j den_j
+        assert r["row_err"] <= 1e-4
+    else:
+        assert abs(r["num_sum"] - r["photons"]) <= 1e-4 * r["photons"]
     assert abs(r["g_den"] - r["npix"] * r["den_sum"]) <= 1e-6 * r["g_den"]
     assert abs(r["g_num"] - r["num_sum"]) <= 1e-6 * r["g_num"]
 
@@ -123,20 +154,24 @@ def _check(r, sample):
 def test_fullsize_emc64(torch_cuda, oracle):
     sample = np.array([0, 7, 4321, 12345, 19999])
     r = _run(torch_cuda, oracle, "emc64", 50100, sample)
-    _check(r, sample)
+    _check(r["poisson"], sample)
 
 
 def test_fullsize_emc128(torch_cuda, oracle):
     sample = np.array([3, 54321, 99999])
     r = _run(torch_cuda, oracle, "emc128", 8192, sample)
-    _check(r, sample)
+    _check(r["poisson"], sample)
 
 
 def test_fullsize_emc160(torch_cuda, oracle):
+    # both noise models on the same frames: the frames carry log-normal
+    # fluence, which the Poisson-fluence model fits; a few pixels of the
+    # brightest frames exceed 256 photons (duplicate columns)
     sample = np.array([1, 123456, 199999])
-    # a few pixels of the brightest frames exceed 256 photons: duplicate columns
-    r = _run(torch_cuda, oracle, "emc160", 8192, sample, wide=True)
-    _check(r, sample)
+    r = _run(torch_cuda, oracle, "emc160", 8192, sample, wide=True,
+             models=("poisson", "poisson_fluence"))
+    for m in r:
+        _check(r[m], sample)
 
 
 def test_fullsize_emc32_every_output(torch_cuda, oracle):

@@ -221,6 +221,38 @@ def test_iteration_chunked_equals_whole(torch_cuda, small_problem, precision):
     assert rel_l2(b.cpu().numpy().astype(np.float64), a.cpu().numpy().astype(np.float64)) < 1e-7
 
 
+def _steps_dense(torch, ctx, g, nrot, stored):
+    # the step calls: their update contracts every block of P
+    L, bias = ctx.expand(g, 0, nrot)
+    Sb = ctx.scores_buffer(nrot) if stored else None
+    m, s = ctx.loglik(L, bias, nrot, scores=Sb)
+    P = ctx.normalize(L, bias, nrot, m, s, scores=Sb)
+    Num, den = ctx.update(P, nrot)
+    gn, gd = ctx.compress(0, nrot, Num, den)
+    return ctx.finalize(gn, gd, g)
+
+
+@pytest.mark.parametrize("precision", ["bf16_split", "fp16_split", "bf16"])
+@pytest.mark.parametrize("stored", [True, False])
+@pytest.mark.parametrize("n_frames", [300, 1])
+def test_iteration_skips_only_zero_blocks(torch_cuda, small_problem, precision, stored, n_frames):
+    # emc_iteration's update contracts only the 128-rotation x 64-frame blocks
+    # of P that hold a non-zero value; blocks of exact zeros add nothing, so the
+    # model equals the dense step calls' up to the order of the FP64 reductions.
+    # One frame: most row tiles have no non-zero block at all.
+    torch, p = torch_cuda, dict(small_problem)
+    p["K"] = p["K"][:n_frames]
+    nrot = p["quat"].shape[0]
+    g = grid_dev(torch, p)
+    ctx = make_ctx(torch, p, precision, store_scores=stored)
+    a, st = ctx.iteration(g)
+    b = _steps_dense(torch, ctx, g, nrot, stored)
+    torch.cuda.synchronize()
+    assert st["device_status"] == 0 and ctx.status() == 0
+    a, b = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+    assert rel_l2(a, b) <= 1e-12
+
+
 def test_iteration_idw_mode(torch_cuda, small_problem, ref):
     torch, p = torch_cuda, small_problem
     ctx = make_ctx(torch, p, "fp32", compress_mode=1)
