@@ -378,9 +378,16 @@ struct NormArgs {
   float* den;          // Gaussian, Poisson-fluence
   const double* Bsum;  // Poisson-fluence: B_j
   const float* invn;   // Poisson-fluence: 1 / N_k
-  uint8_t* kb_flag;    // optional: 1 where the CTA's 128 x 64 block of P is non-zero
+  uint8_t* kb_flag;    // optional: 1 where the CTA's 128 x 64 block of P is non-zero;
+                       // blocks found zero are then not written (their readers skip them)
   int64_t kb_ld;
 };
+
+// A 32-row group of stored scores whose maximum r lies more than 110 below
+// lse_k has P_jk = exp(d + r - lse_k) = 0 exactly for all its rows (d <= 2^-7,
+// and e^-110 < 2^-158 is below FP32's smallest subnormal, however exp is
+// evaluated): such groups are not read.
+constexpr float kUnderflowArg = -110.0f;
 
 constexpr int kNormRows = 128, kNormFrames = 64;
 
@@ -394,18 +401,51 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
   __shared__ float sg[kNormFrames];
   const int64_t j0 = (int64_t)blockIdx.y * kNormRows, k0 = (int64_t)blockIdx.x * kNormFrames;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float4 v[8];
-#pragma unroll
-  for (int r = 0; r < 8; r++) {  // warp w: frames w + 8 r; lane: rows 4 lane .. 4 lane + 3
-    const int k = warp + 8 * r;
-    v[r] = __ldcs(reinterpret_cast<const float4*>(a.S + (k0 + k) * a.ldS + j0) + lane);
-  }
   if (tid < kNormFrames) {
     sl[tid] = a.lse2[k0 + tid];
     if (OUT == 4) sg[tid] = a.gk[k0 + tid].z;
     if (OUT == 5) sg[tid] = a.invn[k0 + tid];
   }
   sr[tid >> 6][tid & 63] = a.Sref[((j0 >> 5) + (tid >> 6)) * a.ld_data + k0 + (tid & 63)];
+  __syncthreads();
+  {  // a block whose every (group, frame) underflows: P = 0 without reading S
+    const int gk = tid & 63;
+    const bool live = (sr[tid >> 6][gk] - sl[gk].x) - sl[gk].y >= kUnderflowArg;
+    if (!__syncthreads_or(live)) {
+      if (a.kb_flag) {
+        if (tid == 0) a.kb_flag[(int64_t)blockIdx.y * a.kb_ld + blockIdx.x] = 0;
+        return;
+      }
+      // dense output: zeros, 32 frames of one row per thread
+      const int64_t j = j0 + (tid >> 1), k = k0 + 32 * (tid & 1);
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      if (OUT == 0) {
+        uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<float*>(a.P) + j * a.ld_data + k);
+#pragma unroll
+        for (int q = 0; q < 8; q++) o[q] = z;
+      } else {
+        uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(a.P) + j * a.ld_data + k);
+        uint4* o2 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(a.P) + a.P_plane +
+                                             j * a.ld_data + k);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          o[q] = z;
+          o2[q] = z;
+        }
+      }
+      return;
+    }
+  }
+  float4 v[8];
+#pragma unroll
+  for (int r = 0; r < 8; r++) {  // warp w: frames w + 8 r; lane: rows 4 lane .. 4 lane + 3
+    const int k = warp + 8 * r;
+    const float2 lk = sl[k];
+    if ((sr[lane >> 3][k] - lk.x) - lk.y >= kUnderflowArg)
+      v[r] = __ldcs(reinterpret_cast<const float4*>(a.S + (k0 + k) * a.ldS + j0) + lane);
+    else  // the lane's 4 rows lie in an underflowing group: P = 0
+      v[r] = make_float4(-1.0e30f, -1.0e30f, -1.0e30f, -1.0e30f);
+  }
 #pragma unroll
   for (int r = 0; r < 8; r++) {
     const int k = warp + 8 * r;  // (k >> 3) & 7 == r

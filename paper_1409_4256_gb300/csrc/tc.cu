@@ -118,16 +118,14 @@ struct TcArgs {
 };
 
 // K blocks a tile contracts: every block, or (update with lists) the row
-// tile's non-zero P blocks -- at least one, so that a tile whose P is zero
-// still clears its accumulator (block 0 of it holds zeros).
+// tile's non-zero P blocks. A tile without any issues no load and no MMA; its
+// epilogue writes zeros instead of reading the accumulator (P itself need not
+// hold zeros there).
 __device__ __forceinline__ int tile_kblocks(const TcArgs& a, int mt) {
-  if (!a.kb_cnt) return a.kblocks;
-  const int n = a.kb_cnt[mt];
-  return n > 0 ? n : 1;
+  return a.kb_cnt ? a.kb_cnt[mt] : a.kblocks;
 }
 __device__ __forceinline__ int tile_kblock(const TcArgs& a, int mt, int x) {
-  if (!a.kb_cnt) return x;
-  return a.kb_cnt[mt] > 0 ? a.kb_list[(int64_t)mt * a.kb_ld + x] : 0;
+  return a.kb_cnt ? a.kb_list[(int64_t)mt * a.kb_ld + x] : x;
 }
 
 __device__ __forceinline__ void tile_coords(int t, const TcArgs& a, int* mt, int* nt) {
@@ -366,6 +364,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (MODE == MODE_UPDATE) {
           const int64_t n0 = (int64_t)nt * BN + col0;
+          if (a.kb_cnt && a.kb_cnt[mt] == 0) {  // no non-zero block: Num = 0, den = 0
+#pragma unroll
+            for (int i = 0; i < 32; i++) v0[i] = 0u;
+          }
           if (n0 < a.ld_pix) {
             if (F16) {  // FP16 responsibilities carry a 2^14 scale
 #pragma unroll
