@@ -540,7 +540,7 @@ def run_ours(args):
     traffic = None
     if (args.workload == "emc64" and args.precision == "bf16_split" and n_data == 20000
             and n_rot == 50100 and not args.recompute):
-        traffic = 6.82e9 + 4.25e9
+        traffic = 6.744e9 + 4.249e9
     roof.update({"kernel": "E-step pass 1 (scores + online log-sum-exp)", "achieved": achieved,
                  "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "traffic": traffic, "traffic_unit": "bytes per launch",
