@@ -229,6 +229,7 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
     phases = {k: 0.0 for k in ("ms_expand", "ms_loglik", "ms_normalize", "ms_update",
                                 "ms_compress")}
     kernels = 0
+    tiles = [0, 0, 0]  # pass-1 tiles, of them contracted exactly, iterations bound-pruned
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             ctx.iteration(grid, out, stats=True, stream=stream)
@@ -244,6 +245,9 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
             for k in phases:
                 phases[k] += st[k]
             kernels += st["kernels"]
+            tiles[0] += st["pass1_tiles"]
+            tiles[1] += st["pass1_exact"]
+            tiles[2] += st["pass1_pruned"]
             lls.append(st["loglik"])
             if st["device_status"] != 0:
                 raise RuntimeError(f"device status {st['device_status']}")
@@ -251,7 +255,10 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
         e1.synchronize()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    return ms, {k: v / steps for k, v in phases.items()}, kernels, lls[-1]
+    ph = {k: v / steps for k, v in phases.items()}
+    ph["pass1_exact_tile_fraction"] = tiles[1] / tiles[0] if tiles[0] else None
+    ph["pass1_bound_pruned_steps"] = tiles[2]
+    return ms, ph, kernels, lls[-1]
 
 
 def rot_chunk_for(n_rot: int, n_data: int, cap: float = 8e9) -> int:
@@ -535,18 +542,25 @@ def run_ours(args):
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "peak_source": f"{pk_src} bf16 sustained"}
     achieved = flops / (dom_ms * 1e-3) / 1e12
-    # DRAM bytes of pass 1 from one ncu capture of this exact configuration
-    # (profiles/tc_pass1_update_emc64_dram_bytes.md); other configurations: unmeasured
+    planes = 3 if args.precision == "bf16_split" else 2 if args.precision == "fp16_split" else 1
+    pruned = bool(phases.get("pass1_bound_pruned_steps"))
+    exact = phases.get("pass1_exact_tile_fraction")
+    # executed tensor work: every plane over every tile, or (bound-pruned) the hi
+    # plane over every tile and every plane over the tiles left live
+    executed = flops * ((1 + planes * exact) if pruned else planes)
+    # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
+    # dram__bytes_write.sum) of this exact configuration; otherwise unmeasured
     traffic = None
     if (args.workload == "emc64" and args.precision == "bf16_split" and n_data == 20000
-            and n_rot == 50100 and not args.recompute):
+            and n_rot == 50100 and not args.recompute and not pruned):
         traffic = 6.744e9 + 4.249e9
-    roof.update({"kernel": "E-step pass 1 (scores + online log-sum-exp)", "achieved": achieved,
-                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    roof.update({"kernel": ("E-step pass 1: hi-plane bound over every tile, exact contraction "
+                            "of the tiles it leaves live, online log-sum-exp" if pruned else
+                            "E-step pass 1 (scores + online log-sum-exp)"),
+                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "traffic": traffic, "traffic_unit": "bytes per launch",
-                 "algorithmic_flops_per_launch": flops,
-                 "executed_flops_per_launch": flops * (3 if args.precision == "bf16_split" else
-                                                       2 if args.precision == "fp16_split" else 1)})
+                 "algorithmic_flops_per_launch": flops, "executed_flops_per_launch": executed,
+                 "exact_tile_fraction": exact})
 
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}

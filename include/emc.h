@@ -121,6 +121,25 @@ typedef enum emc_compress_mode {
                                    columns needed: EMC_ERR_UNSUPPORTED in the
                                    device status. Frame totals keep their
                                    limits. Not for emc_loglik_static. */
+#define EMC_FLAG_DENSE_ESTEP 8  /* emc_iteration contracts every (rotation tile,
+                                   frame tile) in pass 1. Without it, a context
+                                   with EMC_FLAG_STORE_SCORES, the BF16 split,
+                                   a Poisson model and no candidate sets first
+                                   bounds every tile's scores by a contraction
+                                   of the hi plane alone (|S - S_hi| <= N_k/16
+                                   + 1), then contracts exactly only the tiles
+                                   that can hold a score within 110 of their
+                                   frames' maxima. The others have P = 0 in
+                                   FP32 and no weight in lse at FP64 precision,
+                                   so the results are those of the dense pass.
+                                   Frames are regrouped internally by the row
+                                   tile of their best rotation after every
+                                   iteration (a second copy of the frames in
+                                   the workspace); the grouping is kept when
+                                   emc_set_frames loads frames again. The stored scores of such a
+                                   context are then in that internal order and
+                                   hold only the contracted tiles;
+                                   emc_targets_from_scores does not read them. */
 #define EMC_FLAG_SPARSE_K 2     /* emc_set_frames also lists every frame's
                                    non-zero pixels (n_data x n_pix x 4 B of
                                    workspace at most) for emc_loglik_sparse_k;
@@ -169,6 +188,11 @@ typedef struct emc_iter_stats {
   double ms_expand, ms_loglik, ms_normalize, ms_update, ms_compress, ms_total;
   int32_t device_status; /* emc_status recorded on the device (0 = OK) */
   int32_t kernels;       /* kernel launches made by the call */
+  int64_t pass1_tiles;   /* (128-rotation, 256-frame) tiles of the E-step pass 1 */
+  int64_t pass1_exact;   /* of those, contracted with every plane (all of them
+                            unless the pass was bound-pruned) */
+  int32_t pass1_pruned;  /* 1: a hi-plane bound pass over every tile ran first */
+  int32_t reserved;
 } emc_iter_stats;
 
 typedef struct emc_ctx emc_ctx;

@@ -22,7 +22,9 @@ struct Layout {
   size_t qh, ql, quat, rot, logw, Kb, status, L, bias, lse_m, lse_s, lse2, part_m, part_s, S, P,
       Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, gk, gauss,
       Kb2, skcnt, skoff, skent, dupsrc, duprank, pixmax, fcn, finvn, fB, kbflag, kbcnt, kblist,
-      total;
+      Kp, perm, perm2, iperm, nsum, nsum_p, cn_p, invn_p, best, lsem_s, lses_s, live, tlist,
+      tcount, sortH, sortoff, total;
+  int64_t sort_entries;
 };
 
 // Gaussian scalars inside the 256-byte block at Layout::gauss
@@ -36,6 +38,12 @@ size_t score_bytes(int64_t rows, int64_t ld_data) {
 
 bool is_gauss(const emc_config* c) { return c->model == EMC_MODEL_GAUSSIAN; }
 bool is_flu(const emc_config* c) { return c->model == EMC_MODEL_POISSON_FLUENCE; }
+// emc_iteration's bound-pruned pass 1 (EMC_FLAG_DENSE_ESTEP clears it)
+bool prune_ok(const emc_config* c) {
+  return (c->flags & EMC_FLAG_STORE_SCORES) && !(c->flags & EMC_FLAG_DENSE_ESTEP) &&
+         c->precision == EMC_PREC_BF16_SPLIT && c->n_cand == 0 &&
+         (c->model == EMC_MODEL_POISSON || c->model == EMC_MODEL_POISSON_FLUENCE);
+}
 // Poisson-fluence model: the constant c of L = log(W / B_j) + c, log n_pix on
 // the 1/8 grid (L is then the log of W over the slice's mean)
 double flu_shift(const emc_config* c) { return rint(8.0 * log((double)c->n_pix)) / 8.0; }
@@ -82,8 +90,8 @@ int check_config(const emc_config* c) {
              log(c->w_floor) < (double)kHiMin) {
     return EMC_ERR_UNSUPPORTED;
   }
-  if (c->rot_chunk < 0 ||
-      (c->flags & ~(EMC_FLAG_STORE_SCORES | EMC_FLAG_SPARSE_K | EMC_FLAG_WIDE_COUNTS)) != 0)
+  if (c->rot_chunk < 0 || (c->flags & ~(EMC_FLAG_STORE_SCORES | EMC_FLAG_SPARSE_K |
+                                         EMC_FLAG_WIDE_COUNTS | EMC_FLAG_DENSE_ESTEP)) != 0)
     return EMC_ERR_ARG;
   if ((c->flags & EMC_FLAG_SPARSE_K) && c->n_pix > 65536) return EMC_ERR_UNSUPPORTED;
   if (c->n_cand < 0 || c->n_cand > c->n_rot || c->n_cand > 4096) return EMC_ERR_ARG;
@@ -163,6 +171,26 @@ Layout make_layout(const emc_config* c) {
   y.kbflag = tc ? take((size_t)ctiles * kbs) : 0;
   y.kbcnt = tc ? take(sizeof(int32_t) * (size_t)ctiles) : 0;
   y.kblist = tc ? take(sizeof(int32_t) * (size_t)ctiles * kbs) : 0;
+  // bound-pruned pass 1: frames in their internal order and the tile bookkeeping
+  const bool pr = prune_ok(c);
+  const int64_t nmt = y.rows / 128, nnt = y.ld_data / 256;
+  y.sort_entries = pr ? sort_scratch_entries(c->n_data, (int)nmt) : 0;
+  y.Kp = pr ? take(2 * (size_t)y.ld_data * y.ld_pix) : 0;
+  y.perm = pr ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
+  y.perm2 = pr ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
+  y.iperm = pr ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
+  y.nsum = pr ? take(sizeof(float) * (size_t)y.ld_data) : 0;
+  y.nsum_p = pr ? take(sizeof(float) * (size_t)y.ld_data) : 0;
+  y.cn_p = pr && is_flu(c) ? take(sizeof(double) * (size_t)y.ld_data) : 0;
+  y.invn_p = pr && is_flu(c) ? take(sizeof(float) * (size_t)y.ld_data) : 0;
+  y.best = pr ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
+  y.lsem_s = pr ? take(sizeof(double) * (size_t)y.ld_data) : 0;
+  y.lses_s = pr ? take(sizeof(double) * (size_t)y.ld_data) : 0;
+  y.live = pr ? take((size_t)nmt * nnt) : 0;
+  y.tlist = pr ? take(sizeof(int32_t) * (size_t)nmt * nnt) : 0;
+  y.tcount = pr ? take(256) : 0;
+  y.sortH = pr ? take(sizeof(int32_t) * (size_t)y.sort_entries) : 0;
+  y.sortoff = pr ? take(sizeof(int64_t) * (size_t)(y.sort_entries + 1)) : 0;
   y.total = o;
   return y;
 }
@@ -194,6 +222,11 @@ struct emc_ctx {
   float* flu_invn;            // Poisson-fluence: 1 / N_k (0 for empty frames)
   double* flu_B;              // Poisson-fluence: B_j = sum_i W_ij of the last emc_expand
   double flu_c;               // Poisson-fluence: c of L = log(W / B_j) + c
+  bool prune;                 // emc_iteration prunes pass 1 (prune_ok)
+  bool perm_valid;            // the internal frame order comes from an iteration
+  int32_t* perm;              // internal position -> frame (swapped with perm2)
+  int32_t* perm2;
+  bool scores_internal;       // the stored scores are in the internal order, pruned
   bool frames_loaded;
   bool cand_loaded;
   cudaEvent_t ev[8];
@@ -352,6 +385,9 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   c->flu_invn = y.finvn ? (float*)(c->ws + y.finvn) : nullptr;
   c->flu_B = y.fB ? (double*)(c->ws + y.fB) : nullptr;
   c->flu_c = is_flu(cfg) ? flu_shift(cfg) : 0.0;
+  c->prune = prune_ok(cfg);
+  c->perm = y.perm ? (int32_t*)(c->ws + y.perm) : nullptr;
+  c->perm2 = y.perm2 ? (int32_t*)(c->ws + y.perm2) : nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   bool ok = true;
   ok &= cudaMemcpyAsync(c->ws + y.qh, qh.data(), sizeof(float4) * y.ld_pix,
@@ -426,6 +462,23 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
   if (is_flu(&ctx->cfg))
     CU(launch_flu_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, ctx->flu_c,
                          ctx->flu_cn, ctx->flu_invn, s));
+  if (ctx->prune) {
+    // the internal frame order starts as the given one; a context that already
+    // has one keeps it for new frames (it only decides how many pass-1 tiles
+    // the bound skips, and the same frames loaded again keep their grouping)
+    float* nsum = (float*)(ctx->ws + y.nsum);
+    CU(launch_frame_totals(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, nsum, s));
+    if (!ctx->perm_valid) {
+      CU(launch_identity(ctx->perm, y.ld_data, s));
+      CU(launch_identity(ctx->perm2, y.ld_data, s));
+    }
+    CU(launch_permute_frames(ctx->perm, y.ld_data, y.ld_pix, ctx->Kb, (uint16_t*)(ctx->ws + y.Kp),
+                             nsum, (float*)(ctx->ws + y.nsum_p), ctx->flu_cn,
+                             y.cn_p ? (double*)(ctx->ws + y.cn_p) : nullptr, ctx->flu_invn,
+                             y.invn_p ? (float*)(ctx->ws + y.invn_p) : nullptr,
+                             (int32_t*)(ctx->ws + y.iperm), s));
+    ctx->scores_internal = false;
+  }
   if (g) {
     CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb2,
                           2, dsrc, drank, ctx->status, s));
@@ -494,23 +547,38 @@ int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const d
   return EMC_OK;
 }
 
+// Frames in emc_iteration's internal order (bound-pruned pass 1): their BF16
+// matrix, the Poisson-fluence arrays, and the contracted tiles of these rows.
+struct FrameView {
+  const uint16_t* K;
+  const double* cn;
+  const float* invn;
+  const uint8_t* tile_live;
+};
+
 // S, Sref: stored scores of these rows, S frame-major with leading dimension
 // ldS (NULL: recompute from L and bias). Bsum: the rows' B_j (Poisson-fluence model).
+// fv (may be NULL): frames in the internal order (stored scores only).
 int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const double* bias,
                  int64_t nrot, const double* lse_m, const double* lse_s, const float* S,
                  int64_t ldS, const float* Sref, void* P, int64_t Prows, cudaStream_t s,
-                 const double* Bsum = nullptr, uint8_t* kbf = nullptr) {
+                 const double* Bsum = nullptr, uint8_t* kbf = nullptr,
+                 const FrameView* fv = nullptr) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
+  if (fv && !S) return EMC_ERR_ARG;
+  const uint8_t* tlive = fv ? fv->tile_live : nullptr;
   if (is_flu(&c->cfg)) {
     if (!bias || !Bsum) return EMC_ERR_ARG;
     float2* lse2 = (float2*)(c->ws + y.lse2);
     float* den = (float*)((char*)P + P_plane_bytes(&c->cfg, Prows, y.ld_data));
+    const double* cn = fv ? fv->cn : c->flu_cn;
+    const float* invn = fv ? fv->invn : c->flu_invn;
     if (S) {
-      CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s, c->flu_cn));
-      CU(launch_normalize_scores_flu(S, ldS, Sref, lse2, Bsum, c->flu_invn, rows, nrot,
+      CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s, cn));
+      CU(launch_normalize_scores_flu(S, ldS, Sref, lse2, Bsum, invn, rows, nrot,
                                      y.ld_data, c->cfg.n_data, (uint16_t*)P, Prows * y.ld_data,
-                                     den, s, kbf));
+                                     den, s, kbf, tlive));
     } else {
       Planes lp{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
       Planes pp{P, Prows * y.ld_data, y.ld_data};
@@ -534,7 +602,7 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
     float2* lse2 = (float2*)(c->ws + y.lse2);
     CU(launch_lse_split(lse_m, lse_s, c->cfg.n_data, y.ld_data, lse2, s));
     CU(launch_normalize_scores(S, ldS, Sref, lse2, rows, nrot, y.ld_data, c->cfg.n_data,
-                               c->cfg.precision, P, Prows * y.ld_data, s, kbf));
+                               c->cfg.precision, P, Prows * y.ld_data, s, kbf, tlive));
     return EMC_OK;
   }
   if (c->cfg.precision == EMC_PREC_FP32) {
@@ -551,9 +619,11 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
   return EMC_OK;
 }
 
-// kbc, kbl (optional): the non-zero 64-frame blocks of each row tile of P
+// kbc, kbl (optional): the non-zero 64-frame blocks of each row tile of P;
+// Kf (optional): frames in emc_iteration's internal order
 int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num, float* den,
-              cudaStream_t s, const int32_t* kbc = nullptr, const int32_t* kbl = nullptr) {
+              cudaStream_t s, const int32_t* kbc = nullptr, const int32_t* kbl = nullptr,
+              const uint16_t* Kf = nullptr) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
   if (c->cfg.precision == EMC_PREC_FP32) {
@@ -564,14 +634,14 @@ int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num
     if (is_gauss(&c->cfg) || is_flu(&c->cfg)) {
       // BF16 hi + lo planes of P / phi against the BF16 frames (the Gaussian
       // model's BF16 copy)
-      CU(launch_tc_update(pp, EMC_PREC_BF16_SPLIT, rows, is_gauss(&c->cfg) ? c->Kb2 : c->Kb,
-                          y.ld_data, y.ld_pix, c->cfg.n_pix, Num, nullptr, c->status, s, kbc,
-                          kbl));
+      CU(launch_tc_update(pp, EMC_PREC_BF16_SPLIT, rows,
+                          Kf ? Kf : (is_gauss(&c->cfg) ? c->Kb2 : c->Kb), y.ld_data, y.ld_pix,
+                          c->cfg.n_pix, Num, nullptr, c->status, s, kbc, kbl));
       const char* tail = (const char*)P + P_plane_bytes(&c->cfg, Prows, y.ld_data);
       CU(cudaMemcpyAsync(den, tail, sizeof(float) * rows, cudaMemcpyDeviceToDevice, s));
     } else {
-      CU(launch_tc_update(pp, c->cfg.precision, rows, c->Kb, y.ld_data, y.ld_pix, c->cfg.n_pix, Num,
-                          den, c->status, s, kbc, kbl));
+      CU(launch_tc_update(pp, c->cfg.precision, rows, Kf ? Kf : c->Kb, y.ld_data, y.ld_pix,
+                          c->cfg.n_pix, Num, den, c->status, s, kbc, kbl));
     }
   }
   return EMC_OK;
@@ -699,9 +769,42 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   kernels += is_gauss(&c->cfg) ? 3 : 1;  // Gaussian: grid maximum and scales first
   if (stats) CU(cudaEventRecord(c->ev[1], s));
   float* S = (c->cfg.flags & EMC_FLAG_STORE_SCORES) ? (float*)(c->ws + y.S) : nullptr;
-  if ((st = do_loglik(c, L, y.rows, 0, bias, n_rot, lse_m, lse_s, 0, S, s))) return st;
+  // bound-pruned pass 1 over the frames in their internal order
+  const bool pr = c->prune;
+  const int64_t nmt = y.rows / 128, nnt = y.ld_data / 256;
+  const uint16_t* Kp = pr ? (const uint16_t*)(c->ws + y.Kp) : nullptr;
+  uint8_t* live = pr ? (uint8_t*)(c->ws + y.live) : nullptr;
+  const bool pruned = pr && c->perm_valid;
+  double* lm = pr ? (double*)(c->ws + y.lsem_s) : lse_m;  // lse in the internal order
+  double* ls = pr ? (double*)(c->ws + y.lses_s) : lse_s;
+  const double* cn_p = y.cn_p ? (const double*)(c->ws + y.cn_p) : nullptr;
+  if (pr) {
+    double* pm = (double*)(c->ws + y.part_m);
+    float* ps = (float*)(c->ws + y.part_s);
+    Planes p3{L, y.rows * y.ld_pix, y.ld_pix};
+    int32_t* tlist = (int32_t*)(c->ws + y.tlist);
+    int32_t* tcount = (int32_t*)(c->ws + y.tcount);
+    if (pruned) {
+      // bound: the hi plane alone (one plane of L read as plain BF16 log W)
+      CU(launch_tc_pass1(p3, EMC_PREC_BF16, bias, y.rows, Kp, y.ld_data, c->cfg.n_data, y.ld_pix,
+                         pm, ps, nullptr, nullptr, nullptr, nullptr, c->status, s));
+      CU(launch_bound_live(pm, nmt, y.ld_data, c->cfg.n_data,
+                           (const float*)(c->ws + y.nsum_p), live, s));
+      CU(launch_tile_list(live, (int)nmt, (int)nnt, 8, tlist, tcount, s));
+    }
+    CU(launch_tc_pass1(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, c->cfg.n_data, y.ld_pix,
+                       pm, ps, S, S + y.rows * y.ld_data, nullptr, nullptr, c->status, s,
+                       pruned ? tlist : nullptr, pruned ? tcount : nullptr));
+    CU(launch_lse_merge(pm, ps, nmt, y.ld_data, c->cfg.n_data, lm, ls, 0, 0, c->status, s, cn_p,
+                        pruned ? live : nullptr, (int32_t*)(c->ws + y.best)));
+    CU(launch_unpermute_lse(c->perm, c->cfg.n_data, lm, ls, lse_m, lse_s, s));
+    kernels += pruned ? 6 : 3;  // (bound, liveness, list,) pass 1, merge, lse order
+  } else {
+    if ((st = do_loglik(c, L, y.rows, 0, bias, n_rot, lse_m, lse_s, 0, S, s))) return st;
+    kernels += 2;
+  }
   CU(launch_loglik_sum(lse_m, lse_s, c->cfg.n_data, ll, s));
-  kernels += 3;
+  kernels += 1;
   if (stats) CU(cudaEventRecord(c->ev[2], s));
   CU(cudaMemsetAsync(gn, 0, gb, s));
   CU(cudaMemsetAsync(gd, 0, gb, s));
@@ -717,14 +820,16 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     uint8_t* kbf = y.kbflag ? (uint8_t*)(c->ws + y.kbflag) : nullptr;
     const int32_t* kbc = kbf ? (const int32_t*)(c->ws + y.kbcnt) : nullptr;
     const int32_t* kbl = kbf ? (const int32_t*)(c->ws + y.kblist) : nullptr;
-    if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lse_m, lse_s, Sc, y.rows, Sr, P, crows,
-                           s, c->flu_B ? c->flu_B + r0 : nullptr, kbf)))
+    FrameView fv{Kp, cn_p, y.invn_p ? (const float*)(c->ws + y.invn_p) : nullptr,
+                 pruned ? live + (r0 / 128) * nnt : nullptr};
+    if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lm, ls, Sc, y.rows, Sr, P, crows, s,
+                           c->flu_B ? c->flu_B + r0 : nullptr, kbf, pr ? &fv : nullptr)))
       return st;
     if (kbf)
       CU(launch_kb_lists(kbf, crows / 128, (int)(y.ld_data / 64), (int32_t*)kbc, (int32_t*)kbl,
                          s));
     if (stats) CU(cudaEventRecord(c->ev[4], s));
-    if ((st = do_update(c, P, crows, nr, Num, den, s, kbc, kbl))) return st;
+    if ((st = do_update(c, P, crows, nr, Num, den, s, kbc, kbl, Kp))) return st;
     if (stats) CU(cudaEventRecord(c->ev[5], s));
     CU(launch_compress(c->geom, c->rot + r0, nr, Num, den, c->cfg.compress_mode, gn, gd, y.nrep,
                        s));
@@ -747,6 +852,23 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, y.nrep, grid_in, grid_out,
                      s));
   kernels++;
+  if (pr) {
+    // next iteration's frame order: grouped by the row tile of the best rotation
+    // (counting sort, stable), then the frames and their arrays in that order
+    CU(launch_sort_frames((const int32_t*)(c->ws + y.best), c->perm, c->cfg.n_data, (int)nmt,
+                          (int32_t*)(c->ws + y.sortH), (int64_t*)(c->ws + y.sortoff), c->perm2,
+                          s));
+    std::swap(c->perm, c->perm2);
+    CU(launch_permute_frames(c->perm, y.ld_data, y.ld_pix, c->Kb, (uint16_t*)(c->ws + y.Kp),
+                             (const float*)(c->ws + y.nsum), (float*)(c->ws + y.nsum_p),
+                             c->flu_cn, y.cn_p ? (double*)(c->ws + y.cn_p) : nullptr,
+                             c->flu_invn, y.invn_p ? (float*)(c->ws + y.invn_p) : nullptr,
+                             (int32_t*)(c->ws + y.iperm), s));
+    // sort_frames writes positions below n_data only; perm2's tail stays the identity
+    c->perm_valid = true;
+    c->scores_internal = true;
+    kernels += 4;
+  }
   if (stats) CU(cudaEventRecord(c->ev[7], s));
   c->kernels = kernels;
   if (stats) {
@@ -768,6 +890,14 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     CU(cudaMemcpy(&dst, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
     stats->device_status = dst;
     stats->kernels = kernels;
+    stats->pass1_tiles = nmt * nnt;
+    stats->pass1_exact = nmt * nnt;
+    if (pruned) {
+      int32_t cnt = 0;
+      CU(cudaMemcpy(&cnt, c->ws + y.tcount, sizeof(int32_t), cudaMemcpyDeviceToHost));
+      stats->pass1_exact = cnt;
+      stats->pass1_pruned = 1;
+    }
   }
   return EMC_OK;
 }
@@ -834,6 +964,8 @@ int emc_targets_from_scores(emc_ctx* ctx, const void* scores, int R, int32_t* ti
   const Layout& y = ctx->lay;
   if (!scores) {
     if (!(ctx->cfg.flags & EMC_FLAG_STORE_SCORES)) return EMC_ERR_ARG;
+    // a bound-pruned iteration leaves them in its internal order, pruned
+    if (ctx->scores_internal) return EMC_ERR_UNSUPPORTED;
     scores = ctx->ws + y.S;
   }
   const float* S = (const float*)scores;

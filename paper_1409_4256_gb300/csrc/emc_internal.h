@@ -68,7 +68,8 @@ cudaError_t launch_normalize_scores_flu(const float* S, int64_t ldS, const float
                                         const float2* lse2, const double* Bsum, const float* invn,
                                         int64_t rows, int64_t nrot, int64_t ld_data,
                                         int64_t n_data, uint16_t* P, int64_t P_plane, float* den,
-                                        cudaStream_t s, uint8_t* kb_flag = nullptr);
+                                        cudaStream_t s, uint8_t* kb_flag = nullptr,
+                                        const uint8_t* tile_live = nullptr);
 // Non-zero P blocks (update over those only): the normalisations set
 // flag[mt * kb_ld + kb] (kb_ld = ld_data / 64) for every 128-row x 64-frame
 // block of P with a non-zero entry; this lists them per row tile.
@@ -112,10 +113,13 @@ int64_t simt_pass1_tiles(int64_t rows);
 // Merge of per-tile (max, sum) pairs into the running per-frame (m, s).
 // shift (may be NULL): per-frame constant carried by the tiles' scores
 // (double[ld_data]), removed before the merge.
+// live (may be NULL): [n_tiles][ld_data / 256] flags of the contracted tiles
+// of a pruned pass 1; best (may be NULL): row tile of each frame's largest maximum.
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
                              int accumulate, int gauss, int32_t* status, cudaStream_t s,
-                             const double* shift = nullptr);
+                             const double* shift = nullptr, const uint8_t* live = nullptr,
+                             int32_t* best = nullptr);
 // shift (may be NULL): added back to lse before the split.
 cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n_data,
                              int64_t ld_data, float2* out, cudaStream_t s,
@@ -125,17 +129,21 @@ cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n
 cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sref,
                                     const float2* lse2, int64_t rows, int64_t nrot,
                                     int64_t ld_data, int64_t n_data, int precision, void* P,
-                                    int64_t P_plane, cudaStream_t s, uint8_t* kb_flag = nullptr);
+                                    int64_t P_plane, cudaStream_t s, uint8_t* kb_flag = nullptr,
+                                    const uint8_t* tile_live = nullptr);
 cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
                               double* out, cudaStream_t s);
 
 // tcgen05 forms (precision EMC_PREC_BF16 / BF16_SPLIT / FP16_SPLIT).
 // gk, gsc != NULL: the Gaussian model's pass 1 (three FP16 planes of s W).
+// tile_list, tile_count (device, optional): contract only the listed
+// (row tile, frame tile) pairs, codes mt * (ld_data / 256) + nt, *tile_count of them
 cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
                             const float4* gk, const float4* gsc, int32_t* status,
-                            cudaStream_t s);
+                            cudaStream_t s, const int32_t* tile_list = nullptr,
+                            const int32_t* tile_count = nullptr);
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
 // Bsum != NULL: Poisson-fluence model -- shift[ld_data] is added back to lse,
 // the planes receive BF16 hi + lo of P B_j invn[k] and den[rows] = sum_k P_jk
@@ -219,6 +227,29 @@ cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, i
 cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, int64_t ld_data,
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
                                float* missed, cudaStream_t s);
+
+// ---- pruned pass 1 and the frame order (prune.cu) ----
+// live[mt * (ld_data / 256) + nt] from the hi-plane tile maxima part_m (sorted
+// frames) and the frame totals nsum
+cudaError_t launch_bound_live(const double* part_m, int64_t n_mtiles, int64_t ld_data,
+                              int64_t n_data, const float* nsum, uint8_t* live, cudaStream_t s);
+cudaError_t launch_tile_list(const uint8_t* live, int n_mtiles, int n_ntiles, int group,
+                             int32_t* list, int32_t* count, cudaStream_t s);
+// entries of the histogram scratch H (int32) of launch_sort_frames; off needs one more (int64)
+int64_t sort_scratch_entries(int64_t n_data, int nbins);
+// new_perm[pos] = perm[s] for the frames s stably sorted by key[s] in [0, nbins)
+cudaError_t launch_sort_frames(const int32_t* key, const int32_t* perm, int64_t n_data, int nbins,
+                               int32_t* H, int64_t* off, int32_t* new_perm, cudaStream_t s);
+// frames in the order perm: rows of Kb into Kp, nsum (and cn, invn if non-NULL); iperm
+cudaError_t launch_permute_frames(const int32_t* perm, int64_t ld_data, int64_t ld_pix,
+                                  const uint16_t* Kb, uint16_t* Kp, const float* nsum,
+                                  float* nsum_p, const double* cn, double* cn_p, const float* invn,
+                                  float* invn_p, int32_t* iperm, cudaStream_t s);
+cudaError_t launch_frame_totals(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                                int64_t ld_data, float* nsum, cudaStream_t s);
+cudaError_t launch_identity(int32_t* p, int64_t n, cudaStream_t s);
+cudaError_t launch_unpermute_lse(const int32_t* perm, int64_t n_data, const double* m_s,
+                                 const double* s_s, double* m, double* s, cudaStream_t st);
 
 // exclusive scan of cnt[0, n) into off[0, n] (off[n] = total), one CTA
 cudaError_t launch_scan_counts(const int32_t* cnt, int64_t n, int64_t* off, cudaStream_t s);

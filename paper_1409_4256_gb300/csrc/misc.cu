@@ -246,19 +246,32 @@ cudaError_t launch_gauss_scales(const float* grid, int64_t n_vox, unsigned* gmax
 // (m_k, s_k) in FP64 (Eq. 2.4's denominator; only maxima and sums travel, as
 // in Sec. 3.3). Reads are coalesced along k. shift (may be NULL): a per-frame
 // constant the tiles' scores carry (the Poisson-fluence model's c N_k),
-// subtracted from their maxima before the merge.
+// subtracted from their maxima before the merge. live (may be NULL): only row
+// tiles t with live[t * nnt + k / 256] were contracted (the others underflow);
+// best (may be NULL) receives the row tile of the largest maximum.
 __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float* __restrict__ part_s,
                                  int64_t n_tiles, int64_t ld_data, int64_t n_data,
                                  double* __restrict__ lse_m, double* __restrict__ lse_s,
                                  int accumulate, double clamp, const double* __restrict__ shift,
-                                 int32_t* status) {
+                                 const uint8_t* __restrict__ live, int64_t nnt,
+                                 int32_t* __restrict__ best, int32_t* status) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_data) return;
   double M = accumulate ? lse_m[k] : -INFINITY;
   double S = accumulate ? lse_s[k] : 0.0;
   const double sh = shift ? shift[k] : 0.0;
+  const uint8_t* lv = live ? live + (k >> 8) : nullptr;
   double mt = -INFINITY;
-  for (int64_t t = 0; t < n_tiles; t++) mt = fmax(mt, part_m[t * ld_data + k] - sh);
+  int tbest = 0;
+  for (int64_t t = 0; t < n_tiles; t++) {
+    if (lv && !lv[t * nnt]) continue;
+    const double m = part_m[t * ld_data + k] - sh;
+    if (m > mt) {
+      mt = m;
+      tbest = (int)t;
+    }
+  }
+  if (best) best[k] = tbest;
   double Mn = fmax(M, mt);
   if (Mn == -INFINITY) {  // nothing seen yet
     lse_m[k] = M;
@@ -270,6 +283,7 @@ __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float*
   // this part and the loop runs over every rotation tile
   double acc = (S > 0.0) ? S * exp(M - Mn) : 0.0;
   for (int64_t t = 0; t < n_tiles; t++) {
+    if (lv && !lv[t * nnt]) continue;
     double m = part_m[t * ld_data + k] - sh;
     float sv = part_s[t * ld_data + k];
     if (sv > 0.f) acc += (double)(sv * __expf((float)(m - Mn)));
@@ -284,11 +298,11 @@ __global__ void lse_merge_kernel(const double* __restrict__ part_m, const float*
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
                              int accumulate, int gauss, int32_t* status, cudaStream_t s,
-                             const double* shift) {
+                             const double* shift, const uint8_t* live, int32_t* best) {
   unsigned blocks = (unsigned)((n_data + 255) / 256);
   lse_merge_kernel<<<blocks, 256, 0, s>>>(part_m, part_s, n_tiles, ld_data, n_data, lse_m, lse_s,
                                           accumulate, gauss ? -(double)kGaussClamp : -INFINITY,
-                                          shift, status);
+                                          shift, live, ld_data / 256, best, status);
   return cudaGetLastError();
 }
 
@@ -381,6 +395,8 @@ struct NormArgs {
   uint8_t* kb_flag;    // optional: 1 where the CTA's 128 x 64 block of P is non-zero;
                        // blocks found zero are then not written (their readers skip them)
   int64_t kb_ld;
+  const uint8_t* tile_live;  // optional: [row tile][256-frame tile] of a pruned pass 1;
+                             // a block in a tile not contracted has P = 0
 };
 
 // A 32-row group of stored scores whose maximum r lies more than 110 below
@@ -410,7 +426,9 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
   __syncthreads();
   {  // a block whose every (group, frame) underflows: P = 0 without reading S
     const int gk = tid & 63;
-    const bool live = (sr[tid >> 6][gk] - sl[gk].x) - sl[gk].y >= kUnderflowArg;
+    const bool tile_on =
+        !a.tile_live || a.tile_live[(int64_t)blockIdx.y * (a.ld_data >> 8) + (k0 >> 8)];
+    const bool live = tile_on && (sr[tid >> 6][gk] - sl[gk].x) - sl[gk].y >= kUnderflowArg;
     if (!__syncthreads_or(live)) {
       if (a.kb_flag) {
         if (tid == 0) a.kb_flag[(int64_t)blockIdx.y * a.kb_ld + blockIdx.x] = 0;
@@ -535,11 +553,13 @@ __global__ void __launch_bounds__(256) normalize_scores_kernel(const NormArgs a)
 cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sref,
                                     const float2* lse2, int64_t rows, int64_t nrot,
                                     int64_t ld_data, int64_t n_data, int precision, void* P,
-                                    int64_t P_plane, cudaStream_t s, uint8_t* kb_flag) {
+                                    int64_t P_plane, cudaStream_t s, uint8_t* kb_flag,
+                                    const uint8_t* tile_live) {
   NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane,
              nullptr, nullptr, nullptr, nullptr, nullptr};
   a.kb_flag = kb_flag;
   a.kb_ld = ld_data / kNormFrames;
+  a.tile_live = tile_live;
   dim3 grid((unsigned)(ld_data / kNormFrames), (unsigned)(rows / kNormRows));
   if (precision == EMC_PREC_FP32)
     normalize_scores_kernel<0><<<grid, 256, 0, s>>>(a);
@@ -573,13 +593,15 @@ cudaError_t launch_normalize_scores_flu(const float* S, int64_t ldS, const float
                                         const float2* lse2, const double* Bsum, const float* invn,
                                         int64_t rows, int64_t nrot, int64_t ld_data,
                                         int64_t n_data, uint16_t* P, int64_t P_plane, float* den,
-                                        cudaStream_t s, uint8_t* kb_flag) {
+                                        cudaStream_t s, uint8_t* kb_flag,
+                                        const uint8_t* tile_live) {
   cudaError_t e = cudaMemsetAsync(den, 0, sizeof(float) * rows, s);
   if (e != cudaSuccess) return e;
   NormArgs a{S, ldS, Sref, lse2, nrot, ld_data, n_data, P, P_plane, nullptr, nullptr, den, Bsum,
              invn};
   a.kb_flag = kb_flag;
   a.kb_ld = ld_data / kNormFrames;
+  a.tile_live = tile_live;
   dim3 grid((unsigned)(ld_data / kNormFrames), (unsigned)(rows / kNormRows));
   normalize_scores_kernel<5><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();

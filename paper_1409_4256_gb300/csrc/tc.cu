@@ -114,6 +114,10 @@ struct TcArgs {
   // normalize: kb_flag[mt * kb_ld + kb] set to 1 where the block's P is non-zero
   uint8_t* kb_flag;
   int kb_ld;
+  // pass 1 over listed tiles only (NULL: every tile): tile_list[t] =
+  // mt * n_ntiles + nt for t < *tile_count, in raster order
+  const int32_t* tile_list;
+  const int32_t* tile_count;
   int32_t* status;
 };
 
@@ -129,6 +133,12 @@ __device__ __forceinline__ int tile_kblock(const TcArgs& a, int mt, int x) {
 }
 
 __device__ __forceinline__ void tile_coords(int t, const TcArgs& a, int* mt, int* nt) {
+  if (a.tile_list) {
+    const int code = a.tile_list[t];
+    *mt = code / a.n_ntiles;
+    *nt = code % a.n_ntiles;
+    return;
+  }
   const int per_group = a.group * a.n_ntiles;
   const int g = t / per_group, rem = t % per_group;
   const int gsize = min(a.group, a.n_mtiles - g * a.group);
@@ -203,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int T = a.n_mtiles * a.n_ntiles;
+  const int T = a.tile_count ? *a.tile_count : a.n_mtiles * a.n_ntiles;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer --
@@ -576,7 +586,8 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs a, cudaS
   }
   const int T = a.n_mtiles * a.n_ntiles;
   if (T <= 0) return cudaSuccess;
-  const int grid = T < num_sms() ? T : num_sms();
+  // a device-side tile list: one persistent CTA per SM (the count is read on the device)
+  const int grid = (!a.tile_list && T < num_sms()) ? T : num_sms();
   tc_kernel<MODE, NA, F16><<<grid, kThreads, C::SMEM, s>>>(mA, mB, a);
   return cudaGetLastError();
 }
@@ -617,7 +628,8 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
                             const float4* gk, const float4* gsc, int32_t* status,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int32_t* tile_list,
+                            const int32_t* tile_count) {
   const bool gauss = gk != nullptr;
   const int nterms = gauss ? 3 : score_planes(precision);
   const bool f16 = gauss || precision == EMC_PREC_FP16_SPLIT;
@@ -636,6 +648,8 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
   a.Sref = Sref;
   a.gk = gk;
   a.gsc = gsc;
+  a.tile_list = tile_list;
+  a.tile_count = tile_list ? tile_count : nullptr;
   a.status = status;
   if (gauss) return launch<MODE_PASS1, 3, true>(mA, mB, a, s);
   if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_PASS1, 2, true>(mA, mB, a, s);

@@ -23,6 +23,7 @@ COMPRESS_DEFERRED, COMPRESS_IDW = 0, 1
 FLAG_STORE_SCORES = 1
 FLAG_SPARSE_K = 2
 FLAG_WIDE_COUNTS = 4
+FLAG_DENSE_ESTEP = 8
 MODEL_POISSON, MODEL_GAUSSIAN, MODEL_POISSON_FLUENCE = 0, 1, 2
 MODELS = {"poisson": MODEL_POISSON, "gaussian": MODEL_GAUSSIAN,
           "poisson_fluence": MODEL_POISSON_FLUENCE}
@@ -57,7 +58,9 @@ class IterStats(ctypes.Structure):
                 ("ms_loglik", ctypes.c_double), ("ms_normalize", ctypes.c_double),
                 ("ms_update", ctypes.c_double), ("ms_compress", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("device_status", ctypes.c_int32),
-                ("kernels", ctypes.c_int32)]
+                ("kernels", ctypes.c_int32), ("pass1_tiles", ctypes.c_int64),
+                ("pass1_exact", ctypes.c_int64), ("pass1_pruned", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _vp, _i64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
@@ -211,7 +214,7 @@ class Context:
                  precision=None, w_floor: float = 1e-10, compress_mode: int = 0,
                  rot_chunk: int = 0, store_scores: bool = False, n_cand: int = 0,
                  device: str = "cuda", stream=None, model: str = "poisson", sigma: float = 1.0,
-                 sparse_k: bool = False, wide_counts: bool = False):
+                 sparse_k: bool = False, wide_counts: bool = False, dense_estep: bool = False):
         import torch
         self.torch = torch
         gauss = MODELS[model] == MODEL_GAUSSIAN
@@ -227,7 +230,8 @@ class Context:
                           n_data=n_data, w_floor=w_floor, compress_mode=compress_mode,
                           flags=(FLAG_STORE_SCORES if store_scores else 0) |
                           (FLAG_SPARSE_K if sparse_k else 0) |
-                          (FLAG_WIDE_COUNTS if wide_counts else 0), rot_chunk=rot_chunk,
+                          (FLAG_WIDE_COUNTS if wide_counts else 0) |
+                          (FLAG_DENSE_ESTEP if dense_estep else 0), rot_chunk=rot_chunk,
                           n_cand=n_cand, model=MODELS[model], sigma=float(sigma))
         L = lib()
         nb = ctypes.c_size_t()

@@ -132,7 +132,7 @@ def test_sparse_k_config_checks(libemc):
     small = nb.value
     assert ws(flags=0) == 0 and nb.value < small  # the non-zero lists take workspace
     assert ws(n_pix=70000) == -4  # pixel indices must fit 16 bits
-    assert ws(flags=8) == -1
+    assert ws(flags=16) == -1
     assert ws(model=1, precision=3, flags=3) == -4  # Poisson only
 
 
@@ -145,3 +145,26 @@ def test_wide_counts_reserve_duplicate_columns(libemc):
                          compress_mode=0, flags=flags, rot_chunk=0, n_cand=0, model=0, sigma=1.0)
         assert libemc.emc_buffer_sizes_for(ctypes.byref(cfg), 50, ctypes.byref(b)) == 0
         assert b.ld_pix == want
+
+
+def test_pruned_estep_workspace(libemc):
+    # stored scores + BF16 split + a Poisson model + no candidates: emc_iteration
+    # prunes pass 1 and keeps a second, reordered copy of the frames;
+    # EMC_FLAG_DENSE_ESTEP (or any other configuration) does without
+    from paper_1409_4256_gb300 import emc
+    nb = ctypes.c_size_t()
+
+    def ws(**kw):
+        base = dict(N=32, precision=2, n_pix=100, n_rot=500, n_data=3000, w_floor=1e-10,
+                    compress_mode=0, flags=1, rot_chunk=0, n_cand=0, model=0, sigma=1.0)
+        base.update(kw)
+        assert libemc.emc_workspace_size(ctypes.byref(emc.Config(**base)), ctypes.byref(nb)) == 0
+        return nb.value
+
+    pruned, dense = ws(), ws(flags=1 | 8)
+    frames = 2 * 3072 * 128  # BF16 [ld_data][ld_pix]
+    assert pruned - dense >= frames
+    assert ws(flags=0) == ws(flags=8)                        # no stored scores: no pruning
+    assert ws(precision=3, flags=1) == ws(precision=3, flags=9)  # FP16 split: none
+    assert ws(n_cand=8) == ws(n_cand=8, flags=9)             # candidate sets: none
+    assert ws(model=2) > ws(model=2, flags=9)                # the fluence model prunes too

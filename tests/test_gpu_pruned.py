@@ -1,0 +1,88 @@
+"""emc_iteration's bound-pruned E-step pass 1 against the dense one.
+
+With stored scores, the BF16 split and a Poisson model, emc_iteration bounds
+every (128-rotation, 256-frame) tile's scores by a contraction of the hi plane
+alone and contracts exactly only the tiles that can hold a score within 110 of
+their frames' maxima; it also regroups the frames by their best rotation
+after every iteration. The first call on fresh frames runs the dense pass (no
+order yet); later calls prune. Skipped tiles have P = 0 in FP32 and no weight
+in lse at FP64 precision, so:
+  * from the same input, the log-likelihood equals the dense pass's to FP64
+    summation order (1e-12 relative);
+  * the model equals it to FP32 summation order in the M-step, whose frames
+    are in another order (rel-L2 1e-6), and the oracle's to the usual 1e-5.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4256_gb300 import build
+    build.build()
+    return torch
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _ctx(torch, p, dense, **kw):
+    from paper_1409_4256_gb300 import emc
+    ctx = emc.Context(p["N"], p["q"], p["quat"], p["w"], p["K"].shape[0],
+                      precision="bf16_split", w_floor=p["w_floor"], store_scores=True,
+                      dense_estep=dense, **kw)
+    ctx.set_frames(torch.as_tensor(p["K"], device="cuda"))
+    return ctx
+
+
+@pytest.mark.parametrize("model,chunk", [("poisson", 0), ("poisson", 384),
+                                         ("poisson_fluence", 0)])
+def test_pruned_iterations_equal_dense(torch_cuda, oracle, small_problem, model, chunk):
+    torch, p = torch_cuda, small_problem
+    g = torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
+    a = _ctx(torch, p, False, model=model, rot_chunk=chunk)
+    d = _ctx(torch, p, True, model=model, rot_chunk=chunk)
+    ga, gd = g, g
+    for it in range(4):  # the first call has no frame order yet and runs dense
+        oa, sa = a.iteration(ga)
+        od, sd = d.iteration(gd)
+        assert sa["device_status"] == 0 and sd["device_status"] == 0
+        # two trajectories: their models part at FP32 rounding (M-step frame order)
+        assert abs(sa["loglik"] - sd["loglik"]) <= 1e-8 * abs(sd["loglik"])
+        assert _rel(oa.cpu().numpy(), od.cpu().numpy()) <= 1e-6
+        if it >= 1:
+            assert sa["kernels"] > sd["kernels"]  # the bound, liveness and list kernels ran
+        ga, gd = oa, od
+    # the same input through both (one pruned step from the dense result): the
+    # same scores, hence lse to FP64 summation order
+    oa, sa = a.iteration(gd)
+    od, sd = d.iteration(gd)
+    assert abs(sa["loglik"] - sd["loglik"]) <= 1e-12 * abs(sd["loglik"])
+    assert _rel(oa.cpu().numpy(), od.cpu().numpy()) <= 1e-6
+    # against the oracle from the same input
+    gin = gd.double().cpu().numpy()
+    if model == "poisson":
+        want, _, L = oracle.iteration(gin, p["quat"], p["w"], p["q"], p["K"].astype(np.float64),
+                                      p["w_floor"])
+    else:
+        want, _, L = oracle.iteration_poisson_fluence(gin, p["quat"], p["w"], p["q"],
+                                                      p["K"].astype(np.float64), p["w_floor"])
+    assert _rel(oa.cpu().numpy(), want) <= 1e-5
+    assert abs(sa["loglik"] - L) <= 1e-4 * p["K"].shape[0]
+
+
+def test_targets_refuse_internal_order_scores(torch_cuda, small_problem):
+    from paper_1409_4256_gb300 import emc
+    torch, p = torch_cuda, small_problem
+    g = torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
+    a = _ctx(torch, p, False)
+    a.iteration(g)
+    with pytest.raises(emc.EmcError):
+        a.targets_from_scores(8)
