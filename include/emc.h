@@ -123,11 +123,13 @@ typedef enum emc_compress_mode {
                                    limits. Not for emc_loglik_static. */
 #define EMC_FLAG_DENSE_ESTEP 8  /* emc_iteration contracts every (rotation tile,
                                    frame tile) in pass 1. Without it, a context
-                                   with EMC_FLAG_STORE_SCORES, the BF16 split,
-                                   a Poisson model and no candidate sets first
-                                   bounds every tile's scores by a contraction
-                                   of the hi plane alone (|S - S_hi| <= N_k/16
-                                   + 1), then contracts exactly only the tiles
+                                   with EMC_FLAG_STORE_SCORES, a split
+                                   precision (BF16 or FP16) and a Poisson
+                                   model first bounds every tile's scores by a
+                                   contraction of the hi plane alone
+                                   (|S - S_hi| <= N_k/16 + 1 for the BF16
+                                   split, N_k/128 + 1 for the FP16 split),
+                                   then contracts exactly only the tiles
                                    that can hold a score within 110 of their
                                    frames' maxima. The others have P = 0 in
                                    FP32 and no weight in lse at FP64 precision,
@@ -136,10 +138,13 @@ typedef enum emc_compress_mode {
                                    tile of their best rotation after every
                                    iteration (a second copy of the frames in
                                    the workspace); the grouping is kept when
-                                   emc_set_frames loads frames again. The stored scores of such a
-                                   context are then in that internal order and
-                                   hold only the contracted tiles;
-                                   emc_targets_from_scores does not read them. */
+                                   emc_set_frames loads frames again. The
+                                   context's stored scores are then in that
+                                   internal order and hold only the contracted
+                                   tiles; emc_targets_from_scores and
+                                   emc_missed_mass read them that way (a
+                                   target among the skipped tiles would carry
+                                   a weight below e^-110). */
 #define EMC_FLAG_SPARSE_K 2     /* emc_set_frames also lists every frame's
                                    non-zero pixels (n_data x n_pix x 4 B of
                                    workspace at most) for emc_loglik_sparse_k;

@@ -41,9 +41,12 @@ bool is_flu(const emc_config* c) { return c->model == EMC_MODEL_POISSON_FLUENCE;
 // emc_iteration's bound-pruned pass 1 (EMC_FLAG_DENSE_ESTEP clears it)
 bool prune_ok(const emc_config* c) {
   return (c->flags & EMC_FLAG_STORE_SCORES) && !(c->flags & EMC_FLAG_DENSE_ESTEP) &&
-         c->precision == EMC_PREC_BF16_SPLIT && c->n_cand == 0 &&
+         (c->precision == EMC_PREC_BF16_SPLIT || c->precision == EMC_PREC_FP16_SPLIT) &&
          (c->model == EMC_MODEL_POISSON || c->model == EMC_MODEL_POISSON_FLUENCE);
 }
+// |S - S_hi| <= n_k / bound_div + 1: the rest below the hi grid is at most 1/16
+// (BF16 split, hi on the 1/8 grid) or 1/128 (FP16 split, hi on the 1/64 grid)
+float bound_div(const emc_config* c) { return c->precision == EMC_PREC_FP16_SPLIT ? 128.f : 16.f; }
 // Poisson-fluence model: the constant c of L = log(W / B_j) + c, log n_pix on
 // the 1/8 grid (L is then the log of W over the slice's mean)
 double flu_shift(const emc_config* c) { return rint(8.0 * log((double)c->n_pix)) / 8.0; }
@@ -226,7 +229,9 @@ struct emc_ctx {
   bool perm_valid;            // the internal frame order comes from an iteration
   int32_t* perm;              // internal position -> frame (swapped with perm2)
   int32_t* perm2;
-  bool scores_internal;       // the stored scores are in the internal order, pruned
+  bool order_pending;         // perm2 holds the order for the next iteration
+  bool scores_internal;       // the stored scores are in the internal order (iperm)
+  bool last_pruned;           // ... and hold only the live tiles (live flags)
   bool frames_loaded;
   bool cand_loaded;
   cudaEvent_t ev[8];
@@ -471,6 +476,9 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
     if (!ctx->perm_valid) {
       CU(launch_identity(ctx->perm, y.ld_data, s));
       CU(launch_identity(ctx->perm2, y.ld_data, s));
+    } else if (ctx->order_pending) {
+      std::swap(ctx->perm, ctx->perm2);
+      ctx->order_pending = false;
     }
     CU(launch_permute_frames(ctx->perm, y.ld_data, y.ld_pix, ctx->Kb, (uint16_t*)(ctx->ws + y.Kp),
                              nsum, (float*)(ctx->ws + y.nsum_p), ctx->flu_cn,
@@ -778,6 +786,17 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   double* lm = pr ? (double*)(c->ws + y.lsem_s) : lse_m;  // lse in the internal order
   double* ls = pr ? (double*)(c->ws + y.lses_s) : lse_s;
   const double* cn_p = y.cn_p ? (const double*)(c->ws + y.cn_p) : nullptr;
+  if (pr && c->order_pending) {
+    // the order the previous iteration found: frames and their arrays follow it
+    std::swap(c->perm, c->perm2);
+    CU(launch_permute_frames(c->perm, y.ld_data, y.ld_pix, c->Kb, (uint16_t*)(c->ws + y.Kp),
+                             (const float*)(c->ws + y.nsum), (float*)(c->ws + y.nsum_p),
+                             c->flu_cn, y.cn_p ? (double*)(c->ws + y.cn_p) : nullptr,
+                             c->flu_invn, y.invn_p ? (float*)(c->ws + y.invn_p) : nullptr,
+                             (int32_t*)(c->ws + y.iperm), s));
+    c->order_pending = false;
+    kernels++;
+  }
   if (pr) {
     double* pm = (double*)(c->ws + y.part_m);
     float* ps = (float*)(c->ws + y.part_s);
@@ -785,11 +804,12 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     int32_t* tlist = (int32_t*)(c->ws + y.tlist);
     int32_t* tcount = (int32_t*)(c->ws + y.tcount);
     if (pruned) {
-      // bound: the hi plane alone (one plane of L read as plain BF16 log W)
-      CU(launch_tc_pass1(p3, EMC_PREC_BF16, bias, y.rows, Kp, y.ld_data, c->cfg.n_data, y.ld_pix,
-                         pm, ps, nullptr, nullptr, nullptr, nullptr, c->status, s));
+      // bound: the hi plane alone (the first plane of L)
+      CU(launch_tc_pass1(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, c->cfg.n_data,
+                         y.ld_pix, pm, ps, nullptr, nullptr, nullptr, nullptr, c->status, s,
+                         nullptr, nullptr, 1));
       CU(launch_bound_live(pm, nmt, y.ld_data, c->cfg.n_data,
-                           (const float*)(c->ws + y.nsum_p), live, s));
+                           (const float*)(c->ws + y.nsum_p), bound_div(&c->cfg), live, s));
       CU(launch_tile_list(live, (int)nmt, (int)nnt, 8, tlist, tcount, s));
     }
     CU(launch_tc_pass1(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, c->cfg.n_data, y.ld_pix,
@@ -853,21 +873,18 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
                      s));
   kernels++;
   if (pr) {
-    // next iteration's frame order: grouped by the row tile of the best rotation
-    // (counting sort, stable), then the frames and their arrays in that order
+    // the next iteration's frame order: grouped by the row tile of the best
+    // rotation (counting sort, stable); applied when that iteration starts, so
+    // that until then the stored scores, iperm and the live flags agree
+    // (sort_frames writes positions below n_data only; the tails stay the identity)
     CU(launch_sort_frames((const int32_t*)(c->ws + y.best), c->perm, c->cfg.n_data, (int)nmt,
                           (int32_t*)(c->ws + y.sortH), (int64_t*)(c->ws + y.sortoff), c->perm2,
                           s));
-    std::swap(c->perm, c->perm2);
-    CU(launch_permute_frames(c->perm, y.ld_data, y.ld_pix, c->Kb, (uint16_t*)(c->ws + y.Kp),
-                             (const float*)(c->ws + y.nsum), (float*)(c->ws + y.nsum_p),
-                             c->flu_cn, y.cn_p ? (double*)(c->ws + y.cn_p) : nullptr,
-                             c->flu_invn, y.invn_p ? (float*)(c->ws + y.invn_p) : nullptr,
-                             (int32_t*)(c->ws + y.iperm), s));
-    // sort_frames writes positions below n_data only; perm2's tail stays the identity
+    c->order_pending = true;
     c->perm_valid = true;
     c->scores_internal = true;
-    kernels += 4;
+    c->last_pruned = pruned;
+    kernels += 3;
   }
   if (stats) CU(cudaEventRecord(c->ev[7], s));
   c->kernels = kernels;
@@ -964,13 +981,17 @@ int emc_targets_from_scores(emc_ctx* ctx, const void* scores, int R, int32_t* ti
   const Layout& y = ctx->lay;
   if (!scores) {
     if (!(ctx->cfg.flags & EMC_FLAG_STORE_SCORES)) return EMC_ERR_ARG;
-    // a bound-pruned iteration leaves them in its internal order, pruned
-    if (ctx->scores_internal) return EMC_ERR_UNSUPPORTED;
     scores = ctx->ws + y.S;
   }
   const float* S = (const float*)scores;
+  // the context's own scores after emc_iteration: its internal frame order and,
+  // if that pass was bound-pruned, its live tiles only
+  const bool internal = scores == (const void*)(ctx->ws + y.S) && ctx->scores_internal;
   CU(launch_topr_columns(S, y.rows, S + y.rows * y.ld_data, y.ld_data, ctx->cfg.n_rot,
-                         ctx->cfg.n_data, R, tidx, tprob, (cudaStream_t)stream));
+                         ctx->cfg.n_data, R, tidx, tprob, (cudaStream_t)stream,
+                         internal ? (const int32_t*)(ctx->ws + y.iperm) : nullptr,
+                         internal && ctx->last_pruned ? (const uint8_t*)(ctx->ws + y.live)
+                                                      : nullptr));
   return EMC_OK;
 }
 
@@ -1097,9 +1118,12 @@ int emc_missed_mass(emc_ctx* ctx, const void* scores, const double* lse_m, const
   float2* lse2 = (float2*)(ctx->ws + y.lse2);
   CU(launch_lse_split(lse_m, lse_s, ctx->cfg.n_data, y.ld_data, lse2, s, ctx->flu_cn));
   const float* S = (const float*)scores;
+  const bool internal = scores == (const void*)(ctx->ws + y.S) && ctx->scores_internal;
   CU(launch_missed_mass(S, y.rows, S + y.rows * y.ld_data, y.ld_data, lse2,
                         (const int32_t*)(ctx->ws + y.cand), ctx->cfg.n_cand, ctx->cfg.n_data,
-                        missed, s));
+                        missed, s, internal ? (const int32_t*)(ctx->ws + y.iperm) : nullptr,
+                        internal && ctx->last_pruned ? (const uint8_t*)(ctx->ws + y.live)
+                                                     : nullptr));
   return EMC_OK;
 }
 

@@ -138,12 +138,14 @@ cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t 
 // gk, gsc != NULL: the Gaussian model's pass 1 (three FP16 planes of s W).
 // tile_list, tile_count (device, optional): contract only the listed
 // (row tile, frame tile) pairs, codes mt * (ld_data / 256) + nt, *tile_count of them
+// hi_only: contract the first plane of L alone (the bound pass of the split
+// forms; per-tile maxima and sums, no stored scores)
 cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
                             const float4* gk, const float4* gsc, int32_t* status,
                             cudaStream_t s, const int32_t* tile_list = nullptr,
-                            const int32_t* tile_count = nullptr);
+                            const int32_t* tile_count = nullptr, int hi_only = 0);
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
 // Bsum != NULL: Poisson-fluence model -- shift[ld_data] is added back to lse,
 // the planes receive BF16 hi + lo of P B_j invn[k] and den[rows] = sum_k P_jk
@@ -199,9 +201,12 @@ cudaError_t mlp_train_step(const MlpLayout& y, float* params, float* grads, floa
 // ---- candidates and the sparse Maximize (sparse.cu) ----
 cudaError_t launch_topm(const float* logits, int64_t B, int64_t n, int64_t ld, int M,
                         int32_t* cand, cudaStream_t s);
+// iperm, live (may be NULL): scores in emc_iteration's internal frame order
+// (frame k in column iperm[k]) holding only the live row tiles
 cudaError_t launch_topr_columns(const float* S, int64_t ldS, const float* Sref, int64_t ld, int64_t nrot,
                                 int64_t n_data, int R, int32_t* tidx, float* tprob,
-                                cudaStream_t s);
+                                cudaStream_t s, const int32_t* iperm = nullptr,
+                                const uint8_t* live = nullptr);
 cudaError_t launch_merge_candidates(const int32_t* first, int R, const int32_t* rest, int M_rest,
                                     int64_t n, int M, int32_t* out, cudaStream_t s);
 cudaError_t launch_csr_build(const int32_t* cand, int64_t n_data, int M, int64_t n_rot,
@@ -226,13 +231,16 @@ cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, i
                                  const double* Bsum = nullptr, const float* invn = nullptr);
 cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, int64_t ld_data,
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
-                               float* missed, cudaStream_t s);
+                               float* missed, cudaStream_t s, const int32_t* iperm = nullptr,
+                               const uint8_t* live = nullptr);
 
 // ---- pruned pass 1 and the frame order (prune.cu) ----
-// live[mt * (ld_data / 256) + nt] from the hi-plane tile maxima part_m (sorted
-// frames) and the frame totals nsum
+// live[mt * (ld_data / 256) + nt] from the hi-plane tile maxima part_m (frames
+// in the internal order), the frame totals nsum and the bound's divisor
+// (|S - S_hi| <= nsum / div + 1)
 cudaError_t launch_bound_live(const double* part_m, int64_t n_mtiles, int64_t ld_data,
-                              int64_t n_data, const float* nsum, uint8_t* live, cudaStream_t s);
+                              int64_t n_data, const float* nsum, float div, uint8_t* live,
+                              cudaStream_t s);
 cudaError_t launch_tile_list(const uint8_t* live, int n_mtiles, int n_ntiles, int group,
                              int32_t* list, int32_t* count, cudaStream_t s);
 // entries of the histogram scratch H (int32) of launch_sort_frames; off needs one more (int64)

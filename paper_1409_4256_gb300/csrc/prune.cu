@@ -1,10 +1,11 @@
 // prune.cu -- exact pruning of the E-step pass 1 inside emc_iteration.
 //
-// The three-term split writes log W = hi + mid + lo with hi on the 1/8 grid and
-// |mid + lo| <= 1/16 (plus 2^-16 of it). A contraction of the hi plane alone
-// gives, for every (j, k), S^hi_jk = sum_i K_ik hi_ij + bias_j with
-//   |S_jk - S^hi_jk| <= E_k = N_k / 16 + 1,   N_k = sum_i K_ik
-// (one unit covers the bias rest and every rounding). A row tile t whose
+// The BF16 three-term split writes log W = hi + mid + lo with hi on the 1/8
+// grid and |mid + lo| <= 1/16 (plus 2^-16 of it); the FP16 split, hi on the
+// 1/64 grid and |rest| <= 1/128. A contraction of the hi plane alone gives,
+// for every (j, k), S^hi_jk = sum_i K_ik hi_ij + bias_j with
+//   |S_jk - S^hi_jk| <= E_k = N_k / div + 1,   N_k = sum_i K_ik
+// (div = 16 or 128; one unit covers the bias rest and every rounding). A row tile t whose
 // maximum of S^hi over its rows, for frame k, lies below
 //   M^hi_k - 2 E_k - 111,   M^hi_k = max_j S^hi_jk,
 // has every S_jk < max_j S_jk - 110: its responsibilities e^(S - lse) are
@@ -28,14 +29,15 @@ namespace emc {
 // frame, then live[mt * nnt + nt] for every row tile.
 __global__ void __launch_bounds__(256)
     bound_live_kernel(const double* __restrict__ part_m, int64_t n_mtiles, int64_t ld_data,
-                      int64_t n_data, const float* __restrict__ nsum, uint8_t* __restrict__ live) {
+                      int64_t n_data, const float* __restrict__ nsum, float div,
+                      uint8_t* __restrict__ live) {
   const int64_t nt = blockIdx.x, nnt = gridDim.x;
   const int64_t s = nt * 256 + threadIdx.x;
   double thr = INFINITY;  // padding frames never make a tile live
   if (s < n_data) {
     double M = -INFINITY;
     for (int64_t mt = 0; mt < n_mtiles; mt++) M = fmax(M, part_m[mt * ld_data + s]);
-    thr = M - (2.0 * ((double)nsum[s] / 16.0 + 1.0) + 111.0);
+    thr = M - (2.0 * ((double)nsum[s] / (double)div + 1.0) + 111.0);
   }
   for (int64_t mt = 0; mt < n_mtiles; mt++) {
     const bool on = part_m[mt * ld_data + s] >= thr;
@@ -177,9 +179,10 @@ __global__ void unpermute_lse_kernel(const int32_t* __restrict__ perm, int64_t n
 }
 
 cudaError_t launch_bound_live(const double* part_m, int64_t n_mtiles, int64_t ld_data,
-                              int64_t n_data, const float* nsum, uint8_t* live, cudaStream_t s) {
+                              int64_t n_data, const float* nsum, float div, uint8_t* live,
+                              cudaStream_t s) {
   bound_live_kernel<<<(unsigned)(ld_data / 256), 256, 0, s>>>(part_m, n_mtiles, ld_data, n_data,
-                                                               nsum, live);
+                                                               nsum, div, live);
   return cudaGetLastError();
 }
 

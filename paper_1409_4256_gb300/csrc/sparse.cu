@@ -105,13 +105,20 @@ cudaError_t launch_topm(const float* logits, int64_t B, int64_t n, int64_t ld, i
 // ------------------------------------------------- training targets (top R) --
 // Per frame (one thread, reading its frame-major scores sequentially): the R
 // largest stored dense scores over rows [0, nrot) and their softmax
-// (targets proportional to the dense responsibilities).
+// (targets proportional to the dense responsibilities). iperm (may be NULL):
+// the scores are in emc_iteration's internal frame order, frame k in column
+// iperm[k]; live (may be NULL): only the row tiles t with
+// live[t * (ld / 256) + column / 256] were contracted (the others hold no score).
 __global__ void topr_columns_kernel(const float* __restrict__ S, int64_t ldS,
                                     const float* __restrict__ Sref, int64_t ld, int64_t nrot,
-                                    int64_t n_data, int R,
+                                    int64_t n_data, int R, const int32_t* __restrict__ iperm,
+                                    const uint8_t* __restrict__ live,
                                     int32_t* __restrict__ tidx, float* __restrict__ tprob) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_data) return;
+  const int64_t kk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kk >= n_data) return;
+  const int64_t k = iperm ? iperm[kk] : kk;  // the score column
+  const uint8_t* lv = live ? live + (k >> 8) : nullptr;
+  const int64_t nnt = ld >> 8;
   float val[kMaxTargets];
   int idx[kMaxTargets];
   for (int r = 0; r < R; r++) {
@@ -121,6 +128,10 @@ __global__ void topr_columns_kernel(const float* __restrict__ S, int64_t ldS,
   int mpos = 0;
   float mval = -INFINITY;
   for (int64_t j = 0; j < nrot; j++) {
+    if (lv && !lv[(j >> 7) * nnt]) {
+      j |= 127;  // a tile not contracted: its scores underflow next to the frame's best
+      continue;
+    }
     const float v = S[k * ldS + j] + Sref[(j >> 5) * ld + k];
     if (v > mval) {
       val[mpos] = v;
@@ -139,17 +150,17 @@ __global__ void topr_columns_kernel(const float* __restrict__ S, int64_t ldS,
   float sum = 0.f;
   for (int r = 0; r < R; r++) sum += __expf(val[r] - mx);
   for (int r = 0; r < R; r++) {
-    tidx[k * R + r] = idx[r];
-    tprob[k * R + r] = __expf(val[r] - mx) / sum;
+    tidx[kk * R + r] = idx[r];
+    tprob[kk * R + r] = __expf(val[r] - mx) / sum;
   }
 }
 
 cudaError_t launch_topr_columns(const float* S, int64_t ldS, const float* Sref, int64_t ld,
                                 int64_t nrot, int64_t n_data, int R, int32_t* tidx, float* tprob,
-                                cudaStream_t s) {
+                                cudaStream_t s, const int32_t* iperm, const uint8_t* live) {
   if (R < 1 || R > kMaxTargets) return cudaErrorInvalidValue;
-  topr_columns_kernel<<<(unsigned)((n_data + 127) / 128), 128, 0, s>>>(S, ldS, Sref, ld, nrot,
-                                                                       n_data, R, tidx, tprob);
+  topr_columns_kernel<<<(unsigned)((n_data + 127) / 128), 128, 0, s>>>(
+      S, ldS, Sref, ld, nrot, n_data, R, iperm, live, tidx, tprob);
   return cudaGetLastError();
 }
 
@@ -552,18 +563,25 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// 1 - sum_{j in C_k} P_jk of a dense E-step, from its stored scores.
+// 1 - sum_{j in C_k} P_jk of a dense E-step, from its stored scores (lse2 in
+// the given frame order). iperm, live (may be NULL): scores in emc_iteration's
+// internal order, and the row tiles contracted there (P = 0 in the others).
 __global__ void missed_mass_kernel(const float* __restrict__ S, int64_t ldS,
                                    const float* __restrict__ Sref, int64_t ld_data, const float2* __restrict__ lse2,
                                    const int32_t* __restrict__ cand, int M, int64_t n_data,
-                                   float* __restrict__ missed) {
+                                   const int32_t* __restrict__ iperm,
+                                   const uint8_t* __restrict__ live, float* __restrict__ missed) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_data) return;
+  const int64_t c = iperm ? iperm[k] : k;  // the score column
+  const uint8_t* lv = live ? live + (c >> 8) : nullptr;
+  const int64_t nnt = ld_data >> 8;
   const float2 L = lse2[k];
   double sum = 0.0;
   for (int m = 0; m < M; m++) {
     const int64_t j = cand[k * M + m];
-    const float e = S[k * ldS + j] + ((Sref[(j >> 5) * ld_data + k] - L.x) - L.y);
+    if (lv && !lv[(j >> 7) * nnt]) continue;
+    const float e = S[c * ldS + j] + ((Sref[(j >> 5) * ld_data + c] - L.x) - L.y);
     sum += (double)__expf(e);
   }
   missed[k] = (float)(1.0 - sum);
@@ -632,9 +650,10 @@ cudaError_t launch_sparse_update(const uint16_t* Kb, int kf16, int64_t ld_pix, i
 
 cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, int64_t ld_data,
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
-                               float* missed, cudaStream_t s) {
-  missed_mass_kernel<<<(unsigned)((n_data + 255) / 256), 256, 0, s>>>(S, ldS, Sref, ld_data, lse2,
-                                                                     cand, M, n_data, missed);
+                               float* missed, cudaStream_t s, const int32_t* iperm,
+                               const uint8_t* live) {
+  missed_mass_kernel<<<(unsigned)((n_data + 255) / 256), 256, 0, s>>>(
+      S, ldS, Sref, ld_data, lse2, cand, M, n_data, iperm, live, missed);
   return cudaGetLastError();
 }
 

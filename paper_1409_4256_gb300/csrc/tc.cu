@@ -629,9 +629,9 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
                             double* part_m, float* part_s, float* S, float* Sref,
                             const float4* gk, const float4* gsc, int32_t* status,
                             cudaStream_t s, const int32_t* tile_list,
-                            const int32_t* tile_count) {
+                            const int32_t* tile_count, int hi_only) {
   const bool gauss = gk != nullptr;
-  const int nterms = gauss ? 3 : score_planes(precision);
+  const int nterms = hi_only ? 1 : (gauss ? 3 : score_planes(precision));
   const bool f16 = gauss || precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
   if (!maps_scores(L, nterms, f16, rows, Kb, ld_data, ld_pix, &mA, &mB))
@@ -651,6 +651,11 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
   a.tile_list = tile_list;
   a.tile_count = tile_list ? tile_count : nullptr;
   a.status = status;
+  if (hi_only) {
+    if (gauss) return cudaErrorInvalidValue;
+    return f16 ? launch<MODE_PASS1, 1, true>(mA, mB, a, s)
+               : launch<MODE_PASS1, 1, false>(mA, mB, a, s);
+  }
   if (gauss) return launch<MODE_PASS1, 3, true>(mA, mB, a, s);
   if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_PASS1, 2, true>(mA, mB, a, s);
   return nterms == 3 ? launch<MODE_PASS1, 3, false>(mA, mB, a, s)

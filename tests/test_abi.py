@@ -148,8 +148,8 @@ def test_wide_counts_reserve_duplicate_columns(libemc):
 
 
 def test_pruned_estep_workspace(libemc):
-    # stored scores + BF16 split + a Poisson model + no candidates: emc_iteration
-    # prunes pass 1 and keeps a second, reordered copy of the frames;
+    # stored scores + a split precision + a Poisson model: emc_iteration prunes
+    # pass 1 and keeps a second, reordered copy of the frames;
     # EMC_FLAG_DENSE_ESTEP (or any other configuration) does without
     from paper_1409_4256_gb300 import emc
     nb = ctypes.c_size_t()
@@ -165,6 +165,8 @@ def test_pruned_estep_workspace(libemc):
     frames = 2 * 3072 * 128  # BF16 [ld_data][ld_pix]
     assert pruned - dense >= frames
     assert ws(flags=0) == ws(flags=8)                        # no stored scores: no pruning
-    assert ws(precision=3, flags=1) == ws(precision=3, flags=9)  # FP16 split: none
-    assert ws(n_cand=8) == ws(n_cand=8, flags=9)             # candidate sets: none
-    assert ws(model=2) > ws(model=2, flags=9)                # the fluence model prunes too
+    assert ws(precision=1) == ws(precision=1, flags=9)       # plain BF16 (no hi plane): none
+    assert ws(precision=0) == ws(precision=0, flags=9)       # FP32: none
+    assert ws(precision=3) > ws(precision=3, flags=9)        # the FP16 split prunes
+    assert ws(n_cand=8) > ws(n_cand=8, flags=9)              # with candidate sets too
+    assert ws(model=2) > ws(model=2, flags=9)                # and the fluence model

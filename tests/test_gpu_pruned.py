@@ -78,11 +78,37 @@ def test_pruned_iterations_equal_dense(torch_cuda, oracle, small_problem, model,
     assert abs(sa["loglik"] - L) <= 1e-4 * p["K"].shape[0]
 
 
-def test_targets_refuse_internal_order_scores(torch_cuda, small_problem):
+@pytest.mark.parametrize("precision", ["bf16_split", "fp16_split"])
+def test_targets_and_missed_mass_after_pruned_iterations(torch_cuda, small_problem, precision):
+    # after pruned iterations the context's stored scores are in its internal
+    # frame order and hold the live tiles only; the training targets (top R and
+    # their softmax) and the missed mass read them as the dense context's
     from paper_1409_4256_gb300 import emc
     torch, p = torch_cuda, small_problem
+    nd, nrot, M, R = p["K"].shape[0], p["quat"].shape[0], 64, 8
     g = torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
-    a = _ctx(torch, p, False)
-    a.iteration(g)
-    with pytest.raises(emc.EmcError):
-        a.targets_from_scores(8)
+
+    def ctx(dense):
+        c = emc.Context(p["N"], p["q"], p["quat"], p["w"], nd, precision=precision,
+                        w_floor=p["w_floor"], store_scores=True, n_cand=M, dense_estep=dense)
+        c.set_frames(torch.as_tensor(p["K"], device="cuda"))
+        return c
+
+    a, d = ctx(False), ctx(True)
+    rng = np.random.default_rng(7)
+    cand = np.stack([rng.choice(nrot, M, replace=False) for _ in range(nd)]).astype(np.int32)
+    for c in (a, d):
+        c.set_candidates(torch.as_tensor(cand, device="cuda"))
+        for _ in range(3):  # the second and third iterations are bound-pruned in `a`
+            _, st = c.iteration(g)
+            assert st["device_status"] == 0
+    ta, pa = (x.cpu().numpy() for x in a.targets_from_scores(R))
+    td, pd = (x.cpu().numpy() for x in d.targets_from_scores(R))
+    for k in range(nd):
+        big_a = {int(j): float(q) for j, q in zip(ta[k], pa[k]) if q > 1e-6}
+        big_d = {int(j): float(q) for j, q in zip(td[k], pd[k]) if q > 1e-6}
+        assert big_a.keys() == big_d.keys()
+        assert all(abs(big_a[j] - big_d[j]) <= 1e-6 for j in big_d)
+    # the missed mass of the same candidate sets
+    ma, md = a.missed_mass().cpu().numpy(), d.missed_mass().cpu().numpy()
+    assert np.abs(ma - md).max() <= 1e-6
