@@ -804,10 +804,9 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     int32_t* tlist = (int32_t*)(c->ws + y.tlist);
     int32_t* tcount = (int32_t*)(c->ws + y.tcount);
     if (pruned) {
-      // bound: the hi plane alone (the first plane of L)
-      CU(launch_tc_pass1(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, c->cfg.n_data,
-                         y.ld_pix, pm, ps, nullptr, nullptr, nullptr, nullptr, c->status, s,
-                         nullptr, nullptr, 1));
+      // bound: the hi plane alone (the first plane of L), per-tile maxima
+      CU(launch_tc_bound(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, y.ld_pix, pm,
+                         c->status, s));
       CU(launch_bound_live(pm, nmt, y.ld_data, c->cfg.n_data,
                            (const float*)(c->ws + y.nsum_p), bound_div(&c->cfg), live, s));
       CU(launch_tile_list(live, (int)nmt, (int)nnt, 8, tlist, tcount, s));

@@ -138,14 +138,12 @@ cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t 
 // gk, gsc != NULL: the Gaussian model's pass 1 (three FP16 planes of s W).
 // tile_list, tile_count (device, optional): contract only the listed
 // (row tile, frame tile) pairs, codes mt * (ld_data / 256) + nt, *tile_count of them
-// hi_only: contract the first plane of L alone (the bound pass of the split
-// forms; per-tile maxima and sums, no stored scores)
 cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
                             const float4* gk, const float4* gsc, int32_t* status,
                             cudaStream_t s, const int32_t* tile_list = nullptr,
-                            const int32_t* tile_count = nullptr, int hi_only = 0);
+                            const int32_t* tile_count = nullptr);
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
 // Bsum != NULL: Poisson-fluence model -- shift[ld_data] is added back to lse,
 // the planes receive BF16 hi + lo of P B_j invn[k] and den[rows] = sum_k P_jk
@@ -166,6 +164,12 @@ cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const
                              int32_t* status, cudaStream_t s, const int32_t* kb_cnt = nullptr,
                              const int32_t* kb_list = nullptr);
 int64_t tc_pass1_tiles(int64_t rows);
+// Bound pass of the pruned pass 1: per 128-row tile and frame, the maximum of
+// S^hi = (first plane of L) K^T + bias into part_m[rows / 128][ld_data]
+// (pairs of row tiles per CTA tile sharing the frame operand).
+cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, int64_t rows,
+                            const uint16_t* Kb, int64_t ld_data, int64_t ld_pix, double* part_m,
+                            int32_t* status, cudaStream_t s);
 
 // nrep grid replicas of n_vox each (row j reduces into replica j mod nrep)
 cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const float* Num,

@@ -118,6 +118,7 @@ struct TcArgs {
   // mt * n_ntiles + nt for t < *tile_count, in raster order
   const int32_t* tile_list;
   const int32_t* tile_count;
+  int n_rowtiles;          // bound pass: 128-row tiles (n_mtiles counts pairs of them)
   int32_t* status;
 };
 
@@ -533,6 +534,191 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------------- pass-1 bound --
+// The bound pass of the pruned pass 1: the hi plane of L alone, S^hi = hi K^T
+// + bias, and only the maximum over each 128-row tile for every frame into
+// part_m[tile][frame]. One CTA tile is a pair of row tiles sharing the
+// 256-frame operand (two 128 x 256 accumulators, 512 TMEM columns): per
+// 64-wide K block, 64 KB of operands feed eight 128 x 256 x 16 MMAs, where a
+// single row tile would fetch its 32 KB frame block for four. A pair whose
+// second row tile lies past the last one loads and contracts the first only.
+// Roles, rings and bounded waits as in tc_kernel.
+template <bool F16>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_bound_kernel(const __grid_constant__ CUtensorMap mapA,
+                    const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
+  constexpr int BK = 64;
+  constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  constexpr int STAGE = 2 * A_BYTES + B_BYTES;
+  constexpr int STAGES = (kSmemBudget - kScratchBytes - 1024 - 256) / STAGE;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr uint32_t IDESC = idesc_f16kind(BM, BN, 0, F16);
+  static_assert(STAGES >= 2, "shared memory too small for two stages");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  uint8_t* stages = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* scratch = reinterpret_cast<float*>(smem + STAGES * STAGE + 256);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);
+    mbar_init(drain, 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    prefetch_tmap(&mapA);
+    prefetch_tmap(&mapB);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int T = a.n_mtiles * a.n_ntiles;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer --
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
+        int mp, nt;
+        tile_coords(t, a, &mp, &nt);
+        const bool two = 2 * mp + 1 < a.n_rowtiles;
+        for (int kb = 0; kb < a.kblocks; kb++, it++) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait(empty + s, ph ^ 1u, abort, kWaitLimitNs)) {
+            fail(abort, a.status);
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(full + s, two ? STAGE : STAGE - A_BYTES);
+          uint8_t* st = stages + s * STAGE;
+          tma_load_3d(st, &mapA, full + s, kb * BK, 2 * mp * BM, 0);
+          if (two) tma_load_3d(st + A_BYTES, &mapA, full + s, kb * BK, (2 * mp + 1) * BM, 0);
+          tma_load_2d(st + 2 * A_BYTES, &mapB, full + s, kb * BK, nt * BN);
+        }
+      }
+      if (!ok) {
+        for (int back = 1; back <= STAGES && it - back >= 0; back++) {
+          const int j = it - back;
+          mbar_wait(full + (j % STAGES), (uint32_t)(j / STAGES) & 1u, abort, kWaitLimitNs);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA --
+    if (lane == 0) {
+      int it = 0, tcount = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < T && ok; t += gridDim.x, tcount++) {
+        if (!mbar_wait(acc_empty, ((uint32_t)tcount & 1u) ^ 1u, abort, kWaitLimitNs)) {
+          fail(abort, a.status);
+          break;
+        }
+        tc_fence_after();
+        int mp, nt;
+        tile_coords(t, a, &mp, &nt);
+        const int nr = 2 * mp + 1 < a.n_rowtiles ? 2 : 1;
+        for (int kb = 0; kb < a.kblocks; kb++, it++) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait(full + s, ph, abort, kWaitLimitNs)) {
+            fail(abort, a.status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = smem_u32(stages + s * STAGE);
+          const uint32_t sB = sA + 2 * A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 16; k++) {
+            const uint64_t bdesc = kmajor_desc<BK>(sB, k);
+            for (int r = 0; r < nr; r++)
+              umma_bf16(tmem + r * BN, kmajor_desc<BK>(sA + r * A_BYTES, k), bdesc, IDESC,
+                        (kb == 0 && k == 0) ? 0u : 1u);
+          }
+          umma_commit(empty + s);
+        }
+        if (ok) umma_commit(acc_full);
+      }
+      umma_commit(drain);
+      mbar_wait(drain, 0, abort, kWaitLimitNs);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue --
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int half = e >> 2;
+    const int r_in = 32 * q + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    const int et = e * 32 + lane;
+    int tcount = 0;
+    for (int t = blockIdx.x; t < T; t += gridDim.x, tcount++) {
+      int mp, nt;
+      tile_coords(t, a, &mp, &nt);
+      const int nr = 2 * mp + 1 < a.n_rowtiles ? 2 : 1;
+      if (!mbar_wait(acc_full, (uint32_t)tcount & 1u, abort, kWaitLimitNs)) {
+        fail(abort, a.status);
+        break;
+      }
+      tc_fence_after();
+      for (int r = 0; r < nr; r++) {
+        const int mt = 2 * mp + r;
+        const int64_t row = (int64_t)mt * BM + r_in;
+        const double b = a.bias[row];
+        const bool valid = row < a.nrot && b > -INFINITY;
+        const float bf = valid ? (float)b : 0.f;
+#pragma unroll 1
+        for (int c = 0; c < 4; c++) {
+          const int col0 = half * 128 + c * 32;
+          uint32_t v0[32];
+          tmem_ld32(lane_addr + r * BN + col0, v0);
+          tmem_ld_wait();
+          if (r == nr - 1 && c == 3) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+          }
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; i++) v[i] = valid ? __uint_as_float(v0[i]) + bf : kSentinel;
+          scratch[q * BN + col0 + lane] = warp_transpose_reduce<true>(v, lane);
+        }
+        named_bar(1, kEpiThreads);
+        float M = scratch[et];
+#pragma unroll
+        for (int qq = 1; qq < 4; qq++) M = fmaxf(M, scratch[qq * BN + et]);
+        a.part_m[(int64_t)mt * a.ld_data + (int64_t)nt * BN + et] = (double)M;
+        named_bar(1, kEpiThreads);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
 // ------------------------------------------------------------- host side --
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -624,14 +810,53 @@ TcArgs base_args(int64_t rows, int n_ntiles, int kblocks) {
 
 int64_t tc_pass1_tiles(int64_t rows) { return rows / BM; }
 
+cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, int64_t rows,
+                            const uint16_t* Kb, int64_t ld_data, int64_t ld_pix, double* part_m,
+                            int32_t* status, cudaStream_t s) {
+  const bool f16 = precision == EMC_PREC_FP16_SPLIT;
+  CUtensorMap mA, mB;
+  if (!maps_scores(L, 1, f16, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
+  const int nrt = (int)(rows / BM);
+  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / 64));
+  a.n_mtiles = (nrt + 1) / 2;  // pairs of row tiles
+  a.group = 4;                 // raster groups of 8 row tiles, as the other passes
+  a.n_rowtiles = nrt;
+  a.nrot = rows;  // validity comes from the bias (-inf on padding rows)
+  a.ld_data = ld_data;
+  a.bias = bias;
+  a.part_m = part_m;
+  a.status = status;
+  constexpr int kStage = 2 * BM * 64 * 2 + BN * 64 * 2;
+  constexpr int kStages = (kSmemBudget - kScratchBytes - 1024 - 256) / kStage;
+  constexpr int kSmem = 1024 + kStages * kStage + 256 + kScratchBytes;
+  static bool attr[2] = {false, false};
+  cudaError_t e = cudaSuccess;
+  if (!attr[f16]) {
+    e = f16 ? cudaFuncSetAttribute(tc_bound_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem)
+            : cudaFuncSetAttribute(tc_bound_kernel<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    attr[f16] = true;
+  }
+  const int T = a.n_mtiles * a.n_ntiles;
+  if (T <= 0) return cudaSuccess;
+  const int grid = T < num_sms() ? T : num_sms();
+  if (f16)
+    tc_bound_kernel<true><<<grid, kThreads, kSmem, s>>>(mA, mB, a);
+  else
+    tc_bound_kernel<false><<<grid, kThreads, kSmem, s>>>(mA, mB, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
                             const float4* gk, const float4* gsc, int32_t* status,
                             cudaStream_t s, const int32_t* tile_list,
-                            const int32_t* tile_count, int hi_only) {
+                            const int32_t* tile_count) {
   const bool gauss = gk != nullptr;
-  const int nterms = hi_only ? 1 : (gauss ? 3 : score_planes(precision));
+  const int nterms = gauss ? 3 : score_planes(precision);
   const bool f16 = gauss || precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
   if (!maps_scores(L, nterms, f16, rows, Kb, ld_data, ld_pix, &mA, &mB))
@@ -651,11 +876,6 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
   a.tile_list = tile_list;
   a.tile_count = tile_list ? tile_count : nullptr;
   a.status = status;
-  if (hi_only) {
-    if (gauss) return cudaErrorInvalidValue;
-    return f16 ? launch<MODE_PASS1, 1, true>(mA, mB, a, s)
-               : launch<MODE_PASS1, 1, false>(mA, mB, a, s);
-  }
   if (gauss) return launch<MODE_PASS1, 3, true>(mA, mB, a, s);
   if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_PASS1, 2, true>(mA, mB, a, s);
   return nterms == 3 ? launch<MODE_PASS1, 3, false>(mA, mB, a, s)
