@@ -123,13 +123,13 @@ typedef enum emc_compress_mode {
                                    limits. Not for emc_loglik_static. */
 #define EMC_FLAG_DENSE_ESTEP 8  /* emc_iteration contracts every (rotation tile,
                                    frame tile) in pass 1. Without it, a context
-                                   with EMC_FLAG_STORE_SCORES, a split
-                                   precision (BF16 or FP16) and a Poisson
-                                   model first bounds every tile's scores by a
-                                   contraction of the hi plane alone
+                                   with a split precision (BF16 or FP16) and a
+                                   Poisson model first bounds every tile's
+                                   scores by a contraction of the hi plane alone
                                    (|S - S_hi| <= N_k/16 + 1 for the BF16
                                    split, N_k/128 + 1 for the FP16 split),
-                                   then contracts exactly only the tiles
+                                   then contracts exactly (in pass 1, and in a
+                                   recomputing pass 2) only the tiles
                                    that can hold a score within 110 of their
                                    frames' maxima. The others have P = 0 in
                                    FP32 and no weight in lse at FP64 precision,

@@ -40,7 +40,7 @@ bool is_gauss(const emc_config* c) { return c->model == EMC_MODEL_GAUSSIAN; }
 bool is_flu(const emc_config* c) { return c->model == EMC_MODEL_POISSON_FLUENCE; }
 // emc_iteration's bound-pruned pass 1 (EMC_FLAG_DENSE_ESTEP clears it)
 bool prune_ok(const emc_config* c) {
-  return (c->flags & EMC_FLAG_STORE_SCORES) && !(c->flags & EMC_FLAG_DENSE_ESTEP) &&
+  return !(c->flags & EMC_FLAG_DENSE_ESTEP) &&
          (c->precision == EMC_PREC_BF16_SPLIT || c->precision == EMC_PREC_FP16_SPLIT) &&
          (c->model == EMC_MODEL_POISSON || c->model == EMC_MODEL_POISSON_FLUENCE);
 }
@@ -561,12 +561,14 @@ struct FrameView {
   const uint16_t* K;
   const double* cn;
   const float* invn;
-  const uint8_t* tile_live;
+  const uint8_t* tile_live;   // stored scores: the contracted tiles of these rows
+  const int32_t* tile_list;   // recomputed scores: the live tiles of these rows
+  const int32_t* tile_count;
 };
 
 // S, Sref: stored scores of these rows, S frame-major with leading dimension
 // ldS (NULL: recompute from L and bias). Bsum: the rows' B_j (Poisson-fluence model).
-// fv (may be NULL): frames in the internal order (stored scores only).
+// fv (may be NULL): frames in the internal order.
 int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const double* bias,
                  int64_t nrot, const double* lse_m, const double* lse_s, const float* S,
                  int64_t ldS, const float* Sref, void* P, int64_t Prows, cudaStream_t s,
@@ -574,8 +576,10 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
                  const FrameView* fv = nullptr) {
   const Layout& y = c->lay;
   const int64_t rows = round_up(nrot, 128);
-  if (fv && !S) return EMC_ERR_ARG;
   const uint8_t* tlive = fv ? fv->tile_live : nullptr;
+  const uint16_t* Kf = fv ? fv->K : c->Kb;
+  const int32_t* tl = fv ? fv->tile_list : nullptr;
+  const int32_t* tc = fv ? fv->tile_count : nullptr;
   if (is_flu(&c->cfg)) {
     if (!bias || !Bsum) return EMC_ERR_ARG;
     float2* lse2 = (float2*)(c->ws + y.lse2);
@@ -590,9 +594,9 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
     } else {
       Planes lp{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
       Planes pp{P, Prows * y.ld_data, y.ld_data};
-      CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, c->Kb, y.ld_data,
+      CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, Kf, y.ld_data,
                              c->cfg.n_data, y.ld_pix, lse_m, lse_s, lse2, pp, c->status, s,
-                             c->flu_cn, Bsum, c->flu_invn, den, kbf));
+                             cn, Bsum, invn, den, kbf, tl, tc));
     }
     return EMC_OK;
   }
@@ -620,9 +624,9 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
   } else {
     Planes lp{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
     Planes pp{P, Prows * y.ld_data, y.ld_data};
-    CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix,
-                           lse_m, lse_s, (float2*)(c->ws + y.lse2), pp, c->status, s, nullptr,
-                           nullptr, nullptr, nullptr, kbf));
+    CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, Kf, y.ld_data, c->cfg.n_data,
+                           y.ld_pix, lse_m, lse_s, (float2*)(c->ws + y.lse2), pp, c->status, s,
+                           nullptr, nullptr, nullptr, nullptr, kbf, tl, tc));
   }
   return EMC_OK;
 }
@@ -839,8 +843,17 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     uint8_t* kbf = y.kbflag ? (uint8_t*)(c->ws + y.kbflag) : nullptr;
     const int32_t* kbc = kbf ? (const int32_t*)(c->ws + y.kbcnt) : nullptr;
     const int32_t* kbl = kbf ? (const int32_t*)(c->ws + y.kblist) : nullptr;
+    // (the chunk's count sits after pass 1's in the same block, which the stats read)
+    int32_t* tlist = pr ? (int32_t*)(c->ws + y.tlist) : nullptr;
+    int32_t* tcount = pr ? (int32_t*)(c->ws + y.tcount) + 16 : nullptr;
+    if (pruned && !S) {  // recomputed pass 2: the live tiles of this chunk's rows
+      CU(launch_tile_list(live + (r0 / 128) * nnt, (int)(crows / 128), (int)nnt, 8, tlist, tcount,
+                          s));
+      kernels++;
+    }
     FrameView fv{Kp, cn_p, y.invn_p ? (const float*)(c->ws + y.invn_p) : nullptr,
-                 pruned ? live + (r0 / 128) * nnt : nullptr};
+                 pruned && S ? live + (r0 / 128) * nnt : nullptr,
+                 pruned && !S ? tlist : nullptr, pruned && !S ? tcount : nullptr};
     if ((st = do_normalize(c, L, y.rows, r0, bias + r0, nr, lm, ls, Sc, y.rows, Sr, P, crows, s,
                            c->flu_B ? c->flu_B + r0 : nullptr, kbf, pr ? &fv : nullptr)))
       return st;

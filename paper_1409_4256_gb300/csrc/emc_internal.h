@@ -147,14 +147,17 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
 // Bsum != NULL: Poisson-fluence model -- shift[ld_data] is added back to lse,
 // the planes receive BF16 hi + lo of P B_j invn[k] and den[rows] = sum_k P_jk
-// (zeroed here, then FP32 atomics).
+// (zeroed here, then FP32 atomics). tile_list, tile_count (optional): only the
+// listed (row tile, frame tile) pairs are recomputed and written (P elsewhere
+// is left as it was: with kb_flag, readers skip those blocks).
 cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bias, int64_t rows,
                                 int64_t nrot, const uint16_t* Kb, int64_t ld_data, int64_t n_data,
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
                                 float2* lse2, Planes P, int32_t* status, cudaStream_t s,
                                 const double* shift = nullptr, const double* Bsum = nullptr,
                                 const float* invn = nullptr, float* den = nullptr,
-                                uint8_t* kb_flag = nullptr);
+                                uint8_t* kb_flag = nullptr, const int32_t* tile_list = nullptr,
+                                const int32_t* tile_count = nullptr);
 // P planes: hi + lo (BF16 split, FP16 split) or hi only (BF16); FP16 planes
 // carry the scale 2^14. den NULL: not written.
 // kb_cnt, kb_list (optional, from launch_kb_lists): contract only the listed

@@ -155,9 +155,12 @@ __global__ void __launch_bounds__(kExpandThreads)
 // (stashed in shared memory when the row fits, STASH, else interpolated again)
 // and its sum, then the split of log W_ij + a_j, a_j = c - log B_j. a_j is
 // carried as ah (1/8 grid) + al: x + ah is formed with its exact rounding
-// error e (two-sum), hi = rint8(x + ah) and the rest r = ((x + ah - hi) + e) + al
-// goes to mid + lo, so no per-rotation rounding of a_j enters the contraction
-// (it would be multiplied by N_k). bias = double[2][rows]: log w_j, then B_j
+// error e (two-sum), hi is the 1/8-grid rounding of the whole x + ah + e + al,
+// and the rest r = ((x + ah - hi) + e) + al goes to mid + lo. No per-rotation
+// rounding of a_j enters the contraction (it would be multiplied by N_k), and
+// the rest stays centred on zero: were al left in every rest, the mid/lo
+// accumulator would grow to N_k al and round at that size on every K step.
+// bias = double[2][rows]: log w_j, then B_j
 // (FP64); Bctx[row] = B_j as well (the context's copy for the sparse steps).
 template <bool INTERIOR, bool STASH>
 __global__ void __launch_bounds__(kExpandThreads)
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kExpandThreads)
       const float s = x + ah;  // two-sum: s + e = x + ah exactly
       const float bb = s - x;
       const float e = (x - (s - bb)) + (ah - bb);
-      hi = rintf(s * kHiScale) * (1.0f / kHiScale);
+      hi = rintf((s + (e + al)) * kHiScale) * (1.0f / kHiScale);
       if (hi < kHiMin || hi > kHiMax) bad = 1;
       hi = fminf(fmaxf(hi, kHiMin), kHiMax);
       r = ((s - hi) + e) + al;

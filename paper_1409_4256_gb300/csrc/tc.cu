@@ -887,7 +887,8 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
                                 int64_t ld_pix, const double* lse_m, const double* lse_s,
                                 float2* lse2, Planes P, int32_t* status, cudaStream_t s,
                                 const double* shift, const double* Bsum, const float* invn,
-                                float* den, uint8_t* kb_flag) {
+                                float* den, uint8_t* kb_flag, const int32_t* tile_list,
+                                const int32_t* tile_count) {
   cudaError_t e = launch_lse_split(lse_m, lse_s, n_data, ld_data, lse2, s, shift);
   if (e != cudaSuccess) return e;
   if (kb_flag) {
@@ -918,6 +919,8 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
   a.den = den;
   a.kb_flag = kb_flag;
   a.kb_ld = (int)(ld_data / 64);
+  a.tile_list = tile_list;
+  a.tile_count = tile_list ? tile_count : nullptr;
   a.status = status;
   if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_NORMALIZE, 2, true>(mA, mB, a, s);
   return nterms == 3 ? launch<MODE_NORMALIZE, 3, false>(mA, mB, a, s)

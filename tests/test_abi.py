@@ -148,8 +148,8 @@ def test_wide_counts_reserve_duplicate_columns(libemc):
 
 
 def test_pruned_estep_workspace(libemc):
-    # stored scores + a split precision + a Poisson model: emc_iteration prunes
-    # pass 1 and keeps a second, reordered copy of the frames;
+    # a split precision + a Poisson model: emc_iteration prunes pass 1 (and a
+    # recomputed pass 2) and keeps a second, reordered copy of the frames;
     # EMC_FLAG_DENSE_ESTEP (or any other configuration) does without
     from paper_1409_4256_gb300 import emc
     nb = ctypes.c_size_t()
@@ -164,7 +164,7 @@ def test_pruned_estep_workspace(libemc):
     pruned, dense = ws(), ws(flags=1 | 8)
     frames = 2 * 3072 * 128  # BF16 [ld_data][ld_pix]
     assert pruned - dense >= frames
-    assert ws(flags=0) == ws(flags=8)                        # no stored scores: no pruning
+    assert ws(flags=0) > ws(flags=8)                         # recomputed scores prune too
     assert ws(precision=1) == ws(precision=1, flags=9)       # plain BF16 (no hi plane): none
     assert ws(precision=0) == ws(precision=0, flags=9)       # FP32: none
     assert ws(precision=3) > ws(precision=3, flags=9)        # the FP16 split prunes

@@ -203,3 +203,40 @@ def test_fluence_model_is_scale_free(torch_cuda, oracle, fprob):
     assert st1["device_status"] == 0 and st8["device_status"] == 0
     assert _rel(out8.cpu().numpy() / 8.0, out1.cpu().numpy()) <= 1e-5
     assert abs(st8["loglik"] - st1["loglik"]) <= 1e-4 * p["K"].shape[0]
+
+
+def test_fluence_bright_frames(torch_cuda, oracle):
+    # frames of a few thousand photons over a finer detector (64 x 64 on the
+    # 32^3 grid, central beamstop): an error in the per-rotation shift of
+    # log(W / B_j), or a split rest that does not average out, is multiplied by
+    # N_k in every score (the few-photon frames of the other tests hide it)
+    from paper_1409_4256_gb300 import emc, synth
+    torch = torch_cuda
+    ds = synth.make_dataset(32, 64, 200, 1.0, radius=8.0, fluence_sigma=0.3,
+                            masked_fraction=0.1)
+    quat, w = oracle.quat_generate(3)
+    K = ds.K
+    nrot, nd = quat.shape[0], K.shape[0]
+    assert K.sum(1).max() > 4000 and K.max() <= 256
+    grid = ds.model_start.astype(np.float32).astype(np.float64)
+    floor = 1e-10 * float(grid.mean())
+    ctx = emc.Context(32, ds.q, quat, w, nd, precision="bf16_split", w_floor=floor,
+                      model="poisson_fluence")
+    ctx.set_frames(torch.as_tensor(K, device="cuda"))
+    g = torch.as_tensor(grid.astype(np.float32), device="cuda")
+    L, bias = ctx.expand(g, 0, nrot)
+    lse_m, lse_s = ctx.loglik(L, bias, nrot)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    W = oracle.expand(grid, quat, ds.q, floor)
+    S = oracle.scores_poisson_fluence(W, w, K.astype(np.float64))
+    _, lse_o, _ = oracle.estep(S)
+    lse = (lse_m + torch.log(lse_s)).cpu().numpy()[:nd]
+    # the FP32 trilinear W carries ~2e-7 relative error per element, which enters
+    # S weighted by the counts: |d lse_k| <= 1e-4 + 6e-7 sqrt(sum_i K_ik^2). The
+    # rest carrying the per-rotation shift gave 4e-4 to 1e-3 here.
+    tol = 1e-4 + 6e-7 * np.sqrt((K.astype(np.float64) ** 2).sum(1))
+    assert np.all(np.abs(lse - lse_o) <= tol), np.abs(lse - lse_o).max()
+    out, st = ctx.iteration(g)
+    want, _, _ = oracle.iteration_poisson_fluence(grid, quat, w, ds.q, K.astype(np.float64), floor)
+    assert st["device_status"] == 0 and _rel(out.cpu().numpy(), want) <= 1e-5

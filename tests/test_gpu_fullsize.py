@@ -11,10 +11,13 @@ by one and on identities that hold at any size.
   and the sparse E-step over 512 candidates per frame (seeded sets made on
   the host) against the oracle's scores over the same candidates.
 * emc160 (160^3, 160x160 detector, n=20 -> 400200 rotations, 200000 frames
-  with log-normal fluence): the dense steps over rotation blocks of 8192.
+  with log-normal fluence): the dense steps over rotation blocks of 8192, for
+  the Poisson model and the Poisson-fluence model.
 
 Sampled outputs: lse_k and the column P_{.k} of a few frames, against the FP64
-oracle's scores of those frames over every rotation. Identities (exact in
+oracle's scores of those frames over every rotation (P within 1e-4; lse within
+1e-4 + 6e-7 sqrt(sum_i K_ik^2), the floor that FP32 interpolation of W sets for
+frames with many photons per pixel). Identities (exact in
 real arithmetic, checked to FP32-accumulation accuracy):
   sum_j P_jk = 1 per frame            -> sum_j den_j = M_data
   sum_{i<n_pix} Num_ij = sum_k P_jk N_k  -> sum_ij Num_ij = sum_k N_k (photons)
@@ -69,8 +72,12 @@ def _run(torch, oracle, name, block, sample, wide=False, models=("poisson",)):
     grid = ds.model_start.astype(np.float32).astype(np.float64)
     cols = _oracle_columns(oracle, grid, quat_o, w_o, ds.q, ds.K[sample].astype(np.float64),
                            1e-10 * float(ds.model_start.mean()), models=models)
+    # the FP32 trilinear W carries ~2e-7 relative error per element, which enters
+    # S weighted by the counts: lse within 1e-4 + 6e-7 sqrt(sum_i K_ik^2)
+    tol = 1e-4 + 6e-7 * np.sqrt((ds.K[sample].astype(np.float64) ** 2).sum(1))
     for m in models:
         res[m]["lse_o"], res[m]["P_o"] = cols[m]
+        res[m]["tol_lse"] = tol
     return res
 
 
@@ -140,7 +147,8 @@ def _run_model(torch, cfg, ds, block, sample, wide, model):
 
 
 def _check(r, sample):
-    assert np.abs(r["lse"][sample] - r["lse_o"]).max() <= 1e-4
+    assert np.all(np.abs(r["lse"][sample] - r["lse_o"]) <= r["tol_lse"]), \
+        np.abs(r["lse"][sample] - r["lse_o"])
     assert np.abs(r["P"] - r["P_o"]).max() <= 1e-4
     assert abs(r["den_sum"] - r["nd"]) <= 1e-4 * r["nd"]
     if r["flu"]:  # no frame is empty: sum_i Num_ij = sum_k P_jk B_j = B_j den_j

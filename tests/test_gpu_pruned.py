@@ -33,22 +33,26 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def _ctx(torch, p, dense, **kw):
+def _ctx(torch, p, dense, stored=True, **kw):
     from paper_1409_4256_gb300 import emc
     ctx = emc.Context(p["N"], p["q"], p["quat"], p["w"], p["K"].shape[0],
-                      precision="bf16_split", w_floor=p["w_floor"], store_scores=True,
+                      precision="bf16_split", w_floor=p["w_floor"], store_scores=stored,
                       dense_estep=dense, **kw)
     ctx.set_frames(torch.as_tensor(p["K"], device="cuda"))
     return ctx
 
 
-@pytest.mark.parametrize("model,chunk", [("poisson", 0), ("poisson", 384),
-                                         ("poisson_fluence", 0)])
-def test_pruned_iterations_equal_dense(torch_cuda, oracle, small_problem, model, chunk):
+@pytest.mark.parametrize("model,chunk,stored", [("poisson", 0, True), ("poisson", 384, True),
+                                                ("poisson_fluence", 0, True),
+                                                ("poisson", 0, False), ("poisson", 384, False),
+                                                ("poisson_fluence", 384, False)])
+def test_pruned_iterations_equal_dense(torch_cuda, oracle, small_problem, model, chunk, stored):
+    # stored: pass 2 reads the live tiles' stored scores; otherwise it recomputes
+    # the scores of the live tiles only (the form for sizes whose scores do not fit)
     torch, p = torch_cuda, small_problem
     g = torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
-    a = _ctx(torch, p, False, model=model, rot_chunk=chunk)
-    d = _ctx(torch, p, True, model=model, rot_chunk=chunk)
+    a = _ctx(torch, p, False, stored, model=model, rot_chunk=chunk)
+    d = _ctx(torch, p, True, stored, model=model, rot_chunk=chunk)
     ga, gd = g, g
     for it in range(4):  # the first call has no frame order yet and runs dense
         oa, sa = a.iteration(ga)
