@@ -46,6 +46,7 @@ LEARNED_FORMS = ("learned",)
 ADAPTIVE_FORMS = ("adaptive",)
 GAUSS_FORMS = ("gaussian",)
 FLUENCE_FORMS = ("poisson_fluence",)
+RECON_FORMS = ("reconstruct",)
 SPARSE_K_FORMS = ("sparse_k",)
 
 
@@ -65,6 +66,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-iters", type=int, default=30,
                     help="iterations of the learned-vs-dense model comparison (0 to skip)")
+    ap.add_argument("--recon-iters", type=int, default=10,
+                    help="iterations of the reconstruct form")
     ap.add_argument("--adaptive-iters", type=int, default=12,
                     help="iterations of the adaptive-sampling schedule")
     ap.add_argument("--sigma", type=float, default=1.0,
@@ -386,6 +389,47 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
     return res
 
 
+def reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot):
+    """Consecutive iterations from the start model in the workload's noise model
+    (the Poisson-fluence model where frames carry a random fluence): time per
+    iteration and the model's relative L2 error against the true intensity over
+    the voxels the detector's q-range reaches, after a least-squares scale (the
+    fluence model fixes the model only up to one)."""
+    model = "poisson_fluence" if cfg.get("fluence_sigma", 0.0) > 0 else "poisson"
+    prec = args.precision if args.precision in ("bf16_split", "fp16_split") else "bf16_split"
+    ctx = make_ctx(prec, model=model)
+    N = cfg["N"]
+    ax = torch.arange(N, device=grid.device, dtype=torch.float64) - N // 2
+    r2 = ax[:, None, None] ** 2 + ax[None, :, None] ** 2 + ax[None, None, :] ** 2
+    inside = r2 <= (N / 2 - 1) ** 2
+    truth = torch.as_tensor(ds.model_true, device=grid.device)[inside]
+
+    def err(g):
+        x = g.double()[inside]
+        sc = float((x * truth).sum() / (x * x).sum())
+        return float(torch.linalg.norm(sc * x - truth) / torch.linalg.norm(truth))
+
+    errs, ms, tiles = [err(grid)], [], []
+    a, b = grid.clone(), torch.empty_like(grid)
+    with torch.cuda.stream(stream):
+        for _ in range(args.recon_iters):
+            _, st = ctx.iteration(a, b, stats=True, stream=stream)
+            if st["device_status"] != 0:
+                raise RuntimeError(f"device status {st['device_status']}")
+            ms.append(st["ms_total"])
+            tiles.append(st["pass1_exact"] / st["pass1_tiles"])
+            errs.append(err(b))
+            a, b = b, a
+    del ctx
+    # pairs/s over the iterations after the first (which has no frame order yet
+    # and runs the dense pass 1)
+    later = ms[1:] if len(ms) > 1 else ms
+    return {"model": model, "precision": prec, "iterations": args.recon_iters,
+            "ms_per_iteration": ms, "pass1_exact_tile_fraction": tiles,
+            "rel_err_vs_truth_after_scale_fit": errs,
+            "value": n_rot * ds.K.shape[0] / (sum(later) / len(later) * 1e-3)}
+
+
 def sparse_k_form(torch, emc, cfg, ds, quat, w, grid, K_dev, stream, tensor_pass1_ms):
     """E-step pass 1 gathered over each frame's non-zero pixels (FP32 log W),
     timed beside the same pass as a dense FP32 SIMT contraction and the
@@ -488,10 +532,12 @@ def run_ours(args):
     K_dev = torch.as_tensor(ds.K, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
+    wide = bool(ds.K.max() > 256)  # counts above 256 (160^3): duplicate pixel columns
+
     def make_ctx(prec, **kw):
         c = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision=prec, w_floor=floor,
                         store_scores=not args.recompute, device=str(dev), stream=stream,
-                        rot_chunk=rot_chunk_for(n_rot, n_data), **kw)
+                        rot_chunk=rot_chunk_for(n_rot, n_data), wide_counts=wide, **kw)
         c.set_frames(K_dev, stream=stream)
         return c
 
@@ -560,7 +606,12 @@ def run_ours(args):
                  "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "traffic": traffic, "traffic_unit": "bytes per launch",
                  "algorithmic_flops_per_launch": flops, "executed_flops_per_launch": executed,
-                 "exact_tile_fraction": exact})
+                 "executed_frac": executed / (dom_ms * 1e-3) / 1e12 / peak,
+                 "exact_tile_fraction": exact,
+                 "frac_basis": ("dense-equivalent: 2 n_pix per pair over every pair; the pruned "
+                                "pass executes executed_flops (hi-plane bound over every tile, "
+                                "every plane over the live tiles)" if pruned else
+                                "2 n_pix per pair over every pair")})
 
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
@@ -573,6 +624,12 @@ def run_ours(args):
     del ctx  # every other form builds its own context
     torch.cuda.empty_cache()
     for f in [x for x in others if x not in ADAPTIVE_FORMS]:
+        if f in RECON_FORMS:
+            try:
+                forms[f] = reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot)
+            except Exception as e:
+                forms[f] = {"error": str(e)[:300]}
+            continue
         if f in SPARSE_K_FORMS:
             try:
                 forms[f] = sparse_k_form(torch, emc, cfg, ds, quat, w, grid, K_dev, stream,
