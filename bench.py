@@ -40,6 +40,8 @@ WORKLOAD_TEXT = {
              "frames, 1 photon/pixel",
     "emc128": "128^3 grid, 128x128 detector, n=16 -> 204960 rotations, 100000 Poisson frames, "
               "0.3 photons/pixel",
+    "emc160": "160^3 grid, 160x160 detector, n=20 -> 400200 rotations, 200000 Poisson frames, "
+              "0.2 photons/pixel, log-normal fluence (sigma 0.3)",
 }
 DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16_split": "bf16x3", "fp16_split": "f16x2"}
 LEARNED_FORMS = ("learned",)

@@ -208,7 +208,10 @@ def _stream(stream) -> int:
 
 
 class Context:
-    """An emc_ctx plus its caller-owned workspace (a torch uint8 tensor)."""
+    """An emc_ctx plus its caller-owned workspace (a torch uint8 tensor).
+
+    model: "poisson", "poisson_fluence" or "gaussian"; dense_estep=True sets
+    EMC_FLAG_DENSE_ESTEP (emc_iteration then contracts every pass-1 tile)."""
 
     def __init__(self, N: int, q: np.ndarray, quat: np.ndarray, weight: np.ndarray, n_data: int,
                  precision=None, w_floor: float = 1e-10, compress_mode: int = 0,

@@ -1,10 +1,10 @@
 """emc_iteration's bound-pruned E-step pass 1 against the dense one.
 
-With stored scores, the BF16 split and a Poisson model, emc_iteration bounds
-every (128-rotation, 256-frame) tile's scores by a contraction of the hi plane
-alone and contracts exactly only the tiles that can hold a score within 110 of
-their frames' maxima; it also regroups the frames by their best rotation
-after every iteration. The first call on fresh frames runs the dense pass (no
+With a split precision and a Poisson model, emc_iteration bounds every
+(128-rotation, 256-frame) tile's scores by a contraction of the hi plane alone
+and contracts exactly only the tiles that can hold a score within 110 of their
+frames' maxima, in pass 1 and (without stored scores) in the recomputing pass
+2; it also regroups the frames by their best rotation after every iteration. The first call on fresh frames runs the dense pass (no
 order yet); later calls prune. Skipped tiles have P = 0 in FP32 and no weight
 in lse at FP64 precision, so:
   * from the same input, the log-likelihood equals the dense pass's to FP64
