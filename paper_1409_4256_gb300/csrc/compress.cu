@@ -1,85 +1,232 @@
 // compress.cu -- c-step of EMC (Eq. 2.12; Eq. 2.5 + 2.10 in IDW mode).
 //
-// One CTA per rotation row j, threads over pixels. Each (i, j) recomputes the
-// double-float grid point p = R_j q_i + N/2 (the same weights f(p_l - R_j q_i)
-// that expansion used) and scatters f * Num_ij into g_num and f * den_j into
-// g_den with FP64 atomics resolved in L2 (the N^3 FP64 grids, 2 MB at 64^3,
-// stay L2-resident). The paper's insert_slices kernel also used one block
-// per slice. Rotations without responsibility mass (den_j = 0) are skipped.
-// Every slice passes through the centre of the grid, so concurrent CTAs
-// reduce into the same central voxels; with nrep > 1 the CTA of row j uses
-// grid replica j mod nrep (nrep x N^3 per grid, summed by the final division)
-// to spread those reductions over more addresses.
+// One CTA per rotation row j. Each (i, j) recomputes the double-float grid
+// point p = R_j q_i + N/2 (the same weights f(p_l - R_j q_i) that expansion
+// used) and contributes f * Num_ij to g_num and f * den_j to g_den, which are
+// reduced with FP64 atomics resolved in L2 (the N^3 FP64 grids, 2 MB at 64^3,
+// stay L2-resident). The paper's insert_slices kernel also used one block per
+// slice. Rotations without responsibility mass (den_j = 0) are skipped. Every
+// slice passes through the centre of the grid, so concurrent CTAs reduce into
+// the same central voxels; with nrep > 1 the CTA of row j uses grid replica
+// j mod nrep (nrep x N^3 per grid, summed by the final division) to spread
+// those reductions over more addresses.
+//
+// Corner merging. The used pixels are grouped by cells of (q_x, q_y), so a
+// group is a small patch of the detector sheet, and neighbouring pixels share
+// most of their trilinear corners (about 8 corner terms per 2.5 distinct
+// voxels). A warp takes one group (up to two pixels per lane), bounds its
+// corners by a box, and sums the terms per voxel in a shared-memory box of
+// FP32 pairs (numerator, denominator) before one FP64 reduction per touched
+// voxel:
+//  * pixels with the same floor cell share all eight voxels; __match_any_sync
+//    finds them and the lowest lane sums their terms in lane order;
+//  * the remaining lanes have distinct floor cells, so for one corner offset c
+//    their voxels are distinct: corner by corner (a __syncwarp between
+//    corners) each lane adds into its slot without atomics;
+//  * the flush walks the same order, reduces a non-zero slot once and zeroes it.
+// The order of every FP32 addition is fixed, so the result does not depend on
+// scheduling beyond the FP64 order of the L2 reductions. A group whose box
+// exceeds kAggCap slots reduces its corners directly.
+#include <limits.h>
+
 #include "emc_common.cuh"
 #include "emc_internal.h"
 
 namespace emc {
 
-constexpr int kCompressThreads = 256;
+constexpr int kAggWarps = 4;
+constexpr int kAggCap = 672;       // box slots per warp (float2 each)
+constexpr int kAggStage = 32 * 8;  // merge staging: 8 corner terms per lane
+constexpr int kAggThreads = kAggWarps * 32;
+// 29.7 KB per CTA: seven CTAs (28 warps) per SM
+constexpr size_t kAggSmem = sizeof(float2) * kAggWarps * (kAggCap + kAggStage);
+static_assert(kCompressGroup == 64, "at most two pixels per lane");
+
+__device__ __forceinline__ bool in_grid(int x, int y, int z, int N) {
+  return (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N && (unsigned)z < (unsigned)N;
+}
+
+// the eight corner terms of one pixel straight into the grids
+template <bool INTERIOR>
+__device__ __forceinline__ void reduce_direct(const int* f, const float* t, float v, float dvi,
+                                              int N, double* g_num, double* g_den) {
+  const int64_t nn = (int64_t)N * N;
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
+    const int x = f[0] + cx, y = f[1] + cy, z = f[2] + cz;
+    if (!INTERIOR && !in_grid(x, y, z, N)) continue;
+    const float w = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
+    if (w == 0.f) continue;
+    const int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
+    // FP32 products (relative error 6e-8), FP64 accumulation in L2
+    atomicAdd(g_num + l, (double)(w * v));
+    if (dvi != 0.f) atomicAdd(g_den + l, (double)(w * dvi));
+  }
+}
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 // INTERIOR: all trilinear corners of every pixel lie inside the grid (checked
-// on the host from max |q_i|), so no bounds checks and one base index.
+// on the host from max |q_i|), so no bounds checks.
 template <bool INTERIOR>
-__global__ void __launch_bounds__(kCompressThreads)
-    compress_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
-                    int64_t ld_pix, int N, const RotDF* __restrict__ rot,
-                    const float* __restrict__ Num, const float* __restrict__ den, int mode,
-                    double* __restrict__ g_num, double* __restrict__ g_den, int nrep,
-                    int64_t n_vox) {
-  const int64_t row = blockIdx.x;
-  const int64_t rep = (row % nrep) * n_vox;
-  g_num += rep;
-  g_den += rep;
+__global__ void __launch_bounds__(kAggThreads)
+    compress_kernel(Geom g, const RotDF* __restrict__ rot, const float* __restrict__ Num,
+                    const float* __restrict__ den, int mode, double* __restrict__ g_num,
+                    double* __restrict__ g_den, int nrep, int64_t n_vox) {
+  extern __shared__ float2 agg_smem[];
   __shared__ RotDF R;
+  const int64_t row = blockIdx.x;
   const float dj = den[row];
   // a rotation without responsibility mass has Num = 0 and den = 0 (both
   // modes): it adds nothing, and sparse iterations leave most rows so
   if (!(dj > 0.f)) return;
+  const int64_t rep = (row % nrep) * n_vox;
+  g_num += rep;
+  g_den += rep;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* box = agg_smem + warp * (kAggCap + kAggStage);
+  float2* stage = box + kAggCap;
   if (threadIdx.x < 18)
     reinterpret_cast<float*>(&R)[threadIdx.x] = reinterpret_cast<const float*>(rot + row)[threadIdx.x];
+  for (int s = lane; s < kAggCap; s += 32) box[s] = make_float2(0.f, 0.f);
   __syncthreads();
-  const float half_n = 0.5f * (float)N;
+  const int N = g.N;
   const int64_t nn = (int64_t)N * N;
-  const float* Nr = Num + row * ld_pix;
+  const float half_n = 0.5f * (float)N;
+  const float* Nr = Num + row * g.ld_pix;
   const float inv_d = (mode == EMC_COMPRESS_IDW) ? 1.0f / dj : 1.0f;
   const float dv = (mode == EMC_COMPRESS_IDW) ? 1.0f : dj;
-  // every column with geometry: pixels (w = 1) and duplicate columns carrying
-  // counts above 256 (w = kDupMark), which add numerator but no denominator
-  for (int64_t i = threadIdx.x; i < ld_pix; i += kCompressThreads) {
-    float4 a = qh[i], b = ql[i];
-    if (a.w == 0.f) continue;
-    int f[3];
-    float t[3];
-    rotate_to_grid(R, a, b, half_n, f, t);
-    const float v = Nr[i] * inv_d;
-    const float dvi = a.w == 1.f ? dv : 0.f;
-    if constexpr (INTERIOR) {
-      const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
-      const int nn32 = N * N;
-      const int base = f[0] * nn32 + f[1] * N + f[2];
+
+  for (int grp = warp; grp < g.ngroups; grp += kAggWarps) {
+    const int p0 = g.gstart[grp], np = g.gstart[grp + 1] - p0;
+    const int halves = np > 32 ? 2 : 1;  // warp-uniform
+    int f[2][3];
+    float t[2][3], v[2];
+    bool has[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int k = lane + 32 * h;
+      has[h] = k < np;
+      if (has[h]) {
+        rotate_to_grid(R, g.gqh[p0 + k], g.gql[p0 + k], half_n, f[h], t[h]);
+        v[h] = Nr[g.gpix[p0 + k]] * inv_d;
+      } else {
+        f[h][0] = f[h][1] = f[h][2] = 0;
+        t[h][0] = t[h][1] = t[h][2] = 0.f;
+        v[h] = 0.f;
+      }
+    }
+    // the box of every corner of the group: floors lo .. hi, corners to hi + 1
+    int lo[3], dim[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const int mn = min(has[0] ? f[0][a] : INT_MAX, has[1] ? f[1][a] : INT_MAX);
+      const int mx = max(has[0] ? f[0][a] : INT_MIN, has[1] ? f[1][a] : INT_MIN);
+      lo[a] = warp_min(mn);
+      dim[a] = warp_max(mx) - lo[a] + 2;
+    }
+    const int64_t vol = (int64_t)dim[0] * dim[1] * dim[2];
+    if (vol > kAggCap) {
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+        if (has[h]) reduce_direct<INTERIOR>(f[h], t[h], v[h], dv, N, g_num, g_den);
+      continue;
+    }
+    int key[2] = {0, 0};
+    bool lead[2] = {false, false};
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      if (h >= halves) break;
+      // slot of corner 0; absent lanes get distinct negative keys
+      key[h] = has[h] ? ((f[h][0] - lo[0]) * dim[1] + (f[h][1] - lo[1])) * dim[2] + (f[h][2] - lo[2])
+                      : -1 - lane;
+      const unsigned m = __match_any_sync(0xffffffffu, key[h]);
+      lead[h] = has[h] && (__ffs(m) - 1 == lane);
+      float2 acc[8];
 #pragma unroll
       for (int c = 0; c < 8; c++) {
         const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
-        const float w = wx[cx] * wy[cy] * wz[cz];
-        if (w == 0.f) continue;
-        const int l = base + cx * nn32 + cy * N + cz;
-        atomicAdd(g_num + l, (double)(w * v));
-        if (dvi != 0.f) atomicAdd(g_den + l, (double)(w * dvi));
+        const float w = (cx ? t[h][0] : 1.f - t[h][0]) * (cy ? t[h][1] : 1.f - t[h][1]) *
+                        (cz ? t[h][2] : 1.f - t[h][2]);
+        acc[c] = make_float2(w * v[h], w * dv);
       }
-    } else {
+      // pixels sharing a floor cell: the lowest lane sums the terms in lane order
+      const bool shared = has[h] && m != (1u << lane);
+      if (__any_sync(0xffffffffu, shared)) {
+        if (shared && !lead[h])
+#pragma unroll
+          for (int c = 0; c < 8; c++) stage[lane * 8 + c] = acc[c];
+        __syncwarp();
+        if (shared && lead[h]) {
+          unsigned rest = m & ~(1u << lane);
+          while (rest) {
+            const int l = __ffs(rest) - 1;
+            rest &= rest - 1;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+              const float2 o = stage[l * 8 + c];
+              acc[c].x += o.x;
+              acc[c].y += o.y;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      // corner by corner: the leaders' slots for one offset are distinct
 #pragma unroll
       for (int c = 0; c < 8; c++) {
-        int x = f[0] + ((c >> 2) & 1), y = f[1] + ((c >> 1) & 1), z = f[2] + (c & 1);
-        if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= N) continue;
-        float w = (((c >> 2) & 1) ? t[0] : 1.f - t[0]) * (((c >> 1) & 1) ? t[1] : 1.f - t[1]) *
-                  ((c & 1) ? t[2] : 1.f - t[2]);
-        if (w == 0.f) continue;
-        int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
-        // FP32 products (relative error 6e-8), FP64 accumulation in L2
-        atomicAdd(g_num + l, (double)(w * v));
-        if (dvi != 0.f) atomicAdd(g_den + l, (double)(w * dvi));
+        const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
+        if (lead[h] && (INTERIOR || in_grid(f[h][0] + cx, f[h][1] + cy, f[h][2] + cz, N))) {
+          const int s = key[h] + (cx * dim[1] + cy) * dim[2] + cz;
+          float2 b = box[s];
+          b.x += acc[c].x;
+          b.y += acc[c].y;
+          box[s] = b;
+        }
+        __syncwarp();
       }
     }
+    // flush in the same order: the first visit of a slot reduces and zeroes it
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      if (h >= halves) break;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
+        const int x = f[h][0] + cx, y = f[h][1] + cy, z = f[h][2] + cz;
+        if (lead[h] && (INTERIOR || in_grid(x, y, z, N))) {
+          const int s = key[h] + (cx * dim[1] + cy) * dim[2] + cz;
+          const float2 b = box[s];
+          if (b.x != 0.f || b.y != 0.f) {
+            const int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
+            if (b.x != 0.f) atomicAdd(g_num + l, (double)b.x);
+            if (b.y != 0.f) atomicAdd(g_den + l, (double)b.y);
+            box[s] = make_float2(0.f, 0.f);
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  // duplicate columns carrying counts above 256 (w = kDupMark) share their
+  // pixel's geometry and add numerator only
+  for (int64_t i = g.n_pix + threadIdx.x; i < g.ld_pix; i += kAggThreads) {
+    const float4 a = g.qh[i];
+    if (a.w == 0.f) continue;
+    int f[3];
+    float t[3];
+    rotate_to_grid(R, a, g.ql[i], half_n, f, t);
+    reduce_direct<INTERIOR>(f, t, Nr[i] * inv_d, a.w == 1.f ? dv : 0.f, N, g_num, g_den);
   }
 }
 
@@ -89,11 +236,11 @@ cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const
   if (nrot <= 0) return cudaSuccess;
   const int64_t n_vox = (int64_t)g.N * g.N * g.N;
   if (g.interior)
-    compress_kernel<true><<<(unsigned)nrot, kCompressThreads, 0, s>>>(
-        g.qh, g.ql, g.n_pix, g.ld_pix, g.N, rot, Num, den, mode, g_num, g_den, nrep, n_vox);
+    compress_kernel<true><<<(unsigned)nrot, kAggThreads, kAggSmem, s>>>(
+        g, rot, Num, den, mode, g_num, g_den, nrep, n_vox);
   else
-    compress_kernel<false><<<(unsigned)nrot, kCompressThreads, 0, s>>>(
-        g.qh, g.ql, g.n_pix, g.ld_pix, g.N, rot, Num, den, mode, g_num, g_den, nrep, n_vox);
+    compress_kernel<false><<<(unsigned)nrot, kAggThreads, kAggSmem, s>>>(
+        g, rot, Num, den, mode, g_num, g_den, nrep, n_vox);
   return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <numeric>
 #include <vector>
 
 #include "emc_common.cuh"
@@ -23,7 +25,7 @@ struct Layout {
       Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, gk, gauss,
       Kb2, skcnt, skoff, skent, dupsrc, duprank, pixmax, fcn, finvn, fB, kbflag, kbcnt, kblist,
       Kp, perm, perm2, iperm, nsum, nsum_p, cn_p, invn_p, best, lsem_s, lses_s, live, tlist,
-      tcount, sortH, sortoff, total;
+      tcount, sortH, sortoff, cgs, cgp, cgqh, cgql, total;
   int64_t sort_entries;
 };
 
@@ -119,6 +121,10 @@ Layout make_layout(const emc_config* c) {
   };
   y.qh = take(sizeof(float4) * y.ld_pix);
   y.ql = take(sizeof(float4) * y.ld_pix);
+  y.cgs = take(sizeof(int32_t) * (c->n_pix + 1));
+  y.cgp = take(sizeof(int32_t) * (c->n_pix + 1));
+  y.cgqh = take(sizeof(float4) * (c->n_pix + 1));
+  y.cgql = take(sizeof(float4) * (c->n_pix + 1));
   y.quat = take(sizeof(double) * 4 * c->n_rot);
   y.rot = take(sizeof(RotDF) * c->n_rot);
   y.logw = take(sizeof(double) * c->n_rot);
@@ -324,6 +330,32 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
     qh[i] = a;
     ql[i] = b;
   }
+  // compression groups: a stable sort of the pixels by their cell of
+  // (q_x, q_y); a sheet of pixels crosses each cell in a small patch, whose
+  // trilinear corners the compression merges before reducing them into the grid
+  std::vector<int32_t> gord(cfg->n_pix), gstart;
+  std::vector<float4> gqh(cfg->n_pix + 1), gql(cfg->n_pix + 1);
+  {
+    std::vector<int64_t> key(cfg->n_pix);
+    for (int64_t i = 0; i < cfg->n_pix; i++) {
+      const int64_t cx = (int64_t)floor(q[3 * i] / kCompressCell) + 4096;
+      const int64_t cy = (int64_t)floor(q[3 * i + 1] / kCompressCell) + 4096;
+      key[i] = cy * 16384 + cx;
+    }
+    std::iota(gord.begin(), gord.end(), 0);
+    std::stable_sort(gord.begin(), gord.end(),
+                     [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    for (int64_t p = 0, run = 0; p < cfg->n_pix; p++) {
+      if (p == 0 || key[gord[p]] != key[gord[p - 1]] || run == kCompressGroup) {
+        gstart.push_back((int32_t)p);
+        run = 0;
+      }
+      run++;
+      gqh[p] = qh[gord[p]];
+      gql[p] = ql[gord[p]];
+    }
+    gstart.push_back((int32_t)cfg->n_pix);
+  }
   std::vector<double> lw(cfg->n_rot);
   for (int64_t j = 0; j < cfg->n_rot; j++) lw[j] = log(weight[j]);
   std::vector<RotDF> rot(cfg->n_rot);
@@ -364,6 +396,11 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   c->geom.n_pix = cfg->n_pix;
   c->geom.ld_pix = y.ld_pix;
   c->geom.N = cfg->N;
+  c->geom.ngroups = (int)gstart.size() - 1;
+  c->geom.gstart = (const int32_t*)(c->ws + y.cgs);
+  c->geom.gpix = (const int32_t*)(c->ws + y.cgp);
+  c->geom.gqh = (const float4*)(c->ws + y.cgqh);
+  c->geom.gql = (const float4*)(c->ws + y.cgql);
   {
     // |R q| = |q|: with every |q_i| below N/2 - 1 (less a margin far above the
     // 1e-9-voxel error of the rotation) each p = R q + N/2 has floor in
@@ -398,6 +435,14 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
   ok &= cudaMemcpyAsync(c->ws + y.qh, qh.data(), sizeof(float4) * y.ld_pix,
                         cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->ws + y.ql, ql.data(), sizeof(float4) * y.ld_pix,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.cgs, gstart.data(), sizeof(int32_t) * gstart.size(),
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.cgp, gord.data(), sizeof(int32_t) * cfg->n_pix,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.cgqh, gqh.data(), sizeof(float4) * cfg->n_pix,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.cgql, gql.data(), sizeof(float4) * cfg->n_pix,
                         cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->quat, quat, sizeof(double) * 4 * cfg->n_rot, cudaMemcpyHostToDevice,
                         s) == cudaSuccess;

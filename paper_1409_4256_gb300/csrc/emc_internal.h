@@ -20,7 +20,18 @@ struct Geom {
   int64_t ld_pix;
   int N;
   int interior;  // every |q_i| < N/2 - 1 with margin: all 8 corners of every R_j q_i lie in the grid
+  // compression groups: the used pixels binned by kCompressCell-voxel cells of
+  // (q_x, q_y), at most kCompressGroup per group; group g holds the positions
+  // gstart[g] .. gstart[g + 1] of gpix (pixel columns) and of gqh/gql (their
+  // geometry in that order)
+  int ngroups;
+  const int32_t* gstart;
+  const int32_t* gpix;
+  const float4* gqh;
+  const float4* gql;
 };
+constexpr int kCompressGroup = 64;
+constexpr double kCompressCell = 6.0;
 
 // A block of rows of a (possibly multi-plane) row-major matrix.
 struct Planes {
