@@ -23,7 +23,10 @@
 //  * the remaining lanes have distinct floor cells, so for one corner offset c
 //    their voxels are distinct: corner by corner (a __syncwarp between
 //    corners) each lane adds into its slot without atomics;
-//  * the flush walks the same order, reduces a non-zero slot once and zeroes it.
+//  * the lane that touches a slot first (in that fixed order) owns it; after the
+//    last step each owner reduces its slots once and clears them. The slot keeps
+//    the negated denominator sum, so +0.0 (the cleared state) means untouched and
+//    -0.0 a slot touched by zero terms (denominator terms are never negative).
 // The order of every FP32 addition is fixed, so the result does not depend on
 // scheduling beyond the FP64 order of the L2 reductions. A group whose box
 // exceeds kAggCap slots reduces its corners directly.
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(kAggThreads)
     }
     int key[2] = {0, 0};
     bool lead[2] = {false, false};
+    unsigned own = 0;  // bit 8h + c: this lane reduces the slot of corner c of pixel h
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       if (h >= halves) break;
@@ -189,34 +193,34 @@ __global__ void __launch_bounds__(kAggThreads)
         if (lead[h] && (INTERIOR || in_grid(f[h][0] + cx, f[h][1] + cy, f[h][2] + cz, N))) {
           const int s = key[h] + (cx * dim[1] + cy) * dim[2] + cz;
           float2 b = box[s];
+          if (__float_as_uint(b.y) == 0u) own |= 1u << (8 * h + c);
           b.x += acc[c].x;
-          b.y += acc[c].y;
+          // negated sum with the sign bit forced, so a first term of +0 leaves -0
+          b.y = __uint_as_float(__float_as_uint(b.y - acc[c].y) | 0x80000000u);
           box[s] = b;
         }
         __syncwarp();
       }
     }
-    // flush in the same order: the first visit of a slot reduces and zeroes it
+    // each touched slot has exactly one owner: no ordering among the reductions
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       if (h >= halves) break;
 #pragma unroll
       for (int c = 0; c < 8; c++) {
-        const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
-        const int x = f[h][0] + cx, y = f[h][1] + cy, z = f[h][2] + cz;
-        if (lead[h] && (INTERIOR || in_grid(x, y, z, N))) {
+        if (own & (1u << (8 * h + c))) {
+          const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
           const int s = key[h] + (cx * dim[1] + cy) * dim[2] + cz;
           const float2 b = box[s];
-          if (b.x != 0.f || b.y != 0.f) {
-            const int64_t l = (int64_t)x * nn + (int64_t)y * N + z;
-            if (b.x != 0.f) atomicAdd(g_num + l, (double)b.x);
-            if (b.y != 0.f) atomicAdd(g_den + l, (double)b.y);
-            box[s] = make_float2(0.f, 0.f);
-          }
+          const int64_t l = (int64_t)(f[h][0] + cx) * nn + (int64_t)(f[h][1] + cy) * N +
+                            (f[h][2] + cz);
+          if (b.x != 0.f) atomicAdd(g_num + l, (double)b.x);
+          if (b.y != 0.f) atomicAdd(g_den + l, (double)(-b.y));
+          box[s] = make_float2(0.f, 0.f);
         }
-        __syncwarp();
       }
     }
+    __syncwarp();  // slots cleared before the next group's steps
   }
   // duplicate columns carrying counts above 256 (w = kDupMark) share their
   // pixel's geometry and add numerator only
