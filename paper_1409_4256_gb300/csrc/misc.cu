@@ -249,45 +249,67 @@ cudaError_t launch_gauss_scales(const float* grid, int64_t n_vox, unsigned* gmax
 // subtracted from their maxima before the merge. live (may be NULL): only row
 // tiles t with live[t * nnt + k / 256] were contracted (the others underflow);
 // best (may be NULL) receives the row tile of the largest maximum.
-__global__ void lse_merge_kernel(const double* __restrict__ part_m, const float* __restrict__ part_s,
-                                 int64_t n_tiles, int64_t ld_data, int64_t n_data,
-                                 double* __restrict__ lse_m, double* __restrict__ lse_s,
-                                 int accumulate, double clamp, const double* __restrict__ shift,
-                                 const uint8_t* __restrict__ live, int64_t nnt,
-                                 int32_t* __restrict__ best, int32_t* status) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_data) return;
-  double M = accumulate ? lse_m[k] : -INFINITY;
-  double S = accumulate ? lse_s[k] : 0.0;
-  const double sh = shift ? shift[k] : 0.0;
+__global__ void __launch_bounds__(256)
+    lse_merge_kernel(const double* __restrict__ part_m, const float* __restrict__ part_s,
+                     int64_t n_tiles, int64_t ld_data, int64_t n_data, double* __restrict__ lse_m,
+                     double* __restrict__ lse_s, int accumulate, double clamp,
+                     const double* __restrict__ shift, const uint8_t* __restrict__ live,
+                     int64_t nnt, int32_t* __restrict__ best, int32_t* status) {
+  // 32 frames (lanes) x 8 strides of tiles (warps); partials combined in stride order
+  __shared__ double rm[8][32], rs[8][32];
+  __shared__ int rb[8][32];
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int64_t k = (int64_t)blockIdx.x * 32 + lane;
+  const bool ok = k < n_data;
+  const double sh = (ok && shift) ? shift[k] : 0.0;
   const uint8_t* lv = live ? live + (k >> 8) : nullptr;
   double mt = -INFINITY;
   int tbest = 0;
-  for (int64_t t = 0; t < n_tiles; t++) {
-    if (lv && !lv[t * nnt]) continue;
-    const double m = part_m[t * ld_data + k] - sh;
-    if (m > mt) {
-      mt = m;
-      tbest = (int)t;
+  if (ok)
+    for (int64_t t = r; t < n_tiles; t += 8) {
+      if (lv && !lv[t * nnt]) continue;
+      const double m = part_m[t * ld_data + k] - sh;
+      if (m > mt) {
+        mt = m;
+        tbest = (int)t;
+      }
     }
-  }
+  rm[r][lane] = mt;
+  rb[r][lane] = tbest;
+  __syncthreads();
+  // the largest maximum; ties go to the lowest tile, as a scan in tile order would
+  mt = rm[0][lane];
+  tbest = rb[0][lane];
+  for (int q = 1; q < 8; q++)
+    if (rm[q][lane] > mt || (rm[q][lane] == mt && rb[q][lane] < tbest)) {
+      mt = rm[q][lane];
+      tbest = rb[q][lane];
+    }
+  const double M = (ok && accumulate) ? lse_m[k] : -INFINITY;
+  const double S = (ok && accumulate) ? lse_s[k] : 0.0;
+  const double Mn = fmax(M, mt);
+  // FP64 accumulation; the factors exp(m_t - Mn) <= 1 are taken in FP32 (relative
+  // error ~1e-6 for the terms that matter, |m_t - Mn| < 30) -- FP64 exp is rare on
+  // this part and the loop runs over every rotation tile
+  double acc = 0.0;
+  if (ok && Mn != -INFINITY)
+    for (int64_t t = r; t < n_tiles; t += 8) {
+      if (lv && !lv[t * nnt]) continue;
+      const double m = part_m[t * ld_data + k] - sh;
+      const float sv = part_s[t * ld_data + k];
+      if (sv > 0.f) acc += (double)(sv * __expf((float)(m - Mn)));
+    }
+  rs[r][lane] = acc;
+  __syncthreads();
+  if (r != 0 || !ok) return;
   if (best) best[k] = tbest;
-  double Mn = fmax(M, mt);
   if (Mn == -INFINITY) {  // nothing seen yet
     lse_m[k] = M;
     lse_s[k] = S;
     return;
   }
-  // FP64 accumulation; the factors exp(m_t - Mn) <= 1 are taken in FP32 (relative
-  // error ~1e-6 for the terms that matter, |m_t - Mn| < 30) -- FP64 exp is rare on
-  // this part and the loop runs over every rotation tile
-  double acc = (S > 0.0) ? S * exp(M - Mn) : 0.0;
-  for (int64_t t = 0; t < n_tiles; t++) {
-    if (lv && !lv[t * nnt]) continue;
-    double m = part_m[t * ld_data + k] - sh;
-    float sv = part_s[t * ld_data + k];
-    if (sv > 0.f) acc += (double)(sv * __expf((float)(m - Mn)));
-  }
+  acc = (S > 0.0) ? S * exp(M - Mn) : 0.0;
+  for (int q = 0; q < 8; q++) acc += rs[q][lane];
   // a best score at the clamp (Gaussian model) means every rotation was clamped
   if (!isfinite(Mn) || !(acc > 0.0) || !isfinite(acc) || Mn <= clamp)
     set_status(status, EMC_ERR_NUMERIC);
@@ -299,7 +321,7 @@ cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t 
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
                              int accumulate, int gauss, int32_t* status, cudaStream_t s,
                              const double* shift, const uint8_t* live, int32_t* best) {
-  unsigned blocks = (unsigned)((n_data + 255) / 256);
+  unsigned blocks = (unsigned)((n_data + 31) / 32);
   lse_merge_kernel<<<blocks, 256, 0, s>>>(part_m, part_s, n_tiles, ld_data, n_data, lse_m, lse_s,
                                           accumulate, gauss ? -(double)kGaussClamp : -INFINITY,
                                           shift, live, ld_data / 256, best, status);

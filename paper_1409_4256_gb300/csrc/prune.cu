@@ -25,24 +25,33 @@
 
 namespace emc {
 
-// One CTA per frame tile (256 frames, one per thread): the threshold of each
-// frame, then live[mt * nnt + nt] for every row tile.
+// One CTA per 32 frames (lanes) x 8 strides of row tiles (warps): the threshold
+// of each frame from the maxima over every row tile, then, for each row tile, a
+// ballot over the warp's 32 frames; a tile with a frame above its threshold sets
+// live[mt * nnt + nt] = 1 (live is zeroed first; eight CTAs share a frame tile).
 __global__ void __launch_bounds__(256)
     bound_live_kernel(const double* __restrict__ part_m, int64_t n_mtiles, int64_t ld_data,
                       int64_t n_data, const float* __restrict__ nsum, float div,
                       uint8_t* __restrict__ live) {
-  const int64_t nt = blockIdx.x, nnt = gridDim.x;
-  const int64_t s = nt * 256 + threadIdx.x;
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int64_t s = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t nnt = ld_data / 256;
+  const bool ok = s < n_data;
+  double M = -INFINITY;
+  if (ok)
+    for (int64_t mt = r; mt < n_mtiles; mt += 8) M = fmax(M, part_m[mt * ld_data + s]);
+  red[r][lane] = M;
+  __syncthreads();
   double thr = INFINITY;  // padding frames never make a tile live
-  if (s < n_data) {
-    double M = -INFINITY;
-    for (int64_t mt = 0; mt < n_mtiles; mt++) M = fmax(M, part_m[mt * ld_data + s]);
+  if (ok) {
+    M = red[0][lane];
+    for (int q = 1; q < 8; q++) M = fmax(M, red[q][lane]);
     thr = M - (2.0 * ((double)nsum[s] / (double)div + 1.0) + 111.0);
   }
-  for (int64_t mt = 0; mt < n_mtiles; mt++) {
-    const bool on = part_m[mt * ld_data + s] >= thr;
-    const int any = __syncthreads_or(on);
-    if (threadIdx.x == 0) live[mt * nnt + nt] = any ? 1 : 0;
+  for (int64_t mt = r; mt < n_mtiles; mt += 8) {
+    const bool on = ok && part_m[mt * ld_data + s] >= thr;
+    if (__any_sync(0xffffffffu, on) && lane == 0) live[mt * nnt + (s >> 8)] = 1;
   }
 }
 
@@ -181,8 +190,10 @@ __global__ void unpermute_lse_kernel(const int32_t* __restrict__ perm, int64_t n
 cudaError_t launch_bound_live(const double* part_m, int64_t n_mtiles, int64_t ld_data,
                               int64_t n_data, const float* nsum, float div, uint8_t* live,
                               cudaStream_t s) {
-  bound_live_kernel<<<(unsigned)(ld_data / 256), 256, 0, s>>>(part_m, n_mtiles, ld_data, n_data,
-                                                               nsum, div, live);
+  cudaError_t e = cudaMemsetAsync(live, 0, (size_t)n_mtiles * (ld_data / 256), s);
+  if (e != cudaSuccess) return e;
+  bound_live_kernel<<<(unsigned)(ld_data / 32), 256, 0, s>>>(part_m, n_mtiles, ld_data, n_data,
+                                                              nsum, div, live);
   return cudaGetLastError();
 }
 
