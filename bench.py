@@ -163,6 +163,22 @@ def peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def max_over_ranks(dist, x: float, device) -> float:
+    """The largest x over all ranks (x itself without a process group): the
+    slowest replica's time is the job's time."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, pairs_per_rank: int, ms: float) -> float:
+    """pairs/s of the whole job: every rank's pairs over the slowest rank's time."""
+    return world * pairs_per_rank / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
@@ -548,11 +564,8 @@ def run_ours(args):
         ms, phases, kernels, loglik = time_form(torch, emc, ctx, grid, args.steps, args.warmup,
                                                 stream, dist)
     clocks = clk.summary()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * pairs / (ms * 1e-3)
+    ms = max_over_ranks(dist, ms, dev)
+    value = whole_job_rate(world, pairs, ms)
 
     # ---- e2e: host frames in, new model out, through the public API ----------
     K_host = torch.as_tensor(ds.K).pin_memory()
@@ -571,12 +584,8 @@ def run_ours(args):
             out_host.copy_(out_dev, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
+    e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1) / e2e_steps, dev)
+    e2e = {"value": whole_job_rate(world, pairs, e2e_ms), "unit": "pairs/s",
            "h2d_bytes_per_step": int(ds.K.nbytes), "d2h_bytes_per_step": int(out_host.numel() * 4)}
 
     # ---- roofline of the dominant kernel ------------------------------------
