@@ -14,7 +14,7 @@
  * OpenMP only distributes independent outer iterations.
  *
  * Readings taken where the paper is silent (each listed in the design notes):
- *  - Poisson noise model (Sec. 2.2: "the signal is Poissonian"):
+ *  - Poisson noise model (Sec. 2.2, the original EMC's Poisson signal):
  *      log P(K_ik | W_ij) = K_ik log W_ij - W_ij - log K_ik!,
  *    the last term dropped (constant per frame, cancels in Eq. 2.4).
  *  - interpolation kernel f of Eq. 2.8 = trilinear (tent) weights;
