@@ -4,12 +4,11 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include <algorithm>
-#include <numeric>
 #include <vector>
 
 #include "emc_common.cuh"
 #include "emc_internal.h"
+#include "pixel_groups.h"
 
 using namespace emc;
 
@@ -330,31 +329,13 @@ int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, c
     qh[i] = a;
     ql[i] = b;
   }
-  // compression groups: a stable sort of the pixels by their cell of
-  // (q_x, q_y); a sheet of pixels crosses each cell in a small patch, whose
-  // trilinear corners the compression merges before reducing them into the grid
-  std::vector<int32_t> gord(cfg->n_pix), gstart;
+  // compression groups (pixel_groups.h) and their geometry in group order
+  std::vector<int32_t> gord, gstart;
+  build_pixel_groups(q, cfg->n_pix, kCompressCell, kCompressGroup, gord, gstart);
   std::vector<float4> gqh(cfg->n_pix + 1), gql(cfg->n_pix + 1);
-  {
-    std::vector<int64_t> key(cfg->n_pix);
-    for (int64_t i = 0; i < cfg->n_pix; i++) {
-      const int64_t cx = (int64_t)floor(q[3 * i] / kCompressCell) + 4096;
-      const int64_t cy = (int64_t)floor(q[3 * i + 1] / kCompressCell) + 4096;
-      key[i] = cy * 16384 + cx;
-    }
-    std::iota(gord.begin(), gord.end(), 0);
-    std::stable_sort(gord.begin(), gord.end(),
-                     [&](int32_t a, int32_t b) { return key[a] < key[b]; });
-    for (int64_t p = 0, run = 0; p < cfg->n_pix; p++) {
-      if (p == 0 || key[gord[p]] != key[gord[p - 1]] || run == kCompressGroup) {
-        gstart.push_back((int32_t)p);
-        run = 0;
-      }
-      run++;
-      gqh[p] = qh[gord[p]];
-      gql[p] = ql[gord[p]];
-    }
-    gstart.push_back((int32_t)cfg->n_pix);
+  for (int64_t p = 0; p < cfg->n_pix; p++) {
+    gqh[p] = qh[gord[p]];
+    gql[p] = ql[gord[p]];
   }
   std::vector<double> lw(cfg->n_rot);
   for (int64_t j = 0; j < cfg->n_rot; j++) lw[j] = log(weight[j]);
