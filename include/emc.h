@@ -46,7 +46,7 @@ typedef enum emc_status {
   EMC_OK = 0,
   EMC_ERR_ARG = -1,         /* bad argument, size or alignment */
   EMC_ERR_CUDA = -2,        /* a CUDA runtime call failed */
-  EMC_ERR_NOMEM = -3,       /* workspace too small */
+  EMC_ERR_NOMEM = -3,       /* workspace too small, or host memory for the staging ran out */
   EMC_ERR_UNSUPPORTED = -4, /* input outside what the kernels handle exactly */
   EMC_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
   EMC_ERR_NUMERIC = -6      /* non-finite or out-of-range value met on device */
@@ -214,7 +214,8 @@ const char* emc_status_string(int status);
  * for c = x, y, z, ties by round(q * 2^30) lexicographically) and prior
  * weights weight[cap] (host, sum 1; w_j ~ 1/|x_j|^4 for the flat lattice point
  * x_j, or equal weights when uniform != 0). Returns the count written, or a
- * negative emc_status (EMC_ERR_ARG if cap is too small). */
+ * negative emc_status (EMC_ERR_ARG if cap is too small, EMC_ERR_NOMEM if the
+ * host memory of the construction runs out). */
 int64_t emc_quat_count(int n);
 int64_t emc_quat_generate(int n, int uniform, double* quat, double* weight, int64_t cap);
 
@@ -229,7 +230,8 @@ int emc_workspace_size(const emc_config* cfg, size_t* bytes);
  * weight: host double[n_rot] prior weights w_j (> 0). workspace: device
  * memory of at least emc_workspace_size() bytes, 256-byte aligned, owned by
  * the caller and used until emc_ctx_destroy. Geometry and rotations are
- * copied into the workspace on `stream`. */
+ * staged in host memory and copied into the workspace on `stream`; if that
+ * host memory cannot be had, EMC_ERR_NOMEM and nothing is created. */
 int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat,
                    const double* weight, void* workspace, size_t workspace_bytes,
                    emc_stream stream, emc_ctx** out);

@@ -264,7 +264,11 @@ int64_t emc_quat_count(int n) {
 }
 
 int64_t emc_quat_generate(int n, int uniform, double* quat, double* weight, int64_t cap) {
-  return emc::quat_generate(n, uniform, quat, weight, cap);
+  try {  // no C++ exception crosses the C ABI
+    return emc::quat_generate(n, uniform, quat, weight, cap);
+  } catch (...) {
+    return EMC_ERR_NOMEM;
+  }
 }
 
 int emc_buffer_sizes_for(const emc_config* cfg, int64_t nrot, emc_buffer_sizes* out) {
@@ -294,8 +298,24 @@ int emc_workspace_size(const emc_config* cfg, size_t* bytes) {
   return EMC_OK;
 }
 
+static int ctx_create(const emc_config* cfg, const double* q, const double* quat,
+                      const double* weight, void* workspace, size_t workspace_bytes,
+                      emc_stream stream, emc_ctx** out);
+
 int emc_ctx_create(const emc_config* cfg, const double* q, const double* quat, const double* weight,
                    void* workspace, size_t workspace_bytes, emc_stream stream, emc_ctx** out) {
+  // the host staging vectors are all allocated before the context itself, so a
+  // failed allocation leaves nothing behind; no C++ exception crosses the C ABI
+  try {
+    return ctx_create(cfg, q, quat, weight, workspace, workspace_bytes, stream, out);
+  } catch (...) {
+    return EMC_ERR_NOMEM;
+  }
+}
+
+static int ctx_create(const emc_config* cfg, const double* q, const double* quat,
+                      const double* weight, void* workspace, size_t workspace_bytes,
+                      emc_stream stream, emc_ctx** out) {
   int st = check_config(cfg);
   if (st) return st;
   if (!q || !quat || !weight || !workspace || !out) return EMC_ERR_ARG;
