@@ -103,3 +103,32 @@ def test_single_rotation_mean_of_frames(oracle):
     out, lse, L = oracle.iteration(grid, np.array([[1.0, 0, 0, 0]]), np.array([1.0]), qi, K, 1e-12)
     ii = (qi + N / 2).astype(int)
     assert np.allclose(out[ii[:, 0], ii[:, 1], ii[:, 2]], K.mean(0), rtol=1e-13)
+
+
+def test_round_trip_error_is_second_order(oracle):
+    # Expansion followed by compression with unit weights (Eqs. 2.9, 2.12) is a
+    # smoothing operator: on a smooth field its error falls with the square of the
+    # field's length scale (trilinear interpolation is second order), so doubling
+    # a Gaussian blob's width divides it by 4. Speckles of about 2 voxels lose a
+    # quarter of their norm, which is where EMC's fixed point sits against the
+    # true intensity of the synthetic particles.
+    from paper_1409_4256_gb300 import synth
+    N = 32
+    q = synth.make_detector(N, N, 0.0).q
+    quat, _ = oracle.quat_generate(4)
+    ax = np.arange(N) - N // 2
+    r2 = ax[:, None, None] ** 2 + ax[None, :, None] ** 2 + ax[None, None, :] ** 2
+    inside = r2 <= (N / 2 - 1) ** 2
+
+    def round_trip_error(G):
+        W = oracle.expand(G, quat, q, 0.0)
+        out, _, _ = oracle.compress(N, quat, q, W, np.ones(quat.shape[0]), G)
+        return np.linalg.norm(out[inside] - G[inside]) / np.linalg.norm(G[inside])
+
+    e2 = round_trip_error(np.exp(-r2 / 8.0))    # sigma 2 voxels
+    e4 = round_trip_error(np.exp(-r2 / 32.0))   # sigma 4 voxels
+    assert 3.6 < e2 / e4 < 4.4
+    assert e4 < 0.02
+    atoms = synth.make_atoms(50, 8.0)
+    speckled = synth.intensity(synth.grid_points(N), atoms, N).reshape(N, N, N)
+    assert 0.2 < round_trip_error(speckled) < 0.3
