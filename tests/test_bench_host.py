@@ -4,6 +4,8 @@
   line with the contract's keys on rank 0, and nothing on the other ranks.
 * With N replicas the job's time is the slowest rank's: max_over_ranks under a
   two-rank gloo process group, and the whole-job rate from it.
+* The clock record: median SM clock, maximum clock and every throttle reason seen
+  in nvidia-smi's samples; "unsampled" where nvidia-smi is missing.
 """
 import json
 import os
@@ -84,3 +86,31 @@ def test_no_process_group_is_identity():
     import bench
     assert bench.max_over_ranks(None, 3.25, "cpu") == 3.25
     assert bench.whole_job_rate(1, 500, 2.0) == pytest.approx(250000.0)
+
+
+def test_clock_summary_parses_samples():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    # index, sm, max sm, power, active mask, hw, hw thermal, sw thermal, sw power cap
+    c.rows = [["0", "2070", "2070", "900.1", "0x0", "Not Active", "Not Active", "Not Active",
+               "Not Active"],
+              ["0", "1980", "2070", "1390.5", "0x4", "Not Active", "Not Active", "Not Active",
+               "Active"],
+              ["0", "2070", "2070", "1201.0", "0x0", "Not Active", "Not Active", "Not Active",
+               "Not Active"],
+              ["garbled line"]]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+    c.rows[0][6] = "Active"  # a thermal slowdown anywhere in the region is reported
+    assert bench.ClockSampler.summary(c)["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("PATH", "/nonexistent")
+    with bench.ClockSampler(0) as c:
+        pass
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
