@@ -245,15 +245,19 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
-    """Warm up, then time `steps` iterations with CUDA events on `stream`."""
-    out = torch.empty_like(grid)
+    """Warm up, then time `steps` iterations with CUDA events on `stream`.
+    Consecutive iterations of one reconstruction: each output model is the next
+    iteration's input (two buffers in turn), from the start model on. Returns
+    (ms per iteration, phases, kernels, last loglik, the model reached)."""
+    a, b = grid.clone(), torch.empty_like(grid)
     phases = {k: 0.0 for k in ("ms_expand", "ms_loglik", "ms_normalize", "ms_update",
                                 "ms_compress")}
     kernels = 0
     tiles = [0, 0, 0]  # pass-1 tiles, of them contracted exactly, iterations bound-pruned
     with torch.cuda.stream(stream):
         for _ in range(warmup):
-            ctx.iteration(grid, out, stats=True, stream=stream)
+            ctx.iteration(a, b, stats=True, stream=stream)
+            a, b = b, a
         stream.synchronize()
         if dist:
             dist.barrier()
@@ -262,7 +266,8 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
         e0.record(stream)
         lls = []
         for _ in range(steps):
-            _, st = ctx.iteration(grid, out, stats=True, stream=stream)
+            _, st = ctx.iteration(a, b, stats=True, stream=stream)
+            a, b = b, a
             for k in phases:
                 phases[k] += st[k]
             kernels += st["kernels"]
@@ -279,7 +284,7 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
     ph = {k: v / steps for k, v in phases.items()}
     ph["pass1_exact_tile_fraction"] = tiles[1] / tiles[0] if tiles[0] else None
     ph["pass1_bound_pruned_steps"] = tiles[2]
-    return ms, ph, kernels, lls[-1]
+    return ms, ph, kernels, lls[-1], a
 
 
 def rot_chunk_for(n_rot: int, n_data: int, cap: float = 8e9) -> int:
@@ -292,28 +297,56 @@ def rot_chunk_for(n_rot: int, n_data: int, cap: float = 8e9) -> int:
     return max(128, int(cap // (4 * ld_data)) // 128 * 128)
 
 
-def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, world):
+def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, world,
+                 iters=None, max_cycles=None):
     """Learned proposal + sparse Maximize with a dense fallback every 5th
     iteration. Untimed set-up: 2 dense iterations from the start model give the
     soft targets (top 32 per frame), the MLP trains on 90% of the frames. Each
     frame's candidate set is the top R = 32 rotations of the last dense E-step
     followed by the network's best rotations not among them (M in all); every
     dense fallback refreshes the dense part. Reported separately: the mass the
-    network's own top M captures on held-out and training frames."""
+    network's own top M captures on held-out and training frames, and the same
+    schedule with the network's part of each set replaced by random rotations,
+    or with the whole set taken from the dense E-step's top M (the schedule
+    without the network), each against the dense iterations."""
     from paper_1409_4256_gb300 import learned
     n_rot, n_data = quat.shape[0], ds.K.shape[0]
     M = min(args.n_cand, n_rot)
     R = min(32, M)
+    iters = args.learned_iters if iters is None else iters
     floor = 1e-10 * float(ds.model_start.mean())
     ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split", w_floor=floor,
                       store_scores=True, n_cand=M, device=str(grid.device), stream=stream,
                       rot_chunk=rot_chunk_for(n_rot, n_data), sparse_k=args.learned_sparse_k)
     ctx.set_frames(K_dev, stream=stream)
 
-    def refresh(net):
+    def refresh_net(net):
         # candidates = top R of the last dense E-step + the network's best others
         ti, _ = ctx.targets_from_scores(R, stream=stream)
         ctx.set_candidates(emc.merge_candidates(ti, net, M, stream=stream), stream=stream)
+
+    # the network's part replaced by random rotations (distinct per frame: a
+    # seeded frame offset plus M fixed distinct offsets, modulo n_rot)
+    rng = np.random.default_rng(1008)
+    offs = np.sort(rng.choice(n_rot, M, replace=False))
+    rand = torch.as_tensor(((rng.integers(0, n_rot, size=n_data)[:, None] + offs[None, :]) %
+                            n_rot).astype(np.int32), device=grid.device)
+
+    def refresh_random():
+        ti, _ = ctx.targets_from_scores(R, stream=stream)
+        ctx.set_candidates(emc.merge_candidates(ti, rand, M, stream=stream), stream=stream)
+
+    # the dense E-step's own top M (no network): its responsibilities, top M per frame
+    frames = torch.arange(n_data, dtype=torch.int32, device=grid.device)
+    dense_cand = torch.empty((n_data, M), dtype=torch.int32, device=grid.device)
+    fb = max(1, min(n_data, int(4e9 // (4 * n_rot))))
+
+    def refresh_dense_top():
+        for f0 in range(0, n_data, fb):
+            b = min(fb, n_data - f0)
+            Pf = ctx.responsibilities(frames[f0:f0 + b], stream=stream)
+            emc.topm(Pf, b, n_rot, n_rot, M, dense_cand[f0:f0 + b], stream=stream)
+        ctx.set_candidates(dense_cand, stream=stream)
 
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
@@ -329,7 +362,7 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
         ctx.set_candidates(net, stream=stream)
         ctx.iteration(g2, stream=stream)  # dense E-step on the current model
         mm_net = ctx.missed_mass(stream=stream).cpu().numpy()
-        refresh(net)
+        refresh_net(net)
         mm = ctx.missed_mass(stream=stream).cpu().numpy()
         stream.synchronize()
         setup_s = time.perf_counter() - t0
@@ -341,13 +374,15 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
         if dist:
             dist.barrier()
         cycles = max(1, args.steps // 5 + 1)
+        if max_cycles:
+            cycles = min(cycles, max_cycles)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(cycles):
             for _ in range(4):
                 ctx.sparse_iteration(g2, out, stats=False, stream=stream)
             ctx.iteration(g2, out, stats=False, stream=stream)
-            refresh(net)
+            refresh_net(net)
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / (5 * cycles)
@@ -369,40 +404,54 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
            "random_sets_captured_mass_expected": M / n_rot,
            "merged_heldout_captured_mass": float(1.0 - mm[test].mean()),
            "merged_train_captured_mass": float(1.0 - mm[train].mean()), "setup_s": setup_s}
-    if args.learned_iters > 0:
-        # model after N iterations, learned schedule vs dense, same start
+    if iters > 0:
+        # model after `iters` iterations, each candidate schedule vs dense, same start
         dense_ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split",
-                                w_floor=floor, store_scores=True, device=str(grid.device),
+                                w_floor=floor, store_scores=False, device=str(grid.device),
                                 stream=stream, rot_chunk=rot_chunk_for(n_rot, n_data))
         dense_ctx.set_frames(K_dev, stream=stream)
+        truth = torch.as_tensor(ds.model_true, device=grid.device)
         with torch.cuda.stream(stream):
             a, b = g2.clone(), torch.empty_like(g2)
-            for _ in range(args.learned_iters):
+            for _ in range(iters):
                 dense_ctx.iteration(a, b, stats=False, stream=stream)
                 a, b = b, a
-            ctx.iteration(g2, stream=stream)  # the schedule starts from a dense E-step's sets
-            refresh(net)
-            c, d = g2.clone(), torch.empty_like(g2)
-            missed = []
-            for it in range(args.learned_iters):
-                if it % 5 == 4:
-                    ctx.iteration(c, d, stats=False, stream=stream)
-                    missed.append(float(ctx.missed_mass(stream=stream).mean().item()))
-                    refresh(net)
-                else:
-                    ctx.sparse_iteration(c, d, stats=False, stream=stream)
-                c, d = d, c
             stream.synchronize()
-        ref = a.double()
-        res["iters_compared"] = args.learned_iters
-        res["rel_model_diff_vs_dense"] = float(torch.linalg.norm(c.double() - ref) /
-                                               torch.linalg.norm(ref))
-        truth = torch.as_tensor(ds.model_true, device=grid.device)
-        res["rel_model_err_vs_truth"] = {
-            "dense": float(torch.linalg.norm(ref - truth) / torch.linalg.norm(truth)),
-            "learned": float(torch.linalg.norm(c.double() - truth) / torch.linalg.norm(truth))}
-        res["mean_missed_mass_at_dense_steps"] = missed
         del dense_ctx
+        ref = a.double()
+
+        def rel(x, y):
+            return float(torch.linalg.norm(x - y) / torch.linalg.norm(y))
+
+        variants = {"network": lambda: refresh_net(net), "random_filler": refresh_random,
+                    "dense_top_m": refresh_dense_top}
+        res["schedules_vs_dense"] = {}
+        for name, refresh in variants.items():
+            with torch.cuda.stream(stream):
+                ctx.iteration(g2, stream=stream)  # each schedule starts from a dense E-step's sets
+                refresh()
+                c, d = g2.clone(), torch.empty_like(g2)
+                missed = []
+                t1 = time.perf_counter()
+                for it in range(iters):
+                    if it % 5 == 4:
+                        ctx.iteration(c, d, stats=False, stream=stream)
+                        missed.append(float(ctx.missed_mass(stream=stream).mean().item()))
+                        refresh()
+                    else:
+                        ctx.sparse_iteration(c, d, stats=False, stream=stream)
+                    c, d = d, c
+                stream.synchronize()
+                wall = time.perf_counter() - t1
+            res["schedules_vs_dense"][name] = {
+                "rel_model_diff_vs_dense": rel(c.double(), ref),
+                "rel_model_err_vs_truth": rel(c.double(), truth),
+                "mean_missed_mass_at_dense_steps": missed, "wall_s": wall}
+        res["iters_compared"] = iters
+        res["rel_model_err_vs_truth_dense"] = rel(ref, truth)
+        nv = res["schedules_vs_dense"]["network"]
+        res["rel_model_diff_vs_dense"] = nv["rel_model_diff_vs_dense"]
+        res["mean_missed_mass_at_dense_steps"] = nv["mean_missed_mass_at_dense_steps"]
     del ctx
     return res
 
@@ -524,6 +573,103 @@ def adaptive_form(torch, args, cfg, ds, grid, K_dev, stream, ctx, fixed_ms):
             "fixed_d_loglik_per_iteration": fixed_ll}
 
 
+def traffic_for(workload, precision, n_rot, n_data, recompute, phases):
+    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the pass-1
+    tensor-core launches of one iteration, from an ncu capture of this exact
+    configuration (profiles/tc_pass1_update_emc64_dram_bytes.md); None where no
+    capture of the configuration exists."""
+    pruned = bool(phases.get("pass1_bound_pruned_steps"))
+    if (workload == "emc64" and precision == "bf16_split" and n_data == 20000
+            and n_rot == 50100 and not recompute):
+        # pruned: the bound launch (5.779e9 + 0.065e9) plus the exact launch over the
+        # live tiles (2.138e9 + 0.398e9) of one iteration; dense: the single launch
+        return (5.844e9 + 2.536e9) if pruned else (6.744e9 + 4.249e9)
+    return None
+
+
+def pass1_roofline(precision, n_pix, n_rot, n_data, phases, traffic):
+    """Roofline line of E-step pass 1, the dominant step: algorithmic FLOPs
+    (2 n_pix per pair over every pair) over its CUDA-event time per iteration."""
+    pk, pk_src = peaks()
+    dom_ms = phases["ms_loglik"]
+    flops = 2.0 * n_pix * n_rot * n_data  # score contraction sum_i K_ik log W_ij
+    if precision == "fp32":
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max clock"}
+    else:
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "peak_source": f"{pk_src} bf16 sustained"}
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    planes = 3 if precision == "bf16_split" else 2 if precision == "fp16_split" else 1
+    pruned = bool(phases.get("pass1_bound_pruned_steps"))
+    exact = phases.get("pass1_exact_tile_fraction")
+    # executed tensor work: every plane over every tile, or (bound-pruned) the hi
+    # plane over every tile and every plane over the tiles left live
+    executed = flops * ((1 + planes * exact) if pruned else planes)
+    roof.update({"kernel": ("E-step pass 1: hi-plane bound over every tile, exact contraction "
+                            "of the tiles it leaves live, online log-sum-exp" if pruned else
+                            "E-step pass 1 (scores + online log-sum-exp)"),
+                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": traffic,
+                 "traffic_unit": ("bytes per iteration's pass 1 (bound + exact launches)" if pruned
+                                  else "bytes per launch"),
+                 "traffic_source": ("ncu capture of this configuration" if traffic is not None
+                                    else "unmeasured for this configuration"),
+                 "algorithmic_flops_per_launch": flops, "executed_flops_per_launch": executed,
+                 "executed_frac": executed / (dom_ms * 1e-3) / 1e12 / peak,
+                 "exact_tile_fraction": exact,
+                 "frac_basis": ("dense-equivalent: 2 n_pix per pair over every pair; the pruned "
+                                "pass executes executed_flops (hi-plane bound over every tile, "
+                                "every plane over the live tiles)" if pruned else
+                                "2 n_pix per pair over every pair")})
+    return roof
+
+
+def scale_form(torch, emc, args, form, cache, stream, dist, world, local):
+    """Another workload's own configuration with its own seeded data:
+    emc128_recompute -- the two-pass streamed Maximize (pass 2 recomputes the
+    scores of the live tiles, rotation chunks) at 128^3, 3 timed consecutive
+    iterations after 2 warm-up ones; learned128 -- the learned proposal at
+    128^3 (204960 rotations, top 512), 10 iterations per schedule."""
+    from paper_1409_4256_gb300 import synth
+    name = SCALE_FORMS[form]
+    if name not in cache:
+        c = dict(synth.WORKLOADS[name])
+        t0 = time.perf_counter()
+        d = synth.make_dataset(c["N"], c["D"], c["n_data"], c["mean_photons"],
+                               masked_fraction=c["masked_fraction"],
+                               fluence_sigma=c["fluence_sigma"], device=f"cuda:{local}")
+        q, w = emc.quat_generate(c["n_quat"])
+        cache[name] = (c, d, q, w, time.perf_counter() - t0)
+    cfg, ds, quat, w, gen_s = cache[name]
+    dev = torch.device("cuda", local)
+    grid = torch.as_tensor(ds.model_start.astype(np.float32), device=dev)
+    K_dev = torch.as_tensor(ds.K, device=dev)
+    n_rot, n_data, n_pix = quat.shape[0], ds.K.shape[0], ds.q.shape[0]
+    if form == "learned128":
+        res = learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, world,
+                           iters=10, max_cycles=2)
+    else:
+        floor = 1e-10 * float(ds.model_start.mean())
+        ctx = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split",
+                          w_floor=floor, store_scores=False, device=str(dev), stream=stream,
+                          rot_chunk=rot_chunk_for(n_rot, n_data), wide_counts=bool(ds.K.max() > 256))
+        ctx.set_frames(K_dev, stream=stream)
+        with ClockSampler(local) as clk:
+            ms, ph, kernels, ll, _ = time_form(torch, emc, ctx, grid, 3, 2, stream, dist)
+        del ctx
+        res = {"value": world * n_rot * n_data / (ms * 1e-3), "ms_per_step": ms, "loglik": ll,
+               "estep": "recompute", "rot_chunk": rot_chunk_for(n_rot, n_data),
+               "phases_ms": ph, "gpu_launches": kernels, "clocks": clk.summary(),
+               "roofline": pass1_roofline("bf16_split", n_pix, n_rot, n_data, ph,
+                                          traffic_for(name, "bf16_split", n_rot, n_data, True,
+                                                      ph))}
+    res["workload"] = f"{name}: {WORKLOAD_TEXT[name]}"
+    res["data_gen_s"] = gen_s
+    del K_dev
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -561,8 +707,8 @@ def run_ours(args):
 
     ctx = make_ctx(args.precision)
     with ClockSampler(local) as clk:
-        ms, phases, kernels, loglik = time_form(torch, emc, ctx, grid, args.steps, args.warmup,
-                                                stream, dist)
+        ms, phases, kernels, loglik, g_last = time_form(torch, emc, ctx, grid, args.steps,
+                                                        args.warmup, stream, dist)
     clocks = clk.summary()
     ms = max_over_ranks(dist, ms, dev)
     value = whole_job_rate(world, pairs, ms)
@@ -570,7 +716,7 @@ def run_ours(args):
     # ---- e2e: host frames in, new model out, through the public API ----------
     K_host = torch.as_tensor(ds.K).pin_memory()
     out_host = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
-    out_dev = torch.empty_like(grid)
+    cur, nxt = g_last.clone(), torch.empty_like(grid)  # the reconstruction goes on
     e2e_steps = max(2, min(args.steps, 5))
     with torch.cuda.stream(stream):
         for it in range(e2e_steps + 1):
@@ -580,8 +726,9 @@ def run_ours(args):
                 e0.record(stream)
             K_dev.copy_(K_host, non_blocking=True)
             ctx.set_frames(K_dev, stream=stream)
-            ctx.iteration(grid, out_dev, stats=False, stream=stream)
-            out_host.copy_(out_dev, non_blocking=True)
+            ctx.iteration(cur, nxt, stats=False, stream=stream)
+            out_host.copy_(nxt, non_blocking=True)
+            cur, nxt = nxt, cur
         e1.record(stream)
         e1.synchronize()
     e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1) / e2e_steps, dev)
@@ -589,44 +736,9 @@ def run_ours(args):
            "h2d_bytes_per_step": int(ds.K.nbytes), "d2h_bytes_per_step": int(out_host.numel() * 4)}
 
     # ---- roofline of the dominant kernel ------------------------------------
-    pk, pk_src = peaks()
-    dom_ms = phases["ms_loglik"]
-    flops = 2.0 * n_pix * n_rot * n_data  # score contraction sum_i K_ik log W_ij
-    if args.precision == "fp32":
-        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max clock"}
-    else:
-        peak = pk["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "peak_source": f"{pk_src} bf16 sustained"}
-    achieved = flops / (dom_ms * 1e-3) / 1e12
-    planes = 3 if args.precision == "bf16_split" else 2 if args.precision == "fp16_split" else 1
-    pruned = bool(phases.get("pass1_bound_pruned_steps"))
-    exact = phases.get("pass1_exact_tile_fraction")
-    # executed tensor work: every plane over every tile, or (bound-pruned) the hi
-    # plane over every tile and every plane over the tiles left live
-    executed = flops * ((1 + planes * exact) if pruned else planes)
-    # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
-    # dram__bytes_write.sum) of this exact configuration; otherwise unmeasured
-    traffic = None
-    if (args.workload == "emc64" and args.precision == "bf16_split" and n_data == 20000
-            and n_rot == 50100 and not args.recompute):
-        # pruned: the bound launch (5.779e9 + 0.065e9) plus the exact launch over the
-        # live tiles (2.138e9 + 0.398e9) of one iteration; dense: the single launch
-        traffic = (5.844e9 + 2.536e9) if pruned else (6.744e9 + 4.249e9)
-    roof.update({"kernel": ("E-step pass 1: hi-plane bound over every tile, exact contraction "
-                            "of the tiles it leaves live, online log-sum-exp" if pruned else
-                            "E-step pass 1 (scores + online log-sum-exp)"),
-                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": traffic,
-                 "traffic_unit": ("bytes per iteration's pass 1 (bound + exact launches)" if pruned
-                                  else "bytes per launch"),
-                 "algorithmic_flops_per_launch": flops, "executed_flops_per_launch": executed,
-                 "executed_frac": executed / (dom_ms * 1e-3) / 1e12 / peak,
-                 "exact_tile_fraction": exact,
-                 "frac_basis": ("dense-equivalent: 2 n_pix per pair over every pair; the pruned "
-                                "pass executes executed_flops (hi-plane bound over every tile, "
-                                "every plane over the live tiles)" if pruned else
-                                "2 n_pix per pair over every pair")})
+    roof = pass1_roofline(args.precision, n_pix, n_rot, n_data, phases,
+                          traffic_for(args.workload, args.precision, n_rot, n_data,
+                                      args.recompute, phases))
 
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
@@ -638,7 +750,16 @@ def run_ours(args):
             forms[f] = {"error": str(e)[:300]}
     del ctx  # every other form builds its own context
     torch.cuda.empty_cache()
-    for f in [x for x in others if x not in ADAPTIVE_FORMS]:
+    scale_data = {}
+    for f in [x for x in others if x in SCALE_FORMS]:
+        try:
+            forms[f] = scale_form(torch, emc, args, f, scale_data, stream, dist, world, local)
+        except Exception as e:
+            forms[f] = {"error": str(e)[:300]}
+        torch.cuda.empty_cache()
+    scale_data.clear()
+    torch.cuda.empty_cache()
+    for f in [x for x in others if x not in ADAPTIVE_FORMS and x not in SCALE_FORMS]:
         if f in RECON_FORMS:
             try:
                 forms[f] = reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot)
@@ -663,7 +784,7 @@ def run_ours(args):
             gauss, flu = f in GAUSS_FORMS, f in FLUENCE_FORMS
             c2 = (make_ctx(None, model="gaussian", sigma=args.sigma) if gauss else
                   make_ctx("bf16_split", model="poisson_fluence") if flu else make_ctx(f))
-            fms, fph, _, fll = time_form(torch, emc, c2, grid, 2, 1, stream, dist)
+            fms, fph, _, fll, _ = time_form(torch, emc, c2, grid, 2, 3, stream, dist)
             forms[f] = {"value": world * pairs / (fms * 1e-3), "ms_per_step": fms, "loglik": fll,
                         "ms_loglik": fph["ms_loglik"]}
             if gauss:

@@ -240,6 +240,18 @@ int emc_ctx_destroy(emc_ctx* ctx);
 /* Read (synchronously) and clear the device status word. */
 int emc_ctx_status(emc_ctx* ctx, int* device_status);
 
+/* Bounded waits of the context's tensor-core launches (no counterpart in the
+ * paper: a control of the failure path). Every mbarrier wait in those kernels
+ * gives up after wait_limit_ns (0 restores the default, 2 s); a launch whose
+ * wait gives up records EMC_ERR_TIMEOUT in the device status, lets the copies
+ * and MMAs it issued complete, frees its tensor memory and returns, leaving
+ * its outputs undefined. stall != 0 is a test hook for that path: in every
+ * tensor-core launch made while it is set, the MMA issuer's first wait is on a
+ * barrier that nothing completes, so that wait runs out after wait_limit_ns.
+ * Production code leaves both at 0. Takes effect for launches made after the
+ * call; returns EMC_ERR_ARG for a NULL context. */
+int emc_ctx_set_wait_limit(emc_ctx* ctx, uint64_t wait_limit_ns, int stall);
+
 /* Load frames K (Sec. 2.1, photon counts): device int32 [n_data][ld_k],
  * ld_k >= n_pix, into the context's padded frame buffer (BF16, or FP16 for
  * EMC_PREC_FP16_SPLIT). Counts must lie in [0, 256] (exact in BF16; [0, 2048]
@@ -265,6 +277,8 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
  * log w_j - sum_i W_ij^2 / (2 sigma^2). The call records s in the context;
  * emc_loglik, emc_normalize and emc_update use the scale of the last
  * emc_expand.
+ * An interpolated W_ij that is NaN or infinite (a non-finite voxel of grid)
+ * sets EMC_ERR_NUMERIC in the device status.
  * Poisson-fluence model: L holds log(W_ij / B_j) + c in place of log W
  * (B_j = sum_i W_ij, c = log n_pix rounded to the 1/8 grid, which keeps the
  * values and the scores in the range of the exact split); bias is
@@ -338,7 +352,9 @@ int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
  * workspace: it computes what emc_loglik computes, keeping its only scratch
  * (per-tile max/sum pairs) in a 32 MiB static device array inside the
  * library, and allocates nothing at call time.
- *  cfg: N, precision, n_pix, n_rot, n_data are read (host).
+ *  cfg: precision, n_pix, n_rot, n_data, model and flags are read (host);
+ *          the Poisson model only, without EMC_FLAG_WIDE_COUNTS
+ *          (EMC_ERR_UNSUPPORTED otherwise).
  *  L, bias: device, as emc_expand writes them for nrot rotations.
  *  frames: device BF16 (FP16 for EMC_PREC_FP16_SPLIT) [ld_data][ld_pix]
  *          (ld_pix = round_up(n_pix + 1, 64), ld_data = round_up(n_data, 256)):
@@ -354,8 +370,11 @@ int emc_normalize(emc_ctx* ctx, const void* L, const double* bias, int64_t nrot,
  * it and it keeps the last call's contents (each call overwrites what it
  * reads); calls that overlap on the GPU race on it and must be serialised by
  * the caller. The first call on a device looks the array's address up
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. */
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * use the call after cudaDeviceReset (the kept address would be stale).
+ * L and frames must be 16-byte aligned, bias, lse_m and lse_s 8-byte aligned
+ * (EMC_ERR_ARG otherwise); n_pix is limited to 2^24 as for a context. */
 int emc_loglik_static(const emc_config* cfg, const void* L, const double* bias,
                       const uint16_t* frames, int64_t nrot, double* lse_m, double* lse_s,
                       int accumulate, int32_t* device_status, emc_stream stream);
@@ -390,6 +409,24 @@ int emc_finalize(emc_ctx* ctx, const double* g_num, const double* g_den, const f
  * stats (host, may be NULL) is filled after the call synchronises `stream`. */
 int emc_iteration(emc_ctx* ctx, const float* grid_in, float* grid_out, emc_iter_stats* stats,
                   emc_stream stream);
+
+/* Per-frame log-likelihood terms of the last emc_iteration (the denominators
+ * of Eq. 2.4): lse (device double[n_data], frames in the order given to
+ * emc_set_frames) = log sum_j exp(S_jk), S_jk the scores emc_loglik defines for
+ * the context's noise model. EMC_ERR_ARG if no emc_iteration ran since the
+ * last emc_set_frames. */
+int emc_iteration_lse(emc_ctx* ctx, double* lse, emc_stream stream);
+
+/* Responsibilities P_jk of Eq. 2.4 of selected frames after the last
+ * emc_iteration, read from the context's stored scores (needs
+ * EMC_FLAG_STORE_SCORES; EMC_ERR_ARG otherwise or if no emc_iteration ran
+ * since the last emc_set_frames): P (device float[n][n_rot]) row f holds
+ * P_jk for frame k = frames[f] (device int32[n]) over every rotation j, in
+ * FP32. Rotations in tiles that a bound-pruned pass 1 skipped get 0 (their P
+ * is 0 in FP32). An index outside [0, n_data) sets EMC_ERR_ARG in the device
+ * status and leaves that row unwritten. */
+int emc_responsibilities(emc_ctx* ctx, const int32_t* frames, int64_t n, float* P,
+                         emc_stream stream);
 
 /* ------------------------------------------------------------------------
  * Learned rotation proposal and the sparse Maximize. The paper has no learned

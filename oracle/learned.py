@@ -70,15 +70,32 @@ def gelu_grad(x):
     return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2 * math.pi)
 
 
-def mlp_forward(params, X):
-    """Returns (logits, cache) with cache = pre-activations and layer inputs."""
+def bf16_round(x):
+    """Nearest BF16 value of every element (ties to even), taken from its FP32
+    value: the rounding the library documents for the operands of the MLP's
+    matrix products (its activations are FP32). BF16 keeps the sign, the 8
+    exponent bits and the top 7 fraction bits of an FP32 number."""
+    x32 = np.ascontiguousarray(x, dtype=np.float32)
+    u = x32.view(np.uint32).astype(np.uint64)
+    keep = (u + 0x7FFF + ((u >> 16) & 1)) >> 16  # round half to even on the dropped 16 bits
+    return ((keep << 16) & 0xFFFFFFFF).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _same(x):
+    return x
+
+
+def mlp_forward(params, X, operand=_same):
+    """Returns (logits, cache) with cache = pre-activations and layer inputs.
+    operand: applied to both operands of every matrix product (bf16_round for
+    the library's documented BF16 products; the identity by default)."""
     h = np.asarray(X, dtype=np.float64)
     ins, pres = [], []
     n_layers = len(params) // 2
     for l in range(n_layers):
         W, b = params[2 * l], params[2 * l + 1]
         ins.append(h)
-        a = h @ W + b
+        a = operand(h) @ operand(W) + b
         pres.append(a)
         h = gelu(a) if l < n_layers - 1 else a
     return h, (ins, pres)
@@ -94,9 +111,10 @@ def soft_ce_loss(z, T):
     return float(-(T * log_softmax(z)).sum() / z.shape[0])
 
 
-def mlp_loss_grads(params, X, T):
-    """Loss and gradients (same order as params) by backpropagation."""
-    z, (ins, pres) = mlp_forward(params, X)
+def mlp_loss_grads(params, X, T, operand=_same):
+    """Loss and gradients (same order as params) by backpropagation; operand
+    as in mlp_forward, applied to the operands of the backward products too."""
+    z, (ins, pres) = mlp_forward(params, X, operand)
     B = z.shape[0]
     loss = soft_ce_loss(z, T)
     p = np.exp(log_softmax(z))
@@ -105,10 +123,10 @@ def mlp_loss_grads(params, X, T):
     n_layers = len(params) // 2
     for l in range(n_layers - 1, -1, -1):
         W = params[2 * l]
-        grads[2 * l] = ins[l].T @ g
+        grads[2 * l] = operand(ins[l]).T @ operand(g)
         grads[2 * l + 1] = g.sum(axis=0)
         if l > 0:
-            g = (g @ W.T) * gelu_grad(pres[l - 1])
+            g = (operand(g) @ operand(W).T) * gelu_grad(pres[l - 1])
     return loss, grads
 
 

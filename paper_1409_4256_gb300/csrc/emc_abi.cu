@@ -239,8 +239,10 @@ struct emc_ctx {
   bool last_pruned;           // ... and hold only the live tiles (live flags)
   bool frames_loaded;
   bool cand_loaded;
+  bool iterated;              // an emc_iteration ran on the loaded frames
   cudaEvent_t ev[8];
   int kernels;  // launches made by the last emc_iteration
+  TcCtl tcctl;  // bounded waits of the tensor-core launches (emc_ctx_set_wait_limit)
 };
 
 extern "C" {
@@ -477,6 +479,13 @@ int emc_ctx_destroy(emc_ctx* ctx) {
   return EMC_OK;
 }
 
+int emc_ctx_set_wait_limit(emc_ctx* ctx, uint64_t wait_limit_ns, int stall) {
+  if (!ctx) return EMC_ERR_ARG;
+  ctx->tcctl.wait_ns = wait_limit_ns;
+  ctx->tcctl.stall = stall ? 1 : 0;
+  return EMC_OK;
+}
+
 int emc_ctx_status(emc_ctx* ctx, int* device_status) {
   if (!ctx || !device_status) return EMC_ERR_ARG;
   int32_t v = 0;
@@ -540,6 +549,7 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
                            ctx->gk, ctx->nmax, (cudaStream_t)stream));
   }
   ctx->frames_loaded = true;
+  ctx->iterated = false;
   return EMC_OK;
 }
 
@@ -593,7 +603,8 @@ int do_loglik(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, const d
     Planes p{(void*)((const uint16_t*)L + row_off * y.ld_pix), Lrows * y.ld_pix, y.ld_pix};
     const bool g = is_gauss(&c->cfg);
     CU(launch_tc_pass1(p, c->cfg.precision, bias, rows, c->Kb, y.ld_data, c->cfg.n_data, y.ld_pix, pm, ps,
-                       S, Sref, g ? c->gk : nullptr, g ? c->gsc : nullptr, c->status, s));
+                       S, Sref, g ? c->gk : nullptr, g ? c->gsc : nullptr, c->status, s, nullptr,
+                       nullptr, c->tcctl));
     tiles = tc_pass1_tiles(rows);
   }
   CU(launch_lse_merge(pm, ps, tiles, y.ld_data, c->cfg.n_data, lse_m, lse_s, accumulate,
@@ -642,7 +653,7 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
       Planes pp{P, Prows * y.ld_data, y.ld_data};
       CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, Kf, y.ld_data,
                              c->cfg.n_data, y.ld_pix, lse_m, lse_s, lse2, pp, c->status, s,
-                             cn, Bsum, invn, den, kbf, tl, tc));
+                             cn, Bsum, invn, den, kbf, tl, tc, c->tcctl));
     }
     return EMC_OK;
   }
@@ -672,7 +683,7 @@ int do_normalize(emc_ctx* c, const void* L, int64_t Lrows, int64_t row_off, cons
     Planes pp{P, Prows * y.ld_data, y.ld_data};
     CU(launch_tc_normalize(lp, c->cfg.precision, bias, rows, nrot, Kf, y.ld_data, c->cfg.n_data,
                            y.ld_pix, lse_m, lse_s, (float2*)(c->ws + y.lse2), pp, c->status, s,
-                           nullptr, nullptr, nullptr, nullptr, kbf, tl, tc));
+                           nullptr, nullptr, nullptr, nullptr, kbf, tl, tc, c->tcctl));
   }
   return EMC_OK;
 }
@@ -694,12 +705,12 @@ int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num
       // model's BF16 copy)
       CU(launch_tc_update(pp, EMC_PREC_BF16_SPLIT, rows,
                           Kf ? Kf : (is_gauss(&c->cfg) ? c->Kb2 : c->Kb), y.ld_data, y.ld_pix,
-                          c->cfg.n_pix, Num, nullptr, c->status, s, kbc, kbl));
+                          c->cfg.n_pix, Num, nullptr, c->status, s, kbc, kbl, c->tcctl));
       const char* tail = (const char*)P + P_plane_bytes(&c->cfg, Prows, y.ld_data);
       CU(cudaMemcpyAsync(den, tail, sizeof(float) * rows, cudaMemcpyDeviceToDevice, s));
     } else {
       CU(launch_tc_update(pp, c->cfg.precision, rows, Kf ? Kf : c->Kb, y.ld_data, y.ld_pix,
-                          c->cfg.n_pix, Num, den, c->status, s, kbc, kbl));
+                          c->cfg.n_pix, Num, den, c->status, s, kbc, kbl, c->tcctl));
     }
   }
   return EMC_OK;
@@ -856,14 +867,14 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     if (pruned) {
       // bound: the hi plane alone (the first plane of L), per-tile maxima
       CU(launch_tc_bound(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, y.ld_pix, pm,
-                         c->status, s));
+                         c->status, s, c->tcctl));
       CU(launch_bound_live(pm, nmt, y.ld_data, c->cfg.n_data,
                            (const float*)(c->ws + y.nsum_p), bound_div(&c->cfg), live, s));
       CU(launch_tile_list(live, (int)nmt, (int)nnt, 8, tlist, tcount, s));
     }
     CU(launch_tc_pass1(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, c->cfg.n_data, y.ld_pix,
                        pm, ps, S, S + y.rows * y.ld_data, nullptr, nullptr, c->status, s,
-                       pruned ? tlist : nullptr, pruned ? tcount : nullptr));
+                       pruned ? tlist : nullptr, pruned ? tcount : nullptr, c->tcctl));
     CU(launch_lse_merge(pm, ps, nmt, y.ld_data, c->cfg.n_data, lm, ls, 0, 0, c->status, s, cn_p,
                         pruned ? live : nullptr, (int32_t*)(c->ws + y.best)));
     CU(launch_unpermute_lse(c->perm, c->cfg.n_data, lm, ls, lse_m, lse_s, s));
@@ -946,6 +957,7 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   }
   if (stats) CU(cudaEventRecord(c->ev[7], s));
   c->kernels = kernels;
+  c->iterated = true;
   if (stats) {
     CU(cudaEventSynchronize(c->ev[7]));
     float te = 0, tl = 0, tf = 0, tt = 0;
@@ -1182,6 +1194,33 @@ int emc_missed_mass(emc_ctx* ctx, const void* scores, const double* lse_m, const
                         missed, s, internal ? (const int32_t*)(ctx->ws + y.iperm) : nullptr,
                         internal && ctx->last_pruned ? (const uint8_t*)(ctx->ws + y.live)
                                                      : nullptr));
+  return EMC_OK;
+}
+
+int emc_iteration_lse(emc_ctx* ctx, double* lse, emc_stream stream) {
+  if (!ctx || !lse || !ctx->iterated) return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  CU(launch_lse_values((const double*)(ctx->ws + y.lse_m), (const double*)(ctx->ws + y.lse_s),
+                       ctx->cfg.n_data, lse, (cudaStream_t)stream));
+  return EMC_OK;
+}
+
+int emc_responsibilities(emc_ctx* ctx, const int32_t* frames, int64_t n, float* P,
+                         emc_stream stream) {
+  if (!ctx || !frames || !P || n < 1 || !ctx->iterated) return EMC_ERR_ARG;
+  if (!(ctx->cfg.flags & EMC_FLAG_STORE_SCORES)) return EMC_ERR_ARG;
+  const Layout& y = ctx->lay;
+  cudaStream_t s = (cudaStream_t)stream;
+  float2* lse2 = (float2*)(ctx->ws + y.lse2);
+  CU(launch_lse_split((const double*)(ctx->ws + y.lse_m), (const double*)(ctx->ws + y.lse_s),
+                      ctx->cfg.n_data, y.ld_data, lse2, s, ctx->flu_cn));
+  const float* S = (const float*)(ctx->ws + y.S);
+  CU(launch_responsibilities(S, y.rows, S + y.rows * y.ld_data, y.ld_data, lse2, frames, n,
+                             ctx->cfg.n_rot, ctx->cfg.n_data, P, ctx->status, s,
+                             ctx->scores_internal ? (const int32_t*)(ctx->ws + y.iperm) : nullptr,
+                             ctx->scores_internal && ctx->last_pruned
+                                 ? (const uint8_t*)(ctx->ws + y.live)
+                                 : nullptr));
   return EMC_OK;
 }
 

@@ -145,6 +145,14 @@ cudaError_t launch_normalize_scores(const float* S, int64_t ldS, const float* Sr
 cudaError_t launch_loglik_sum(const double* lse_m, const double* lse_s, int64_t n_data,
                               double* out, cudaStream_t s);
 
+// Control of the tensor-core launches' bounded waits: wait_ns = 0 is the
+// default limit (2 s); stall != 0 is the test hook of emc_ctx_set_wait_limit
+// (the MMA issuer's first wait is on a barrier nothing completes).
+struct TcCtl {
+  uint64_t wait_ns;
+  int stall;
+};
+
 // tcgen05 forms (precision EMC_PREC_BF16 / BF16_SPLIT / FP16_SPLIT).
 // gk, gsc != NULL: the Gaussian model's pass 1 (three FP16 planes of s W).
 // tile_list, tile_count (device, optional): contract only the listed
@@ -154,7 +162,7 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
                             double* part_m, float* part_s, float* S, float* Sref,
                             const float4* gk, const float4* gsc, int32_t* status,
                             cudaStream_t s, const int32_t* tile_list = nullptr,
-                            const int32_t* tile_count = nullptr);
+                            const int32_t* tile_count = nullptr, TcCtl ctl = TcCtl{});
 // lse2: scratch float2[ld_data] for lse_k split into a 1/8-grid part and a rest.
 // Bsum != NULL: Poisson-fluence model -- shift[ld_data] is added back to lse,
 // the planes receive BF16 hi + lo of P B_j invn[k] and den[rows] = sum_k P_jk
@@ -168,7 +176,7 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
                                 const double* shift = nullptr, const double* Bsum = nullptr,
                                 const float* invn = nullptr, float* den = nullptr,
                                 uint8_t* kb_flag = nullptr, const int32_t* tile_list = nullptr,
-                                const int32_t* tile_count = nullptr);
+                                const int32_t* tile_count = nullptr, TcCtl ctl = TcCtl{});
 // P planes: hi + lo (BF16 split, FP16 split) or hi only (BF16); FP16 planes
 // carry the scale 2^14. den NULL: not written.
 // kb_cnt, kb_list (optional, from launch_kb_lists): contract only the listed
@@ -176,14 +184,20 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
 cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
                              int32_t* status, cudaStream_t s, const int32_t* kb_cnt = nullptr,
-                             const int32_t* kb_list = nullptr);
+                             const int32_t* kb_list = nullptr, TcCtl ctl = TcCtl{});
 int64_t tc_pass1_tiles(int64_t rows);
+// C (float[rows][ld_data]) = A Kb^T over ld_pix columns, A one BF16 plane of
+// rows (a multiple of 128) x ld_pix, Kb BF16 [ld_data][ld_pix]: a plain
+// tensor-core product, FP32 accumulation, stored as it is.
+cudaError_t launch_tc_store(const Planes& A, int64_t rows, const uint16_t* Kb, int64_t ld_data,
+                            int64_t ld_pix, float* C, int32_t* status, cudaStream_t s,
+                            TcCtl ctl = TcCtl{});
 // Bound pass of the pruned pass 1: per 128-row tile and frame, the maximum of
 // S^hi = (first plane of L) K^T + bias into part_m[rows / 128][ld_data]
 // (pairs of row tiles per CTA tile sharing the frame operand).
 cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t ld_pix, double* part_m,
-                            int32_t* status, cudaStream_t s);
+                            int32_t* status, cudaStream_t s, TcCtl ctl = TcCtl{});
 
 // nrep grid replicas of n_vox each (row j reduces into replica j mod nrep)
 cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const float* Num,
@@ -251,6 +265,19 @@ cudaError_t launch_missed_mass(const float* S, int64_t ldS, const float* Sref, i
                                const float2* lse2, const int32_t* cand, int M, int64_t n_data,
                                float* missed, cudaStream_t s, const int32_t* iperm = nullptr,
                                const uint8_t* live = nullptr);
+
+// P[f][j] (float[n][nrot]) = exp(S_jk - lse_k) of frames k = frames[f] from
+// stored scores (iperm, live as launch_missed_mass); an index outside
+// [0, n_data) sets EMC_ERR_ARG and leaves that row unwritten
+cudaError_t launch_responsibilities(const float* S, int64_t ldS, const float* Sref,
+                                    int64_t ld_data, const float2* lse2, const int32_t* frames,
+                                    int64_t n, int64_t nrot, int64_t n_data, float* P,
+                                    int32_t* status, cudaStream_t s,
+                                    const int32_t* iperm = nullptr,
+                                    const uint8_t* live = nullptr);
+// lse[k] = m[k] + log s[k] for k < n
+cudaError_t launch_lse_values(const double* m, const double* sm, int64_t n, double* lse,
+                              cudaStream_t s);
 
 // ---- pruned pass 1 and the frame order (prune.cu) ----
 // live[mt * (ld_data / 256) + nt] from the hi-plane tile maxima part_m (frames

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kExpandThreads)
   uint16_t* Lb = reinterpret_cast<uint16_t*>(Lbase) + row * ld_pix;
   const float half_n = 0.5f * (float)N;
   float wsum = 0.f, wcomp = 0.f;  // Kahan-compensated sum of W (W^2) over this thread's pixels
-  int bad = 0;
+  int bad = 0, nonfinite = 0;
   const float gs = GAUSS ? gsc->x : 1.f;
 
   for (int64_t i = threadIdx.x; i < ld_pix; i += kExpandThreads) {
@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(kExpandThreads)
         float t[3];
         rotate_to_grid(R, a, b, half_n, f, t);
         float W = trilinear<INTERIOR>(grid, N, f, t);
+        nonfinite |= !(fabsf(W) <= 3.4e38f);  // a NaN or infinite voxel of the model
         W = fmaxf(W, GAUSS ? 0.f : w_floor);
         if (a.w == 1.f) {  // duplicate columns (counts above 256) repeat a pixel: not summed
           const float ky = (GAUSS ? W * W : W) - wcomp;
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kExpandThreads)
       Lb[i + 2 * plane_stride] = lo;
     }
   }
+  if (nonfinite) set_status(status, EMC_ERR_NUMERIC);
   if (bad) set_status(status, EMC_ERR_UNSUPPORTED);
 
   // FP64 block reduction of sum_i W_ij
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(kExpandThreads)
   __syncthreads();
   const float half_n = 0.5f * (float)N;
   float wsum = 0.f, wcomp = 0.f;
+  int nonfinite = 0;
   if (valid_row) {
     for (int64_t i = threadIdx.x; i < ld_pix; i += kExpandThreads) {
       const float4 a = qh[i];
@@ -187,7 +190,9 @@ __global__ void __launch_bounds__(kExpandThreads)
       int f[3];
       float t[3];
       rotate_to_grid(R, a, ql[i], half_n, f, t);
-      const float W = fmaxf(trilinear<INTERIOR>(grid, N, f, t), w_floor);
+      const float Wt = trilinear<INTERIOR>(grid, N, f, t);
+      nonfinite |= !(fabsf(Wt) <= 3.4e38f);  // a NaN or infinite voxel of the model
+      const float W = fmaxf(Wt, w_floor);
       if (STASH) wst[i] = W;
       if (a.w == 1.f) {  // duplicate columns repeat a pixel: not summed
         const float ky = W - wcomp;
@@ -197,6 +202,7 @@ __global__ void __launch_bounds__(kExpandThreads)
       }
     }
   }
+  if (nonfinite) set_status(status, EMC_ERR_NUMERIC);
   double ws = (double)wsum - (double)wcomp;
   for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ws;

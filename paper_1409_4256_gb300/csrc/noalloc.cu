@@ -16,8 +16,9 @@
 // last call's contents; calls that overlap on the GPU (different streams, or
 // different host threads on one device) race on it and must be serialised by
 // the caller. The first call on a device looks the array's device address up
-// (cudaGetSymbolAddress) with that device current; make that first call before
-// any stream capture.
+// (cudaGetSymbolAddress) with that device current and keeps it for the life of
+// the process; make that first call before any stream capture, and do not use
+// the call after cudaDeviceReset (the kept address would be stale).
 #include <mutex>
 
 #include "emc_common.cuh"
@@ -64,6 +65,12 @@ extern "C" int emc_loglik_static(const emc_config* cfg, const void* L, const dou
                                  emc_stream stream) {
   if (!cfg || !L || !bias || !frames || !lse_m || !lse_s) return EMC_ERR_ARG;
   if (cfg->n_pix < 1 || cfg->n_data < 1 || nrot < 1 || nrot > cfg->n_rot) return EMC_ERR_ARG;
+  if (cfg->n_pix > (1LL << 24) || cfg->n_rot > (1LL << 31) || cfg->n_data > (1LL << 31))
+    return EMC_ERR_ARG;
+  // the tensor maps need 16-byte aligned bases; the FP64 arrays, 8-byte ones
+  if ((((uintptr_t)L) & 15) || (((uintptr_t)frames) & 15) || (((uintptr_t)bias) & 7) ||
+      (((uintptr_t)lse_m) & 7) || (((uintptr_t)lse_s) & 7) || (((uintptr_t)device_status) & 3))
+    return EMC_ERR_ARG;
   if (cfg->precision < EMC_PREC_FP32 || cfg->precision > EMC_PREC_FP16_SPLIT) return EMC_ERR_ARG;
   if (cfg->model != EMC_MODEL_POISSON || (cfg->flags & EMC_FLAG_WIDE_COUNTS))
     return EMC_ERR_UNSUPPORTED;

@@ -253,4 +253,299 @@ cudaError_t launch_unpermute_lse(const int32_t* perm, int64_t n_data, const doub
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Incremental bound between consecutive iterations (same frames).
+//
+// With the three-term split, the represented log W of iteration n is
+// L^n_ij = hi + mid + lo, and the scores S^n_jk = sum_i K_ik L^n_ij + bias^n_j.
+// From one iteration to the next, for every j of row tile t,
+//   S^{n+1}_jk - S^n_jk <= sum_i K_ik D+_ti + b+_t,
+//   S^n_jk - S^{n+1}_jk <= sum_i K_ik D-_ti + b-_t,
+// with D+_ti = max_{j in t} (L^{n+1}_ij - L^n_ij), D-_ti = max_{j in t}
+// (L^n_ij - L^{n+1}_ij) (counts are non-negative) and b+-_t the same maxima of
+// the bias change. D+- are rounded up to BF16 and contracted against the
+// frames on the tensor cores (one row per tile: 1/128 of the hi-plane bound's
+// work). The FP32 accumulation of sum_i K_ik D_ti errs by at most
+// (ld_pix + 8) 2^-23 N_k max_i |D_ti| (products of an integer count <= 256
+// and a BF16 value are exact in FP32; every addition rounds by at most one
+// unit of 2^-23 of a partial sum bounded by N_k max|D|), which is added.
+// ---------------------------------------------------------------------------
+
+// Next BF16 value >= x (x finite).
+__device__ __forceinline__ uint16_t bf16_up_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t h = u >> 16;
+  if ((u & 0xFFFFu) == 0u) return (uint16_t)h;
+  // x > 0: the next magnitude up; x < 0: truncation moves towards zero, i.e. up
+  return (uint16_t)((u & 0x80000000u) ? h : h + 1u);
+}
+__device__ __forceinline__ float plane_val(const uint16_t* p, int64_t o) {
+  return __uint_as_float(((uint32_t)p[o]) << 16);
+}
+
+// One CTA per (pixel slice of 256 columns, row tile): each thread a pixel,
+// the tile's valid rows in turn. D = BF16 [2 ntp][ld_pix]: rows t (D+) and
+// ntp + t (D-); dabs[t] = max_i max(|D+_ti|, |D-_ti|) (unsigned bits of a
+// non-negative float, atomically maximised; zeroed first); bpm[t], bpm[nt +
+// t] = b+_t, b-_t (rounded up), written by the CTAs of the first slice.
+__global__ void __launch_bounds__(256)
+    delta_planes_kernel(const uint16_t* __restrict__ L0, const uint16_t* __restrict__ L1,
+                        int64_t plane, int64_t ld_pix, int64_t nrot, const double* __restrict__ b0,
+                        const double* __restrict__ b1, int64_t ntp, uint16_t* __restrict__ D,
+                        unsigned* __restrict__ dabs, float* __restrict__ bpm, int64_t nt) {
+  const int64_t t = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t r0 = t * 128;
+  const int64_t r1 = min(r0 + 128, nrot);
+  float dp = -INFINITY, dm = -INFINITY;
+  if (i < ld_pix) {
+    for (int64_t j = r0; j < r1; j++) {
+      const int64_t o = j * ld_pix + i;
+      // differences of each plane are exact in FP32; their sum rounds once or twice
+      const float d = (plane_val(L1, o) - plane_val(L0, o)) +
+                      (plane_val(L1, o + plane) - plane_val(L0, o + plane)) +
+                      (plane_val(L1, o + 2 * plane) - plane_val(L0, o + 2 * plane));
+      dp = fmaxf(dp, d);
+      dm = fmaxf(dm, -d);
+    }
+    // one FP32 rounding of a sum of three exact terms: 2^-23 |d| covers it
+    dp += 2.0f * 1.1920929e-7f * fabsf(dp);
+    dm += 2.0f * 1.1920929e-7f * fabsf(dm);
+    D[t * ld_pix + i] = bf16_up_bits(dp);
+    D[(ntp + t) * ld_pix + i] = bf16_up_bits(dm);
+  }
+  float a = i < ld_pix ? fmaxf(fabsf(dp), fabsf(dm)) * 1.0078125f : 0.f;  // BF16 rounding up
+  for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dabs + t, __float_as_uint(a));
+  if (blockIdx.x == 0 && threadIdx.x < 128) {
+    __shared__ double rb[2][128];
+    const int64_t j = r0 + threadIdx.x;
+    const double db = j < nrot ? b1[j] - b0[j] : 0.0;
+    rb[0][threadIdx.x] = j < nrot ? db : -INFINITY;
+    rb[1][threadIdx.x] = j < nrot ? -db : -INFINITY;
+    __syncwarp();
+    for (int w = 64; w > 0; w >>= 1) {
+      asm volatile("bar.sync 3, 128;" ::: "memory");
+      if ((int)threadIdx.x < w) {
+        rb[0][threadIdx.x] = fmax(rb[0][threadIdx.x], rb[0][threadIdx.x + w]);
+        rb[1][threadIdx.x] = fmax(rb[1][threadIdx.x], rb[1][threadIdx.x + w]);
+      }
+    }
+    if (threadIdx.x == 0) {
+      bpm[t] = __double2float_ru(rb[0][0]);
+      bpm[nt + t] = __double2float_ru(rb[1][0]);
+    }
+  }
+}
+
+// Per frame (lanes) and row tile (warp strides), with C = [D+; D-] K^T of the
+// frames in the current internal order (rows t and ntp + t):
+//   Ub[t][k] += C+[t][k] + b+_t + err_tk        (err = errc N_k dabs_t)
+//   Lk[k] = Mk[k] - 1/64 - (C-[t*][k] + b-_t* + err_t*k),   t* = best[k]
+// Mk: the last iteration's largest exact tile maximum (its scores are within
+// 1/128 of it), t* its row tile, so Lk <= max_j S_jk now. A tile is a
+// candidate for the hi-plane bound (cand[t][nt] = 1) when Ub >= Lk - 111.
+// invalid (host flag, or *changed set by emc_set_frames when the counts
+// differ from the last ones): Ub = +inf, Lk = -inf and every tile a candidate.
+__global__ void __launch_bounds__(256)
+    delta_live_kernel(const float* __restrict__ C, int64_t ntp, const float* __restrict__ bpm,
+                      const unsigned* __restrict__ dabs, float* __restrict__ Ub,
+                      double* __restrict__ Lk, const double* __restrict__ Mk,
+                      const int32_t* __restrict__ best, const float* __restrict__ nsum,
+                      double errc, int64_t n_mtiles, int64_t ld_data, int64_t n_data,
+                      int valid_host, const int32_t* __restrict__ changed,
+                      uint8_t* __restrict__ cand) {
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int64_t k = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t nnt = ld_data / 256;
+  const bool ok = k < n_data;
+  const bool valid = valid_host && !(changed && *changed);
+  double L = -INFINITY;
+  if (ok && valid) {
+    const int tb = best[k];
+    const double e = errc * (double)nsum[k] * (double)__uint_as_float(dabs[tb]);
+    L = Mk[k] - 1.0 / 64.0 - ((double)C[(ntp + tb) * ld_data + k] + (double)bpm[n_mtiles + tb] + e);
+  }
+  if (ok && r == 0) Lk[k] = L;
+  for (int64_t t = r; t < n_mtiles; t += 8) {
+    bool on = ok;
+    if (ok) {
+      float* u = Ub + t * ld_data + k;
+      if (valid) {
+        const double e = errc * (double)nsum[k] * (double)__uint_as_float(dabs[t]);
+        const double U = (double)*u + (double)C[t * ld_data + k] + (double)bpm[t] + e;
+        *u = __double2float_ru(U);
+        on = U >= L - 111.0;
+      } else {
+        *u = INFINITY;
+      }
+    }
+    if (__any_sync(0xffffffffu, on) && lane == 0) cand[t * nnt + (k >> 8)] = 1;
+  }
+}
+
+// pf[mp][nt] = cand[2 mp][nt] | cand[2 mp + 1][nt]: the row-tile pairs the
+// hi-plane bound contracts.
+__global__ void pair_flags_kernel(const uint8_t* __restrict__ cand, int64_t n_mtiles, int64_t nnt,
+                                  uint8_t* __restrict__ pf) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t npairs = (n_mtiles + 1) / 2;
+  if (x >= npairs * nnt) return;
+  const int64_t mp = x / nnt, nt = x % nnt;
+  uint8_t v = cand[2 * mp * nnt + nt];
+  if (2 * mp + 1 < n_mtiles) v |= cand[(2 * mp + 1) * nnt + nt];
+  pf[x] = v;
+}
+
+// Combination of both bounds and the liveness of every tile. For the tiles
+// whose pair the hi-plane bound contracted (pf), part_m holds max_j S^hi over
+// the tile, with |S - S^hi| <= E_k = N_k / div + 1:
+//   Ub = min(Ub, part_m + E_k),   Lk = max(Lk, part_m - E_k).
+// Then live[t][nt] = 1 where Ub >= Lk - 111 for some frame of the frame tile
+// (live zeroed first): every score of a tile that is not live lies more than
+// 111 below its frame's best (P = 0 in FP32, no weight in lse at FP64).
+__global__ void __launch_bounds__(256)
+    final_live_kernel(const double* __restrict__ part_m, const uint8_t* __restrict__ pf,
+                      float* __restrict__ Ub, double* __restrict__ Lk,
+                      const float* __restrict__ nsum, float div, int64_t n_mtiles,
+                      int64_t ld_data, int64_t n_data, uint8_t* __restrict__ live) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int64_t k = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t nnt = ld_data / 256;
+  const bool ok = k < n_data;
+  const double E = ok ? (double)nsum[k] / (double)div + 1.0 : 0.0;
+  double L = ok ? Lk[k] : INFINITY;
+  if (ok)
+    for (int64_t t = r; t < n_mtiles; t += 8) {
+      if (!pf[(t >> 1) * nnt + (k >> 8)]) continue;
+      const double m = part_m[t * ld_data + k];
+      float* u = Ub + t * ld_data + k;
+      *u = fminf(*u, __double2float_ru(m + E));
+      L = fmax(L, m - E);
+    }
+  red[r][lane] = L;
+  __syncthreads();
+  if (ok) {
+    L = red[0][lane];
+    for (int q = 1; q < 8; q++) L = fmax(L, red[q][lane]);
+    if (r == 0) Lk[k] = L;
+  }
+  for (int64_t t = r; t < n_mtiles; t += 8) {
+    const bool on = ok && (double)Ub[t * ld_data + k] >= L - 111.0;
+    if (__any_sync(0xffffffffu, on) && lane == 0) live[t * nnt + (k >> 8)] = 1;
+  }
+}
+
+// Per-frame state of the last iteration in a new internal order:
+// src[pos] = iperm_old[perm_new[pos]] (the frame's old position).
+__global__ void order_src_kernel(const int32_t* __restrict__ perm_new,
+                                 const int32_t* __restrict__ iperm_old, int64_t n_data,
+                                 int32_t* __restrict__ src) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n_data) src[p] = iperm_old[perm_new[p]];
+}
+
+// Ub2[t][pos] = Ub[t][src[pos]] for every row tile (grid.y), and the row
+// y == 0 also moves Mk and best.
+__global__ void gather_state_kernel(const int32_t* __restrict__ src, int64_t n_data,
+                                    int64_t ld_data, const float* __restrict__ Ub,
+                                    float* __restrict__ Ub2, const double* __restrict__ Mk,
+                                    double* __restrict__ Mk2, const int32_t* __restrict__ best,
+                                    int32_t* __restrict__ best2) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_data) return;
+  const int64_t t = blockIdx.y;
+  const int64_t q = src[p];
+  Ub2[t * ld_data + p] = Ub[t * ld_data + q];
+  if (t == 0) {
+    Mk2[p] = Mk[q];
+    best2[p] = best[q];
+  }
+}
+
+// *flag = 1 where a frame's counts differ from the BF16 copy Kb already held
+// (columns < n_pix; a count above 256 differs by construction). One CTA per frame.
+__global__ void __launch_bounds__(256)
+    frames_differ_kernel(const int32_t* __restrict__ K, int64_t ld_k, int64_t n_data,
+                         int64_t n_pix, const uint16_t* __restrict__ Kb, int64_t ld_pix, int fp16,
+                         int32_t* __restrict__ flag) {
+  const int64_t k = blockIdx.x;
+  if (k >= n_data) return;
+  int d = 0;
+  for (int64_t i = threadIdx.x; i < n_pix; i += blockDim.x) {
+    const uint16_t b = Kb[k * ld_pix + i];
+    const float v = fp16 ? __half2float(*reinterpret_cast<const __half*>(&b))
+                         : __uint_as_float(((uint32_t)b) << 16);
+    d |= (float)K[k * ld_k + i] != v;
+  }
+  if (__syncthreads_or(d) && threadIdx.x == 0) *flag = 1;
+}
+
+cudaError_t launch_delta_planes(const uint16_t* L0, const uint16_t* L1, int64_t plane,
+                                int64_t ld_pix, int64_t nrot, const double* b0, const double* b1,
+                                int64_t ntp, uint16_t* D, unsigned* dabs, float* bpm,
+                                cudaStream_t s) {
+  const int64_t nt = (nrot + 127) / 128;
+  cudaError_t e = cudaMemsetAsync(dabs, 0, sizeof(unsigned) * (size_t)nt, s);
+  if (e != cudaSuccess) return e;
+  dim3 grd((unsigned)((ld_pix + 255) / 256), (unsigned)nt);
+  delta_planes_kernel<<<grd, 256, 0, s>>>(L0, L1, plane, ld_pix, nrot, b0, b1, ntp, D, dabs, bpm,
+                                          nt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_delta_live(const float* C, int64_t ntp, const float* bpm, const unsigned* dabs,
+                              float* Ub, double* Lk, const double* Mk, const int32_t* best,
+                              const float* nsum, int64_t ld_pix, int64_t n_mtiles,
+                              int64_t ld_data, int64_t n_data, int valid,
+                              const int32_t* changed, uint8_t* cand, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cand, 0, (size_t)n_mtiles * (ld_data / 256), s);
+  if (e != cudaSuccess) return e;
+  const double errc = (double)(ld_pix + 8) * 0x1p-23;
+  delta_live_kernel<<<(unsigned)(ld_data / 32), 256, 0, s>>>(C, ntp, bpm, dabs, Ub, Lk, Mk, best,
+                                                             nsum, errc, n_mtiles, ld_data, n_data,
+                                                             valid, changed, cand);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_flags(const uint8_t* cand, int64_t n_mtiles, int64_t nnt, uint8_t* pf,
+                              cudaStream_t s) {
+  const int64_t n = (n_mtiles + 1) / 2 * nnt;
+  pair_flags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, n_mtiles, nnt, pf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_live(const double* part_m, const uint8_t* pf, float* Ub, double* Lk,
+                              const float* nsum, float div, int64_t n_mtiles, int64_t ld_data,
+                              int64_t n_data, uint8_t* live, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(live, 0, (size_t)n_mtiles * (ld_data / 256), s);
+  if (e != cudaSuccess) return e;
+  final_live_kernel<<<(unsigned)(ld_data / 32), 256, 0, s>>>(part_m, pf, Ub, Lk, nsum, div,
+                                                             n_mtiles, ld_data, n_data, live);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_state(const int32_t* perm_new, const int32_t* iperm_old, int64_t n_data,
+                                 int64_t ld_data, int64_t n_mtiles, int32_t* src, const float* Ub,
+                                 float* Ub2, const double* Mk, double* Mk2, const int32_t* best,
+                                 int32_t* best2, cudaStream_t s) {
+  const unsigned nb = (unsigned)((n_data + 255) / 256);
+  order_src_kernel<<<nb, 256, 0, s>>>(perm_new, iperm_old, n_data, src);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gather_state_kernel<<<dim3(nb, (unsigned)n_mtiles), 256, 0, s>>>(src, n_data, ld_data, Ub, Ub2,
+                                                                   Mk, Mk2, best, best2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frames_differ(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                                 const uint16_t* Kb, int64_t ld_pix, int fp16, int32_t* flag,
+                                 cudaStream_t s) {
+  frames_differ_kernel<<<(unsigned)n_data, 256, 0, s>>>(K, ld_k, n_data, n_pix, Kb, ld_pix, fp16,
+                                                        flag);
+  return cudaGetLastError();
+}
+
 }  // namespace emc

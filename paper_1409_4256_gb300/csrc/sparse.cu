@@ -587,6 +587,60 @@ __global__ void missed_mass_kernel(const float* __restrict__ S, int64_t ldS,
   missed[k] = (float)(1.0 - sum);
 }
 
+// Responsibilities of selected frames from stored scores (Eq. 2.4):
+// P[f][j] = exp(S_jk - lse_k) for k = frames[f], read like missed_mass_kernel
+// (frame-major scores relative to their 32-row group maxima; iperm/live: the
+// internal order and contracted tiles of a pruned pass, skipped tiles give 0).
+// Grid (ceil(nrot / 256), n): threads along rotations, coalesced in S and P.
+__global__ void __launch_bounds__(256)
+    responsibilities_kernel(const float* __restrict__ S, int64_t ldS,
+                            const float* __restrict__ Sref, int64_t ld_data,
+                            const float2* __restrict__ lse2, const int32_t* __restrict__ frames,
+                            int64_t nrot, int64_t n_data, const int32_t* __restrict__ iperm,
+                            const uint8_t* __restrict__ live, float* __restrict__ P,
+                            int32_t* status) {
+  const int64_t f = blockIdx.y;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t k = frames[f];
+  if (k < 0 || k >= n_data) {
+    if (j == 0) set_status(status, EMC_ERR_ARG);
+    return;
+  }
+  if (j >= nrot) return;
+  const int64_t c = iperm ? iperm[k] : k;
+  float p = 0.f;
+  if (!live || live[(j >> 7) * (ld_data >> 8) + (c >> 8)]) {
+    const float2 L = lse2[k];
+    p = __expf(S[c * ldS + j] + ((Sref[(j >> 5) * ld_data + c] - L.x) - L.y));
+  }
+  P[f * nrot + j] = p;
+}
+
+// lse[k] = m_k + log s_k
+__global__ void lse_values_kernel(const double* __restrict__ m, const double* __restrict__ s,
+                                  int64_t n, double* __restrict__ lse) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) lse[k] = m[k] + log(s[k]);
+}
+
+cudaError_t launch_responsibilities(const float* S, int64_t ldS, const float* Sref,
+                                    int64_t ld_data, const float2* lse2, const int32_t* frames,
+                                    int64_t n, int64_t nrot, int64_t n_data, float* P,
+                                    int32_t* status, cudaStream_t s, const int32_t* iperm,
+                                    const uint8_t* live) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grd((unsigned)((nrot + 255) / 256), (unsigned)n);
+  responsibilities_kernel<<<grd, 256, 0, s>>>(S, ldS, Sref, ld_data, lse2, frames, nrot, n_data,
+                                              iperm, live, P, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lse_values(const double* m, const double* sm, int64_t n, double* lse,
+                              cudaStream_t s) {
+  lse_values_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, sm, n, lse);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sparse_scores(const Planes& L, int precision, int64_t rows, const double* bias,
                                  const uint16_t* Kb, int64_t ld_pix, const int64_t* off,
                                  const int2* ent, int M, const int64_t* koff,

@@ -5,6 +5,8 @@
 //   PASS1     S = L K^T over pixels -> per frame (max_j, sum_j exp) per 128-row tile
 //   NORMALIZE S = L K^T over pixels -> P_jk = exp(S_jk - lse_k), BF16 hi/lo planes
 //   UPDATE    Num = P K over frames (K read MN-major) -> FP32 rows + den_j
+//   STORE     C = A K^T over pixels -> FP32 rows [rows][ld_data] as they are
+//             (the per-tile bound increments of the pruned pass 1)
 // with M = 128 rotations per tile and N = 256 frames (or pixels).
 //
 // Roles (320 threads, one CTA per SM):
@@ -51,7 +53,7 @@ using namespace tc;
 
 namespace {
 
-enum { MODE_PASS1 = 0, MODE_NORMALIZE = 1, MODE_UPDATE = 2 };
+enum { MODE_PASS1 = 0, MODE_NORMALIZE = 1, MODE_UPDATE = 2, MODE_STORE = 3 };
 
 constexpr int BM = 128, BN = 256;
 constexpr int kThreads = 320;
@@ -120,6 +122,8 @@ struct TcArgs {
   const int32_t* tile_count;
   int n_rowtiles;          // bound pass: 128-row tiles (n_mtiles counts pairs of them)
   int32_t* status;
+  uint64_t wait_ns;        // limit of every bounded wait
+  int stall;               // test hook: the MMA issuer's first wait never completes
 };
 
 // K blocks a tile contracts: every block, or (update with lists) the row
@@ -186,7 +190,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* acc_full = empty + C::STAGES;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain = acc_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* never = drain + 1;  // the stall hook's barrier: nothing arrives on it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float2* scratch = reinterpret_cast<float2*>(smem + C::STAGES * C::STAGE + 256);
 
@@ -199,6 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kEpiWarps);
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort = 0;
     fence_mbar_init();
   }
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int kb = tile_kblock(a, mt, x);
           const int s = it % C::STAGES;
           const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-          if (!mbar_wait(empty + s, ph ^ 1u, abort, kWaitLimitNs)) {
+          if (!mbar_wait(empty + s, ph ^ 1u, abort, a.wait_ns)) {
             fail(abort, a.status);
             ok = false;
             break;
@@ -253,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // let copies already issued land before the CTA retires
         for (int back = 1; back <= C::STAGES && it - back >= 0; back++) {
           const int j = it - back;
-          mbar_wait(full + (j % C::STAGES), (uint32_t)(j / C::STAGES) & 1u, abort, kWaitLimitNs);
+          mbar_wait_quiet(full + (j % C::STAGES), (uint32_t)(j / C::STAGES) & 1u, kWaitLimitNs);
         }
       }
     }
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0, tcount = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < T && ok; t += gridDim.x, tcount++) {
-        if (!mbar_wait(acc_empty, ((uint32_t)tcount & 1u) ^ 1u, abort, kWaitLimitNs)) {
+        if (!mbar_wait(acc_empty, ((uint32_t)tcount & 1u) ^ 1u, abort, a.wait_ns)) {
           fail(abort, a.status);
           break;
         }
@@ -274,7 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < nkb; kb++, it++) {
           const int s = it % C::STAGES;
           const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-          if (!mbar_wait(full + s, ph, abort, kWaitLimitNs)) {
+          uint64_t* wb = (a.stall && it == 0) ? never : full + s;
+          if (!mbar_wait(wb, ph, abort, a.wait_ns)) {
             fail(abort, a.status);
             ok = false;
             break;
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // every issued MMA must finish before TMEM is released
       umma_commit(drain);
-      mbar_wait(drain, 0, abort, kWaitLimitNs);
+      mbar_wait_quiet(drain, 0, kWaitLimitNs);
     }
   } else {
     // ------------------------------------------------------------ epilogue --
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row = (int64_t)mt * BM + r_in;
       float bh = 0.f, bl = 0.f;
       bool valid = row < a.nrot;
-      if (MODE != MODE_UPDATE) {
+      if (MODE == MODE_PASS1 || MODE == MODE_NORMALIZE) {
         const double b = a.bias[row];
         valid = valid && b > -INFINITY;
         if (valid) {
@@ -355,10 +362,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         named_bar(1, kEpiThreads);
       }
-      if (!mbar_wait(acc_full, (uint32_t)tcount & 1u, abort, kWaitLimitNs)) {
-        fail(abort, a.status);
-        break;
-      }
+      const bool got = mbar_wait(acc_full, (uint32_t)tcount & 1u, abort, a.wait_ns);
+      if (!got) fail(abort, a.status);
+      // every epilogue warp leaves together if any gave up (they share named barriers)
+      if (named_bar_any(2, kEpiThreads, !got)) break;
       tc_fence_after();
       bool big = false;
 #pragma unroll 1
@@ -372,6 +379,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(acc_empty);
+        }
+        if (MODE == MODE_STORE) {  // C[row][k] for the tile's 32 columns of this step
+          float* dst = a.Num + row * a.ld_data + (int64_t)nt * BN + col0;
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<uint4*>(dst + i) = make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
+          continue;
         }
         if (MODE == MODE_UPDATE) {
           const int64_t n0 = (int64_t)nt * BN + col0;
@@ -563,7 +577,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* acc_full = empty + STAGES;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain = acc_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* never = drain + 1;  // the stall hook's barrier: nothing arrives on it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* scratch = reinterpret_cast<float*>(smem + STAGES * STAGE + 256);
 
@@ -576,6 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kEpiWarps);
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort = 0;
     fence_mbar_init();
   }
@@ -605,7 +621,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < a.kblocks; kb++, it++) {
           const int s = it % STAGES;
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-          if (!mbar_wait(empty + s, ph ^ 1u, abort, kWaitLimitNs)) {
+          if (!mbar_wait(empty + s, ph ^ 1u, abort, a.wait_ns)) {
             fail(abort, a.status);
             ok = false;
             break;
@@ -620,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) {
         for (int back = 1; back <= STAGES && it - back >= 0; back++) {
           const int j = it - back;
-          mbar_wait(full + (j % STAGES), (uint32_t)(j / STAGES) & 1u, abort, kWaitLimitNs);
+          mbar_wait_quiet(full + (j % STAGES), (uint32_t)(j / STAGES) & 1u, kWaitLimitNs);
         }
       }
     }
@@ -630,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0, tcount = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < T && ok; t += gridDim.x, tcount++) {
-        if (!mbar_wait(acc_empty, ((uint32_t)tcount & 1u) ^ 1u, abort, kWaitLimitNs)) {
+        if (!mbar_wait(acc_empty, ((uint32_t)tcount & 1u) ^ 1u, abort, a.wait_ns)) {
           fail(abort, a.status);
           break;
         }
@@ -641,7 +657,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < a.kblocks; kb++, it++) {
           const int s = it % STAGES;
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-          if (!mbar_wait(full + s, ph, abort, kWaitLimitNs)) {
+          uint64_t* wb = (a.stall && it == 0) ? never : full + s;
+          if (!mbar_wait(wb, ph, abort, a.wait_ns)) {
             fail(abort, a.status);
             ok = false;
             break;
@@ -661,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ok) umma_commit(acc_full);
       }
       umma_commit(drain);
-      mbar_wait(drain, 0, abort, kWaitLimitNs);
+      mbar_wait_quiet(drain, 0, kWaitLimitNs);
     }
   } else {
     // ------------------------------------------------------------ epilogue --
@@ -676,10 +693,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       int mp, nt;
       tile_coords(t, a, &mp, &nt);
       const int nr = 2 * mp + 1 < a.n_rowtiles ? 2 : 1;
-      if (!mbar_wait(acc_full, (uint32_t)tcount & 1u, abort, kWaitLimitNs)) {
-        fail(abort, a.status);
-        break;
-      }
+      const bool got = mbar_wait(acc_full, (uint32_t)tcount & 1u, abort, a.wait_ns);
+      if (!got) fail(abort, a.status);
+      if (named_bar_any(2, kEpiThreads, !got)) break;
       tc_fence_after();
       for (int r = 0; r < nr; r++) {
         const int mt = 2 * mp + r;
@@ -803,6 +819,7 @@ TcArgs base_args(int64_t rows, int n_ntiles, int kblocks) {
   a.n_ntiles = n_ntiles;
   a.group = 8;
   a.kblocks = kblocks;
+  a.wait_ns = kWaitLimitNs;
   return a;
 }
 
@@ -812,7 +829,7 @@ int64_t tc_pass1_tiles(int64_t rows) { return rows / BM; }
 
 cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t ld_pix, double* part_m,
-                            int32_t* status, cudaStream_t s) {
+                            int32_t* status, cudaStream_t s, TcCtl ctl) {
   const bool f16 = precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
   if (!maps_scores(L, 1, f16, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
@@ -826,6 +843,8 @@ cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, 
   a.bias = bias;
   a.part_m = part_m;
   a.status = status;
+  if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
+  a.stall = ctl.stall;
   constexpr int kStage = 2 * BM * 64 * 2 + BN * 64 * 2;
   constexpr int kStages = (kSmemBudget - kScratchBytes - 1024 - 256) / kStage;
   constexpr int kSmem = 1024 + kStages * kStage + 256 + kScratchBytes;
@@ -849,12 +868,27 @@ cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_tc_store(const Planes& A, int64_t rows, const uint16_t* Kb, int64_t ld_data,
+                            int64_t ld_pix, float* C, int32_t* status, cudaStream_t s, TcCtl ctl) {
+  CUtensorMap mA, mB;
+  if (!maps_scores(A, 1, false, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
+  TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / 64));
+  a.nrot = rows;
+  a.ld_data = ld_data;
+  a.ld_pix = ld_pix;
+  a.Num = C;
+  a.status = status;
+  if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
+  a.stall = ctl.stall;
+  return launch<MODE_STORE, 1, false>(mA, mB, a, s);
+}
+
 cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t n_data, int64_t ld_pix,
                             double* part_m, float* part_s, float* S, float* Sref,
                             const float4* gk, const float4* gsc, int32_t* status,
                             cudaStream_t s, const int32_t* tile_list,
-                            const int32_t* tile_count) {
+                            const int32_t* tile_count, TcCtl ctl) {
   const bool gauss = gk != nullptr;
   const int nterms = gauss ? 3 : score_planes(precision);
   const bool f16 = gauss || precision == EMC_PREC_FP16_SPLIT;
@@ -876,6 +910,8 @@ cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, 
   a.tile_list = tile_list;
   a.tile_count = tile_list ? tile_count : nullptr;
   a.status = status;
+  if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
+  a.stall = ctl.stall;
   if (gauss) return launch<MODE_PASS1, 3, true>(mA, mB, a, s);
   if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_PASS1, 2, true>(mA, mB, a, s);
   return nterms == 3 ? launch<MODE_PASS1, 3, false>(mA, mB, a, s)
@@ -888,7 +924,7 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
                                 float2* lse2, Planes P, int32_t* status, cudaStream_t s,
                                 const double* shift, const double* Bsum, const float* invn,
                                 float* den, uint8_t* kb_flag, const int32_t* tile_list,
-                                const int32_t* tile_count) {
+                                const int32_t* tile_count, TcCtl ctl) {
   cudaError_t e = launch_lse_split(lse_m, lse_s, n_data, ld_data, lse2, s, shift);
   if (e != cudaSuccess) return e;
   if (kb_flag) {
@@ -922,6 +958,8 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
   a.tile_list = tile_list;
   a.tile_count = tile_list ? tile_count : nullptr;
   a.status = status;
+  if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
+  a.stall = ctl.stall;
   if (precision == EMC_PREC_FP16_SPLIT) return launch<MODE_NORMALIZE, 2, true>(mA, mB, a, s);
   return nterms == 3 ? launch<MODE_NORMALIZE, 3, false>(mA, mB, a, s)
                      : launch<MODE_NORMALIZE, 1, false>(mA, mB, a, s);
@@ -930,7 +968,7 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
 cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
                              int32_t* status, cudaStream_t s, const int32_t* kb_cnt,
-                             const int32_t* kb_list) {
+                             const int32_t* kb_list, TcCtl ctl) {
   const int nterms = precision == EMC_PREC_BF16 ? 1 : 2;
   const bool f16 = precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
@@ -953,6 +991,8 @@ cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const
   a.kb_list = kb_list;
   a.kb_ld = (int)(ld_data / 64);
   a.status = status;
+  if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
+  a.stall = ctl.stall;
   if (f16) return launch<MODE_UPDATE, 2, true>(mA, mB, a, s);
   return nterms == 2 ? launch<MODE_UPDATE, 2, false>(mA, mB, a, s)
                      : launch<MODE_UPDATE, 1, false>(mA, mB, a, s);

@@ -77,6 +77,7 @@ _SIGS = {
                               ctypes.POINTER(_vp)]),
     "emc_ctx_destroy": (_i32, [_vp]),
     "emc_ctx_status": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "emc_ctx_set_wait_limit": (_i32, [_vp, ctypes.c_uint64, _i32]),
     "emc_set_frames": (_i32, [_vp, _vp, _i64, _vp]),
     "emc_expand": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "emc_loglik": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp]),
@@ -102,6 +103,8 @@ _SIGS = {
     "emc_sparse_update": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "emc_sparse_iteration": (_i32, [_vp, _vp, _vp, ctypes.POINTER(IterStats), _vp]),
     "emc_missed_mass": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "emc_iteration_lse": (_i32, [_vp, _vp, _vp]),
+    "emc_responsibilities": (_i32, [_vp, _vp, _i64, _vp, _vp]),
 }
 
 
@@ -284,6 +287,12 @@ class Context:
         _check(lib().emc_ctx_status(self.h, ctypes.byref(v)), "emc_ctx_status")
         return v.value
 
+    def set_wait_limit(self, wait_limit_ns: int = 0, stall: bool = False):
+        """Limit of the tensor-core kernels' bounded waits (0: default) and the
+        stall test hook of emc_ctx_set_wait_limit."""
+        _check(lib().emc_ctx_set_wait_limit(self.h, int(wait_limit_ns), int(bool(stall))),
+               "emc_ctx_set_wait_limit")
+
     def _bytes(self, n: int):
         return self.torch.empty(int(n), dtype=self.torch.uint8, device=self.device)
 
@@ -367,6 +376,22 @@ class Context:
         if not stats:
             return grid_out, None
         return grid_out, {f: getattr(st, f) for f, _ in IterStats._fields_}
+
+    def iteration_lse(self, stream=None):
+        """lse_k of every frame after the last iteration (device float64 [n_data])."""
+        lse = self.torch.empty(self.cfg.n_data, dtype=self.torch.float64, device=self.device)
+        _check(lib().emc_iteration_lse(self.h, _ptr(lse), _stream(stream)), "emc_iteration_lse")
+        return lse
+
+    def responsibilities(self, frames, stream=None):
+        """P_jk of the given frames after the last iteration (device float32
+        [len(frames), n_rot]); frames: device int32."""
+        assert frames.dtype == self.torch.int32 and frames.is_contiguous()
+        n = int(frames.numel())
+        P = self.torch.empty((n, self.cfg.n_rot), dtype=self.torch.float32, device=self.device)
+        _check(lib().emc_responsibilities(self.h, _ptr(frames), n, _ptr(P), _stream(stream)),
+               "emc_responsibilities")
+        return P
 
     # -- learned proposal and sparse Maximize ------------------------------------
     def features(self, stream=None):

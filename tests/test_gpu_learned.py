@@ -2,7 +2,11 @@
 FP64 oracle (oracle/learned.py, oracle/emc_oracle.c) on the same inputs.
 
 Tolerances: features 1e-5 absolute (FP32 log1p of exact bin sums); MLP logits,
-loss and gradients rel-L2 2e-2 (products take BF16-rounded operands);
+loss and gradients rel-L2 1e-2 against the FP64 oracle (the products take
+BF16-rounded operands, unit roundoff 2^-8: measured on the CPU, that rounding
+alone moves them by 5e-3 to 6e-3 rel-L2 at K = 512) and 1e-3 against the
+oracle with the same operand rounding (what remains is FP32 accumulation and
+the FP32 GELU, plus operands that land on the other side of a BF16 rounding);
 sparse responsibilities max|dP| <= 1e-4, lse 1e-4, model rel-L2 <= 1e-5 (the
 same bar as the dense forms, same exact score split)."""
 import numpy as np
@@ -91,7 +95,9 @@ def test_mlp_forward_and_gradients(torch_cuda, B):
     # forward
     z = prop.logits(Xd, batch=B).cpu().numpy()[:, :n_out]
     zr, _ = ol.mlp_forward(ps, X.astype(np.float64))
-    assert rel_l2(z, zr) < 2e-2
+    zb, _ = ol.mlp_forward(ps, X.astype(np.float64), operand=ol.bf16_round)
+    assert rel_l2(z, zr) < 1e-2
+    assert rel_l2(z, zb) < 1e-3
     # one training step: loss and the gradients it used
     work = torch.empty(emc.mlp_work_size(n_out, B), dtype=torch.uint8, device="cuda")
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -101,7 +107,9 @@ def test_mlp_forward_and_gradients(torch_cuda, B):
     torch.cuda.synchronize()
     T = ol.dense_targets(tidx, tprob.astype(np.float64), n_out)
     lr_, gr = ol.mlp_loss_grads(ps, X.astype(np.float64), T)
-    assert abs(loss.item() - lr_) < 2e-2 * abs(lr_)
+    lb_, gb_ = ol.mlp_loss_grads(ps, X.astype(np.float64), T, operand=ol.bf16_round)
+    assert abs(loss.item() - lr_) < 1e-2 * abs(lr_)
+    assert abs(loss.item() - lb_) < 1e-3 * abs(lb_)
     g = prop.grads.cpu().numpy().astype(np.float64)
     H, ld = 512, prop.ld_out
     o = 0
@@ -112,8 +120,10 @@ def test_mlp_forward_and_gradients(torch_cuda, B):
         gb = g[o:o + out]
         o += out
         cols = out if l < 3 else n_out
-        assert rel_l2(gw[:, :cols], gr[2 * l]) < 2e-2, l
-        assert rel_l2(gb[:cols], gr[2 * l + 1]) < 2e-2, l
+        assert rel_l2(gw[:, :cols], gr[2 * l]) < 1e-2, l
+        assert rel_l2(gb[:cols], gr[2 * l + 1]) < 1e-2, l
+        assert rel_l2(gw[:, :cols], gb_[2 * l]) < 1e-3, l
+        assert rel_l2(gb[:cols], gb_[2 * l + 1]) < 1e-3, l
         if l == 3:
             assert np.all(gw[:, n_out:] == 0) and np.all(gb[n_out:] == 0)
 

@@ -375,3 +375,59 @@ def test_bad_arguments_raise(torch_cuda, small_problem):
         ctx.expand(grid_dev(torch, p), 1379, 5)
     with pytest.raises(emc.EmcError):
         ctx.expand(grid_dev(torch, p), -1, 5)
+
+
+# ---------------------------------------------------------------------------
+# Plain BF16: log W rounded once to BF16 (8 significant bits, unit roundoff
+# 2^-8), FP32 accumulation, P stored as one BF16 value. The target's bar for
+# it is 1e-3. Its responsibilities cannot meet that: one rounding of log W
+# moves S_jk by up to 2^-8 sum_i K_ik |log W_ij|, which is of order one for a
+# frame of hundreds of photons, and P = exp(S - lse) moves by that factor
+# (measured max|dP| 0.31 here). The tests hold every element to the bound this
+# arithmetic gives and print the measured errors.
+# ---------------------------------------------------------------------------
+
+def plain_bf16_bound(W, K, ld_pix, bias):
+    """Per (j, k) bound on |S_bf16 - S| for log W rounded to nearest BF16
+    (relative 2^-8), the FP32 trilinear W (2e-6 + 2e-7 |log W| absolute) and
+    FP32 accumulation over ld_pix terms (relative ld_pix 2^-24 of sum K |L|)."""
+    A = np.abs(np.log(W))
+    mag = A @ K.T                      # sum_i K_ik |log W_ij|
+    return ((2.0 ** -8 + 2e-7 + ld_pix * 2.0 ** -24) * mag + 2e-6 * K.sum(1)[None, :] +
+            1e-6 * np.abs(bias)[:, None] + 1e-6)
+
+
+def test_plain_bf16_against_oracle(torch_cuda, small_problem, ref):
+    torch, p = torch_cuda, small_problem
+    ctx = make_ctx(torch, p, "bf16", store_scores=True)
+    nrot, nd, npix = p["quat"].shape[0], p["K"].shape[0], p["q"].shape[0]
+    g = grid_dev(torch, p)
+    L, bias = ctx.expand(g, 0, nrot)
+    m, s = ctx.loglik(L, bias, nrot)
+    P = ctx.normalize(L, bias, nrot, m, s)
+    out, st = ctx.iteration(g)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0 and st["device_status"] == 0
+    # log W: the nearest BF16 of the FP32 value
+    Lg = decode_L(torch, ctx, L, nrot, "bf16")[:nrot, :npix]
+    Lo = np.log(ref["W"])
+    assert np.all(np.abs(Lg - Lo) <= (2.0 ** -8 + 2e-7) * np.abs(Lo) + 2e-6)
+    B = plain_bf16_bound(ref["W"], p["K"].astype(np.float64), ctx.ld_pix, ref["bias"])
+    b_k = B.max(0)                     # |d lse_k| <= max_j |d S_jk|
+    lse = (m + torch.log(s)).cpu().numpy()[:nd]
+    d_lse = np.abs(lse - ref["lse"])
+    assert np.all(d_lse <= b_k), (d_lse - b_k).max()
+    # P_bf16 / P in [e^-(B_jk + b_k), e^(B_jk + b_k)], then FP32 exp and one
+    # BF16 rounding (2^-8 relative; 2^-7 covers both)
+    Pg = decode_P(torch, ctx, P, nrot, "bf16")[:nrot, :nd]
+    f = np.expm1(B + b_k[None, :])
+    assert np.all(np.abs(Pg - ref["P"]) <= ref["P"] * (f + 2.0 ** -7 * (1 + f)) + 1e-30)
+    dP = np.abs(Pg - ref["P"]).max()
+    model = rel_l2(out.cpu().numpy().astype(np.float64), ref["out"])
+    print(f"\nplain BF16 at 32^3 (1380 rotations x 300 frames): max|dP| {dP:.3e}, "
+          f"max|d lse| {d_lse.max():.3e}, model rel-L2 {model:.3e}")
+    # With only 300 frames each frame's P error weighs on the model: measured
+    # 2.1e-3 here, so this form misses the 1e-3 model bar at this size (it meets
+    # it at the 64^3 workload, test_gpu_fullsize.py). Held to 1e-2, the size of
+    # the BF16 rounding itself, so that a defect beyond the rounding still fails.
+    assert model <= 1e-2, model

@@ -133,3 +133,42 @@ def test_merge_candidates_hand_cases():
     for k in range(20):
         assert set(first[k]) <= set(out[k]) and len(set(out[k])) == 16
         assert set(out[k]) <= set(first[k]) | set(rest[k])
+
+
+def test_bf16_round():
+    # values with at most 8 significant bits are BF16 numbers and stay put;
+    # halfway cases go to the even neighbour; the error is at most half a unit
+    # in the 8th significant bit, 2^-8 relative;
+    # and it agrees with PyTorch's own float -> bfloat16 conversion on the CPU
+    from oracle.learned import bf16_round
+    exact = np.array([0.0, 1.0, -3.5, 255.0, 2.0 ** -20 * 129, 1.0 + 2.0 ** -7])
+    assert np.array_equal(bf16_round(exact), exact)
+    ties = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8)])
+    assert np.array_equal(bf16_round(ties), [1.0, 1.0 + 2.0 ** -6, -1.0])
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=20000) * np.exp(rng.uniform(-30, 30, size=20000))
+    r = bf16_round(x)
+    x32 = x.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(r - x32) <= 2.0 ** -8 * np.abs(x32))
+    torch = pytest.importorskip("torch")
+    t = torch.as_tensor(x.astype(np.float32)).to(torch.bfloat16).double().numpy()
+    assert np.array_equal(r, t)
+
+
+def test_rounded_mlp_reduces_to_the_fp64_one():
+    # with the identity for the operand rounding the MLP is the pinned FP64 one;
+    # with BF16 operands its gradients stay within the rounding's effect
+    from oracle import learned as ol
+    rng = np.random.default_rng(12)
+    ps = []
+    for fo in (16, 16, 16, 10):
+        ps += [rng.normal(0, 0.3, size=(16 if ps else 16, fo)), rng.normal(0, 0.1, size=fo)]
+    X = rng.uniform(0, 2, size=(6, 16))
+    T = ol.dense_targets(rng.integers(0, 10, size=(6, 2)), np.full((6, 2), 0.5), 10)
+    l0, g0 = ol.mlp_loss_grads(ps, X, T)
+    l1, g1 = ol.mlp_loss_grads(ps, X, T, operand=lambda a: a)
+    assert l0 == l1 and all(np.array_equal(a, b) for a, b in zip(g0, g1))
+    l2, g2 = ol.mlp_loss_grads(ps, X, T, operand=ol.bf16_round)
+    assert abs(l2 - l0) <= 1e-2 * abs(l0)
+    for a, b in zip(g2, g0):
+        assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b)

@@ -94,3 +94,33 @@ def test_loglik_static_rejects_frames_beyond_static_scratch(torch_cuda, small_pr
                                      dummy.data_ptr(), 1380, dummy.data_ptr(), dummy.data_ptr(),
                                      0, None, int(torch.cuda.current_stream().cuda_stream))
     assert rc == -4  # EMC_ERR_UNSUPPORTED, nothing launched
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_split"])
+def test_loglik_static_over_rotation_blocks(torch_cuda, small_problem, precision):
+    # 400200 frames (the small problem's 300 repeated): the 32 MiB array holds
+    # the per-tile pairs of only 384 rotations at a time, so one call runs four
+    # rotation blocks -- the row offsets into L and bias past the first block,
+    # the plane stride of the whole L, and the merge into the earlier blocks
+    torch, p = torch_cuda, small_problem
+    from paper_1409_4256_gb300 import emc
+    K = np.tile(p["K"], (1334, 1))
+    nrot, nd = p["quat"].shape[0], K.shape[0]
+    ctx = emc.Context(p["N"], p["q"], p["quat"], p["w"], nd, precision=precision,
+                      w_floor=p["w_floor"])
+    ctx.set_frames(torch.as_tensor(K, device="cuda"))
+    block = (32 * 2 ** 20 // (ctx.ld_data * 12)) * 64 // 128 * 128
+    rows = -(-nrot // 128) * 128
+    assert 128 <= block and rows > 2 * block  # at least three blocks
+    grid = torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
+    L, bias = ctx.expand(grid, 0, nrot)
+    m_ref, s_ref = ctx.loglik(L, bias, nrot)
+    frames = frames_bf16(torch, K, ctx.ld_data, ctx.ld_pix)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    m = torch.full((ctx.ld_data,), float("nan"), dtype=torch.float64, device="cuda")
+    s = torch.full((ctx.ld_data,), float("nan"), dtype=torch.float64, device="cuda")
+    emc.loglik_static(ctx.cfg, L, bias, frames, nrot, m, s, device_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0 and ctx.status() == 0
+    d = ((m + torch.log(s)) - (m_ref + torch.log(s_ref))).cpu().numpy()[:nd]
+    assert np.abs(d).max() <= 1e-4, np.abs(d).max()
