@@ -50,6 +50,8 @@ GAUSS_FORMS = ("gaussian",)
 FLUENCE_FORMS = ("poisson_fluence",)
 RECON_FORMS = ("reconstruct",)
 SPARSE_K_FORMS = ("sparse_k",)
+# other workloads' own configurations (their own seeded data, built once)
+SCALE_FORMS = {"emc128_recompute": "emc128", "learned128": "emc128"}
 
 
 def parse_args():
@@ -63,7 +65,8 @@ def parse_args():
     ap.add_argument("--n-data", type=int, default=None, help="override the frame count")
     ap.add_argument("--n-quat", type=int, default=None, help="override the rotation sampling n")
     ap.add_argument("--forms",
-                    default="fp32,bf16,fp16_split,learned,adaptive,gaussian,poisson_fluence,sparse_k",
+                    default="fp32,bf16,fp16_split,learned,adaptive,gaussian,poisson_fluence,"
+                            "sparse_k,emc128_recompute,learned128",
                     help="other forms to time briefly (comma list, or 'none')")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-iters", type=int, default=30,
@@ -476,7 +479,7 @@ def reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot):
         sc = float((x * truth).sum() / (x * x).sum())
         return float(torch.linalg.norm(sc * x - truth) / torch.linalg.norm(truth))
 
-    errs, ms, tiles = [err(grid)], [], []
+    errs, ms, tiles, phases = [err(grid)], [], [], []
     a, b = grid.clone(), torch.empty_like(grid)
     with torch.cuda.stream(stream):
         for _ in range(args.recon_iters):
@@ -485,6 +488,10 @@ def reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot):
                 raise RuntimeError(f"device status {st['device_status']}")
             ms.append(st["ms_total"])
             tiles.append(st["pass1_exact"] / st["pass1_tiles"])
+            phases.append({k: round(st[k], 2) for k in ("ms_expand", "ms_loglik", "ms_normalize",
+                                                        "ms_update", "ms_compress")} |
+                          {"bound_pairs": st["pass1_bound_pairs"],
+                           "incremental_bound": st["pass1_delta"]})
             errs.append(err(b))
             a, b = b, a
     del ctx
@@ -492,7 +499,7 @@ def reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot):
     # and runs the dense pass 1)
     later = ms[1:] if len(ms) > 1 else ms
     return {"model": model, "precision": prec, "iterations": args.recon_iters,
-            "ms_per_iteration": ms, "pass1_exact_tile_fraction": tiles,
+            "ms_per_iteration": ms, "pass1_exact_tile_fraction": tiles, "phases_ms": phases,
             "rel_err_vs_truth_after_scale_fit": errs,
             "value": n_rot * ds.K.shape[0] / (sum(later) / len(later) * 1e-3)}
 

@@ -134,6 +134,16 @@ typedef enum emc_compress_mode {
                                    frames' maxima. The others have P = 0 in
                                    FP32 and no weight in lse at FP64 precision,
                                    so the results are those of the dense pass.
+                                   From the second pruned iteration on the same
+                                   frames, an incremental bound (the last
+                                   iteration's tile maxima plus the largest
+                                   change of log W over each tile, contracted
+                                   per tile against the frames) first rules out
+                                   tiles, and the hi-plane bound runs only over
+                                   the rest. The context keeps the last
+                                   iteration's L and bias for that (a second
+                                   copy of each in the workspace); emc_set_frames
+                                   with other counts voids it for one iteration.
                                    Frames are regrouped internally by the row
                                    tile of their best rotation after every
                                    iteration (a second copy of the frames in
@@ -196,8 +206,12 @@ typedef struct emc_iter_stats {
   int64_t pass1_tiles;   /* (128-rotation, 256-frame) tiles of the E-step pass 1 */
   int64_t pass1_exact;   /* of those, contracted with every plane (all of them
                             unless the pass was bound-pruned) */
-  int32_t pass1_pruned;  /* 1: a hi-plane bound pass over every tile ran first */
-  int32_t reserved;
+  int32_t pass1_pruned;  /* 1: the pass was bound-pruned (a hi-plane bound ran first) */
+  int32_t pass1_delta;   /* 1: the incremental bound from the last iteration ran before
+                            the hi-plane bound, which then covered only the tiles it
+                            could not rule out */
+  int64_t pass1_bound_pairs; /* pairs of row tiles x frame tiles the hi-plane bound
+                                contracted (pruned passes) */
 } emc_iter_stats;
 
 typedef struct emc_ctx emc_ctx;

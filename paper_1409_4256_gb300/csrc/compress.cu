@@ -1,8 +1,9 @@
 // compress.cu -- c-step of EMC (Eq. 2.12; Eq. 2.5 + 2.10 in IDW mode).
 //
-// One CTA per rotation row j. Each (i, j) recomputes the double-float grid
-// point p = R_j q_i + N/2 (the same weights f(p_l - R_j q_i) that expansion
-// used) and contributes f * Num_ij to g_num and f * den_j to g_den, which are
+// One CTA per rotation row j. Each (i, j) recomputes the grid point
+// p = R_j q_i + N/2 (in fixed point, rotate_fx: the weights f(p_l - R_j q_i)
+// of the expansion) and contributes f * Num_ij to g_num and f * den_j to
+// g_den, which are
 // reduced with FP64 atomics resolved in L2 (the N^3 FP64 grids, 2 MB at 64^3,
 // stay L2-resident). The paper's insert_slices kernel also used one block per
 // slice. Rotations without responsibility mass (den_j = 0) are skipped. Every
@@ -83,11 +84,12 @@ __device__ __forceinline__ int warp_max(int v) {
 // on the host from max |q_i|), so no bounds checks.
 template <bool INTERIOR>
 __global__ void __launch_bounds__(kAggThreads)
-    compress_kernel(Geom g, const RotDF* __restrict__ rot, const float* __restrict__ Num,
+    compress_kernel(Geom g, const RotFX* __restrict__ rot, const float* __restrict__ Num,
                     const float* __restrict__ den, int mode, double* __restrict__ g_num,
                     double* __restrict__ g_den, int nrep, int64_t n_vox) {
   extern __shared__ float2 agg_smem[];
-  __shared__ RotDF R;
+  __shared__ int Rh[9];
+  __shared__ float Rhf[9], Rl[9];
   const int64_t row = blockIdx.x;
   const float dj = den[row];
   // a rotation without responsibility mass has Num = 0 and den = 0 (both
@@ -99,13 +101,16 @@ __global__ void __launch_bounds__(kAggThreads)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* box = agg_smem + warp * (kAggCap + kAggStage);
   float2* stage = box + kAggCap;
-  if (threadIdx.x < 18)
-    reinterpret_cast<float*>(&R)[threadIdx.x] = reinterpret_cast<const float*>(rot + row)[threadIdx.x];
+  if (threadIdx.x < 9) {
+    const int h = rot[row].hi[threadIdx.x];
+    Rh[threadIdx.x] = h;
+    Rhf[threadIdx.x] = (float)h * 0x1p-20f;
+    Rl[threadIdx.x] = rot[row].lo[threadIdx.x];
+  }
   for (int s = lane; s < kAggCap; s += 32) box[s] = make_float2(0.f, 0.f);
   __syncthreads();
   const int N = g.N;
   const int64_t nn = (int64_t)N * N;
-  const float half_n = 0.5f * (float)N;
   const float* Nr = Num + row * g.ld_pix;
   const float inv_d = (mode == EMC_COMPRESS_IDW) ? 1.0f / dj : 1.0f;
   const float dv = (mode == EMC_COMPRESS_IDW) ? 1.0f : dj;
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(kAggThreads)
       const int k = lane + 32 * h;
       has[h] = k < np;
       if (has[h]) {
-        rotate_to_grid(R, g.gqh[p0 + k], g.gql[p0 + k], half_n, f[h], t[h]);
+        rotate_fx(Rh, Rhf, Rl, g.gqi[p0 + k], g.gqf[p0 + k], g.gqlo[p0 + k], N, f[h], t[h]);
         v[h] = Nr[g.gpix[p0 + k]] * inv_d;
       } else {
         f[h][0] = f[h][1] = f[h][2] = 0;
@@ -225,16 +230,18 @@ __global__ void __launch_bounds__(kAggThreads)
   // duplicate columns carrying counts above 256 (w = kDupMark) share their
   // pixel's geometry and add numerator only
   for (int64_t i = g.n_pix + threadIdx.x; i < g.ld_pix; i += kAggThreads) {
-    const float4 a = g.qh[i];
-    if (a.w == 0.f) continue;
+    const int4 qi = g.qi[i];
+    if (qi.w == 0) continue;
     int f[3];
     float t[3];
-    rotate_to_grid(R, a, g.ql[i], half_n, f, t);
-    reduce_direct<INTERIOR>(f, t, Nr[i] * inv_d, a.w == 1.f ? dv : 0.f, N, g_num, g_den);
+    const float4 qhf = make_float4((float)qi.x * 0x1p-12f, (float)qi.y * 0x1p-12f,
+                                   (float)qi.z * 0x1p-12f, 0.f);
+    rotate_fx(Rh, Rhf, Rl, qi, qhf, g.qlo[i], N, f, t);
+    reduce_direct<INTERIOR>(f, t, Nr[i] * inv_d, qi.w == 1 ? dv : 0.f, N, g_num, g_den);
   }
 }
 
-cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const float* Num,
+cudaError_t launch_compress(const Geom& g, const RotFX* rot, int64_t nrot, const float* Num,
                             const float* den, int mode, double* g_num, double* g_den, int nrep,
                             cudaStream_t s) {
   if (nrot <= 0) return cudaSuccess;

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <utility>
 #include <vector>
 
 #include "emc_common.cuh"
@@ -24,8 +25,10 @@ struct Layout {
       Num, den, gnum, gden, scalar, fbin, finv, cand, ccnt, coff, cent, Sc, Pc, lsec, gk, gauss,
       Kb2, skcnt, skoff, skent, dupsrc, duprank, pixmax, fcn, finvn, fB, kbflag, kbcnt, kblist,
       Kp, perm, perm2, iperm, nsum, nsum_p, cn_p, invn_p, best, lsem_s, lses_s, live, tlist,
-      tcount, sortH, sortoff, cgs, cgp, cgqh, cgql, total;
+      tcount, sortH, sortoff, cgs, cgp, cgqh, cgql, cgqi, cgqlo, cgqf, L2, bias2, Ub, Ub2, Lk, Mk, Mk2, best2,
+      osrc, Dd, Cd, bpm, Ua, Ua2, dcand, pflag, plist, flags, qi, qlo, rotfx, epart, total;
   int64_t sort_entries;
+  int64_t ntp;  // row tiles rounded up to 128: rows of each half of the bound increments
 };
 
 // Gaussian scalars inside the 256-byte block at Layout::gauss
@@ -124,8 +127,15 @@ Layout make_layout(const emc_config* c) {
   y.cgp = take(sizeof(int32_t) * (c->n_pix + 1));
   y.cgqh = take(sizeof(float4) * (c->n_pix + 1));
   y.cgql = take(sizeof(float4) * (c->n_pix + 1));
+  y.cgqi = take(sizeof(int4) * (c->n_pix + 1));
+  y.cgqlo = take(sizeof(float4) * (c->n_pix + 1));
+  y.cgqf = take(sizeof(float4) * (c->n_pix + 1));
+  y.qi = take(sizeof(int4) * y.ld_pix);
+  y.qlo = take(sizeof(float4) * y.ld_pix);
   y.quat = take(sizeof(double) * 4 * c->n_rot);
   y.rot = take(sizeof(RotDF) * c->n_rot);
+  y.rotfx = take(sizeof(RotFX) * c->n_rot);
+  y.epart = take(sizeof(double) * (size_t)expand_tile_slices(y.ld_pix) * y.rows);
   y.logw = take(sizeof(double) * c->n_rot);
   y.Kb = take(2 * (size_t)y.ld_data * y.ld_pix);
   y.status = take(256);
@@ -199,6 +209,32 @@ Layout make_layout(const emc_config* c) {
   y.tcount = pr ? take(256) : 0;
   y.sortH = pr ? take(sizeof(int32_t) * (size_t)y.sort_entries) : 0;
   y.sortoff = pr ? take(sizeof(int64_t) * (size_t)(y.sort_entries + 1)) : 0;
+  // the incremental bound between consecutive iterations: a second L and bias
+  // (the last iteration's stay for the differences), per-tile bounds Ub in the
+  // internal frame order (and a copy for reordering), per-frame lower bounds,
+  // the last exact maxima, the BF16 increments D and their products C
+  y.ntp = round_up(nmt, 128);
+  const int64_t npairs = (nmt + 1) / 2;
+  y.L2 = pr ? take(L_bytes(c, y.rows, y.ld_pix)) : 0;
+  y.bias2 = pr ? take(sizeof(double) * y.rows * (is_flu(c) ? 2 : 1)) : 0;
+  y.Ub = pr ? take(sizeof(float) * (size_t)nmt * y.ld_data) : 0;
+  y.Ub2 = pr ? take(sizeof(float) * (size_t)nmt * y.ld_data) : 0;
+  y.Ua = pr ? take(sizeof(float) * (size_t)nmt * y.ld_data) : 0;
+  y.Ua2 = pr ? take(sizeof(float) * (size_t)nmt * y.ld_data) : 0;
+  y.Lk = pr ? take(sizeof(double) * (size_t)y.ld_data) : 0;
+  y.Mk = pr ? take(sizeof(double) * (size_t)y.ld_data) : 0;
+  y.Mk2 = pr ? take(sizeof(double) * (size_t)y.ld_data) : 0;
+  y.best2 = pr ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
+  y.osrc = pr ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
+  y.Dd = pr ? take(2 * (size_t)(3 * y.ntp) * y.ld_pix) : 0;
+  y.Cd = pr ? take(sizeof(float) * (size_t)(3 * y.ntp) * y.ld_data) : 0;
+  y.bpm = pr ? take(sizeof(float) * 2 * (size_t)nmt) : 0;
+  y.dcand = pr ? take((size_t)nmt * nnt) : 0;
+  y.pflag = pr ? take((size_t)npairs * nnt) : 0;
+  y.plist = pr ? take(sizeof(int32_t) * (size_t)npairs * nnt) : 0;
+  // int32 [0]: the frames changed since the last iteration; [2]: the device
+  // status when the last pass 1 ended (non-zero voids the tile bounds)
+  y.flags = pr ? take(256) : 0;
   y.total = o;
   return y;
 }
@@ -240,10 +276,39 @@ struct emc_ctx {
   bool frames_loaded;
   bool cand_loaded;
   bool iterated;              // an emc_iteration ran on the loaded frames
+  int lcur;                   // L and bias buffer of the last emc_iteration (pruned contexts)
+  bool ub_valid;              // the tile bounds, maxima and best tiles belong to that iteration
+  int32_t* best;              // per-frame state in the internal order (swapped with *2)
+  int32_t* best2;
+  double* Mk;
+  double* Mk2;
+  float* Ub;
+  float* Ub2;
+  float* Ua;  // widening gathered since each tile bound's refresh (swapped with Ua2)
+  float* Ua2;
   cudaEvent_t ev[8];
   int kernels;  // launches made by the last emc_iteration
   TcCtl tcctl;  // bounded waits of the tensor-core launches (emc_ctx_set_wait_limit)
 };
+
+// The internal frame order the last iteration found (perm2) becomes the
+// current one. The per-frame state of the incremental bound (tile bounds, last
+// exact maxima, best tiles) moves with the frames: each new position takes the
+// values of its frame's old position (iperm before the frames are permuted).
+// The caller then permutes the frames themselves (launch_permute_frames).
+static int reorder_state(emc_ctx* c, cudaStream_t s) {
+  const Layout& y = c->lay;
+  std::swap(c->perm, c->perm2);
+  CU(launch_reorder_state(c->perm, (const int32_t*)(c->ws + y.iperm), c->cfg.n_data, y.ld_data,
+                          y.rows / 128, (int32_t*)(c->ws + y.osrc), c->Ub, c->Ub2, c->Ua, c->Ua2,
+                          c->Mk, c->Mk2, c->best, c->best2, s));
+  std::swap(c->Ub, c->Ub2);
+  std::swap(c->Ua, c->Ua2);
+  std::swap(c->Mk, c->Mk2);
+  std::swap(c->best, c->best2);
+  c->order_pending = false;
+  return EMC_OK;
+}
 
 extern "C" {
 
@@ -363,6 +428,17 @@ static int ctx_create(const emc_config* cfg, const double* q, const double* quat
   for (int64_t j = 0; j < cfg->n_rot; j++) lw[j] = log(weight[j]);
   std::vector<RotDF> rot(cfg->n_rot);
   for (int64_t j = 0; j < cfg->n_rot; j++) quat_to_rot_df(quat + 4 * j, &rot[j]);
+  // the same matrices in fixed point: hi = round(R 2^20), lo = R - hi 2^-20
+  std::vector<RotFX> rotfx(cfg->n_rot);
+  for (int64_t j = 0; j < cfg->n_rot; j++) {
+    double R[9];
+    quat_to_rot(quat + 4 * j, R);
+    for (int e = 0; e < 9; e++) {
+      const double h = rint(R[e] * 1048576.0);
+      rotfx[j].hi[e] = (int32_t)h;
+      rotfx[j].lo[e] = (float)(R[e] - h / 1048576.0);
+    }
+  }
   // feature bins of the learned proposal: radial floor(32 |q| / max|q|),
   // angular floor(16 (atan2(q_y, q_x) + pi) / (2 pi)); both capped at the top bin
   std::vector<int16_t> fbin(y.ld_pix, 0);
@@ -396,6 +472,8 @@ static int ctx_create(const emc_config* cfg, const double* q, const double* quat
   c->ws_bytes = workspace_bytes;
   c->geom.qh = (const float4*)(c->ws + y.qh);
   c->geom.ql = (const float4*)(c->ws + y.ql);
+  c->geom.qi = (const int4*)(c->ws + y.qi);
+  c->geom.qlo = (const float4*)(c->ws + y.qlo);
   c->geom.n_pix = cfg->n_pix;
   c->geom.ld_pix = y.ld_pix;
   c->geom.N = cfg->N;
@@ -404,6 +482,9 @@ static int ctx_create(const emc_config* cfg, const double* q, const double* quat
   c->geom.gpix = (const int32_t*)(c->ws + y.cgp);
   c->geom.gqh = (const float4*)(c->ws + y.cgqh);
   c->geom.gql = (const float4*)(c->ws + y.cgql);
+  c->geom.gqi = (const int4*)(c->ws + y.cgqi);
+  c->geom.gqlo = (const float4*)(c->ws + y.cgqlo);
+  c->geom.gqf = (const float4*)(c->ws + y.cgqf);
   {
     // |R q| = |q|: with every |q_i| below N/2 - 1 (less a margin far above the
     // 1e-9-voxel error of the rotation) each p = R q + N/2 has floor in
@@ -433,6 +514,14 @@ static int ctx_create(const emc_config* cfg, const double* q, const double* quat
   c->prune = prune_ok(cfg);
   c->perm = y.perm ? (int32_t*)(c->ws + y.perm) : nullptr;
   c->perm2 = y.perm2 ? (int32_t*)(c->ws + y.perm2) : nullptr;
+  c->best = y.best ? (int32_t*)(c->ws + y.best) : nullptr;
+  c->best2 = y.best2 ? (int32_t*)(c->ws + y.best2) : nullptr;
+  c->Mk = y.Mk ? (double*)(c->ws + y.Mk) : nullptr;
+  c->Mk2 = y.Mk2 ? (double*)(c->ws + y.Mk2) : nullptr;
+  c->Ub = y.Ub ? (float*)(c->ws + y.Ub) : nullptr;
+  c->Ub2 = y.Ub2 ? (float*)(c->ws + y.Ub2) : nullptr;
+  c->Ua = y.Ua ? (float*)(c->ws + y.Ua) : nullptr;
+  c->Ua2 = y.Ua2 ? (float*)(c->ws + y.Ua2) : nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   bool ok = true;
   ok &= cudaMemcpyAsync(c->ws + y.qh, qh.data(), sizeof(float4) * y.ld_pix,
@@ -453,8 +542,17 @@ static int ctx_create(const emc_config* cfg, const double* q, const double* quat
                         s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->ws + y.rot, rot.data(), sizeof(RotDF) * cfg->n_rot,
                         cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(c->ws + y.rotfx, rotfx.data(), sizeof(RotFX) * cfg->n_rot,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= launch_fixed_geometry((const float4*)(c->ws + y.qh), (const float4*)(c->ws + y.ql),
+                              y.ld_pix, (int4*)(c->ws + y.qi), (float4*)(c->ws + y.qlo),
+                              nullptr, s) == cudaSuccess;
+  ok &= launch_fixed_geometry((const float4*)(c->ws + y.cgqh), (const float4*)(c->ws + y.cgql),
+                              cfg->n_pix, (int4*)(c->ws + y.cgqi), (float4*)(c->ws + y.cgqlo),
+                              (float4*)(c->ws + y.cgqf), s) == cudaSuccess;
   ok &= cudaMemsetAsync(c->status, 0, 256, s) == cudaSuccess;
   ok &= cudaMemsetAsync(c->ws + y.gauss, 0, 256, s) == cudaSuccess;
+  if (y.flags) ok &= cudaMemsetAsync(c->ws + y.flags, 0, 256, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->ws + y.fbin, fbin.data(), sizeof(int16_t) * y.ld_pix,
                         cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(c->ws + y.finv, finv.data(), sizeof(float) * kFeat, cudaMemcpyHostToDevice,
@@ -511,6 +609,21 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
                                 (float4*)(ctx->ws + y.ql), (int16_t*)(ctx->ws + y.fbin),
                                 (int32_t*)(ctx->ws + y.dupsrc), (int32_t*)(ctx->ws + y.duprank),
                                 ctx->status, s));
+    CU(launch_fixed_geometry((const float4*)(ctx->ws + y.qh), (const float4*)(ctx->ws + y.ql),
+                             y.ld_pix, (int4*)(ctx->ws + y.qi), (float4*)(ctx->ws + y.qlo),
+                             nullptr, s));
+  }
+  if (ctx->prune) {
+    // the incremental bound of the next iteration holds for the frames of the
+    // last one only: flag counts that differ from the held copy (frames with
+    // counts above 256 are always flagged: their copy holds parts of them)
+    int32_t* changed = (int32_t*)(ctx->ws + y.flags);
+    if (ctx->frames_loaded && !(ctx->cfg.flags & EMC_FLAG_WIDE_COUNTS)) {
+      CU(launch_frames_differ(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, ctx->Kb, y.ld_pix,
+                              ctx->cfg.precision == EMC_PREC_FP16_SPLIT ? 1 : 0, changed, s));
+    } else {
+      CU(cudaMemsetAsync(changed, 1, sizeof(int32_t), s));
+    }
   }
   CU(launch_prep_frames(K, ld_k, ctx->cfg.n_data, ctx->cfg.n_pix, y.ld_data, y.ld_pix, ctx->Kb,
                         g ? 3 : (ctx->cfg.precision == EMC_PREC_FP16_SPLIT ? 1 : 0), dsrc, drank,
@@ -532,8 +645,8 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
       CU(launch_identity(ctx->perm, y.ld_data, s));
       CU(launch_identity(ctx->perm2, y.ld_data, s));
     } else if (ctx->order_pending) {
-      std::swap(ctx->perm, ctx->perm2);
-      ctx->order_pending = false;
+      int st = reorder_state(ctx, s);
+      if (st) return st;
     }
     CU(launch_permute_frames(ctx->perm, y.ld_data, y.ld_pix, ctx->Kb, (uint16_t*)(ctx->ws + y.Kp),
                              nsum, (float*)(ctx->ws + y.nsum_p), ctx->flu_cn,
@@ -561,11 +674,22 @@ int emc_set_frames(emc_ctx* ctx, const int32_t* K, int64_t ld_k, emc_stream stre
 // ---------------------------------------------------------------------------
 namespace {
 
+// Lold, bias_old (optional, Poisson model): the last iteration's L and bias;
+// the expansion then also writes the incremental bound's increments.
 int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L, double* bias,
-              cudaStream_t s) {
+              cudaStream_t s, const void* Lold = nullptr, const double* bias_old = nullptr) {
   const int64_t rows = round_up(nrot, 128);
   Planes p{L, rows * c->lay.ld_pix, c->lay.ld_pix};
   const bool g = is_gauss(&c->cfg);
+  if (!g && !is_flu(&c->cfg)) {
+    const Layout& y = c->lay;
+    CU(launch_expand_tile(c->geom, grid, (const RotFX*)(c->ws + y.rotfx) + rot0, c->logw + rot0,
+                          nrot, rows, c->cfg.precision, (float)c->cfg.w_floor, p, bias,
+                          (double*)(c->ws + y.epart), Lold, bias_old,
+                          Lold ? (uint16_t*)(c->ws + y.Dd) : nullptr, y.ntp,
+                          Lold ? (float*)(c->ws + y.bpm) : nullptr, c->status, s));
+    return EMC_OK;
+  }
   if (is_flu(&c->cfg)) {
     CU(launch_expand_flu(c->geom, grid, c->rot + rot0, c->logw + rot0, nrot, rows,
                          c->cfg.precision, (float)c->cfg.w_floor, c->flu_c, p, bias,
@@ -799,7 +923,7 @@ int emc_compress(emc_ctx* ctx, int64_t rot0, int64_t nrot, const float* Num, con
     CU(cudaMemsetAsync(g_num, 0, gb, s));
     CU(cudaMemsetAsync(g_den, 0, gb, s));
   }
-  CU(launch_compress(ctx->geom, ctx->rot + rot0, nrot, Num, den, ctx->cfg.compress_mode, g_num,
+  CU(launch_compress(ctx->geom, (const RotFX*)(ctx->ws + ctx->lay.rotfx) + rot0, nrot, Num, den, ctx->cfg.compress_mode, g_num,
                      g_den, 1, s));
   return EMC_OK;
 }
@@ -819,8 +943,12 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   cudaStream_t s = (cudaStream_t)stream;
   const Layout& y = c->lay;
   const int64_t n_rot = c->cfg.n_rot;
-  void* L = c->ws + y.L;
-  double* bias = (double*)(c->ws + y.bias);
+  // pruned contexts alternate between two L and bias buffers: the last
+  // iteration's stay for the incremental bound
+  const bool pr = c->prune;
+  const int lnew = pr ? 1 - c->lcur : 0;
+  void* L = c->ws + (lnew ? y.L2 : y.L);
+  double* bias = (double*)(c->ws + (lnew ? y.bias2 : y.bias));
   double* lse_m = (double*)(c->ws + y.lse_m);
   double* lse_s = (double*)(c->ws + y.lse_s);
   void* P = c->ws + y.P;
@@ -832,31 +960,40 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   const size_t gb = sizeof(double) * (size_t)c->cfg.N * c->cfg.N * c->cfg.N * c->lay.nrep;
   int kernels = 0;
   int st;
+  bool delta = false;  // the incremental bound ran
 
+  // the incremental bound runs when the last iteration left its tile bounds;
+  // for the Poisson model the expansion computes its increments on the way
+  const bool pruned = pr && c->perm_valid;
+  delta = pruned && c->ub_valid;
+  const void* Lold = delta ? c->ws + (lnew ? y.L : y.L2) : nullptr;
+  const double* bold = delta ? (const double*)(c->ws + (lnew ? y.bias : y.bias2)) : nullptr;
+  const bool fused = delta && !is_flu(&c->cfg);
   if (stats) CU(cudaEventRecord(c->ev[0], s));
-  if ((st = do_expand(c, grid_in, 0, n_rot, L, bias, s))) return st;
-  kernels += is_gauss(&c->cfg) ? 3 : 1;  // Gaussian: grid maximum and scales first
+  if ((st = do_expand(c, grid_in, 0, n_rot, L, bias, s, fused ? Lold : nullptr,
+                      fused ? bold : nullptr)))
+    return st;
+  // Gaussian: grid maximum and scales first; Poisson: the row tiles and the bias sums
+  kernels += is_gauss(&c->cfg) ? 3 : (is_flu(&c->cfg) ? 1 : 2);
   if (stats) CU(cudaEventRecord(c->ev[1], s));
   float* S = (c->cfg.flags & EMC_FLAG_STORE_SCORES) ? (float*)(c->ws + y.S) : nullptr;
   // bound-pruned pass 1 over the frames in their internal order
-  const bool pr = c->prune;
   const int64_t nmt = y.rows / 128, nnt = y.ld_data / 256;
   const uint16_t* Kp = pr ? (const uint16_t*)(c->ws + y.Kp) : nullptr;
   uint8_t* live = pr ? (uint8_t*)(c->ws + y.live) : nullptr;
-  const bool pruned = pr && c->perm_valid;
   double* lm = pr ? (double*)(c->ws + y.lsem_s) : lse_m;  // lse in the internal order
   double* ls = pr ? (double*)(c->ws + y.lses_s) : lse_s;
   const double* cn_p = y.cn_p ? (const double*)(c->ws + y.cn_p) : nullptr;
   if (pr && c->order_pending) {
-    // the order the previous iteration found: frames and their arrays follow it
-    std::swap(c->perm, c->perm2);
+    // the order the previous iteration found: frames, their arrays and the
+    // per-frame state of the incremental bound follow it
+    if ((st = reorder_state(c, s))) return st;
     CU(launch_permute_frames(c->perm, y.ld_data, y.ld_pix, c->Kb, (uint16_t*)(c->ws + y.Kp),
                              (const float*)(c->ws + y.nsum), (float*)(c->ws + y.nsum_p),
                              c->flu_cn, y.cn_p ? (double*)(c->ws + y.cn_p) : nullptr,
                              c->flu_invn, y.invn_p ? (float*)(c->ws + y.invn_p) : nullptr,
                              (int32_t*)(c->ws + y.iperm), s));
-    c->order_pending = false;
-    kernels++;
+    kernels += 3;
   }
   if (pr) {
     double* pm = (double*)(c->ws + y.part_m);
@@ -864,21 +1001,62 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     Planes p3{L, y.rows * y.ld_pix, y.ld_pix};
     int32_t* tlist = (int32_t*)(c->ws + y.tlist);
     int32_t* tcount = (int32_t*)(c->ws + y.tcount);
+    const float* nsum_p = (const float*)(c->ws + y.nsum_p);
     if (pruned) {
-      // bound: the hi plane alone (the first plane of L), per-tile maxima
+      // 1. the incremental bound from the last iteration (same frames, its L
+      //    and tile bounds kept): candidates for the hi-plane bound
+      uint8_t* cand = (uint8_t*)(c->ws + y.dcand);
+      uint8_t* pf = (uint8_t*)(c->ws + y.pflag);
+      int32_t* plist = (int32_t*)(c->ws + y.plist);
+      int32_t* pcount = tcount + 32;
+      const float* Cd = (const float*)(c->ws + y.Cd);
+      const float* bpm = (const float*)(c->ws + y.bpm);
+      if (delta) {
+        const int f16 = c->cfg.precision == EMC_PREC_FP16_SPLIT ? 1 : 0;
+        if (!fused) {  // Poisson-fluence: the increments from both L in a pass of their own
+          CU(launch_delta_planes((const uint16_t*)Lold, (const uint16_t*)L, y.rows * y.ld_pix,
+                                 y.ld_pix, n_rot, bold, bias, y.ntp, (uint16_t*)(c->ws + y.Dd),
+                                 (float*)bpm, f16, s));
+          kernels++;
+        }
+        Planes pd{c->ws + y.Dd, 3 * y.ntp * y.ld_pix, y.ld_pix};
+        CU(launch_tc_store(pd, 3 * y.ntp, Kp, y.ld_data, y.ld_pix, (float*)Cd, f16, c->status, s,
+                           c->tcctl));
+        kernels++;
+      }
+      CU(launch_delta_live(Cd, y.ntp, bpm, c->Ub, c->Ua, (double*)(c->ws + y.Lk), c->Mk,
+                           c->best,
+                           nsum_p, bound_div(&c->cfg), y.ld_pix, nmt, y.ld_data, c->cfg.n_data,
+                           delta ? 1 : 0,
+                           (const int32_t*)(c->ws + y.flags), cand, s));
+      // 2. the hi plane alone (the first plane of L) over the candidate pairs of
+      //    row tiles (none when the incremental bound is tighter everywhere):
+      //    per-tile maxima of S_hi
+      CU(launch_pair_flags(cand, nmt, nnt, pf, s));
+      CU(launch_tile_list(pf, (int)((nmt + 1) / 2), (int)nnt, 4, plist, pcount, s));
       CU(launch_tc_bound(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, y.ld_pix, pm,
-                         c->status, s, c->tcctl));
-      CU(launch_bound_live(pm, nmt, y.ld_data, c->cfg.n_data,
-                           (const float*)(c->ws + y.nsum_p), bound_div(&c->cfg), live, s));
+                         c->status, s, c->tcctl, plist, pcount));
+      // 3. both bounds together: the live tiles, listed for the exact pass
+      CU(launch_final_live(pm, pf, c->Ub, c->Ua, (double*)(c->ws + y.Lk), nsum_p,
+                           bound_div(&c->cfg),
+                           nmt, y.ld_data, c->cfg.n_data, live, s));
       CU(launch_tile_list(live, (int)nmt, (int)nnt, 8, tlist, tcount, s));
+      kernels += 6;
     }
     CU(launch_tc_pass1(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, c->cfg.n_data, y.ld_pix,
                        pm, ps, S, S + y.rows * y.ld_data, nullptr, nullptr, c->status, s,
                        pruned ? tlist : nullptr, pruned ? tcount : nullptr, c->tcctl));
+    // the merge also keeps, for the next iteration's incremental bound, every
+    // contracted tile's maximum (plus 1/64) in Ub, the frames' largest maxima and best tiles
     CU(launch_lse_merge(pm, ps, nmt, y.ld_data, c->cfg.n_data, lm, ls, 0, 0, c->status, s, cn_p,
-                        pruned ? live : nullptr, (int32_t*)(c->ws + y.best)));
+                        pruned ? live : nullptr, c->best, c->Ub, c->Mk, c->Ua));
     CU(launch_unpermute_lse(c->perm, c->cfg.n_data, lm, ls, lse_m, lse_s, s));
-    kernels += pruned ? 6 : 3;  // (bound, liveness, list,) pass 1, merge, lse order
+    // the frames are consumed; a device status recorded by now (a wait that
+    // gave up, a non-finite value) voids the tile bounds for the next iteration
+    CU(cudaMemsetAsync(c->ws + y.flags, 0, sizeof(int32_t), s));
+    CU(cudaMemcpyAsync(c->ws + y.flags + 8, c->status, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                       s));
+    kernels += 3;  // pass 1, merge, lse order
   } else {
     if ((st = do_loglik(c, L, y.rows, 0, bias, n_rot, lse_m, lse_s, 0, S, s))) return st;
     kernels += 2;
@@ -920,7 +1098,7 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     if (stats) CU(cudaEventRecord(c->ev[4], s));
     if ((st = do_update(c, P, crows, nr, Num, den, s, kbc, kbl, Kp))) return st;
     if (stats) CU(cudaEventRecord(c->ev[5], s));
-    CU(launch_compress(c->geom, c->rot + r0, nr, Num, den, c->cfg.compress_mode, gn, gd, y.nrep,
+    CU(launch_compress(c->geom, (const RotFX*)(c->ws + y.rotfx) + r0, nr, Num, den, c->cfg.compress_mode, gn, gd, y.nrep,
                        s));
     if (stats) CU(cudaEventRecord(c->ev[6], s));
     // normalize: lse split + the pass (one SIMT kernel when recomputing in FP32)
@@ -946,13 +1124,15 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     // rotation (counting sort, stable); applied when that iteration starts, so
     // that until then the stored scores, iperm and the live flags agree
     // (sort_frames writes positions below n_data only; the tails stay the identity)
-    CU(launch_sort_frames((const int32_t*)(c->ws + y.best), c->perm, c->cfg.n_data, (int)nmt,
+    CU(launch_sort_frames(c->best, c->perm, c->cfg.n_data, (int)nmt,
                           (int32_t*)(c->ws + y.sortH), (int64_t*)(c->ws + y.sortoff), c->perm2,
                           s));
     c->order_pending = true;
     c->perm_valid = true;
     c->scores_internal = true;
     c->last_pruned = pruned;
+    c->lcur = lnew;
+    c->ub_valid = true;
     kernels += 3;
   }
   if (stats) CU(cudaEventRecord(c->ev[7], s));
@@ -980,10 +1160,12 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     stats->pass1_tiles = nmt * nnt;
     stats->pass1_exact = nmt * nnt;
     if (pruned) {
-      int32_t cnt = 0;
-      CU(cudaMemcpy(&cnt, c->ws + y.tcount, sizeof(int32_t), cudaMemcpyDeviceToHost));
-      stats->pass1_exact = cnt;
+      int32_t cnt[33] = {0};
+      CU(cudaMemcpy(cnt, c->ws + y.tcount, sizeof(cnt), cudaMemcpyDeviceToHost));
+      stats->pass1_exact = cnt[0];
       stats->pass1_pruned = 1;
+      stats->pass1_delta = delta ? 1 : 0;
+      stats->pass1_bound_pairs = cnt[32];
     }
   }
   return EMC_OK;
@@ -1125,8 +1307,11 @@ int emc_sparse_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_
   if (!c->frames_loaded || !c->cand_loaded) return EMC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const Layout& y = c->lay;
-  void* L = c->ws + y.L;
-  double* bias = (double*)(c->ws + y.bias);
+  // pruned contexts: the buffer the last emc_iteration did not write, so that
+  // its L stays for the next one's incremental bound
+  const bool other = c->prune && c->lcur == 0;
+  void* L = c->ws + (other ? y.L2 : y.L);
+  double* bias = (double*)(c->ws + (other ? y.bias2 : y.bias));
   float* Pc = (float*)(c->ws + y.Pc);
   double* lsec = (double*)(c->ws + y.lsec);
   float* Num = (float*)(c->ws + y.Num);
@@ -1146,7 +1331,7 @@ int emc_sparse_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_
   if (stats) CU(cudaEventRecord(c->ev[3], s));
   CU(cudaMemsetAsync(gn, 0, gb, s));
   CU(cudaMemsetAsync(gd, 0, gb, s));
-  CU(launch_compress(c->geom, c->rot, c->cfg.n_rot, Num, den, c->cfg.compress_mode, gn, gd,
+  CU(launch_compress(c->geom, (const RotFX*)(c->ws + y.rotfx), c->cfg.n_rot, Num, den, c->cfg.compress_mode, gn, gd,
                      y.nrep, s));
   CU(launch_finalize((int64_t)c->cfg.N * c->cfg.N * c->cfg.N, gn, gd, y.nrep, grid_in, grid_out,
                      s));

@@ -11,11 +11,21 @@ namespace emc {
 // computed once per context on the host in FP64.
 struct RotDF;
 
+// Rotation R_j in fixed point for the e-step: R = hi 2^-20 + lo (hi integer,
+// |lo| <= 2^-21), row-major 3x3.
+struct RotFX {
+  int32_t hi[9];
+  float lo[9];
+};
+
 // Pixel geometry as stored in the workspace: positions q_i split into FP32
-// hi/lo pairs, w component 1 for a used pixel and 0 for padding.
+// hi/lo pairs, w component 1 for a used pixel and 0 for padding; the same in
+// fixed point for the e-step: q = qi 2^-12 + qlo (qi.w = the w component).
 struct Geom {
   const float4* qh;
   const float4* ql;
+  const int4* qi;
+  const float4* qlo;
   int64_t n_pix;
   int64_t ld_pix;
   int N;
@@ -29,6 +39,9 @@ struct Geom {
   const int32_t* gpix;
   const float4* gqh;
   const float4* gql;
+  const int4* gqi;    // the same in fixed point
+  const float4* gqlo;
+  const float4* gqf;  // gqi 2^-12 as FP32
 };
 constexpr int kCompressGroup = 64;
 constexpr double kCompressCell = 6.0;
@@ -62,6 +75,21 @@ cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
                           float w_floor, Planes L, double* bias, const float4* gsc, double sigma,
                           int32_t* status, cudaStream_t s);
+
+// Poisson model: the e-step per row tile of 128 rotations (expand_tile.cu).
+// partial: scratch of expand_tile_slices(ld_pix) x rows doubles. With Lold
+// (the last iteration's L, same layout) it also writes the incremental bound's
+// increments D ([2 ntp][ld_pix], rounded up to the frames' type), dabs[t] and,
+// from bias_old, bpm (as launch_delta_planes).
+int64_t expand_tile_slices(int64_t ld_pix);
+cudaError_t launch_expand_tile(const Geom& g, const float* grid, const RotFX* rot,
+                               const double* logw, int64_t nrot, int64_t rows, int precision,
+                               float w_floor, Planes L, double* bias, double* partial,
+                               const void* Lold, const double* bias_old, uint16_t* D, int64_t ntp,
+                               float* bpm, int32_t* status, cudaStream_t s);
+// qi, qlo (and qf = qi 2^-12 as FP32, if non-NULL) from qh, ql for ld_pix columns
+cudaError_t launch_fixed_geometry(const float4* qh, const float4* ql, int64_t ld_pix, int4* qi,
+                                  float4* qlo, float4* qf, cudaStream_t s);
 
 // Poisson-fluence model: L = log(W / B_j) + c as the BF16 three-term split
 // (precision EMC_PREC_BF16_SPLIT only); bias = double[2][rows]: log w_j, then
@@ -126,11 +154,57 @@ int64_t simt_pass1_tiles(int64_t rows);
 // (double[ld_data]), removed before the merge.
 // live (may be NULL): [n_tiles][ld_data / 256] flags of the contracted tiles
 // of a pruned pass 1; best (may be NULL): row tile of each frame's largest maximum.
+// Ub, Mk (may be NULL): for the incremental bound, every merged tile's maximum
+// + 1/64 into Ub[tile][frame] (rounded up to FP32) and each frame's largest
+// maximum, as the scores carry it (shift included), into Mk.
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
                              int accumulate, int gauss, int32_t* status, cudaStream_t s,
                              const double* shift = nullptr, const uint8_t* live = nullptr,
-                             int32_t* best = nullptr);
+                             int32_t* best = nullptr, float* Ub = nullptr, double* Mk = nullptr,
+                             float* Ua = nullptr);
+// ---- incremental bound between consecutive iterations (prune.cu) ----
+// D ([3 ntp][ld_pix], BF16, or FP16 when f16) rows t and ntp + t: max over the
+// tile's valid rows of L1 - L0 and of L0 - L1 (BF16 split: three planes; f16,
+// the FP16 split's two; plane stride `plane`), rows 2 ntp + t: a bound of both
+// magnitudes; all rounded up; bpm[t], bpm[nt + t] = the same maxima of the
+// bias change (b1 - b0), rounded up.
+cudaError_t launch_delta_planes(const uint16_t* L0, const uint16_t* L1, int64_t plane,
+                                int64_t ld_pix, int64_t nrot, const double* b0, const double* b1,
+                                int64_t ntp, uint16_t* D, float* bpm, int f16, cudaStream_t s);
+// Ub += C+ + b+ + err, Lk from Mk, best and C- (C = D K^T, rows t, ntp + t and
+// 2 ntp + t, the last giving err);
+// cand[t][nt] where Ub >= Lk - 111 and the widening exceeds the hi-plane
+// bound's 2 (N_k / div + 1); valid = 0, changed[0] or changed[2]: every tile
+// a candidate, Ub = +inf, Lk = -inf.
+// Ua: the widening gathered since each tile bound's last refresh (cleared by
+// the refreshes: the hi-plane bound in launch_final_live, the exact maxima in
+// the merge).
+cudaError_t launch_delta_live(const float* C, int64_t ntp, const float* bpm,
+                              float* Ub, float* Ua, double* Lk, const double* Mk,
+                              const int32_t* best,
+                              const float* nsum, float div, int64_t ld_pix, int64_t n_mtiles,
+                              int64_t ld_data, int64_t n_data, int valid,
+                              const int32_t* changed, uint8_t* cand, cudaStream_t s);
+// pf[mp][nt] = cand[2 mp][nt] | cand[2 mp + 1][nt]
+cudaError_t launch_pair_flags(const uint8_t* cand, int64_t n_mtiles, int64_t nnt, uint8_t* pf,
+                              cudaStream_t s);
+// hi-plane maxima of the flagged pairs tighten Ub and Lk; live[t][nt] where Ub >= Lk - 111
+cudaError_t launch_final_live(const double* part_m, const uint8_t* pf, float* Ub, float* Ua,
+                              double* Lk,
+                              const float* nsum, float div, int64_t n_mtiles, int64_t ld_data,
+                              int64_t n_data, uint8_t* live, cudaStream_t s);
+// Ub2, Mk2, best2 = Ub, Mk, best at each frame's old position
+// (src[pos] = iperm_old[perm_new[pos]])
+cudaError_t launch_reorder_state(const int32_t* perm_new, const int32_t* iperm_old, int64_t n_data,
+                                 int64_t ld_data, int64_t n_mtiles, int32_t* src, const float* Ub,
+                                 float* Ub2, const float* Ua, float* Ua2, const double* Mk,
+                                 double* Mk2, const int32_t* best, int32_t* best2,
+                                 cudaStream_t s);
+// *flag = 1 if any count of K (columns < n_pix) differs from the BF16 (FP16) copy Kb
+cudaError_t launch_frames_differ(const int32_t* K, int64_t ld_k, int64_t n_data, int64_t n_pix,
+                                 const uint16_t* Kb, int64_t ld_pix, int fp16, int32_t* flag,
+                                 cudaStream_t s);
 // shift (may be NULL): added back to lse before the split.
 cudaError_t launch_lse_split(const double* lse_m, const double* lse_s, int64_t n_data,
                              int64_t ld_data, float2* out, cudaStream_t s,
@@ -186,21 +260,25 @@ cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const
                              int32_t* status, cudaStream_t s, const int32_t* kb_cnt = nullptr,
                              const int32_t* kb_list = nullptr, TcCtl ctl = TcCtl{});
 int64_t tc_pass1_tiles(int64_t rows);
-// C (float[rows][ld_data]) = A Kb^T over ld_pix columns, A one BF16 plane of
-// rows (a multiple of 128) x ld_pix, Kb BF16 [ld_data][ld_pix]: a plain
-// tensor-core product, FP32 accumulation, stored as it is.
+// C (float[rows][ld_data]) = A Kb^T over ld_pix columns, A one plane of rows
+// (a multiple of 128) x ld_pix, Kb [ld_data][ld_pix], both BF16 (or both FP16
+// when f16): a plain tensor-core product, FP32 accumulation, stored as it is.
 cudaError_t launch_tc_store(const Planes& A, int64_t rows, const uint16_t* Kb, int64_t ld_data,
-                            int64_t ld_pix, float* C, int32_t* status, cudaStream_t s,
+                            int64_t ld_pix, float* C, int f16, int32_t* status, cudaStream_t s,
                             TcCtl ctl = TcCtl{});
 // Bound pass of the pruned pass 1: per 128-row tile and frame, the maximum of
 // S^hi = (first plane of L) K^T + bias into part_m[rows / 128][ld_data]
 // (pairs of row tiles per CTA tile sharing the frame operand).
+// pair_list, pair_count (device, optional): contract only the listed pairs,
+// codes mp * (ld_data / 256) + nt for row tiles 2 mp and 2 mp + 1.
 cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t ld_pix, double* part_m,
-                            int32_t* status, cudaStream_t s, TcCtl ctl = TcCtl{});
+                            int32_t* status, cudaStream_t s, TcCtl ctl = TcCtl{},
+                            const int32_t* pair_list = nullptr,
+                            const int32_t* pair_count = nullptr);
 
 // nrep grid replicas of n_vox each (row j reduces into replica j mod nrep)
-cudaError_t launch_compress(const Geom& g, const RotDF* rot, int64_t nrot, const float* Num,
+cudaError_t launch_compress(const Geom& g, const RotFX* rot, int64_t nrot, const float* Num,
                             const float* den, int mode, double* g_num, double* g_den, int nrep,
                             cudaStream_t s);
 // grid_out = (sum of nrep numerator replicas) / (sum of denominator replicas)
@@ -280,12 +358,6 @@ cudaError_t launch_lse_values(const double* m, const double* sm, int64_t n, doub
                               cudaStream_t s);
 
 // ---- pruned pass 1 and the frame order (prune.cu) ----
-// live[mt * (ld_data / 256) + nt] from the hi-plane tile maxima part_m (frames
-// in the internal order), the frame totals nsum and the bound's divisor
-// (|S - S_hi| <= nsum / div + 1)
-cudaError_t launch_bound_live(const double* part_m, int64_t n_mtiles, int64_t ld_data,
-                              int64_t n_data, const float* nsum, float div, uint8_t* live,
-                              cudaStream_t s);
 cudaError_t launch_tile_list(const uint8_t* live, int n_mtiles, int n_ntiles, int group,
                              int32_t* list, int32_t* count, cudaStream_t s);
 // entries of the histogram scratch H (int32) of launch_sort_frames; off needs one more (int64)

@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(256)
                      int64_t n_tiles, int64_t ld_data, int64_t n_data, double* __restrict__ lse_m,
                      double* __restrict__ lse_s, int accumulate, double clamp,
                      const double* __restrict__ shift, const uint8_t* __restrict__ live,
-                     int64_t nnt, int32_t* __restrict__ best, int32_t* status) {
+                     int64_t nnt, int32_t* __restrict__ best, int32_t* status,
+                     float* __restrict__ Ub, double* __restrict__ Mk, float* __restrict__ Ua) {
   // 32 frames (lanes) x 8 strides of tiles (warps); partials combined in stride order
   __shared__ double rm[8][32], rs[8][32];
   __shared__ int rb[8][32];
@@ -268,7 +269,13 @@ __global__ void __launch_bounds__(256)
   if (ok)
     for (int64_t t = r; t < n_tiles; t += 8) {
       if (lv && !lv[t * nnt]) continue;
-      const double m = part_m[t * ld_data + k] - sh;
+      const double pmv = part_m[t * ld_data + k];
+      // the tile's scores lie within 1/128 of its maximum on the 1/64 grid
+      if (Ub) {
+        Ub[t * ld_data + k] = __double2float_ru(pmv + 1.0 / 64.0);
+        Ua[t * ld_data + k] = 0.f;
+      }
+      const double m = pmv - sh;
       if (m > mt) {
         mt = m;
         tbest = (int)t;
@@ -303,6 +310,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (r != 0 || !ok) return;
   if (best) best[k] = tbest;
+  if (Mk) Mk[k] = mt + sh;
   if (Mn == -INFINITY) {  // nothing seen yet
     lse_m[k] = M;
     lse_s[k] = S;
@@ -320,11 +328,12 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_lse_merge(const double* part_m, const float* part_s, int64_t n_tiles,
                              int64_t ld_data, int64_t n_data, double* lse_m, double* lse_s,
                              int accumulate, int gauss, int32_t* status, cudaStream_t s,
-                             const double* shift, const uint8_t* live, int32_t* best) {
+                             const double* shift, const uint8_t* live, int32_t* best, float* Ub,
+                             double* Mk, float* Ua) {
   unsigned blocks = (unsigned)((n_data + 31) / 32);
   lse_merge_kernel<<<blocks, 256, 0, s>>>(part_m, part_s, n_tiles, ld_data, n_data, lse_m, lse_s,
                                           accumulate, gauss ? -(double)kGaussClamp : -INFINITY,
-                                          shift, live, ld_data / 256, best, status);
+                                          shift, live, ld_data / 256, best, status, Ub, Mk, Ua);
   return cudaGetLastError();
 }
 

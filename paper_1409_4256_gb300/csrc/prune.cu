@@ -14,6 +14,18 @@
 // frame tile) pairs are skipped by the exact contraction; lse and P are those
 // of the full one.
 //
+// In general terms: with an upper bound Ub_tk >= max_{j in t} S_jk for every
+// row tile and a lower bound Lk <= max_j S_jk, a tile with Ub_tk < Lk - 111
+// for every frame of a frame tile is skipped. Three stages give the bounds:
+//  1. from the last iteration on the same frames (its exact tile maxima and
+//     bounds, kept in Ub): the incremental bound below, for every tile, at
+//     1/128 of the hi-plane contraction's work;
+//  2. the hi-plane contraction over the pairs of row tiles that stage 1 could
+//     not rule out (every pair on the first pruned pass, or after new frames):
+//     Ub = min(Ub, S^hi max + E_k), Lk = max(Lk, S^hi max - E_k);
+//  3. the exact three-plane contraction of the tiles left live, whose maxima
+//     (plus 1/64) replace their bounds for the next iteration.
+//
 // Frames are kept in an order that groups them by the row tile of their best
 // rotation (rotations are numbered along a space-filling curve, so a row tile
 // is a compact region of SO(3)): the frames of a 256-frame tile then share
@@ -24,36 +36,6 @@
 #include "emc_internal.h"
 
 namespace emc {
-
-// One CTA per 32 frames (lanes) x 8 strides of row tiles (warps): the threshold
-// of each frame from the maxima over every row tile, then, for each row tile, a
-// ballot over the warp's 32 frames; a tile with a frame above its threshold sets
-// live[mt * nnt + nt] = 1 (live is zeroed first; eight CTAs share a frame tile).
-__global__ void __launch_bounds__(256)
-    bound_live_kernel(const double* __restrict__ part_m, int64_t n_mtiles, int64_t ld_data,
-                      int64_t n_data, const float* __restrict__ nsum, float div,
-                      uint8_t* __restrict__ live) {
-  __shared__ double red[8][32];
-  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
-  const int64_t s = (int64_t)blockIdx.x * 32 + lane;
-  const int64_t nnt = ld_data / 256;
-  const bool ok = s < n_data;
-  double M = -INFINITY;
-  if (ok)
-    for (int64_t mt = r; mt < n_mtiles; mt += 8) M = fmax(M, part_m[mt * ld_data + s]);
-  red[r][lane] = M;
-  __syncthreads();
-  double thr = INFINITY;  // padding frames never make a tile live
-  if (ok) {
-    M = red[0][lane];
-    for (int q = 1; q < 8; q++) M = fmax(M, red[q][lane]);
-    thr = M - (2.0 * ((double)nsum[s] / (double)div + 1.0) + 111.0);
-  }
-  for (int64_t mt = r; mt < n_mtiles; mt += 8) {
-    const bool on = ok && part_m[mt * ld_data + s] >= thr;
-    if (__any_sync(0xffffffffu, on) && lane == 0) live[mt * nnt + (s >> 8)] = 1;
-  }
-}
 
 // One CTA: the live tiles in the raster order of the dense kernel (groups of
 // `group` row tiles, frame tiles within a group, row tiles within those) into
@@ -187,16 +169,6 @@ __global__ void unpermute_lse_kernel(const int32_t* __restrict__ perm, int64_t n
   s[k] = s_s[pos];
 }
 
-cudaError_t launch_bound_live(const double* part_m, int64_t n_mtiles, int64_t ld_data,
-                              int64_t n_data, const float* nsum, float div, uint8_t* live,
-                              cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(live, 0, (size_t)n_mtiles * (ld_data / 256), s);
-  if (e != cudaSuccess) return e;
-  bound_live_kernel<<<(unsigned)(ld_data / 32), 256, 0, s>>>(part_m, n_mtiles, ld_data, n_data,
-                                                              nsum, div, live);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_tile_list(const uint8_t* live, int n_mtiles, int n_ntiles, int group,
                              int32_t* list, int32_t* count, cudaStream_t s) {
   tile_list_kernel<<<1, 1024, 0, s>>>(live, n_mtiles, n_ntiles, group, list, count);
@@ -269,31 +241,39 @@ cudaError_t launch_unpermute_lse(const int32_t* perm, int64_t n_data, const doub
 // work). The FP32 accumulation of sum_i K_ik D_ti errs by at most
 // (ld_pix + 8) 2^-23 N_k max_i |D_ti| (products of an integer count <= 256
 // and a BF16 value are exact in FP32; every addition rounds by at most one
-// unit of 2^-23 of a partial sum bounded by N_k max|D|), which is added.
+// unit of 2^-23 of a partial sum, and every partial sum is bounded by
+// sum_i K_ik A_ti, A_ti = max(|D+_ti|, |D-_ti|)), which is added: A is
+// contracted with the increments, as a third block of rows.
 // ---------------------------------------------------------------------------
 
-// Next BF16 value >= x (x finite).
-__device__ __forceinline__ uint16_t bf16_up_bits(float x) {
-  const uint32_t u = __float_as_uint(x);
-  const uint32_t h = u >> 16;
-  if ((u & 0xFFFFu) == 0u) return (uint16_t)h;
-  // x > 0: the next magnitude up; x < 0: truncation moves towards zero, i.e. up
-  return (uint16_t)((u & 0x80000000u) ? h : h + 1u);
-}
+// One plane value of L: BF16 or FP16 bits.
+template <bool F16>
 __device__ __forceinline__ float plane_val(const uint16_t* p, int64_t o) {
+  if (F16) return __half2float(*reinterpret_cast<const __half*>(p + o));
   return __uint_as_float(((uint32_t)p[o]) << 16);
+}
+// The next BF16 (FP16) value >= x, as bits: the operand type of the frames.
+template <bool F16>
+__device__ __forceinline__ uint16_t round_up_bits(float x) {
+  if (F16) {
+    __half h = __float2half_ru(x);
+    return *reinterpret_cast<uint16_t*>(&h);
+  }
+  __nv_bfloat16 b = __float2bfloat16_ru(x);
+  return *reinterpret_cast<uint16_t*>(&b);
 }
 
 // One CTA per (pixel slice of 256 columns, row tile): each thread a pixel,
-// the tile's valid rows in turn. D = BF16 [2 ntp][ld_pix]: rows t (D+) and
-// ntp + t (D-); dabs[t] = max_i max(|D+_ti|, |D-_ti|) (unsigned bits of a
-// non-negative float, atomically maximised; zeroed first); bpm[t], bpm[nt +
-// t] = b+_t, b-_t (rounded up), written by the CTAs of the first slice.
+// the tile's valid rows in turn. D = [3 ntp][ld_pix]: rows t (D+), ntp + t
+// (D-) and 2 ntp + t (A = max(|D+|, |D-|)), all rounded up to the frames'
+// operand type; bpm[t], bpm[nt + t] = b+_t, b-_t (rounded up), written by the
+// CTAs of the first slice.
+template <int NP, bool F16>
 __global__ void __launch_bounds__(256)
     delta_planes_kernel(const uint16_t* __restrict__ L0, const uint16_t* __restrict__ L1,
                         int64_t plane, int64_t ld_pix, int64_t nrot, const double* __restrict__ b0,
                         const double* __restrict__ b1, int64_t ntp, uint16_t* __restrict__ D,
-                        unsigned* __restrict__ dabs, float* __restrict__ bpm, int64_t nt) {
+                        float* __restrict__ bpm, int64_t nt) {
   const int64_t t = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int64_t r0 = t * 128;
@@ -302,22 +282,22 @@ __global__ void __launch_bounds__(256)
   if (i < ld_pix) {
     for (int64_t j = r0; j < r1; j++) {
       const int64_t o = j * ld_pix + i;
-      // differences of each plane are exact in FP32; their sum rounds once or twice
-      const float d = (plane_val(L1, o) - plane_val(L0, o)) +
-                      (plane_val(L1, o + plane) - plane_val(L0, o + plane)) +
-                      (plane_val(L1, o + 2 * plane) - plane_val(L0, o + 2 * plane));
+      // the difference of each plane is exact in FP32; their sum rounds at most twice
+      float d = plane_val<F16>(L1, o) - plane_val<F16>(L0, o);
+#pragma unroll
+      for (int q = 1; q < NP; q++) d += plane_val<F16>(L1, o + q * plane) - plane_val<F16>(L0, o + q * plane);
       dp = fmaxf(dp, d);
       dm = fmaxf(dm, -d);
     }
-    // one FP32 rounding of a sum of three exact terms: 2^-23 |d| covers it
+    // those roundings: 2^-23 |d| covers them
     dp += 2.0f * 1.1920929e-7f * fabsf(dp);
     dm += 2.0f * 1.1920929e-7f * fabsf(dm);
-    D[t * ld_pix + i] = bf16_up_bits(dp);
-    D[(ntp + t) * ld_pix + i] = bf16_up_bits(dm);
+    const uint16_t up = round_up_bits<F16>(dp), um = round_up_bits<F16>(dm);
+    D[t * ld_pix + i] = up;
+    D[(ntp + t) * ld_pix + i] = um;
+    // A bounds the magnitude of both rounded values
+    D[(2 * ntp + t) * ld_pix + i] = round_up_bits<F16>(fmaxf(fabsf(dp), fabsf(dm)) * 1.0078125f);
   }
-  float a = i < ld_pix ? fmaxf(fabsf(dp), fabsf(dm)) * 1.0078125f : 0.f;  // BF16 rounding up
-  for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(dabs + t, __float_as_uint(a));
   if (blockIdx.x == 0 && threadIdx.x < 128) {
     __shared__ double rb[2][128];
     const int64_t j = r0 + threadIdx.x;
@@ -339,46 +319,60 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Per frame (lanes) and row tile (warp strides), with C = [D+; D-] K^T of the
-// frames in the current internal order (rows t and ntp + t):
-//   Ub[t][k] += C+[t][k] + b+_t + err_tk        (err = errc N_k dabs_t)
+// Per frame (lanes) and row tile (warp strides), with C = [D+; D-; A] K^T of
+// the frames in the current internal order (rows t, ntp + t, 2 ntp + t):
+//   Ub[t][k] += C+[t][k] + b+_t + err_tk        (err = errc (1 + errc) CA[t][k])
 //   Lk[k] = Mk[k] - 1/64 - (C-[t*][k] + b-_t* + err_t*k),   t* = best[k]
 // Mk: the last iteration's largest exact tile maximum (its scores are within
-// 1/128 of it), t* its row tile, so Lk <= max_j S_jk now. A tile is a
-// candidate for the hi-plane bound (cand[t][nt] = 1) when Ub >= Lk - 111.
-// invalid (host flag, or *changed set by emc_set_frames when the counts
-// differ from the last ones): Ub = +inf, Lk = -inf and every tile a candidate.
+// 1/128 of it), t* its row tile, so Lk <= max_j S_jk now. A tile that this
+// does not rule out (Ub >= Lk - 111) is a candidate for the hi-plane bound
+// (cand[t][nt] = 1) only where that bound could do better: where the
+// widening the incremental bound has gathered since the tile's bound was last
+// refreshed (Ua, the C+ terms summed over iterations), plus this iteration's
+// C- term, exceeds the hi-plane bound's 2 E_k = 2 (N_k / div + 1). Otherwise
+// it goes to the exact pass. Both refresh the bound and clear Ua.
+// invalid (host flag; changed[0], set by emc_set_frames when the counts
+// differ from the last ones; or changed[2], the device status the last pass
+// left): Ub = +inf, Lk = -inf and every tile a candidate.
 __global__ void __launch_bounds__(256)
     delta_live_kernel(const float* __restrict__ C, int64_t ntp, const float* __restrict__ bpm,
-                      const unsigned* __restrict__ dabs, float* __restrict__ Ub,
-                      double* __restrict__ Lk, const double* __restrict__ Mk,
+                      float* __restrict__ Ub,
+                      float* __restrict__ Ua, double* __restrict__ Lk,
+                      const double* __restrict__ Mk,
                       const int32_t* __restrict__ best, const float* __restrict__ nsum,
-                      double errc, int64_t n_mtiles, int64_t ld_data, int64_t n_data,
-                      int valid_host, const int32_t* __restrict__ changed,
+                      double errc, float div, int64_t n_mtiles, int64_t ld_data,
+                      int64_t n_data, int valid_host, const int32_t* __restrict__ changed,
                       uint8_t* __restrict__ cand) {
   const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
   const int64_t k = (int64_t)blockIdx.x * 32 + lane;
   const int64_t nnt = ld_data / 256;
   const bool ok = k < n_data;
-  const bool valid = valid_host && !(changed && *changed);
-  double L = -INFINITY;
+  const bool valid = valid_host && !(changed && (changed[0] || changed[2]));
+  double L = -INFINITY, wl = 0.0;
+  const double E2 = ok ? 2.0 * ((double)nsum[k] / (double)div + 1.0) : 0.0;
   if (ok && valid) {
     const int tb = best[k];
-    const double e = errc * (double)nsum[k] * (double)__uint_as_float(dabs[tb]);
-    L = Mk[k] - 1.0 / 64.0 - ((double)C[(ntp + tb) * ld_data + k] + (double)bpm[n_mtiles + tb] + e);
+    const double e = errc * (double)C[(2 * ntp + tb) * ld_data + k];
+    wl = (double)C[(ntp + tb) * ld_data + k] + (double)bpm[n_mtiles + tb] + e + 1.0 / 64.0;
+    L = Mk[k] - wl;
   }
   if (ok && r == 0) Lk[k] = L;
   for (int64_t t = r; t < n_mtiles; t += 8) {
     bool on = ok;
     if (ok) {
       float* u = Ub + t * ld_data + k;
+      float* ua = Ua + t * ld_data + k;
       if (valid) {
-        const double e = errc * (double)nsum[k] * (double)__uint_as_float(dabs[t]);
-        const double U = (double)*u + (double)C[t * ld_data + k] + (double)bpm[t] + e;
+        const double e = errc * (double)C[(2 * ntp + t) * ld_data + k];
+        const double wu = (double)C[t * ld_data + k] + (double)bpm[t] + e;
+        const double U = (double)*u + wu;
+        const double acc = (double)*ua + fmax(wu, 0.0);
         *u = __double2float_ru(U);
-        on = U >= L - 111.0;
+        *ua = (float)acc;
+        on = U >= L - 111.0 && acc + wl > E2;
       } else {
         *u = INFINITY;
+        *ua = 0.f;
       }
     }
     if (__any_sync(0xffffffffu, on) && lane == 0) cand[t * nnt + (k >> 8)] = 1;
@@ -407,7 +401,7 @@ __global__ void pair_flags_kernel(const uint8_t* __restrict__ cand, int64_t n_mt
 // 111 below its frame's best (P = 0 in FP32, no weight in lse at FP64).
 __global__ void __launch_bounds__(256)
     final_live_kernel(const double* __restrict__ part_m, const uint8_t* __restrict__ pf,
-                      float* __restrict__ Ub, double* __restrict__ Lk,
+                      float* __restrict__ Ub, float* __restrict__ Ua, double* __restrict__ Lk,
                       const float* __restrict__ nsum, float div, int64_t n_mtiles,
                       int64_t ld_data, int64_t n_data, uint8_t* __restrict__ live) {
   __shared__ double red[8][32];
@@ -422,7 +416,11 @@ __global__ void __launch_bounds__(256)
       if (!pf[(t >> 1) * nnt + (k >> 8)]) continue;
       const double m = part_m[t * ld_data + k];
       float* u = Ub + t * ld_data + k;
-      *u = fminf(*u, __double2float_ru(m + E));
+      const float h = __double2float_ru(m + E);
+      if (h < *u) {  // the hi-plane bound is the tighter one: refreshed
+        *u = h;
+        Ua[t * ld_data + k] = 0.f;
+      }
       L = fmax(L, m - E);
     }
   red[r][lane] = L;
@@ -451,7 +449,8 @@ __global__ void order_src_kernel(const int32_t* __restrict__ perm_new,
 // y == 0 also moves Mk and best.
 __global__ void gather_state_kernel(const int32_t* __restrict__ src, int64_t n_data,
                                     int64_t ld_data, const float* __restrict__ Ub,
-                                    float* __restrict__ Ub2, const double* __restrict__ Mk,
+                                    float* __restrict__ Ub2, const float* __restrict__ Ua,
+                                    float* __restrict__ Ua2, const double* __restrict__ Mk,
                                     double* __restrict__ Mk2, const int32_t* __restrict__ best,
                                     int32_t* __restrict__ best2) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -459,6 +458,7 @@ __global__ void gather_state_kernel(const int32_t* __restrict__ src, int64_t n_d
   const int64_t t = blockIdx.y;
   const int64_t q = src[p];
   Ub2[t * ld_data + p] = Ub[t * ld_data + q];
+  Ua2[t * ld_data + p] = Ua[t * ld_data + q];
   if (t == 0) {
     Mk2[p] = Mk[q];
     best2[p] = best[q];
@@ -485,28 +485,32 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_delta_planes(const uint16_t* L0, const uint16_t* L1, int64_t plane,
                                 int64_t ld_pix, int64_t nrot, const double* b0, const double* b1,
-                                int64_t ntp, uint16_t* D, unsigned* dabs, float* bpm,
-                                cudaStream_t s) {
+                                int64_t ntp, uint16_t* D, float* bpm, int f16, cudaStream_t s) {
   const int64_t nt = (nrot + 127) / 128;
-  cudaError_t e = cudaMemsetAsync(dabs, 0, sizeof(unsigned) * (size_t)nt, s);
-  if (e != cudaSuccess) return e;
   dim3 grd((unsigned)((ld_pix + 255) / 256), (unsigned)nt);
-  delta_planes_kernel<<<grd, 256, 0, s>>>(L0, L1, plane, ld_pix, nrot, b0, b1, ntp, D, dabs, bpm,
-                                          nt);
+  if (f16)  // FP16 split: hi + rest
+    delta_planes_kernel<2, true><<<grd, 256, 0, s>>>(L0, L1, plane, ld_pix, nrot, b0, b1, ntp, D,
+                                                     bpm, nt);
+  else      // BF16 split: hi + mid + lo
+    delta_planes_kernel<3, false><<<grd, 256, 0, s>>>(L0, L1, plane, ld_pix, nrot, b0, b1, ntp, D,
+                                                      bpm, nt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_delta_live(const float* C, int64_t ntp, const float* bpm, const unsigned* dabs,
-                              float* Ub, double* Lk, const double* Mk, const int32_t* best,
-                              const float* nsum, int64_t ld_pix, int64_t n_mtiles,
+cudaError_t launch_delta_live(const float* C, int64_t ntp, const float* bpm,
+                              float* Ub, float* Ua, double* Lk, const double* Mk,
+                              const int32_t* best,
+                              const float* nsum, float div, int64_t ld_pix, int64_t n_mtiles,
                               int64_t ld_data, int64_t n_data, int valid,
                               const int32_t* changed, uint8_t* cand, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(cand, 0, (size_t)n_mtiles * (ld_data / 256), s);
   if (e != cudaSuccess) return e;
-  const double errc = (double)(ld_pix + 8) * 0x1p-23;
-  delta_live_kernel<<<(unsigned)(ld_data / 32), 256, 0, s>>>(C, ntp, bpm, dabs, Ub, Lk, Mk, best,
-                                                             nsum, errc, n_mtiles, ld_data, n_data,
-                                                             valid, changed, cand);
+  // accumulation error per unit of sum_i K |D|, and the FP32 error of that sum itself
+  const double ec = (double)(ld_pix + 8) * 0x1p-23;
+  const double errc = ec * (1.0 + ec);
+  delta_live_kernel<<<(unsigned)(ld_data / 32), 256, 0, s>>>(C, ntp, bpm, Ub, Ua, Lk, Mk, best,
+                                                             nsum, errc, div, n_mtiles, ld_data,
+                                                             n_data, valid, changed, cand);
   return cudaGetLastError();
 }
 
@@ -517,26 +521,28 @@ cudaError_t launch_pair_flags(const uint8_t* cand, int64_t n_mtiles, int64_t nnt
   return cudaGetLastError();
 }
 
-cudaError_t launch_final_live(const double* part_m, const uint8_t* pf, float* Ub, double* Lk,
+cudaError_t launch_final_live(const double* part_m, const uint8_t* pf, float* Ub, float* Ua,
+                              double* Lk,
                               const float* nsum, float div, int64_t n_mtiles, int64_t ld_data,
                               int64_t n_data, uint8_t* live, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(live, 0, (size_t)n_mtiles * (ld_data / 256), s);
   if (e != cudaSuccess) return e;
-  final_live_kernel<<<(unsigned)(ld_data / 32), 256, 0, s>>>(part_m, pf, Ub, Lk, nsum, div,
+  final_live_kernel<<<(unsigned)(ld_data / 32), 256, 0, s>>>(part_m, pf, Ub, Ua, Lk, nsum, div,
                                                              n_mtiles, ld_data, n_data, live);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reorder_state(const int32_t* perm_new, const int32_t* iperm_old, int64_t n_data,
                                  int64_t ld_data, int64_t n_mtiles, int32_t* src, const float* Ub,
-                                 float* Ub2, const double* Mk, double* Mk2, const int32_t* best,
-                                 int32_t* best2, cudaStream_t s) {
+                                 float* Ub2, const float* Ua, float* Ua2, const double* Mk,
+                                 double* Mk2, const int32_t* best, int32_t* best2,
+                                 cudaStream_t s) {
   const unsigned nb = (unsigned)((n_data + 255) / 256);
   order_src_kernel<<<nb, 256, 0, s>>>(perm_new, iperm_old, n_data, src);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gather_state_kernel<<<dim3(nb, (unsigned)n_mtiles), 256, 0, s>>>(src, n_data, ld_data, Ub, Ub2,
-                                                                   Mk, Mk2, best, best2);
+                                                                   Ua, Ua2, Mk, Mk2, best, best2);
   return cudaGetLastError();
 }
 

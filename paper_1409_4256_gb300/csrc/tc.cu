@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int T = a.n_mtiles * a.n_ntiles;
+  const int T = a.tile_count ? *a.tile_count : a.n_mtiles * a.n_ntiles;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer --
@@ -829,7 +829,8 @@ int64_t tc_pass1_tiles(int64_t rows) { return rows / BM; }
 
 cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, int64_t rows,
                             const uint16_t* Kb, int64_t ld_data, int64_t ld_pix, double* part_m,
-                            int32_t* status, cudaStream_t s, TcCtl ctl) {
+                            int32_t* status, cudaStream_t s, TcCtl ctl, const int32_t* pair_list,
+                            const int32_t* pair_count) {
   const bool f16 = precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
   if (!maps_scores(L, 1, f16, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
@@ -845,6 +846,8 @@ cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, 
   a.status = status;
   if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
   a.stall = ctl.stall;
+  a.tile_list = pair_list;
+  a.tile_count = pair_list ? pair_count : nullptr;
   constexpr int kStage = 2 * BM * 64 * 2 + BN * 64 * 2;
   constexpr int kStages = (kSmemBudget - kScratchBytes - 1024 - 256) / kStage;
   constexpr int kSmem = 1024 + kStages * kStage + 256 + kScratchBytes;
@@ -860,7 +863,8 @@ cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, 
   }
   const int T = a.n_mtiles * a.n_ntiles;
   if (T <= 0) return cudaSuccess;
-  const int grid = T < num_sms() ? T : num_sms();
+  // a device-side pair list: one persistent CTA per SM (the count is read on the device)
+  const int grid = (!pair_list && T < num_sms()) ? T : num_sms();
   if (f16)
     tc_bound_kernel<true><<<grid, kThreads, kSmem, s>>>(mA, mB, a);
   else
@@ -869,9 +873,11 @@ cudaError_t launch_tc_bound(const Planes& L, int precision, const double* bias, 
 }
 
 cudaError_t launch_tc_store(const Planes& A, int64_t rows, const uint16_t* Kb, int64_t ld_data,
-                            int64_t ld_pix, float* C, int32_t* status, cudaStream_t s, TcCtl ctl) {
+                            int64_t ld_pix, float* C, int f16, int32_t* status, cudaStream_t s,
+                            TcCtl ctl) {
   CUtensorMap mA, mB;
-  if (!maps_scores(A, 1, false, rows, Kb, ld_data, ld_pix, &mA, &mB)) return cudaErrorInvalidValue;
+  if (!maps_scores(A, 1, f16 != 0, rows, Kb, ld_data, ld_pix, &mA, &mB))
+    return cudaErrorInvalidValue;
   TcArgs a = base_args(rows, (int)(ld_data / BN), (int)(ld_pix / 64));
   a.nrot = rows;
   a.ld_data = ld_data;
@@ -880,6 +886,8 @@ cudaError_t launch_tc_store(const Planes& A, int64_t rows, const uint16_t* Kb, i
   a.status = status;
   if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
   a.stall = ctl.stall;
+  // A and B of one MMA always share their type: FP16 frames take FP16 increments
+  if (f16) return launch<MODE_STORE, 1, true>(mA, mB, a, s);
   return launch<MODE_STORE, 1, false>(mA, mB, a, s);
 }
 

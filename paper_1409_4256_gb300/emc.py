@@ -60,7 +60,7 @@ class IterStats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("device_status", ctypes.c_int32),
                 ("kernels", ctypes.c_int32), ("pass1_tiles", ctypes.c_int64),
                 ("pass1_exact", ctypes.c_int64), ("pass1_pruned", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("pass1_delta", ctypes.c_int32), ("pass1_bound_pairs", ctypes.c_int64)]
 
 
 _vp, _i64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int

@@ -298,3 +298,74 @@ def test_trained_proposal_beats_untrained(torch_cuda, oracle):
     after = recall(prop)
     assert hist[-1] < hist[0]
     assert after > before + 0.1 and after > 2 * M / nrot, (before, after, hist[0], hist[-1])
+
+
+def test_schedules_with_and_without_the_network(torch_cuda):
+    """The learned schedule against the same schedule without the network, at
+    equal M: candidates = the last dense E-step's top R plus the network's best
+    others, plus random rotations instead, or the dense E-step's own top M;
+    4 sparse iterations per dense one, 10 iterations from the same model. Each
+    is held to the target's 1e-3 (model rel-L2 against the dense iterations);
+    the printed missed mass at the dense steps shows what each set leaves out."""
+    from paper_1409_4256_gb300 import emc, learned, synth
+    torch = torch_cuda
+    ds = synth.make_dataset(32, 32, 3000, 2.0, radius=8.0)
+    quat, w = emc.quat_generate(3)
+    nrot, nd, M, R = quat.shape[0], ds.K.shape[0], 64, 8
+    floor = 1e-10 * float(ds.model_start.mean())
+    Kd = torch.as_tensor(ds.K, device="cuda")
+    ctx = emc.Context(32, ds.q, quat, w, nd, precision="bf16_split", w_floor=floor, n_cand=M,
+                      store_scores=True)
+    dense = emc.Context(32, ds.q, quat, w, nd, precision="bf16_split", w_floor=floor)
+    for c in (ctx, dense):
+        c.set_frames(Kd)
+    g0 = torch.as_tensor(ds.model_start.astype(np.float32), device="cuda")
+    g1, _ = ctx.iteration(g0)
+    g2, _ = ctx.iteration(g1)
+    tidx, tprob = ctx.targets_from_scores(16)
+    feat = ctx.features()
+    train, test = learned.split_rows(nd)
+    prop = learned.Proposal(nrot)
+    prop.train(feat, tidx, tprob, train, epochs=30, batch=256, lr=1e-3)
+    net = prop.propose(feat, M, nd)
+    rng = np.random.default_rng(1008)
+    offs = np.sort(rng.choice(nrot, M, replace=False))
+    rand = torch.as_tensor(((rng.integers(0, nrot, size=nd)[:, None] + offs[None, :]) % nrot)
+                           .astype(np.int32), device="cuda")
+    frames = torch.arange(nd, dtype=torch.int32, device="cuda")
+
+    def dense_top_m():
+        cand = torch.empty((nd, M), dtype=torch.int32, device="cuda")
+        emc.topm(ctx.responsibilities(frames), nd, nrot, nrot, M, cand)
+        return cand
+
+    refresh = {
+        "network": lambda: emc.merge_candidates(ctx.targets_from_scores(R)[0], net, M),
+        "random_filler": lambda: emc.merge_candidates(ctx.targets_from_scores(R)[0], rand, M),
+        "dense_top_m": dense_top_m}
+    a, b = g2.clone(), torch.empty_like(g2)
+    for _ in range(10):
+        dense.iteration(a, b)
+        a, b = b, a
+    ref = a.double()
+    out = {}
+    for name, make in refresh.items():
+        ctx.iteration(g2)
+        ctx.set_candidates(make())
+        c, d = g2.clone(), torch.empty_like(g2)
+        missed = []
+        for it in range(10):
+            if it % 5 == 4:
+                ctx.iteration(c, d)
+                missed.append(float(ctx.missed_mass().mean().item()))
+                ctx.set_candidates(make())
+            else:
+                ctx.sparse_iteration(c, d)
+            c, d = d, c
+        diff = float(torch.linalg.norm(c.double() - ref) / torch.linalg.norm(ref))
+        out[name] = (diff, missed)
+    print("\nschedules at 32^3 (1380 rotations, 3000 frames, M = 64, dense top 8 kept): " +
+          ", ".join(f"{k}: model rel-L2 vs dense {v[0]:.2e}, missed mass {v[1]}"
+                    for k, v in out.items()))
+    for name in out:
+        assert out[name][0] <= 1e-3, (name, out[name])

@@ -1,11 +1,13 @@
 """emc_iteration's bound-pruned E-step pass 1 against the dense one.
 
 With a split precision and a Poisson model, emc_iteration bounds every
-(128-rotation, 256-frame) tile's scores by a contraction of the hi plane alone
-and contracts exactly only the tiles that can hold a score within 110 of their
-frames' maxima, in pass 1 and (without stored scores) in the recomputing pass
-2; it also regroups the frames by their best rotation after every iteration. The first call on fresh frames runs the dense pass (no
-order yet); later calls prune. Skipped tiles have P = 0 in FP32 and no weight
+(128-rotation, 256-frame) tile's scores -- by the incremental bound from the
+last iteration on the same frames and by a contraction of the hi plane alone
+where that is tighter -- and contracts exactly only the tiles that can hold a
+score within 110 of their frames' maxima, in pass 1 and (without stored
+scores) in the recomputing pass 2; it also regroups the frames by their best
+rotation after every iteration. The first call on fresh frames runs the dense
+pass (no order yet); later calls prune. Skipped tiles have P = 0 in FP32 and no weight
 in lse at FP64 precision, so:
   * from the same input, the log-likelihood equals the dense pass's to FP64
     summation order (1e-12 relative);
@@ -116,3 +118,82 @@ def test_targets_and_missed_mass_after_pruned_iterations(torch_cuda, small_probl
     # the missed mass of the same candidate sets
     ma, md = a.missed_mass().cpu().numpy(), d.missed_mass().cpu().numpy()
     assert np.abs(ma - md).max() <= 1e-6
+
+
+def _same_input_check(a, d, g):
+    """One step of each context from the same input: lse to FP64 summation
+    order, the model to FP32 summation order of the M-step."""
+    oa, sa = a.iteration(g)
+    od, sd = d.iteration(g)
+    assert sa["device_status"] == 0 and sd["device_status"] == 0
+    assert abs(sa["loglik"] - sd["loglik"]) <= 1e-12 * abs(sd["loglik"])
+    assert _rel(oa.cpu().numpy(), od.cpu().numpy()) <= 1e-6
+    return oa, sa
+
+
+@pytest.mark.parametrize("precision", ["bf16_split", "fp16_split"])
+def test_incremental_bound_on_reloaded_frames(torch_cuda, small_problem, precision):
+    # From the second pruned iteration on the same frames the incremental bound
+    # runs first (pass1_delta). Loading the same counts again changes nothing
+    # (context b, reloaded, takes the same steps as a); other counts void the
+    # bound for one iteration, so the hi-plane bound covers every pair of row
+    # tiles. Every step equals the dense pass from the same input.
+    from paper_1409_4256_gb300 import emc
+    torch, p = torch_cuda, small_problem
+    nd = p["K"].shape[0]
+
+    def ctx(dense):
+        c = emc.Context(p["N"], p["q"], p["quat"], p["w"], nd, precision=precision,
+                        w_floor=p["w_floor"], store_scores=True, dense_estep=dense)
+        c.set_frames(torch.as_tensor(p["K"], device="cuda"))
+        return c
+
+    a, b, d = ctx(False), ctx(False), ctx(True)
+    g = torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
+    g1, s1 = a.iteration(g)
+    b.iteration(g)
+    assert s1["pass1_pruned"] == 0
+    g2, s2 = _same_input_check(a, d, g1)
+    _, t2 = b.iteration(g1)
+    assert s2["pass1_pruned"] == 1 and s2["pass1_delta"] == 1
+    b.set_frames(torch.as_tensor(p["K"], device="cuda"))  # the same counts again
+    g3, s3 = _same_input_check(a, d, g2)
+    _, t3 = b.iteration(g2)
+    assert t3["pass1_delta"] == 1 and abs(t3["loglik"] - s3["loglik"]) <= 1e-12 * abs(s3["loglik"])
+    for key in ("pass1_bound_pairs", "pass1_exact"):
+        assert t3[key] == s3[key] and t2[key] == s2[key]
+    # other counts: the frames of the dense context change the same way
+    npairs = ((p["quat"].shape[0] + 127) // 128 + 1) // 2 * (-(-nd // 256))
+    K2 = np.roll(p["K"], 1, axis=0)
+    for c in (a, d):
+        c.set_frames(torch.as_tensor(K2, device="cuda"))
+    g4, s4 = _same_input_check(a, d, g3)
+    assert s4["pass1_bound_pairs"] == npairs
+    _, s5 = _same_input_check(a, d, g4)
+    assert s5["pass1_delta"] == 1
+
+
+def test_incremental_bound_across_sparse_iterations(torch_cuda, small_problem):
+    # the learned schedule's sparse iterations expand into the other L buffer:
+    # the next dense iteration's incremental bound still starts from the last
+    # dense one, across the model change of the sparse iterations
+    from paper_1409_4256_gb300 import emc
+    torch, p = torch_cuda, small_problem
+    nd, nrot, M = p["K"].shape[0], p["quat"].shape[0], 64
+    a = emc.Context(p["N"], p["q"], p["quat"], p["w"], nd, precision="bf16_split",
+                    w_floor=p["w_floor"], store_scores=True, n_cand=M)
+    d = emc.Context(p["N"], p["q"], p["quat"], p["w"], nd, precision="bf16_split",
+                    w_floor=p["w_floor"], store_scores=True, dense_estep=True)
+    for c in (a, d):
+        c.set_frames(torch.as_tensor(p["K"], device="cuda"))
+    rng = np.random.default_rng(3)
+    a.set_candidates(torch.as_tensor(
+        np.stack([rng.choice(nrot, M, replace=False) for _ in range(nd)]).astype(np.int32),
+        device="cuda"))
+    g = torch.as_tensor(p["grid"].astype(np.float32), device="cuda")
+    g1, _ = a.iteration(g)
+    g2, _ = _same_input_check(a, d, g1)
+    g3, _ = a.sparse_iteration(g2)
+    g4, _ = a.sparse_iteration(g3)
+    _, s = _same_input_check(a, d, g4)
+    assert s["pass1_delta"] == 1
