@@ -250,13 +250,15 @@ def run_reference(args):
 def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
     """Warm up, then time `steps` iterations with CUDA events on `stream`.
     Consecutive iterations of one reconstruction: each output model is the next
-    iteration's input (two buffers in turn), from the start model on. Returns
-    (ms per iteration, phases, kernels, last loglik, the model reached)."""
+    iteration's input (two buffers in turn), from the start model on. The timed
+    iterations run without statistics (no host wait inside the loop); the
+    phase times come from `steps` more iterations with statistics after it.
+    Returns (ms per iteration, phases, kernels, last loglik, the model reached)."""
     a, b = grid.clone(), torch.empty_like(grid)
     phases = {k: 0.0 for k in ("ms_expand", "ms_loglik", "ms_normalize", "ms_update",
                                 "ms_compress")}
     kernels = 0
-    tiles = [0, 0, 0]  # pass-1 tiles, of them contracted exactly, iterations bound-pruned
+    tiles = [0, 0, 0, 0, 0]  # pass-1 tiles, exact, bound-pruned steps, incremental, hi pairs
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             ctx.iteration(a, b, stats=True, stream=stream)
@@ -267,6 +269,12 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        for _ in range(steps):
+            ctx.iteration(a, b, stats=False, stream=stream)
+            a, b = b, a
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
         lls = []
         for _ in range(steps):
             _, st = ctx.iteration(a, b, stats=True, stream=stream)
@@ -277,16 +285,17 @@ def time_form(torch, emc, ctx, grid, steps, warmup, stream, dist=None):
             tiles[0] += st["pass1_tiles"]
             tiles[1] += st["pass1_exact"]
             tiles[2] += st["pass1_pruned"]
+            tiles[3] += st["pass1_delta"]
+            tiles[4] += st["pass1_bound_pairs"]
             lls.append(st["loglik"])
             if st["device_status"] != 0:
                 raise RuntimeError(f"device status {st['device_status']}")
-        e1.record(stream)
-        e1.synchronize()
-        torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     ph = {k: v / steps for k, v in phases.items()}
     ph["pass1_exact_tile_fraction"] = tiles[1] / tiles[0] if tiles[0] else None
     ph["pass1_bound_pruned_steps"] = tiles[2]
+    ph["pass1_incremental_bound_steps"] = tiles[3]
+    ph["pass1_hi_bound_pairs_per_step"] = tiles[4] / steps
     return ms, ph, kernels, lls[-1], a
 
 
@@ -610,12 +619,21 @@ def pass1_roofline(precision, n_pix, n_rot, n_data, phases, traffic):
     planes = 3 if precision == "bf16_split" else 2 if precision == "fp16_split" else 1
     pruned = bool(phases.get("pass1_bound_pruned_steps"))
     exact = phases.get("pass1_exact_tile_fraction")
-    # executed tensor work: every plane over every tile, or (bound-pruned) the hi
-    # plane over every tile and every plane over the tiles left live
-    executed = flops * ((1 + planes * exact) if pruned else planes)
-    roof.update({"kernel": ("E-step pass 1: hi-plane bound over every tile, exact contraction "
-                            "of the tiles it leaves live, online log-sum-exp" if pruned else
-                            "E-step pass 1 (scores + online log-sum-exp)"),
+    # executed tensor work: every plane over every tile; or (pruned) every plane
+    # over the tiles left live, the hi plane over the pairs of row tiles the
+    # hi-plane bound covered (256 x 256 per pair and frame tile), and the
+    # incremental bound's product (3 rows per row tile, 1/128 of the hi plane)
+    if pruned:
+        steps = max(1, phases.get("pass1_bound_pruned_steps", 1))
+        inc = phases.get("pass1_incremental_bound_steps", 0) / steps
+        hi_pairs = phases.get("pass1_hi_bound_pairs_per_step", 0.0)
+        executed = (flops * planes * exact + hi_pairs * 256 * 256 * 2.0 * n_pix +
+                    inc * flops * 3 / 128)
+    else:
+        executed = flops * planes
+    roof.update({"kernel": ("E-step pass 1: incremental and hi-plane bounds, exact "
+                            "contraction of the tiles they leave live, online log-sum-exp"
+                            if pruned else "E-step pass 1 (scores + online log-sum-exp)"),
                  "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "traffic": traffic,
                  "traffic_unit": ("bytes per iteration's pass 1 (bound + exact launches)" if pruned
@@ -626,10 +644,41 @@ def pass1_roofline(precision, n_pix, n_rot, n_data, phases, traffic):
                  "executed_frac": executed / (dom_ms * 1e-3) / 1e12 / peak,
                  "exact_tile_fraction": exact,
                  "frac_basis": ("dense-equivalent: 2 n_pix per pair over every pair; the pruned "
-                                "pass executes executed_flops (hi-plane bound over every tile, "
-                                "every plane over the live tiles)" if pruned else
+                                "pass executes executed_flops (every plane over the live tiles, "
+                                "the hi plane where the hi-plane bound ran, the incremental "
+                                "bound's product)" if pruned else
                                 "2 n_pix per pair over every pair")})
     return roof
+
+
+def phase_rooflines(precision, n_pix, ld_pix, n_rot, n_data, phases, pass1_roof):
+    """Roofline of every phase of the iteration (CUDA-event times per iteration
+    inside emc_iteration), and the dominant one. Expansion and compression are
+    measured against the copy bandwidth on the bytes the method itself must move
+    (L written; Num read), the passes on the tensor cores against the BF16 peak."""
+    pk, pk_src = peaks()
+    hbm = pk["hbm_gbs"]
+    planes = 3 if precision == "bf16_split" else 2 if precision == "fp16_split" else 1
+    esz = 4 if precision == "fp32" else 2
+    pairs = n_rot * n_data
+    out = {}
+    ms = phases["ms_expand"]
+    b = planes * esz * n_rot * ld_pix  # L written
+    out["expand"] = {"bound": "hbm", "unit": "GB/s", "achieved": b / (ms * 1e-3) / 1e9,
+                     "peak": hbm, "peak_source": f"{pk_src} copy bandwidth", "ms": ms,
+                     "algorithmic_bytes": b, "per_unit": f"{planes * esz} B of L per (i, j)"}
+    ms = phases["ms_compress"]
+    b = 4 * n_rot * ld_pix  # Num read
+    out["compress"] = {"bound": "hbm", "unit": "GB/s", "achieved": b / (ms * 1e-3) / 1e9,
+                       "peak": hbm, "peak_source": f"{pk_src} copy bandwidth", "ms": ms,
+                       "algorithmic_bytes": b, "per_unit": "4 B of Num per (i, j)"}
+    out["pass1"] = dict(pass1_roof, ms=phases["ms_loglik"])
+    for k in ("expand", "compress"):
+        out[k]["frac"] = out[k]["achieved"] / out[k]["peak"]
+    out["normalize"] = {"ms": phases["ms_normalize"]}
+    out["update"] = {"ms": phases["ms_update"]}
+    dom = max(("expand", "pass1", "normalize", "update", "compress"), key=lambda k: out[k]["ms"])
+    return out, dom
 
 
 def scale_form(torch, emc, args, form, cache, stream, dist, world, local):
@@ -743,9 +792,23 @@ def run_ours(args):
            "h2d_bytes_per_step": int(ds.K.nbytes), "d2h_bytes_per_step": int(out_host.numel() * 4)}
 
     # ---- roofline of the dominant kernel ------------------------------------
-    roof = pass1_roofline(args.precision, n_pix, n_rot, n_data, phases,
-                          traffic_for(args.workload, args.precision, n_rot, n_data,
-                                      args.recompute, phases))
+    roof1 = pass1_roofline(args.precision, n_pix, n_rot, n_data, phases,
+                           traffic_for(args.workload, args.precision, n_rot, n_data,
+                                       args.recompute, phases))
+    rooflines, dominant = phase_rooflines(args.precision, n_pix,
+                                          ctx.buffer_sizes(n_rot).ld_pix, n_rot, n_data,
+                                          phases, roof1)
+    # the roofline line is the dominant phase's; the others follow in "rooflines"
+    roof = dict(rooflines[dominant], phase=dominant)
+    if dominant == "compress":
+        roof.update({"kernel": "compress_kernel (c-step, Eq. 2.12): trilinear scatter of the "
+                               "slices into the grid, corner terms merged in shared memory, "
+                               "FP64 reductions in L2", "traffic": None,
+                     "traffic_source": "unmeasured for this configuration"})
+    elif dominant == "expand":
+        roof.update({"kernel": "expand_tile_kernel (e-step, Eq. 2.9): trilinear gather of "
+                               "the slices, log W split into planes", "traffic": None,
+                     "traffic_source": "unmeasured for this configuration"})
 
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
@@ -826,7 +889,8 @@ def run_ours(args):
                            "estep": "recompute" if args.recompute else "stored scores",
                            "pixels_used": n_pix, "parallelism": "replicas",
                            "l2": "inputs larger than L2 (log W and frames re-read every step)"},
-                "phases_ms": phases, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "phases_ms": phases, "roofline": roof, "rooflines": rooflines,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": kernels, "forms": forms, "loglik": loglik}
         print(json.dumps(line), flush=True)
     if dist:

@@ -26,7 +26,7 @@ struct Layout {
       Kb2, skcnt, skoff, skent, dupsrc, duprank, pixmax, fcn, finvn, fB, kbflag, kbcnt, kblist,
       Kp, perm, perm2, iperm, nsum, nsum_p, cn_p, invn_p, best, lsem_s, lses_s, live, tlist,
       tcount, sortH, sortoff, cgs, cgp, cgqh, cgql, cgqi, cgqlo, cgqf, L2, bias2, Ub, Ub2, Lk, Mk, Mk2, best2,
-      osrc, Dd, Cd, bpm, Ua, Ua2, dcand, pflag, plist, flags, qi, qlo, rotfx, epart, total;
+      osrc, Dd, Cd, bpm, g4, Ua, Ua2, dcand, pflag, plist, flags, qi, qlo, rotfx, epart, total;
   int64_t sort_entries;
   int64_t ntp;  // row tiles rounded up to 128: rows of each half of the bound increments
 };
@@ -136,6 +136,9 @@ Layout make_layout(const emc_config* c) {
   y.rot = take(sizeof(RotDF) * c->n_rot);
   y.rotfx = take(sizeof(RotFX) * c->n_rot);
   y.epart = take(sizeof(double) * (size_t)expand_tile_slices(y.ld_pix) * y.rows);
+  // the model in the corner-pair layout of the expansions' gathers (16 B a voxel;
+  // grids up to 256^3, 268 MB)
+  y.g4 = c->N <= 256 ? take(sizeof(float4) * (size_t)nvox) : 0;
   y.logw = take(sizeof(double) * c->n_rot);
   y.Kb = take(2 * (size_t)y.ld_data * y.ld_pix);
   y.status = take(256);
@@ -681,9 +684,11 @@ int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L
   const int64_t rows = round_up(nrot, 128);
   Planes p{L, rows * c->lay.ld_pix, c->lay.ld_pix};
   const bool g = is_gauss(&c->cfg);
+  const Layout& y = c->lay;
+  float4* g4 = (y.g4 && c->geom.interior) ? (float4*)(c->ws + y.g4) : nullptr;
+  if (g4) CU(launch_grid_pairs(grid, c->cfg.N, g4, s));
   if (!g && !is_flu(&c->cfg)) {
-    const Layout& y = c->lay;
-    CU(launch_expand_tile(c->geom, grid, (const RotFX*)(c->ws + y.rotfx) + rot0, c->logw + rot0,
+    CU(launch_expand_tile(c->geom, grid, g4, (const RotFX*)(c->ws + y.rotfx) + rot0, c->logw + rot0,
                           nrot, rows, c->cfg.precision, (float)c->cfg.w_floor, p, bias,
                           (double*)(c->ws + y.epart), Lold, bias_old,
                           Lold ? (uint16_t*)(c->ws + y.Dd) : nullptr, y.ntp,
@@ -691,7 +696,7 @@ int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L
     return EMC_OK;
   }
   if (is_flu(&c->cfg)) {
-    CU(launch_expand_flu(c->geom, grid, c->rot + rot0, c->logw + rot0, nrot, rows,
+    CU(launch_expand_flu(c->geom, grid, g4, c->rot + rot0, c->logw + rot0, nrot, rows,
                          c->cfg.precision, (float)c->cfg.w_floor, c->flu_c, p, bias,
                          c->flu_B + rot0, c->status, s));
     return EMC_OK;
@@ -699,7 +704,7 @@ int do_expand(emc_ctx* c, const float* grid, int64_t rot0, int64_t nrot, void* L
   if (g)
     CU(launch_gauss_scales(grid, (int64_t)c->cfg.N * c->cfg.N * c->cfg.N, c->gmax, c->nmax,
                            c->gsc, c->status, s));
-  CU(launch_expand(c->geom, grid, c->rot + rot0, c->logw + rot0, nrot, rows,
+  CU(launch_expand(c->geom, grid, g4, c->rot + rot0, c->logw + rot0, nrot, rows,
                    c->cfg.precision, (float)c->cfg.w_floor, p, bias, g ? c->gsc : nullptr,
                    c->cfg.sigma, c->status, s));
   return EMC_OK;
@@ -973,8 +978,10 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   if ((st = do_expand(c, grid_in, 0, n_rot, L, bias, s, fused ? Lold : nullptr,
                       fused ? bold : nullptr)))
     return st;
-  // Gaussian: grid maximum and scales first; Poisson: the row tiles and the bias sums
-  kernels += is_gauss(&c->cfg) ? 3 : (is_flu(&c->cfg) ? 1 : 2);
+  // Gaussian: grid maximum and scales first; Poisson: the row tiles and the bias
+  // sums; the corner-pair layout of the model first where it is used
+  kernels += (is_gauss(&c->cfg) ? 3 : (is_flu(&c->cfg) ? 1 : 2)) +
+             ((y.g4 && c->geom.interior) ? 1 : 0);
   if (stats) CU(cudaEventRecord(c->ev[1], s));
   float* S = (c->cfg.flags & EMC_FLAG_STORE_SCORES) ? (float*)(c->ws + y.S) : nullptr;
   // bound-pruned pass 1 over the frames in their internal order

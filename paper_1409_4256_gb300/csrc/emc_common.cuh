@@ -153,6 +153,43 @@ __device__ __forceinline__ void rotate_fx(const int* Rh, const float* Rhf, const
   }
 }
 
+// Trilinear value (Eq. 2.8, tent weights) at p = f + t from the grid in its
+// corner-pair layout g4[(x N + y) N + z] = (g[x][y][z], g[x][y][z+1],
+// g[x][y+1][z], g[x][y+1][z+1]) (0 beyond the grid): two 16-byte loads per
+// point where the plain layout needs eight scattered 4-byte ones, which is
+// what limits the expansion (its loads are gathers: every lane of a warp reads
+// another cache line). Corners inside the grid only (interior points).
+__device__ __forceinline__ float trilinear_g4(const float4* __restrict__ g4, int N, const int* f,
+                                              const float* t) {
+  const int64_t o = ((int64_t)f[0] * N + f[1]) * N + f[2];
+  const float4 a = __ldg(g4 + o), b = __ldg(g4 + o + (int64_t)N * N);
+  const float tz = t[2], sz = 1.f - tz, ty = t[1], sy = 1.f - ty;
+  const float va = sy * fmaf(tz, a.y, sz * a.x) + ty * fmaf(tz, a.w, sz * a.z);
+  const float vb = sy * fmaf(tz, b.y, sz * b.x) + ty * fmaf(tz, b.w, sz * b.z);
+  return fmaf(t[0], vb, (1.f - t[0]) * va);
+}
+
+// FP32 -> FP64 with integer operations (the conversion instruction runs on the
+// FP64 pipe, at 1/64 of the FP32 rate on this part): sign, exponent rebiased by
+// 1023 - 127, mantissa moved up 29 bits; a subnormal input a 2^-149 is
+// normalised by its leading bit. Exact for every finite input.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t a = u & 0x7fffffffu;
+  const unsigned long long sgn = ((unsigned long long)(u >> 31)) << 63;
+  unsigned long long d;
+  if (a >= 0x00800000u) {
+    d = ((unsigned long long)a + (896ull << 23)) << 29;
+  } else if (a != 0u) {
+    const int p = 31 - __clz(a);  // a = 2^p (1 + f), p < 23
+    d = ((unsigned long long)(p - 149 + 1023) << 52) |
+        (((unsigned long long)a << (52 - p)) & 0xfffffffffffffull);
+  } else {
+    d = 0ull;
+  }
+  return __longlong_as_double((long long)(sgn | d));
+}
+
 // ---------------------------------------------------------------------------
 // BF16 helpers (round to nearest even).
 // ---------------------------------------------------------------------------

@@ -71,7 +71,8 @@ cudaError_t launch_assign_duplicates(const int32_t* K, int64_t ld_k, int64_t n_d
                                      int32_t* status, cudaStream_t s);
 
 // gsc != NULL: Gaussian model (FP16 three-plane s W, bias log w - sum W^2 / 2 sigma^2)
-cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
+// g4 (may be NULL): the grid in the corner-pair layout (launch_grid_pairs)
+cudaError_t launch_expand(const Geom& g, const float* grid, const float4* g4, const RotDF* rot,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
                           float w_floor, Planes L, double* bias, const float4* gsc, double sigma,
                           int32_t* status, cudaStream_t s);
@@ -82,7 +83,11 @@ cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
 // increments D ([2 ntp][ld_pix], rounded up to the frames' type), dabs[t] and,
 // from bias_old, bpm (as launch_delta_planes).
 int64_t expand_tile_slices(int64_t ld_pix);
-cudaError_t launch_expand_tile(const Geom& g, const float* grid, const RotFX* rot,
+// g4 (may be NULL): the grid in the corner-pair layout (launch_grid_pairs),
+// read where every corner lies inside the grid
+cudaError_t launch_grid_pairs(const float* grid, int N, float4* g4, cudaStream_t s);
+cudaError_t launch_expand_tile(const Geom& g, const float* grid, const float4* g4,
+                               const RotFX* rot,
                                const double* logw, int64_t nrot, int64_t rows, int precision,
                                float w_floor, Planes L, double* bias, double* partial,
                                const void* Lold, const double* bias_old, uint16_t* D, int64_t ntp,
@@ -94,7 +99,7 @@ cudaError_t launch_fixed_geometry(const float4* qh, const float4* ql, int64_t ld
 // Poisson-fluence model: L = log(W / B_j) + c as the BF16 three-term split
 // (precision EMC_PREC_BF16_SPLIT only); bias = double[2][rows]: log w_j, then
 // B_j = sum_i W_ij; Bctx[row] = B_j too.
-cudaError_t launch_expand_flu(const Geom& g, const float* grid, const RotDF* rot,
+cudaError_t launch_expand_flu(const Geom& g, const float* grid, const float4* g4, const RotDF* rot,
                               const double* logw, int64_t nrot, int64_t rows, int precision,
                               float w_floor, double c, Planes L, double* bias, double* Bctx,
                               int32_t* status, cudaStream_t s);

@@ -62,6 +62,7 @@ template <int PREC, bool GAUSS, bool INTERIOR>
 __global__ void __launch_bounds__(kExpandThreads)
     expand_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql, int64_t n_pix,
                   int64_t ld_pix, int N, const float* __restrict__ grid,
+                  const float4* __restrict__ g4,
                   const RotDF* __restrict__ rot, const double* __restrict__ logw, int64_t nrot,
                   float w_floor, void* __restrict__ Lbase, int64_t plane_stride,
                   double* __restrict__ bias, const float4* __restrict__ gsc, double inv2s2,
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kExpandThreads)
         int f[3];
         float t[3];
         rotate_to_grid(R, a, b, half_n, f, t);
-        float W = trilinear<INTERIOR>(grid, N, f, t);
+        float W = (INTERIOR && g4) ? trilinear_g4(g4, N, f, t) : trilinear<INTERIOR>(grid, N, f, t);
         nonfinite |= !(fabsf(W) <= 3.4e38f);  // a NaN or infinite voxel of the model
         W = fmaxf(W, GAUSS ? 0.f : w_floor);
         if (a.w == 1.f) {  // duplicate columns (counts above 256) repeat a pixel: not summed
@@ -168,6 +169,7 @@ template <bool INTERIOR, bool STASH>
 __global__ void __launch_bounds__(kExpandThreads)
     expand_flu_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql,
                       int64_t ld_pix, int N, const float* __restrict__ grid,
+                      const float4* __restrict__ g4,
                       const RotDF* __restrict__ rot, const double* __restrict__ logw, int64_t nrot,
                       float w_floor, double c, uint16_t* __restrict__ Lbase, int64_t plane_stride,
                       double* __restrict__ bias, double* __restrict__ Bctx, int32_t* status) {
@@ -190,7 +192,8 @@ __global__ void __launch_bounds__(kExpandThreads)
       int f[3];
       float t[3];
       rotate_to_grid(R, a, ql[i], half_n, f, t);
-      const float Wt = trilinear<INTERIOR>(grid, N, f, t);
+      const float Wt = (INTERIOR && g4) ? trilinear_g4(g4, N, f, t)
+                                        : trilinear<INTERIOR>(grid, N, f, t);
       nonfinite |= !(fabsf(Wt) <= 3.4e38f);  // a NaN or infinite voxel of the model
       const float W = fmaxf(Wt, w_floor);
       if (STASH) wst[i] = W;
@@ -233,7 +236,8 @@ __global__ void __launch_bounds__(kExpandThreads)
         int f[3];
         float t[3];
         rotate_to_grid(R, a, ql[i], half_n, f, t);
-        W = fmaxf(trilinear<INTERIOR>(grid, N, f, t), w_floor);
+        W = fmaxf((INTERIOR && g4) ? trilinear_g4(g4, N, f, t) : trilinear<INTERIOR>(grid, N, f, t),
+                  w_floor);
       }
       const float x = logf(W);
       const float s = x + ah;  // two-sum: s + e = x + ah exactly
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(kExpandThreads)
 // shared memory for one stashed row of W: rows up to 96 KB (24576 pixels)
 constexpr size_t kFluStashMax = 96 * 1024;
 
-cudaError_t launch_expand_flu(const Geom& g, const float* grid, const RotDF* rot,
+cudaError_t launch_expand_flu(const Geom& g, const float* grid, const float4* g4, const RotDF* rot,
                               const double* logw, int64_t nrot, int64_t rows, int precision,
                               float w_floor, double c, Planes L, double* bias, double* Bctx,
                               int32_t* status, cudaStream_t s) {
@@ -273,7 +277,7 @@ cudaError_t launch_expand_flu(const Geom& g, const float* grid, const RotDF* rot
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);         \
     if (e == cudaSuccess)                                                                     \
       expand_flu_kernel<I, S><<<grd, blk, sm, s>>>(                                           \
-          g.qh, g.ql, g.ld_pix, g.N, grid, rot, logw, nrot, w_floor, c,                       \
+          g.qh, g.ql, g.ld_pix, g.N, grid, g4, rot, logw, nrot, w_floor, c,                   \
           reinterpret_cast<uint16_t*>(L.base), L.plane_stride, bias, Bctx, status);           \
   } while (0)
   if (g.interior) {
@@ -288,14 +292,14 @@ cudaError_t launch_expand_flu(const Geom& g, const float* grid, const RotDF* rot
   return cudaGetLastError();
 }
 
-cudaError_t launch_expand(const Geom& g, const float* grid, const RotDF* rot,
+cudaError_t launch_expand(const Geom& g, const float* grid, const float4* g4, const RotDF* rot,
                           const double* logw, int64_t nrot, int64_t rows, int precision,
                           float w_floor, Planes L, double* bias, const float4* gsc, double sigma,
                           int32_t* status, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
   dim3 grd((unsigned)rows), blk(kExpandThreads);
 #define EMC_EXPAND_I(P, G, I)                                                                \
-  expand_kernel<P, G, I><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid, rot,     \
+  expand_kernel<P, G, I><<<grd, blk, 0, s>>>(g.qh, g.ql, g.n_pix, g.ld_pix, g.N, grid, g4, rot, \
                                              logw, nrot, w_floor, L.base, L.plane_stride, bias, \
                                              gsc, gsc ? 1.0 / (2.0 * sigma * sigma) : 0.0, status)
 #define EMC_EXPAND(P, G)        \

@@ -8,8 +8,10 @@
 // log W_ij in the layout of the chosen precision (as expand.cu), written two
 // pixels at a time. The row sums sum_i W_ij of the bias
 //   bias_j = log w_j - sum_i W_ij
-// are reduced per warp in FP64 and per CTA in shared memory; a second kernel
-// adds the slices' partial sums in slice order (deterministic).
+// are reduced per warp as double-float pairs of FP32 (exact two-sums: FP64
+// is rare on this part, and a per-row FP64 reduction kept its pipe 65% busy),
+// per CTA in FP64 in shared memory; a second kernel adds the slices' partial
+// sums in slice order (deterministic).
 //
 // The grid point is formed in fixed point (rotate_fx): exact 64-bit integer
 // products for the large part, six FP32 FMAs for the rest (error ~1e-10
@@ -31,10 +33,12 @@ constexpr int kTThreads = 256;
 constexpr int kTRows = 128;
 constexpr int kTPix = 2 * kTThreads;
 
-struct RowsFX {
-  int hi[kTRows][9];
-  float hf[kTRows][9];  // hi as FP32 (hi 2^-20, exact)
-  float lo[kTRows][9];
+// one rotation in shared memory: read as seven 16-byte words
+struct __align__(16) RowFX {
+  int hi[9];
+  float hf[9];  // hi as FP32 (hi 2^-20, exact)
+  float lo[9];
+  float pad;
 };
 
 template <bool INTERIOR>
@@ -99,15 +103,16 @@ __device__ __forceinline__ uint16_t round_up_operand(float x) {
 }
 
 template <int PREC, bool INTERIOR, bool DELTA>
-__global__ void __launch_bounds__(kTThreads)
+__global__ void __launch_bounds__(kTThreads, 3)
     expand_tile_kernel(const int4* __restrict__ qi_g, const float4* __restrict__ qlo_g,
                        int64_t ld_pix, int N, const float* __restrict__ grid,
+                       const float4* __restrict__ g4,
                        const RotFX* __restrict__ rot, int64_t nrot, int64_t rows, float w_floor,
                        void* __restrict__ Lbase, int64_t ps, double* __restrict__ partial,
                        const void* __restrict__ Lold, uint16_t* __restrict__ D, int64_t ntp,
                        int32_t* status) {
-  __shared__ RowsFX R;
-  __shared__ double rsum[kTThreads / 32][kTRows];
+  __shared__ RowFX R[kTRows];
+  __shared__ float2 rsum[kTThreads / 32][kTRows];
   const int64_t t = blockIdx.y;
   const int64_t r0 = t * kTRows;
   const int nr = (int)min((int64_t)kTRows, nrot - r0);  // >= 1 for every tile of rows
@@ -120,9 +125,9 @@ __global__ void __launch_bounds__(kTThreads)
       h = rot[r0 + r].hi[e];
       l = rot[r0 + r].lo[e];
     }
-    R.hi[r][e] = h;
-    R.hf[r][e] = (float)h * 0x1p-20f;
-    R.lo[r][e] = l;
+    R[r].hi[e] = h;
+    R[r].hf[e] = (float)h * 0x1p-20f;
+    R[r].lo[e] = l;
   }
   const int64_t i0 = (int64_t)blockIdx.x * kTPix + 2 * threadIdx.x;
   const bool inside = i0 < ld_pix;  // ld_pix is even: both pixels or neither
@@ -142,17 +147,23 @@ __global__ void __launch_bounds__(kTThreads)
     const int64_t row = r0 + r;
     const bool vrow = r < nr;
     float L[2] = {0.f, 0.f};
-    double s = 0.0;
+    float s = 0.f, se = 0.f;  // row sum of the pair as s + se
+    const RowFX Rr = R[r];
 #pragma unroll
     for (int u = 0; u < 2; u++) {
       if (vrow && qi[u].w != 0) {  // w: 1 pixel, 2 duplicate column, 0 padding / ones
         int f[3];
         float tt[3];
-        rotate_fx(R.hi[r], R.hf[r], R.lo[r], qi[u], qh[u], ql[u], N, f, tt);
-        float W = trilinear_fx<INTERIOR>(grid, N, f, tt);
+        rotate_fx(Rr.hi, Rr.hf, Rr.lo, qi[u], qh[u], ql[u], N, f, tt);
+        float W = (INTERIOR && g4) ? trilinear_g4(g4, N, f, tt)
+                                   : trilinear_fx<INTERIOR>(grid, N, f, tt);
         nonfinite |= !(fabsf(W) <= 3.4e38f);  // a NaN or infinite voxel of the model
         W = fmaxf(W, w_floor);
-        if (qi[u].w == 1) s += (double)W;  // duplicate columns repeat a pixel: not summed
+        if (qi[u].w == 1) {  // duplicate columns repeat a pixel: not summed
+          const f2 a = two_sum(s, W);
+          s = a.h;
+          se += a.l;
+        }
         L[u] = logf(W);
       }
     }
@@ -224,21 +235,32 @@ __global__ void __launch_bounds__(kTThreads)
         }
       }
     }
-    // row sum: warp reduction in FP64, one value per warp and row
+    // row sum: warp reduction of the double-float pairs, one FP64 value per warp and row
     if (vrow) {
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (lane == 0) rsum[warp][r] = s;
+      for (int off = 16; off > 0; off >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, off);
+        const float eo = __shfl_xor_sync(0xffffffffu, se, off);
+        const f2 a = two_sum(s, so);
+        s = a.h;
+        se += eo + a.l;
+      }
+      if (lane == 0) rsum[warp][r] = make_float2(s, se);
     }
   }
   if (nonfinite) set_status(status, EMC_ERR_NUMERIC);
   if (bad) set_status(status, EMC_ERR_UNSUPPORTED);
   __syncthreads();
   if (threadIdx.x < kTRows) {
-    double s = 0.0;
+    float s = 0.f, se = 0.f;
     if ((int)threadIdx.x < nr)
-      for (int w = 0; w < kTThreads / 32; w++) s += rsum[w][threadIdx.x];
-    partial[(int64_t)blockIdx.x * rows + r0 + threadIdx.x] = s;
+      for (int w = 0; w < kTThreads / 32; w++) {
+        const float2 v = rsum[w][threadIdx.x];
+        const f2 a = two_sum(s, v.x);
+        s = a.h;
+        se += v.y + a.l;
+      }
+    partial[(int64_t)blockIdx.x * rows + r0 + threadIdx.x] = f32_to_f64(s) + f32_to_f64(se);
   }
   if (DELTA && inside) {
     float a[2];
@@ -292,6 +314,17 @@ __global__ void __launch_bounds__(kTRows)
   }
 }
 
+// the grid in the corner-pair layout of trilinear_g4
+__global__ void grid_pairs_kernel(const float* __restrict__ g, int N, float4* __restrict__ g4) {
+  const int64_t n3 = (int64_t)N * N * N;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n3) return;
+  const int z = (int)(l % N), y = (int)((l / N) % N);
+  const bool zi = z + 1 < N, yi = y + 1 < N;
+  g4[l] = make_float4(g[l], zi ? g[l + 1] : 0.f, yi ? g[l + N] : 0.f,
+                      (zi && yi) ? g[l + N + 1] : 0.f);
+}
+
 // fixed-point pixel geometry from the double-float one
 __global__ void fixed_geometry_kernel(const float4* __restrict__ qh, const float4* __restrict__ ql,
                                       int64_t ld_pix, int4* __restrict__ qi,
@@ -318,6 +351,12 @@ __global__ void fixed_geometry_kernel(const float4* __restrict__ qh, const float
 
 int64_t expand_tile_slices(int64_t ld_pix) { return (ld_pix + kTPix - 1) / kTPix; }
 
+cudaError_t launch_grid_pairs(const float* grid, int N, float4* g4, cudaStream_t s) {
+  const int64_t n3 = (int64_t)N * N * N;
+  grid_pairs_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(grid, N, g4);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fixed_geometry(const float4* qh, const float4* ql, int64_t ld_pix, int4* qi,
                                   float4* qlo, float4* qf, cudaStream_t s) {
   fixed_geometry_kernel<<<(unsigned)((ld_pix + 255) / 256), 256, 0, s>>>(qh, ql, ld_pix, qi, qlo,
@@ -325,7 +364,8 @@ cudaError_t launch_fixed_geometry(const float4* qh, const float4* ql, int64_t ld
   return cudaGetLastError();
 }
 
-cudaError_t launch_expand_tile(const Geom& g, const float* grid, const RotFX* rot,
+cudaError_t launch_expand_tile(const Geom& g, const float* grid, const float4* g4,
+                               const RotFX* rot,
                                const double* logw, int64_t nrot, int64_t rows, int precision,
                                float w_floor, Planes L, double* bias, double* partial,
                                const void* Lold, const double* bias_old, uint16_t* D, int64_t ntp,
@@ -337,7 +377,7 @@ cudaError_t launch_expand_tile(const Geom& g, const float* grid, const RotFX* ro
   dim3 grd((unsigned)ns, (unsigned)nt);
 #define EMC_TILE(P, I, DL)                                                                    \
   expand_tile_kernel<P, I, DL><<<grd, kTThreads, 0, s>>>(                                     \
-      g.qi, g.qlo, g.ld_pix, g.N, grid, rot, nrot, rows, w_floor, L.base, L.plane_stride,     \
+      g.qi, g.qlo, g.ld_pix, g.N, grid, g4, rot, nrot, rows, w_floor, L.base, L.plane_stride, \
       partial, Lold, D, ntp, status)
 #define EMC_TILE_P(P)                          \
   if (g.interior) {                            \

@@ -348,13 +348,19 @@ __global__ void __launch_bounds__(256)
   const int64_t nnt = ld_data / 256;
   const bool ok = k < n_data;
   const bool valid = valid_host && !(changed && (changed[0] || changed[2]));
-  double L = -INFINITY, wl = 0.0;
-  const double E2 = ok ? 2.0 * ((double)nsum[k] / (double)div + 1.0) : 0.0;
+  // FP32 with upward rounding for the upper bounds (FP64 is rare on this part);
+  // the frame's lower bound in FP64 once, then rounded down for the comparisons
+  double L = -INFINITY;
+  float wl = 0.f, Lf = -INFINITY;
+  const float ec = __double2float_ru(errc);
+  const float E2 = ok ? 2.f * (nsum[k] / div + 1.f) : 0.f;
   if (ok && valid) {
     const int tb = best[k];
-    const double e = errc * (double)C[(2 * ntp + tb) * ld_data + k];
-    wl = (double)C[(ntp + tb) * ld_data + k] + (double)bpm[n_mtiles + tb] + e + 1.0 / 64.0;
-    L = Mk[k] - wl;
+    const float e = __fmul_ru(ec, C[(2 * ntp + tb) * ld_data + k]);
+    wl = __fadd_ru(__fadd_ru(__fadd_ru(C[(ntp + tb) * ld_data + k], bpm[n_mtiles + tb]), e),
+                   1.0f / 64.0f);
+    L = Mk[k] - (double)wl;
+    Lf = __double2float_rd(L - 111.0);
   }
   if (ok && r == 0) Lk[k] = L;
   for (int64_t t = r; t < n_mtiles; t += 8) {
@@ -363,13 +369,13 @@ __global__ void __launch_bounds__(256)
       float* u = Ub + t * ld_data + k;
       float* ua = Ua + t * ld_data + k;
       if (valid) {
-        const double e = errc * (double)C[(2 * ntp + t) * ld_data + k];
-        const double wu = (double)C[t * ld_data + k] + (double)bpm[t] + e;
-        const double U = (double)*u + wu;
-        const double acc = (double)*ua + fmax(wu, 0.0);
-        *u = __double2float_ru(U);
-        *ua = (float)acc;
-        on = U >= L - 111.0 && acc + wl > E2;
+        const float e = __fmul_ru(ec, C[(2 * ntp + t) * ld_data + k]);
+        const float wu = __fadd_ru(__fadd_ru(C[t * ld_data + k], bpm[t]), e);
+        const float U = __fadd_ru(*u, wu);
+        const float acc = *ua + fmaxf(wu, 0.f);
+        *u = U;
+        *ua = acc;
+        on = U >= Lf && acc + wl > E2;
       } else {
         *u = INFINITY;
         *ua = 0.f;
@@ -430,8 +436,9 @@ __global__ void __launch_bounds__(256)
     for (int q = 1; q < 8; q++) L = fmax(L, red[q][lane]);
     if (r == 0) Lk[k] = L;
   }
+  const float Lf = ok ? __double2float_rd(L - 111.0) : INFINITY;  // rounded down: safe side
   for (int64_t t = r; t < n_mtiles; t += 8) {
-    const bool on = ok && (double)Ub[t * ld_data + k] >= L - 111.0;
+    const bool on = ok && Ub[t * ld_data + k] >= Lf;
     if (__any_sync(0xffffffffu, on) && lane == 0) live[t * nnt + (k >> 8)] = 1;
   }
 }
