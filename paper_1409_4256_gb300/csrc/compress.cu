@@ -14,7 +14,7 @@
 //
 // Corner merging. The used pixels are grouped by cells of (q_x, q_y), so a
 // group is a small patch of the detector sheet, and neighbouring pixels share
-// most of their trilinear corners (about 8 corner terms per 2.5 distinct
+// most of their trilinear corners (about 8 corner terms per 3.2 distinct
 // voxels). A warp takes one group (up to two pixels per lane), bounds its
 // corners by a box, and sums the terms per voxel in a shared-memory box of
 // FP32 pairs (numerator, denominator) before one FP64 reduction per touched
@@ -24,10 +24,10 @@
 //  * the remaining lanes have distinct floor cells, so for one corner offset c
 //    their voxels are distinct: corner by corner (a __syncwarp between
 //    corners) each lane adds into its slot without atomics;
-//  * the lane that touches a slot first (in that fixed order) owns it; after the
-//    last step each owner reduces its slots once and clears them. The slot keeps
-//    the negated denominator sum, so +0.0 (the cleared state) means untouched and
-//    -0.0 a slot touched by zero terms (denominator terms are never negative).
+//  * the warp then sweeps the box in slot order: each non-zero slot is reduced
+//    once and cleared. Consecutive lanes hold consecutive slots (neighbouring
+//    z of one (x, y) column), so the sweep's loads are conflict-free and its
+//    reductions touch few sectors per instruction.
 // The order of every FP32 addition is fixed, so the result does not depend on
 // scheduling beyond the FP64 order of the L2 reductions. A group whose box
 // exceeds kAggCap slots reduces its corners directly.
@@ -83,13 +83,11 @@ __device__ __forceinline__ int warp_max(int v) {
 // INTERIOR: all trilinear corners of every pixel lie inside the grid (checked
 // on the host from max |q_i|), so no bounds checks.
 template <bool INTERIOR>
-__global__ void __launch_bounds__(kAggThreads)
+__global__ void __launch_bounds__(kAggThreads, 7)
     compress_kernel(Geom g, const RotFX* __restrict__ rot, const float* __restrict__ Num,
                     const float* __restrict__ den, int mode, double* __restrict__ g_num,
                     double* __restrict__ g_den, int nrep, int64_t n_vox) {
   extern __shared__ float2 agg_smem[];
-  __shared__ int Rh[9];
-  __shared__ float Rhf[9], Rl[9];
   const int64_t row = blockIdx.x;
   const float dj = den[row];
   // a rotation without responsibility mass has Num = 0 and den = 0 (both
@@ -101,14 +99,17 @@ __global__ void __launch_bounds__(kAggThreads)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* box = agg_smem + warp * (kAggCap + kAggStage);
   float2* stage = box + kAggCap;
-  if (threadIdx.x < 9) {
-    const int h = rot[row].hi[threadIdx.x];
-    Rh[threadIdx.x] = h;
-    Rhf[threadIdx.x] = (float)h * 0x1p-20f;
-    Rl[threadIdx.x] = rot[row].lo[threadIdx.x];
+  // the row's rotation in registers (uniform loads, once per CTA)
+  int Rh[9];
+  float Rhf[9], Rl[9];
+#pragma unroll
+  for (int e = 0; e < 9; e++) {
+    Rh[e] = __ldg(&rot[row].hi[e]);
+    Rhf[e] = (float)Rh[e] * 0x1p-20f;
+    Rl[e] = __ldg(&rot[row].lo[e]);
   }
   for (int s = lane; s < kAggCap; s += 32) box[s] = make_float2(0.f, 0.f);
-  __syncthreads();
+  __syncwarp();
   const int N = g.N;
   const int64_t nn = (int64_t)N * N;
   const float* Nr = Num + row * g.ld_pix;
@@ -152,7 +153,6 @@ __global__ void __launch_bounds__(kAggThreads)
     }
     int key[2] = {0, 0};
     bool lead[2] = {false, false};
-    unsigned own = 0;  // bit 8h + c: this lane reduces the slot of corner c of pixel h
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       if (h >= halves) break;
@@ -198,31 +198,30 @@ __global__ void __launch_bounds__(kAggThreads)
         if (lead[h] && (INTERIOR || in_grid(f[h][0] + cx, f[h][1] + cy, f[h][2] + cz, N))) {
           const int s = key[h] + (cx * dim[1] + cy) * dim[2] + cz;
           float2 b = box[s];
-          if (__float_as_uint(b.y) == 0u) own |= 1u << (8 * h + c);
           b.x += acc[c].x;
-          // negated sum with the sign bit forced, so a first term of +0 leaves -0
-          b.y = __uint_as_float(__float_as_uint(b.y - acc[c].y) | 0x80000000u);
+          b.y += acc[c].y;
           box[s] = b;
         }
         __syncwarp();
       }
     }
-    // each touched slot has exactly one owner: no ordering among the reductions
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      if (h >= halves) break;
-#pragma unroll
-      for (int c = 0; c < 8; c++) {
-        if (own & (1u << (8 * h + c))) {
-          const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
-          const int s = key[h] + (cx * dim[1] + cy) * dim[2] + cz;
-          const float2 b = box[s];
-          const int64_t l = (int64_t)(f[h][0] + cx) * nn + (int64_t)(f[h][1] + cy) * N +
-                            (f[h][2] + cz);
-          if (b.x != 0.f) atomicAdd(g_num + l, (double)b.x);
-          if (b.y != 0.f) atomicAdd(g_den + l, (double)(-b.y));
-          box[s] = make_float2(0.f, 0.f);
-        }
+    // sweep the box in slot order: one reduction per non-zero slot. Slot
+    // s = (x dim1 + y) dim2 + z; the quotients come from FP32 reciprocals,
+    // exact here: (s + 1/2) / d is at least 1/(2d) from an integer and the
+    // product's error is below 672 * 2^-22.
+    const int d12 = dim[1] * dim[2];
+    const float inv12 = 1.0f / (float)d12, inv2 = 1.0f / (float)dim[2];
+    for (int s = lane; s < (int)vol; s += 32) {
+      const float2 b = box[s];
+      if (b.x != 0.f || b.y != 0.f) {
+        const int x = (int)(((float)s + 0.5f) * inv12);
+        const int r = s - x * d12;
+        const int y = (int)(((float)r + 0.5f) * inv2);
+        const int z = r - y * dim[2];
+        const int64_t l = (int64_t)(lo[0] + x) * nn + (int64_t)(lo[1] + y) * N + (lo[2] + z);
+        if (b.x != 0.f) atomicAdd(g_num + l, (double)b.x);
+        if (b.y != 0.f) atomicAdd(g_den + l, (double)b.y);
+        box[s] = make_float2(0.f, 0.f);
       }
     }
     __syncwarp();  // slots cleared before the next group's steps

@@ -8,10 +8,13 @@
 // log W_ij in the layout of the chosen precision (as expand.cu), written two
 // pixels at a time. The row sums sum_i W_ij of the bias
 //   bias_j = log w_j - sum_i W_ij
-// are reduced per warp as double-float pairs of FP32 (exact two-sums: FP64
-// is rare on this part, and a per-row FP64 reduction kept its pipe 65% busy),
-// per CTA in FP64 in shared memory; a second kernel adds the slices' partial
-// sums in slice order (deterministic).
+// are kept as double-float pairs of FP32 (exact two-sums: FP64 is rare on
+// this part, and a per-row FP64 reduction kept its pipe 65% busy). A warp
+// parks its lanes' pairs of eight rows in shared memory and reduces them
+// transposed (each lane sums a quarter of one row, two shuffles finish it),
+// a quarter of the instructions of eight butterfly reductions; the CTA adds
+// its warps' sums, and a second kernel the slices' partial sums in slice
+// order (deterministic).
 //
 // The grid point is formed in fixed point (rotate_fx): exact 64-bit integer
 // products for the large part, six FP32 FMAs for the rest (error ~1e-10
@@ -113,6 +116,9 @@ __global__ void __launch_bounds__(kTThreads, 3)
                        int32_t* status) {
   __shared__ RowFX R[kTRows];
   __shared__ float2 rsum[kTThreads / 32][kTRows];
+  // eight rows of every lane's pair, rows padded to 33 so that the transposed
+  // reads hit 16 distinct bank pairs per half warp
+  __shared__ float2 park[kTThreads / 32][8 * 33];
   const int64_t t = blockIdx.y;
   const int64_t r0 = t * kTRows;
   const int nr = (int)min((int64_t)kTRows, nrot - r0);  // >= 1 for every tile of rows
@@ -235,17 +241,31 @@ __global__ void __launch_bounds__(kTThreads, 3)
         }
       }
     }
-    // row sum: warp reduction of the double-float pairs, one FP64 value per warp and row
-    if (vrow) {
+    // row sums: park the pair; every eighth row, lane l sums eight lanes'
+    // pairs of row l mod 8, and the lanes l, l ^ 8, l ^ 16, l ^ 24 combine
+    float2* pk = park[warp];
+    pk[(r & 7) * 33 + lane] = make_float2(s, se);
+    if ((r & 7) == 7) {
+      __syncwarp();
+      const float2* src = pk + (lane & 7) * 33 + (lane >> 3) * 8;
+      float a = 0.f, ae = 0.f;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float so = __shfl_xor_sync(0xffffffffu, s, off);
-        const float eo = __shfl_xor_sync(0xffffffffu, se, off);
-        const f2 a = two_sum(s, so);
-        s = a.h;
-        se += eo + a.l;
+      for (int m = 0; m < 8; m++) {
+        const float2 v = src[m];
+        const f2 z = two_sum(a, v.x);
+        a = z.h;
+        ae += v.y + z.l;
       }
-      if (lane == 0) rsum[warp][r] = make_float2(s, se);
+#pragma unroll
+      for (int off = 8; off <= 16; off <<= 1) {
+        const float ao = __shfl_xor_sync(0xffffffffu, a, off);
+        const float eo = __shfl_xor_sync(0xffffffffu, ae, off);
+        const f2 z = two_sum(a, ao);
+        a = z.h;
+        ae += eo + z.l;
+      }
+      if (lane < 8) rsum[warp][r - 7 + lane] = make_float2(a, ae);
+      __syncwarp();
     }
   }
   if (nonfinite) set_status(status, EMC_ERR_NUMERIC);
