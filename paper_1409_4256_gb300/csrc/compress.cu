@@ -39,7 +39,7 @@
 namespace emc {
 
 constexpr int kAggWarps = 4;
-constexpr int kAggCap = 672;       // box slots per warp (float2 each)
+constexpr int kAggCap = 672;       // box slots per warp (float2 each), below 1024
 constexpr int kAggStage = 32 * 8;  // merge staging: 8 corner terms per lane
 constexpr int kAggThreads = kAggWarps * 32;
 // 29.7 KB per CTA: seven CTAs (28 warps) per SM
@@ -206,17 +206,19 @@ __global__ void __launch_bounds__(kAggThreads, 7)
       }
     }
     // sweep the box in slot order: one reduction per non-zero slot. Slot
-    // s = (x dim1 + y) dim2 + z; the quotients come from FP32 reciprocals,
-    // exact here: (s + 1/2) / d is at least 1/(2d) from an integer and the
-    // product's error is below 672 * 2^-22.
+    // s = (x dim1 + y) dim2 + z; the quotients by multiply and shift with
+    // m = ceil(2^20 / d): floor(s m / 2^20) = floor(s / d) for s < 1024,
+    // since s (m - 2^20 / d) / 2^20 < 2^-10 < 1/d for d <= kAggCap. (Integer
+    // arithmetic: conversions between int and float run on the FP64 pipe here.)
     const int d12 = dim[1] * dim[2];
-    const float inv12 = 1.0f / (float)d12, inv2 = 1.0f / (float)dim[2];
+    const unsigned m12 = ((1u << 20) + (unsigned)d12 - 1u) / (unsigned)d12;
+    const unsigned m2 = ((1u << 20) + (unsigned)dim[2] - 1u) / (unsigned)dim[2];
     for (int s = lane; s < (int)vol; s += 32) {
       const float2 b = box[s];
       if (b.x != 0.f || b.y != 0.f) {
-        const int x = (int)(((float)s + 0.5f) * inv12);
+        const int x = (int)(((unsigned)s * m12) >> 20);
         const int r = s - x * d12;
-        const int y = (int)(((float)r + 0.5f) * inv2);
+        const int y = (int)(((unsigned)r * m2) >> 20);
         const int z = r - y * dim[2];
         const int64_t l = (int64_t)(lo[0] + x) * nn + (int64_t)(lo[1] + y) * N + (lo[2] + z);
         if (b.x != 0.f) atomicAdd(g_num + l, (double)b.x);

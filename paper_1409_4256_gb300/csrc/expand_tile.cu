@@ -1,5 +1,6 @@
 // expand_tile.cu -- e-step of EMC (Eq. 2.9) for the Poisson model, one row
-// tile of 128 rotations per CTA (and a slice of 512 pixels).
+// tile of 128 rotations per CTA (and a slice of 256 pixels: small CTAs, so
+// that the last wave of the grid leaves few SMs idle).
 //
 // Each thread owns two neighbouring pixels and takes the tile's rotations in
 // turn, so the pixels' geometry stays in registers and the rotations come from
@@ -32,7 +33,7 @@ namespace emc {
 
 namespace {
 
-constexpr int kTThreads = 256;
+constexpr int kTThreads = 128;
 constexpr int kTRows = 128;
 constexpr int kTPix = 2 * kTThreads;
 
@@ -106,7 +107,7 @@ __device__ __forceinline__ uint16_t round_up_operand(float x) {
 }
 
 template <int PREC, bool INTERIOR, bool DELTA>
-__global__ void __launch_bounds__(kTThreads, 3)
+__global__ void __launch_bounds__(kTThreads, 6)
     expand_tile_kernel(const int4* __restrict__ qi_g, const float4* __restrict__ qlo_g,
                        int64_t ld_pix, int N, const float* __restrict__ grid,
                        const float4* __restrict__ g4,
