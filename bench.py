@@ -48,7 +48,7 @@ LEARNED_FORMS = ("learned",)
 ADAPTIVE_FORMS = ("adaptive",)
 GAUSS_FORMS = ("gaussian",)
 FLUENCE_FORMS = ("poisson_fluence",)
-RECON_FORMS = ("reconstruct",)
+RECON_FORMS = ("reconstruct", "reconstruct_learned")
 SPARSE_K_FORMS = ("sparse_k",)
 # other workloads' own configurations (their own seeded data, built once)
 SCALE_FORMS = {"emc128_recompute": "emc128", "learned128": "emc128"}
@@ -468,6 +468,22 @@ def learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, dist, 
     return res
 
 
+def truth_error(torch, N, ds, dev):
+    """The model's relative L2 error against the true intensity over the voxels
+    the detector's q-range reaches, after a least-squares scale (the fluence
+    model fixes the model only up to one)."""
+    ax = torch.arange(N, device=dev, dtype=torch.float64) - N // 2
+    r2 = ax[:, None, None] ** 2 + ax[None, :, None] ** 2 + ax[None, None, :] ** 2
+    inside = r2 <= (N / 2 - 1) ** 2
+    truth = torch.as_tensor(ds.model_true, device=dev)[inside]
+
+    def err(g):
+        x = g.double()[inside]
+        sc = float((x * truth).sum() / (x * x).sum())
+        return float(torch.linalg.norm(sc * x - truth) / torch.linalg.norm(truth))
+    return err
+
+
 def reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot):
     """Consecutive iterations from the start model in the workload's noise model
     (the Poisson-fluence model where frames carry a random fluence): time per
@@ -477,16 +493,7 @@ def reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot):
     model = "poisson_fluence" if cfg.get("fluence_sigma", 0.0) > 0 else "poisson"
     prec = args.precision if args.precision in ("bf16_split", "fp16_split") else "bf16_split"
     ctx = make_ctx(prec, model=model)
-    N = cfg["N"]
-    ax = torch.arange(N, device=grid.device, dtype=torch.float64) - N // 2
-    r2 = ax[:, None, None] ** 2 + ax[None, :, None] ** 2 + ax[None, None, :] ** 2
-    inside = r2 <= (N / 2 - 1) ** 2
-    truth = torch.as_tensor(ds.model_true, device=grid.device)[inside]
-
-    def err(g):
-        x = g.double()[inside]
-        sc = float((x * truth).sum() / (x * x).sum())
-        return float(torch.linalg.norm(sc * x - truth) / torch.linalg.norm(truth))
+    err = truth_error(torch, cfg["N"], ds, grid.device)
 
     errs, ms, tiles, phases = [err(grid)], [], [], []
     a, b = grid.clone(), torch.empty_like(grid)
@@ -511,6 +518,108 @@ def reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot):
             "ms_per_iteration": ms, "pass1_exact_tile_fraction": tiles, "phases_ms": phases,
             "rel_err_vs_truth_after_scale_fit": errs,
             "value": n_rot * ds.K.shape[0] / (sum(later) / len(later) * 1e-3)}
+
+
+def reconstruct_learned_form(torch, emc, args, cfg, ds, quat, w, grid, K_dev, stream, n_rot,
+                             iters=30):
+    """The learned schedule as a reconstruction in the workload's noise model:
+    `iters` iterations from the start model, the first two dense (their
+    recorded responsibilities give the network's soft targets, top 32 per
+    frame, and it trains on 90% of the frames), then cycles of 4 sparse
+    iterations over the candidate sets and a dense fallback, which measures the
+    sets' missed mass and refreshes them (dense top 32 + the network's best
+    others). The dense iterations record their non-zero responsibilities, so no
+    scores are stored (pass 2 recomputes them where they do not fit). Reported
+    per iteration: time and the model's error against the true intensity after a
+    scale fit; beside it the same number of dense iterations from the same start."""
+    from paper_1409_4256_gb300 import learned
+    model = "poisson_fluence" if cfg.get("fluence_sigma", 0.0) > 0 else "poisson"
+    n_data = ds.K.shape[0]
+    M, R = min(args.n_cand, n_rot), 32
+    floor = 1e-10 * float(ds.model_start.mean())
+    wide = bool(ds.K.max() > 256)
+    dev = grid.device
+
+    def make(n_cand):
+        c = emc.Context(cfg["N"], ds.q, quat, w, n_data, precision="bf16_split", w_floor=floor,
+                        store_scores=not args.recompute, model=model, n_cand=n_cand,
+                        device=str(dev), stream=stream, rot_chunk=rot_chunk_for(n_rot, n_data),
+                        wide_counts=wide, sparse_k=bool(args.learned_sparse_k and n_cand))
+        c.set_frames(K_dev, stream=stream)
+        return c
+
+    err = truth_error(torch, cfg["N"], ds, dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, *a):
+        ev[0].record(stream)
+        fn(*a, stats=False, stream=stream)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1])
+
+    ctx = make(M)
+    ctx.collect(256)  # entries per frame: the rotations with a non-zero P, a few at most
+    kinds, ms, errs, missed = [], [], [err(grid)], []
+    bufs = [grid.clone(), torch.empty_like(grid)]
+    with torch.cuda.stream(stream):
+        for it in range(2):
+            ms.append(timed(ctx.iteration, bufs[0], bufs[1]))
+            kinds.append("dense")
+            bufs.reverse()
+            errs.append(err(bufs[0]))
+        t0 = time.perf_counter()
+        tidx, tprob = ctx.collected_targets(R, stream=stream)
+        feat = ctx.features(stream=stream)
+        train, _ = learned.split_rows(n_data)
+        prop = learned.Proposal(n_rot, device=str(dev))
+        hist = prop.train(feat, tidx, tprob, train, epochs=8, batch=512, lr=1e-3, stream=stream)
+        net = prop.propose(feat, M, n_data, stream=stream)
+        ctx.set_candidates(emc.merge_candidates(tidx, net, M, stream=stream), stream=stream)
+        stream.synchronize()
+        setup_s = time.perf_counter() - t0
+        for it in range(2, iters):
+            if it % 5 == 4:
+                ms.append(timed(ctx.iteration, bufs[0], bufs[1]))
+                kinds.append("dense")
+                ti, _, mm = ctx.collected_targets(R, missed=True, stream=stream)
+                missed.append(float(mm.mean().item()))
+                ctx.set_candidates(emc.merge_candidates(ti, net, M, stream=stream),
+                                   stream=stream)
+            else:
+                ms.append(timed(ctx.sparse_iteration, bufs[0], bufs[1]))
+                kinds.append("sparse")
+            bufs.reverse()
+            errs.append(err(bufs[0]))
+        if ctx.status() != 0:
+            raise RuntimeError("device status set in the learned reconstruction")
+        learned_grid = bufs[0].clone()
+    del ctx, prop
+    torch.cuda.empty_cache()
+    dctx = make(0)
+    dms, derrs = [], [err(grid)]
+    bufs = [grid.clone(), torch.empty_like(grid)]
+    with torch.cuda.stream(stream):
+        for it in range(iters):
+            dms.append(timed(dctx.iteration, bufs[0], bufs[1]))
+            bufs.reverse()
+            derrs.append(err(bufs[0]))
+    diff = float(torch.linalg.norm(learned_grid.double() - bufs[0].double()) /
+                 torch.linalg.norm(bufs[0].double()))
+    del dctx
+    sched = ms[2:]
+    return {"model": model, "iterations": iters, "candidates": M, "dense_top_kept": R,
+            "schedule": "2 dense (targets), then 4 sparse + 1 dense per 5 iterations; "
+                        "candidates = dense top 32 + the network's best others",
+            "ms_per_iteration": [round(x, 2) for x in ms], "kinds": kinds,
+            "rel_err_vs_truth_after_scale_fit": errs,
+            "mean_missed_mass_at_dense_steps": missed,
+            "train_loss_first_last": [hist[0], hist[-1]], "setup_s": setup_s,
+            "value": n_rot * n_data / (sum(sched) / len(sched) * 1e-3),
+            "dense_schedule": {"ms_per_iteration": [round(x, 2) for x in dms],
+                               "rel_err_vs_truth_after_scale_fit": derrs,
+                               "value": n_rot * n_data / (sum(dms[2:]) / len(dms[2:]) * 1e-3)},
+            "rel_model_diff_learned_vs_dense": diff}
 
 
 def sparse_k_form(torch, emc, cfg, ds, quat, w, grid, K_dev, stream, tensor_pass1_ms):
@@ -843,7 +952,12 @@ def run_ours(args):
     for f in [x for x in others if x not in ADAPTIVE_FORMS and x not in SCALE_FORMS]:
         if f in RECON_FORMS:
             try:
-                forms[f] = reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx, n_rot)
+                if f == "reconstruct_learned":
+                    forms[f] = reconstruct_learned_form(torch, emc, args, cfg, ds, quat, w, grid,
+                                                        K_dev, stream, n_rot)
+                else:
+                    forms[f] = reconstruct_form(torch, args, cfg, ds, grid, stream, make_ctx,
+                                                n_rot)
             except Exception as e:
                 forms[f] = {"error": str(e)[:300]}
             continue

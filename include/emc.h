@@ -539,6 +539,40 @@ int emc_sparse_iteration(emc_ctx* ctx, const float* grid_in, float* grid_out,
 int emc_missed_mass(emc_ctx* ctx, const void* scores, const double* lse_m, const double* lse_s,
                     float* missed, emc_stream stream);
 
+/* Responsibilities recorded during emc_iteration (no counterpart in the
+ * paper: the learned schedule's targets and missed mass where the scores are
+ * not stored). emc_collect_bytes: the size of the caller-owned buffer for cap
+ * entries and the scratch of emc_collected_targets for the context's n_data
+ * frames (0 if ctx is NULL or cap < 1). */
+size_t emc_collect_bytes(const emc_ctx* ctx, int64_t cap);
+
+/* With buf non-NULL (device, 256-byte aligned, emc_collect_bytes(ctx, cap)
+ * bytes, owned by the caller and kept until emc_set_collect(ctx, NULL, 0) or
+ * emc_ctx_destroy), every later emc_iteration appends each P_jk of Eq. 2.4 that
+ * is non-zero in FP32 as (frame, rotation, P_jk) to it, read from the blocks of
+ * P its M-step contracts (the rounding of those operands: 2^-16 relative for
+ * the split forms, 2^-8 for plain BF16); each iteration starts the list
+ * afresh. NULL stops recording. The tensor-core precisions with the Poisson
+ * model, BF16 or BF16 split with the Poisson-fluence model; EMC_ERR_UNSUPPORTED
+ * otherwise. */
+int emc_set_collect(emc_ctx* ctx, void* buf, int64_t cap);
+
+/* From the entries the last emc_iteration recorded, per frame k:
+ *  tidx, tprob (device int32 / float [n_data][R], 1 <= R <= 64): the R
+ *    rotations of largest P_jk (ties: the lower index first) and P_jk over
+ *    their sum, the softmax of their scores. Rotations whose P_jk is 0 in FP32
+ *    rank last: a frame with fewer than R non-zero entries gets distinct other
+ *    rotations with weight 0 (from the 128-rotation tile of its best one on).
+ *    The weights equal those of emc_targets_from_scores wherever they exceed
+ *    the rounding above;
+ *  missed (device float[n_data], may be NULL; needs emc_set_candidates): the
+ *    sum of P_jk over the recorded j outside the frame's candidate set, i.e.
+ *    1 - sum_{j in C_k} P_jk as emc_missed_mass defines it.
+ * EMC_ERR_ARG if the last emc_iteration recorded nothing; a list that
+ * overflowed sets EMC_ERR_UNSUPPORTED in the device status. */
+int emc_collected_targets(emc_ctx* ctx, int R, int32_t* tidx, float* tprob, float* missed,
+                          emc_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

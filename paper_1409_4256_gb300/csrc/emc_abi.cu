@@ -289,6 +289,9 @@ struct emc_ctx {
   float* Ub2;
   float* Ua;  // widening gathered since each tile bound's refresh (swapped with Ua2)
   float* Ua2;
+  CollectBuf col;   // responsibilities recorded by emc_iteration (emc_set_collect)
+  bool collecting;
+  bool collected;   // the last emc_iteration recorded into col
   cudaEvent_t ev[8];
   int kernels;  // launches made by the last emc_iteration
   TcCtl tcctl;  // bounded waits of the tensor-core launches (emc_ctx_set_wait_limit)
@@ -975,6 +978,8 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   const double* bold = delta ? (const double*)(c->ws + (lnew ? y.bias : y.bias2)) : nullptr;
   const bool fused = delta && !is_flu(&c->cfg);
   if (stats) CU(cudaEventRecord(c->ev[0], s));
+  c->collected = false;
+  if (c->collecting) CU(cudaMemsetAsync(c->col.count, 0, sizeof(unsigned long long), s));
   if ((st = do_expand(c, grid_in, 0, n_rot, L, bias, s, fused ? Lold : nullptr,
                       fused ? bold : nullptr)))
     return st;
@@ -1102,6 +1107,16 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     if (kbf)
       CU(launch_kb_lists(kbf, crows / 128, (int)(y.ld_data / 64), (int32_t*)kbc, (int32_t*)kbl,
                          s));
+    if (c->collecting && kbf) {  // the chunk's non-zero P_jk, before the update reads them
+      const float* invn = is_flu(&c->cfg)
+                              ? ((pr && y.invn_p) ? (const float*)(c->ws + y.invn_p) : c->flu_invn)
+                              : nullptr;
+      CU(launch_collect(P, crows * y.ld_data, y.ld_data, c->cfg.precision,
+                        c->flu_B ? c->flu_B + r0 : nullptr, invn, r0, nr, crows / 128, kbc, kbl,
+                        (int)(y.ld_data / 64), pr ? c->perm : nullptr, c->cfg.n_data, c->col,
+                        s));
+      kernels++;
+    }
     if (stats) CU(cudaEventRecord(c->ev[4], s));
     if ((st = do_update(c, P, crows, nr, Num, den, s, kbc, kbl, Kp))) return st;
     if (stats) CU(cudaEventRecord(c->ev[5], s));
@@ -1145,6 +1160,7 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
   if (stats) CU(cudaEventRecord(c->ev[7], s));
   c->kernels = kernels;
   c->iterated = true;
+  c->collected = c->collecting;
   if (stats) {
     CU(cudaEventSynchronize(c->ev[7]));
     float te = 0, tl = 0, tf = 0, tt = 0;
@@ -1386,6 +1402,40 @@ int emc_missed_mass(emc_ctx* ctx, const void* scores, const double* lse_m, const
                         missed, s, internal ? (const int32_t*)(ctx->ws + y.iperm) : nullptr,
                         internal && ctx->last_pruned ? (const uint8_t*)(ctx->ws + y.live)
                                                      : nullptr));
+  return EMC_OK;
+}
+
+size_t emc_collect_bytes(const emc_ctx* ctx, int64_t cap) {
+  if (!ctx || cap < 1) return 0;
+  return collect_layout(cap, ctx->cfg.n_data, nullptr, nullptr);
+}
+
+int emc_set_collect(emc_ctx* ctx, void* buf, int64_t cap) {
+  if (!ctx) return EMC_ERR_ARG;
+  if (!buf) {
+    ctx->collecting = false;
+    ctx->collected = false;
+    return EMC_OK;
+  }
+  if (cap < 1 || cap > (1LL << 31) || ((uintptr_t)buf & 255)) return EMC_ERR_ARG;
+  const int p = ctx->cfg.precision;
+  if (p == EMC_PREC_FP32 || is_gauss(&ctx->cfg)) return EMC_ERR_UNSUPPORTED;
+  if (is_flu(&ctx->cfg) && p != EMC_PREC_BF16 && p != EMC_PREC_BF16_SPLIT)
+    return EMC_ERR_UNSUPPORTED;
+  collect_layout(cap, ctx->cfg.n_data, &ctx->col, (char*)buf);
+  ctx->collecting = true;
+  ctx->collected = false;
+  return EMC_OK;
+}
+
+int emc_collected_targets(emc_ctx* ctx, int R, int32_t* tidx, float* tprob, float* missed,
+                          emc_stream stream) {
+  if (!ctx || !tidx || !tprob || R < 1 || R > 64 || R > ctx->cfg.n_rot) return EMC_ERR_ARG;
+  if (!ctx->collected || !ctx->collecting) return EMC_ERR_ARG;
+  if (missed && !ctx->cand_loaded) return EMC_ERR_ARG;
+  CU(launch_collected_targets(ctx->col, ctx->cfg.n_data, ctx->cfg.n_rot, R, tidx, tprob,
+                              missed ? (const int32_t*)(ctx->ws + ctx->lay.cand) : nullptr,
+                              ctx->cfg.n_cand, missed, ctx->status, (cudaStream_t)stream));
   return EMC_OK;
 }
 

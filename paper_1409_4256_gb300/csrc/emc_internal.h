@@ -397,6 +397,36 @@ cudaError_t launch_sparse_k_pass1(const float* L, int64_t ld_pix, int64_t n_pix,
                                   cudaStream_t s);
 size_t sparse_k_smem(int64_t ld_pix);
 
+// ---- recorded responsibilities (collect.cu) ----
+// A caller-owned list of the non-zero P_jk of an iteration and the scratch of
+// the targets computed from it.
+struct CollectBuf {
+  unsigned long long* count;  // entries appended (may exceed cap: overflow)
+  int32_t* ek;                // frame (the user's order)
+  int32_t* ej;                // rotation
+  float* ep;                  // P_jk
+  int32_t* sj;                // the entries grouped by frame
+  float* sp;
+  int32_t* cnt;               // [n_data + 1]
+  int32_t* off;               // [n_data + 1]
+  int32_t* fill;              // [n_data]
+  int64_t cap;
+};
+// bytes of a list of cap entries for n_data frames; with b and base, the
+// pointers into base
+size_t collect_layout(int64_t cap, int64_t n_data, CollectBuf* b, char* base);
+// the non-zero entries of the listed blocks of one chunk's P planes (rows
+// row0 .. row0 + nr of the rotations; frame positions mapped by perm if given)
+cudaError_t launch_collect(const void* P, int64_t plane, int64_t ld_data, int precision,
+                           const double* Bsum, const float* invn, int64_t row0, int64_t nr,
+                           int64_t n_mtiles, const int32_t* kbc, const int32_t* kbl, int kb_ld,
+                           const int32_t* perm, int64_t n_data, const CollectBuf& b,
+                           cudaStream_t s);
+// top-R targets, their weights and (cand non-NULL) the candidate sets' missed mass
+cudaError_t launch_collected_targets(const CollectBuf& b, int64_t n_data, int64_t n_rot, int R,
+                                     int32_t* tidx, float* tprob, const int32_t* cand, int n_cand,
+                                     float* missed, int32_t* status, cudaStream_t s);
+
 // Host side of Eq. 2.7 (emc_quat.cpp).
 int64_t quat_generate(int n, int uniform, double* quat, double* weight, int64_t cap);
 

@@ -105,6 +105,9 @@ _SIGS = {
     "emc_missed_mass": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "emc_iteration_lse": (_i32, [_vp, _vp, _vp]),
     "emc_responsibilities": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "emc_collect_bytes": (ctypes.c_size_t, [_vp, _i64]),
+    "emc_set_collect": (_i32, [_vp, _vp, _i64]),
+    "emc_collected_targets": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -438,6 +441,31 @@ class Context:
         if not stats:
             return grid_out, None
         return grid_out, {f: getattr(st, f) for f, _ in IterStats._fields_}
+
+    def collect(self, per_frame: int = 32):
+        """Record the non-zero responsibilities of every later iteration into a
+        list of per_frame * n_data entries that this object owns (0 stops)."""
+        if per_frame <= 0:
+            _check(lib().emc_set_collect(self.h, None, 0), "emc_set_collect")
+            self._collect_buf = None
+            return
+        cap = per_frame * self.cfg.n_data
+        nbytes = lib().emc_collect_bytes(self.h, cap)
+        buf = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+        _check(lib().emc_set_collect(self.h, _ptr(buf), cap), "emc_set_collect")
+        self._collect_buf = buf
+
+    def collected_targets(self, R: int, missed: bool = False, stream=None):
+        """(tidx, tprob[, missed]) from the responsibilities the last iteration
+        recorded (see collect)."""
+        nd = self.cfg.n_data
+        tidx = self.torch.empty((nd, R), dtype=self.torch.int32, device=self.device)
+        tprob = self.torch.empty((nd, R), dtype=self.torch.float32, device=self.device)
+        mm = (self.torch.empty(nd, dtype=self.torch.float32, device=self.device)
+              if missed else None)
+        _check(lib().emc_collected_targets(self.h, R, _ptr(tidx), _ptr(tprob), _ptr(mm),
+                                           _stream(stream)), "emc_collected_targets")
+        return (tidx, tprob, mm) if missed else (tidx, tprob)
 
     def missed_mass(self, scores=None, lse_m=None, lse_s=None, stream=None):
         out = self.torch.empty(self.cfg.n_data, dtype=self.torch.float32, device=self.device)
