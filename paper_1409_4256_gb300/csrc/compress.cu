@@ -12,10 +12,11 @@
 // j mod nrep (nrep x N^3 per grid, summed by the final division) to spread
 // those reductions over more addresses.
 //
-// Corner merging. The used pixels are grouped by cells of (q_x, q_y), so a
-// group is a small patch of the detector sheet, and neighbouring pixels share
-// most of their trilinear corners (about 8 corner terms per 3.2 distinct
-// voxels). A warp takes one group (up to two pixels per lane), bounds its
+// Corner merging. The used pixels are split by (q_x, q_y) into groups of at
+// most 32 (pixel_groups.h), so a group is a small patch of the detector sheet,
+// and neighbouring pixels share most of their trilinear corners (about 8
+// corner terms per 3.3 distinct voxels). A warp takes one group (one pixel per
+// lane; nearly every group is full, so few lanes idle), bounds its
 // corners by a box, and sums the terms per voxel in a shared-memory box of
 // FP32 pairs (numerator, denominator) before one FP64 reduction per touched
 // voxel:
@@ -44,7 +45,7 @@ constexpr int kAggStage = 32 * 8;  // merge staging: 8 corner terms per lane
 constexpr int kAggThreads = kAggWarps * 32;
 // 29.7 KB per CTA: seven CTAs (28 warps) per SM
 constexpr size_t kAggSmem = sizeof(float2) * kAggWarps * (kAggCap + kAggStage);
-static_assert(kCompressGroup == 64, "at most two pixels per lane");
+static_assert(kCompressGroup == 32, "one pixel per lane");
 
 __device__ __forceinline__ bool in_grid(int x, int y, int z, int N) {
   return (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N && (unsigned)z < (unsigned)N;
@@ -118,92 +119,76 @@ __global__ void __launch_bounds__(kAggThreads, 7)
 
   for (int grp = warp; grp < g.ngroups; grp += kAggWarps) {
     const int p0 = g.gstart[grp], np = g.gstart[grp + 1] - p0;
-    const int halves = np > 32 ? 2 : 1;  // warp-uniform
-    int f[2][3];
-    float t[2][3], v[2];
-    bool has[2];
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int k = lane + 32 * h;
-      has[h] = k < np;
-      if (has[h]) {
-        rotate_fx(Rh, Rhf, Rl, g.gqi[p0 + k], g.gqf[p0 + k], g.gqlo[p0 + k], N, f[h], t[h]);
-        v[h] = Nr[g.gpix[p0 + k]] * inv_d;
-      } else {
-        f[h][0] = f[h][1] = f[h][2] = 0;
-        t[h][0] = t[h][1] = t[h][2] = 0.f;
-        v[h] = 0.f;
-      }
+    int f[3];
+    float t[3], v;
+    const bool has = lane < np;
+    if (has) {
+      rotate_fx(Rh, Rhf, Rl, g.gqi[p0 + lane], g.gqf[p0 + lane], g.gqlo[p0 + lane], N, f, t);
+      v = Nr[g.gpix[p0 + lane]] * inv_d;
+    } else {
+      f[0] = f[1] = f[2] = 0;
+      t[0] = t[1] = t[2] = 0.f;
+      v = 0.f;
     }
     // the box of every corner of the group: floors lo .. hi, corners to hi + 1
     int lo[3], dim[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      const int mn = min(has[0] ? f[0][a] : INT_MAX, has[1] ? f[1][a] : INT_MAX);
-      const int mx = max(has[0] ? f[0][a] : INT_MIN, has[1] ? f[1][a] : INT_MIN);
-      lo[a] = warp_min(mn);
-      dim[a] = warp_max(mx) - lo[a] + 2;
+      lo[a] = warp_min(has ? f[a] : INT_MAX);
+      dim[a] = warp_max(has ? f[a] : INT_MIN) - lo[a] + 2;
     }
     const int64_t vol = (int64_t)dim[0] * dim[1] * dim[2];
     if (vol > kAggCap) {
-#pragma unroll
-      for (int h = 0; h < 2; h++)
-        if (has[h]) reduce_direct<INTERIOR>(f[h], t[h], v[h], dv, N, g_num, g_den);
+      if (has) reduce_direct<INTERIOR>(f, t, v, dv, N, g_num, g_den);
       continue;
     }
-    int key[2] = {0, 0};
-    bool lead[2] = {false, false};
+    // slot of corner 0; absent lanes get distinct negative keys
+    const int key = has ? ((f[0] - lo[0]) * dim[1] + (f[1] - lo[1])) * dim[2] + (f[2] - lo[2])
+                        : -1 - lane;
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    const bool lead = has && (__ffs(m) - 1 == lane);
+    float2 acc[8];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-      if (h >= halves) break;
-      // slot of corner 0; absent lanes get distinct negative keys
-      key[h] = has[h] ? ((f[h][0] - lo[0]) * dim[1] + (f[h][1] - lo[1])) * dim[2] + (f[h][2] - lo[2])
-                      : -1 - lane;
-      const unsigned m = __match_any_sync(0xffffffffu, key[h]);
-      lead[h] = has[h] && (__ffs(m) - 1 == lane);
-      float2 acc[8];
+    for (int c = 0; c < 8; c++) {
+      const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
+      const float w = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) *
+                      (cz ? t[2] : 1.f - t[2]);
+      acc[c] = make_float2(w * v, w * dv);
+    }
+    // pixels sharing a floor cell: the lowest lane sums the terms in lane order
+    const bool shared = has && m != (1u << lane);
+    if (__any_sync(0xffffffffu, shared)) {
+      if (shared && !lead)
 #pragma unroll
-      for (int c = 0; c < 8; c++) {
-        const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
-        const float w = (cx ? t[h][0] : 1.f - t[h][0]) * (cy ? t[h][1] : 1.f - t[h][1]) *
-                        (cz ? t[h][2] : 1.f - t[h][2]);
-        acc[c] = make_float2(w * v[h], w * dv);
-      }
-      // pixels sharing a floor cell: the lowest lane sums the terms in lane order
-      const bool shared = has[h] && m != (1u << lane);
-      if (__any_sync(0xffffffffu, shared)) {
-        if (shared && !lead[h])
+        for (int c = 0; c < 8; c++) stage[lane * 8 + c] = acc[c];
+      __syncwarp();
+      if (shared && lead) {
+        unsigned rest = m & ~(1u << lane);
+        while (rest) {
+          const int l = __ffs(rest) - 1;
+          rest &= rest - 1;
 #pragma unroll
-          for (int c = 0; c < 8; c++) stage[lane * 8 + c] = acc[c];
-        __syncwarp();
-        if (shared && lead[h]) {
-          unsigned rest = m & ~(1u << lane);
-          while (rest) {
-            const int l = __ffs(rest) - 1;
-            rest &= rest - 1;
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-              const float2 o = stage[l * 8 + c];
-              acc[c].x += o.x;
-              acc[c].y += o.y;
-            }
+          for (int c = 0; c < 8; c++) {
+            const float2 o = stage[l * 8 + c];
+            acc[c].x += o.x;
+            acc[c].y += o.y;
           }
         }
-        __syncwarp();
       }
-      // corner by corner: the leaders' slots for one offset are distinct
+      __syncwarp();
+    }
+    // corner by corner: the leaders' slots for one offset are distinct
 #pragma unroll
-      for (int c = 0; c < 8; c++) {
-        const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
-        if (lead[h] && (INTERIOR || in_grid(f[h][0] + cx, f[h][1] + cy, f[h][2] + cz, N))) {
-          const int s = key[h] + (cx * dim[1] + cy) * dim[2] + cz;
-          float2 b = box[s];
-          b.x += acc[c].x;
-          b.y += acc[c].y;
-          box[s] = b;
-        }
-        __syncwarp();
+    for (int c = 0; c < 8; c++) {
+      const int cx = (c >> 2) & 1, cy = (c >> 1) & 1, cz = c & 1;
+      if (lead && (INTERIOR || in_grid(f[0] + cx, f[1] + cy, f[2] + cz, N))) {
+        const int s = key + (cx * dim[1] + cy) * dim[2] + cz;
+        float2 b = box[s];
+        b.x += acc[c].x;
+        b.y += acc[c].y;
+        box[s] = b;
       }
+      __syncwarp();
     }
     // sweep the box in slot order: one reduction per non-zero slot. Slot
     // s = (x dim1 + y) dim2 + z; the quotients by multiply and shift with

@@ -424,7 +424,7 @@ static int ctx_create(const emc_config* cfg, const double* q, const double* quat
   }
   // compression groups (pixel_groups.h) and their geometry in group order
   std::vector<int32_t> gord, gstart;
-  build_pixel_groups(q, cfg->n_pix, kCompressCell, kCompressGroup, gord, gstart);
+  build_pixel_groups(q, cfg->n_pix, kCompressExtent, kCompressGroup, gord, gstart);
   std::vector<float4> gqh(cfg->n_pix + 1), gql(cfg->n_pix + 1);
   for (int64_t p = 0; p < cfg->n_pix; p++) {
     gqh[p] = qh[gord[p]];

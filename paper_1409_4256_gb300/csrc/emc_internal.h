@@ -30,8 +30,9 @@ struct Geom {
   int64_t ld_pix;
   int N;
   int interior;  // every |q_i| < N/2 - 1 with margin: all 8 corners of every R_j q_i lie in the grid
-  // compression groups: the used pixels binned by kCompressCell-voxel cells of
-  // (q_x, q_y), at most kCompressGroup per group; group g holds the positions
+  // compression groups: the used pixels split by (q_x, q_y) into groups of at
+  // most kCompressGroup pixels spanning at most kCompressExtent voxels along
+  // q_x and q_y (pixel_groups.h); group g holds the positions
   // gstart[g] .. gstart[g + 1] of gpix (pixel columns) and of gqh/gql (their
   // geometry in that order)
   int ngroups;
@@ -43,8 +44,8 @@ struct Geom {
   const float4* gqlo;
   const float4* gqf;  // gqi 2^-12 as FP32
 };
-constexpr int kCompressGroup = 64;
-constexpr double kCompressCell = 6.0;
+constexpr int kCompressGroup = 32;
+constexpr double kCompressExtent = 9.0;
 
 // A block of rows of a (possibly multi-plane) row-major matrix.
 struct Planes {
