@@ -40,10 +40,10 @@
 namespace emc {
 
 constexpr int kAggWarps = 4;
-constexpr int kAggCap = 672;       // box slots per warp (float2 each), below 1024
+constexpr int kAggCap = 576;       // box slots per warp (float2 each), below 1024
 constexpr int kAggStage = 32 * 8;  // merge staging: 8 corner terms per lane
 constexpr int kAggThreads = kAggWarps * 32;
-// 29.7 KB per CTA: seven CTAs (28 warps) per SM
+// 26.6 KB per CTA: eight CTAs (32 warps) per SM, at most 64 registers a thread
 constexpr size_t kAggSmem = sizeof(float2) * kAggWarps * (kAggCap + kAggStage);
 static_assert(kCompressGroup == 32, "one pixel per lane");
 
@@ -84,7 +84,7 @@ __device__ __forceinline__ int warp_max(int v) {
 // INTERIOR: all trilinear corners of every pixel lie inside the grid (checked
 // on the host from max |q_i|), so no bounds checks.
 template <bool INTERIOR>
-__global__ void __launch_bounds__(kAggThreads, 7)
+__global__ void __launch_bounds__(kAggThreads, 8)
     compress_kernel(Geom g, const RotFX* __restrict__ rot, const float* __restrict__ Num,
                     const float* __restrict__ den, int mode, double* __restrict__ g_num,
                     double* __restrict__ g_den, int nrep, int64_t n_vox) {

@@ -45,7 +45,7 @@ struct Geom {
   const float4* gqf;  // gqi 2^-12 as FP32
 };
 constexpr int kCompressGroup = 32;
-constexpr double kCompressExtent = 9.0;
+constexpr double kCompressExtent = 8.0;
 
 // A block of rows of a (possibly multi-plane) row-major matrix.
 struct Planes {
