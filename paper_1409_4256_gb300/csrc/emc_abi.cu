@@ -195,7 +195,10 @@ Layout make_layout(const emc_config* c) {
   // bound-pruned pass 1: frames in their internal order and the tile bookkeeping
   const bool pr = prune_ok(c);
   const int64_t nmt = y.rows / 128, nnt = y.ld_data / 256;
-  y.sort_entries = pr ? sort_scratch_entries(c->n_data, (int)nmt) : 0;
+  // the frame sort's histogram; also the tile lists' per-CTA counts (not live at once)
+  y.sort_entries = pr ? std::max(sort_scratch_entries(c->n_data, (int)nmt),
+                                 tile_list_scratch_entries(nmt, y.ld_data / 256))
+                      : 0;
   y.Kp = pr ? take(2 * (size_t)y.ld_data * y.ld_pix) : 0;
   y.perm = pr ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
   y.perm2 = pr ? take(sizeof(int32_t) * (size_t)y.ld_data) : 0;
@@ -1045,14 +1048,16 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
       //    row tiles (none when the incremental bound is tighter everywhere):
       //    per-tile maxima of S_hi
       CU(launch_pair_flags(cand, nmt, nnt, pf, s));
-      CU(launch_tile_list(pf, (int)((nmt + 1) / 2), (int)nnt, 4, plist, pcount, s));
+      CU(launch_tile_list(pf, (int)((nmt + 1) / 2), (int)nnt, 4, plist, pcount,
+                            (int32_t*)(c->ws + y.sortH), s));
       CU(launch_tc_bound(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, y.ld_pix, pm,
                          c->status, s, c->tcctl, plist, pcount));
       // 3. both bounds together: the live tiles, listed for the exact pass
       CU(launch_final_live(pm, pf, c->Ub, c->Ua, (double*)(c->ws + y.Lk), nsum_p,
                            bound_div(&c->cfg),
                            nmt, y.ld_data, c->cfg.n_data, live, s));
-      CU(launch_tile_list(live, (int)nmt, (int)nnt, 8, tlist, tcount, s));
+      CU(launch_tile_list(live, (int)nmt, (int)nnt, 8, tlist, tcount, (int32_t*)(c->ws + y.sortH),
+                            s));
       kernels += 6;
     }
     CU(launch_tc_pass1(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, c->cfg.n_data, y.ld_pix,
@@ -1095,7 +1100,7 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     int32_t* tcount = pr ? (int32_t*)(c->ws + y.tcount) + 16 : nullptr;
     if (pruned && !S) {  // recomputed pass 2: the live tiles of this chunk's rows
       CU(launch_tile_list(live + (r0 / 128) * nnt, (int)(crows / 128), (int)nnt, 8, tlist, tcount,
-                          s));
+                          (int32_t*)(c->ws + y.sortH), s));
       kernels++;
     }
     FrameView fv{Kp, cn_p, y.invn_p ? (const float*)(c->ws + y.invn_p) : nullptr,

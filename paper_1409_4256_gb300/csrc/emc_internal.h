@@ -364,8 +364,12 @@ cudaError_t launch_lse_values(const double* m, const double* sm, int64_t n, doub
                               cudaStream_t s);
 
 // ---- pruned pass 1 and the frame order (prune.cu) ----
+// the live tiles (flags live[mt][nt]) as codes mt * n_ntiles + nt in raster
+// order (groups of `group` row tiles) into list, their number into *count;
+// scratch: tile_list_scratch_entries int32
 cudaError_t launch_tile_list(const uint8_t* live, int n_mtiles, int n_ntiles, int group,
-                             int32_t* list, int32_t* count, cudaStream_t s);
+                             int32_t* list, int32_t* count, int32_t* scratch, cudaStream_t s);
+int64_t tile_list_scratch_entries(int64_t n_mtiles, int64_t n_ntiles);
 // entries of the histogram scratch H (int32) of launch_sort_frames; off needs one more (int64)
 int64_t sort_scratch_entries(int64_t n_data, int nbins);
 // new_perm[pos] = perm[s] for the frames s stably sorted by key[s] in [0, nbins)

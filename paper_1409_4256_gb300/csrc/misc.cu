@@ -266,7 +266,9 @@ __global__ void __launch_bounds__(256)
   const uint8_t* lv = live ? live + (k >> 8) : nullptr;
   double mt = -INFINITY;
   int tbest = 0;
+  // (unrolled: the flag and score loads of several tiles in flight)
   if (ok)
+#pragma unroll 4
     for (int64_t t = r; t < n_tiles; t += 8) {
       if (lv && !lv[t * nnt]) continue;
       const double pmv = part_m[t * ld_data + k];
@@ -300,6 +302,7 @@ __global__ void __launch_bounds__(256)
   // this part and the loop runs over every rotation tile
   double acc = 0.0;
   if (ok && Mn != -INFINITY)
+#pragma unroll 4
     for (int64_t t = r; t < n_tiles; t += 8) {
       if (lv && !lv[t * nnt]) continue;
       const double m = part_m[t * ld_data + k] - sh;

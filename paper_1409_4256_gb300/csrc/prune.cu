@@ -37,44 +37,113 @@
 
 namespace emc {
 
-// One CTA: the live tiles in the raster order of the dense kernel (groups of
-// `group` row tiles, frame tiles within a group, row tiles within those) into
-// list, and their number into *count.
-__global__ void __launch_bounds__(1024)
-    tile_list_kernel(const uint8_t* __restrict__ live, int n_mtiles, int n_ntiles, int group,
-                     int32_t* __restrict__ list, int32_t* __restrict__ count) {
-  __shared__ int wsum[32];
-  __shared__ int base;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) base = 0;
-  __syncthreads();
-  const int T = n_mtiles * n_ntiles;
+// The live tiles in the raster order of the dense kernel (groups of `group`
+// row tiles, frame tiles within a group, row tiles within those) into list,
+// and their number into *count. Three launches: per CTA of kListChunk raster
+// positions the number of live tiles; an exclusive scan of those numbers (in
+// place, in the scratch `cnt`, one entry per CTA); per CTA the codes written
+// from its offset on, each thread its kListItems consecutive positions after a
+// block-wide scan of the threads' numbers. The order is the raster order.
+constexpr int kListThreads = 1024;
+constexpr int kListItems = 8;
+constexpr int kListChunk = kListThreads * kListItems;
+
+__device__ __forceinline__ int raster_code(int t, int n_mtiles, int n_ntiles, int group) {
   const int per_group = group * n_ntiles;
-  for (int t0 = 0; t0 < T; t0 += 1024) {
-    const int t = t0 + tid;
-    int code = 0;
-    bool on = false;
-    if (t < T) {
-      const int g = t / per_group, rem = t % per_group;
-      const int gsize = min(group, n_mtiles - g * group);
-      const int nt = rem / gsize, mt = g * group + rem % gsize;
-      code = mt * n_ntiles + nt;
-      on = live[code] != 0;
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, on);
-    if (lane == 0) wsum[wid] = __popc(m);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < 32; w++) {
-      before += w < wid ? wsum[w] : 0;
-      total += wsum[w];
-    }
-    if (on) list[base + before + __popc(m & ((1u << lane) - 1u))] = code;
-    __syncthreads();
-    if (tid == 0) base += total;
-    __syncthreads();
+  const int g = t / per_group, rem = t % per_group;
+  const int gsize = min(group, n_mtiles - g * group);
+  const int nt = rem / gsize, mt = g * group + rem % gsize;
+  return mt * n_ntiles + nt;
+}
+
+// live flags of the thread's positions as bits; their number
+__device__ __forceinline__ unsigned list_bits(const uint8_t* __restrict__ live, int n_mtiles,
+                                              int n_ntiles, int group, int T, int t0) {
+  unsigned bits = 0;
+#pragma unroll
+  for (int q = 0; q < kListItems; q++) {
+    const int t = t0 + q;
+    if (t < T && live[raster_code(t, n_mtiles, n_ntiles, group)]) bits |= 1u << q;
   }
-  if (tid == 0) *count = base;
+  return bits;
+}
+
+// sum over the CTA (every thread gets it); sh: 32 ints
+__device__ __forceinline__ int block_sum(int v, int* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = __reduce_add_sync(0xffffffffu, v);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  int tot = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+  tot = __reduce_add_sync(0xffffffffu, tot);
+  __syncthreads();
+  return tot;
+}
+
+// exclusive prefix over the CTA in thread order; sh: 32 ints
+__device__ __forceinline__ int block_exclusive(int v, int* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) sh[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  const int before = wid > 0 ? sh[wid - 1] : 0;
+  __syncthreads();
+  return before + inc - v;
+}
+
+__global__ void __launch_bounds__(kListThreads)
+    tile_count_kernel(const uint8_t* __restrict__ live, int n_mtiles, int n_ntiles, int group,
+                      int T, int32_t* __restrict__ cnt) {
+  __shared__ int sh[32];
+  const int t0 = blockIdx.x * kListChunk + threadIdx.x * kListItems;
+  const int n = __popc(list_bits(live, n_mtiles, n_ntiles, group, T, t0));
+  const int tot = block_sum(n, sh);
+  if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
+}
+
+// one CTA: cnt[0 .. nb) to exclusive offsets, their total into *count
+__global__ void __launch_bounds__(kListThreads)
+    tile_scan_kernel(int32_t* __restrict__ cnt, int nb, int32_t* __restrict__ count) {
+  __shared__ int sh[32];
+  int carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += kListThreads) {
+    const int b = b0 + threadIdx.x;
+    const int v = b < nb ? cnt[b] : 0;
+    const int ex = block_exclusive(v, sh);
+    const int tot = block_sum(v, sh);
+    if (b < nb) cnt[b] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *count = carry;
+}
+
+__global__ void __launch_bounds__(kListThreads)
+    tile_write_kernel(const uint8_t* __restrict__ live, int n_mtiles, int n_ntiles, int group,
+                      int T, const int32_t* __restrict__ off, int32_t* __restrict__ list) {
+  __shared__ int sh[32];
+  const int t0 = blockIdx.x * kListChunk + threadIdx.x * kListItems;
+  unsigned bits = list_bits(live, n_mtiles, n_ntiles, group, T, t0);
+  int pos = off[blockIdx.x] + block_exclusive(__popc(bits), sh);
+  while (bits) {
+    const int q = __ffs(bits) - 1;
+    bits &= bits - 1;
+    list[pos++] = raster_code(t0 + q, n_mtiles, n_ntiles, group);
+  }
 }
 
 // Counting sort of the frames by key (their best row tile), stable: per chunk
@@ -170,9 +239,17 @@ __global__ void unpermute_lse_kernel(const int32_t* __restrict__ perm, int64_t n
 }
 
 cudaError_t launch_tile_list(const uint8_t* live, int n_mtiles, int n_ntiles, int group,
-                             int32_t* list, int32_t* count, cudaStream_t s) {
-  tile_list_kernel<<<1, 1024, 0, s>>>(live, n_mtiles, n_ntiles, group, list, count);
+                             int32_t* list, int32_t* count, int32_t* scratch, cudaStream_t s) {
+  const int T = n_mtiles * n_ntiles;
+  const int nb = (T + kListChunk - 1) / kListChunk;
+  tile_count_kernel<<<nb, kListThreads, 0, s>>>(live, n_mtiles, n_ntiles, group, T, scratch);
+  tile_scan_kernel<<<1, kListThreads, 0, s>>>(scratch, nb, count);
+  tile_write_kernel<<<nb, kListThreads, 0, s>>>(live, n_mtiles, n_ntiles, group, T, scratch, list);
   return cudaGetLastError();
+}
+
+int64_t tile_list_scratch_entries(int64_t n_mtiles, int64_t n_ntiles) {
+  return (n_mtiles * n_ntiles + kListChunk - 1) / kListChunk;
 }
 
 int64_t sort_scratch_entries(int64_t n_data, int nbins) {
@@ -363,6 +440,7 @@ __global__ void __launch_bounds__(256)
     Lf = __double2float_rd(L - 111.0);
   }
   if (ok && r == 0) Lk[k] = L;
+#pragma unroll 4
   for (int64_t t = r; t < n_mtiles; t += 8) {
     bool on = ok;
     if (ok) {
@@ -418,6 +496,7 @@ __global__ void __launch_bounds__(256)
   const double E = ok ? (double)nsum[k] / (double)div + 1.0 : 0.0;
   double L = ok ? Lk[k] : INFINITY;
   if (ok)
+#pragma unroll 4
     for (int64_t t = r; t < n_mtiles; t += 8) {
       if (!pf[(t >> 1) * nnt + (k >> 8)]) continue;
       const double m = part_m[t * ld_data + k];
@@ -437,6 +516,7 @@ __global__ void __launch_bounds__(256)
     if (r == 0) Lk[k] = L;
   }
   const float Lf = ok ? __double2float_rd(L - 111.0) : INFINITY;  // rounded down: safe side
+#pragma unroll 4
   for (int64_t t = r; t < n_mtiles; t += 8) {
     const bool on = ok && Ub[t * ld_data + k] >= Lf;
     if (__any_sync(0xffffffffu, on) && lane == 0) live[t * nnt + (k >> 8)] = 1;
