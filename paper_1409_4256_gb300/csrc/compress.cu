@@ -70,16 +70,11 @@ __device__ __forceinline__ void reduce_direct(const int* f, const float* t, floa
   }
 }
 
-__device__ __forceinline__ int warp_min(int v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ int warp_max(int v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
+// warp-wide integer minimum and maximum: one redux instruction each (a
+// butterfly of shuffles costs five shuffles, which share the load/store
+// pipe's wavefronts with the box's shared-memory traffic)
+__device__ __forceinline__ int warp_min(int v) { return __reduce_min_sync(0xffffffffu, v); }
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 
 // INTERIOR: all trilinear corners of every pixel lie inside the grid (checked
 // on the host from max |q_i|), so no bounds checks.
