@@ -764,18 +764,32 @@ def adaptive_form(torch, args, cfg, ds, grid, K_dev, stream, ctx, fixed_ms):
             "fixed_d_loglik_per_iteration": fixed_ll}
 
 
-def traffic_for(workload, precision, n_rot, n_data, recompute, phases):
-    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the pass-1
-    tensor-core launches of one iteration, from an ncu capture of this exact
-    configuration (profiles/tc_pass1_update_emc64_dram_bytes.md); None where no
-    capture of the configuration exists."""
-    pruned = bool(phases.get("pass1_bound_pruned_steps"))
-    if (workload == "emc64" and precision == "bf16_split" and n_data == 20000
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# steady iterations, from the one-pass launch-list capture of this exact
+# configuration (emc64, BF16 split, 20000 frames, stored scores; the full-size
+# workload): profiles/launches_emc64_bf16split.md
+MEASURED_TRAFFIC_EMC64 = {
+    # pass 1 of a steady pruned iteration: the increments' product, the
+    # hi-plane bound over the few listed pairs and the exact pass over the
+    # live tiles; dense: the single three-plane launch of the first iteration
+    "pass1_pruned": 0.328e9 + 0.0002e9 + 2.02e9,
+    "pass1_dense": 6.744e9 + 4.249e9,
+    "compress": 0.325e9,
+    "expand": 1.668e9,
+}
+
+
+def traffic_for(workload, precision, n_rot, n_data, recompute, phases, kernel="pass1"):
+    """DRAM bytes per launch (pass 1: per iteration) of one phase's kernels from
+    the ncu capture of this exact configuration; None where no capture of the
+    configuration exists."""
+    if not (workload == "emc64" and precision == "bf16_split" and n_data == 20000
             and n_rot == 50100 and not recompute):
-        # pruned: the bound launch (5.779e9 + 0.065e9) plus the exact launch over the
-        # live tiles (2.138e9 + 0.398e9) of one iteration; dense: the single launch
-        return (5.844e9 + 2.536e9) if pruned else (6.744e9 + 4.249e9)
-    return None
+        return None
+    if kernel == "pass1":
+        pruned = bool(phases.get("pass1_bound_pruned_steps"))
+        return MEASURED_TRAFFIC_EMC64["pass1_pruned" if pruned else "pass1_dense"]
+    return MEASURED_TRAFFIC_EMC64.get(kernel)
 
 
 def pass1_roofline(precision, n_pix, n_rot, n_data, phases, traffic):
@@ -817,8 +831,8 @@ def pass1_roofline(precision, n_pix, n_rot, n_data, phases, traffic):
                  "dense_equivalent_achieved": achieved,
                  "dense_equivalent_frac": achieved / peak,
                  "traffic": traffic,
-                 "traffic_unit": ("bytes per iteration's pass 1 (bound + exact launches)" if pruned
-                                  else "bytes per launch"),
+                 "traffic_unit": ("bytes per iteration's pass 1 (increments, bound and exact "
+                                  "launches)" if pruned else "bytes per launch"),
                  "traffic_source": ("ncu capture of this configuration" if traffic is not None
                                     else "unmeasured for this configuration"),
                  "algorithmic_flops_per_launch": flops, "executed_flops_per_launch": executed,
@@ -849,15 +863,19 @@ def phase_rooflines(precision, n_pix, ld_pix, n_rot, n_data, phases, pass1_roof)
     out["expand"] = {"bound": "hbm", "unit": "GB/s", "achieved": b / (ms * 1e-3) / 1e9,
                      "peak": hbm, "peak_source": f"{pk_src} copy bandwidth", "ms": ms,
                      "algorithmic_bytes": b, "per_unit": f"{planes * esz} B of L per (i, j)",
-                     "limiter": "instruction issue and gather latency (ncu: 64% issue-active, "
-                                "long-scoreboard stalls first, DRAM at 17%)"}
+                     "limiter": "instruction issue and gather latency",
+                     "limiter_source": "ncu, 8192-frame case: 64% issue-active, long-scoreboard "
+                                       "stalls first, DRAM at 17%"}
     ms = phases["ms_compress"]
     b = 4 * n_rot * ld_pix  # Num read
     out["compress"] = {"bound": "hbm", "unit": "GB/s", "achieved": b / (ms * 1e-3) / 1e9,
                        "peak": hbm, "peak_source": f"{pk_src} copy bandwidth", "ms": ms,
                        "algorithmic_bytes": b, "per_unit": "4 B of Num per (i, j)",
-                       "limiter": "L1 / shared-memory wavefronts of the corner merging and "
-                                  "the L2 reductions (ncu: 76% of the wavefront rate, DRAM 2%)"}
+                       "limiter": "L1 / shared-memory (LSU) wavefronts of the corner merging "
+                                  "and the L2 reductions",
+                       "limiter_frac": 0.86,
+                       "limiter_source": "ncu l1tex__data_pipe_lsu_wavefronts, 8192-frame case "
+                                         "(DRAM at 2%, FP64 pipe 70% for the conversions)"}
     out["pass1"] = dict(pass1_roof, ms=phases["ms_loglik"])
     for k in ("expand", "compress"):
         out[k]["frac"] = out[k]["achieved"] / out[k]["peak"]
@@ -975,16 +993,18 @@ def run_ours(args):
                                           ctx.buffer_sizes(n_rot).ld_pix, n_rot, n_data,
                                           phases, roof1)
     # the roofline line is the dominant phase's; the others follow in "rooflines"
+    traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
+                   "(one-pass launch-list capture of this configuration)")
+    for k, name in (("compress", "compress_kernel (c-step, Eq. 2.12): trilinear scatter of the "
+                                 "slices into the grid, corner terms merged in shared memory, "
+                                 "FP64 reductions in L2"),
+                    ("expand", "expand_tile_kernel (e-step, Eq. 2.9): trilinear gather of the "
+                               "slices, log W split into planes, increments of the bound")):
+        tr = traffic_for(args.workload, args.precision, n_rot, n_data, args.recompute, phases, k)
+        rooflines[k].update({"kernel": name, "traffic": tr,
+                             "traffic_source": traffic_src if tr is not None
+                             else "unmeasured for this configuration"})
     roof = dict(rooflines[dominant], phase=dominant)
-    if dominant == "compress":
-        roof.update({"kernel": "compress_kernel (c-step, Eq. 2.12): trilinear scatter of the "
-                               "slices into the grid, corner terms merged in shared memory, "
-                               "FP64 reductions in L2", "traffic": None,
-                     "traffic_source": "unmeasured for this configuration"})
-    elif dominant == "expand":
-        roof.update({"kernel": "expand_tile_kernel (e-step, Eq. 2.9): trilinear gather of "
-                               "the slices, log W split into planes", "traffic": None,
-                     "traffic_source": "unmeasured for this configuration"})
 
     # ---- other precision forms, briefly --------------------------------------
     forms = {args.precision: {"value": value, "ms_per_step": ms, "loglik": loglik}}
