@@ -52,6 +52,16 @@ def test_quat_count_and_generate_match_oracle(libemc, oracle):
     assert np.allclose(wa, 1 / len(wa))
 
 
+def test_library_counts_printed_in_paper(libemc):
+    # the library's own sampling gives every count printed with Eq. 2.7
+    # (tests/golden/eq2_7_rotation_counts.txt)
+    from paper_1409_4256_gb300 import emc
+    from test_oracle_rotations import printed_counts
+    for d, m in printed_counts():
+        assert emc.quat_count(d) == m
+        assert emc.quat_generate(d)[0].shape[0] == m
+
+
 def test_status_strings_and_config_checks(libemc):
     from paper_1409_4256_gb300 import emc
     assert emc.status_string(0) == "ok"

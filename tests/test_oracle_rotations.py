@@ -1,5 +1,7 @@
 """Pins of the oracle's rotation sampling (Eq. 2.7) against closed forms and
 the geometry of SO(3); none of them re-runs the oracle's own formula."""
+import os
+
 import numpy as np
 import pytest
 
@@ -15,9 +17,21 @@ def test_count_closed_form(oracle, n):
     assert quat.shape == (10 * (5 * n ** 3 + n), 4)
 
 
+def printed_counts():
+    """(d, M_rot) pairs printed with Eq. 2.7 (tests/golden)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "eq2_7_rotation_counts.txt")
+    with open(path) as f:
+        rows = [line.split() for line in f if line.strip() and not line.startswith("#")]
+    return [(int(d), int(m)) for d, m in rows]
+
+
 def test_counts_printed_in_paper(oracle):
-    # Eq. 2.7 prints M_rot = [6300, 10860, 25680] for d = [5, 6, 8]
-    for d, m in [(5, 6300), (6, 10860), (8, 25680)]:
+    # every count printed with Eq. 2.7, generated by the oracle's exact
+    # subdivision of the 600-cell (its rotations, not its formula)
+    pairs = printed_counts()
+    assert [d for d, _ in pairs] == [5, 6, 8, 10, 12]
+    for d, m in pairs:
         assert oracle.quat_generate(d)[0].shape[0] == m
 
 
