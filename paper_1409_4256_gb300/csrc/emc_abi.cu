@@ -1058,7 +1058,7 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
                            nmt, y.ld_data, c->cfg.n_data, live, s));
       CU(launch_tile_list(live, (int)nmt, (int)nnt, 8, tlist, tcount, (int32_t*)(c->ws + y.sortH),
                             s));
-      kernels += 6;
+      kernels += 10;  // a tile list is three launches
     }
     CU(launch_tc_pass1(p3, c->cfg.precision, bias, y.rows, Kp, y.ld_data, c->cfg.n_data, y.ld_pix,
                        pm, ps, S, S + y.rows * y.ld_data, nullptr, nullptr, c->status, s,
@@ -1101,7 +1101,7 @@ int emc_iteration(emc_ctx* c, const float* grid_in, float* grid_out, emc_iter_st
     if (pruned && !S) {  // recomputed pass 2: the live tiles of this chunk's rows
       CU(launch_tile_list(live + (r0 / 128) * nnt, (int)(crows / 128), (int)nnt, 8, tlist, tcount,
                           (int32_t*)(c->ws + y.sortH), s));
-      kernels++;
+      kernels += 3;
     }
     FrameView fv{Kp, cn_p, y.invn_p ? (const float*)(c->ws + y.invn_p) : nullptr,
                  pruned && S ? live + (r0 / 128) * nnt : nullptr,
