@@ -765,9 +765,9 @@ def adaptive_form(torch, args, cfg, ds, grid, K_dev, stream, ctx, fixed_ms):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# steady iterations, from the one-pass launch-list capture of this exact
+# steady iterations, from the one-pass ncu launch-list capture of this exact
 # configuration (emc64, BF16 split, 20000 frames, stored scores; the full-size
-# workload): profiles/launches_emc64_bf16split.md
+# workload; its summary is kept with the other profiles)
 MEASURED_TRAFFIC_EMC64 = {
     # pass 1 of a steady pruned iteration: the increments' product, the
     # hi-plane bound over the few listed pairs and the exact pass over the
