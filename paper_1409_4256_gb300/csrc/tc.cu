@@ -62,6 +62,7 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a tile takes tens of microseconds
 constexpr int kSmemBudget = 220 * 1024;
 constexpr int kScratchBytes = 10 * 1024;
+constexpr int kXpLd = 36;  // row stride (floats) of the update's staging block: 16-byte rows, no bank conflicts
 constexpr float kSentinel = -3.0e38f;
 
 // K-block width: 64 elements with 128-byte swizzle, or 32 with 64-byte swizzle
@@ -75,10 +76,14 @@ struct TcCfg {
   static constexpr int B_BYTES = BN * BK * 2;  // 256 x BK BF16
   static constexpr int STAGE = NA * A_BYTES + B_BYTES;
   static constexpr int NACC = (MODE != MODE_UPDATE && NA >= 2) ? 2 : 1;
-  static constexpr int STAGES_RAW = (kSmemBudget - kScratchBytes - 1024 - 256) / STAGE;
+  // update and store: a 32 x 32 staging block per epilogue warp, through which
+  // the output rows leave as whole 128-byte lines (the lanes of a TMEM load hold rows)
+  static constexpr int XPOSE =
+      (MODE == MODE_UPDATE || MODE == MODE_STORE) ? kEpiWarps * 32 * kXpLd * 4 : 0;
+  static constexpr int STAGES_RAW = (kSmemBudget - kScratchBytes - XPOSE - 1024 - 256) / STAGE;
   static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
   static constexpr uint32_t TMEM_COLS = NACC * BN;
-  static constexpr int SMEM = 1024 + STAGES * STAGE + 256 + kScratchBytes;
+  static constexpr int SMEM = 1024 + STAGES * STAGE + 256 + kScratchBytes + XPOSE;
   static constexpr uint32_t IDESC = idesc_f16kind(BM, BN, MODE == MODE_UPDATE ? 1 : 0, F16);
   static_assert(STAGES >= 2, "shared memory too small for two stages");
 };
@@ -194,6 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float2* scratch = reinterpret_cast<float2*>(smem + C::STAGES * C::STAGE + 256);
+  float* xpose = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + 256 + kScratchBytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -381,10 +387,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) mbar_arrive(acc_empty);
         }
         if (MODE == MODE_STORE) {  // C[row][k] for the tile's 32 columns of this step
-          float* dst = a.Num + row * a.ld_data + (int64_t)nt * BN + col0;
+          float* xp = xpose + e * (32 * kXpLd);  // staged as in the update below
 #pragma unroll
           for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<uint4*>(dst + i) = make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
+            *reinterpret_cast<uint4*>(xp + lane * kXpLd + i) =
+                make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
+          __syncwarp();
+          const int64_t row0 = (int64_t)mt * BM + 32 * q;
+          const int64_t k0 = (int64_t)nt * BN + col0;
+#pragma unroll
+          for (int st = 0; st < 8; st++) {
+            const int r = 4 * st + (lane >> 3), c4 = 4 * (lane & 7);
+            const uint4 w = *reinterpret_cast<const uint4*>(xp + r * kXpLd + c4);
+            *reinterpret_cast<uint4*>(a.Num + (row0 + r) * a.ld_data + k0 + c4) = w;
+          }
+          __syncwarp();
           continue;
         }
         if (MODE == MODE_UPDATE) {
@@ -399,15 +416,29 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int i = 0; i < 32; i++)
                 v0[i] = __float_as_uint(__uint_as_float(v0[i]) * (1.0f / kP16Scale));
             }
-            float* dst = a.Num + row * a.ld_pix + n0;
-#pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<uint4*>(dst + i) = make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
             if (a.den && a.n_pix >= n0 && a.n_pix < n0 + 32) {
 #pragma unroll
               for (int i = 0; i < 32; i++)
                 if (n0 + i == a.n_pix) a.den[row] = __uint_as_float(v0[i]);
             }
+            // the lane's row into the warp's staging block, then out by rows:
+            // in each step 8 lanes write one row's 32 columns (128 bytes), four
+            // rows a step (16-byte rows at a stride of 36 floats: each quarter
+            // warp's accesses fall on distinct banks)
+            float* xp = xpose + e * (32 * kXpLd);
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<uint4*>(xp + lane * kXpLd + i) =
+                  make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
+            __syncwarp();
+            const int64_t row0 = (int64_t)mt * BM + 32 * q;
+#pragma unroll
+            for (int st = 0; st < 8; st++) {
+              const int r = 4 * st + (lane >> 3), c4 = 4 * (lane & 7);
+              const uint4 w = *reinterpret_cast<const uint4*>(xp + r * kXpLd + c4);
+              *reinterpret_cast<uint4*>(a.Num + (row0 + r) * a.ld_pix + n0 + c4) = w;
+            }
+            __syncwarp();  // the block is rewritten by the next step
           }
           continue;
         }
