@@ -838,14 +838,19 @@ int do_update(emc_ctx* c, const void* P, int64_t Prows, int64_t nrot, float* Num
     if (is_gauss(&c->cfg) || is_flu(&c->cfg)) {
       // BF16 hi + lo planes of P / phi against the BF16 frames (the Gaussian
       // model's BF16 copy)
+      // (the Gaussian model's P is not sparse: its update stays on the tensor
+      // pipe's rate and keeps every pipeline stage)
       CU(launch_tc_update(pp, EMC_PREC_BF16_SPLIT, rows,
                           Kf ? Kf : (is_gauss(&c->cfg) ? c->Kb2 : c->Kb), y.ld_data, y.ld_pix,
-                          c->cfg.n_pix, Num, nullptr, c->status, s, kbc, kbl, c->tcctl));
+                          c->cfg.n_pix, Num, nullptr, c->status, s, kbc, kbl, c->tcctl,
+                          kbc != nullptr && !is_gauss(&c->cfg)));
       const char* tail = (const char*)P + P_plane_bytes(&c->cfg, Prows, y.ld_data);
       CU(cudaMemcpyAsync(den, tail, sizeof(float) * rows, cudaMemcpyDeviceToDevice, s));
     } else {
+      // over the listed blocks of a sparse P the update is bound by its output
       CU(launch_tc_update(pp, c->cfg.precision, rows, Kf ? Kf : c->Kb, y.ld_data, y.ld_pix,
-                          c->cfg.n_pix, Num, den, c->status, s, kbc, kbl, c->tcctl));
+                          c->cfg.n_pix, Num, den, c->status, s, kbc, kbl, c->tcctl,
+                          kbc != nullptr));
     }
   }
   return EMC_OK;

@@ -260,11 +260,14 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
 // P planes: hi + lo (BF16 split, FP16 split) or hi only (BF16); FP16 planes
 // carry the scale 2^14. den NULL: not written.
 // kb_cnt, kb_list (optional, from launch_kb_lists): contract only the listed
-// 64-frame blocks of each row tile (the others of P are zero)
+// 64-frame blocks of each row tile (the others of P are zero). staged: write
+// Num through a shared-memory staging block, for updates bound by their output
+// (few listed blocks); it costs the two-plane update a pipeline stage
 cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
                              int32_t* status, cudaStream_t s, const int32_t* kb_cnt = nullptr,
-                             const int32_t* kb_list = nullptr, TcCtl ctl = TcCtl{});
+                             const int32_t* kb_list = nullptr, TcCtl ctl = TcCtl{},
+                             bool staged = false);
 int64_t tc_pass1_tiles(int64_t rows);
 // C (float[rows][ld_data]) = A Kb^T over ld_pix columns, A one plane of rows
 // (a multiple of 128) x ld_pix, Kb [ld_data][ld_pix], both BF16 (or both FP16

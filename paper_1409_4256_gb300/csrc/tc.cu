@@ -69,17 +69,20 @@ constexpr float kSentinel = -3.0e38f;
 // for the multi-plane score contractions, whose 64-80 KB stages would
 // otherwise leave room for only two or three in flight (too shallow to hide
 // the load latency). F16: FP16 operands (FP16 split) instead of BF16.
-template <int MODE, int NA, bool F16>
+template <int MODE, int NA, bool F16, bool XP = false>
 struct TcCfg {
   static constexpr int BK = (MODE != MODE_UPDATE && NA >= 2) ? 32 : 64;
   static constexpr int A_BYTES = BM * BK * 2;  // one 128 x BK BF16 plane
   static constexpr int B_BYTES = BN * BK * 2;  // 256 x BK BF16
   static constexpr int STAGE = NA * A_BYTES + B_BYTES;
   static constexpr int NACC = (MODE != MODE_UPDATE && NA >= 2) ? 2 : 1;
-  // update and store: a 32 x 32 staging block per epilogue warp, through which
-  // the output rows leave as whole 128-byte lines (the lanes of a TMEM load hold rows)
+  // XP (update over listed blocks, store): a 32 x 32 staging block per
+  // epilogue warp, through which the output rows leave as whole 128-byte lines
+  // (the lanes of a TMEM load hold rows). It takes a pipeline stage from the
+  // two-plane update, which the output bounds there; the dense update, bound by
+  // the tensor pipe, keeps its stages and stores rows directly.
   static constexpr int XPOSE =
-      (MODE == MODE_UPDATE || MODE == MODE_STORE) ? kEpiWarps * 32 * kXpLd * 4 : 0;
+      (XP && (MODE == MODE_UPDATE || MODE == MODE_STORE)) ? kEpiWarps * 32 * kXpLd * 4 : 0;
   static constexpr int STAGES_RAW = (kSmemBudget - kScratchBytes - XPOSE - 1024 - 256) / STAGE;
   static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
   static constexpr uint32_t TMEM_COLS = NACC * BN;
@@ -180,11 +183,11 @@ __device__ __forceinline__ void fail(volatile int* abort, int32_t* status) {
   set_status(status, EMC_ERR_TIMEOUT);
 }
 
-template <int MODE, int NA, bool F16>
+template <int MODE, int NA, bool F16, bool XP = false>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const TcArgs a) {
-  using C = TcCfg<MODE, NA, F16>;
+  using C = TcCfg<MODE, NA, F16, XP>;
   constexpr bool GAUSS = (MODE == MODE_PASS1 && NA == 3 && F16);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -387,21 +390,29 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) mbar_arrive(acc_empty);
         }
         if (MODE == MODE_STORE) {  // C[row][k] for the tile's 32 columns of this step
-          float* xp = xpose + e * (32 * kXpLd);  // staged as in the update below
+          if (XP) {
+            float* xp = xpose + e * (32 * kXpLd);  // staged as in the update below
 #pragma unroll
-          for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<uint4*>(xp + lane * kXpLd + i) =
-                make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
-          __syncwarp();
-          const int64_t row0 = (int64_t)mt * BM + 32 * q;
-          const int64_t k0 = (int64_t)nt * BN + col0;
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<uint4*>(xp + lane * kXpLd + i) =
+                  make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
+            __syncwarp();
+            const int64_t row0 = (int64_t)mt * BM + 32 * q;
+            const int64_t k0 = (int64_t)nt * BN + col0;
 #pragma unroll
-          for (int st = 0; st < 8; st++) {
-            const int r = 4 * st + (lane >> 3), c4 = 4 * (lane & 7);
-            const uint4 w = *reinterpret_cast<const uint4*>(xp + r * kXpLd + c4);
-            *reinterpret_cast<uint4*>(a.Num + (row0 + r) * a.ld_data + k0 + c4) = w;
+            for (int st = 0; st < 8; st++) {
+              const int r = 4 * st + (lane >> 3), c4 = 4 * (lane & 7);
+              const uint4 w = *reinterpret_cast<const uint4*>(xp + r * kXpLd + c4);
+              *reinterpret_cast<uint4*>(a.Num + (row0 + r) * a.ld_data + k0 + c4) = w;
+            }
+            __syncwarp();
+          } else {
+            float* dst = a.Num + row * a.ld_data + (int64_t)nt * BN + col0;
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<uint4*>(dst + i) =
+                  make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
           }
-          __syncwarp();
           continue;
         }
         if (MODE == MODE_UPDATE) {
@@ -421,24 +432,32 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int i = 0; i < 32; i++)
                 if (n0 + i == a.n_pix) a.den[row] = __uint_as_float(v0[i]);
             }
-            // the lane's row into the warp's staging block, then out by rows:
-            // in each step 8 lanes write one row's 32 columns (128 bytes), four
-            // rows a step (16-byte rows at a stride of 36 floats: each quarter
-            // warp's accesses fall on distinct banks)
-            float* xp = xpose + e * (32 * kXpLd);
+            if (XP) {
+              // the lane's row into the warp's staging block, then out by rows:
+              // in each step 8 lanes write one row's 32 columns (128 bytes), four
+              // rows a step (16-byte rows at a stride of 36 floats: each quarter
+              // warp's accesses fall on distinct banks)
+              float* xp = xpose + e * (32 * kXpLd);
 #pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<uint4*>(xp + lane * kXpLd + i) =
-                  make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
-            __syncwarp();
-            const int64_t row0 = (int64_t)mt * BM + 32 * q;
+              for (int i = 0; i < 32; i += 4)
+                *reinterpret_cast<uint4*>(xp + lane * kXpLd + i) =
+                    make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
+              __syncwarp();
+              const int64_t row0 = (int64_t)mt * BM + 32 * q;
 #pragma unroll
-            for (int st = 0; st < 8; st++) {
-              const int r = 4 * st + (lane >> 3), c4 = 4 * (lane & 7);
-              const uint4 w = *reinterpret_cast<const uint4*>(xp + r * kXpLd + c4);
-              *reinterpret_cast<uint4*>(a.Num + (row0 + r) * a.ld_pix + n0 + c4) = w;
+              for (int st = 0; st < 8; st++) {
+                const int r = 4 * st + (lane >> 3), c4 = 4 * (lane & 7);
+                const uint4 w = *reinterpret_cast<const uint4*>(xp + r * kXpLd + c4);
+                *reinterpret_cast<uint4*>(a.Num + (row0 + r) * a.ld_pix + n0 + c4) = w;
+              }
+              __syncwarp();  // the block is rewritten by the next step
+            } else {
+              float* dst = a.Num + row * a.ld_pix + n0;
+#pragma unroll
+              for (int i = 0; i < 32; i += 4)
+                *reinterpret_cast<uint4*>(dst + i) =
+                    make_uint4(v0[i], v0[i + 1], v0[i + 2], v0[i + 3]);
             }
-            __syncwarp();  // the block is rewritten by the next step
           }
           continue;
         }
@@ -807,12 +826,12 @@ int num_sms() {
   return n > 0 ? n : 148;
 }
 
-template <int MODE, int NA, bool F16>
+template <int MODE, int NA, bool F16, bool XP = false>
 cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs a, cudaStream_t s) {
-  using C = TcCfg<MODE, NA, F16>;
+  using C = TcCfg<MODE, NA, F16, XP>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel<MODE, NA, F16>,
+    cudaError_t e = cudaFuncSetAttribute(tc_kernel<MODE, NA, F16, XP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -821,7 +840,7 @@ cudaError_t launch(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs a, cudaS
   if (T <= 0) return cudaSuccess;
   // a device-side tile list: one persistent CTA per SM (the count is read on the device)
   const int grid = (!a.tile_list && T < num_sms()) ? T : num_sms();
-  tc_kernel<MODE, NA, F16><<<grid, kThreads, C::SMEM, s>>>(mA, mB, a);
+  tc_kernel<MODE, NA, F16, XP><<<grid, kThreads, C::SMEM, s>>>(mA, mB, a);
   return cudaGetLastError();
 }
 
@@ -918,8 +937,8 @@ cudaError_t launch_tc_store(const Planes& A, int64_t rows, const uint16_t* Kb, i
   if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
   a.stall = ctl.stall;
   // A and B of one MMA always share their type: FP16 frames take FP16 increments
-  if (f16) return launch<MODE_STORE, 1, true>(mA, mB, a, s);
-  return launch<MODE_STORE, 1, false>(mA, mB, a, s);
+  if (f16) return launch<MODE_STORE, 1, true, true>(mA, mB, a, s);
+  return launch<MODE_STORE, 1, false, true>(mA, mB, a, s);
 }
 
 cudaError_t launch_tc_pass1(const Planes& L, int precision, const double* bias, int64_t rows,
@@ -1007,7 +1026,7 @@ cudaError_t launch_tc_normalize(const Planes& L, int precision, const double* bi
 cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const uint16_t* Kb,
                              int64_t ld_data, int64_t ld_pix, int64_t n_pix, float* Num, float* den,
                              int32_t* status, cudaStream_t s, const int32_t* kb_cnt,
-                             const int32_t* kb_list, TcCtl ctl) {
+                             const int32_t* kb_list, TcCtl ctl, bool staged) {
   const int nterms = precision == EMC_PREC_BF16 ? 1 : 2;
   const bool f16 = precision == EMC_PREC_FP16_SPLIT;
   CUtensorMap mA, mB;
@@ -1032,6 +1051,11 @@ cudaError_t launch_tc_update(const Planes& P, int precision, int64_t rows, const
   a.status = status;
   if (ctl.wait_ns) a.wait_ns = ctl.wait_ns;
   a.stall = ctl.stall;
+  if (staged) {  // bound by its output: row stores through the staging block
+    if (f16) return launch<MODE_UPDATE, 2, true, true>(mA, mB, a, s);
+    return nterms == 2 ? launch<MODE_UPDATE, 2, false, true>(mA, mB, a, s)
+                       : launch<MODE_UPDATE, 1, false, true>(mA, mB, a, s);
+  }
   if (f16) return launch<MODE_UPDATE, 2, true>(mA, mB, a, s);
   return nterms == 2 ? launch<MODE_UPDATE, 2, false>(mA, mB, a, s)
                      : launch<MODE_UPDATE, 1, false>(mA, mB, a, s);
