@@ -772,8 +772,8 @@ MEASURED_TRAFFIC_EMC64 = {
     # pass 1 of a steady pruned iteration: the increments' product, the
     # hi-plane bound over the few listed pairs and the exact pass over the
     # live tiles; dense: the single three-plane launch of the first iteration
-    "pass1_pruned": 0.328e9 + 0.0002e9 + 2.02e9,
-    "pass1_dense": 6.744e9 + 4.249e9,
+    "pass1_pruned": 0.331e9 + 0.0002e9 + 2.02e9,
+    "pass1_dense": 6.650e9 + 4.247e9,
     "compress": 0.325e9,
     "expand": 1.668e9,
 }
